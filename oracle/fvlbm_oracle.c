@@ -1,0 +1,809 @@
+/*
+ * fvlbm_oracle.c -- plain, slow, double-precision CPU oracle of the time step of the
+ * simplified finite-volume lattice Boltzmann method with k-omega SST and three-stage IMEX
+ * Runge-Kutta (Wang, Zhong, Cao, Zhuo, arXiv 1812.00394, Part II).
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark load this file.  It shares no code, header, table or helper with the CUDA
+ * library; the product path never calls it.
+ *
+ * Each function restates one passage of the paper, cell by cell, in the paper's order and
+ * notation, in FP64, without blocking, fusion or reordering:
+ *   feq()            D2Q9 equilibrium (Sec. 3.1 names D2Q9 of Qian et al.; form of Part I)
+ *   lsq_gradient()   cell gradient of a field (Sec. 3.2 Step 2; method of Part I)
+ *   boundary_f()     face values f_{alpha,bc} on boundary faces (Step 2; Part I)
+ *   convection()     Gamma^a of Eq. (advection)
+ *   imex_step()      Eqs. (imexone), (imextwo) with the tableau of Sec. 3.1, the moment
+ *                    elimination of Eqs. (sumimeximplicitnew) and (fnewstage)
+ *   sst_update()     Sec. 2 (k-omega SST), discretised per Eq. (SSTequint); tau by
+ *                    Eq. (turbtau); coupled once per step before the stages (Step 1)
+ *   forces()         momentum flux through wall faces -> C_D, C_L, Cp (Sec. 4.3 table)
+ *
+ * Where Part I (not available) or the text is silent, the reading taken is stated beside the
+ * code; each is listed with its reason in the design notes of this repository.
+ *
+ * Parity status: f^eq, the IMEX tableau, the moment elimination, the gradient, the flux,
+ * the wall boundary, mass conservation, Couette flow and the SST point functions are pinned
+ * by tests against closed forms and invariants.  The turbulent cases as a whole (inlet,
+ * outlet and far-field readings together with SST transport) have no closed form: parity
+ * unpinned beyond those invariants.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 9
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* D2Q9 velocities e_alpha and weights w_alpha (Part I reading): rest, 4 axis, 4 diagonal. */
+static const double EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const double EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double WQ[Q] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const double CS2 = 1.0 / 3.0; /* c_s^2 of D2Q9 (text under Eq. turbtau) */
+
+/* IMEX tableau, Sec. 3.1: explicit mt[J][k], implicit m[J][k], weights nt[J], n[J]. */
+static const double MT[3][3] = {{0, 0, 0}, {0.5, 0, 0}, {0.5, 0.5, 0}};
+static const double MI[3][3] = {{0.25, 0, 0}, {0, 0.25, 0}, {1.0 / 3, 1.0 / 3, 1.0 / 3}};
+static const double NT[3] = {1.0 / 3, 1.0 / 3, 1.0 / 3};
+static const double NI[3] = {1.0 / 3, 1.0 / 3, 1.0 / 3};
+
+/* SST constants listed after the f2 definition in Sec. 2. */
+static const double A1 = 0.31, BSTAR = 0.09, KAPPA = 0.41;
+static const double SK1 = 0.85, SW1 = 0.5, B1 = 0.075;
+static const double SK2 = 1.0, SW2 = 0.856, B2 = 0.0828;
+
+enum { BC_WALL = 0, BC_INLET = 1, BC_OUTLET = 2, BC_FARFIELD = 3, BC_PERIODIC = 4 };
+
+typedef struct {
+    int nbr;        /* neighbour cell, or -1 on a boundary face */
+    int bedge;      /* boundary edge when nbr == -1 */
+    double nx, ny;  /* unit normal out of this cell */
+    double len;     /* Delta l */
+    double xm, ym;  /* face midpoint */
+    double sx, sy;  /* neighbour centroid seen from this cell = centroid(nbr) + (sx, sy) */
+} oface;
+
+typedef struct oracle {
+    int nc, nb;
+    int *nface;
+    oface *face;                 /* [nc * 4] */
+    double *area, *cx, *cy, *wdist;
+    int *btype, *bcell;
+    double *bval;                /* [nb * 5]: rho_b, u_b, v_b, k_b, omega_b */
+    double *bxm, *bym, *bnx, *bny, *blen;
+    double nu, rho0, dt, uref, lref, alpha_deg;
+    int sst;
+    double *f;                   /* [nc * Q], cell-major */
+    double *rho, *ux, *uy, *k, *om, *nut, *tau;
+    double residual, moment_defect;
+    long steps;
+    /* work arrays */
+    double *fn, *fst, *ga[3], *gc[3], *gradf, *fbc, *feqs, *X;
+    double *gu, *gv, *gk, *gw, *rk, *rw, *f1, *Sabs;
+} oracle;
+
+/* ------------------------------------------------------------------ equilibrium */
+/* f^eq_alpha(rho, u) = w_alpha rho [1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u]: the second-order
+ * D2Q9 equilibrium with c = 1 (Part I; Sec. 3.1 names the lattice). */
+void oracle_feq(double rho, double u, double v, double *feq)
+{
+    double uu = u * u + v * v;
+    for (int a = 0; a < Q; a++) {
+        double eu = EX[a] * u + EY[a] * v;
+        feq[a] = WQ[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+    }
+}
+
+/* rho = sum_alpha f_alpha, rho u = sum_alpha e_alpha f_alpha (collision invariants). */
+static void moments(const double *f, double *rho, double *u, double *v)
+{
+    double r = 0, mx = 0, my = 0;
+    for (int a = 0; a < Q; a++) {
+        r += f[a];
+        mx += EX[a] * f[a];
+        my += EY[a] * f[a];
+    }
+    *rho = r;
+    *u = mx / r;
+    *v = my / r;
+}
+
+/* ------------------------------------------------------------------ mesh */
+typedef struct { long long key; int cell, local; } edge_rec;
+
+static int cmp_edge(const void *a, const void *b)
+{
+    long long x = ((const edge_rec *)a)->key, y = ((const edge_rec *)b)->key;
+    return (x > y) - (x < y);
+}
+
+static long long edge_key(int a, int b)
+{
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    return ((long long)lo << 32) | (long long)(unsigned)hi;
+}
+
+static double seg_dist(double px, double py, double ax, double ay, double bx, double by)
+{
+    double dx = bx - ax, dy = by - ay;
+    double t = ((px - ax) * dx + (py - ay) * dy) / (dx * dx + dy * dy);
+    if (t < 0) t = 0;
+    if (t > 1) t = 1;
+    double qx = ax + t * dx - px, qy = ay + t * dy - py;
+    return sqrt(qx * qx + qy * qy);
+}
+
+static void *xcalloc(size_t n, size_t s) { return calloc(n ? n : 1, s); }
+
+void oracle_destroy(oracle *o);
+
+/* params: [nu, rho0, dt, cfl, sst, uref, lref, alpha_deg] */
+oracle *oracle_create(int n_nodes, const double *xy, int n_cells, const int *cell_ptr,
+                      const int *cell_nodes, int n_bedges, const int *bedge_nodes,
+                      const int *bedge_type, const double *bedge_val, int n_periodic,
+                      const int *periodic_pairs, const double *periodic_shift,
+                      const double *rho_init, const double *u_init, const double *v_init,
+                      const double *k_init, const double *w_init, const double *params)
+{
+    (void)n_nodes;
+    oracle *o = (oracle *)calloc(1, sizeof(oracle));
+    int nc = n_cells, nb = n_bedges;
+    o->nc = nc;
+    o->nb = nb;
+    o->nu = params[0];
+    o->rho0 = params[1];
+    o->dt = params[2];
+    double cfl = params[3];
+    o->sst = params[4] != 0.0;
+    o->uref = params[5];
+    o->lref = params[6];
+    o->alpha_deg = params[7];
+
+    o->nface = (int *)xcalloc(nc, sizeof(int));
+    o->face = (oface *)xcalloc((size_t)nc * 4, sizeof(oface));
+    o->area = (double *)xcalloc(nc, sizeof(double));
+    o->cx = (double *)xcalloc(nc, sizeof(double));
+    o->cy = (double *)xcalloc(nc, sizeof(double));
+    o->wdist = (double *)xcalloc(nc, sizeof(double));
+    o->btype = (int *)xcalloc(nb, sizeof(int));
+    o->bcell = (int *)xcalloc(nb, sizeof(int));
+    o->bval = (double *)xcalloc((size_t)nb * 5, sizeof(double));
+    o->bxm = (double *)xcalloc(nb, sizeof(double));
+    o->bym = (double *)xcalloc(nb, sizeof(double));
+    o->bnx = (double *)xcalloc(nb, sizeof(double));
+    o->bny = (double *)xcalloc(nb, sizeof(double));
+    o->blen = (double *)xcalloc(nb, sizeof(double));
+    memcpy(o->btype, bedge_type, sizeof(int) * (size_t)nb);
+    memcpy(o->bval, bedge_val, sizeof(double) * 5 * (size_t)nb);
+
+    /* cell area and centroid (polygon formulas, taken relative to the first node) */
+    for (int i = 0; i < nc; i++) {
+        int p0 = cell_ptr[i], nv = cell_ptr[i + 1] - p0;
+        double x0 = xy[2 * cell_nodes[p0]], y0 = xy[2 * cell_nodes[p0] + 1];
+        double A2 = 0, sx = 0, sy = 0;
+        for (int l = 0; l < nv; l++) {
+            int a = cell_nodes[p0 + l], b = cell_nodes[p0 + (l + 1) % nv];
+            double xa = xy[2 * a] - x0, ya = xy[2 * a + 1] - y0;
+            double xb = xy[2 * b] - x0, yb = xy[2 * b + 1] - y0;
+            double cr = xa * yb - xb * ya;
+            A2 += cr;
+            sx += (xa + xb) * cr;
+            sy += (ya + yb) * cr;
+        }
+        o->area[i] = 0.5 * A2;
+        o->cx[i] = x0 + sx / (3.0 * A2);
+        o->cy[i] = y0 + sy / (3.0 * A2);
+        o->nface[i] = nv;
+    }
+
+    /* faces: every cell edge a->b (counter-clockwise) has outward normal (dy, -dx)/|d| */
+    long ne = cell_ptr[nc];
+    edge_rec *er = (edge_rec *)xcalloc((size_t)ne, sizeof(edge_rec));
+    for (int i = 0; i < nc; i++) {
+        int p0 = cell_ptr[i], nv = cell_ptr[i + 1] - p0;
+        for (int l = 0; l < nv; l++) {
+            int a = cell_nodes[p0 + l], b = cell_nodes[p0 + (l + 1) % nv];
+            double dx = xy[2 * b] - xy[2 * a], dy = xy[2 * b + 1] - xy[2 * a + 1];
+            double len = sqrt(dx * dx + dy * dy);
+            oface *F = &o->face[4 * i + l];
+            F->nbr = -1;
+            F->bedge = -1;
+            F->nx = dy / len;
+            F->ny = -dx / len;
+            F->len = len;
+            F->xm = 0.5 * (xy[2 * a] + xy[2 * b]);
+            F->ym = 0.5 * (xy[2 * a + 1] + xy[2 * b + 1]);
+            er[p0 + l].key = edge_key(a, b);
+            er[p0 + l].cell = i;
+            er[p0 + l].local = l;
+        }
+    }
+    qsort(er, (size_t)ne, sizeof(edge_rec), cmp_edge);
+    for (long e = 0; e + 1 < ne; e++) {
+        if (er[e].key == er[e + 1].key) {
+            o->face[4 * er[e].cell + er[e].local].nbr = er[e + 1].cell;
+            o->face[4 * er[e + 1].cell + er[e + 1].local].nbr = er[e].cell;
+            e++;
+        }
+    }
+    /* boundary edges: find the owning cell face by key */
+    int ok = 1;
+    for (int b = 0; b < nb; b++) {
+        long long key = edge_key(bedge_nodes[2 * b], bedge_nodes[2 * b + 1]);
+        long lo = 0, hi = ne - 1, hit = -1;
+        while (lo <= hi) {
+            long mid = (lo + hi) / 2;
+            if (er[mid].key == key) { hit = mid; break; }
+            if (er[mid].key < key) lo = mid + 1; else hi = mid - 1;
+        }
+        if (hit < 0) { ok = 0; break; }
+        oface *F = &o->face[4 * er[hit].cell + er[hit].local];
+        if (F->nbr >= 0) { ok = 0; break; }
+        F->bedge = b;
+        o->bcell[b] = er[hit].cell;
+        o->bxm[b] = F->xm;
+        o->bym[b] = F->ym;
+        o->bnx[b] = F->nx;
+        o->bny[b] = F->ny;
+        o->blen[b] = F->len;
+    }
+    /* periodic pairs: edge b is edge a translated by s; glue the two owner cells */
+    for (int p = 0; p < n_periodic && ok; p++) {
+        int ea = periodic_pairs[2 * p], eb = periodic_pairs[2 * p + 1];
+        double sx = periodic_shift[2 * p], sy = periodic_shift[2 * p + 1];
+        int ca = o->bcell[ea], cb = o->bcell[eb];
+        oface *Fa = NULL, *Fb = NULL;
+        for (int l = 0; l < o->nface[ca]; l++)
+            if (o->face[4 * ca + l].bedge == ea) Fa = &o->face[4 * ca + l];
+        for (int l = 0; l < o->nface[cb]; l++)
+            if (o->face[4 * cb + l].bedge == eb) Fb = &o->face[4 * cb + l];
+        if (!Fa || !Fb) { ok = 0; break; }
+        Fa->nbr = cb; Fa->bedge = -1; Fa->sx = -sx; Fa->sy = -sy;
+        Fb->nbr = ca; Fb->bedge = -1; Fb->sx = sx; Fb->sy = sy;
+        Fb->nx = -Fa->nx; Fb->ny = -Fa->ny; Fb->len = Fa->len;
+        o->btype[ea] = o->btype[eb] = BC_PERIODIC;
+    }
+    free(er);
+    for (int i = 0; i < nc && ok; i++)
+        for (int l = 0; l < o->nface[i]; l++)
+            if (o->face[4 * i + l].nbr < 0 && o->face[4 * i + l].bedge < 0) ok = 0;
+    if (!ok) { oracle_destroy(o); return NULL; }
+
+    /* wall distance d of Sec. 2: centroid to the nearest wall segment */
+    for (int i = 0; i < nc; i++) {
+        double d = 1e30;
+        for (int b = 0; b < nb; b++) {
+            if (o->btype[b] != BC_WALL) continue;
+            int a0 = bedge_nodes[2 * b], a1 = bedge_nodes[2 * b + 1];
+            double s = seg_dist(o->cx[i], o->cy[i], xy[2 * a0], xy[2 * a0 + 1], xy[2 * a1],
+                                xy[2 * a1 + 1]);
+            if (s < d) d = s;
+        }
+        o->wdist[i] = d;
+    }
+
+    /* state and work arrays */
+    size_t nq = (size_t)nc * Q;
+    o->f = (double *)xcalloc(nq, sizeof(double));
+    o->fn = (double *)xcalloc(nq, sizeof(double));
+    o->fst = (double *)xcalloc(nq, sizeof(double));
+    o->feqs = (double *)xcalloc(nq, sizeof(double));
+    o->X = (double *)xcalloc(nq, sizeof(double));
+    for (int J = 0; J < 3; J++) {
+        o->ga[J] = (double *)xcalloc(nq, sizeof(double));
+        o->gc[J] = (double *)xcalloc(nq, sizeof(double));
+    }
+    o->gradf = (double *)xcalloc(nq * 2, sizeof(double));
+    o->fbc = (double *)xcalloc((size_t)nb * Q, sizeof(double));
+    o->rho = (double *)xcalloc(nc, sizeof(double));
+    o->ux = (double *)xcalloc(nc, sizeof(double));
+    o->uy = (double *)xcalloc(nc, sizeof(double));
+    o->k = (double *)xcalloc(nc, sizeof(double));
+    o->om = (double *)xcalloc(nc, sizeof(double));
+    o->nut = (double *)xcalloc(nc, sizeof(double));
+    o->tau = (double *)xcalloc(nc, sizeof(double));
+    o->gu = (double *)xcalloc((size_t)nc * 2, sizeof(double));
+    o->gv = (double *)xcalloc((size_t)nc * 2, sizeof(double));
+    o->gk = (double *)xcalloc((size_t)nc * 2, sizeof(double));
+    o->gw = (double *)xcalloc((size_t)nc * 2, sizeof(double));
+    o->rk = (double *)xcalloc(nc, sizeof(double));
+    o->rw = (double *)xcalloc(nc, sizeof(double));
+    o->f1 = (double *)xcalloc(nc, sizeof(double));
+    o->Sabs = (double *)xcalloc(nc, sizeof(double));
+
+    /* Step 0: f = f^eq(rho, u); k, omega initial; nu_t^0 = k / omega; tau from Eq. turbtau */
+    for (int i = 0; i < nc; i++) {
+        double r = rho_init ? rho_init[i] : o->rho0;
+        double u = u_init ? u_init[i] : 0.0, v = v_init ? v_init[i] : 0.0;
+        oracle_feq(r, u, v, &o->f[(size_t)i * Q]);
+        moments(&o->f[(size_t)i * Q], &o->rho[i], &o->ux[i], &o->uy[i]);
+        o->k[i] = k_init ? k_init[i] : 0.0;
+        o->om[i] = w_init ? w_init[i] : 1.0;
+        o->nut[i] = o->sst ? o->k[i] / o->om[i] : 0.0;
+        o->tau[i] = (o->nu + o->nut[i]) / CS2;
+    }
+
+    /* time step: given, or CFL * (forward-Euler upwind limit) when dt <= 0 */
+    if (o->dt <= 0.0) {
+        double lim = 0.0;
+        for (int i = 0; i < nc; i++)
+            for (int a = 0; a < Q; a++) {
+                double s = 0.0;
+                for (int l = 0; l < o->nface[i]; l++) {
+                    const oface *F = &o->face[4 * i + l];
+                    double en = EX[a] * F->nx + EY[a] * F->ny;
+                    if (en > 0) s += en * F->len;
+                }
+                s /= o->area[i];
+                if (s > lim) lim = s;
+            }
+        o->dt = cfl / lim;
+    }
+    return o;
+}
+
+void oracle_destroy(oracle *o)
+{
+    if (!o) return;
+    free(o->nface); free(o->face); free(o->area); free(o->cx); free(o->cy); free(o->wdist);
+    free(o->btype); free(o->bcell); free(o->bval);
+    free(o->bxm); free(o->bym); free(o->bnx); free(o->bny); free(o->blen);
+    free(o->f); free(o->fn); free(o->fst); free(o->feqs); free(o->X);
+    for (int J = 0; J < 3; J++) { free(o->ga[J]); free(o->gc[J]); }
+    free(o->gradf); free(o->fbc);
+    free(o->rho); free(o->ux); free(o->uy); free(o->k); free(o->om); free(o->nut); free(o->tau);
+    free(o->gu); free(o->gv); free(o->gk); free(o->gw); free(o->rk); free(o->rw);
+    free(o->f1); free(o->Sabs);
+    free(o);
+}
+
+/* ------------------------------------------------------------------ gradient */
+/* Unweighted least-squares gradient (Part I method, reading): data points are the
+ * neighbour centroids (periodic ones shifted) with their cell values and, on boundary faces,
+ * the face midpoint with the boundary value.  g = M^{-1} sum_m d_m (phi_m - phi_i),
+ * M = sum_m d_m d_m^T.  phi is strided (value of cell i at phi[i*stride]). */
+static void lsq_gradient(const oracle *o, int i, const double *phi, int stride,
+                         const double *phib, int bstride, double *gx, double *gy)
+{
+    double mxx = 0, mxy = 0, myy = 0, bx = 0, by = 0;
+    double pi = phi[(size_t)i * stride];
+    for (int l = 0; l < o->nface[i]; l++) {
+        const oface *F = &o->face[4 * i + l];
+        double dx, dy, dp;
+        if (F->nbr >= 0) {
+            dx = o->cx[F->nbr] + F->sx - o->cx[i];
+            dy = o->cy[F->nbr] + F->sy - o->cy[i];
+            dp = phi[(size_t)F->nbr * stride] - pi;
+        } else {
+            dx = F->xm - o->cx[i];
+            dy = F->ym - o->cy[i];
+            dp = phib[(size_t)F->bedge * bstride] - pi;
+        }
+        mxx += dx * dx;
+        mxy += dx * dy;
+        myy += dy * dy;
+        bx += dx * dp;
+        by += dy * dp;
+    }
+    double det = mxx * myy - mxy * mxy;
+    *gx = (myy * bx - mxy * by) / det;
+    *gy = (mxx * by - mxy * bx) / det;
+}
+
+/* ------------------------------------------------------------------ boundary values */
+/* f_{alpha,bc} on boundary faces from the owner cell P (Part I not available; readings):
+ *   wall / inlet:  f^eq(rho_P, u_b) + [f_P - f^eq(rho_P, u_P)]   (non-equilibrium extrapolation)
+ *   outlet:        f^eq(rho_b, u_P) + [f_P - f^eq(rho_P, u_P)]
+ *   far field:     f^eq(rho_b, u_b) where e.n < 0 (incoming), f_P where e.n >= 0 (outgoing) */
+static void boundary_f(const oracle *o, const double *f, double *fbc)
+{
+    for (int b = 0; b < o->nb; b++) {
+        int t = o->btype[b];
+        if (t == BC_PERIODIC) continue;
+        int P = o->bcell[b];
+        const double *fp = &f[(size_t)P * Q];
+        const double *bv = &o->bval[5 * (size_t)b];
+        double *out = &fbc[(size_t)b * Q];
+        double rP, uP, vP, eqP[Q], eqB[Q];
+        moments(fp, &rP, &uP, &vP);
+        oracle_feq(rP, uP, vP, eqP);
+        if (t == BC_WALL || t == BC_INLET) {
+            oracle_feq(rP, bv[1], bv[2], eqB);
+            for (int a = 0; a < Q; a++) out[a] = eqB[a] + (fp[a] - eqP[a]);
+        } else if (t == BC_OUTLET) {
+            oracle_feq(bv[0], uP, vP, eqB);
+            for (int a = 0; a < Q; a++) out[a] = eqB[a] + (fp[a] - eqP[a]);
+        } else { /* BC_FARFIELD */
+            oracle_feq(bv[0], bv[1], bv[2], eqB);
+            for (int a = 0; a < Q; a++) {
+                double en = EX[a] * o->bnx[b] + EY[a] * o->bny[b];
+                out[a] = en < 0.0 ? eqB[a] : fp[a];
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ convection */
+/* Gamma^a_alpha = -(1/A) sum_m [(e_alpha . n) f_{alpha,bc} Delta l]_m, Eq. (advection).
+ * Interior face values: upwind by the sign of e_alpha . n (n out of this cell), linear
+ * reconstruction f + grad f . (x_face - x_cell) from the upwind cell (Part I reading).
+ * Boundary faces use boundary_f(). */
+static void convection(oracle *o, const double *f, double *ga)
+{
+    int nc = o->nc;
+    boundary_f(o, f, o->fbc);
+    for (int i = 0; i < nc; i++)
+        for (int a = 0; a < Q; a++) {
+            double gx, gy;
+            lsq_gradient(o, i, f + a, Q, o->fbc + a, Q, &gx, &gy);
+            o->gradf[((size_t)i * Q + a) * 2] = gx;
+            o->gradf[((size_t)i * Q + a) * 2 + 1] = gy;
+        }
+    for (int i = 0; i < nc; i++) {
+        for (int a = 0; a < Q; a++) {
+            double sum = 0.0;
+            for (int l = 0; l < o->nface[i]; l++) {
+                const oface *F = &o->face[4 * i + l];
+                double en = EX[a] * F->nx + EY[a] * F->ny;
+                double fv;
+                if (F->nbr < 0) {
+                    fv = o->fbc[(size_t)F->bedge * Q + a];
+                } else if (en >= 0.0) {
+                    const double *g = &o->gradf[((size_t)i * Q + a) * 2];
+                    fv = f[(size_t)i * Q + a] + g[0] * (F->xm - o->cx[i]) + g[1] * (F->ym - o->cy[i]);
+                } else {
+                    int j = F->nbr;
+                    const double *g = &o->gradf[((size_t)j * Q + a) * 2];
+                    fv = f[(size_t)j * Q + a] + g[0] * (F->xm - (o->cx[j] + F->sx)) +
+                         g[1] * (F->ym - (o->cy[j] + F->sy));
+                }
+                sum += en * fv * F->len;
+            }
+            ga[(size_t)i * Q + a] = -sum / o->area[i];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ SST */
+/* Point functions of Sec. 2 in kinematic form (rho divided out; reading):
+ * CD_kw = max(2 sigma_w2 / omega grad k . grad omega, 1e-20);
+ * arg1 = min(max(sqrt(k)/(0.09 omega d), 500 nu/(omega d^2)), 4 sigma_w2 k/(CD_kw d^2));
+ * f1 = tanh(arg1^4); arg2 = max(2 sqrt(k)/(0.09 omega d), 500 nu/(omega d^2)); f2 = tanh(arg2^2);
+ * nu_t = a1 k / max(a1 omega, S f2). */
+static double sst_cdkw(double w, double gkx, double gky, double gwx, double gwy)
+{
+    double c = 2.0 * SW2 / w * (gkx * gwx + gky * gwy);
+    return c > 1e-20 ? c : 1e-20;
+}
+
+static double sst_f1(double k, double w, double d, double nu, double cdkw)
+{
+    double a = sqrt(k) / (BSTAR * w * d);
+    double b = 500.0 * nu / (w * d * d);
+    double c = 4.0 * SW2 * k / (cdkw * d * d);
+    double arg1 = fmin(fmax(a, b), c);
+    return tanh(arg1 * arg1 * arg1 * arg1);
+}
+
+static double sst_f2(double k, double w, double d, double nu)
+{
+    double arg2 = fmax(2.0 * sqrt(k) / (BSTAR * w * d), 500.0 * nu / (w * d * d));
+    return tanh(arg2 * arg2);
+}
+
+static double sst_nut(double k, double w, double S, double f2)
+{
+    return A1 * k / fmax(A1 * w, S * f2);
+}
+
+/* out = {f1, f2, CD_kw, nu_t} at one point (for tests). */
+void oracle_sst_point(double k, double w, double d, double gkx, double gky, double gwx,
+                      double gwy, double S, double nu, double *out)
+{
+    double cd = sst_cdkw(w, gkx, gky, gwx, gwy);
+    double f2 = sst_f2(k, w, d, nu);
+    out[0] = sst_f1(k, w, d, nu, cd);
+    out[1] = f2;
+    out[2] = cd;
+    out[3] = sst_nut(k, w, S, f2);
+}
+
+/* Boundary values of u, v, k, omega for the SST gradients and face fluxes (Menter 1994
+ * boundary conditions, Sec. 3.2; readings): wall k = 0, omega = 60 nu / (beta1 d^2) with d
+ * the wall cell's wall distance; inlet / far field k_b, omega_b given; outlet zero gradient.
+ * Velocity: wall / inlet / far field u_b; outlet the cell velocity. */
+static void sst_boundary(const oracle *o, int b, double *ub, double *vb, double *kb, double *wb)
+{
+    int P = o->bcell[b];
+    const double *bv = &o->bval[5 * (size_t)b];
+    switch (o->btype[b]) {
+    case BC_WALL:
+        *ub = bv[1]; *vb = bv[2]; *kb = 0.0;
+        *wb = 60.0 * o->nu / (B1 * o->wdist[P] * o->wdist[P]);
+        break;
+    case BC_OUTLET:
+        *ub = o->ux[P]; *vb = o->uy[P]; *kb = o->k[P]; *wb = o->om[P];
+        break;
+    default: /* inlet, far field */
+        *ub = bv[1]; *vb = bv[2]; *kb = bv[3]; *wb = bv[4];
+        break;
+    }
+}
+
+/* One SST update of size dt from the macros at t^n (Step 1; readings): explicit face
+ * convection (second-order upwind with the mean face velocity) and central diffusion with
+ * the mean face coefficient, explicit production and cross diffusion, point-implicit
+ * destruction, then f2, nu_t and tau = (nu + nu_t) / cs^2 (Eq. turbtau). */
+static void sst_update(oracle *o)
+{
+    int nc = o->nc, nb = o->nb;
+    double *ubc = (double *)xcalloc((size_t)nb * 4, sizeof(double));
+    for (int b = 0; b < nb; b++)
+        if (o->btype[b] != BC_PERIODIC)
+            sst_boundary(o, b, &ubc[4 * b], &ubc[4 * b + 1], &ubc[4 * b + 2], &ubc[4 * b + 3]);
+    for (int i = 0; i < nc; i++) {
+        lsq_gradient(o, i, o->ux, 1, ubc + 0, 4, &o->gu[2 * i], &o->gu[2 * i + 1]);
+        lsq_gradient(o, i, o->uy, 1, ubc + 1, 4, &o->gv[2 * i], &o->gv[2 * i + 1]);
+        lsq_gradient(o, i, o->k, 1, ubc + 2, 4, &o->gk[2 * i], &o->gk[2 * i + 1]);
+        lsq_gradient(o, i, o->om, 1, ubc + 3, 4, &o->gw[2 * i], &o->gw[2 * i + 1]);
+    }
+    double *sk = (double *)xcalloc(nc, sizeof(double));
+    double *sw = (double *)xcalloc(nc, sizeof(double));
+    double *SS = (double *)xcalloc(nc, sizeof(double));
+    double *dv = (double *)xcalloc(nc, sizeof(double));
+    for (int i = 0; i < nc; i++) {
+        double s11 = o->gu[2 * i], s22 = o->gv[2 * i + 1];
+        double s12 = 0.5 * (o->gu[2 * i + 1] + o->gv[2 * i]);
+        SS[i] = s11 * s11 + s22 * s22 + 2.0 * s12 * s12; /* S_ij S_ij */
+        dv[i] = s11 + s22;
+        o->Sabs[i] = sqrt(2.0 * SS[i]);
+        double cd = sst_cdkw(o->om[i], o->gk[2 * i], o->gk[2 * i + 1], o->gw[2 * i], o->gw[2 * i + 1]);
+        o->f1[i] = sst_f1(o->k[i], o->om[i], o->wdist[i], o->nu, cd);
+        sk[i] = o->f1[i] * SK1 + (1.0 - o->f1[i]) * SK2;
+        sw[i] = o->f1[i] * SW1 + (1.0 - o->f1[i]) * SW2;
+    }
+    for (int i = 0; i < nc; i++) {
+        double ck = 0, cw = 0, dk = 0, dw = 0;
+        for (int l = 0; l < o->nface[i]; l++) {
+            const oface *F = &o->face[4 * i + l];
+            double uf, vf, kup, wup, rx = F->xm - o->cx[i], ry = F->ym - o->cy[i];
+            double kin = o->k[i] + o->gk[2 * i] * rx + o->gk[2 * i + 1] * ry;
+            double win = o->om[i] + o->gw[2 * i] * rx + o->gw[2 * i + 1] * ry;
+            if (F->nbr >= 0) {
+                int j = F->nbr;
+                double xj = o->cx[j] + F->sx, yj = o->cy[j] + F->sy;
+                uf = 0.5 * (o->ux[i] + o->ux[j]);
+                vf = 0.5 * (o->uy[i] + o->uy[j]);
+                double un = uf * F->nx + vf * F->ny;
+                double sx = F->xm - xj, sy = F->ym - yj;
+                kup = un >= 0.0 ? kin : o->k[j] + o->gk[2 * j] * sx + o->gk[2 * j + 1] * sy;
+                wup = un >= 0.0 ? win : o->om[j] + o->gw[2 * j] * sx + o->gw[2 * j + 1] * sy;
+                double dist = sqrt((xj - o->cx[i]) * (xj - o->cx[i]) + (yj - o->cy[i]) * (yj - o->cy[i]));
+                double gkf = 0.5 * ((o->nu + sk[i] * o->nut[i]) + (o->nu + sk[j] * o->nut[j]));
+                double gwf = 0.5 * ((o->nu + sw[i] * o->nut[i]) + (o->nu + sw[j] * o->nut[j]));
+                ck += un * kup * F->len;
+                cw += un * wup * F->len;
+                dk += gkf * (o->k[j] - o->k[i]) / dist * F->len;
+                dw += gwf * (o->om[j] - o->om[i]) / dist * F->len;
+            } else {
+                const double *ub = &ubc[4 * F->bedge];
+                double un = ub[0] * F->nx + ub[1] * F->ny;
+                kup = un >= 0.0 ? kin : ub[2];
+                wup = un >= 0.0 ? win : ub[3];
+                double dist = sqrt(rx * rx + ry * ry);
+                ck += un * kup * F->len;
+                cw += un * wup * F->len;
+                dk += (o->nu + sk[i] * o->nut[i]) * (ub[2] - o->k[i]) / dist * F->len;
+                dw += (o->nu + sw[i] * o->nut[i]) * (ub[3] - o->om[i]) / dist * F->len;
+            }
+        }
+        double f1 = o->f1[i];
+        double gam = f1 * (B1 / BSTAR - SW1 * KAPPA * KAPPA / sqrt(BSTAR)) +
+                     (1.0 - f1) * (B2 / BSTAR - SW2 * KAPPA * KAPPA / sqrt(BSTAR));
+        /* production P / rho = nu_t (2 S_ij S_ij - 2/3 (div u)^2) - 2/3 k div u */
+        double pk = o->nut[i] * (2.0 * SS[i] - 2.0 / 3.0 * dv[i] * dv[i]) - 2.0 / 3.0 * o->k[i] * dv[i];
+        /* gamma P / nu_t, with the k div u / nu_t part taken as 0 when nu_t = 0 */
+        double pw = gam * (2.0 * SS[i] - 2.0 / 3.0 * dv[i] * dv[i]);
+        if (o->nut[i] > 0.0) pw -= 2.0 / 3.0 * gam * o->k[i] * dv[i] / o->nut[i];
+        double cross = 2.0 * (1.0 - f1) * SW2 / o->om[i] *
+                       (o->gk[2 * i] * o->gw[2 * i] + o->gk[2 * i + 1] * o->gw[2 * i + 1]);
+        o->rk[i] = (-ck + dk) / o->area[i] + pk;
+        o->rw[i] = (-cw + dw) / o->area[i] + pw + cross;
+    }
+    double wmin = 1e-12 * o->uref / o->lref;
+    for (int i = 0; i < nc; i++) {
+        double f1 = o->f1[i];
+        double beta = f1 * B1 + (1.0 - f1) * B2;
+        double kn = (o->k[i] + o->dt * o->rk[i]) / (1.0 + o->dt * BSTAR * o->om[i]);
+        double wn = (o->om[i] + o->dt * o->rw[i]) / (1.0 + o->dt * beta * o->om[i]);
+        o->k[i] = kn > 0.0 ? kn : 0.0;
+        o->om[i] = wn > wmin ? wn : wmin;
+    }
+    for (int i = 0; i < nc; i++) {
+        double f2 = sst_f2(o->k[i], o->om[i], o->wdist[i], o->nu);
+        o->nut[i] = sst_nut(o->k[i], o->om[i], o->Sabs[i], f2);
+        o->tau[i] = (o->nu + o->nut[i]) / CS2;
+    }
+    free(ubc); free(sk); free(sw); free(SS); free(dv);
+}
+
+/* ------------------------------------------------------------------ IMEX step */
+/* One time step, Steps 1-7 of Sec. 3.2.  Stage J (J = 1, 2, 3):
+ *   rho^(J), (rho u)^(J) = moments of f^n + dt sum_{k<J} mt_Jk Gamma^a(k)   Eq. (sumimeximplicitnew)
+ *   f^(J) = [f^n + dt sum_{k<J} (mt_Jk Gamma^a(k) + m_Jk Gamma^c(k)) + dt/tau m_JJ f^eq(J)]
+ *           / (1 + dt/tau m_JJ)                                           Eq. (fnewstage)
+ *   Gamma^c(J) = -(f^(J) - f^eq(J)) / tau                                 Eq. (collision)
+ *   Gamma^a(J) = convection of f^(J)                                      Eq. (advection)
+ * then f^{n+1} = f^n + dt sum nt_J Gamma^a(J) + dt sum n_J Gamma^c(J)      Eq. (imextwo). */
+static int imex_step(oracle *o)
+{
+    int nc = o->nc;
+    size_t nq = (size_t)nc * Q;
+    double dt = o->dt;
+    if (o->sst) sst_update(o); /* Step 1 */
+    else
+        for (int i = 0; i < nc; i++) o->tau[i] = o->nu / CS2;
+    memcpy(o->fn, o->f, nq * sizeof(double));
+    double defect = 0.0;
+    for (int J = 0; J < 3; J++) {
+        for (int i = 0; i < nc; i++) {
+            double tau = o->tau[i];
+            double *X = &o->X[(size_t)i * Q];
+            const double *fn = &o->fn[(size_t)i * Q];
+            for (int a = 0; a < Q; a++) {
+                double s = fn[a];
+                for (int k = 0; k < J; k++) s += dt * MT[J][k] * o->ga[k][(size_t)i * Q + a];
+                X[a] = s;
+            }
+            double r, u, v, eq[Q];
+            moments(X, &r, &u, &v);
+            oracle_feq(r, u, v, eq);
+            double zJ = dt / tau * MI[J][J];
+            double *fs = &o->fst[(size_t)i * Q];
+            for (int a = 0; a < Q; a++) {
+                double num = fn[a];
+                for (int k = 0; k < J; k++)
+                    num += dt * (MT[J][k] * o->ga[k][(size_t)i * Q + a] +
+                                 MI[J][k] * o->gc[k][(size_t)i * Q + a]);
+                num += zJ * eq[a];
+                fs[a] = num / (1.0 + zJ);
+                o->gc[J][(size_t)i * Q + a] = -(fs[a] - eq[a]) / tau;
+            }
+            /* moment elimination check: sum f^(J) psi must equal the moments of X */
+            double r2, u2, v2;
+            moments(fs, &r2, &u2, &v2);
+            double dd = fabs(r2 - r) + fabs(r2 * u2 - r * u) + fabs(r2 * v2 - r * v);
+            if (dd > defect) defect = dd;
+        }
+        convection(o, o->fst, o->ga[J]); /* Step 2 for the next stage / the final update */
+    }
+    for (size_t q = 0; q < nq; q++) {
+        double s = o->fn[q];
+        for (int J = 0; J < 3; J++) s += dt * (NT[J] * o->ga[J][q] + NI[J] * o->gc[J][q]);
+        o->f[q] = s;
+    }
+    o->moment_defect = defect;
+    /* Step 7: macros; velocity residual e (reading: relative L2 change of u over the step) */
+    double num = 0.0, den = 0.0;
+    int bad = 0;
+    for (int i = 0; i < nc; i++) {
+        double r, u, v;
+        moments(&o->f[(size_t)i * Q], &r, &u, &v);
+        num += (u - o->ux[i]) * (u - o->ux[i]) + (v - o->uy[i]) * (v - o->uy[i]);
+        den += u * u + v * v;
+        o->rho[i] = r;
+        o->ux[i] = u;
+        o->uy[i] = v;
+        if (!(r == r) || !(u == u) || !(v == v)) bad = 1;
+    }
+    o->residual = den > 0.0 ? sqrt(num) / sqrt(den) : sqrt(num);
+    o->steps++;
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------ public entry points */
+int oracle_step(oracle *o, int n)
+{
+    for (int s = 0; s < n; s++)
+        if (imex_step(o) != 0) return -1;
+    return 0;
+}
+
+int oracle_n_cells(const oracle *o) { return o->nc; }
+double oracle_dt(const oracle *o) { return o->dt; }
+double oracle_residual(const oracle *o) { return o->residual; }
+double oracle_moment_defect(const oracle *o) { return o->moment_defect; }
+
+void oracle_get_f(const oracle *o, double *f) { memcpy(f, o->f, sizeof(double) * (size_t)o->nc * Q); }
+
+void oracle_set_f(oracle *o, const double *f)
+{
+    memcpy(o->f, f, sizeof(double) * (size_t)o->nc * Q);
+    for (int i = 0; i < o->nc; i++) moments(&o->f[(size_t)i * Q], &o->rho[i], &o->ux[i], &o->uy[i]);
+}
+
+void oracle_get_fields(const oracle *o, double *rho, double *u, double *v, double *k,
+                       double *w, double *nut)
+{
+    for (int i = 0; i < o->nc; i++) {
+        if (rho) rho[i] = o->rho[i];
+        if (u) u[i] = o->ux[i];
+        if (v) v[i] = o->uy[i];
+        if (k) k[i] = o->k[i];
+        if (w) w[i] = o->om[i];
+        if (nut) nut[i] = o->nut[i];
+    }
+}
+
+void oracle_geometry(const oracle *o, double *area, double *cx, double *cy, double *wdist)
+{
+    for (int i = 0; i < o->nc; i++) {
+        area[i] = o->area[i];
+        cx[i] = o->cx[i];
+        cy[i] = o->cy[i];
+        wdist[i] = o->wdist[i];
+    }
+}
+
+/* Total mass sum_i rho_i A_i. */
+double oracle_mass(const oracle *o)
+{
+    double m = 0.0;
+    for (int i = 0; i < o->nc; i++) {
+        double r = 0.0;
+        for (int a = 0; a < Q; a++) r += o->f[(size_t)i * Q + a];
+        m += r * o->area[i];
+    }
+    return m;
+}
+
+/* Gradient of a per-cell field phi with boundary values phib (one per boundary edge). */
+void oracle_gradient(oracle *o, const double *phi, const double *phib, double *g)
+{
+    for (int i = 0; i < o->nc; i++) lsq_gradient(o, i, phi, 1, phib, 1, &g[2 * i], &g[2 * i + 1]);
+}
+
+/* Gamma^a of a given f [nc * Q] with the mesh's boundary conditions. */
+void oracle_convection(oracle *o, const double *f, double *ga) { convection(o, f, ga); }
+
+/* Force on the walls (reading): F = sum_{wall faces} sum_alpha e_alpha (e_alpha . n) f_{alpha,bc}
+ * Delta l, n out of the fluid cell -- the momentum flux of the face values of Eq. (advection).
+ * out = {Fx, Fy, C_D, C_L} with C_D, C_L along / normal to the free-stream angle and
+ * normalised by 0.5 rho0 U^2 L; cp[b] = (cs^2 rho_P - cs^2 rho0) / (0.5 rho0 U^2) on wall
+ * edges, 0 elsewhere; fxe / fye (optional) receive the force on each wall edge. */
+void oracle_forces(oracle *o, double *out, double *cp, double *fxe, double *fye)
+{
+    boundary_f(o, o->f, o->fbc);
+    double fx = 0.0, fy = 0.0;
+    double q = 0.5 * o->rho0 * o->uref * o->uref;
+    for (int b = 0; b < o->nb; b++) {
+        if (cp) cp[b] = 0.0;
+        if (fxe) fxe[b] = 0.0;
+        if (fye) fye[b] = 0.0;
+        if (o->btype[b] != BC_WALL) continue;
+        double ex = 0.0, ey = 0.0;
+        for (int a = 0; a < Q; a++) {
+            double en = EX[a] * o->bnx[b] + EY[a] * o->bny[b];
+            double m = en * o->fbc[(size_t)b * Q + a] * o->blen[b];
+            ex += EX[a] * m;
+            ey += EY[a] * m;
+        }
+        fx += ex;
+        fy += ey;
+        if (fxe) fxe[b] = ex;
+        if (fye) fye[b] = ey;
+        if (cp) {
+            double r = 0.0;
+            for (int a = 0; a < Q; a++) r += o->f[(size_t)o->bcell[b] * Q + a];
+            cp[b] = (CS2 * r - CS2 * o->rho0) / q;
+        }
+    }
+    double al = o->alpha_deg * M_PI / 180.0;
+    out[0] = fx;
+    out[1] = fy;
+    out[2] = (fx * cos(al) + fy * sin(al)) / (q * o->lref);
+    out[3] = (-fx * sin(al) + fy * cos(al)) / (q * o->lref);
+}

@@ -1,0 +1,300 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Every check here compares the oracle with something other than itself: a closed form, an
+invariant of the lattice or of the scheme, a textbook flow, or a value printed in the paper
+(golden fixtures under tests/golden/).  A plausible slip anywhere in the oracle -- a dropped
+term, a wrong sign, a swapped tableau entry, a transposed gradient -- fails one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle, feq, sst_point
+from paper_1812_00394_gb300 import meshgen as mg
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], float)
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], float)
+CS2 = 1.0 / 3.0
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as fh:
+        return json.load(fh)
+
+
+def _box_at_rest(n=12, kind="tri", jitter=0.25, seed=3):
+    """Closed unit box, all walls at rest, jittered interior nodes."""
+    xs = np.linspace(0, 1, n + 1)
+    xy, cells, sides = mg.quad_grid(xs, xs, jitter, seed)
+    cells = mg.split_quads(cells) if kind == "tri" else cells
+    bn = np.concatenate([sides["bottom"], sides["right"], sides["top"], sides["left"]])
+    ptr = np.arange(cells.shape[0] + 1, dtype=np.int32) * cells.shape[1]
+    bv = np.zeros((bn.shape[0], 5))
+    bv[:, 0] = 1.0
+    return mg.Mesh(xy, ptr, cells.ravel(), bn, np.zeros(bn.shape[0], np.int32), bv).normalized()
+
+
+# ----------------------------------------------------------------- equilibrium (D2Q9)
+@pytest.mark.parametrize("rho,u,v", [(1.0, 0.0, 0.0), (1.3, 0.1, -0.05), (0.7, -0.08, 0.11)])
+def test_feq_moments_closed_form(rho, u, v):
+    """Sum f^eq = rho, sum e f^eq = rho u, sum e e f^eq = cs^2 rho I + rho u u (D2Q9 isotropy)."""
+    f = feq(rho, u, v)
+    assert abs(f.sum() - rho) < 1e-15
+    assert abs((EX * f).sum() - rho * u) < 1e-15
+    assert abs((EY * f).sum() - rho * v) < 1e-15
+    assert abs((EX * EX * f).sum() - (CS2 * rho + rho * u * u)) < 1e-15
+    assert abs((EY * EY * f).sum() - (CS2 * rho + rho * v * v)) < 1e-15
+    assert abs((EX * EY * f).sum() - rho * u * v) < 1e-15
+
+
+def test_feq_rest_weights():
+    """At rest f^eq / rho are the D2Q9 weights 4/9, 1/9, 1/36 (Qian et al.)."""
+    f = feq(2.0, 0.0, 0.0) / 2.0
+    assert np.allclose(f, [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4, rtol=0, atol=1e-16)
+
+
+# ----------------------------------------------------------------- IMEX tableau
+def test_golden_tableau_order_conditions():
+    """The printed tableau (Sec. 3.1) is second order: sum n = 1 and b.c = 1/2 for all four
+    explicit/implicit pairings; the implicit part is stiffly accurate (last row of m = n)."""
+    t = _gold("imex_tableau.json")
+    mt, m = np.array(t["m_tilde"]), np.array(t["m"])
+    nt, n = np.array(t["n_tilde"]), np.array(t["n"])
+    ct, c = mt.sum(1), m.sum(1)
+    assert abs(nt.sum() - 1) < 1e-15 and abs(n.sum() - 1) < 1e-15
+    for b in (nt, n):
+        for cc in (ct, c):
+            assert abs(b @ cc - 0.5) < 1e-15
+    assert np.allclose(m[2], n)
+
+
+def _relaxation_factor_from_tableau(z):
+    """Stability function of the implicit part: R(z) = 1 - z n^T (I + z m)^{-1} 1."""
+    t = _gold("imex_tableau.json")
+    m, n = np.array(t["m"]), np.array(t["n"])
+    return 1.0 - z * n @ np.linalg.solve(np.eye(3) + z * m, np.ones(3))
+
+
+@pytest.mark.parametrize("z", [0.5, 5.0, 50.0, 500.0])
+def test_imex_relaxation_factor(z):
+    """A uniform field in a closed box at rest has Gamma^a = 0, so one step multiplies the
+    non-equilibrium part by the stability function of the printed implicit tableau.  This pins
+    Eq. (fnewstage), the collision term and Eq. (imextwo) stage by stage."""
+    m = _box_at_rest()
+    dt = 0.01                                  # convective CFL ~ 0.25: round-off stays put
+    nu = CS2 * dt / z
+    case = mg.Case(m, nu=nu, dt=dt)
+    o = Oracle(case)
+    eq = feq(1.0, 0.0, 0.0)
+    w = eq.copy()
+    delta = 1e-3 * w * (EX ** 2 - EY ** 2)     # zero mass and momentum: pure non-equilibrium
+    f0 = np.tile(eq + delta, (o.n_cells, 1))
+    o.set_f(f0)
+    o.step(1)
+    f1 = o.get_f()
+    R = _relaxation_factor_from_tableau(z)
+    assert abs(R - (1 - 5 * z / 12) / ((1 + z / 4) * (1 + z / 3))) < 1e-14
+    # Eq. (imextwo) adds dt/tau-weighted collision terms, so a rounding of f^(J) is scaled by ~z
+    np.testing.assert_allclose(f1 - eq, np.tile(R * delta, (o.n_cells, 1)), rtol=0,
+                               atol=1e-16 * (10 + z))
+
+
+def test_moment_elimination():
+    """After Eq. (fnewstage) every stage value carries the moments of Eq. (sumimeximplicitnew)."""
+    case = mg.cavity_quad(16, re=100.0)
+    o = Oracle(case)
+    o.step(5)
+    assert o.moment_defect() < 1e-15
+
+
+# ----------------------------------------------------------------- gradient and flux
+@pytest.mark.parametrize("kind", ["quad", "tri"])
+def test_gradient_exact_on_linear_fields(kind):
+    """The least-squares gradient reproduces a linear field exactly, interior and boundary."""
+    m = _box_at_rest(10, kind, jitter=0.3, seed=11)
+    o = Oracle(mg.Case(m, nu=1e-3, dt=1e-3))
+    g = o.geometry()
+    a, bx, by = 0.3, -1.7, 2.4
+    phi = a + bx * g["cx"] + by * g["cy"]
+    mid = 0.5 * (m.xy[m.bedge_nodes[:, 0]] + m.xy[m.bedge_nodes[:, 1]])
+    phib = a + bx * mid[:, 0] + by * mid[:, 1]
+    grad = o.gradient(phi, phib)
+    np.testing.assert_allclose(grad[:, 0], bx, atol=1e-12)
+    np.testing.assert_allclose(grad[:, 1], by, atol=1e-12)
+
+
+def test_geometry_closed_forms():
+    """Cell areas tile the unit square; on a uniform quad mesh the centroids are the cell
+    centres and the wall distance is min(x, 1-x, y, 1-y)."""
+    case = mg.cavity_quad(8)
+    o = Oracle(case)
+    g = o.geometry()
+    assert abs(g["area"].sum() - 1.0) < 1e-14
+    h = 1.0 / 8
+    ii, jj = np.meshgrid(np.arange(8), np.arange(8), indexing="xy")
+    np.testing.assert_allclose(g["cx"], (ii.ravel() + 0.5) * h, atol=1e-15)
+    np.testing.assert_allclose(g["cy"], (jj.ravel() + 0.5) * h, atol=1e-15)
+    d = np.minimum.reduce([g["cx"], 1 - g["cx"], g["cy"], 1 - g["cy"]])
+    np.testing.assert_allclose(g["wdist"], d, atol=1e-15)
+    tri = Oracle(mg.Case(_box_at_rest(9, "tri", 0.3, 5), nu=1e-3, dt=1e-3)).geometry()
+    assert abs(tri["area"].sum() - 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("kind", ["quad", "tri"])
+def test_free_stream_preserved(kind):
+    """A uniform equilibrium f^eq(rho0, U) on a periodic jittered mesh is a fixed point: the
+    face sums of Eq. (advection) over a closed cell vanish and the collision is zero."""
+    m = mg.periodic_box(10, kind, jitter=0.3, seed=2)
+    o = Oracle(mg.Case(m, nu=1e-3, cfl=0.5))
+    f0 = np.tile(feq(1.0, 0.08, -0.05), (o.n_cells, 1))
+    o.set_f(f0)
+    assert np.abs(o.convection(f0)).max() < 1e-13
+    o.step(10)
+    assert np.abs(o.get_f() - f0).max() < 1e-14
+
+
+def _advection_error(n, kind):
+    m = mg.periodic_box(n, kind)
+    o = Oracle(mg.Case(m, nu=1e30, cfl=0.5))   # tau -> infinity: collision off, pure transport
+    g = o.geometry()
+    w = feq(1.0, 0.0, 0.0)
+
+    def exact(t):
+        X = g["cx"][:, None] - EX[None, :] * t
+        Y = g["cy"][:, None] - EY[None, :] * t
+        return w[None, :] * (1 + 0.1 * np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y))
+    o.set_f(exact(0.0))
+    nst = int(round(0.25 / o.dt))
+    o.step(nst)
+    return math.sqrt(np.mean((o.get_f() - exact(nst * o.dt)) ** 2))
+
+
+@pytest.mark.parametrize("kind", ["quad", "tri"])
+def test_pure_advection_second_order(kind):
+    """Collision off, each f_alpha is transported at e_alpha; the explicit RK part of the
+    tableau with the upwind linear reconstruction converges at second order."""
+    e = [_advection_error(n, kind) for n in (16, 32, 64)]
+    rates = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert min(rates) > 1.85, (e, rates)
+
+
+# ----------------------------------------------------------------- conservation, Couette
+def test_cavity_mass_conservation():
+    """Closed cavity: interior fluxes telescope, wall faces carry no mass (u_w . n = 0) and the
+    collision conserves mass, so sum rho A is constant up to the rounding of f itself."""
+    case = mg.cavity_quad(32, re=400.0)
+    o = Oracle(case)
+    m0 = o.mass()
+    o.step(400)
+    assert abs(o.mass() - m0) / m0 < 400 * 1e-15
+
+
+@pytest.mark.parametrize("kind,n,tol", [("quad", 16, 1e-11), ("tri", 16, 5e-5)])
+def test_couette_profile_and_wall_shear(kind, n, tol):
+    """Plane Couette flow (periodic in x, lid at U): the steady profile is u = U y / H, and the
+    tangential force on the moving wall is -mu U / H per unit length with mu = rho nu and
+    tau = nu / cs^2 (Eq. turbtau without eddy viscosity)."""
+    U, H, nu = 0.1, 1.0, 0.05
+    m = mg.couette_channel(4, n, U=U, H=H, Lx=1.0, kind=kind)
+    o = Oracle(mg.Case(m, nu=nu, cfl=0.5, uref=U))
+    o.step(int(3 * H * H / nu / o.dt))
+    g, fl = o.geometry(), o.fields()
+    err = math.sqrt(np.mean((fl["u"] - U * g["cy"] / H) ** 2)) / U
+    assert err < tol
+    fr = o.forces(per_edge=True)
+    top = (m.bedge_type == mg.BC_WALL) & (m.bedge_val[:, 1] > 0)
+    assert abs(fr["fx_edge"][top].sum() - (-nu * U / H * 1.0)) < 20 * tol * nu * U / H + 1e-13
+
+
+def test_couette_second_order_on_triangles():
+    U, H, nu = 0.1, 1.0, 0.05
+    errs = []
+    for n in (8, 16):
+        m = mg.couette_channel(4, n, U=U, H=H, Lx=1.0, kind="tri")
+        o = Oracle(mg.Case(m, nu=nu, cfl=0.5, uref=U))
+        o.step(int(3 * H * H / nu / o.dt))
+        g, fl = o.geometry(), o.fields()
+        errs.append(math.sqrt(np.mean((fl["u"] - U * g["cy"] / H) ** 2)))
+    assert math.log2(errs[0] / errs[1]) > 1.8, errs
+
+
+def test_forces_fluid_at_rest():
+    """Fluid at rest at uniform rho: the wall force is the pressure cs^2 rho times the wall
+    length, along the outward normal of the fluid; the net force on a closed box is zero."""
+    m = _box_at_rest(8, "tri", 0.2, 4)
+    rho = 1.2
+    case = mg.Case(m, nu=1e-3, dt=1e-3, rho=np.full(m.n_cells, rho))
+    o = Oracle(case)
+    fr = o.forces(per_edge=True)
+    assert abs(fr["fx"]) < 1e-15 and abs(fr["fy"]) < 1e-15
+    mid = 0.5 * (m.xy[m.bedge_nodes[:, 0]] + m.xy[m.bedge_nodes[:, 1]])
+    left = mid[:, 0] < 1e-12
+    assert abs(fr["fx_edge"][left].sum() - (-CS2 * rho * 1.0)) < 1e-14
+    assert abs(fr["fy_edge"][left].sum()) < 1e-15
+
+
+# ----------------------------------------------------------------- SST
+def test_golden_sst_constants_derived():
+    """C_w1, C_w2 from the printed constants (Sec. 2): the standard values 0.5532 and 0.4404."""
+    c = _gold("sst_constants.json")
+    cw1 = c["beta1"] / c["beta_star"] - c["sigma_w1"] * c["kappa"] ** 2 / math.sqrt(c["beta_star"])
+    cw2 = c["beta2"] / c["beta_star"] - c["sigma_w2"] * c["kappa"] ** 2 / math.sqrt(c["beta_star"])
+    assert abs(cw1 - 0.5532) < 1e-4 and abs(cw2 - 0.4404) < 1e-4
+
+
+def test_sst_point_limits():
+    """Limits of the blending functions: far from walls f1 = f2 = 0 and nu_t = k / omega; at
+    a wall f1 = f2 = 1; with large strain nu_t = a1 k / S; CD_kw floors at 1e-20."""
+    nu = 1e-5
+    far = sst_point(1e-4, 10.0, 1e6, (0, 0), (0, 0), 0.0, nu)
+    assert far["f1"] < 1e-30 and far["f2"] < 1e-15
+    assert abs(far["nut"] - 1e-4 / 10.0) < 1e-18
+    assert far["cdkw"] == 1e-20
+    near = sst_point(1e-4, 10.0, 1e-6, (0, 0), (0, 0), 0.0, nu)
+    assert near["f1"] == 1.0 and near["f2"] == 1.0
+    strained = sst_point(1e-4, 10.0, 1e-6, (0, 0), (0, 0), 1e3, nu)
+    assert abs(strained["nut"] - 0.31 * 1e-4 / 1e3) < 1e-18
+    opp = sst_point(1e-4, 10.0, 1.0, (1.0, 0.0), (-1.0, 0.0), 0.0, nu)
+    assert opp["cdkw"] == 1e-20
+    pos = sst_point(1e-4, 10.0, 1.0, (1.0, 0.0), (2.0, 0.0), 0.0, nu)
+    assert abs(pos["cdkw"] - 2 * 0.856 / 10.0 * 2.0) < 1e-15
+
+
+def test_sst_homogeneous_decay():
+    """Homogeneous, unstrained turbulence far from walls: d omega/dt = -beta2 omega^2 and
+    dk/dt = -beta* omega k, with closed forms omega = w0/(1 + beta2 w0 t) and
+    k = k0 (1 + beta2 w0 t)^(-beta*/beta2).  The point-implicit update reproduces omega
+    exactly and converges to k at first order in dt."""
+    m = mg.periodic_box(4, "quad")
+    k0, w0, nu = 1e-3, 2.0, 1e-4
+    T = 5.0
+    errs = []
+    for nst in (50, 100, 200):
+        case = mg.Case(m, nu=nu, dt=T / nst, sst=True, k=np.full(16, k0), omega=np.full(16, w0))
+        o = Oracle(case)
+        o.step(nst)
+        fl = o.fields()
+        w_ex = w0 / (1 + 0.0828 * w0 * T)
+        k_ex = k0 * (1 + 0.0828 * w0 * T) ** (-0.09 / 0.0828)
+        np.testing.assert_allclose(fl["omega"], w_ex, rtol=1e-12)
+        errs.append(abs(fl["k"][0] - k_ex) / k_ex)
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(0.9 < r < 1.1 for r in rates), (errs, rates)
+
+
+def test_sst_with_zero_k_is_laminar():
+    """k = 0 everywhere and on every boundary: nu_t = 0, tau = nu / cs^2, and the coupled step
+    equals the laminar step bit for bit."""
+    case = mg.cavity_quad(12, re=200.0)
+    a = Oracle(case)
+    lam = mg.Case(case.mesh, nu=case.nu, cfl=case.cfl, rho=case.rho, sst=True,
+                  k=np.zeros(case.mesh.n_cells), omega=np.full(case.mesh.n_cells, 5.0))
+    b = Oracle(lam)
+    a.step(20)
+    b.step(20)
+    assert np.array_equal(a.get_f(), b.get_f())
+    assert np.all(b.fields()["nut"] == 0.0)
