@@ -1,0 +1,439 @@
+#!/usr/bin/env python3
+"""Benchmark of the FVLBM time step (arXiv 1812.00394, Part II) on GB300.
+
+Default workload: the uneven batched sweep -- 48 instances (32 laminar Delaunay cavities of
+10k-40k triangles at Re 100-3200, 4 turbulent backward-facing steps of ~80k hybrid cells, 12
+turbulent NACA 0012 C-meshes of 50k-200k cells at 0-12 degrees), advanced together by one
+handle of the CUDA library (every launch of a step covers all instances, CUDA-graph replayed).
+A "step" is one full time step of every instance (SST where enabled, three IMEX stages, final
+update).  The metric is Mcell-steps/s of the FP32 deviation-storage path; the plain FP64 path
+is timed on the same workload beside it, and both are compared with the FP64 CPU oracle.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 run under torch.distributed.run: every rank advances its own copy of the sweep
+(seeded by rank; weak scaling, no data exchange) and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Mcell-steps/s FP32/batched vs plain FP64 at stated L2 error; % HBM roofline"
+UNIT = "Mcell-steps/s"
+L2_BYTES = 129e6
+# Algorithmic HBM bytes per cell-step of the whole step (minimal fused design: 114 state
+# words plus 84 B of neighbour indices; +34 words with k-omega SST), per storage precision.
+STEP_BYTES = {("f32", False): 540.0, ("f32", True): 676.0, ("f64", False): 996.0, ("f64", True): 1268.0}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:  # noqa: BLE001
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- workload
+def make_workload(name: str, rank: int = 0):
+    from paper_1812_00394_gb300 import meshgen as mg
+    if name == "sweep":
+        return mg.batched_sweep(seed=5 + 7919 * rank)
+    if name == "delaunay40k":
+        return [mg.cavity_delaunay(re=1000.0, z=5.0, seed=2 + rank)]
+    if name == "cavity64":
+        return [mg.cavity_quad(64, re=400.0, seed=1 + rank)]
+    raise ValueError(name)
+
+
+def _sample_indices(cases):
+    """One instance of each kind (first cavity, first BFS, first NACA) for oracle checks."""
+    picks, seen = [], set()
+    for i, c in enumerate(cases):
+        kind = c.name.split("_")[0].rstrip("0123456789")
+        if kind not in seen:
+            seen.add(kind)
+            picks.append(i)
+    return picks
+
+
+# ----------------------------------------------------------------------------- reference arm
+def cpu_oracle_rate(cases, budget_s: float, max_steps: int = 50):
+    """Time the FP64 oracle, as it stands, on a bounded sample: each sampled instance is
+    stepped until about budget_s / n_samples seconds are spent.  Returns (Mcell-steps/s, desc)."""
+    from oracle.oracle import Oracle
+    picks = _sample_indices(cases)
+    cell_steps, secs, desc = 0, 0.0, []
+    for i in picks:
+        o = Oracle(cases[i])
+        n, t0 = 0, time.perf_counter()
+        while n < max_steps and time.perf_counter() - t0 < budget_s / len(picks):
+            o.step(1)
+            n += 1
+        dt = time.perf_counter() - t0
+        cell_steps += n * cases[i].mesh.n_cells
+        secs += dt
+        desc.append(f"{cases[i].name} x {n} steps")
+    return cell_steps / secs / 1e6, "; ".join(desc)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cases = make_workload(args.workload)
+    picks = _sample_indices(cases)
+    from oracle.oracle import Oracle
+    oracles = [Oracle(cases[i]) for i in picks]
+    cells = sum(cases[i].mesh.n_cells for i in picks)
+    for _ in range(args.warmup):
+        for o in oracles:
+            o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for o in oracles:
+            o.step(1)
+    el = time.perf_counter() - t0
+    value = cells * args.steps / el / 1e6
+    sample = (f"each step = one FP64 oracle time step of {len(picks)} instances of the sweep "
+              f"({', '.join(cases[i].name for i in picks)}; {cells} cells), single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "sample_cells": cells, "precision": "fp64-cpu"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def _time_steps(torch, solver, stream, steps, dist, world):
+    """K steps bracketed by barrier + synchronize; CUDA events on the handle's stream."""
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    solver.step(steps)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = start.elapsed_time(stop)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def _vel(fields):
+    return np.concatenate([fields["u"], fields["v"]])
+
+
+def run_ours(args):
+    import torch
+    from paper_1812_00394_gb300 import fvlbm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+
+    t_setup = time.perf_counter()
+    cases = make_workload(args.workload, rank)
+    total_cells = sum(c.mesh.n_cells for c in cases)
+    sst_cells = sum(c.mesh.n_cells for c in cases if c.sst)
+    fvlbm.load()
+
+    results = {}
+    solvers = {}
+    for prec, tag in ((fvlbm.FVLBM_FP32_DEV, "f32"), (fvlbm.FVLBM_FP64, "f64")):
+        with torch.cuda.stream(stream):
+            s = fvlbm.Solver(cases, precision=prec, device=dev, stream=stream.cuda_stream)
+            s.step(args.warmup)
+            torch.cuda.synchronize()
+            with ClockSampler(dev) as clk:
+                ms = _time_steps(torch, s, stream, args.steps, dist, world)
+            results[tag] = {"ms": ms, "clocks": clk.summary()}
+        solvers[tag] = s
+    setup_s = time.perf_counter() - t_setup
+
+    ms32 = results["f32"]["ms"]
+    value = total_cells * world * args.steps / (ms32 * 1e-3) / 1e6
+    ms64 = results["f64"]["ms"]
+    value64 = total_cells * world * args.steps / (ms64 * 1e-3) / 1e6
+
+    # FP32 vs FP64 (both GPU, same number of steps) on every cell of the workload
+    s32, s64 = solvers["f32"], solvers["f64"]
+    v32 = np.concatenate([_vel(s32.fields(i)) for i in range(s32.n)])
+    v64 = np.concatenate([_vel(s64.fields(i)) for i in range(s64.n)])
+    l2_32_64 = float(np.linalg.norm(v32 - v64) / np.linalg.norm(v64))
+
+    # per-kernel device times (CUDA events on the handle's stream) for the roofline
+    with torch.cuda.stream(stream):
+        prof = s32.profile_kernels(max(4, min(args.steps, 20)))
+    kname, kstat = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    per_launch_ms = kstat["ms"] / kstat["launches"]
+    hbm, peak_kind = _peaks()
+    lam_cells = total_cells - sst_cells
+    kbytes = _kernel_bytes(kname, "f32", total_cells, sst_cells)
+    achieved = kbytes / (per_launch_ms * 1e-3) / 1e9
+    step_bytes = lam_cells * STEP_BYTES[("f32", False)] + sst_cells * STEP_BYTES[("f32", True)]
+    step_gbs = step_bytes / (ms32 / args.steps * 1e-3) / 1e9
+    lps = s32.footprint()[1]
+    dev_bytes = s32.footprint()[0]
+
+    # errors against the FP64 CPU oracle on sampled instances (fresh short runs)
+    err = {}
+    if rank == 0 and not args.no_oracle_check:
+        err = _oracle_errors(cases, fvlbm, dev, stream, torch, nsteps=args.check_steps)
+
+    # end to end through the C ABI with pinned host buffers: set_f, one step, read u, v
+    e2e = _e2e(torch, fvlbm, s32, stream, args, world, dist)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sample = cpu_oracle_rate(cases, args.cpu_budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": sample + " (FP64 CPU oracle, single thread, this host)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": _workload_desc(args.workload), "instances": len(cases),
+                       "cells_per_gpu": total_cells, "sst_cells_per_gpu": sst_cells,
+                       "precision": "fp32 f-w*rho0 deviation storage, fp32 arithmetic, fp64 reductions",
+                       "l2": f"inputs larger than L2 (device working set {dev_bytes / 1e6:.0f} MB > 129 MB); no flush",
+                       "parallelism": f"{world} process(es), one per GPU, each its own sweep"},
+            "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / args.steps,
+                           "speedup_fp32_over_fp64": value / value64},
+            "error": {"fp32_vs_fp64_gpu_velocity_rel_l2": l2_32_64, **err},
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_launch": kbytes,
+                         "avg_launch_ms": per_launch_ms},
+            "step_roofline": {"bytes_per_cell_step": step_bytes / total_cells,
+                              "achieved": step_gbs, "peak": hbm, "unit": "GB/s",
+                              "frac": step_gbs / hbm, "peak_kind": peak_kind},
+            "kernels": {k: {"avg_ms": v["ms"] / v["launches"], "launches": v["launches"]}
+                        for k, v in prof.items()},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": results["f32"]["clocks"],
+            "clocks_fp64": results["f64"]["clocks"],
+            "gpu_launches": lps * args.steps,
+            "setup_s": setup_s,
+        }
+        print(json.dumps(line))
+    for s in solvers.values():
+        s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _workload_desc(name):
+    return {"sweep": "batched sweep: 48 instances (32 laminar Delaunay cavities 10k-40k cells "
+                     "Re 100-3200, 4 SST backward-facing steps ~80k cells, 12 SST NACA0012 "
+                     "C-meshes 50k-200k cells alpha 0-12 deg), CFL 0.5 each",
+            "delaunay40k": "laminar lid-driven cavity Re 1000, seeded Delaunay ~40k triangles, dt = 5 tau",
+            "cavity64": "laminar lid-driven cavity Re 400, 64x64 quads, CFL 0.5"}[name]
+
+
+def _kernel_bytes(kname, prec, cells, sst_cells):
+    """Algorithmic bytes of one launch of each kernel: its per-cell state reads and writes
+    counted once (neighbour values assumed reused from cache), neighbour indices 4 B each
+    (3.5 per cell), geometry not counted (recomputable)."""
+    w = 4 if prec == "f32" else 8
+    idx = 14.0
+    words = {
+        "stage1": 9 + 1 + 9,                       # f^n, tau -> f^(1)
+        "grad_f": 9 + 18,                          # f^(J) -> gradient
+        "flux_stage1": 9 + 18 + 9 + 1 + 27,        # f1, g, f^n, tau -> f2, B, C
+        "flux_stage2": 9 + 18 + 18 + 1 + 18,       # f2, g, B, C, tau -> f3, C
+        "flux_stage3": 9 + 18 + 9 + 1 + 9 + 3,     # f3, g, C, tau -> f^{n+1}, macros
+        "sst_grad": 3 + 2 + 1 + 12 + 1,
+        "sst_update": 3 + 3 + 12 + 1 + 4,
+    }[kname]
+    n = sst_cells if kname.startswith("sst") else cells
+    return n * (words * w + idx)
+
+
+def _oracle_errors(cases, fvlbm, dev, stream, torch, nsteps):
+    from oracle.oracle import Oracle
+    out = {}
+    worst_vel, worst_force = 0.0, 0.0
+    for i in _sample_indices(cases):
+        c = cases[i]
+        o = Oracle(c)
+        o.step(nsteps)
+        fo = o.fields()
+        for prec, tag in ((fvlbm.FVLBM_FP32_DEV, "f32"), (fvlbm.FVLBM_FP64, "f64")):
+            with torch.cuda.stream(stream):
+                s = fvlbm.Solver(c, precision=prec, device=dev, stream=stream.cuda_stream)
+                s.step(nsteps)
+                fg = s.fields()
+                fr = s.forces()
+                s.close()
+            e = float(np.linalg.norm(_vel(fg) - _vel(fo)) / np.linalg.norm(_vel(fo)))
+            out[f"{tag}_vs_oracle_velocity_rel_l2[{c.name}]"] = e
+            if tag == "f32":
+                worst_vel = max(worst_vel, e)
+                if c.name.startswith("naca"):
+                    ofr = o.forces()
+                    sc = math.hypot(ofr["cd"], ofr["cl"])
+                    worst_force = max(worst_force, abs(fr["cd"] - ofr["cd"]) / sc,
+                                      abs(fr["cl"] - ofr["cl"]) / sc)
+    out["oracle_check_steps"] = nsteps
+    out["f32_worst_velocity_rel_l2"] = worst_vel
+    out["f32_worst_cd_cl_rel"] = worst_force
+    return out
+
+
+def _e2e(torch, fvlbm, solver, stream, args, world, dist):
+    """Same metric through the public API with host buffers: per step, fvlbm_set_f of every
+    instance from pinned host memory, one fvlbm_step, fvlbm_get_fields (u, v) back."""
+    n = solver.n
+    cells = solver.cells
+    host_f = [torch.empty((cells[i], 9), dtype=torch.float64, pin_memory=True).numpy()
+              for i in range(n)]
+    for i in range(n):
+        host_f[i][:] = solver.get_f(i)
+    lib = fvlbm.load()
+    import ctypes as C
+    outs = [[torch.empty(cells[i], dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+            for i in range(n)]
+    k = max(2, min(args.steps // 10, 10))
+
+    def one_step():
+        for i in range(n):
+            lib.fvlbm_set_f(solver.h, i, host_f[i].ctypes.data_as(C.c_void_p))
+        solver.step(1)
+        for i in range(n):
+            lib.fvlbm_get_fields(solver.h, i, None, outs[i][0].ctypes.data_as(C.c_void_p),
+                                 outs[i][1].ctypes.data_as(C.c_void_p), None, None, None)
+    with torch.cuda.stream(stream):
+        one_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            one_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+    total = sum(cells)
+    return {"value": total * world / (el / k) / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": int(total * 9 * 8), "d2h_bytes_per_step": int(total * 2 * 8),
+            "steps": k, "ms_per_step": el / k * 1e3}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "delaunay40k", "cavity64"])
+    ap.add_argument("--check-steps", type=int, default=5)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

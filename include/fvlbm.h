@@ -1,0 +1,161 @@
+/*
+ * fvlbm.h -- C ABI of the GB300 (sm_103a) implementation of the time step of the simplified
+ * finite-volume lattice Boltzmann method on unstructured 2-D grids with k-omega SST eddy
+ * viscosity and a three-stage second-order IMEX Runge-Kutta integrator
+ * (Wang, Zhong, Cao, Zhuo, arXiv 1812.00394, Part II).
+ *
+ * Method (the passages each entry point implements):
+ *   - D2Q9 discrete-velocity BGK equation, Eq. (bgkeq), semi-discretised in finite volumes as
+ *     df/dt = Gamma^a + Gamma^c, Eq. (semibgk).
+ *   - Convection Gamma^a_alpha = -(1/A) sum_m [(e_alpha . n) f_{alpha,bc} Delta l]_m,
+ *     Eq. (advection), with a least-squares cell gradient and upwind linear face values (Sec. 3.2,
+ *     Step 2).
+ *   - Collision Gamma^c_alpha = -(f_alpha - f^eq_alpha)/tau, Eq. (collision), with
+ *     tau = (nu + nu_t)/c_s^2, Eq. (turbtau).
+ *   - IMEX stages, Eqs. (imexone), (imextwo) and the tableau of Sec. 3.1; the implicit collision
+ *     is solved in closed form per cell through the collision invariants,
+ *     Eqs. (sumimeximplicitnew) and (fnewstage).
+ *   - k-omega SST (Sec. 2) in finite volumes, Eq. (SSTequint), solved once per step before the
+ *     stages (Sec. 3.2, Step 1 and the coupling paragraph).
+ *
+ * Conventions for every entry point:
+ *   - All pointers passed in are HOST pointers unless stated otherwise.  The library copies
+ *     whatever it needs during the call; the caller keeps ownership of its arrays.
+ *   - Cell arrays are in the caller's (mesh input) cell order.  Distribution arrays are
+ *     cell-major: f[cell * 9 + alpha], alpha ordered rest, +x, +y, -x, -y, (+1,+1), (-1,+1),
+ *     (-1,-1), (+1,-1).
+ *   - Return 0 on success or a negative FVLBM_ERR_* code.  No entry point aborts the process.
+ *   - A handle is used by one host thread at a time.  All device work is issued on the
+ *     handle's stream.
+ */
+#ifndef FVLBM_H
+#define FVLBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FVLBM_OK 0
+#define FVLBM_ERR_BAD_MESH (-1)    /* connectivity inconsistent, non-positive area, > 4 nodes */
+#define FVLBM_ERR_BAD_BC (-2)      /* boundary edge not on the mesh boundary, open edge left */
+#define FVLBM_ERR_BAD_PARAM (-3)   /* nu <= 0, no dt and no cfl, bad precision, bad index */
+#define FVLBM_ERR_OOM (-4)         /* device allocation failed */
+#define FVLBM_ERR_CUDA (-5)        /* a CUDA runtime call failed */
+#define FVLBM_ERR_DIVERGED (-6)    /* NaN or Inf in the state (watchdog) */
+#define FVLBM_ERR_NOT_SUPPORTED (-7)
+
+/* boundary-edge types */
+#define FVLBM_BC_WALL 0       /* no-slip wall moving at (u_b, v_b) */
+#define FVLBM_BC_INLET 1      /* velocity inlet (u_b, v_b), turbulence (k_b, omega_b) */
+#define FVLBM_BC_OUTLET 2     /* pressure outlet at rho_b */
+#define FVLBM_BC_FARFIELD 3   /* characteristic far field (rho_b, u_b, v_b, k_b, omega_b) */
+#define FVLBM_BC_PERIODIC 4   /* glued to its partner by fvlbm_bc.periodic_pairs */
+
+/* storage precision of the distribution functions */
+#define FVLBM_FP64 0          /* f and all arithmetic in double */
+#define FVLBM_FP32_DEV 1      /* f - w_alpha rho0 stored and computed in float; reductions FP64 */
+
+/* Unstructured 2-D mesh: triangles and quadrilaterals, nodes counter-clockwise. */
+typedef struct {
+    int n_nodes;
+    const double *xy;          /* [2 * n_nodes] x0, y0, x1, y1, ... */
+    int n_cells;
+    const int *cell_ptr;       /* [n_cells + 1] CSR offsets into cell_nodes */
+    const int *cell_nodes;     /* 3 or 4 node ids per cell, counter-clockwise */
+} fvlbm_mesh;
+
+/* Boundary conditions, one record per boundary edge.  Every boundary edge of the mesh must be
+ * listed exactly once. */
+typedef struct {
+    int n_bedges;
+    const int *bedge_nodes;    /* [2 * n_bedges] the two end nodes (any order) */
+    const int *bedge_type;     /* [n_bedges] FVLBM_BC_* */
+    const double *bedge_val;   /* [5 * n_bedges] rho_b, u_b, v_b, k_b, omega_b */
+    int n_periodic;
+    const int *periodic_pairs; /* [2 * n_periodic] boundary-edge indices (a, b) */
+    const double *periodic_shift; /* [2 * n_periodic] edge b = edge a + shift */
+} fvlbm_bc;
+
+typedef struct {
+    double nu;                 /* kinematic viscosity (> 0) */
+    double rho0;               /* reference density (deviation offset, force normalisation) */
+    double dt;                 /* time step; if <= 0, dt = cfl / (max upwind outflow rate) */
+    double cfl;
+    int sst;                   /* 1: k-omega SST eddy viscosity; 0: laminar */
+    int precision;             /* FVLBM_FP64 or FVLBM_FP32_DEV */
+    double uref, lref;         /* reference speed and length (C_D, C_L, Cp, omega floor) */
+    double alpha_deg;          /* free-stream angle for C_D / C_L */
+    const double *rho_init;    /* [n_cells] or NULL (rho0) */
+    const double *u_init;      /* [n_cells] or NULL (0) */
+    const double *v_init;      /* [n_cells] or NULL (0) */
+    const double *k_init;      /* [n_cells] or NULL (0) */
+    const double *omega_init;  /* [n_cells] or NULL (1) */
+} fvlbm_params;
+
+typedef struct {
+    long long steps;           /* steps taken since create */
+    double residual;           /* max over instances of |u^{n+1}-u^n|_2 / |u^{n+1}|_2 (FP64) */
+    double mass;               /* sum over instances of sum_i rho_i A_i (FP64) */
+    int diverged;              /* 1 if a NaN / Inf was seen */
+} fvlbm_stats;
+
+typedef struct fvlbm_handle fvlbm_handle;
+
+/* Build one solver instance on `device` (the current device when < 0), issuing work on
+ * `stream` (a cudaStream_t; NULL creates a private non-blocking stream).  Step 0 of Sec. 3.2:
+ * f = f^eq(rho_init, u_init); k, omega initialised; nu_t = k / omega.  Mesh geometry, the
+ * least-squares matrices, wall distance and a locality-preserving (Morton) renumbering are
+ * computed on the host; the handle owns all device memory it allocates.
+ * Errors: BAD_MESH, BAD_BC, BAD_PARAM, OOM, CUDA. */
+int fvlbm_create(const fvlbm_mesh *mesh, const fvlbm_bc *bc, const fvlbm_params *params,
+                 int device, void *stream, fvlbm_handle **out);
+
+/* Build one handle that advances n independent instances (meshes of any size, each with its
+ * own parameters, laminar or SST) together: every kernel launch of a step covers all
+ * instances.  All instances must share params[*].precision.  Instance indices below run
+ * 0..n-1 in the given order. */
+int fvlbm_create_batch(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs,
+                       const fvlbm_params *params, int device, void *stream,
+                       fvlbm_handle **out);
+
+/* Advance n_steps time steps (Steps 1-7 of Sec. 3.2 each), asynchronously on the handle's
+ * stream.  The steps are replayed from a captured CUDA graph.  When `stats` is non-NULL the
+ * call synchronises and fills it (FP64 residual of the last step, mass, NaN watchdog) and
+ * returns FVLBM_ERR_DIVERGED if the state is not finite. */
+int fvlbm_step(fvlbm_handle *h, int n_steps, fvlbm_stats *stats);
+
+/* Force on the wall faces of `instance`: F = sum over wall faces of sum_alpha e_alpha
+ * (e_alpha . n) f_{alpha,bc} Delta l (momentum flux of the Eq. (advection) face values, FP64).
+ * out[4] = {Fx, Fy, C_D, C_L}, coefficients along / normal to alpha_deg, normalised by
+ * 0.5 rho0 uref^2 lref.  cp (NULL or [n_bedges]) receives (c_s^2 rho_P - c_s^2 rho0) /
+ * (0.5 rho0 uref^2) on wall edges and 0 elsewhere, in boundary-edge input order.
+ * Synchronises the stream. */
+int fvlbm_forces(fvlbm_handle *h, int instance, double *out, double *cp);
+
+/* Host copies of the state of `instance` in input cell order (absolute f, FP64 on output).
+ * Any pointer may be NULL.  Synchronise the stream. */
+int fvlbm_get_f(fvlbm_handle *h, int instance, double *f);
+int fvlbm_set_f(fvlbm_handle *h, int instance, const double *f);
+int fvlbm_get_fields(fvlbm_handle *h, int instance, double *rho, double *u, double *v,
+                     double *k, double *omega, double *nut);
+
+/* Sizes and the time step actually used. */
+int fvlbm_info(fvlbm_handle *h, int instance, int *n_cells, int *n_bedges, double *dt);
+
+/* Bytes of device memory the handle holds, and the number of kernel launches one step issues. */
+int fvlbm_footprint(fvlbm_handle *h, long long *device_bytes, int *launches_per_step);
+
+/* Per-kernel device time over n_steps un-captured steps, measured with CUDA events recorded
+ * on the handle's stream around each launch (for roofline reporting).  names receives up to
+ * max_kernels entries of 32 chars; ms and launches the summed milliseconds and launch counts.
+ * Returns the number of kernels reported (>= 0) or an error. */
+int fvlbm_profile_kernels(fvlbm_handle *h, int n_steps, int max_kernels, char *names,
+                          double *ms, int *launches);
+
+void fvlbm_destroy(fvlbm_handle *h);
+const char *fvlbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FVLBM_H */

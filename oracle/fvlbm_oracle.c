@@ -533,8 +533,35 @@ static void sst_boundary(const oracle *o, int b, double *ub, double *vb, double 
     }
 }
 
+/* Barth-Jespersen limiter of a reconstructed field (reading of the second-order upwind
+ * scheme of Sec. 3.2 on unstructured cells): the largest psi in [0, 1] such that every face
+ * value phi_i + psi grad phi . (x_f - x_i) stays within the min / max of phi_i, its face
+ * neighbours and its boundary values. */
+static double bj_limiter(const oracle *o, int i, const double *phi, const double *phib,
+                         int bstride, const double *g)
+{
+    double lo = phi[i], hi = phi[i];
+    for (int l = 0; l < o->nface[i]; l++) {
+        const oface *F = &o->face[4 * i + l];
+        double q = F->nbr >= 0 ? phi[F->nbr] : phib[(size_t)F->bedge * bstride];
+        if (q < lo) lo = q;
+        if (q > hi) hi = q;
+    }
+    double psi = 1.0;
+    for (int l = 0; l < o->nface[i]; l++) {
+        const oface *F = &o->face[4 * i + l];
+        double d = g[0] * (F->xm - o->cx[i]) + g[1] * (F->ym - o->cy[i]);
+        double r = 1.0;
+        if (d > 0.0) r = (hi - phi[i]) / d;
+        else if (d < 0.0) r = (lo - phi[i]) / d;
+        if (r < psi) psi = r;
+    }
+    return psi;
+}
+
 /* One SST update of size dt from the macros at t^n (Step 1; readings): explicit face
- * convection (second-order upwind with the mean face velocity) and central diffusion with
+ * convection (second-order upwind with the mean face velocity, Barth-Jespersen limited) and
+ * central diffusion with
  * the mean face coefficient, explicit production and cross diffusion, point-implicit
  * destruction, then f2, nu_t and tau = (nu + nu_t) / cs^2 (Eq. turbtau). */
 static void sst_update(oracle *o)
@@ -549,6 +576,17 @@ static void sst_update(oracle *o)
         lsq_gradient(o, i, o->uy, 1, ubc + 1, 4, &o->gv[2 * i], &o->gv[2 * i + 1]);
         lsq_gradient(o, i, o->k, 1, ubc + 2, 4, &o->gk[2 * i], &o->gk[2 * i + 1]);
         lsq_gradient(o, i, o->om, 1, ubc + 3, 4, &o->gw[2 * i], &o->gw[2 * i + 1]);
+    }
+    /* limited gradients for the upwind face values of k and omega */
+    double *lk = (double *)xcalloc((size_t)nc * 2, sizeof(double));
+    double *lw = (double *)xcalloc((size_t)nc * 2, sizeof(double));
+    for (int i = 0; i < nc; i++) {
+        double pk = bj_limiter(o, i, o->k, ubc + 2, 4, &o->gk[2 * i]);
+        double pw = bj_limiter(o, i, o->om, ubc + 3, 4, &o->gw[2 * i]);
+        lk[2 * i] = pk * o->gk[2 * i];
+        lk[2 * i + 1] = pk * o->gk[2 * i + 1];
+        lw[2 * i] = pw * o->gw[2 * i];
+        lw[2 * i + 1] = pw * o->gw[2 * i + 1];
     }
     double *sk = (double *)xcalloc(nc, sizeof(double));
     double *sw = (double *)xcalloc(nc, sizeof(double));
@@ -570,8 +608,8 @@ static void sst_update(oracle *o)
         for (int l = 0; l < o->nface[i]; l++) {
             const oface *F = &o->face[4 * i + l];
             double uf, vf, kup, wup, rx = F->xm - o->cx[i], ry = F->ym - o->cy[i];
-            double kin = o->k[i] + o->gk[2 * i] * rx + o->gk[2 * i + 1] * ry;
-            double win = o->om[i] + o->gw[2 * i] * rx + o->gw[2 * i + 1] * ry;
+            double kin = o->k[i] + lk[2 * i] * rx + lk[2 * i + 1] * ry;
+            double win = o->om[i] + lw[2 * i] * rx + lw[2 * i + 1] * ry;
             if (F->nbr >= 0) {
                 int j = F->nbr;
                 double xj = o->cx[j] + F->sx, yj = o->cy[j] + F->sy;
@@ -579,8 +617,8 @@ static void sst_update(oracle *o)
                 vf = 0.5 * (o->uy[i] + o->uy[j]);
                 double un = uf * F->nx + vf * F->ny;
                 double sx = F->xm - xj, sy = F->ym - yj;
-                kup = un >= 0.0 ? kin : o->k[j] + o->gk[2 * j] * sx + o->gk[2 * j + 1] * sy;
-                wup = un >= 0.0 ? win : o->om[j] + o->gw[2 * j] * sx + o->gw[2 * j + 1] * sy;
+                kup = un >= 0.0 ? kin : o->k[j] + lk[2 * j] * sx + lk[2 * j + 1] * sy;
+                wup = un >= 0.0 ? win : o->om[j] + lw[2 * j] * sx + lw[2 * j + 1] * sy;
                 double dist = sqrt((xj - o->cx[i]) * (xj - o->cx[i]) + (yj - o->cy[i]) * (yj - o->cy[i]));
                 double gkf = 0.5 * ((o->nu + sk[i] * o->nut[i]) + (o->nu + sk[j] * o->nut[j]));
                 double gwf = 0.5 * ((o->nu + sw[i] * o->nut[i]) + (o->nu + sw[j] * o->nut[j]));
@@ -627,7 +665,7 @@ static void sst_update(oracle *o)
         o->nut[i] = sst_nut(o->k[i], o->om[i], o->Sabs[i], f2);
         o->tau[i] = (o->nu + o->nut[i]) / CS2;
     }
-    free(ubc); free(sk); free(sw); free(SS); free(dv);
+    free(ubc); free(sk); free(sw); free(SS); free(dv); free(lk); free(lw);
 }
 
 /* ------------------------------------------------------------------ IMEX step */

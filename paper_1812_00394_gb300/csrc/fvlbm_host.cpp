@@ -1,0 +1,340 @@
+// fvlbm_host.cpp -- host preprocessing of one solver instance: mesh validation, face
+// connectivity, finite-volume geometry (Eq. (advection) needs A, n and Delta l per face), the
+// least-squares gradient weights (Step 2 of Sec. 3.2), periodic gluing, wall distance d
+// (Sec. 2, needed by f1 and f2), the time step from a CFL number, and a Morton renumbering of
+// the cells so that face neighbours sit close in memory on the GPU.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+
+#include "fvlbm_internal.h"
+
+namespace fvlbm {
+namespace {
+
+struct Side {
+    int cell = -1, local = -1;
+};
+
+inline uint64_t edge_id(int a, int b) {
+    uint32_t lo = static_cast<uint32_t>(std::min(a, b)), hi = static_cast<uint32_t>(std::max(a, b));
+    return (static_cast<uint64_t>(lo) << 32) | hi;
+}
+
+// Interleave the low 16 bits of x and y (Morton / Z-order key).
+inline uint32_t morton2(uint32_t x, uint32_t y) {
+    auto spread = [](uint32_t v) {
+        v &= 0xFFFFu;
+        v = (v | (v << 8)) & 0x00FF00FFu;
+        v = (v | (v << 4)) & 0x0F0F0F0Fu;
+        v = (v | (v << 2)) & 0x33333333u;
+        v = (v | (v << 1)) & 0x55555555u;
+        return v;
+    };
+    return spread(x) | (spread(y) << 1);
+}
+
+double point_segment(double px, double py, double ax, double ay, double bx, double by) {
+    const double ex = bx - ax, ey = by - ay;
+    const double L2 = ex * ex + ey * ey;
+    double t = L2 > 0 ? ((px - ax) * ex + (py - ay) * ey) / L2 : 0.0;
+    t = std::min(1.0, std::max(0.0, t));
+    const double dx = ax + t * ex - px, dy = ay + t * ey - py;
+    return std::sqrt(dx * dx + dy * dy);
+}
+
+struct FaceGeo {
+    int nbr = kNone;        // neighbour input cell id, or -(b+1) boundary edge, or kNone
+    double nx = 0, ny = 0;  // unit outward normal
+    double len = 0;
+    double xm = 0, ym = 0;
+    double sx = 0, sy = 0;  // neighbour centroid offset (periodic shift as seen from here)
+};
+
+}  // namespace
+
+int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params &p,
+                     Prepared *out, std::string *why) {
+    const int nc = m.n_cells;
+    if (nc <= 0 || m.n_nodes <= 0 || !m.xy || !m.cell_ptr || !m.cell_nodes) {
+        *why = "empty mesh";
+        return FVLBM_ERR_BAD_MESH;
+    }
+    if (!(p.nu > 0.0) || !(p.rho0 > 0.0) || (p.dt <= 0.0 && !(p.cfl > 0.0))) {
+        *why = "need nu > 0, rho0 > 0 and dt > 0 or cfl > 0";
+        return FVLBM_ERR_BAD_PARAM;
+    }
+    const double *xy = m.xy;
+    std::vector<double> cx(nc), cy(nc), area(nc);
+    std::vector<FaceGeo> face(static_cast<size_t>(nc) * 4);
+    std::unordered_map<uint64_t, Side> open;
+    open.reserve(static_cast<size_t>(nc) * 3);
+    for (int i = 0; i < nc; ++i) {
+        const int p0 = m.cell_ptr[i], nv = m.cell_ptr[i + 1] - p0;
+        if (nv < 3 || nv > 4) {
+            *why = "cell " + std::to_string(i) + " has " + std::to_string(nv) + " nodes";
+            return FVLBM_ERR_BAD_MESH;
+        }
+        for (int l = 0; l < nv; ++l) {
+            const int a = m.cell_nodes[p0 + l];
+            if (a < 0 || a >= m.n_nodes) {
+                *why = "node id out of range";
+                return FVLBM_ERR_BAD_MESH;
+            }
+        }
+        // polygon area and centroid, relative to node 0 of the cell for accuracy on small cells
+        const int n0 = m.cell_nodes[p0];
+        const double ox = xy[2 * n0], oy = xy[2 * n0 + 1];
+        double a2 = 0, mx = 0, my = 0;
+        for (int l = 0; l < nv; ++l) {
+            const int a = m.cell_nodes[p0 + l], b = m.cell_nodes[p0 + (l + 1) % nv];
+            const double x0 = xy[2 * a] - ox, y0 = xy[2 * a + 1] - oy;
+            const double x1 = xy[2 * b] - ox, y1 = xy[2 * b + 1] - oy;
+            const double c = x0 * y1 - x1 * y0;
+            a2 += c;
+            mx += (x0 + x1) * c;
+            my += (y0 + y1) * c;
+        }
+        if (!(a2 > 0.0)) {
+            *why = "cell " + std::to_string(i) + " has non-positive area (nodes must be CCW)";
+            return FVLBM_ERR_BAD_MESH;
+        }
+        area[i] = 0.5 * a2;
+        cx[i] = ox + mx / (3.0 * a2);
+        cy[i] = oy + my / (3.0 * a2);
+        for (int l = 0; l < nv; ++l) {
+            const int a = m.cell_nodes[p0 + l], b = m.cell_nodes[p0 + (l + 1) % nv];
+            const double ex = xy[2 * b] - xy[2 * a], ey = xy[2 * b + 1] - xy[2 * a + 1];
+            FaceGeo &F = face[4 * static_cast<size_t>(i) + l];
+            F.len = std::sqrt(ex * ex + ey * ey);
+            F.nx = ey / F.len;
+            F.ny = -ex / F.len;
+            F.xm = 0.5 * (xy[2 * a] + xy[2 * b]);
+            F.ym = 0.5 * (xy[2 * a + 1] + xy[2 * b + 1]);
+            const uint64_t id = edge_id(a, b);
+            auto it = open.find(id);
+            if (it == open.end()) {
+                open.emplace(id, Side{i, l});
+            } else {
+                if (it->second.cell < 0) {
+                    *why = "edge shared by more than two cells";
+                    return FVLBM_ERR_BAD_MESH;
+                }
+                FaceGeo &G = face[4 * static_cast<size_t>(it->second.cell) + it->second.local];
+                F.nbr = it->second.cell;
+                G.nbr = i;
+                it->second.cell = -1;  // closed
+            }
+        }
+    }
+    // boundary edges
+    const int nbe = bc.n_bedges;
+    std::vector<Side> bside(nbe);
+    for (int b = 0; b < nbe; ++b) {
+        const int a0 = bc.bedge_nodes[2 * b], a1 = bc.bedge_nodes[2 * b + 1];
+        auto it = open.find(edge_id(a0, a1));
+        if (it == open.end() || it->second.cell < 0) {
+            *why = "boundary edge " + std::to_string(b) + " is not a boundary edge of the mesh";
+            return FVLBM_ERR_BAD_BC;
+        }
+        const int t = bc.bedge_type[b];
+        if (t < FVLBM_BC_WALL || t > FVLBM_BC_PERIODIC) {
+            *why = "unknown boundary type";
+            return FVLBM_ERR_BAD_BC;
+        }
+        bside[b] = it->second;
+        face[4 * static_cast<size_t>(it->second.cell) + it->second.local].nbr = -(b + 1);
+    }
+    std::vector<char> glued(nbe, 0);
+    for (int q = 0; q < bc.n_periodic; ++q) {
+        const int ea = bc.periodic_pairs[2 * q], eb = bc.periodic_pairs[2 * q + 1];
+        if (ea < 0 || eb < 0 || ea >= nbe || eb >= nbe || glued[ea] || glued[eb]) {
+            *why = "bad periodic pair";
+            return FVLBM_ERR_BAD_BC;
+        }
+        const double sx = bc.periodic_shift[2 * q], sy = bc.periodic_shift[2 * q + 1];
+        FaceGeo &A = face[4 * static_cast<size_t>(bside[ea].cell) + bside[ea].local];
+        FaceGeo &B = face[4 * static_cast<size_t>(bside[eb].cell) + bside[eb].local];
+        A.nbr = bside[eb].cell;
+        A.sx = -sx;
+        A.sy = -sy;
+        B.nbr = bside[ea].cell;
+        B.sx = sx;
+        B.sy = sy;
+        // the glued face is one face: side B takes side A's normal reversed and its length
+        B.nx = -A.nx;
+        B.ny = -A.ny;
+        B.len = A.len;
+        glued[ea] = glued[eb] = 1;
+    }
+    // every face must now be closed
+    for (int i = 0; i < nc; ++i) {
+        const int nv = m.cell_ptr[i + 1] - m.cell_ptr[i];
+        for (int l = 0; l < nv; ++l) {
+            const FaceGeo &F = face[4 * static_cast<size_t>(i) + l];
+            if (F.nbr == kNone) {
+                *why = "cell " + std::to_string(i) + " has an open edge with no boundary record";
+                return FVLBM_ERR_BAD_BC;
+            }
+            if (F.nbr < 0 && bc.bedge_type[-F.nbr - 1] == FVLBM_BC_PERIODIC &&
+                !glued[-F.nbr - 1]) {
+                *why = "periodic edge without a partner";
+                return FVLBM_ERR_BAD_BC;
+            }
+        }
+    }
+
+    // Morton renumbering of the cells by centroid
+    double x0 = cx[0], x1 = cx[0], y0 = cy[0], y1 = cy[0];
+    for (int i = 0; i < nc; ++i) {
+        x0 = std::min(x0, cx[i]); x1 = std::max(x1, cx[i]);
+        y0 = std::min(y0, cy[i]); y1 = std::max(y1, cy[i]);
+    }
+    const double span = std::max(x1 - x0, y1 - y0) + 1e-300;
+    std::vector<std::pair<uint32_t, int>> key(nc);
+    for (int i = 0; i < nc; ++i) {
+        const uint32_t qx = static_cast<uint32_t>(std::min(65535.0, (cx[i] - x0) / span * 65535.0));
+        const uint32_t qy = static_cast<uint32_t>(std::min(65535.0, (cy[i] - y0) / span * 65535.0));
+        key[i] = {morton2(qx, qy), i};
+    }
+    std::stable_sort(key.begin(), key.end(),
+                     [](const auto &a, const auto &b) { return a.first < b.first; });
+    Prepared &P = *out;
+    P = Prepared();
+    P.nc = nc;
+    P.np = (nc + kTile - 1) / kTile * kTile;
+    P.n_bedges_in = nbe;
+    const size_t np = P.np;
+    P.perm.resize(nc);
+    std::vector<int> inv(nc);
+    for (int k = 0; k < nc; ++k) {
+        P.perm[k] = key[k].second;
+        inv[key[k].second] = k;
+    }
+    // boundary faces (non-periodic edges), numbered in input order
+    std::vector<int> bface_of_edge(nbe, -1);
+    for (int b = 0; b < nbe; ++b) {
+        if (glued[b]) continue;
+        bface_of_edge[b] = P.nb++;
+        P.bedge_of.push_back(b);
+    }
+    P.bowner.resize(P.nb);
+    P.btype.resize(P.nb);
+    P.bval.resize(5 * static_cast<size_t>(P.nb));
+    P.bnrm.resize(2 * static_cast<size_t>(P.nb));
+    P.blen.resize(P.nb);
+    for (int f = 0; f < P.nb; ++f) {
+        const int b = P.bedge_of[f];
+        const FaceGeo &F = face[4 * static_cast<size_t>(bside[b].cell) + bside[b].local];
+        P.bowner[f] = inv[bside[b].cell];
+        P.btype[f] = bc.bedge_type[b];
+        for (int c = 0; c < 5; ++c) P.bval[5 * f + c] = bc.bedge_val[5 * b + c];
+        P.bnrm[2 * f] = F.nx;
+        P.bnrm[2 * f + 1] = F.ny;
+        P.blen[f] = F.len;
+    }
+
+    P.nbr.assign(4 * np, kNone);
+    P.sn.assign(8 * np, 0.0);
+    P.lsq.assign(8 * np, 0.0);
+    P.rown.assign(8 * np, 0.0);
+    P.rnbr.assign(8 * np, 0.0);
+    P.dinv.assign(4 * np, 0.0);
+    P.area.assign(np, 0.0);
+    P.wdist.assign(np, 1e30);
+    for (int k = 0; k < nc; ++k) {
+        const int i = P.perm[k];
+        const int nv = m.cell_ptr[i + 1] - m.cell_ptr[i];
+        P.area[k] = area[i];
+        double dx[4], dy[4];
+        double mxx = 0, mxy = 0, myy = 0;
+        for (int l = 0; l < nv; ++l) {
+            const FaceGeo &F = face[4 * static_cast<size_t>(i) + l];
+            if (F.nbr >= 0) {
+                const double xj = cx[F.nbr] + F.sx, yj = cy[F.nbr] + F.sy;
+                P.nbr[l * np + k] = inv[F.nbr];
+                dx[l] = xj - cx[i];
+                dy[l] = yj - cy[i];
+                P.rnbr[(2 * l) * np + k] = F.xm - xj;
+                P.rnbr[(2 * l + 1) * np + k] = F.ym - yj;
+            } else {
+                P.nbr[l * np + k] = -(bface_of_edge[-F.nbr - 1] + 1);
+                dx[l] = F.xm - cx[i];
+                dy[l] = F.ym - cy[i];
+            }
+            P.sn[(2 * l) * np + k] = F.nx * F.len / area[i];
+            P.sn[(2 * l + 1) * np + k] = F.ny * F.len / area[i];
+            P.rown[(2 * l) * np + k] = F.xm - cx[i];
+            P.rown[(2 * l + 1) * np + k] = F.ym - cy[i];
+            P.dinv[l * np + k] = 1.0 / std::sqrt(dx[l] * dx[l] + dy[l] * dy[l]);
+            mxx += dx[l] * dx[l];
+            mxy += dx[l] * dy[l];
+            myy += dy[l] * dy[l];
+        }
+        const double det = mxx * myy - mxy * mxy;
+        if (!(det > 0.0)) {
+            *why = "degenerate least-squares stencil at cell " + std::to_string(i);
+            return FVLBM_ERR_BAD_MESH;
+        }
+        for (int l = 0; l < nv; ++l) {
+            P.lsq[(2 * l) * np + k] = (myy * dx[l] - mxy * dy[l]) / det;
+            P.lsq[(2 * l + 1) * np + k] = (mxx * dy[l] - mxy * dx[l]) / det;
+        }
+    }
+    // wall distance: centroid to nearest wall face (brute force over wall faces)
+    std::vector<int> walls;
+    for (int b = 0; b < nbe; ++b)
+        if (!glued[b] && bc.bedge_type[b] == FVLBM_BC_WALL) walls.push_back(b);
+    if (!walls.empty()) {
+#pragma omp parallel for schedule(static)
+        for (int k = 0; k < nc; ++k) {
+            const int i = P.perm[k];
+            double best = 1e300;
+            for (int b : walls) {
+                const int a0 = bc.bedge_nodes[2 * b], a1 = bc.bedge_nodes[2 * b + 1];
+                best = std::min(best, point_segment(cx[i], cy[i], xy[2 * a0], xy[2 * a0 + 1],
+                                                    xy[2 * a1], xy[2 * a1 + 1]));
+            }
+            P.wdist[k] = best;
+        }
+    }
+    // time step: dt, or cfl over the largest upwind outflow rate max_i max_alpha
+    // sum_m max(e_alpha . n_m, 0) Delta l_m / A_i (forward-Euler limit of first-order upwind)
+    P.dt = p.dt;
+    if (P.dt <= 0.0) {
+        static const int ex[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+        static const int ey[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+        double rate = 0.0;
+        for (int i = 0; i < nc; ++i) {
+            const int nv = m.cell_ptr[i + 1] - m.cell_ptr[i];
+            for (int a = 1; a < kQ; ++a) {
+                double s = 0.0;
+                for (int l = 0; l < nv; ++l) {
+                    const FaceGeo &F = face[4 * static_cast<size_t>(i) + l];
+                    const double en = ex[a] * F.nx + ey[a] * F.ny;
+                    if (en > 0.0) s += en * F.len;
+                }
+                rate = std::max(rate, s / area[i]);
+            }
+        }
+        P.dt = p.cfl / rate;
+    }
+    // initial fields in internal order (padding cells at rest with rho0)
+    P.rho_i.assign(np, p.rho0);
+    P.u_i.assign(np, 0.0);
+    P.v_i.assign(np, 0.0);
+    P.k_i.assign(np, 0.0);
+    P.w_i.assign(np, 1.0);
+    for (int k = 0; k < nc; ++k) {
+        const int i = P.perm[k];
+        if (p.rho_init) P.rho_i[k] = p.rho_init[i];
+        if (p.u_init) P.u_i[k] = p.u_init[i];
+        if (p.v_init) P.v_i[k] = p.v_init[i];
+        if (p.k_init) P.k_i[k] = p.k_init[i];
+        if (p.omega_init) P.w_i[k] = p.omega_init[i];
+    }
+    return FVLBM_OK;
+}
+
+}  // namespace fvlbm

@@ -1,0 +1,51 @@
+// fvlbm_internal.h -- host-side preprocessed mesh shared by the two translation units of the
+// library (mesh preprocessing in fvlbm_host.cpp, device code and entry points in
+// fvlbm_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fvlbm.h"
+
+namespace fvlbm {
+
+constexpr int kQ = 9;          // D2Q9
+constexpr int kTile = 128;     // cells per thread block; instances are padded to a multiple
+constexpr int kNone = INT32_MIN;  // empty face slot (triangles have 3 faces, padding cells 0)
+
+// One instance after preprocessing, in the library's internal cell order (Morton order of the
+// cell centroids), padded with inert cells (no faces, zero area) to a multiple of kTile.
+// Face slot m of cell i is stored at [m * np + i] (vectors: [(2 m + c) * np + i]) so that one
+// thread per cell reads every array with unit stride.
+struct Prepared {
+    int nc = 0;                 // real cells
+    int np = 0;                 // padded cells
+    int nb = 0;                 // boundary faces (non-periodic boundary edges)
+    int n_bedges_in = 0;        // boundary edges in the input (including periodic ones)
+    std::vector<int> perm;      // internal id -> input cell id   [nc]
+    std::vector<int> nbr;       // [4 np]  neighbour internal id, -(b+1) for boundary face b, kNone
+    std::vector<double> sn;     // [8 np]  n * Delta l / A of face m, out of the cell
+    std::vector<double> lsq;    // [8 np]  least-squares weight W_m = M^{-1} d_m
+    std::vector<double> rown;   // [8 np]  face midpoint - own centroid
+    std::vector<double> rnbr;   // [8 np]  face midpoint - (neighbour centroid + periodic shift)
+    std::vector<double> dinv;   // [4 np]  1 / |d_m| (SST central diffusion distance)
+    std::vector<double> area;   // [np]    0 for padding cells
+    std::vector<double> wdist;  // [np]    distance to the nearest wall face (1e30 if none)
+    // boundary faces, ordered by input boundary-edge index (periodic edges dropped)
+    std::vector<int> bowner;    // internal owner cell
+    std::vector<int> btype;     // FVLBM_BC_*
+    std::vector<double> bval;   // [5 nb] rho_b, u_b, v_b, k_b, omega_b
+    std::vector<double> bnrm;   // [2 nb] unit normal out of the fluid
+    std::vector<double> blen;   // [nb]
+    std::vector<int> bedge_of;  // [nb] input boundary-edge index of each boundary face
+    double dt = 0.0;
+    std::vector<double> rho_i, u_i, v_i, k_i, w_i;  // initial fields, internal order [np]
+};
+
+// Validates and preprocesses one (mesh, bc, params) triple.  Returns FVLBM_OK or an error
+// code, with a message in *why.
+int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params &p,
+                     Prepared *out, std::string *why);
+
+}  // namespace fvlbm

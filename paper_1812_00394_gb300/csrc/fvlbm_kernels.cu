@@ -1,0 +1,1317 @@
+// fvlbm_kernels.cu -- sm_103a kernels and the C ABI entry points of the FVLBM time step.
+//
+// One thread owns one cell.  Cells are Morton ordered per instance and instances are padded
+// to a multiple of kTile (= blockDim.x), so every block belongs to exactly one instance and
+// reads that instance's parameters.  Every per-cell array is structure-of-arrays with stride
+// np (all instances), so a warp reads 32 consecutive words per field.  Face fluxes are
+// accumulated per cell over the cell's own face list (each interior face is evaluated by
+// both of its cells with bit-identical face values), so no atomics are needed and the sum is
+// deterministic.
+//
+// Step (Sec. 3.2, Steps 1-7) as launched per time step:
+//   [k_sst_grad, k_sst_update]      Step 1 (k-omega SST, Eq. (SSTequint), Eq. (turbtau))
+//   k_stage1                        stage 1: f^(1) from f^n (Eq. (fnewstage), J = 1)
+//   k_grad, k_flux_stage<1>         Gamma^a(f^(1)) (Eq. (advection)); stage 2 solve
+//   k_grad, k_flux_stage<2>         Gamma^a(f^(2)); stage 3 solve
+//   k_grad, k_flux_stage<3>         Gamma^a(f^(3)); Eq. (imextwo); macros (Step 7)
+// The stage algebra uses that the last row of the implicit tableau equals its weights:
+//   f^{n+1} = f^(3) + dt (-1/6 Gamma^a(1) - 1/6 Gamma^a(2) + 1/3 Gamma^a(3)),
+// and carries two accumulators B = f^n + dt/2 Gamma^a(1) + dt/3 (Gamma^c(1) + Gamma^c(2)) and
+// C = -dt/6 (Gamma^a(1) + Gamma^a(2)) instead of all six Gamma arrays.
+//
+// Storage of f: the deviation f_alpha - w_alpha rho0, in double (FVLBM_FP64) or float
+// (FVLBM_FP32_DEV).  Every map of the step is affine in f with weights summing to one, and
+// the convection of a constant vanishes on closed cells, so the offset w_alpha rho0 drops out.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "fvlbm_internal.h"
+
+namespace fvlbm {
+
+// ------------------------------------------------------------------ lattice constants
+__device__ __forceinline__ int ex_of(int a) {
+    return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
+}
+__device__ __forceinline__ int ey_of(int a) {
+    return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
+}
+template <class T>
+__device__ __forceinline__ T w_of(int a) {
+    return a == 0 ? T(4.0 / 9.0) : (a < 5 ? T(1.0 / 9.0) : T(1.0 / 36.0));
+}
+
+// SST constants (Sec. 2)
+constexpr double kA1 = 0.31, kBstar = 0.09, kKappa = 0.41;
+constexpr double kSk1 = 0.85, kSw1 = 0.5, kB1 = 0.075;
+constexpr double kSk2 = 1.0, kSw2 = 0.856, kB2 = 0.0828;
+constexpr double kCs2 = 1.0 / 3.0;
+
+struct InstParam {
+    double dt, nu, rho0, omega_min;
+    int sst;  // 1: k-omega SST instance; 0: laminar (SST kernels skip its tiles)
+};
+
+template <class T>
+struct Geo {
+    const int *__restrict__ nbr;   // [4 np]
+    const T *__restrict__ sn;      // [8 np]
+    const T *__restrict__ lsq;     // [8 np]
+    const T *__restrict__ rown;    // [8 np]
+    const T *__restrict__ rnbr;    // [8 np]
+    const T *__restrict__ dinv;    // [4 np]
+    const T *__restrict__ area;    // [np]
+    const T *__restrict__ wdist;   // [np]
+    const int *__restrict__ tile_inst;
+    const InstParam *__restrict__ ip;
+    const int *__restrict__ btype;  // [nbt]
+    const T *__restrict__ bval;     // [5 nbt] field-major: bval[c * nbt + b]
+    int np, nbt;
+};
+
+// ------------------------------------------------------------------ cell algebra
+// Moments of a deviation vector d = f - w rho0: drho = sum d, rho = rho0 + drho, u = sum e d / rho.
+template <class T>
+__device__ __forceinline__ void moments(const T *d, T rho0, T &drho, T &rho, T &u, T &v) {
+    T s = 0, jx = 0, jy = 0;
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+        s += d[a];
+        jx += T(ex_of(a)) * d[a];
+        jy += T(ey_of(a)) * d[a];
+    }
+    drho = s;
+    rho = rho0 + s;
+    u = jx / rho;
+    v = jy / rho;
+}
+
+// Equilibrium deviation f^eq(rho, u) - w rho0 = w [drho + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u.u)].
+template <class T>
+__device__ __forceinline__ void feq_dev(T drho, T rho, T u, T v, T *eq) {
+    const T uu = T(1.5) * (u * u + v * v);
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+        const T eu = T(ex_of(a)) * u + T(ey_of(a)) * v;
+        eq[a] = w_of<T>(a) * (drho + rho * (T(3) * eu + T(4.5) * eu * eu - uu));
+    }
+}
+
+// Boundary face values f_{alpha,bc} (deviation form) from the owner cell: non-equilibrium
+// extrapolation for wall / inlet / outlet, characteristic choice on the far field.
+template <class T>
+__device__ __forceinline__ void boundary_values(int type, const T *__restrict__ bval, int b,
+                                                int nbt, T snx, T sny, const T *fP, T drP, T rP,
+                                                T uP, T vP, T rho0, T *out) {
+    T eqP[kQ], eqB[kQ];
+    feq_dev(drP, rP, uP, vP, eqP);
+    const T rb = bval[0 * nbt + b], ub = bval[1 * nbt + b], vb = bval[2 * nbt + b];
+    if (type == FVLBM_BC_WALL || type == FVLBM_BC_INLET) {
+        feq_dev(drP, rP, ub, vb, eqB);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) out[a] = eqB[a] + (fP[a] - eqP[a]);
+    } else if (type == FVLBM_BC_OUTLET) {
+        feq_dev(rb - rho0, rb, uP, vP, eqB);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) out[a] = eqB[a] + (fP[a] - eqP[a]);
+    } else {
+        feq_dev(rb - rho0, rb, ub, vb, eqB);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+            const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
+            out[a] = en < T(0) ? eqB[a] : fP[a];
+        }
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void load9(const T *__restrict__ f, size_t np, int i, T *o) {
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) o[a] = f[a * np + i];
+}
+template <class T>
+__device__ __forceinline__ void store9(T *__restrict__ f, size_t np, int i, const T *o) {
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) f[a * np + i] = o[a];
+}
+
+// ------------------------------------------------------------------ stage 1 (local)
+// f^(1) = [f^n + (dt/tau)(1/4) f^eq(rho^n, u^n)] / (1 + (dt/tau)/4): Eq. (fnewstage), J = 1.
+template <class T>
+__global__ void __launch_bounds__(kTile) k_stage1(const T *__restrict__ fn, T *__restrict__ fs,
+                                                  const T *__restrict__ tau, Geo<T> G) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
+    const T rho0 = T(P.rho0);
+    T f[kQ], eq[kQ], dr, r, u, v;
+    load9(fn, np, i, f);
+    moments(f, rho0, dr, r, u, v);
+    feq_dev(dr, r, u, v, eq);
+    const T zq = T(P.dt) / tau[i] * T(0.25);
+    const T inv = T(1) / (T(1) + zq);
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) f[a] = (f[a] + zq * eq[a]) * inv;
+    store9(fs, np, i, f);
+}
+
+// ------------------------------------------------------------------ gradient of f
+// Least-squares cell gradient (Step 2): g_i = sum_m W_m (f_m - f_i), data from face neighbours
+// and, on boundary faces, the boundary value at the face midpoint.
+template <class T>
+__global__ void __launch_bounds__(kTile) k_grad(const T *__restrict__ f, T *__restrict__ g,
+                                                Geo<T> G) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    const T rho0 = T(G.ip[G.tile_inst[blockIdx.x]].rho0);
+    T fi[kQ], gx[kQ], gy[kQ];
+    load9(f, np, i, fi);
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) gx[a] = gy[a] = T(0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int nb = G.nbr[m * np + i];
+        if (nb == kNone) continue;
+        const T wx = G.lsq[(2 * m) * np + i], wy = G.lsq[(2 * m + 1) * np + i];
+        if (nb >= 0) {
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) {
+                const T d = f[a * np + nb] - fi[a];
+                gx[a] += wx * d;
+                gy[a] += wy * d;
+            }
+        } else {
+            const int b = -nb - 1;
+            T dr, r, u, v, fb[kQ];
+            moments(fi, rho0, dr, r, u, v);
+            boundary_values(G.btype[b], G.bval + b, 0, G.nbt, G.sn[(2 * m) * np + i],
+                            G.sn[(2 * m + 1) * np + i], fi, dr, r, u, v, rho0, fb);
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) {
+                const T d = fb[a] - fi[a];
+                gx[a] += wx * d;
+                gy[a] += wy * d;
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+        g[(2 * a) * np + i] = gx[a];
+        g[(2 * a + 1) * np + i] = gy[a];
+    }
+}
+
+// ------------------------------------------------------------------ block reduction (FP64)
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N], double *out) {
+    __shared__ double red[kTile / 32][N];
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < N; ++k) red[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double s = 0;
+        for (int w = 0; w < kTile / 32; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// ------------------------------------------------------------------ flux + stage solve
+// Gamma^a_alpha,i = -sum_m (e_alpha . n_m Delta l_m / A_i) f_{alpha,bc,m}  (Eq. (advection)) with
+// upwind linear face values, then the local algebra of the next stage (see file header).
+template <class T, int STAGE, bool STATS>
+__global__ void __launch_bounds__(kTile)
+    k_flux_stage(const T *__restrict__ fs, const T *__restrict__ g, T *__restrict__ fs_out,
+                 T *__restrict__ fn, T *__restrict__ Bacc, T *__restrict__ Cacc,
+                 const T *__restrict__ tau, T *__restrict__ mac, double *__restrict__ partial,
+                 Geo<T> G) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
+    const T rho0 = T(P.rho0);
+    const T dt = T(P.dt);
+    T fi[kQ], acc[kQ];
+    load9(fs, np, i, fi);
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) acc[a] = T(0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int nb = G.nbr[m * np + i];
+        if (nb == kNone) continue;
+        const T snx = G.sn[(2 * m) * np + i], sny = G.sn[(2 * m + 1) * np + i];
+        if (nb >= 0) {
+            const T rox = G.rown[(2 * m) * np + i], roy = G.rown[(2 * m + 1) * np + i];
+            const T rnx = G.rnbr[(2 * m) * np + i], rny = G.rnbr[(2 * m + 1) * np + i];
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) {
+                const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
+                T fv;
+                if (en >= T(0))
+                    fv = fi[a] + g[(2 * a) * np + i] * rox + g[(2 * a + 1) * np + i] * roy;
+                else
+                    fv = fs[a * np + nb] + g[(2 * a) * np + nb] * rnx + g[(2 * a + 1) * np + nb] * rny;
+                acc[a] += en * fv;
+            }
+        } else {
+            const int b = -nb - 1;
+            T dr, r, u, v, fb[kQ];
+            moments(fi, rho0, dr, r, u, v);
+            boundary_values(G.btype[b], G.bval + b, 0, G.nbt, snx, sny, fi, dr, r, u, v, rho0, fb);
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) acc[a] += (T(ex_of(a)) * snx + T(ey_of(a)) * sny) * fb[a];
+        }
+    }
+    // acc = -Gamma^a
+    const T t_i = tau[i];
+    if (STAGE == 1) {
+        // fi = f^(1); f^n, Gamma^c(1) from f^n and f^(1)
+        T f0[kQ], eq[kQ], X[kQ], dr, r, u, v;
+        load9(fn, np, i, f0);
+        moments(f0, rho0, dr, r, u, v);
+        feq_dev(dr, r, u, v, eq);
+        T gc1[kQ];
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+            gc1[a] = (eq[a] - fi[a]) / t_i;
+            X[a] = f0[a] - T(0.5) * dt * acc[a];
+        }
+        moments(X, rho0, dr, r, u, v);
+        feq_dev(dr, r, u, v, eq);
+        const T zq = dt / t_i * T(0.25);
+        const T inv = T(1) / (T(1) + zq);
+        T f2[kQ];
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+            f2[a] = (X[a] + zq * eq[a]) * inv;
+            const T gc2 = (eq[a] - f2[a]) / t_i;
+            Bacc[a * np + i] = X[a] + dt / T(3) * (gc1[a] + gc2);
+            Cacc[a * np + i] = dt / T(6) * acc[a];
+        }
+        store9(fs_out, np, i, f2);
+    } else if (STAGE == 2) {
+        T X[kQ], eq[kQ], dr, r, u, v, f3[kQ];
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) X[a] = Bacc[a * np + i] - T(0.5) * dt * acc[a];
+        moments(X, rho0, dr, r, u, v);
+        feq_dev(dr, r, u, v, eq);
+        const T zt = dt / t_i / T(3);
+        const T inv = T(1) / (T(1) + zt);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+            f3[a] = (X[a] + zt * eq[a]) * inv;
+            Cacc[a * np + i] = Cacc[a * np + i] + dt / T(6) * acc[a];
+        }
+        store9(fs_out, np, i, f3);
+    } else {
+        T fnew[kQ], dr, r, u, v;
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) fnew[a] = fi[a] + Cacc[a * np + i] - dt / T(3) * acc[a];
+        store9(fn, np, i, fnew);
+        moments(fnew, rho0, dr, r, u, v);
+        if (STATS) {
+            const double uo = double(mac[1 * np + i]), vo = double(mac[2 * np + i]);
+            const double un = double(u), vn = double(v);
+            const bool bad = !(isfinite(un) && isfinite(vn) && isfinite(double(r)));
+            double s[4] = {(un - uo) * (un - uo) + (vn - vo) * (vn - vo), un * un + vn * vn,
+                           double(r) * double(G.area[i]), bad ? 1.0 : 0.0};
+            block_sum<4>(s, partial + 4 * blockIdx.x);
+        }
+        mac[0 * np + i] = r;
+        mac[1 * np + i] = u;
+        mac[2 * np + i] = v;
+    }
+}
+
+// Sum per-block partials into per-instance totals (one block per instance).
+__global__ void k_reduce_instances(const double *__restrict__ partial,
+                                   const int *__restrict__ inst_tile0, double *__restrict__ out) {
+    const int inst = blockIdx.x;
+    const int t0 = inst_tile0[inst], t1 = inst_tile0[inst + 1];
+    double s[4] = {0, 0, 0, 0};
+    for (int t = t0 + threadIdx.x; t < t1; t += kTile)
+        for (int k = 0; k < 4; ++k) s[k] += partial[4 * t + k];
+    block_sum<4>(s, out + 4 * inst);
+}
+
+// ------------------------------------------------------------------ SST (Step 1)
+// Gradients of u, v, k, omega (least squares with boundary values), the limited k / omega
+// gradients used for upwind face values, and the blending function f1.
+template <class T>
+__global__ void __launch_bounds__(kTile)
+    k_sst_grad(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
+               T *__restrict__ grads, T *__restrict__ f1out, Geo<T> G) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
+    if (!P.sst) return;  // laminar instance: tau stays nu / cs^2
+    const T nu = T(P.nu);
+    const T ui = mac[np + i], vi = mac[2 * np + i], ki = kk[i], wi = ww[i];
+    const T di = G.wdist[i];
+    T g[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // du/dx du/dy dv/dx dv/dy dk/dx dk/dy dw/dx dw/dy
+    T kq[4], wq[4];                       // face-neighbour (or boundary) values of k, omega
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        kq[m] = ki;
+        wq[m] = wi;
+        const int nb = G.nbr[m * np + i];
+        if (nb == kNone) continue;
+        T du, dv, dk, dw;
+        if (nb >= 0) {
+            du = mac[np + nb] - ui;
+            dv = mac[2 * np + nb] - vi;
+            dk = kk[nb] - ki;
+            dw = ww[nb] - wi;
+        } else {
+            const int b = -nb - 1;
+            const int t = G.btype[b];
+            T ub, vb, kb, wb;
+            if (t == FVLBM_BC_WALL) {
+                ub = G.bval[1 * G.nbt + b]; vb = G.bval[2 * G.nbt + b]; kb = T(0);
+                wb = T(60) * nu / (T(kB1) * di * di);
+            } else if (t == FVLBM_BC_OUTLET) {
+                ub = ui; vb = vi; kb = ki; wb = wi;
+            } else {
+                ub = G.bval[1 * G.nbt + b]; vb = G.bval[2 * G.nbt + b];
+                kb = G.bval[3 * G.nbt + b]; wb = G.bval[4 * G.nbt + b];
+            }
+            du = ub - ui; dv = vb - vi; dk = kb - ki; dw = wb - wi;
+        }
+        kq[m] = ki + dk;
+        wq[m] = wi + dw;
+        const T wx = G.lsq[(2 * m) * np + i], wy = G.lsq[(2 * m + 1) * np + i];
+        g[0] += wx * du; g[1] += wy * du;
+        g[2] += wx * dv; g[3] += wy * dv;
+        g[4] += wx * dk; g[5] += wy * dk;
+        g[6] += wx * dw; g[7] += wy * dw;
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) grads[c * np + i] = g[c];
+    // Barth-Jespersen limiters of the k and omega reconstructions (second-order upwind on
+    // unstructured cells): face values stay within the local min / max
+    T klo = ki, khi = ki, wlo = wi, whi = wi;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        klo = fmin(klo, kq[m]); khi = fmax(khi, kq[m]);
+        wlo = fmin(wlo, wq[m]); whi = fmax(whi, wq[m]);
+    }
+    T pk = T(1), pw = T(1);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (G.nbr[m * np + i] == kNone) continue;
+        const T rx = G.rown[(2 * m) * np + i], ry = G.rown[(2 * m + 1) * np + i];
+        const T dkf = g[4] * rx + g[5] * ry, dwf = g[6] * rx + g[7] * ry;
+        if (dkf > T(0)) pk = fmin(pk, (khi - ki) / dkf);
+        else if (dkf < T(0)) pk = fmin(pk, (klo - ki) / dkf);
+        if (dwf > T(0)) pw = fmin(pw, (whi - wi) / dwf);
+        else if (dwf < T(0)) pw = fmin(pw, (wlo - wi) / dwf);
+    }
+    grads[8 * np + i] = pk * g[4];
+    grads[9 * np + i] = pk * g[5];
+    grads[10 * np + i] = pw * g[6];
+    grads[11 * np + i] = pw * g[7];
+    // f1 = tanh(arg1^4) (Sec. 2), kinematic form
+    T cd = T(2 * kSw2) / wi * (g[4] * g[6] + g[5] * g[7]);
+    cd = cd > T(1e-20) ? cd : T(1e-20);
+    const T a = sqrt(ki) / (T(kBstar) * wi * di);
+    const T bb = T(500) * nu / (wi * di * di);
+    const T c = T(4 * kSw2) * ki / (cd * di * di);
+    const T arg1 = fmin(fmax(a, bb), c);
+    const T a2 = arg1 * arg1;
+    f1out[i] = tanh(a2 * a2);
+}
+
+// Face convection (limited second-order upwind, mean face velocity) and central diffusion (mean face
+// coefficient) of k and omega, explicit production and cross diffusion, point-implicit
+// destruction; then f2, nu_t = a1 k / max(a1 omega, S f2) and tau = (nu + nu_t)/cs^2.
+template <class T>
+__global__ void __launch_bounds__(kTile)
+    k_sst_update(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
+                 const T *__restrict__ nut, const T *__restrict__ grads,
+                 const T *__restrict__ f1a, T *__restrict__ k_out, T *__restrict__ w_out,
+                 T *__restrict__ nut_out, T *__restrict__ tau, Geo<T> G) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
+    if (!P.sst) return;  // laminar instance
+    const T nu = T(P.nu), dt = T(P.dt);
+    const T ui = mac[np + i], vi = mac[2 * np + i], ki = kk[i], wi = ww[i], nti = nut[i];
+    const T di = G.wdist[i];
+    T g[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) g[c] = grads[c * np + i];
+    const T f1 = f1a[i];
+    const T sk_i = f1 * T(kSk1) + (T(1) - f1) * T(kSk2);
+    const T sw_i = f1 * T(kSw1) + (T(1) - f1) * T(kSw2);
+    T ck = 0, cw = 0, dk = 0, dw = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int nb = G.nbr[m * np + i];
+        if (nb == kNone) continue;
+        const T snx = G.sn[(2 * m) * np + i], sny = G.sn[(2 * m + 1) * np + i];  // n dl / A
+        const T rox = G.rown[(2 * m) * np + i], roy = G.rown[(2 * m + 1) * np + i];
+        const T kin = ki + grads[8 * np + i] * rox + grads[9 * np + i] * roy;
+        const T win = wi + grads[10 * np + i] * rox + grads[11 * np + i] * roy;
+        const T dinv = G.dinv[m * np + i];
+        // |n dl / A| -> dl / A
+        const T dla = sqrt(snx * snx + sny * sny);
+        if (nb >= 0) {
+            const T uf = T(0.5) * (ui + mac[np + nb]), vf = T(0.5) * (vi + mac[2 * np + nb]);
+            const T un = uf * snx + vf * sny;  // (u_f . n) dl / A
+            T kup, wup;
+            if (un >= T(0)) {
+                kup = kin; wup = win;
+            } else {
+                const T rnx = G.rnbr[(2 * m) * np + i], rny = G.rnbr[(2 * m + 1) * np + i];
+                kup = kk[nb] + grads[8 * np + nb] * rnx + grads[9 * np + nb] * rny;
+                wup = ww[nb] + grads[10 * np + nb] * rnx + grads[11 * np + nb] * rny;
+            }
+            const T f1j = f1a[nb], ntj = nut[nb];
+            const T skj = f1j * T(kSk1) + (T(1) - f1j) * T(kSk2);
+            const T swj = f1j * T(kSw1) + (T(1) - f1j) * T(kSw2);
+            const T gkf = T(0.5) * ((nu + sk_i * nti) + (nu + skj * ntj));
+            const T gwf = T(0.5) * ((nu + sw_i * nti) + (nu + swj * ntj));
+            ck += un * kup;
+            cw += un * wup;
+            dk += gkf * (kk[nb] - ki) * dinv * dla;
+            dw += gwf * (ww[nb] - wi) * dinv * dla;
+        } else {
+            const int b = -nb - 1;
+            const int t = G.btype[b];
+            T ub, vb, kb, wb;
+            if (t == FVLBM_BC_WALL) {
+                ub = G.bval[1 * G.nbt + b]; vb = G.bval[2 * G.nbt + b]; kb = T(0);
+                wb = T(60) * nu / (T(kB1) * di * di);
+            } else if (t == FVLBM_BC_OUTLET) {
+                ub = ui; vb = vi; kb = ki; wb = wi;
+            } else {
+                ub = G.bval[1 * G.nbt + b]; vb = G.bval[2 * G.nbt + b];
+                kb = G.bval[3 * G.nbt + b]; wb = G.bval[4 * G.nbt + b];
+            }
+            const T un = ub * snx + vb * sny;
+            const T kup = un >= T(0) ? kin : kb;
+            const T wup = un >= T(0) ? win : wb;
+            ck += un * kup;
+            cw += un * wup;
+            dk += (nu + sk_i * nti) * (kb - ki) * dinv * dla;
+            dw += (nu + sw_i * nti) * (wb - wi) * dinv * dla;
+        }
+    }
+    const T s11 = g[0], s22 = g[3], s12 = T(0.5) * (g[1] + g[2]);
+    const T SS = s11 * s11 + s22 * s22 + T(2) * s12 * s12;
+    const T dv = s11 + s22;
+    const T Sabs = sqrt(T(2) * SS);
+    const T cw1 = T(kB1 / kBstar - kSw1 * kKappa * kKappa / 0.3);
+    const T cw2 = T(kB2 / kBstar - kSw2 * kKappa * kKappa / 0.3);
+    const T gam = f1 * cw1 + (T(1) - f1) * cw2;
+    const T pk = nti * (T(2) * SS - T(2.0 / 3.0) * dv * dv) - T(2.0 / 3.0) * ki * dv;
+    T pw = gam * (T(2) * SS - T(2.0 / 3.0) * dv * dv);
+    if (nti > T(0)) pw -= T(2.0 / 3.0) * gam * ki * dv / nti;
+    const T cross = T(2) * (T(1) - f1) * T(kSw2) / wi * (g[4] * g[6] + g[5] * g[7]);
+    const T rk = -ck + dk + pk;
+    const T rw = -cw + dw + pw + cross;
+    const T beta = f1 * T(kB1) + (T(1) - f1) * T(kB2);
+    T kn = (ki + dt * rk) / (T(1) + dt * T(kBstar) * wi);
+    T wn = (wi + dt * rw) / (T(1) + dt * beta * wi);
+    kn = kn > T(0) ? kn : T(0);
+    wn = wn > T(P.omega_min) ? wn : T(P.omega_min);
+    const T arg2 = fmax(T(2) * sqrt(kn) / (T(kBstar) * wn * di), T(500) * nu / (wn * di * di));
+    const T f2 = tanh(arg2 * arg2);
+    const T ntn = T(kA1) * kn / fmax(T(kA1) * wn, Sabs * f2);
+    k_out[i] = kn;
+    w_out[i] = wn;
+    nut_out[i] = ntn;
+    tau[i] = (nu + ntn) / T(kCs2);
+}
+
+// ------------------------------------------------------------------ state I/O kernels
+template <class T>
+__global__ void k_init_state(T *__restrict__ fn, T *__restrict__ mac, const double *__restrict__ r0,
+                             const double *__restrict__ u0, const double *__restrict__ v0,
+                             Geo<T> G) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    const T rho0 = T(G.ip[G.tile_inst[blockIdx.x]].rho0);
+    const T r = T(r0[i]), u = T(u0[i]), v = T(v0[i]);
+    T eq[kQ];
+    feq_dev(T(r0[i] - double(rho0)), r, u, v, eq);
+    store9(fn, np, i, eq);
+    T dr, rr, uu, vv;
+    moments(eq, rho0, dr, rr, uu, vv);
+    mac[i] = rr;
+    mac[np + i] = uu;
+    mac[2 * np + i] = vv;
+}
+
+// out[perm[k] * 9 + a] = f[a][off + k] + w_a rho0   (k < nc)
+template <class T>
+__global__ void k_gather_f(const T *__restrict__ f, const int *__restrict__ perm, int off, int nc,
+                           double rho0, size_t np, double *__restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nc) return;
+    const int dst = perm[k];
+    for (int a = 0; a < kQ; ++a) {
+        const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        out[static_cast<size_t>(dst) * kQ + a] = double(f[a * np + off + k]) + wa * rho0;
+    }
+}
+
+template <class T>
+__global__ void k_scatter_f(T *__restrict__ f, T *__restrict__ mac, const int *__restrict__ perm,
+                            int off, int nc, double rho0, size_t np,
+                            const double *__restrict__ in) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nc) return;
+    const int src = perm[k];
+    T d[kQ];
+    for (int a = 0; a < kQ; ++a) {
+        const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        d[a] = T(in[static_cast<size_t>(src) * kQ + a] - wa * rho0);
+        f[a * np + off + k] = d[a];
+    }
+    T dr, r, u, v;
+    moments(d, T(rho0), dr, r, u, v);
+    mac[off + k] = r;
+    mac[np + off + k] = u;
+    mac[2 * np + off + k] = v;
+}
+
+// fields[c][perm[k]] for c = rho, u, v, k, omega, nu_t
+template <class T>
+__global__ void k_gather_fields(const T *__restrict__ mac, const T *__restrict__ kk,
+                                const T *__restrict__ ww, const T *__restrict__ nut,
+                                const int *__restrict__ perm, int off, int nc, size_t np,
+                                double *__restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nc) return;
+    const int dst = perm[k];
+    const size_t n = nc;
+    out[0 * n + dst] = double(mac[off + k]);
+    out[1 * n + dst] = double(mac[np + off + k]);
+    out[2 * n + dst] = double(mac[2 * np + off + k]);
+    out[3 * n + dst] = double(kk[off + k]);
+    out[4 * n + dst] = double(ww[off + k]);
+    out[5 * n + dst] = double(nut[off + k]);
+}
+
+// Per wall face momentum flux and Cp (FP64): out[3][nb_inst] = fx, fy, cp.
+template <class T>
+__global__ void k_wall_forces(const T *__restrict__ fn, const int *__restrict__ bowner,
+                             const T *__restrict__ bnrm, const T *__restrict__ blen, int b0,
+                             int nbi, double rho0, double uref, Geo<T> G,
+                             double *__restrict__ out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nbi) return;
+    const int b = b0 + q;
+    const size_t np = G.np;
+    out[q] = out[nbi + q] = out[2 * nbi + q] = 0.0;
+    if (G.btype[b] != FVLBM_BC_WALL) return;
+    const int i = bowner[b];
+    T fi[kQ], fb[kQ], dr, r, u, v;
+    load9(fn, np, i, fi);
+    moments(fi, T(rho0), dr, r, u, v);
+    const T nx = bnrm[b], ny = bnrm[G.nbt + b];
+    boundary_values(G.btype[b], G.bval + b, 0, G.nbt, nx, ny, fi, dr, r, u, v, T(rho0), fb);
+    double fx = 0, fy = 0;
+    for (int a = 0; a < kQ; ++a) {
+        const double en = double(ex_of(a)) * double(nx) + double(ey_of(a)) * double(ny);
+        const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        const double m = en * (double(fb[a]) + wa * rho0) * double(blen[b]);
+        fx += ex_of(a) * m;
+        fy += ey_of(a) * m;
+    }
+    out[q] = fx;
+    out[nbi + q] = fy;
+    out[2 * nbi + q] = (kCs2 * double(r) - kCs2 * rho0) / (0.5 * rho0 * uref * uref);
+}
+
+}  // namespace fvlbm
+
+// ==================================================================== handle and C ABI
+using namespace fvlbm;
+
+namespace {
+
+struct InstInfo {
+    int nc, np, nb, n_bedges_in, sst;
+    int cell_off, tile_off, bface_off;
+    double dt, rho0, uref, lref, alpha_deg, nu;
+    std::vector<int> bedge_of;   // boundary face -> input edge (local)
+};
+
+struct KernelTimer {
+    std::string name;
+    double ms = 0;
+    int launches = 0;
+};
+
+}  // namespace
+
+struct fvlbm_handle {
+    int device = 0;
+    int precision = FVLBM_FP64;
+    bool sst = false;
+    bool own_stream = false;
+    cudaStream_t stream = nullptr;
+    int np = 0, nbt = 0, ntiles = 0, ninst = 0;
+    std::vector<InstInfo> inst;
+    long long steps = 0;
+    size_t device_bytes = 0;
+    std::vector<void *> allocs;
+    // device arrays (element type T = double or float; stored as void*)
+    int *d_nbr = nullptr, *d_tile_inst = nullptr, *d_btype = nullptr, *d_bowner = nullptr;
+    int *d_perm = nullptr, *d_inst_tile0 = nullptr;
+    InstParam *d_ip = nullptr;
+    void *sn = nullptr, *lsq = nullptr, *rown = nullptr, *rnbr = nullptr, *dinv = nullptr;
+    void *area = nullptr, *wdist = nullptr, *bval = nullptr, *bnrm = nullptr, *blen = nullptr;
+    void *fn = nullptr, *s0 = nullptr, *s1 = nullptr, *bacc = nullptr, *cacc = nullptr;
+    void *grad = nullptr, *tau = nullptr, *mac = nullptr;
+    void *kk[2] = {nullptr, nullptr}, *ww[2] = {nullptr, nullptr}, *nut[2] = {nullptr, nullptr};
+    void *sgrad = nullptr, *f1 = nullptr;
+    int turb = 0;  // which of the k/omega/nu_t ping-pong buffers is current
+    double *d_partial = nullptr, *d_inst_sums = nullptr, *d_io = nullptr;
+    size_t io_bytes = 0;
+    // [0]: 1 step (laminar); [1 + parity]: kGraphSteps steps starting from k/omega/nu_t
+    // ping-pong parity 0 or 1 (laminar runs use [1] only)
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    bool profiling = false;
+    std::vector<KernelTimer> timers;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+};
+
+namespace {
+
+constexpr int kGraphSteps = 16;
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) return FVLBM_ERR_OOM;
+    return FVLBM_ERR_CUDA;
+}
+
+#define CK(x)                                       \
+    do {                                            \
+        cudaError_t e_ = (x);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+template <class T>
+Geo<T> geo_of(const fvlbm_handle *h) {
+    Geo<T> G;
+    G.nbr = h->d_nbr;
+    G.sn = static_cast<const T *>(h->sn);
+    G.lsq = static_cast<const T *>(h->lsq);
+    G.rown = static_cast<const T *>(h->rown);
+    G.rnbr = static_cast<const T *>(h->rnbr);
+    G.dinv = static_cast<const T *>(h->dinv);
+    G.area = static_cast<const T *>(h->area);
+    G.wdist = static_cast<const T *>(h->wdist);
+    G.tile_inst = h->d_tile_inst;
+    G.ip = h->d_ip;
+    G.btype = h->d_btype;
+    G.bval = static_cast<const T *>(h->bval);
+    G.np = h->np;
+    G.nbt = h->nbt;
+    return G;
+}
+
+int dalloc(fvlbm_handle *h, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->allocs.push_back(*p);
+    h->device_bytes += bytes;
+    return FVLBM_OK;
+}
+
+template <class T>
+int upload_as(fvlbm_handle *h, void **dst, const std::vector<double> &src) {
+    std::vector<T> tmp(src.begin(), src.end());
+    int rc = dalloc(h, dst, tmp.size() * sizeof(T));
+    if (rc) return rc;
+    CK(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return FVLBM_OK;
+}
+
+template <class V>
+int upload_raw(fvlbm_handle *h, V **dst, const std::vector<V> &src) {
+    int rc = dalloc(h, reinterpret_cast<void **>(dst), src.size() * sizeof(V));
+    if (rc) return rc;
+    CK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice));
+    return FVLBM_OK;
+}
+
+// Launch helper: records events around the launch when profiling.
+template <class F>
+void launch(fvlbm_handle *h, int id, const char *name, F &&fn) {
+    if (h->profiling) {
+        if (static_cast<int>(h->timers.size()) <= id) h->timers.resize(id + 1);
+        h->timers[id].name = name;
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, h->stream);
+        fn();
+        cudaEventRecord(b, h->stream);
+        h->pending.push_back({id, {a, b}});
+    } else {
+        fn();
+    }
+}
+
+enum KernelId { K_SST_GRAD, K_SST_UPDATE, K_STAGE1, K_GRAD, K_FLUX1, K_FLUX2, K_FLUX3, K_REDUCE };
+
+template <class T>
+void enqueue_step(fvlbm_handle *h, bool stats) {
+    Geo<T> G = geo_of<T>(h);
+    const dim3 grid(h->ntiles), block(kTile);
+    cudaStream_t s = h->stream;
+    T *fn = static_cast<T *>(h->fn), *s0 = static_cast<T *>(h->s0), *s1 = static_cast<T *>(h->s1);
+    T *B = static_cast<T *>(h->bacc), *C = static_cast<T *>(h->cacc);
+    T *g = static_cast<T *>(h->grad), *tau = static_cast<T *>(h->tau), *mac = static_cast<T *>(h->mac);
+    if (h->sst) {
+        const int c = h->turb, n = 1 - h->turb;
+        T *kc = static_cast<T *>(h->kk[c]), *wc = static_cast<T *>(h->ww[c]);
+        T *nc = static_cast<T *>(h->nut[c]);
+        T *kn = static_cast<T *>(h->kk[n]), *wn = static_cast<T *>(h->ww[n]);
+        T *nn = static_cast<T *>(h->nut[n]);
+        T *sg = static_cast<T *>(h->sgrad), *f1 = static_cast<T *>(h->f1);
+        launch(h, K_SST_GRAD, "sst_grad", [&] { k_sst_grad<T><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G); });
+        launch(h, K_SST_UPDATE, "sst_update", [&] {
+            k_sst_update<T><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G);
+        });
+        h->turb = n;
+    }
+    launch(h, K_STAGE1, "stage1", [&] { k_stage1<T><<<grid, block, 0, s>>>(fn, s0, tau, G); });
+    launch(h, K_GRAD, "grad_f", [&] { k_grad<T><<<grid, block, 0, s>>>(s0, g, G); });
+    launch(h, K_FLUX1, "flux_stage1", [&] {
+        k_flux_stage<T, 1, false><<<grid, block, 0, s>>>(s0, g, s1, fn, B, C, tau, mac, nullptr, G);
+    });
+    launch(h, K_GRAD, "grad_f", [&] { k_grad<T><<<grid, block, 0, s>>>(s1, g, G); });
+    launch(h, K_FLUX2, "flux_stage2", [&] {
+        k_flux_stage<T, 2, false><<<grid, block, 0, s>>>(s1, g, s0, fn, B, C, tau, mac, nullptr, G);
+    });
+    launch(h, K_GRAD, "grad_f", [&] { k_grad<T><<<grid, block, 0, s>>>(s0, g, G); });
+    if (stats) {
+        launch(h, K_FLUX3, "flux_stage3", [&] {
+            k_flux_stage<T, 3, true><<<grid, block, 0, s>>>(s0, g, s1, fn, B, C, tau, mac, h->d_partial, G);
+        });
+        launch(h, K_REDUCE, "reduce", [&] {
+            k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->d_inst_tile0, h->d_inst_sums);
+        });
+    } else {
+        launch(h, K_FLUX3, "flux_stage3", [&] {
+            k_flux_stage<T, 3, false><<<grid, block, 0, s>>>(s0, g, s1, fn, B, C, tau, mac, nullptr, G);
+        });
+    }
+}
+
+void enqueue(fvlbm_handle *h, bool stats) {
+    if (h->precision == FVLBM_FP64)
+        enqueue_step<double>(h, stats);
+    else
+        enqueue_step<float>(h, stats);
+}
+
+int launches_per_step(const fvlbm_handle *h) { return (h->sst ? 2 : 0) + 7; }
+
+// Capture `nsteps` plain steps into an executable graph.  A replay always starts from the
+// k / omega / nu_t ping-pong parity the graph was captured with, and an even step count ends
+// on the same parity, so SST runs keep one graph per starting parity.
+int build_graph(fvlbm_handle *h, int nsteps, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    const int turb0 = h->turb;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < nsteps; ++k) enqueue(h, false);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->turb = turb0;
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return FVLBM_OK;
+}
+
+template <class T>
+int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
+    const size_t np = h->np;
+    int rc;
+    const size_t ts = sizeof(T);
+    for (void **p : {&h->fn, &h->s0, &h->s1, &h->bacc, &h->cacc})
+        if ((rc = dalloc(h, p, kQ * np * ts))) return rc;
+    if ((rc = dalloc(h, &h->grad, 2 * kQ * np * ts))) return rc;
+    if ((rc = dalloc(h, &h->tau, np * ts))) return rc;
+    if ((rc = dalloc(h, &h->mac, 3 * np * ts))) return rc;
+    for (int b = 0; b < 2; ++b)
+        for (void **p : {&h->kk[b], &h->ww[b], &h->nut[b]})
+            if ((rc = dalloc(h, p, np * ts))) return rc;
+    if (h->sst) {
+        if ((rc = dalloc(h, &h->sgrad, 12 * np * ts))) return rc;
+        if ((rc = dalloc(h, &h->f1, np * ts))) return rc;
+    }
+    // geometry, concatenated over instances with neighbour / boundary ids offset
+    std::vector<int> nbr(4 * np, kNone), btype(h->nbt), bowner(h->nbt), perm;
+    std::vector<double> sn(8 * np, 0), lsq(8 * np, 0), rown(8 * np, 0), rnbr(8 * np, 0);
+    std::vector<double> dinv(4 * np, 0), area(np, 0), wdist(np, 1e30);
+    std::vector<double> bval(5 * static_cast<size_t>(h->nbt)), bnrm(2 * static_cast<size_t>(h->nbt));
+    std::vector<double> blen(h->nbt);
+    std::vector<double> r0(np), u0(np), v0(np), k0(np), w0(np), tau0(np), nut0(np);
+    for (int q = 0; q < h->ninst; ++q) {
+        const Prepared &p = *P[q];
+        const InstInfo &I = h->inst[q];
+        const size_t o = I.cell_off, pn = p.np;
+        for (int m = 0; m < 4; ++m)
+            for (size_t k = 0; k < pn; ++k) {
+                const int v = p.nbr[m * pn + k];
+                nbr[m * np + o + k] = v == kNone ? kNone : (v >= 0 ? v + I.cell_off : v - I.bface_off);
+                dinv[m * np + o + k] = p.dinv[m * pn + k];
+            }
+        for (int c = 0; c < 8; ++c)
+            for (size_t k = 0; k < pn; ++k) {
+                sn[c * np + o + k] = p.sn[c * pn + k];
+                lsq[c * np + o + k] = p.lsq[c * pn + k];
+                rown[c * np + o + k] = p.rown[c * pn + k];
+                rnbr[c * np + o + k] = p.rnbr[c * pn + k];
+            }
+        for (size_t k = 0; k < pn; ++k) {
+            area[o + k] = p.area[k];
+            wdist[o + k] = p.wdist[k];
+            r0[o + k] = p.rho_i[k];
+            u0[o + k] = p.u_i[k];
+            v0[o + k] = p.v_i[k];
+            k0[o + k] = p.k_i[k];
+            w0[o + k] = p.w_i[k];
+            nut0[o + k] = I.sst ? p.k_i[k] / p.w_i[k] : 0.0;
+            tau0[o + k] = (I.nu + nut0[o + k]) / kCs2;
+        }
+        for (int b = 0; b < p.nb; ++b) {
+            const int gb = I.bface_off + b;
+            btype[gb] = p.btype[b];
+            bowner[gb] = p.bowner[b] + I.cell_off;
+            for (int c = 0; c < 5; ++c) bval[c * h->nbt + gb] = p.bval[5 * b + c];
+            bnrm[gb] = p.bnrm[2 * b];
+            bnrm[h->nbt + gb] = p.bnrm[2 * b + 1];
+            blen[gb] = p.blen[b];
+        }
+        for (int k = 0; k < p.nc; ++k) perm.push_back(p.perm[k]);
+    }
+    if ((rc = upload_raw(h, &h->d_nbr, nbr))) return rc;
+    if ((rc = upload_raw(h, &h->d_btype, btype))) return rc;
+    if ((rc = upload_raw(h, &h->d_bowner, bowner))) return rc;
+    if ((rc = upload_raw(h, &h->d_perm, perm))) return rc;
+    if ((rc = upload_as<T>(h, &h->sn, sn))) return rc;
+    if ((rc = upload_as<T>(h, &h->lsq, lsq))) return rc;
+    if ((rc = upload_as<T>(h, &h->rown, rown))) return rc;
+    if ((rc = upload_as<T>(h, &h->rnbr, rnbr))) return rc;
+    if ((rc = upload_as<T>(h, &h->dinv, dinv))) return rc;
+    if ((rc = upload_as<T>(h, &h->area, area))) return rc;
+    if ((rc = upload_as<T>(h, &h->wdist, wdist))) return rc;
+    if ((rc = upload_as<T>(h, &h->bval, bval))) return rc;
+    if ((rc = upload_as<T>(h, &h->bnrm, bnrm))) return rc;
+    if ((rc = upload_as<T>(h, &h->blen, blen))) return rc;
+    {
+        std::vector<double> kt(k0), wt(w0);
+        void *tmp = nullptr;
+        for (int b = 0; b < 2; ++b) {
+            std::vector<T> a(kt.begin(), kt.end()), c(wt.begin(), wt.end()), n(nut0.begin(), nut0.end());
+            CK(cudaMemcpy(h->kk[b], a.data(), np * ts, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(h->ww[b], c.data(), np * ts, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(h->nut[b], n.data(), np * ts, cudaMemcpyHostToDevice));
+        }
+        (void)tmp;
+        std::vector<T> t(tau0.begin(), tau0.end());
+        CK(cudaMemcpy(h->tau, t.data(), np * ts, cudaMemcpyHostToDevice));
+    }
+    // initial state: f = f^eq(rho, u) (Step 0)
+    double *d_init = nullptr;
+    if ((rc = dalloc(h, reinterpret_cast<void **>(&d_init), 3 * np * sizeof(double)))) return rc;
+    CK(cudaMemcpy(d_init, r0.data(), np * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_init + np, u0.data(), np * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_init + 2 * np, v0.data(), np * sizeof(double), cudaMemcpyHostToDevice));
+    Geo<T> G = geo_of<T>(h);
+    k_init_state<T><<<h->ntiles, kTile, 0, h->stream>>>(static_cast<T *>(h->fn), static_cast<T *>(h->mac),
+                                                       d_init, d_init + np, d_init + 2 * np, G);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return FVLBM_OK;
+}
+
+void free_all(fvlbm_handle *h) {
+    for (int k = 0; k < 3; ++k)
+        if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlbm_params *params,
+                int device, void *stream, fvlbm_handle **out) {
+    if (!out || n <= 0 || !meshes || !bcs || !params) return FVLBM_ERR_BAD_PARAM;
+    *out = nullptr;
+    const int prec = params[0].precision;
+    int sst = 0;
+    if (prec != FVLBM_FP64 && prec != FVLBM_FP32_DEV) return FVLBM_ERR_BAD_PARAM;
+    for (int q = 0; q < n; ++q) {
+        if (params[q].precision != prec) return FVLBM_ERR_BAD_PARAM;
+        sst |= params[q].sst ? 1 : 0;
+    }
+    std::vector<std::unique_ptr<Prepared>> prep(n);
+    std::vector<const Prepared *> P(n);
+    for (int q = 0; q < n; ++q) {
+        prep[q].reset(new Prepared());
+        std::string why;
+        const int rc = prepare_instance(meshes[q], bcs[q], params[q], prep[q].get(), &why);
+        if (rc) {
+            fprintf(stderr, "fvlbm_create: instance %d: %s\n", q, why.c_str());
+            return rc;
+        }
+        P[q] = prep[q].get();
+    }
+    std::unique_ptr<fvlbm_handle> h(new fvlbm_handle());
+    if (device < 0) {
+        if (cudaGetDevice(&device) != cudaSuccess) return FVLBM_ERR_CUDA;
+    }
+    h->device = device;
+    CK(cudaSetDevice(device));
+    h->precision = prec;
+    h->sst = sst != 0;
+    h->ninst = n;
+    int cell_off = 0, bface_off = 0;
+    std::vector<int> tile_inst, inst_tile0;
+    std::vector<InstParam> ip(n);
+    for (int q = 0; q < n; ++q) {
+        const Prepared &p = *P[q];
+        InstInfo I;
+        I.nc = p.nc;
+        I.np = p.np;
+        I.nb = p.nb;
+        I.n_bedges_in = p.n_bedges_in;
+        I.sst = params[q].sst ? 1 : 0;
+        I.cell_off = cell_off;
+        I.tile_off = cell_off / kTile;
+        I.bface_off = bface_off;
+        I.dt = p.dt;
+        I.rho0 = params[q].rho0;
+        I.uref = params[q].uref;
+        I.lref = params[q].lref;
+        I.alpha_deg = params[q].alpha_deg;
+        I.nu = params[q].nu;
+        I.bedge_of = p.bedge_of;
+        inst_tile0.push_back(I.tile_off);
+        for (int t = 0; t < p.np / kTile; ++t) tile_inst.push_back(q);
+        ip[q] = InstParam{p.dt, params[q].nu, params[q].rho0,
+                          1e-12 * params[q].uref / params[q].lref, params[q].sst ? 1 : 0};
+        cell_off += p.np;
+        bface_off += p.nb;
+        h->inst.push_back(I);
+    }
+    inst_tile0.push_back(cell_off / kTile);
+    h->np = cell_off;
+    h->nbt = bface_off;
+    h->ntiles = cell_off / kTile;
+    if (stream) {
+        h->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    int rc;
+    if ((rc = upload_raw(h.get(), &h->d_tile_inst, tile_inst))) { free_all(h.get()); return rc; }
+    if ((rc = upload_raw(h.get(), &h->d_inst_tile0, inst_tile0))) { free_all(h.get()); return rc; }
+    if ((rc = upload_raw(h.get(), &h->d_ip, ip))) { free_all(h.get()); return rc; }
+    if ((rc = dalloc(h.get(), reinterpret_cast<void **>(&h->d_partial), 4 * sizeof(double) * h->ntiles)) ||
+        (rc = dalloc(h.get(), reinterpret_cast<void **>(&h->d_inst_sums), 4 * sizeof(double) * n))) {
+        free_all(h.get());
+        return rc;
+    }
+    rc = prec == FVLBM_FP64 ? allocate_state<double>(h.get(), P) : allocate_state<float>(h.get(), P);
+    if (rc) {
+        free_all(h.get());
+        return rc;
+    }
+    *out = h.release();
+    return FVLBM_OK;
+}
+
+int io_buffer(fvlbm_handle *h, size_t bytes) {
+    if (h->io_bytes >= bytes) return FVLBM_OK;
+    if (h->d_io) {
+        cudaFree(h->d_io);
+        h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), static_cast<void *>(h->d_io)));
+        h->device_bytes -= h->io_bytes;
+        h->d_io = nullptr;
+    }
+    int rc = dalloc(h, reinterpret_cast<void **>(&h->d_io), bytes);
+    if (rc) return rc;
+    h->io_bytes = bytes;
+    return FVLBM_OK;
+}
+
+int perm_offset(const fvlbm_handle *h, int instance) {
+    int o = 0;
+    for (int q = 0; q < instance; ++q) o += h->inst[q].nc;
+    return o;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fvlbm_create(const fvlbm_mesh *mesh, const fvlbm_bc *bc, const fvlbm_params *params,
+                 int device, void *stream, fvlbm_handle **out) {
+    return create_impl(1, mesh, bc, params, device, stream, out);
+}
+
+int fvlbm_create_batch(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs,
+                       const fvlbm_params *params, int device, void *stream, fvlbm_handle **out) {
+    return create_impl(n, meshes, bcs, params, device, stream, out);
+}
+
+int fvlbm_step(fvlbm_handle *h, int n_steps, fvlbm_stats *stats) {
+    if (!h || n_steps < 0) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    int remaining = n_steps;
+    const bool want_stats = stats != nullptr && n_steps > 0;
+    if (want_stats) --remaining;  // the last step runs un-captured with the reductions
+    // graphs: laminar runs replay freely; SST runs keep the ping-pong parity (graphs of an
+    // even number of steps only)
+    while (remaining >= kGraphSteps) {
+        const int gi = 1 + (h->sst ? h->turb : 0);
+        if (!h->graph[gi]) {
+            int rc = build_graph(h, kGraphSteps, &h->graph[gi]);
+            if (rc) return rc;
+        }
+        CK(cudaGraphLaunch(h->graph[gi], h->stream));
+        remaining -= kGraphSteps;
+        h->steps += kGraphSteps;
+    }
+    while (remaining > 0) {
+        if (!h->sst) {
+            if (!h->graph[0]) {
+                int rc = build_graph(h, 1, &h->graph[0]);
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(h->graph[0], h->stream));
+        } else {
+            enqueue(h, false);
+        }
+        --remaining;
+        ++h->steps;
+    }
+    if (want_stats) {
+        enqueue(h, true);
+        ++h->steps;
+    }
+    CK(cudaGetLastError());
+    if (want_stats) {
+        std::vector<double> sums(4 * static_cast<size_t>(h->ninst));
+        CK(cudaMemcpyAsync(sums.data(), h->d_inst_sums, sums.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        stats->steps = h->steps;
+        stats->residual = 0;
+        stats->mass = 0;
+        stats->diverged = 0;
+        for (int q = 0; q < h->ninst; ++q) {
+            const double num = sums[4 * q], den = sums[4 * q + 1];
+            const double e = den > 0 ? std::sqrt(num) / std::sqrt(den) : std::sqrt(num);
+            stats->residual = std::max(stats->residual, e);
+            stats->mass += sums[4 * q + 2];
+            if (sums[4 * q + 3] != 0.0 || !std::isfinite(e)) stats->diverged = 1;
+        }
+        if (stats->diverged) return FVLBM_ERR_DIVERGED;
+    }
+    return FVLBM_OK;
+}
+
+int fvlbm_get_f(fvlbm_handle *h, int instance, double *f) {
+    if (!h || instance < 0 || instance >= h->ninst || !f) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    const InstInfo &I = h->inst[instance];
+    int rc = io_buffer(h, sizeof(double) * kQ * I.nc);
+    if (rc) return rc;
+    const int po = perm_offset(h, instance);
+    const int nb = (I.nc + 255) / 256;
+    if (h->precision == FVLBM_FP64)
+        k_gather_f<double><<<nb, 256, 0, h->stream>>>(static_cast<double *>(h->fn), h->d_perm + po,
+                                                      I.cell_off, I.nc, I.rho0, h->np, h->d_io);
+    else
+        k_gather_f<float><<<nb, 256, 0, h->stream>>>(static_cast<float *>(h->fn), h->d_perm + po,
+                                                     I.cell_off, I.nc, I.rho0, h->np, h->d_io);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(f, h->d_io, sizeof(double) * kQ * I.nc, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FVLBM_OK;
+}
+
+int fvlbm_set_f(fvlbm_handle *h, int instance, const double *f) {
+    if (!h || instance < 0 || instance >= h->ninst || !f) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    const InstInfo &I = h->inst[instance];
+    int rc = io_buffer(h, sizeof(double) * kQ * I.nc);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->d_io, f, sizeof(double) * kQ * I.nc, cudaMemcpyHostToDevice, h->stream));
+    const int po = perm_offset(h, instance);
+    const int nb = (I.nc + 255) / 256;
+    if (h->precision == FVLBM_FP64)
+        k_scatter_f<double><<<nb, 256, 0, h->stream>>>(static_cast<double *>(h->fn), static_cast<double *>(h->mac),
+                                                       h->d_perm + po, I.cell_off, I.nc, I.rho0, h->np, h->d_io);
+    else
+        k_scatter_f<float><<<nb, 256, 0, h->stream>>>(static_cast<float *>(h->fn), static_cast<float *>(h->mac),
+                                                      h->d_perm + po, I.cell_off, I.nc, I.rho0, h->np, h->d_io);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return FVLBM_OK;
+}
+
+int fvlbm_get_fields(fvlbm_handle *h, int instance, double *rho, double *u, double *v, double *k,
+                     double *omega, double *nut) {
+    if (!h || instance < 0 || instance >= h->ninst) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    const InstInfo &I = h->inst[instance];
+    const size_t n = I.nc;
+    int rc = io_buffer(h, sizeof(double) * 6 * n);
+    if (rc) return rc;
+    const int po = perm_offset(h, instance);
+    const int nb = (I.nc + 255) / 256;
+    const int c = h->turb;
+    if (h->precision == FVLBM_FP64)
+        k_gather_fields<double><<<nb, 256, 0, h->stream>>>(
+            static_cast<double *>(h->mac), static_cast<double *>(h->kk[c]), static_cast<double *>(h->ww[c]),
+            static_cast<double *>(h->nut[c]), h->d_perm + po, I.cell_off, I.nc, h->np, h->d_io);
+    else
+        k_gather_fields<float><<<nb, 256, 0, h->stream>>>(
+            static_cast<float *>(h->mac), static_cast<float *>(h->kk[c]), static_cast<float *>(h->ww[c]),
+            static_cast<float *>(h->nut[c]), h->d_perm + po, I.cell_off, I.nc, h->np, h->d_io);
+    CK(cudaGetLastError());
+    double *dst[6] = {rho, u, v, k, omega, nut};
+    for (int q = 0; q < 6; ++q)
+        if (dst[q])
+            CK(cudaMemcpyAsync(dst[q], h->d_io + q * n, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FVLBM_OK;
+}
+
+int fvlbm_forces(fvlbm_handle *h, int instance, double *out, double *cp) {
+    if (!h || instance < 0 || instance >= h->ninst || !out) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    const InstInfo &I = h->inst[instance];
+    const int nbi = I.nb;
+    int rc = io_buffer(h, sizeof(double) * 3 * std::max(nbi, 1));
+    if (rc) return rc;
+    if (nbi > 0) {
+        const int nb = (nbi + 255) / 256;
+        if (h->precision == FVLBM_FP64)
+            k_wall_forces<double><<<nb, 256, 0, h->stream>>>(
+                static_cast<double *>(h->fn), h->d_bowner, static_cast<double *>(h->bnrm),
+                static_cast<double *>(h->blen), I.bface_off, nbi, I.rho0, I.uref, geo_of<double>(h), h->d_io);
+        else
+            k_wall_forces<float><<<nb, 256, 0, h->stream>>>(
+                static_cast<float *>(h->fn), h->d_bowner, static_cast<float *>(h->bnrm),
+                static_cast<float *>(h->blen), I.bface_off, nbi, I.rho0, I.uref, geo_of<float>(h), h->d_io);
+        CK(cudaGetLastError());
+    }
+    std::vector<double> host(3 * static_cast<size_t>(std::max(nbi, 1)));
+    CK(cudaMemcpyAsync(host.data(), h->d_io, host.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double fx = 0, fy = 0;
+    if (cp)
+        for (int b = 0; b < I.n_bedges_in; ++b) cp[b] = 0.0;
+    for (int b = 0; b < nbi; ++b) {
+        fx += host[b];
+        fy += host[nbi + b];
+        if (cp) cp[I.bedge_of[b]] = host[2 * nbi + b];
+    }
+    const double q = 0.5 * I.rho0 * I.uref * I.uref;
+    const double al = I.alpha_deg * M_PI / 180.0;
+    out[0] = fx;
+    out[1] = fy;
+    out[2] = (fx * std::cos(al) + fy * std::sin(al)) / (q * I.lref);
+    out[3] = (-fx * std::sin(al) + fy * std::cos(al)) / (q * I.lref);
+    return FVLBM_OK;
+}
+
+int fvlbm_info(fvlbm_handle *h, int instance, int *n_cells, int *n_bedges, double *dt) {
+    if (!h || instance < 0 || instance >= h->ninst) return FVLBM_ERR_BAD_PARAM;
+    const InstInfo &I = h->inst[instance];
+    if (n_cells) *n_cells = I.nc;
+    if (n_bedges) *n_bedges = I.n_bedges_in;
+    if (dt) *dt = I.dt;
+    return FVLBM_OK;
+}
+
+int fvlbm_footprint(fvlbm_handle *h, long long *device_bytes, int *lps) {
+    if (!h) return FVLBM_ERR_BAD_PARAM;
+    if (device_bytes) *device_bytes = static_cast<long long>(h->device_bytes);
+    if (lps) *lps = launches_per_step(h);
+    return FVLBM_OK;
+}
+
+int fvlbm_profile_kernels(fvlbm_handle *h, int n_steps, int max_kernels, char *names, double *ms,
+                          int *launches) {
+    if (!h || n_steps <= 0) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    h->profiling = true;
+    h->timers.clear();
+    for (int k = 0; k < n_steps; ++k) enqueue(h, false);
+    h->steps += n_steps;
+    h->profiling = false;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    for (auto &pe : h->pending) {
+        float t = 0;
+        if (e == cudaSuccess) cudaEventElapsedTime(&t, pe.second.first, pe.second.second);
+        h->timers[pe.first].ms += t;
+        h->timers[pe.first].launches += 1;
+        cudaEventDestroy(pe.second.first);
+        cudaEventDestroy(pe.second.second);
+    }
+    h->pending.clear();
+    if (e != cudaSuccess) return cuda_fail(e);
+    int nk = 0;
+    for (const auto &t : h->timers) {
+        if (t.launches == 0) continue;
+        if (nk < max_kernels) {
+            if (names) {
+                std::memset(names + 32 * nk, 0, 32);
+                std::strncpy(names + 32 * nk, t.name.c_str(), 31);
+            }
+            if (ms) ms[nk] = t.ms;
+            if (launches) launches[nk] = t.launches;
+        }
+        ++nk;
+    }
+    return std::min(nk, max_kernels);
+}
+
+void fvlbm_destroy(fvlbm_handle *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+const char *fvlbm_strerror(int code) {
+    switch (code) {
+    case FVLBM_OK: return "ok";
+    case FVLBM_ERR_BAD_MESH: return "bad mesh";
+    case FVLBM_ERR_BAD_BC: return "bad boundary conditions";
+    case FVLBM_ERR_BAD_PARAM: return "bad parameter";
+    case FVLBM_ERR_OOM: return "out of device memory";
+    case FVLBM_ERR_CUDA: return "CUDA runtime error";
+    case FVLBM_ERR_DIVERGED: return "state diverged (NaN or Inf)";
+    case FVLBM_ERR_NOT_SUPPORTED: return "not supported";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

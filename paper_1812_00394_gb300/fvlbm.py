@@ -1,0 +1,277 @@
+"""Python binding of the C ABI in include/fvlbm.h (argument marshalling only).
+
+Every entry point of the library is exposed under its C name (``fvlbm_create``,
+``fvlbm_step``, ...); ``Solver`` is a small convenience wrapper around them.  All arithmetic
+of the time step runs in the CUDA library; this module only converts numpy arrays to
+pointers.  It raises if the compiled library is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FVLBM_OK = 0
+FVLBM_ERR_DIVERGED = -6
+FVLBM_FP64 = 0
+FVLBM_FP32_DEV = 1
+Q = 9
+
+
+class FvlbmError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+class fvlbm_mesh(C.Structure):
+    _fields_ = [("n_nodes", C.c_int), ("xy", C.c_void_p), ("n_cells", C.c_int),
+                ("cell_ptr", C.c_void_p), ("cell_nodes", C.c_void_p)]
+
+
+class fvlbm_bc(C.Structure):
+    _fields_ = [("n_bedges", C.c_int), ("bedge_nodes", C.c_void_p), ("bedge_type", C.c_void_p),
+                ("bedge_val", C.c_void_p), ("n_periodic", C.c_int), ("periodic_pairs", C.c_void_p),
+                ("periodic_shift", C.c_void_p)]
+
+
+class fvlbm_params(C.Structure):
+    _fields_ = [("nu", C.c_double), ("rho0", C.c_double), ("dt", C.c_double), ("cfl", C.c_double),
+                ("sst", C.c_int), ("precision", C.c_int), ("uref", C.c_double),
+                ("lref", C.c_double), ("alpha_deg", C.c_double), ("rho_init", C.c_void_p),
+                ("u_init", C.c_void_p), ("v_init", C.c_void_p), ("k_init", C.c_void_p),
+                ("omega_init", C.c_void_p)]
+
+
+class fvlbm_stats(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("residual", C.c_double), ("mass", C.c_double),
+                ("diverged", C.c_int)]
+
+
+EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "fvlbm_get_f",
+           "fvlbm_set_f", "fvlbm_get_fields", "fvlbm_info", "fvlbm_footprint",
+           "fvlbm_profile_kernels", "fvlbm_destroy", "fvlbm_strerror"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load libfvlbm.so (building it in-tree first if allowed and missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise FileNotFoundError(f"libfvlbm.so not built at {path}")
+        _build.build()
+    lib = C.CDLL(path)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    P = C.POINTER
+    lib.fvlbm_create.argtypes = [P(fvlbm_mesh), P(fvlbm_bc), P(fvlbm_params), i, vp, P(vp)]
+    lib.fvlbm_create_batch.argtypes = [i, P(fvlbm_mesh), P(fvlbm_bc), P(fvlbm_params), i, vp, P(vp)]
+    lib.fvlbm_step.argtypes = [vp, i, P(fvlbm_stats)]
+    lib.fvlbm_forces.argtypes = [vp, i, vp, vp]
+    lib.fvlbm_get_f.argtypes = [vp, i, vp]
+    lib.fvlbm_set_f.argtypes = [vp, i, vp]
+    lib.fvlbm_get_fields.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
+    lib.fvlbm_info.argtypes = [vp, i, P(i), P(i), P(d)]
+    lib.fvlbm_footprint.argtypes = [vp, P(C.c_longlong), P(i)]
+    lib.fvlbm_profile_kernels.argtypes = [vp, i, i, vp, vp, vp]
+    lib.fvlbm_destroy.argtypes = [vp]
+    lib.fvlbm_destroy.restype = None
+    lib.fvlbm_strerror.argtypes = [i]
+    lib.fvlbm_strerror.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("fvlbm_destroy", "fvlbm_strerror"):
+            getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().fvlbm_strerror(int(code)).decode()
+    except Exception:  # noqa: BLE001 -- message only
+        return "unknown"
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise FvlbmError(rc, what)
+    return rc
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# ------------------------------------------------------------------ C-named wrappers
+def fvlbm_create(mesh: fvlbm_mesh, bc: fvlbm_bc, params: fvlbm_params, device: int = -1,
+                 stream: int | None = None) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(load().fvlbm_create(C.byref(mesh), C.byref(bc), C.byref(params), device,
+                               C.c_void_p(stream) if stream else None, C.byref(h)), "fvlbm_create")
+    return h
+
+
+def fvlbm_create_batch(meshes, bcs, params, device: int = -1, stream: int | None = None):
+    n = len(meshes)
+    M = (fvlbm_mesh * n)(*meshes)
+    B = (fvlbm_bc * n)(*bcs)
+    Pm = (fvlbm_params * n)(*params)
+    h = C.c_void_p()
+    _check(load().fvlbm_create_batch(n, M, B, Pm, device, C.c_void_p(stream) if stream else None,
+                                     C.byref(h)), "fvlbm_create_batch")
+    return h
+
+
+def fvlbm_step(h, n_steps: int, stats: bool = False):
+    st = fvlbm_stats() if stats else None
+    rc = load().fvlbm_step(h, int(n_steps), C.byref(st) if st is not None else None)
+    if rc == FVLBM_ERR_DIVERGED and st is not None:
+        return {"steps": st.steps, "residual": st.residual, "mass": st.mass, "diverged": 1}
+    _check(rc, "fvlbm_step")
+    if st is None:
+        return None
+    return {"steps": st.steps, "residual": st.residual, "mass": st.mass, "diverged": st.diverged}
+
+
+def fvlbm_info(h, instance: int = 0):
+    n, b, dt = C.c_int(), C.c_int(), C.c_double()
+    _check(load().fvlbm_info(h, instance, C.byref(n), C.byref(b), C.byref(dt)), "fvlbm_info")
+    return n.value, b.value, dt.value
+
+
+def fvlbm_get_f(h, instance: int, out: np.ndarray | None = None) -> np.ndarray:
+    n, _, _ = fvlbm_info(h, instance)
+    f = np.empty((n, Q)) if out is None else out
+    _check(load().fvlbm_get_f(h, instance, _p(f)), "fvlbm_get_f")
+    return f
+
+
+def fvlbm_set_f(h, instance: int, f: np.ndarray) -> None:
+    f = np.ascontiguousarray(f, np.float64)
+    _check(load().fvlbm_set_f(h, instance, _p(f)), "fvlbm_set_f")
+
+
+def fvlbm_get_fields(h, instance: int = 0) -> dict:
+    n, _, _ = fvlbm_info(h, instance)
+    out = {key: np.empty(n) for key in ("rho", "u", "v", "k", "omega", "nut")}
+    _check(load().fvlbm_get_fields(h, instance, *(_p(out[k]) for k in
+                                                  ("rho", "u", "v", "k", "omega", "nut"))),
+           "fvlbm_get_fields")
+    return out
+
+
+def fvlbm_forces(h, instance: int = 0, with_cp: bool = False) -> dict:
+    _, nb, _ = fvlbm_info(h, instance)
+    out = np.zeros(4)
+    cp = np.zeros(nb) if with_cp else None
+    _check(load().fvlbm_forces(h, instance, _p(out), _p(cp)), "fvlbm_forces")
+    res = {"fx": out[0], "fy": out[1], "cd": out[2], "cl": out[3]}
+    if with_cp:
+        res["cp"] = cp
+    return res
+
+
+def fvlbm_footprint(h):
+    b, lps = C.c_longlong(), C.c_int()
+    _check(load().fvlbm_footprint(h, C.byref(b), C.byref(lps)), "fvlbm_footprint")
+    return b.value, lps.value
+
+
+def fvlbm_profile_kernels(h, n_steps: int) -> dict:
+    maxk = 16
+    names = C.create_string_buffer(32 * maxk)
+    ms = np.zeros(maxk)
+    launches = np.zeros(maxk, np.int32)
+    nk = _check(load().fvlbm_profile_kernels(h, int(n_steps), maxk, names, _p(ms), _p(launches)),
+                "fvlbm_profile_kernels")
+    raw = names.raw
+    res = {}
+    for k in range(nk):
+        nm = raw[32 * k:32 * (k + 1)].split(b"\0", 1)[0].decode()
+        res[nm] = {"ms": float(ms[k]), "launches": int(launches[k])}
+    return res
+
+
+def fvlbm_destroy(h) -> None:
+    if h:
+        load().fvlbm_destroy(h)
+
+
+def fvlbm_strerror(code: int) -> str:
+    return strerror(code)
+
+
+# ------------------------------------------------------------------ convenience wrapper
+class _Pack:
+    """Keeps the numpy arrays alive that a (mesh, bc, params) triple points into."""
+
+    def __init__(self, case, precision: int):
+        m = case.mesh.normalized()
+        rho, u, v, k, w = case.init_arrays()
+        self.keep = (m, rho, u, v, k, w)
+        self.mesh = fvlbm_mesh(m.n_nodes, _p(m.xy), m.n_cells, _p(m.cell_ptr), _p(m.cell_nodes))
+        self.bc = fvlbm_bc(m.n_bedges, _p(m.bedge_nodes), _p(m.bedge_type), _p(m.bedge_val),
+                           m.periodic_pairs.shape[0], _p(m.periodic_pairs), _p(m.periodic_shift))
+        self.params = fvlbm_params(case.nu, case.rho0, case.dt, case.cfl, int(bool(case.sst)),
+                                   precision, case.uref, case.lref, case.alpha_deg, _p(rho), _p(u),
+                                   _p(v), _p(k), _p(w))
+
+
+class Solver:
+    """One handle over one case or a batch of cases (``meshgen.Case``)."""
+
+    def __init__(self, cases, precision: int = FVLBM_FP64, device: int = -1,
+                 stream: int | None = None):
+        if not isinstance(cases, (list, tuple)):
+            cases = [cases]
+        packs = [_Pack(c, precision) for c in cases]
+        if len(packs) == 1:
+            self.h = fvlbm_create(packs[0].mesh, packs[0].bc, packs[0].params, device, stream)
+        else:
+            self.h = fvlbm_create_batch([p.mesh for p in packs], [p.bc for p in packs],
+                                        [p.params for p in packs], device, stream)
+        self.n = len(cases)
+        self.cells = [fvlbm_info(self.h, i)[0] for i in range(self.n)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            fvlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def dt(self, i: int = 0) -> float:
+        return fvlbm_info(self.h, i)[2]
+
+    def step(self, n: int = 1, stats: bool = False):
+        return fvlbm_step(self.h, n, stats)
+
+    def get_f(self, i: int = 0) -> np.ndarray:
+        return fvlbm_get_f(self.h, i)
+
+    def set_f(self, f: np.ndarray, i: int = 0) -> None:
+        fvlbm_set_f(self.h, i, f)
+
+    def fields(self, i: int = 0) -> dict:
+        return fvlbm_get_fields(self.h, i)
+
+    def forces(self, i: int = 0, with_cp: bool = False) -> dict:
+        return fvlbm_forces(self.h, i, with_cp)
+
+    def footprint(self):
+        return fvlbm_footprint(self.h)
+
+    def profile_kernels(self, n_steps: int) -> dict:
+        return fvlbm_profile_kernels(self.h, n_steps)

@@ -279,12 +279,13 @@ def cavity_quad(n: int = 64, re: float = 400.0, lid_u: float = 0.1, cfl: float =
 
 def cavity_delaunay(h_boundary: float = 1.0 / 200.0, n_target: int = 40000, re: float = 1000.0,
                     lid_u: float = 0.1, z: float = 5.0, seed: int = 2,
-                    noise: float = 1e-6) -> Case:
+                    noise: float = 1e-6, cfl: float = 0.0) -> Case:
     """Lid-driven cavity on a seeded Delaunay triangulation of the unit square.
 
     Boundary points sit at spacing ``h_boundary``; interior points form a hexagonal lattice
     sized for about ``n_target`` triangles, each point jittered by the seed.  The time step
-    is ``z`` relaxation times (dt = z * tau, tau = nu / cs^2).
+    is ``z`` relaxation times (dt = z * tau, tau = nu / cs^2), or, when ``cfl`` > 0, ``cfl``
+    times the convective limit of the mesh.
     """
     from scipy.spatial import Delaunay
 
@@ -319,8 +320,11 @@ def cavity_delaunay(h_boundary: float = 1.0 / 200.0, n_target: int = 40000, re: 
     m = Mesh(xy, ptr, cn, bn, bt, bv, name=f"cavity_delaunay_{tri.shape[0]}").normalized()
     nu = lid_u / re
     rho = 1.0 + noise * splitmix64_uniform(seed, m.n_cells)
+    if cfl > 0.0:
+        return Case(m, nu=nu, cfl=cfl, uref=lid_u, lref=1.0, rho=rho,
+                    name=f"cavity_delaunay{m.n_cells}_re{re:.0f}_cfl{cfl:g}")
     return Case(m, nu=nu, dt=z * nu / CS2, uref=lid_u, lref=1.0, rho=rho,
-                name=f"cavity_delaunay{m.n_cells}_re{re:g}_z{z:g}")
+                name=f"cavity_delaunay{m.n_cells}_re{re:.0f}_z{z:g}")
 
 
 # --------------------------------------------------------------------------- turbulent meshes
@@ -345,23 +349,27 @@ def _two_sided(n: int, L: float, first: float) -> np.ndarray:
 
 
 def _hybrid_cells(cells4: np.ndarray, tri_mask: np.ndarray):
-    """Keep quads where ``tri_mask`` is false; split the others into two triangles."""
+    """Keep quads where ``tri_mask`` is false; split the others into two triangles.
+    Returns CSR (ptr, nodes)."""
     quads = cells4[~tri_mask]
     tris = split_quads(cells4[tri_mask])
-    return [list(q) for q in quads] + [list(t) for t in tris]
+    nq, nt = quads.shape[0], tris.shape[0]
+    ptr = np.concatenate([np.arange(nq + 1) * 4, 4 * nq + np.arange(1, nt + 1) * 3]).astype(np.int32)
+    return ptr, np.concatenate([quads.ravel(), tris.ravel()]).astype(np.int32)
 
 
 def bfs_hybrid(n_target: int = 80000, h: float = 1.0, expansion: float = 1.125,
                re_h: float = 3.6e4, uref: float = 0.1, yplus1: float = 1.0,
-               intensity: float = 0.01, nut_ratio: float = 10.0, z: float = 60.0,
-               seed: int = 3) -> Case:
+               intensity: float = 0.01, nut_ratio: float = 10.0, cfl: float = 0.5,
+               seed: int = 3, _res: float = 1.0) -> Case:
     """Turbulent backward-facing step on a hybrid mesh (Sec. 4.2 geometry family).
 
     Step height h; channel height downstream ``expansion / (expansion - 1) * h``; inlet at
     -4h, outlet at +30h.  Quads are clustered at every wall (first cell height from y+ ~
     ``yplus1`` with a flat-plate skin-friction estimate) and cells away from walls are split
     into triangles.  Inlet: 1/7 power-law profile, turbulence intensity ``intensity`` and
-    nu_t / nu = ``nut_ratio``.  Time step ``z`` relaxation times.
+    nu_t / nu = ``nut_ratio``.  The time step is ``cfl`` times the convective limit of the
+    smallest (wall) cells.
     """
     H = expansion / (expansion - 1.0) * h          # downstream height
     Hin = H - h                                     # upstream channel height
@@ -373,13 +381,13 @@ def bfs_hybrid(n_target: int = 80000, h: float = 1.0, expansion: float = 1.125,
     # grid lines: x clustered at the step corner, y clustered at walls
     frac_up = 4.0 / 34.0
     # choose resolution from the target: cells ~ nx * ny (upstream only covers Hin)
-    ny_lo = max(8, int(round(math.sqrt(n_target / 34.0 * 0.9) * 1.2)))
+    ny_lo = max(8, int(round(math.sqrt(n_target / 34.0 * 0.9) * 1.2 * _res)))
     ny_lo = ny_lo + (ny_lo % 2)
     ny_up = max(8, int(round(ny_lo * Hin / H * 1.6)))
     ny_up = ny_up + (ny_up % 2)
     ny_step = max(4, int(round(ny_lo * h / H * 3.0)))
     ny_step += ny_step % 2
-    nx_total = max(20, int(n_target / (ny_up + ny_step)))
+    nx_total = max(20, int(n_target / (ny_up + ny_step) / 1.6 * _res))
     nx_up = max(6, int(round(nx_total * frac_up)))
     nx_dn = nx_total - nx_up
     xs_up = x_in + (-x_in) * (1.0 - _stretched(nx_up, 1.0, 0.5 / nx_up * 0.3)[::-1])
@@ -410,7 +418,7 @@ def bfs_hybrid(n_target: int = 80000, h: float = 1.0, expansion: float = 1.125,
     dist = np.minimum(H - yc, np.where(xc < 0.0, yc - h, yc))
     dist = np.where((xc >= 0.0) & (yc < h), np.minimum(dist, np.abs(xc)), dist)
     tri_mask = dist > 0.25 * h
-    cells = _hybrid_cells(cells4.astype(np.int32), tri_mask)
+    ptr, cn = _hybrid_cells(cells4.astype(np.int32), tri_mask)
     # boundary edges
     bn, bt, bvl = [], [], []
     k_in = 1.5 * (intensity * uref) ** 2
@@ -435,11 +443,13 @@ def bfs_hybrid(n_target: int = 80000, h: float = 1.0, expansion: float = 1.125,
         add(nid[j, 0], nid[j + 1, 0], BC_INLET, (1.0, uin, 0.0, k_in, w_in))
     for j in range(ny):
         add(nid[j, nx], nid[j + 1, nx], BC_OUTLET, (1.0, 0.0, 0.0, k_in, w_in))
-    ptr, cn = _cells_to_csr(cells)
     m = Mesh(xy, ptr, cn, np.asarray(bn, np.int32), np.asarray(bt, np.int32),
-             np.asarray(bvl, np.float64), name=f"bfs_hybrid_{len(cells)}").normalized()
+             np.asarray(bvl, np.float64), name=f"bfs_hybrid_{len(ptr) - 1}").normalized()
     n = m.n_cells
-    return Case(m, nu=nu, dt=z * nu / CS2, sst=True, uref=uref, lref=h,
+    if _res == 1.0 and abs(n - n_target) > 0.05 * n_target:   # one resize to hit the target
+        return bfs_hybrid(n_target, h, expansion, re_h, uref, yplus1, intensity, nut_ratio, cfl,
+                          seed, _res=math.sqrt(n_target / n))
+    return Case(m, nu=nu, cfl=cfl, sst=True, uref=uref, lref=h,
                 rho=np.ones(n), u=np.zeros(n), v=np.zeros(n), k=np.full(n, k_in),
                 omega=np.full(n, w_in), name=f"bfs{n}_reh{re_h:g}")
 
@@ -453,13 +463,14 @@ def _naca0012_y(x: np.ndarray) -> np.ndarray:
 
 def naca0012_cmesh(n_target: int = 200000, re_c: float = 6e6, uref: float = 0.1,
                    alpha_deg: float = 0.0, far: float = 20.0, yplus1: float = 1.0,
-                   intensity: float = 0.01, nut_ratio: float = 1.0, z: float = 180.0,
-                   seed: int = 4) -> Case:
+                   intensity: float = 0.01, nut_ratio: float = 1.0, cfl: float = 0.5,
+                   quad_layer: float = 0.4, seed: int = 4) -> Case:
     """Turbulent NACA 0012 on an algebraic C-mesh (Sec. 4.3 case family).
 
     Chord 1, far-field boundary at ``far`` chords, first cell from y+ ~ ``yplus1`` at Re_c.
-    Near-wall rows are quads; outer rows are split into triangles (hybrid).  Free stream at
-    angle ``alpha_deg``.
+    Rows within ``quad_layer`` chords of the wall are quads; outer rows are split into
+    triangles (hybrid).  Free stream at angle ``alpha_deg``.  The time step is ``cfl`` times the
+    convective limit of the smallest cells (the collision is implicit, so dt >> tau).
     """
     nu = uref / re_c
     cf = 0.026 / re_c ** (1.0 / 7.0)
@@ -467,7 +478,10 @@ def naca0012_cmesh(n_target: int = 200000, re_c: float = 6e6, uref: float = 0.1,
     dy1 = yplus1 * nu / utau
     # points along the C: wake (lower), airfoil lower TE->LE, upper LE->TE, wake (upper)
     n_j = max(24, int(round(math.sqrt(n_target / 3.2))))
-    n_i = max(48, int(round(n_target / n_j)))
+    eta = _stretched(n_j, 1.0, dy1 / far)
+    n_quad_rows = int(np.sum(eta[1:] <= quad_layer / far))
+    per_col = n_quad_rows + 2 * (n_j - n_quad_rows)
+    n_i = max(48, int(round(n_target / per_col)))
     n_af = max(16, int(n_i * 0.55) // 2)          # points per airfoil side
     n_wk = max(8, (n_i - 2 * n_af) // 2)          # wake points per side
     beta = np.linspace(0.0, math.pi, n_af + 1)
@@ -492,22 +506,23 @@ def naca0012_cmesh(n_target: int = 200000, re_c: float = 6e6, uref: float = 0.1,
             th = math.pi * 1.5 - math.pi * (idx - n_wk) / (ni - 2 * n_wk)
             outer[idx] = (0.5 + far * math.cos(th), far * math.sin(th))
     del ang, s
-    # normal spacing: geometric from dy1 out to the far field
-    eta = _stretched(n_j, 1.0, dy1 / far)
-    # wall-normal direction for the near-wall layer (orthogonal start, blend to the outer line)
+    # wall-normal direction for the near-wall layer (orthogonal start, blend to the outer line
+    # within a few hundredths of a chord; tapered to zero at the sharp trailing edge)
     tang = np.gradient(inner, axis=0)
     nrm = np.stack([-tang[:, 1], tang[:, 0]], 1)
     nrm /= np.linalg.norm(nrm, axis=1, keepdims=True) + 1e-300
-    # on the lower wake the C runs in -x: the left normal points to -y there (outwards)
+    on_af = (np.arange(ni + 1) >= n_wk) & (np.arange(ni + 1) <= ni - n_wk)
+    taper = np.where(on_af, np.clip((1.0 - inner[:, 0]) / 0.05, 0.0, 1.0), 0.0)[:, None]
     X = np.empty((n_j + 1, ni + 1, 2))
     for j, e in enumerate(eta):
         lin = inner + e * (outer - inner)
         orth = inner + e * far * nrm
-        wgt = np.exp(-e / 0.02)
+        wgt = taper * math.exp(-e * far / 0.01)
         X[j] = wgt * orth + (1.0 - wgt) * lin
-    # node ids; the wake cut (j = 0, idx < n_wk) and (j = 0, idx > ni - n_wk) coincide
+    # node ids; the wake cut (j = 0, idx <= n_wk) and (j = 0, idx >= ni - n_wk) coincide,
+    # trailing-edge node included
     nid = np.arange((n_j + 1) * (ni + 1)).reshape(n_j + 1, ni + 1)
-    for i in range(n_wk):
+    for i in range(n_wk + 1):
         nid[0, ni - i] = nid[0, i]
     used_ids = np.unique(nid)
     remap = -np.ones(nid.max() + 1, np.int64)
@@ -522,8 +537,8 @@ def naca0012_cmesh(n_target: int = 200000, re_c: float = 6e6, uref: float = 0.1,
     P = xy[cells4]
     area2 = np.sum(P[:, :, 0] * np.roll(P[:, :, 1], -1, 1) - np.roll(P[:, :, 0], -1, 1) * P[:, :, 1], 1)
     cells4[area2 < 0] = cells4[area2 < 0][:, ::-1]
-    tri_mask = eta[jj] > 0.02
-    cells = _hybrid_cells(cells4.astype(np.int32), tri_mask)
+    tri_mask = eta[jj + 1] > quad_layer / far
+    ptr, cn = _hybrid_cells(cells4.astype(np.int32), tri_mask)
     bn, bt, bvl = [], [], []
     a = math.radians(alpha_deg)
     uinf, vinf = uref * math.cos(a), uref * math.sin(a)
@@ -539,27 +554,27 @@ def naca0012_cmesh(n_target: int = 200000, re_c: float = 6e6, uref: float = 0.1,
         bvl.append((1.0, uinf, vinf, k_inf, w_inf))
         bn.append((nid[j, ni], nid[j + 1, ni])); bt.append(BC_FARFIELD)
         bvl.append((1.0, uinf, vinf, k_inf, w_inf))
-    ptr, cn = _cells_to_csr(cells)
     m = Mesh(xy, ptr, cn, np.asarray(bn, np.int32), np.asarray(bt, np.int32),
-             np.asarray(bvl, np.float64), name=f"naca0012_cmesh_{len(cells)}").normalized()
+             np.asarray(bvl, np.float64), name=f"naca0012_cmesh_{len(ptr) - 1}").normalized()
     n = m.n_cells
-    return Case(m, nu=nu, dt=z * nu / CS2, sst=True, uref=uref, lref=1.0, alpha_deg=alpha_deg,
+    return Case(m, nu=nu, cfl=cfl, sst=True, uref=uref, lref=1.0, alpha_deg=alpha_deg,
                 rho=np.ones(n), u=np.full(n, uinf), v=np.full(n, vinf), k=np.full(n, k_inf),
                 omega=np.full(n, w_inf), name=f"naca{n}_a{alpha_deg:g}")
 
 
 def batched_sweep(seed: int = 5, n_cavity: int = 32, n_bfs: int = 4, n_naca: int = 12,
                   scale: float = 1.0) -> list[Case]:
-    """The uneven multi-instance sweep: cavities 10k-40k triangles at Re 100-3200, BFS 80k
-    cells and NACA 0012 meshes of 50k-200k cells at angles 0-12 degrees (``scale``
-    multiplies every size, for small test versions)."""
+    """The uneven multi-instance sweep: cavities 10k-40k triangles at Re 100-3200 (laminar),
+    BFS 80k cells and NACA 0012 meshes of 50k-200k cells at angles 0-12 degrees (k-omega SST);
+    every time step at CFL 0.5 of its own mesh.  ``scale`` multiplies every size (small test
+    versions)."""
     rng = np.random.default_rng(seed)
     cases: list[Case] = []
     for i in range(n_cavity):
         n = int(round(math.exp(rng.uniform(math.log(10000), math.log(40000))) * scale))
         re = math.exp(rng.uniform(math.log(100.0), math.log(3200.0)))
         hb = 1.0 / max(8, int(round(math.sqrt(n) / 1.0)))
-        cases.append(cavity_delaunay(h_boundary=hb, n_target=max(64, n), re=re, z=5.0,
+        cases.append(cavity_delaunay(h_boundary=hb, n_target=max(64, n), re=re, cfl=0.5,
                                      seed=1000 + i))
     for i in range(n_bfs):
         cases.append(bfs_hybrid(n_target=max(400, int(80000 * scale)), seed=2000 + i))

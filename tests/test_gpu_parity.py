@@ -1,0 +1,196 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle, element by element.
+
+Tolerances: FP64 storage matches the oracle to 1e-10 relative per step (summation order
+differs); the FP32 deviation path matches to 1e-4 relative L2 on velocity and 0.5 % on
+C_D / C_L.  Sizes span several 128-cell tiles with ragged tails; the full-size cases run the
+launch configuration the benchmark times.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle
+from paper_1812_00394_gb300 import fvlbm, meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+FP64, FP32 = fvlbm.FVLBM_FP64, fvlbm.FVLBM_FP32_DEV
+
+
+def _rel_max(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _vel_l2(fg, fo):
+    return _rel_l2(np.concatenate([fg["u"], fg["v"]]), np.concatenate([fo["u"], fo["v"]]))
+
+
+CASES_FP64 = {
+    "cavity_quad64": lambda: mg.cavity_quad(64, re=400.0),
+    "cavity_quad50_ragged": lambda: mg.cavity_quad(50, re=400.0, jitter=0.2, seed=9),
+    "cavity_delaunay3k": lambda: mg.cavity_delaunay(h_boundary=1 / 40, n_target=3000, re=1000.0,
+                                                    z=5.0, seed=3),
+    "couette_tri_periodic": lambda: mg.Case(mg.couette_channel(20, 16, kind="tri", jitter=0.2,
+                                                               seed=4), nu=0.01, cfl=0.5),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES_FP64))
+def test_fp64_step_parity(name):
+    case = CASES_FP64[name]()
+    s = fvlbm.Solver(case, precision=FP64, device=0)
+    o = Oracle(case)
+    assert abs(s.dt() - o.dt) <= 1e-15 * o.dt
+    for n in (1, 4, 20):
+        s.step(n)
+        o.step(n)
+        assert _rel_max(s.get_f(), o.get_f()) < 1e-10, (name, n)
+    fg, fo = s.fields(), o.fields()
+    for key in ("rho", "u", "v"):
+        assert np.abs(fg[key] - fo[key]).max() < 1e-11, key
+
+
+def test_fp64_delaunay_full_size_z5_and_z50():
+    """The ~40k-triangle Delaunay cavity at dt = 5 tau and 50 tau (convective CFL ~0.3 and ~3)."""
+    for z, nst in ((5.0, 3), (50.0, 2)):
+        case = mg.cavity_delaunay(re=1000.0, z=z)
+        s = fvlbm.Solver(case, precision=FP64, device=0)
+        o = Oracle(case)
+        s.step(nst)
+        o.step(nst)
+        assert _rel_max(s.get_f(), o.get_f()) < 1e-10, z
+
+
+@pytest.mark.parametrize("maker", [lambda: mg.bfs_hybrid(n_target=3000),
+                                   lambda: mg.naca0012_cmesh(n_target=4000, alpha_deg=5.0)])
+def test_fp64_sst_parity(maker):
+    case = maker()
+    s = fvlbm.Solver(case, precision=FP64, device=0)
+    o = Oracle(case)
+    for n in (1, 3):
+        s.step(n)
+        o.step(n)
+        assert _rel_max(s.get_f(), o.get_f()) < 1e-10
+        fg, fo = s.fields(), o.fields()
+        for key in ("k", "omega", "nut"):
+            assert _rel_max(fg[key], fo[key]) < 1e-9, key
+
+
+def test_fp64_forces_and_cp_parity():
+    case = mg.naca0012_cmesh(n_target=4000, alpha_deg=5.0)
+    s = fvlbm.Solver(case, precision=FP64, device=0)
+    o = Oracle(case)
+    s.step(4)
+    o.step(4)
+    fg = s.forces(with_cp=True)
+    fo = o.forces(per_edge=True)
+    for key in ("fx", "fy", "cd", "cl"):
+        assert abs(fg[key] - fo[key]) <= 1e-9 * max(abs(fo[key]), 1e-12), key
+    assert np.abs(fg["cp"] - fo["cp"]).max() <= 1e-9 * np.abs(fo["cp"]).max()
+
+
+def test_fp64_stats_residual_and_mass():
+    case = mg.cavity_quad(32, re=400.0)
+    s = fvlbm.Solver(case, precision=FP64, device=0)
+    o = Oracle(case)
+    m0 = o.mass()
+    st = s.step(50, stats=True)
+    o.step(50)
+    assert st["steps"] == 50 and st["diverged"] == 0
+    assert abs(st["residual"] - o.residual()) <= 1e-8 * o.residual()
+    assert abs(st["mass"] - m0) / m0 < 1e-12
+
+
+def test_graph_replay_equals_eager_steps():
+    """Replaying captured graphs (16-step and 1-step) gives the same bits as stepping one by one."""
+    for case in (mg.cavity_quad(24, re=400.0), mg.bfs_hybrid(n_target=2000)):
+        a = fvlbm.Solver(case, precision=FP64, device=0)
+        b = fvlbm.Solver(case, precision=FP64, device=0)
+        a.step(34)
+        for _ in range(34):
+            b.step(1)
+        assert np.array_equal(a.get_f(), b.get_f())
+        assert np.array_equal(a.fields()["omega"], b.fields()["omega"])
+
+
+def test_batch_equals_separate_fp64():
+    cases = [mg.cavity_quad(20, re=300.0), mg.cavity_delaunay(h_boundary=1 / 30, n_target=1500,
+                                                             re=2000.0, z=5.0, seed=8),
+             mg.cavity_quad(33, re=1000.0, jitter=0.1, seed=2)]
+    batch = fvlbm.Solver(cases, precision=FP64, device=0)
+    batch.step(7)
+    for i, c in enumerate(cases):
+        one = fvlbm.Solver(c, precision=FP64, device=0)
+        one.step(7)
+        assert np.array_equal(batch.get_f(i), one.get_f())
+    turb = [mg.bfs_hybrid(n_target=1500), mg.naca0012_cmesh(n_target=2500, alpha_deg=3.0)]
+    bt = fvlbm.Solver(turb, precision=FP64, device=0)
+    bt.step(3)
+    for i, c in enumerate(turb):
+        one = fvlbm.Solver(c, precision=FP64, device=0)
+        one.step(3)
+        assert np.array_equal(bt.get_f(i), one.get_f())
+        assert np.array_equal(bt.fields(i)["nut"], one.fields()["nut"])
+
+
+def test_set_f_get_f_roundtrip_and_watchdog():
+    case = mg.cavity_quad(16)
+    s = fvlbm.Solver(case, precision=FP64, device=0)
+    f = s.get_f()
+    f2 = f * (1 + 1e-3 * mg.splitmix64_uniform(5, f.size).reshape(f.shape))
+    s.set_f(f2)
+    assert np.array_equal(s.get_f(), f2)
+    f2[7, 3] = np.nan                      # NaN injected on the host copy
+    s.set_f(f2)
+    st = s.step(1, stats=True)
+    assert st["diverged"] == 1
+
+
+def test_fp32_dev_cavity_parity():
+    case = mg.cavity_quad(64, re=400.0)
+    s = fvlbm.Solver(case, precision=FP32, device=0)
+    o = Oracle(case)
+    s.step(200)
+    o.step(200)
+    assert _vel_l2(s.fields(), o.fields()) < 1e-4
+    assert _rel_max(s.get_f(), o.get_f()) < 1e-5
+
+
+def test_fp32_dev_delaunay_full_size():
+    case = mg.cavity_delaunay(re=1000.0, z=5.0)
+    s = fvlbm.Solver(case, precision=FP32, device=0)
+    o = Oracle(case)
+    s.step(20)
+    o.step(20)
+    assert _vel_l2(s.fields(), o.fields()) < 1e-4
+
+
+@pytest.mark.parametrize("maker", [lambda: mg.bfs_hybrid(n_target=3000),
+                                   lambda: mg.naca0012_cmesh(n_target=4000, alpha_deg=7.0)])
+def test_fp32_dev_sst_parity(maker):
+    case = maker()
+    s = fvlbm.Solver(case, precision=FP32, device=0)
+    o = Oracle(case)
+    s.step(10)
+    o.step(10)
+    fg, fo = s.fields(), o.fields()
+    assert _vel_l2(fg, fo) < 1e-4
+    assert _rel_l2(fg["k"], fo["k"]) < 1e-3
+    assert _rel_l2(fg["omega"], fo["omega"]) < 1e-3
+
+
+def test_fp32_dev_forces_within_half_percent():
+    case = mg.naca0012_cmesh(n_target=4000, alpha_deg=7.0)
+    s = fvlbm.Solver(case, precision=FP32, device=0)
+    o = Oracle(case)
+    s.step(10)
+    o.step(10)
+    fg, fo = s.forces(), o.forces()
+    scale = math.hypot(fo["cd"], fo["cl"])
+    assert abs(fg["cd"] - fo["cd"]) <= 5e-3 * scale
+    assert abs(fg["cl"] - fo["cl"]) <= 5e-3 * scale
