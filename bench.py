@@ -342,6 +342,9 @@ def _kernel_bytes(kname, prec, cells, sst_cells):
         "flux_stage3": 9 + 18 + 9 + 1 + 9 + 3,     # f3, g, C, tau -> f^{n+1}, macros
         "sst_grad": 3 + 2 + 1 + 12 + 1,
         "sst_update": 3 + 3 + 12 + 1 + 4,
+        "fused_stage1": 9 + 1 + 27,                # f^n, tau -> f2, B, C (gradient in smem)
+        "fused_stage2": 9 + 18 + 1 + 18,           # f2, B, C, tau -> f3, C
+        "fused_stage3": 9 + 9 + 1 + 12,            # f3, C, tau -> f^{n+1}, macros
     }[kname]
     n = sst_cells if kname.startswith("sst") else cells
     return n * (words * w + idx)

@@ -90,6 +90,8 @@ typedef struct {
     const double *v_init;      /* [n_cells] or NULL (0) */
     const double *k_init;      /* [n_cells] or NULL (0) */
     const double *omega_init;  /* [n_cells] or NULL (1) */
+    int kernel_path;           /* 0: fused stage kernels with shared-memory halo staging
+                                  (default); 1: two-pass kernels (gradient array in HBM) */
 } fvlbm_params;
 
 typedef struct {
@@ -104,7 +106,7 @@ typedef struct fvlbm_handle fvlbm_handle;
 /* Build one solver instance on `device` (the current device when < 0), issuing work on
  * `stream` (a cudaStream_t; NULL creates a private non-blocking stream).  Step 0 of Sec. 3.2:
  * f = f^eq(rho_init, u_init); k, omega initialised; nu_t = k / omega.  Mesh geometry, the
- * least-squares matrices, wall distance and a locality-preserving (Morton) renumbering are
+ * least-squares matrices, wall distance and a locality-preserving (Hilbert) renumbering are
  * computed on the host; the handle owns all device memory it allocates.
  * Errors: BAD_MESH, BAD_BC, BAD_PARAM, OOM, CUDA. */
 int fvlbm_create(const fvlbm_mesh *mesh, const fvlbm_bc *bc, const fvlbm_params *params,

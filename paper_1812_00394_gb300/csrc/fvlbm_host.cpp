@@ -1,8 +1,8 @@
 // fvlbm_host.cpp -- host preprocessing of one solver instance: mesh validation, face
 // connectivity, finite-volume geometry (Eq. (advection) needs A, n and Delta l per face), the
 // least-squares gradient weights (Step 2 of Sec. 3.2), periodic gluing, wall distance d
-// (Sec. 2, needed by f1 and f2), the time step from a CFL number, and a Morton renumbering of
-// the cells so that face neighbours sit close in memory on the GPU.
+// (Sec. 2, needed by f1 and f2), the time step from a CFL number, and a renumbering of
+// the cells (Hilbert curve) so that face neighbours sit close in memory on the GPU.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -22,17 +22,23 @@ inline uint64_t edge_id(int a, int b) {
     return (static_cast<uint64_t>(lo) << 32) | hi;
 }
 
-// Interleave the low 16 bits of x and y (Morton / Z-order key).
-inline uint32_t morton2(uint32_t x, uint32_t y) {
-    auto spread = [](uint32_t v) {
-        v &= 0xFFFFu;
-        v = (v | (v << 8)) & 0x00FF00FFu;
-        v = (v | (v << 4)) & 0x0F0F0F0Fu;
-        v = (v | (v << 2)) & 0x33333333u;
-        v = (v | (v << 1)) & 0x55555555u;
-        return v;
-    };
-    return spread(x) | (spread(y) << 1);
+// Position of (x, y) along a Hilbert curve over a 2^32 x 2^32 grid (iterative quadrant
+// descent with the curve's reflections).  Consecutive keys are face neighbours on the grid, so
+// runs of consecutive cells are compact patches with short perimeters.
+inline uint64_t hilbert_key(uint64_t x, uint64_t y) {
+    uint64_t d = 0;
+    for (uint64_t s = uint64_t(1) << 31; s > 0; s >>= 1) {
+        const uint64_t rx = (x & s) ? 1 : 0, ry = (y & s) ? 1 : 0;
+        d += s * s * ((3 * rx) ^ ry);
+        if (ry == 0) {  // rotate / reflect the sub-square
+            if (rx == 1) {
+                x = (s - 1) - (x & (s - 1)) + (x & ~(s - 1));
+                y = (s - 1) - (y & (s - 1)) + (y & ~(s - 1));
+            }
+            std::swap(x, y);
+        }
+    }
+    return d;
 }
 
 double point_segment(double px, double py, double ax, double ay, double bx, double by) {
@@ -46,6 +52,7 @@ double point_segment(double px, double py, double ax, double ay, double bx, doub
 
 struct FaceGeo {
     int nbr = kNone;        // neighbour input cell id, or -(b+1) boundary edge, or kNone
+    int back = -1;          // local slot of this face in the neighbour's face list
     double nx = 0, ny = 0;  // unit outward normal
     double len = 0;
     double xm = 0, ym = 0;
@@ -123,7 +130,9 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
                 }
                 FaceGeo &G = face[4 * static_cast<size_t>(it->second.cell) + it->second.local];
                 F.nbr = it->second.cell;
+                F.back = it->second.local;
                 G.nbr = i;
+                G.back = l;
                 it->second.cell = -1;  // closed
             }
         }
@@ -157,9 +166,11 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
         FaceGeo &A = face[4 * static_cast<size_t>(bside[ea].cell) + bside[ea].local];
         FaceGeo &B = face[4 * static_cast<size_t>(bside[eb].cell) + bside[eb].local];
         A.nbr = bside[eb].cell;
+        A.back = bside[eb].local;
         A.sx = -sx;
         A.sy = -sy;
         B.nbr = bside[ea].cell;
+        B.back = bside[ea].local;
         B.sx = sx;
         B.sy = sy;
         // the glued face is one face: side B takes side A's normal reversed and its length
@@ -185,25 +196,27 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
         }
     }
 
-    // Morton renumbering of the cells by centroid
+    // Hilbert renumbering of the cells by centroid (32-bit resolution per axis, so that even
+    // wall cells of 1e-6 chord on a 40-chord domain get distinct keys)
     double x0 = cx[0], x1 = cx[0], y0 = cy[0], y1 = cy[0];
     for (int i = 0; i < nc; ++i) {
         x0 = std::min(x0, cx[i]); x1 = std::max(x1, cx[i]);
         y0 = std::min(y0, cy[i]); y1 = std::max(y1, cy[i]);
     }
     const double span = std::max(x1 - x0, y1 - y0) + 1e-300;
-    std::vector<std::pair<uint32_t, int>> key(nc);
+    const double qmax = 4294967295.0;
+    std::vector<std::pair<uint64_t, int>> key(nc);
     for (int i = 0; i < nc; ++i) {
-        const uint32_t qx = static_cast<uint32_t>(std::min(65535.0, (cx[i] - x0) / span * 65535.0));
-        const uint32_t qy = static_cast<uint32_t>(std::min(65535.0, (cy[i] - y0) / span * 65535.0));
-        key[i] = {morton2(qx, qy), i};
+        const uint64_t qx = static_cast<uint64_t>(std::min(qmax, (cx[i] - x0) / span * qmax));
+        const uint64_t qy = static_cast<uint64_t>(std::min(qmax, (cy[i] - y0) / span * qmax));
+        key[i] = {hilbert_key(qx, qy), i};
     }
     std::stable_sort(key.begin(), key.end(),
                      [](const auto &a, const auto &b) { return a.first < b.first; });
     Prepared &P = *out;
     P = Prepared();
     P.nc = nc;
-    P.np = (nc + kTile - 1) / kTile * kTile;
+    P.np = (nc + kBlock - 1) / kBlock * kBlock;
     P.n_bedges_in = nbe;
     const size_t np = P.np;
     P.perm.resize(nc);
@@ -236,6 +249,9 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
     }
 
     P.nbr.assign(4 * np, kNone);
+    P.back.assign(4 * np, -1);
+    P.nface.assign(np, 0);
+    P.gq.assign(8 * np, 0.0);
     P.sn.assign(8 * np, 0.0);
     P.lsq.assign(8 * np, 0.0);
     P.rown.assign(8 * np, 0.0);
@@ -247,6 +263,12 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
         const int i = P.perm[k];
         const int nv = m.cell_ptr[i + 1] - m.cell_ptr[i];
         P.area[k] = area[i];
+        P.nface[k] = nv;
+        for (int l = 0; l < nv; ++l) {  // node positions relative to the centroid
+            const int a = m.cell_nodes[m.cell_ptr[i] + l];
+            P.gq[(2 * l) * np + k] = xy[2 * a] - cx[i];
+            P.gq[(2 * l + 1) * np + k] = xy[2 * a + 1] - cy[i];
+        }
         double dx[4], dy[4];
         double mxx = 0, mxy = 0, myy = 0;
         for (int l = 0; l < nv; ++l) {
@@ -254,6 +276,7 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
             if (F.nbr >= 0) {
                 const double xj = cx[F.nbr] + F.sx, yj = cy[F.nbr] + F.sy;
                 P.nbr[l * np + k] = inv[F.nbr];
+                P.back[l * np + k] = F.back;
                 dx[l] = xj - cx[i];
                 dy[l] = yj - cy[i];
                 P.rnbr[(2 * l) * np + k] = F.xm - xj;

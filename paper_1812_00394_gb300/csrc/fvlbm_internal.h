@@ -11,11 +11,13 @@
 namespace fvlbm {
 
 constexpr int kQ = 9;          // D2Q9
-constexpr int kTile = 128;     // cells per thread block; instances are padded to a multiple
+constexpr int kTile = 128;     // cells per thread block of the per-cell kernels
+constexpr int kBlock = 256;    // cells per block of the fused stage kernel (= 2 tiles);
+                               // instances are padded to a multiple of kBlock
 constexpr int kNone = INT32_MIN;  // empty face slot (triangles have 3 faces, padding cells 0)
 
-// One instance after preprocessing, in the library's internal cell order (Morton order of the
-// cell centroids), padded with inert cells (no faces, zero area) to a multiple of kTile.
+// One instance after preprocessing, in the library's internal cell order (Hilbert order of the
+// cell centroids), padded with inert cells (no faces, zero area) to a multiple of kBlock.
 // Face slot m of cell i is stored at [m * np + i] (vectors: [(2 m + c) * np + i]) so that one
 // thread per cell reads every array with unit stride.
 struct Prepared {
@@ -25,6 +27,10 @@ struct Prepared {
     int n_bedges_in = 0;        // boundary edges in the input (including periodic ones)
     std::vector<int> perm;      // internal id -> input cell id   [nc]
     std::vector<int> nbr;       // [4 np]  neighbour internal id, -(b+1) for boundary face b, kNone
+    std::vector<int> back;      // [4 np]  face slot of this face in the neighbour's list (or -1)
+    std::vector<int> nface;     // [np]    3 or 4 (0 for padding cells)
+    std::vector<double> gq;     // [8 np]  node k position minus centroid (x, y) for k < nface;
+                                //         face m joins nodes m and (m + 1) mod nface
     std::vector<double> sn;     // [8 np]  n * Delta l / A of face m, out of the cell
     std::vector<double> lsq;    // [8 np]  least-squares weight W_m = M^{-1} d_m
     std::vector<double> rown;   // [8 np]  face midpoint - own centroid

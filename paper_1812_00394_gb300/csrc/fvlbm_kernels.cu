@@ -1,8 +1,8 @@
 // fvlbm_kernels.cu -- sm_103a kernels and the C ABI entry points of the FVLBM time step.
 //
-// One thread owns one cell.  Cells are Morton ordered per instance and instances are padded
-// to a multiple of kTile (= blockDim.x), so every block belongs to exactly one instance and
-// reads that instance's parameters.  Every per-cell array is structure-of-arrays with stride
+// One thread owns one cell.  Cells are Hilbert ordered per instance and instances are padded
+// to a multiple of kBlock (two kTile tiles), so every thread block belongs to exactly one
+// instance and reads that instance's parameters.  Every per-cell array is structure-of-arrays with stride
 // np (all instances), so a warp reads 32 consecutive words per field.  Face fluxes are
 // accumulated per cell over the cell's own face list (each interior face is evaluated by
 // both of its cells with bit-identical face values), so no atomics are needed and the sum is
@@ -209,9 +209,9 @@ __global__ void __launch_bounds__(kTile) k_grad(const T *__restrict__ f, T *__re
 }
 
 // ------------------------------------------------------------------ block reduction (FP64)
-template <int N>
+template <int N, int NT = kTile>
 __device__ __forceinline__ void block_sum(double (&v)[N], double *out) {
-    __shared__ double red[kTile / 32][N];
+    __shared__ double red[NT / 32][N];
 #pragma unroll
     for (int k = 0; k < N; ++k)
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
@@ -221,57 +221,24 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *out) {
     __syncthreads();
     if (threadIdx.x < N) {
         double s = 0;
-        for (int w = 0; w < kTile / 32; ++w) s += red[w][threadIdx.x];
+        for (int w = 0; w < NT / 32; ++w) s += red[w][threadIdx.x];
         out[threadIdx.x] = s;
     }
 }
 
-// ------------------------------------------------------------------ flux + stage solve
-// Gamma^a_alpha,i = -sum_m (e_alpha . n_m Delta l_m / A_i) f_{alpha,bc,m}  (Eq. (advection)) with
-// upwind linear face values, then the local algebra of the next stage (see file header).
-template <class T, int STAGE, bool STATS>
-__global__ void __launch_bounds__(kTile)
-    k_flux_stage(const T *__restrict__ fs, const T *__restrict__ g, T *__restrict__ fs_out,
-                 T *__restrict__ fn, T *__restrict__ Bacc, T *__restrict__ Cacc,
-                 const T *__restrict__ tau, T *__restrict__ mac, double *__restrict__ partial,
-                 Geo<T> G) {
-    const int i = blockIdx.x * kTile + threadIdx.x;
-    const size_t np = G.np;
-    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
+// Local algebra after Gamma^a(J) of a cell is known (acc = -Gamma^a(J)); fi = f^(J).
+//   J = 1: Gamma^c(1) from f^n and f^(1); stage 2 solve (Eq. (fnewstage)); B, C
+//   J = 2: stage 3 solve from B + dt/2 Gamma^a(2); C update
+//   J = 3: f^{n+1} = f^(3) + C + dt/3 Gamma^a(3) (Eq. (imextwo)); macros; FP64 partial sums
+template <class T, int STAGE, bool STATS, int NT>
+__device__ __forceinline__ void stage_update(int i, size_t np, const T *fi, const T *acc,
+                                             const InstParam &P, T *__restrict__ fs_out,
+                                             T *__restrict__ fn, T *__restrict__ Bacc,
+                                             T *__restrict__ Cacc, const T *__restrict__ tau,
+                                             T *__restrict__ mac, double *__restrict__ partial,
+                                             const T *__restrict__ area) {
     const T rho0 = T(P.rho0);
     const T dt = T(P.dt);
-    T fi[kQ], acc[kQ];
-    load9(fs, np, i, fi);
-#pragma unroll
-    for (int a = 0; a < kQ; ++a) acc[a] = T(0);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const int nb = G.nbr[m * np + i];
-        if (nb == kNone) continue;
-        const T snx = G.sn[(2 * m) * np + i], sny = G.sn[(2 * m + 1) * np + i];
-        if (nb >= 0) {
-            const T rox = G.rown[(2 * m) * np + i], roy = G.rown[(2 * m + 1) * np + i];
-            const T rnx = G.rnbr[(2 * m) * np + i], rny = G.rnbr[(2 * m + 1) * np + i];
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) {
-                const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
-                T fv;
-                if (en >= T(0))
-                    fv = fi[a] + g[(2 * a) * np + i] * rox + g[(2 * a + 1) * np + i] * roy;
-                else
-                    fv = fs[a * np + nb] + g[(2 * a) * np + nb] * rnx + g[(2 * a + 1) * np + nb] * rny;
-                acc[a] += en * fv;
-            }
-        } else {
-            const int b = -nb - 1;
-            T dr, r, u, v, fb[kQ];
-            moments(fi, rho0, dr, r, u, v);
-            boundary_values(G.btype[b], G.bval + b, 0, G.nbt, snx, sny, fi, dr, r, u, v, rho0, fb);
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) acc[a] += (T(ex_of(a)) * snx + T(ey_of(a)) * sny) * fb[a];
-        }
-    }
-    // acc = -Gamma^a
     const T t_i = tau[i];
     if (STAGE == 1) {
         // fi = f^(1); f^n, Gamma^c(1) from f^n and f^(1)
@@ -323,13 +290,237 @@ __global__ void __launch_bounds__(kTile)
             const double un = double(u), vn = double(v);
             const bool bad = !(isfinite(un) && isfinite(vn) && isfinite(double(r)));
             double s[4] = {(un - uo) * (un - uo) + (vn - vo) * (vn - vo), un * un + vn * vn,
-                           double(r) * double(G.area[i]), bad ? 1.0 : 0.0};
-            block_sum<4>(s, partial + 4 * blockIdx.x);
+                           double(r) * double(area[i]), bad ? 1.0 : 0.0};
+            block_sum<4, NT>(s, partial + 4 * blockIdx.x);
         }
         mac[0 * np + i] = r;
         mac[1 * np + i] = u;
         mac[2 * np + i] = v;
     }
+}
+
+// ------------------------------------------------------------------ flux + stage solve
+// Gamma^a_alpha,i = -sum_m (e_alpha . n_m Delta l_m / A_i) f_{alpha,bc,m}  (Eq. (advection)) with
+// upwind linear face values, then the local algebra of the next stage (see file header).
+template <class T, int STAGE, bool STATS>
+__global__ void __launch_bounds__(kTile)
+    k_flux_stage(const T *__restrict__ fs, const T *__restrict__ g, T *__restrict__ fs_out,
+                 T *__restrict__ fn, T *__restrict__ Bacc, T *__restrict__ Cacc,
+                 const T *__restrict__ tau, T *__restrict__ mac, double *__restrict__ partial,
+                 Geo<T> G) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
+    const T rho0 = T(P.rho0);
+    T fi[kQ], acc[kQ];
+    load9(fs, np, i, fi);
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) acc[a] = T(0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int nb = G.nbr[m * np + i];
+        if (nb == kNone) continue;
+        const T snx = G.sn[(2 * m) * np + i], sny = G.sn[(2 * m + 1) * np + i];
+        if (nb >= 0) {
+            const T rox = G.rown[(2 * m) * np + i], roy = G.rown[(2 * m + 1) * np + i];
+            const T rnx = G.rnbr[(2 * m) * np + i], rny = G.rnbr[(2 * m + 1) * np + i];
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) {
+                const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
+                T fv;
+                if (en >= T(0))
+                    fv = fi[a] + g[(2 * a) * np + i] * rox + g[(2 * a + 1) * np + i] * roy;
+                else
+                    fv = fs[a * np + nb] + g[(2 * a) * np + nb] * rnx + g[(2 * a + 1) * np + nb] * rny;
+                acc[a] += en * fv;
+            }
+        } else {
+            const int b = -nb - 1;
+            T dr, r, u, v, fb[kQ];
+            moments(fi, rho0, dr, r, u, v);
+            boundary_values(G.btype[b], G.bval + b, 0, G.nbt, snx, sny, fi, dr, r, u, v, rho0, fb);
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) acc[a] += (T(ex_of(a)) * snx + T(ey_of(a)) * sny) * fb[a];
+        }
+    }
+    stage_update<T, STAGE, STATS, kTile>(i, np, fi, acc, P, fs_out, fn, Bacc, Cacc, tau, mac, partial,
+                                         G.area);
+}
+
+// ------------------------------------------------------------------ fused stage kernel
+// Per block of kBlock consecutive cells (Hilbert order): the ring-1 and ring-2 halo cells are
+// listed on the host; the local adjacency of block and ring-1 cells is stored with 16-bit local
+// indices.  Encoding of one adjacency word: kAdjNone (no face), kAdjBnd | global boundary face,
+// or local index | back slot << 16 | (neighbour is a triangle) << 18.
+constexpr unsigned kAdjNone = 0xFFFFFFFFu;
+constexpr unsigned kAdjBnd = 0x80000000u;
+
+struct Halo {
+    const int *__restrict__ halo_ptr;   // [nblk + 1] offsets into halo
+    const int *__restrict__ halo;       // global ids: ring 1 then ring 2, per block
+    const int *__restrict__ r1;         // [nblk] ring-1 count
+    const int *__restrict__ adj_ptr;    // [nblk + 1] offsets (cells) into adj / 4
+    const unsigned *__restrict__ adj;   // per block [4][kBlock + r1] adjacency words
+    int emax, gmax;                     // max ext cells, max gradient cells per block
+};
+
+// Face m of a cell with node positions q (relative to its centroid, [8][np] layout):
+// midpoint r = (q_m + q_{m+1}) / 2 and edge vector e = q_{m+1} - q_m.
+template <class T>
+__device__ __forceinline__ void face_geo(const T *__restrict__ gq, size_t np, int gid, int m,
+                                         int nv, T &rx, T &ry, T &exv, T &eyv) {
+    const int m1 = (m + 1 == nv) ? 0 : m + 1;
+    const T x0 = gq[(2 * m) * np + gid], y0 = gq[(2 * m + 1) * np + gid];
+    const T x1 = gq[(2 * m1) * np + gid], y1 = gq[(2 * m1 + 1) * np + gid];
+    rx = T(0.5) * (x0 + x1);
+    ry = T(0.5) * (y0 + y1);
+    exv = x1 - x0;
+    eyv = y1 - y0;
+}
+
+// One IMEX stage for a block: halo f^(J) (for J = 1, f^n relaxed to f^(1) on the fly) staged
+// in shared memory, gradients of block + ring-1 cells in shared memory, then the flux
+// (Eq. (advection)) and the local stage algebra of each block cell.  No gradient array goes
+// through HBM; geometry comes from node positions and the least-squares weights.
+template <class T, int STAGE, bool STATS>
+__global__ void __launch_bounds__(kBlock)
+    k_fused_stage(const T *__restrict__ fin, T *__restrict__ fs_out, T *__restrict__ fn,
+                  T *__restrict__ Bacc, T *__restrict__ Cacc, const T *__restrict__ tau,
+                  T *__restrict__ mac, double *__restrict__ partial, Geo<T> G, Halo H,
+                  const T *__restrict__ gq) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sf = reinterpret_cast<T *>(smem_raw);          // [9][emax]
+    T *sg = sf + kQ * H.emax;                          // [18][gmax]
+    const int b = blockIdx.x, t = threadIdx.x;
+    const int base = b * kBlock;
+    const size_t np = G.np;
+    const int E0 = H.emax, G0 = H.gmax;
+    const InstParam P = G.ip[G.tile_inst[2 * b]];
+    const T rho0 = T(P.rho0);
+    const int h0 = H.halo_ptr[b], nh = H.halo_ptr[b + 1] - h0, nr1 = H.r1[b];
+    const int E = kBlock + nh, NG = kBlock + nr1;
+    const unsigned *__restrict__ adj = H.adj + 4 * static_cast<size_t>(H.adj_ptr[b]);
+
+    // 1. stage the block and its two halo rings
+    for (int e = t; e < E; e += kBlock) {
+        const int gid = e < kBlock ? base + e : H.halo[h0 + e - kBlock];
+        T v[kQ];
+        load9(fin, np, gid, v);
+        if (STAGE == 1) {  // f^(1) = [f^n + z/4 f^eq(f^n)] / (1 + z/4), as k_stage1
+            T eq[kQ], dr, r, u, w;
+            moments(v, rho0, dr, r, u, w);
+            feq_dev(dr, r, u, w, eq);
+            const T zq = T(P.dt) / tau[gid] * T(0.25);
+            const T inv = T(1) / (T(1) + zq);
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) v[a] = (v[a] + zq * eq[a]) * inv;
+        }
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) sf[a * E0 + e] = v[a];
+    }
+    __syncthreads();
+
+    // 2. least-squares gradients of block and ring-1 cells
+    for (int c = t; c < NG; c += kBlock) {
+        const int gid = c < kBlock ? base + c : H.halo[h0 + c - kBlock];
+        T fc[kQ], gx[kQ], gy[kQ];
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+            fc[a] = sf[a * E0 + c];
+            gx[a] = gy[a] = T(0);
+        }
+        const int nv = adj[3 * NG + c] == kAdjNone ? 3 : 4;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const unsigned w = adj[m * NG + c];
+            if (w == kAdjNone) continue;
+            const T wx = G.lsq[(2 * m) * np + gid], wy = G.lsq[(2 * m + 1) * np + gid];
+            if (w & kAdjBnd) {
+                const int bf = static_cast<int>(w & ~kAdjBnd);
+                T rx, ry, exv, eyv, dr, r, u, v, fb[kQ];
+                face_geo(gq, np, gid, m, nv, rx, ry, exv, eyv);
+                moments(fc, rho0, dr, r, u, v);
+                boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, eyv, -exv, fc, dr, r, u, v,
+                                rho0, fb);
+#pragma unroll
+                for (int a = 0; a < kQ; ++a) {
+                    const T d = fb[a] - fc[a];
+                    gx[a] += wx * d;
+                    gy[a] += wy * d;
+                }
+            } else {
+                const int j = static_cast<int>(w & 0xFFFFu);
+#pragma unroll
+                for (int a = 0; a < kQ; ++a) {
+                    const T d = sf[a * E0 + j] - fc[a];
+                    gx[a] += wx * d;
+                    gy[a] += wy * d;
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+            sg[(2 * a) * G0 + c] = gx[a];
+            sg[(2 * a + 1) * G0 + c] = gy[a];
+        }
+    }
+    __syncthreads();
+
+    // 3. flux of block cell t and the stage algebra
+    const int i = base + t;
+    T fi[kQ], acc[kQ];
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+        fi[a] = sf[a * E0 + t];
+        acc[a] = T(0);
+    }
+    const int nv = adj[3 * NG + t] == kAdjNone ? 3 : 4;
+    // cell area from its node positions (shoelace relative to the centroid)
+    T a2 = T(0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (m < nv) {
+            const int m1 = (m + 1 == nv) ? 0 : m + 1;
+            a2 += gq[(2 * m) * np + i] * gq[(2 * m1 + 1) * np + i] -
+                  gq[(2 * m1) * np + i] * gq[(2 * m + 1) * np + i];
+        }
+    }
+    const T inv_a = a2 > T(0) ? T(2) / a2 : T(0);  // padding cells have no faces
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const unsigned w = adj[m * NG + t];
+        if (w == kAdjNone) continue;
+        T rox, roy, exv, eyv;
+        face_geo(gq, np, i, m, nv, rox, roy, exv, eyv);
+        const T snx = eyv * inv_a, sny = -exv * inv_a;   // n dl / A
+        if (w & kAdjBnd) {
+            const int bf = static_cast<int>(w & ~kAdjBnd);
+            T dr, r, u, v, fb[kQ];
+            moments(fi, rho0, dr, r, u, v);
+            boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, snx, sny, fi, dr, r, u, v, rho0, fb);
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) acc[a] += (T(ex_of(a)) * snx + T(ey_of(a)) * sny) * fb[a];
+        } else {
+            const int j = static_cast<int>(w & 0xFFFFu);
+            const int mp = static_cast<int>((w >> 16) & 3u);
+            const int nvj = (w >> 18) & 1u ? 3 : 4;
+            const int gj = j < kBlock ? base + j : H.halo[h0 + j - kBlock];
+            T rnx, rny, ejx, ejy;
+            face_geo(gq, np, gj, mp, nvj, rnx, rny, ejx, ejy);
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) {
+                const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
+                T fv;
+                if (en >= T(0))
+                    fv = fi[a] + sg[(2 * a) * G0 + t] * rox + sg[(2 * a + 1) * G0 + t] * roy;
+                else
+                    fv = sf[a * E0 + j] + sg[(2 * a) * G0 + j] * rnx + sg[(2 * a + 1) * G0 + j] * rny;
+                acc[a] += en * fv;
+            }
+        }
+    }
+    stage_update<T, STAGE, STATS, kBlock>(i, np, fi, acc, P, fs_out, fn, Bacc, Cacc, tau, mac,
+                                          partial, G.area);
 }
 
 // Sum per-block partials into per-instance totals (one block per instance).
@@ -669,7 +860,14 @@ struct fvlbm_handle {
     std::vector<void *> allocs;
     // device arrays (element type T = double or float; stored as void*)
     int *d_nbr = nullptr, *d_tile_inst = nullptr, *d_btype = nullptr, *d_bowner = nullptr;
-    int *d_perm = nullptr, *d_inst_tile0 = nullptr;
+    int *d_perm = nullptr, *d_inst_tile0 = nullptr, *d_inst_blk0 = nullptr;
+    // fused path: per-block halo lists and local adjacency
+    bool fused = false;
+    int nblk = 0, emax = 0, gmax = 0;
+    size_t fused_smem = 0;
+    int *d_halo_ptr = nullptr, *d_halo = nullptr, *d_r1 = nullptr, *d_adj_ptr = nullptr;
+    unsigned *d_adj = nullptr;
+    void *gq = nullptr;
     InstParam *d_ip = nullptr;
     void *sn = nullptr, *lsq = nullptr, *rown = nullptr, *rnbr = nullptr, *dinv = nullptr;
     void *area = nullptr, *wdist = nullptr, *bval = nullptr, *bnrm = nullptr, *blen = nullptr;
@@ -768,7 +966,10 @@ void launch(fvlbm_handle *h, int id, const char *name, F &&fn) {
     }
 }
 
-enum KernelId { K_SST_GRAD, K_SST_UPDATE, K_STAGE1, K_GRAD, K_FLUX1, K_FLUX2, K_FLUX3, K_REDUCE };
+enum KernelId {
+    K_SST_GRAD, K_SST_UPDATE, K_STAGE1, K_GRAD, K_FLUX1, K_FLUX2, K_FLUX3, K_REDUCE,
+    K_FUSED1, K_FUSED2, K_FUSED3
+};
 
 template <class T>
 void enqueue_step(fvlbm_handle *h, bool stats) {
@@ -790,6 +991,31 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
             k_sst_update<T><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G);
         });
         h->turb = n;
+    }
+    if (h->fused) {
+        Halo H{h->d_halo_ptr, h->d_halo, h->d_r1, h->d_adj_ptr, h->d_adj, h->emax, h->gmax};
+        const T *gq = static_cast<const T *>(h->gq);
+        const dim3 fg(h->nblk), fb(kBlock);
+        const size_t sm = h->fused_smem;
+        launch(h, K_FUSED1, "fused_stage1", [&] {
+            k_fused_stage<T, 1, false><<<fg, fb, sm, s>>>(fn, s1, fn, B, C, tau, mac, nullptr, G, H, gq);
+        });
+        launch(h, K_FUSED2, "fused_stage2", [&] {
+            k_fused_stage<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, H, gq);
+        });
+        if (stats) {
+            launch(h, K_FUSED3, "fused_stage3", [&] {
+                k_fused_stage<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, H, gq);
+            });
+            launch(h, K_REDUCE, "reduce", [&] {
+                k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->d_inst_blk0, h->d_inst_sums);
+            });
+        } else {
+            launch(h, K_FUSED3, "fused_stage3", [&] {
+                k_fused_stage<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, H, gq);
+            });
+        }
+        return;
     }
     launch(h, K_STAGE1, "stage1", [&] { k_stage1<T><<<grid, block, 0, s>>>(fn, s0, tau, G); });
     launch(h, K_GRAD, "grad_f", [&] { k_grad<T><<<grid, block, 0, s>>>(s0, g, G); });
@@ -822,7 +1048,7 @@ void enqueue(fvlbm_handle *h, bool stats) {
         enqueue_step<float>(h, stats);
 }
 
-int launches_per_step(const fvlbm_handle *h) { return (h->sst ? 2 : 0) + 7; }
+int launches_per_step(const fvlbm_handle *h) { return (h->sst ? 2 : 0) + (h->fused ? 3 : 7); }
 
 // Capture `nsteps` plain steps into an executable graph.  A replay always starts from the
 // k / omega / nu_t ping-pong parity the graph was captured with, and an even step count ends
@@ -838,6 +1064,86 @@ int build_graph(fvlbm_handle *h, int nsteps, cudaGraphExec_t *out) {
     e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e);
+    return FVLBM_OK;
+}
+
+// Per block of kBlock cells: ring-1 and ring-2 halo lists and the local adjacency of block and
+// ring-1 cells.  Falls back to the two-pass kernels (h->fused = false) when a block's halo does
+// not fit the 16-bit local index or the shared-memory budget.
+template <class T>
+int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<int> &back,
+                const std::vector<int> &nface) {
+    const size_t np = h->np;
+    h->nblk = static_cast<int>(np / kBlock);
+    std::vector<int> local(np, -1), halo_ptr(1, 0), halo, r1n, adj_ptr(1, 0);
+    std::vector<unsigned> adj;
+    int emax = 0, gmax = 0;
+    std::vector<int> ring1, ring2;
+    for (int b = 0; b < h->nblk; ++b) {
+        const int base = b * kBlock;
+        for (int c = 0; c < kBlock; ++c) local[base + c] = c;
+        ring1.clear();
+        ring2.clear();
+        int next = kBlock;
+        for (int c = 0; c < kBlock; ++c)
+            for (int m = 0; m < 4; ++m) {
+                const int v = nbr[m * np + base + c];
+                if (v >= 0 && local[v] < 0) { local[v] = next++; ring1.push_back(v); }
+            }
+        for (int g : ring1)
+            for (int m = 0; m < 4; ++m) {
+                const int v = nbr[m * np + g];
+                if (v >= 0 && local[v] < 0) { local[v] = next++; ring2.push_back(v); }
+            }
+        const int E = next, NG = kBlock + static_cast<int>(ring1.size());
+        emax = std::max(emax, E);
+        gmax = std::max(gmax, NG);
+        halo.insert(halo.end(), ring1.begin(), ring1.end());
+        halo.insert(halo.end(), ring2.begin(), ring2.end());
+        halo_ptr.push_back(static_cast<int>(halo.size()));
+        r1n.push_back(static_cast<int>(ring1.size()));
+        const size_t a0 = adj.size();
+        adj.resize(a0 + 4 * static_cast<size_t>(NG), kAdjNone);
+        for (int c = 0; c < NG; ++c) {
+            const int g = c < kBlock ? base + c : ring1[c - kBlock];
+            for (int m = 0; m < 4; ++m) {
+                const int v = nbr[m * np + g];
+                unsigned w = kAdjNone;
+                if (v == kNone) {
+                    w = kAdjNone;
+                } else if (v < 0) {
+                    w = kAdjBnd | static_cast<unsigned>(-v - 1);
+                } else {
+                    w = static_cast<unsigned>(local[v]) | (static_cast<unsigned>(back[m * np + g]) << 16) |
+                        (nface[v] == 3 ? (1u << 18) : 0u);
+                }
+                adj[a0 + static_cast<size_t>(m) * NG + c] = w;
+            }
+        }
+        adj_ptr.push_back(adj_ptr.back() + NG);
+        for (int c = 0; c < kBlock; ++c) local[base + c] = -1;
+        for (int g : ring1) local[g] = -1;
+        for (int g : ring2) local[g] = -1;
+    }
+    const size_t smem = (static_cast<size_t>(kQ) * emax + 18u * gmax) * sizeof(T);
+    if (emax >= 65536 || smem > 200 * 1024) {
+        h->fused = false;
+        return FVLBM_OK;
+    }
+    h->emax = emax;
+    h->gmax = gmax;
+    h->fused_smem = smem;
+    int rc;
+    if ((rc = upload_raw(h, &h->d_halo_ptr, halo_ptr))) return rc;
+    if (halo.empty()) halo.push_back(0);
+    if ((rc = upload_raw(h, &h->d_halo, halo))) return rc;
+    if ((rc = upload_raw(h, &h->d_r1, r1n))) return rc;
+    if ((rc = upload_raw(h, &h->d_adj_ptr, adj_ptr))) return rc;
+    if ((rc = upload_raw(h, &h->d_adj, adj))) return rc;
+    CK(cudaFuncSetAttribute(k_fused_stage<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    CK(cudaFuncSetAttribute(k_fused_stage<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    CK(cudaFuncSetAttribute(k_fused_stage<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    CK(cudaFuncSetAttribute(k_fused_stage<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     return FVLBM_OK;
 }
 
@@ -859,7 +1165,9 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
         if ((rc = dalloc(h, &h->f1, np * ts))) return rc;
     }
     // geometry, concatenated over instances with neighbour / boundary ids offset
-    std::vector<int> nbr(4 * np, kNone), btype(h->nbt), bowner(h->nbt), perm;
+    std::vector<int> nbr(4 * np, kNone), back(4 * np, -1), nface(np, 0);
+    std::vector<int> btype(h->nbt), bowner(h->nbt), perm;
+    std::vector<double> gq(8 * np, 0);
     std::vector<double> sn(8 * np, 0), lsq(8 * np, 0), rown(8 * np, 0), rnbr(8 * np, 0);
     std::vector<double> dinv(4 * np, 0), area(np, 0), wdist(np, 1e30);
     std::vector<double> bval(5 * static_cast<size_t>(h->nbt)), bnrm(2 * static_cast<size_t>(h->nbt));
@@ -873,6 +1181,7 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
             for (size_t k = 0; k < pn; ++k) {
                 const int v = p.nbr[m * pn + k];
                 nbr[m * np + o + k] = v == kNone ? kNone : (v >= 0 ? v + I.cell_off : v - I.bface_off);
+                back[m * np + o + k] = p.back[m * pn + k];
                 dinv[m * np + o + k] = p.dinv[m * pn + k];
             }
         for (int c = 0; c < 8; ++c)
@@ -881,7 +1190,9 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
                 lsq[c * np + o + k] = p.lsq[c * pn + k];
                 rown[c * np + o + k] = p.rown[c * pn + k];
                 rnbr[c * np + o + k] = p.rnbr[c * pn + k];
+                gq[c * np + o + k] = p.gq[c * pn + k];
             }
+        for (size_t k = 0; k < pn; ++k) nface[o + k] = p.nface[k];
         for (size_t k = 0; k < pn; ++k) {
             area[o + k] = p.area[k];
             wdist[o + k] = p.wdist[k];
@@ -918,6 +1229,8 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
     if ((rc = upload_as<T>(h, &h->bval, bval))) return rc;
     if ((rc = upload_as<T>(h, &h->bnrm, bnrm))) return rc;
     if ((rc = upload_as<T>(h, &h->blen, blen))) return rc;
+    if ((rc = upload_as<T>(h, &h->gq, gq))) return rc;
+    if (h->fused && (rc = build_halos<T>(h, nbr, back, nface))) return rc;
     {
         std::vector<double> kt(k0), wt(w0);
         void *tmp = nullptr;
@@ -984,6 +1297,7 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     CK(cudaSetDevice(device));
     h->precision = prec;
     h->sst = sst != 0;
+    h->fused = params[0].kernel_path == 0;
     h->ninst = n;
     int cell_off = 0, bface_off = 0;
     std::vector<int> tile_inst, inst_tile0;
@@ -1027,6 +1341,11 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     int rc;
     if ((rc = upload_raw(h.get(), &h->d_tile_inst, tile_inst))) { free_all(h.get()); return rc; }
     if ((rc = upload_raw(h.get(), &h->d_inst_tile0, inst_tile0))) { free_all(h.get()); return rc; }
+    {
+        std::vector<int> inst_blk0(inst_tile0.size());
+        for (size_t q = 0; q < inst_tile0.size(); ++q) inst_blk0[q] = inst_tile0[q] / 2;
+        if ((rc = upload_raw(h.get(), &h->d_inst_blk0, inst_blk0))) { free_all(h.get()); return rc; }
+    }
     if ((rc = upload_raw(h.get(), &h->d_ip, ip))) { free_all(h.get()); return rc; }
     if ((rc = dalloc(h.get(), reinterpret_cast<void **>(&h->d_partial), 4 * sizeof(double) * h->ntiles)) ||
         (rc = dalloc(h.get(), reinterpret_cast<void **>(&h->d_inst_sums), 4 * sizeof(double) * n))) {

@@ -40,10 +40,11 @@ CASES_FP64 = {
 }
 
 
+@pytest.mark.parametrize("path", [0, 1], ids=["fused", "twopass"])
 @pytest.mark.parametrize("name", sorted(CASES_FP64))
-def test_fp64_step_parity(name):
+def test_fp64_step_parity(name, path):
     case = CASES_FP64[name]()
-    s = fvlbm.Solver(case, precision=FP64, device=0)
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=path)
     o = Oracle(case)
     assert abs(s.dt() - o.dt) <= 1e-15 * o.dt
     for n in (1, 4, 20):
@@ -66,11 +67,12 @@ def test_fp64_delaunay_full_size_z5_and_z50():
         assert _rel_max(s.get_f(), o.get_f()) < 1e-10, z
 
 
+@pytest.mark.parametrize("path", [0, 1], ids=["fused", "twopass"])
 @pytest.mark.parametrize("maker", [lambda: mg.bfs_hybrid(n_target=3000),
                                    lambda: mg.naca0012_cmesh(n_target=4000, alpha_deg=5.0)])
-def test_fp64_sst_parity(maker):
+def test_fp64_sst_parity(maker, path):
     case = maker()
-    s = fvlbm.Solver(case, precision=FP64, device=0)
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=path)
     o = Oracle(case)
     for n in (1, 3):
         s.step(n)
@@ -151,9 +153,10 @@ def test_set_f_get_f_roundtrip_and_watchdog():
     assert st["diverged"] == 1
 
 
-def test_fp32_dev_cavity_parity():
+@pytest.mark.parametrize("path", [0, 1], ids=["fused", "twopass"])
+def test_fp32_dev_cavity_parity(path):
     case = mg.cavity_quad(64, re=400.0)
-    s = fvlbm.Solver(case, precision=FP32, device=0)
+    s = fvlbm.Solver(case, precision=FP32, device=0, kernel_path=path)
     o = Oracle(case)
     s.step(200)
     o.step(200)
@@ -170,11 +173,12 @@ def test_fp32_dev_delaunay_full_size():
     assert _vel_l2(s.fields(), o.fields()) < 1e-4
 
 
+@pytest.mark.parametrize("path", [0, 1], ids=["fused", "twopass"])
 @pytest.mark.parametrize("maker", [lambda: mg.bfs_hybrid(n_target=3000),
                                    lambda: mg.naca0012_cmesh(n_target=4000, alpha_deg=7.0)])
-def test_fp32_dev_sst_parity(maker):
+def test_fp32_dev_sst_parity(maker, path):
     case = maker()
-    s = fvlbm.Solver(case, precision=FP32, device=0)
+    s = fvlbm.Solver(case, precision=FP32, device=0, kernel_path=path)
     o = Oracle(case)
     s.step(10)
     o.step(10)
@@ -194,3 +198,26 @@ def test_fp32_dev_forces_within_half_percent():
     scale = math.hypot(fo["cd"], fo["cl"])
     assert abs(fg["cd"] - fo["cd"]) <= 5e-3 * scale
     assert abs(fg["cl"] - fo["cl"]) <= 5e-3 * scale
+
+
+def test_fused_matches_twopass_fp64():
+    """The fused shared-memory kernels and the two-pass kernels compute the same step (FP64, up
+    to the rounding of the neighbour reconstruction offsets)."""
+    case = mg.naca0012_cmesh(n_target=6000, alpha_deg=4.0)
+    a = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=0)
+    b = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    a.step(5)
+    b.step(5)
+    assert _rel_max(a.get_f(), b.get_f()) < 1e-12
+
+
+def test_full_sweep_fp32_sampled_against_oracle():
+    """The benchmark's workload and launch configuration (48 instances in one FP32 handle, fused
+    kernels, graph replay): after 2 steps, sampled instances match the FP64 oracle."""
+    cases = mg.batched_sweep()
+    s = fvlbm.Solver(cases, precision=FP32, device=0)
+    s.step(2)
+    for i in (0, 17, 32, 36, 47):
+        o = Oracle(cases[i])
+        o.step(2)
+        assert _vel_l2(s.fields(i), o.fields()) < 1e-4, cases[i].name
