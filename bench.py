@@ -398,11 +398,15 @@ def _e2e(torch, fvlbm, solver, stream, args, world, dist):
 
     def one_step():
         for i in range(n):
-            lib.fvlbm_set_f(solver.h, i, host_f[i].ctypes.data_as(C.c_void_p))
+            rc = lib.fvlbm_set_f(solver.h, i, host_f[i].ctypes.data_as(C.c_void_p))
+            if rc:
+                raise fvlbm.FvlbmError(rc, "fvlbm_set_f")
         solver.step(1)
         for i in range(n):
-            lib.fvlbm_get_fields(solver.h, i, None, outs[i][0].ctypes.data_as(C.c_void_p),
-                                 outs[i][1].ctypes.data_as(C.c_void_p), None, None, None)
+            rc = lib.fvlbm_get_fields(solver.h, i, None, outs[i][0].ctypes.data_as(C.c_void_p),
+                                      outs[i][1].ctypes.data_as(C.c_void_p), None, None, None)
+            if rc:
+                raise fvlbm.FvlbmError(rc, "fvlbm_get_fields")
     with torch.cuda.stream(stream):
         one_step()
         torch.cuda.synchronize()

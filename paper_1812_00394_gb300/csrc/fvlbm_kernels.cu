@@ -352,6 +352,7 @@ __global__ void __launch_bounds__(kTile)
 // listed on the host; the local adjacency of block and ring-1 cells is stored with 16-bit local
 // indices.  Encoding of one adjacency word: kAdjNone (no face), kAdjBnd | global boundary face,
 // or local index | back slot << 16 | (neighbour is a triangle) << 18.
+constexpr int kFusedSmemCap = 200 * 1024;  // dynamic shared memory cap of the fused kernel
 constexpr unsigned kAdjNone = 0xFFFFFFFFu;
 constexpr unsigned kAdjBnd = 0x80000000u;
 
@@ -1126,7 +1127,7 @@ int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<
         for (int g : ring2) local[g] = -1;
     }
     const size_t smem = (static_cast<size_t>(kQ) * emax + 18u * gmax) * sizeof(T);
-    if (emax >= 65536 || smem > 200 * 1024) {
+    if (emax >= 65536 || smem > static_cast<size_t>(kFusedSmemCap)) {
         h->fused = false;
         return FVLBM_OK;
     }
@@ -1140,10 +1141,13 @@ int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<
     if ((rc = upload_raw(h, &h->d_r1, r1n))) return rc;
     if ((rc = upload_raw(h, &h->d_adj_ptr, adj_ptr))) return rc;
     if ((rc = upload_raw(h, &h->d_adj, adj))) return rc;
-    CK(cudaFuncSetAttribute(k_fused_stage<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    CK(cudaFuncSetAttribute(k_fused_stage<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    CK(cudaFuncSetAttribute(k_fused_stage<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-    CK(cudaFuncSetAttribute(k_fused_stage<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    // The attribute is per function and process-wide, shared by every handle: always raise it
+    // to the library's cap so that a handle with a smaller halo never lowers another's limit.
+    const int cap = kFusedSmemCap;
+    CK(cudaFuncSetAttribute(k_fused_stage<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    CK(cudaFuncSetAttribute(k_fused_stage<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    CK(cudaFuncSetAttribute(k_fused_stage<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    CK(cudaFuncSetAttribute(k_fused_stage<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     return FVLBM_OK;
 }
 

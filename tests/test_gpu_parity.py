@@ -221,3 +221,13 @@ def test_full_sweep_fp32_sampled_against_oracle():
         o = Oracle(cases[i])
         o.step(2)
         assert _vel_l2(s.fields(i), o.fields()) < 1e-4, cases[i].name
+
+
+def test_handles_with_different_halo_sizes_coexist():
+    """A small handle created after a large one must not lower the large one's launch limits."""
+    big = fvlbm.Solver(mg.naca0012_cmesh(n_target=20000, alpha_deg=2.0), precision=FP32, device=0)
+    small = fvlbm.Solver(mg.cavity_quad(16), precision=FP32, device=0)
+    small.step(2)
+    small.close()
+    big.step(3, stats=True)
+    assert np.isfinite(big.fields()["u"]).all()
