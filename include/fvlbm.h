@@ -157,6 +157,37 @@ int fvlbm_profile_kernels(fvlbm_handle *h, int n_steps, int max_kernels, char *n
 void fvlbm_destroy(fvlbm_handle *h);
 const char *fvlbm_strerror(int code);
 
+/* ---------------------------------------------------------------------------------------------
+ * Allocation-free FP64 step statistics (no counterpart in the paper).
+ *
+ * For callers that cannot call cudaMalloc -- for example code that runs while a framework's
+ * caching allocator or a start-up memory pool owns all device memory, or real-time loops that
+ * must never block in the allocator.  Computes the same FP64 reduction fvlbm_step reports
+ * with stats (its velocity residual and mass), from caller-owned DEVICE arrays, without
+ * allocating anything: the per-block partial sums live in a fixed file-scope device array of
+ * FVLBM_STATS_STATIC_MAX_CELLS / 256 x 4 doubles (512 KiB), which every GPU that loads the
+ * library holds until the process exits.
+ *
+ * Inputs (device pointers, n doubles each): the velocity before (u_old, v_old) and after
+ * (u_new, v_new) a step, the density rho and the cell areas.  Output: `out`, a device pointer
+ * to 4 doubles = {sum |u_new - u_old|^2, sum |u_new|^2, sum rho * area, number of non-finite
+ * cells}; the residual of fvlbm_stats is sqrt(out[0]) / sqrt(out[1]).  Work is issued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream) on the current device and is
+ * asynchronous; read `out` after synchronising that stream.
+ *
+ * The first call on a device looks up the device address of the scratch array
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  Every call shares
+ * the one scratch array, so calls that overlap on the GPU (several streams or host threads)
+ * race; serialise them.  Each call overwrites all the scratch it reads, so no clearing is
+ * needed between calls.
+ *
+ * Errors: FVLBM_ERR_BAD_PARAM for a NULL pointer, n < 0, or n > FVLBM_STATS_STATIC_MAX_CELLS
+ * (message on stderr); FVLBM_ERR_CUDA if the symbol lookup or a launch fails. */
+#define FVLBM_STATS_STATIC_MAX_CELLS 4194304
+int fvlbm_stats_reduce_static(const double *u_old, const double *v_old, const double *u_new,
+                              const double *v_new, const double *rho, const double *area, int n,
+                              double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfvlbm.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["fvlbm_host.cpp", "fvlbm_kernels.cu"]
+SOURCES = ["fvlbm_host.cpp", "fvlbm_kernels.cu", "fvlbm_noalloc.cu"]
 HEADERS = ["fvlbm_internal.h"]
 
 
@@ -46,11 +46,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     inc = ["-I", INCLUDE, "-I", CSRC]
     host_o = os.path.join(BUILD, "fvlbm_host.o")
     dev_o = os.path.join(BUILD, "fvlbm_kernels.o")
+    na_o = os.path.join(BUILD, "fvlbm_noalloc.o")
     cmds = [
         ["g++", "-O2", "-std=c++17", "-fPIC", "-fopenmp", *inc, "-c",
          os.path.join(CSRC, "fvlbm_host.cpp"), "-o", host_o],
         [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
          *inc, "-c", os.path.join(CSRC, "fvlbm_kernels.cu"), "-o", dev_o],
+        [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+         *inc, "-c", os.path.join(CSRC, "fvlbm_noalloc.cu"), "-o", na_o],
     ]
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
              for c in cmds]
@@ -63,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with open(os.path.join(BUILD, "ptxas.log"), "w") as fh:
         fh.write(outs[1])
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([nvcc, ARCH, "-shared", "-Xcompiler", "-fopenmp", host_o, dev_o,
+    subprocess.check_call([nvcc, ARCH, "-shared", "-Xcompiler", "-fopenmp", host_o, dev_o, na_o,
                            "-o", tmp])
     os.replace(tmp, LIB)
     return LIB

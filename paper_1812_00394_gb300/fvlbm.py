@@ -53,7 +53,8 @@ class fvlbm_stats(C.Structure):
 
 EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "fvlbm_get_f",
            "fvlbm_set_f", "fvlbm_get_fields", "fvlbm_info", "fvlbm_footprint",
-           "fvlbm_profile_kernels", "fvlbm_destroy", "fvlbm_strerror"]
+           "fvlbm_profile_kernels", "fvlbm_destroy", "fvlbm_strerror",
+           "fvlbm_stats_reduce_static"]
 
 _lib = None
 
@@ -89,6 +90,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_destroy.restype = None
     lib.fvlbm_strerror.argtypes = [i]
     lib.fvlbm_strerror.restype = C.c_char_p
+    lib.fvlbm_stats_reduce_static.argtypes = [vp] * 6 + [i, vp, vp]
     for name in EXPORTS:
         if name not in ("fvlbm_destroy", "fvlbm_strerror"):
             getattr(lib, name).restype = i
@@ -201,6 +203,14 @@ def fvlbm_profile_kernels(h, n_steps: int) -> dict:
         nm = raw[32 * k:32 * (k + 1)].split(b"\0", 1)[0].decode()
         res[nm] = {"ms": float(ms[k]), "launches": int(launches[k])}
     return res
+
+
+def fvlbm_stats_reduce_static(u_old: int, v_old: int, u_new: int, v_new: int, rho: int,
+                              area: int, n: int, out: int, stream: int | None = None) -> None:
+    """Allocation-free FP64 statistics over caller-owned DEVICE arrays (raw pointers); writes 4
+    doubles to the device pointer ``out``.  For callers that cannot allocate device memory."""
+    _check(load().fvlbm_stats_reduce_static(u_old, v_old, u_new, v_new, rho, area, int(n), out,
+                                            stream), "fvlbm_stats_reduce_static")
 
 
 def fvlbm_destroy(h) -> None:
