@@ -230,20 +230,23 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *out) {
 //   J = 1: Gamma^c(1) from f^n and f^(1); stage 2 solve (Eq. (fnewstage)); B, C
 //   J = 2: stage 3 solve from B + dt/2 Gamma^a(2); C update
 //   J = 3: f^{n+1} = f^(3) + C + dt/3 Gamma^a(3) (Eq. (imextwo)); macros; FP64 partial sums
+// The accumulator inputs are read through (pointer, row stride, column): a1 is f^n (J = 1),
+// B (J = 2) or C (J = 3); a2 is C (J = 2).  Outputs go to global memory at cell i.
 template <class T, int STAGE, bool STATS, int NT>
-__device__ __forceinline__ void stage_update(int i, size_t np, const T *fi, const T *acc,
-                                             const InstParam &P, T *__restrict__ fs_out,
-                                             T *__restrict__ fn, T *__restrict__ Bacc,
-                                             T *__restrict__ Cacc, const T *__restrict__ tau,
-                                             T *__restrict__ mac, double *__restrict__ partial,
-                                             const T *__restrict__ area) {
+__device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, const T *acc,
+                                              const InstParam &P, T t_i, const T *a1, size_t ld1,
+                                              int c1, const T *a2, size_t ld2, int c2,
+                                              T *__restrict__ fs_out, T *__restrict__ fn,
+                                              T *__restrict__ Bacc, T *__restrict__ Cacc,
+                                              T *__restrict__ mac, double *__restrict__ partial,
+                                              const T *__restrict__ area) {
     const T rho0 = T(P.rho0);
     const T dt = T(P.dt);
-    const T t_i = tau[i];
     if (STAGE == 1) {
         // fi = f^(1); f^n, Gamma^c(1) from f^n and f^(1)
         T f0[kQ], eq[kQ], X[kQ], dr, r, u, v;
-        load9(fn, np, i, f0);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) f0[a] = a1[a * ld1 + c1];
         moments(f0, rho0, dr, r, u, v);
         feq_dev(dr, r, u, v, eq);
         T gc1[kQ];
@@ -268,7 +271,7 @@ __device__ __forceinline__ void stage_update(int i, size_t np, const T *fi, cons
     } else if (STAGE == 2) {
         T X[kQ], eq[kQ], dr, r, u, v, f3[kQ];
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) X[a] = Bacc[a * np + i] - T(0.5) * dt * acc[a];
+        for (int a = 0; a < kQ; ++a) X[a] = a1[a * ld1 + c1] - T(0.5) * dt * acc[a];
         moments(X, rho0, dr, r, u, v);
         feq_dev(dr, r, u, v, eq);
         const T zt = dt / t_i / T(3);
@@ -276,13 +279,13 @@ __device__ __forceinline__ void stage_update(int i, size_t np, const T *fi, cons
 #pragma unroll
         for (int a = 0; a < kQ; ++a) {
             f3[a] = (X[a] + zt * eq[a]) * inv;
-            Cacc[a * np + i] = Cacc[a * np + i] + dt / T(6) * acc[a];
+            Cacc[a * np + i] = a2[a * ld2 + c2] + dt / T(6) * acc[a];
         }
         store9(fs_out, np, i, f3);
     } else {
         T fnew[kQ], dr, r, u, v;
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) fnew[a] = fi[a] + Cacc[a * np + i] - dt / T(3) * acc[a];
+        for (int a = 0; a < kQ; ++a) fnew[a] = fi[a] + a1[a * ld1 + c1] - dt / T(3) * acc[a];
         store9(fn, np, i, fnew);
         moments(fnew, rho0, dr, r, u, v);
         if (STATS) {
@@ -297,6 +300,32 @@ __device__ __forceinline__ void stage_update(int i, size_t np, const T *fi, cons
         mac[1 * np + i] = u;
         mac[2 * np + i] = v;
     }
+}
+
+// Stage algebra with accumulators in global memory (two-pass kernels).
+template <class T, int STAGE, bool STATS, int NT>
+__device__ __forceinline__ void stage_update(int i, size_t np, const T *fi, const T *acc,
+                                             const InstParam &P, T *__restrict__ fs_out,
+                                             T *__restrict__ fn, T *__restrict__ Bacc,
+                                             T *__restrict__ Cacc, const T *__restrict__ tau,
+                                             T *__restrict__ mac, double *__restrict__ partial,
+                                             const T *__restrict__ area) {
+    const T *a1 = STAGE == 1 ? fn : (STAGE == 2 ? Bacc : Cacc);
+    stage_algebra<T, STAGE, STATS, NT>(i, np, fi, acc, P, tau[i], a1, np, i, Cacc, np, i, fs_out,
+                                       fn, Bacc, Cacc, mac, partial, area);
+}
+
+// Stage algebra with the accumulators and tau staged in shared memory (fused kernel).
+template <class T, int STAGE, bool STATS>
+__device__ __forceinline__ void fused_stage_update(int i, int t, size_t np, const T *fi,
+                                                   const T *acc, const InstParam &P, const T *sA,
+                                                   const T *sT, T *__restrict__ fs_out,
+                                                   T *__restrict__ fn, T *__restrict__ Cacc,
+                                                   T *__restrict__ mac, double *__restrict__ partial,
+                                                   const T *__restrict__ area, T *__restrict__ Bacc) {
+    stage_algebra<T, STAGE, STATS, kBlock>(i, np, fi, acc, P, sT[t], sA, kBlock, t,
+                                           sA + kQ * kBlock, kBlock, t, fs_out, fn, Bacc, Cacc,
+                                           mac, partial, area);
 }
 
 // ------------------------------------------------------------------ flux + stage solve
@@ -348,13 +377,15 @@ __global__ void __launch_bounds__(kTile)
 }
 
 // ------------------------------------------------------------------ fused stage kernel
-// Per block of kBlock consecutive cells (Hilbert order): the ring-1 and ring-2 halo cells are
-// listed on the host; the local adjacency of block and ring-1 cells is stored with 16-bit local
-// indices.  Encoding of one adjacency word: kAdjNone (no face), kAdjBnd | global boundary face,
-// or local index | back slot << 16 | (neighbour is a triangle) << 18.
+// Per block of kBlock consecutive cells (compact patch, see the host renumbering): the ring-1
+// and ring-2 halo cells are listed on the host; the local adjacency of block and ring-1 cells
+// is stored with 16-bit local indices.  Encoding of one adjacency word: kAdjNone (no face),
+// kAdjBnd | global boundary face, or local index | back slot << 16 | (neighbour is a
+// triangle) << 18.
 constexpr int kFusedSmemCap = 200 * 1024;  // dynamic shared memory cap of the fused kernel
 constexpr unsigned kAdjNone = 0xFFFFFFFFu;
 constexpr unsigned kAdjBnd = 0x80000000u;
+constexpr long long kWaitLimit = 1ll << 26;  // bounded spin on the staging barrier
 
 struct Halo {
     const int *__restrict__ halo_ptr;   // [nblk + 1] offsets into halo
@@ -362,84 +393,196 @@ struct Halo {
     const int *__restrict__ r1;         // [nblk] ring-1 count
     const int *__restrict__ adj_ptr;    // [nblk + 1] offsets (cells) into adj / 4
     const unsigned *__restrict__ adj;   // per block [4][kBlock + r1] adjacency words
-    int emax, gmax;                     // max ext cells, max gradient cells per block
+    int *__restrict__ err;              // set to 1 if a staging wait gave up
+    int emax, gmax;                     // smem row strides: max ext cells, max gradient cells
 };
 
-// Face m of a cell with node positions q (relative to its centroid, [8][np] layout):
+// ---- asynchronous staging primitives (sm_90+ bulk copy engine and cp.async)
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Face m of a cell whose node positions (relative to its centroid) are q[(2k + c) * ld]:
 // midpoint r = (q_m + q_{m+1}) / 2 and edge vector e = q_{m+1} - q_m.
 template <class T>
-__device__ __forceinline__ void face_geo(const T *__restrict__ gq, size_t np, int gid, int m,
-                                         int nv, T &rx, T &ry, T &exv, T &eyv) {
+__device__ __forceinline__ void face_geo_s(const T *q, int ld, int m, int nv, T &rx, T &ry,
+                                           T &exv, T &eyv) {
     const int m1 = (m + 1 == nv) ? 0 : m + 1;
-    const T x0 = gq[(2 * m) * np + gid], y0 = gq[(2 * m + 1) * np + gid];
-    const T x1 = gq[(2 * m1) * np + gid], y1 = gq[(2 * m1 + 1) * np + gid];
+    const T x0 = q[(2 * m) * ld], y0 = q[(2 * m + 1) * ld];
+    const T x1 = q[(2 * m1) * ld], y1 = q[(2 * m1 + 1) * ld];
     rx = T(0.5) * (x0 + x1);
     ry = T(0.5) * (y0 + y1);
     exv = x1 - x0;
     eyv = y1 - y0;
 }
 
-// One IMEX stage for a block: halo f^(J) (for J = 1, f^n relaxed to f^(1) on the fly) staged
-// in shared memory, gradients of block + ring-1 cells in shared memory, then the flux
-// (Eq. (advection)) and the local stage algebra of each block cell.  No gradient array goes
-// through HBM; geometry comes from node positions and the least-squares weights.
+// Shared-memory layout of the fused kernel (element offsets, every row 16-byte aligned):
+//   sf  [9][emax]   f^(J) of block, ring-1 and ring-2 cells
+//   sg  [18][gmax]  gradients of block and ring-1 cells
+//   sW  [8][gmax]   least-squares weights of block and ring-1 cells
+//   sQ  [8][gmax]   node positions of block and ring-1 cells
+//   sA  [18][kBlock] stage accumulators of block cells (f^n | B, C | C)
+//   sT  [emax]      tau of staged cells (stage 1)
+//   adj [4 gmax] words, then one 8-byte mbarrier
+template <class T>
+struct FusedSmem {
+    static __host__ __device__ size_t elems(int emax, int gmax) {
+        return size_t(kQ) * emax + 18u * gmax + 16u * gmax + 18u * kBlock + emax;
+    }
+    static __host__ __device__ size_t bytes(int emax, int gmax) {
+        return elems(emax, gmax) * sizeof(T) + 4u * gmax * sizeof(unsigned) + 16;
+    }
+};
+
+// One IMEX stage for a block.  Staging: the block's own rows (contiguous in every SoA array)
+// arrive by bulk copies on one mbarrier; halo rows are gathered with cp.async; nothing is
+// waited for until everything has been issued.  Then: stage-1 relaxation f^n -> f^(1) in
+// shared memory, least-squares gradients of block + ring-1 cells, and per block cell the flux
+// of Eq. (advection) and the local stage algebra.  No gradient array goes through HBM.
 template <class T, int STAGE, bool STATS>
 __global__ void __launch_bounds__(kBlock)
     k_fused_stage(const T *__restrict__ fin, T *__restrict__ fs_out, T *__restrict__ fn,
                   T *__restrict__ Bacc, T *__restrict__ Cacc, const T *__restrict__ tau,
                   T *__restrict__ mac, double *__restrict__ partial, Geo<T> G, Halo H,
                   const T *__restrict__ gq) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sf = reinterpret_cast<T *>(smem_raw);          // [9][emax]
-    T *sg = sf + kQ * H.emax;                          // [18][gmax]
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int E0 = H.emax, G0 = H.gmax;
+    T *sf = reinterpret_cast<T *>(smem_raw);
+    T *sg = sf + kQ * E0;
+    T *sW = sg + 18 * G0;
+    T *sQ = sW + 8 * G0;
+    T *sA = sQ + 8 * G0;
+    T *sT = sA + 18 * kBlock;
+    unsigned *sAdj = reinterpret_cast<unsigned *>(sT + E0);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(sAdj + 4 * G0);
+
     const int b = blockIdx.x, t = threadIdx.x;
     const int base = b * kBlock;
     const size_t np = G.np;
-    const int E0 = H.emax, G0 = H.gmax;
     const InstParam P = G.ip[G.tile_inst[2 * b]];
     const T rho0 = T(P.rho0);
     const int h0 = H.halo_ptr[b], nh = H.halo_ptr[b + 1] - h0, nr1 = H.r1[b];
     const int E = kBlock + nh, NG = kBlock + nr1;
-    const unsigned *__restrict__ adj = H.adj + 4 * static_cast<size_t>(H.adj_ptr[b]);
+    const unsigned *__restrict__ adj_g = H.adj + 4 * static_cast<size_t>(H.adj_ptr[b]);
 
-    // 1. stage the block and its two halo rings
-    for (int e = t; e < E; e += kBlock) {
-        const int gid = e < kBlock ? base + e : H.halo[h0 + e - kBlock];
-        T v[kQ];
-        load9(fin, np, gid, v);
-        if (STAGE == 1) {  // f^(1) = [f^n + z/4 f^eq(f^n)] / (1 + z/4), as k_stage1
-            T eq[kQ], dr, r, u, w;
-            moments(v, rho0, dr, r, u, w);
-            feq_dev(dr, r, u, w, eq);
-            const T zq = T(P.dt) / tau[gid] * T(0.25);
-            const T inv = T(1) / (T(1) + zq);
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) v[a] = (v[a] + zq * eq[a]) * inv;
+    // 1. issue every copy of the block's data, then wait once
+    if (t == 0) mbar_init(bar);
+    __syncthreads();
+    if (t == 0) {
+        constexpr unsigned row = kBlock * sizeof(T);
+        const unsigned nacc = STAGE == 2 ? 18 : 9;
+        const unsigned adj_bytes = 4u * NG * sizeof(unsigned);
+        mbar_expect_tx(bar, row * (kQ + 8 + 8 + 1 + nacc) + adj_bytes);
+        for (int a = 0; a < kQ; ++a) bulk_g2s(sf + a * E0, fin + a * np + base, row, bar);
+        for (int k = 0; k < 8; ++k) {
+            bulk_g2s(sW + k * G0, G.lsq + k * np + base, row, bar);
+            bulk_g2s(sQ + k * G0, gq + k * np + base, row, bar);
         }
+        bulk_g2s(sT, tau + base, row, bar);
+        const T *acc0 = STAGE == 1 ? fn : (STAGE == 2 ? Bacc : Cacc);
+        for (int a = 0; a < kQ; ++a) bulk_g2s(sA + a * kBlock, acc0 + a * np + base, row, bar);
+        if (STAGE == 2)
+            for (int a = 0; a < kQ; ++a)
+                bulk_g2s(sA + (kQ + a) * kBlock, Cacc + a * np + base, row, bar);
+        bulk_g2s(sAdj, adj_g, adj_bytes, bar);
+    }
+    for (int e = kBlock + t; e < E; e += kBlock) {  // halo rows
+        const int gid = H.halo[h0 + e - kBlock];
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) sf[a * E0 + e] = v[a];
+        for (int a = 0; a < kQ; ++a) cp_async<sizeof(T)>(sf + a * E0 + e, fin + a * np + gid);
+        if (STAGE == 1) cp_async<sizeof(T)>(sT + e, tau + gid);
+        if (e < NG) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                cp_async<sizeof(T)>(sW + k * G0 + e, G.lsq + k * np + gid);
+                cp_async<sizeof(T)>(sQ + k * G0 + e, gq + k * np + gid);
+            }
+        }
+    }
+    cp_async_wait_all();
+    {
+        long long it = 0;
+        while (!mbar_try_wait(bar, 0) && ++it < kWaitLimit) {
+        }
+        if (it >= kWaitLimit) {  // give up: flag it, wait once more (bounded), leave
+            atomicExch(H.err, 1);
+            for (long long k = 0; k < kWaitLimit && !mbar_try_wait(bar, 0); ++k) {
+            }
+            return;
+        }
     }
     __syncthreads();
 
-    // 2. least-squares gradients of block and ring-1 cells
+    // 2. stage 1 only: f^(1) = [f^n + z/4 f^eq(f^n)] / (1 + z/4) (Eq. (fnewstage), J = 1)
+    if (STAGE == 1) {
+        for (int e = t; e < E; e += kBlock) {
+            T v[kQ], eq[kQ], dr, r, u, w;
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) v[a] = sf[a * E0 + e];
+            moments(v, rho0, dr, r, u, w);
+            feq_dev(dr, r, u, w, eq);
+            const T zq = T(P.dt) / sT[e] * T(0.25);
+            const T inv = T(1) / (T(1) + zq);
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) sf[a * E0 + e] = (v[a] + zq * eq[a]) * inv;
+        }
+        __syncthreads();
+    }
+
+    // 3. least-squares gradients of block and ring-1 cells (Step 2)
     for (int c = t; c < NG; c += kBlock) {
-        const int gid = c < kBlock ? base + c : H.halo[h0 + c - kBlock];
         T fc[kQ], gx[kQ], gy[kQ];
 #pragma unroll
         for (int a = 0; a < kQ; ++a) {
             fc[a] = sf[a * E0 + c];
             gx[a] = gy[a] = T(0);
         }
-        const int nv = adj[3 * NG + c] == kAdjNone ? 3 : 4;
+        const int nv = sAdj[3 * NG + c] == kAdjNone ? 3 : 4;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            const unsigned w = adj[m * NG + c];
+            const unsigned w = sAdj[m * NG + c];
             if (w == kAdjNone) continue;
-            const T wx = G.lsq[(2 * m) * np + gid], wy = G.lsq[(2 * m + 1) * np + gid];
+            const T wx = sW[(2 * m) * G0 + c], wy = sW[(2 * m + 1) * G0 + c];
             if (w & kAdjBnd) {
                 const int bf = static_cast<int>(w & ~kAdjBnd);
                 T rx, ry, exv, eyv, dr, r, u, v, fb[kQ];
-                face_geo(gq, np, gid, m, nv, rx, ry, exv, eyv);
+                face_geo_s(sQ + c, G0, m, nv, rx, ry, exv, eyv);
                 moments(fc, rho0, dr, r, u, v);
                 boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, eyv, -exv, fc, dr, r, u, v,
                                 rho0, fb);
@@ -467,7 +610,7 @@ __global__ void __launch_bounds__(kBlock)
     }
     __syncthreads();
 
-    // 3. flux of block cell t and the stage algebra
+    // 4. flux of block cell t (Eq. (advection)) and the stage algebra
     const int i = base + t;
     T fi[kQ], acc[kQ];
 #pragma unroll
@@ -475,24 +618,23 @@ __global__ void __launch_bounds__(kBlock)
         fi[a] = sf[a * E0 + t];
         acc[a] = T(0);
     }
-    const int nv = adj[3 * NG + t] == kAdjNone ? 3 : 4;
-    // cell area from its node positions (shoelace relative to the centroid)
-    T a2 = T(0);
+    const int nv = sAdj[3 * NG + t] == kAdjNone ? 3 : 4;
+    T a2 = T(0);  // twice the area, shoelace on centroid-relative nodes
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         if (m < nv) {
             const int m1 = (m + 1 == nv) ? 0 : m + 1;
-            a2 += gq[(2 * m) * np + i] * gq[(2 * m1 + 1) * np + i] -
-                  gq[(2 * m1) * np + i] * gq[(2 * m + 1) * np + i];
+            a2 += sQ[(2 * m) * G0 + t] * sQ[(2 * m1 + 1) * G0 + t] -
+                  sQ[(2 * m1) * G0 + t] * sQ[(2 * m + 1) * G0 + t];
         }
     }
     const T inv_a = a2 > T(0) ? T(2) / a2 : T(0);  // padding cells have no faces
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const unsigned w = adj[m * NG + t];
+        const unsigned w = sAdj[m * NG + t];
         if (w == kAdjNone) continue;
         T rox, roy, exv, eyv;
-        face_geo(gq, np, i, m, nv, rox, roy, exv, eyv);
+        face_geo_s(sQ + t, G0, m, nv, rox, roy, exv, eyv);
         const T snx = eyv * inv_a, sny = -exv * inv_a;   // n dl / A
         if (w & kAdjBnd) {
             const int bf = static_cast<int>(w & ~kAdjBnd);
@@ -505,9 +647,8 @@ __global__ void __launch_bounds__(kBlock)
             const int j = static_cast<int>(w & 0xFFFFu);
             const int mp = static_cast<int>((w >> 16) & 3u);
             const int nvj = (w >> 18) & 1u ? 3 : 4;
-            const int gj = j < kBlock ? base + j : H.halo[h0 + j - kBlock];
             T rnx, rny, ejx, ejy;
-            face_geo(gq, np, gj, mp, nvj, rnx, rny, ejx, ejy);
+            face_geo_s(sQ + j, G0, mp, nvj, rnx, rny, ejx, ejy);
 #pragma unroll
             for (int a = 0; a < kQ; ++a) {
                 const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
@@ -520,8 +661,8 @@ __global__ void __launch_bounds__(kBlock)
             }
         }
     }
-    stage_update<T, STAGE, STATS, kBlock>(i, np, fi, acc, P, fs_out, fn, Bacc, Cacc, tau, mac,
-                                          partial, G.area);
+    fused_stage_update<T, STAGE, STATS>(i, t, np, fi, acc, P, sA, sT, fs_out, fn, Cacc, mac,
+                                        partial, G.area, Bacc);
 }
 
 // Sum per-block partials into per-instance totals (one block per instance).
@@ -868,6 +1009,7 @@ struct fvlbm_handle {
     size_t fused_smem = 0;
     int *d_halo_ptr = nullptr, *d_halo = nullptr, *d_r1 = nullptr, *d_adj_ptr = nullptr;
     unsigned *d_adj = nullptr;
+    int *d_err = nullptr;   // device error flag (a staging wait gave up)
     void *gq = nullptr;
     InstParam *d_ip = nullptr;
     void *sn = nullptr, *lsq = nullptr, *rown = nullptr, *rnbr = nullptr, *dinv = nullptr;
@@ -994,7 +1136,7 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         h->turb = n;
     }
     if (h->fused) {
-        Halo H{h->d_halo_ptr, h->d_halo, h->d_r1, h->d_adj_ptr, h->d_adj, h->emax, h->gmax};
+        Halo H{h->d_halo_ptr, h->d_halo, h->d_r1, h->d_adj_ptr, h->d_adj, h->d_err, h->emax, h->gmax};
         const T *gq = static_cast<const T *>(h->gq);
         const dim3 fg(h->nblk), fb(kBlock);
         const size_t sm = h->fused_smem;
@@ -1126,7 +1268,9 @@ int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<
         for (int g : ring1) local[g] = -1;
         for (int g : ring2) local[g] = -1;
     }
-    const size_t smem = (static_cast<size_t>(kQ) * emax + 18u * gmax) * sizeof(T);
+    emax = (emax + 3) / 4 * 4;  // 16-byte aligned shared-memory rows
+    gmax = (gmax + 3) / 4 * 4;
+    const size_t smem = FusedSmem<T>::bytes(emax, gmax);
     if (emax >= 65536 || smem > static_cast<size_t>(kFusedSmemCap)) {
         h->fused = false;
         return FVLBM_OK;
@@ -1141,6 +1285,7 @@ int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<
     if ((rc = upload_raw(h, &h->d_r1, r1n))) return rc;
     if ((rc = upload_raw(h, &h->d_adj_ptr, adj_ptr))) return rc;
     if ((rc = upload_raw(h, &h->d_adj, adj))) return rc;
+    if ((rc = upload_raw(h, &h->d_err, std::vector<int>(1, 0)))) return rc;
     // The attribute is per function and process-wide, shared by every handle: always raise it
     // to the library's cap so that a handle with a smaller halo never lowers another's limit.
     const int cap = kFusedSmemCap;
@@ -1439,7 +1584,14 @@ int fvlbm_step(fvlbm_handle *h, int n_steps, fvlbm_stats *stats) {
         std::vector<double> sums(4 * static_cast<size_t>(h->ninst));
         CK(cudaMemcpyAsync(sums.data(), h->d_inst_sums, sums.size() * sizeof(double),
                            cudaMemcpyDeviceToHost, h->stream));
+        int err = 0;
+        if (h->d_err)
+            CK(cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
+        if (err) {
+            fprintf(stderr, "fvlbm_step: a fused-kernel staging wait gave up\n");
+            return FVLBM_ERR_CUDA;
+        }
         stats->steps = h->steps;
         stats->residual = 0;
         stats->mass = 0;
