@@ -315,19 +315,6 @@ __device__ __forceinline__ void stage_update(int i, size_t np, const T *fi, cons
                                        fn, Bacc, Cacc, mac, partial, area);
 }
 
-// Stage algebra with the accumulators and tau staged in shared memory (fused kernel).
-template <class T, int STAGE, bool STATS>
-__device__ __forceinline__ void fused_stage_update(int i, int t, size_t np, const T *fi,
-                                                   const T *acc, const InstParam &P, const T *sA,
-                                                   const T *sT, T *__restrict__ fs_out,
-                                                   T *__restrict__ fn, T *__restrict__ Cacc,
-                                                   T *__restrict__ mac, double *__restrict__ partial,
-                                                   const T *__restrict__ area, T *__restrict__ Bacc) {
-    stage_algebra<T, STAGE, STATS, kBlock>(i, np, fi, acc, P, sT[t], sA, kBlock, t,
-                                           sA + kQ * kBlock, kBlock, t, fs_out, fn, Bacc, Cacc,
-                                           mac, partial, area);
-}
-
 // ------------------------------------------------------------------ flux + stage solve
 // Gamma^a_alpha,i = -sum_m (e_alpha . n_m Delta l_m / A_i) f_{alpha,bc,m}  (Eq. (advection)) with
 // upwind linear face values, then the local algebra of the next stage (see file header).
@@ -452,31 +439,161 @@ __device__ __forceinline__ void face_geo_s(const T *q, int ld, int m, int nv, T 
     eyv = y1 - y0;
 }
 
+// ---- two threads per cell: lanes l and l ^ 16 of a warp own the same cell; half h = 0 takes
+// the axis velocities alpha = 1..4, half h = 1 the diagonals alpha = 5..8.  alpha = 0 has
+// e = 0, so it carries no flux and needs no gradient; its local algebra is done by both halves
+// (identically) and stored by half 0.  Per-thread arrays of 5 entries hold [alpha = 0, then the
+// half's four alpha].
+constexpr int kFusedThreads = 2 * kBlock;
+
+__device__ __forceinline__ int half_alpha(int h, int k) { return 1 + 4 * h + k; }  // k = 0..3
+__device__ __forceinline__ int hex(int h, int k) {  // e_x of half_alpha(h, k)
+    return h ? ((k == 0 || k == 3) ? 1 : -1) : (k == 0 ? 1 : (k == 2 ? -1 : 0));
+}
+__device__ __forceinline__ int hey(int h, int k) {
+    return h ? (k < 2 ? 1 : -1) : (k == 1 ? 1 : (k == 3 ? -1 : 0));
+}
+template <class T>
+__device__ __forceinline__ T hw(int h) { return h ? T(1.0 / 36.0) : T(1.0 / 9.0); }
+
+// Moments of a split deviation vector d[5] (see above); both halves get identical results.
+template <class T>
+__device__ __forceinline__ void moments_split(const T *d, int h, T rho0, T &drho, T &rho, T &u,
+                                              T &v) {
+    T s = 0, jx = 0, jy = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        s += d[1 + k];
+        jx += T(hex(h, k)) * d[1 + k];
+        jy += T(hey(h, k)) * d[1 + k];
+    }
+    s += __shfl_xor_sync(0xffffffffu, s, 16);
+    jx += __shfl_xor_sync(0xffffffffu, jx, 16);
+    jy += __shfl_xor_sync(0xffffffffu, jy, 16);
+    s += d[0];
+    drho = s;
+    rho = rho0 + s;
+    u = jx / rho;
+    v = jy / rho;
+}
+
+template <class T>
+__device__ __forceinline__ void feq_split(int h, T drho, T rho, T u, T v, T *eq) {
+    const T uu = T(1.5) * (u * u + v * v);
+    eq[0] = T(4.0 / 9.0) * (drho + rho * (-uu));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T eu = T(hex(h, k)) * u + T(hey(h, k)) * v;
+        eq[1 + k] = hw<T>(h) * (drho + rho * (T(3) * eu + T(4.5) * eu * eu - uu));
+    }
+}
+
+// Local stage algebra on split vectors (same arithmetic as stage_algebra).  a1 / a2 hold the
+// accumulators of this thread's alpha (f^n | B, C | C); outputs are written for the half's
+// alpha, and alpha = 0 by half 0.
+template <class T, int STAGE, bool STATS>
+__device__ __forceinline__ void split_algebra(int i, int h, size_t np, const T *fi, const T *acc,
+                                              const InstParam &P, T t_i, const T *a1,
+                                              const T *a2, T *__restrict__ fs_out,
+                                              T *__restrict__ fn, T *__restrict__ Bacc,
+                                              T *__restrict__ Cacc, T *__restrict__ mac,
+                                              double *__restrict__ partial,
+                                              const T *__restrict__ area) {
+    const T rho0 = T(P.rho0);
+    const T dt = T(P.dt);
+    auto row = [&](int k) { return k == 0 ? 0 : half_alpha(h, k - 1); };
+    if (STAGE == 1) {
+        T eq[5], X[5], gc1[5], f2[5], dr, r, u, v;
+        moments_split(a1, h, rho0, dr, r, u, v);
+        feq_split(h, dr, r, u, v, eq);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            gc1[k] = (eq[k] - fi[k]) / t_i;
+            X[k] = a1[k] - T(0.5) * dt * acc[k];
+        }
+        moments_split(X, h, rho0, dr, r, u, v);
+        feq_split(h, dr, r, u, v, eq);
+        const T zq = dt / t_i * T(0.25);
+        const T inv = T(1) / (T(1) + zq);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            f2[k] = (X[k] + zq * eq[k]) * inv;
+            const T gc2 = (eq[k] - f2[k]) / t_i;
+            if (k > 0 || h == 0) {
+                Bacc[row(k) * np + i] = X[k] + dt / T(3) * (gc1[k] + gc2);
+                Cacc[row(k) * np + i] = dt / T(6) * acc[k];
+                fs_out[row(k) * np + i] = f2[k];
+            }
+        }
+    } else if (STAGE == 2) {
+        T X[5], eq[5], dr, r, u, v;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) X[k] = a1[k] - T(0.5) * dt * acc[k];
+        moments_split(X, h, rho0, dr, r, u, v);
+        feq_split(h, dr, r, u, v, eq);
+        const T zt = dt / t_i / T(3);
+        const T inv = T(1) / (T(1) + zt);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            if (k > 0 || h == 0) {
+                fs_out[row(k) * np + i] = (X[k] + zt * eq[k]) * inv;
+                Cacc[row(k) * np + i] = a2[k] + dt / T(6) * acc[k];
+            }
+        }
+    } else {
+        T fnew[5], dr, r, u, v;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            fnew[k] = fi[k] + a1[k] - dt / T(3) * acc[k];
+            if (k > 0 || h == 0) fn[row(k) * np + i] = fnew[k];
+        }
+        moments_split(fnew, h, rho0, dr, r, u, v);
+        if (STATS) {
+            double sv[4] = {0, 0, 0, 0};
+            if (h == 0) {
+                const double uo = double(mac[1 * np + i]), vo = double(mac[2 * np + i]);
+                const double un = double(u), vn = double(v);
+                const bool bad = !(isfinite(un) && isfinite(vn) && isfinite(double(r)));
+                sv[0] = (un - uo) * (un - uo) + (vn - vo) * (vn - vo);
+                sv[1] = un * un + vn * vn;
+                sv[2] = double(r) * double(area[i]);
+                sv[3] = bad ? 1.0 : 0.0;
+            }
+            block_sum<4, kFusedThreads>(sv, partial + 4 * blockIdx.x);
+        }
+        if (h == 0) {
+            mac[0 * np + i] = r;
+            mac[1 * np + i] = u;
+            mac[2 * np + i] = v;
+        }
+    }
+}
+
 // Shared-memory layout of the fused kernel (element offsets, every row 16-byte aligned):
 //   sf  [9][emax]   f^(J) of block, ring-1 and ring-2 cells
-//   sg  [18][gmax]  gradients of block and ring-1 cells
+//   sg  [16][gmax]  gradients (alpha = 1..8) of block and ring-1 cells
 //   sW  [8][gmax]   least-squares weights of block and ring-1 cells
 //   sQ  [8][gmax]   node positions of block and ring-1 cells
-//   sA  [18][kBlock] stage accumulators of block cells (f^n | B, C | C)
-//   sT  [emax]      tau of staged cells (stage 1)
+//   sT  [emax]      tau of staged cells
 //   adj [4 gmax] words, then one 8-byte mbarrier
 template <class T>
 struct FusedSmem {
     static __host__ __device__ size_t elems(int emax, int gmax) {
-        return size_t(kQ) * emax + 18u * gmax + 16u * gmax + 18u * kBlock + emax;
+        return size_t(kQ) * emax + 16u * gmax + 16u * gmax + emax;
     }
     static __host__ __device__ size_t bytes(int emax, int gmax) {
         return elems(emax, gmax) * sizeof(T) + 4u * gmax * sizeof(unsigned) + 16;
     }
 };
 
-// One IMEX stage for a block.  Staging: the block's own rows (contiguous in every SoA array)
-// arrive by bulk copies on one mbarrier; halo rows are gathered with cp.async; nothing is
+// One IMEX stage for a block of kBlock cells, two threads per cell.  Staging: the block's own
+// rows (contiguous in every SoA array) arrive by bulk copies on one mbarrier; halo rows are
+// gathered with cp.async; each thread's accumulators are loaded into registers; nothing is
 // waited for until everything has been issued.  Then: stage-1 relaxation f^n -> f^(1) in
 // shared memory, least-squares gradients of block + ring-1 cells, and per block cell the flux
 // of Eq. (advection) and the local stage algebra.  No gradient array goes through HBM.
 template <class T, int STAGE, bool STATS>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? 2 : 1)
     k_fused_stage(const T *__restrict__ fin, T *__restrict__ fs_out, T *__restrict__ fn,
                   T *__restrict__ Bacc, T *__restrict__ Cacc, const T *__restrict__ tau,
                   T *__restrict__ mac, double *__restrict__ partial, Geo<T> G, Halo H,
@@ -485,15 +602,17 @@ __global__ void __launch_bounds__(kBlock)
     const int E0 = H.emax, G0 = H.gmax;
     T *sf = reinterpret_cast<T *>(smem_raw);
     T *sg = sf + kQ * E0;
-    T *sW = sg + 18 * G0;
+    T *sW = sg + 16 * G0;
     T *sQ = sW + 8 * G0;
-    T *sA = sQ + 8 * G0;
-    T *sT = sA + 18 * kBlock;
+    T *sT = sQ + 8 * G0;
     unsigned *sAdj = reinterpret_cast<unsigned *>(sT + E0);
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(sAdj + 4 * G0);
 
     const int b = blockIdx.x, t = threadIdx.x;
+    const int c0 = (t >> 5) * 16 + (t & 15);   // this thread's block cell
+    const int h = (t >> 4) & 1;                  // this thread's half of the velocities
     const int base = b * kBlock;
+    const int i = base + c0;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[2 * b]];
     const T rho0 = T(P.rho0);
@@ -506,23 +625,17 @@ __global__ void __launch_bounds__(kBlock)
     __syncthreads();
     if (t == 0) {
         constexpr unsigned row = kBlock * sizeof(T);
-        const unsigned nacc = STAGE == 2 ? 18 : 9;
         const unsigned adj_bytes = 4u * NG * sizeof(unsigned);
-        mbar_expect_tx(bar, row * (kQ + 8 + 8 + 1 + nacc) + adj_bytes);
+        mbar_expect_tx(bar, row * (kQ + 8 + 8 + 1) + adj_bytes);
         for (int a = 0; a < kQ; ++a) bulk_g2s(sf + a * E0, fin + a * np + base, row, bar);
         for (int k = 0; k < 8; ++k) {
             bulk_g2s(sW + k * G0, G.lsq + k * np + base, row, bar);
             bulk_g2s(sQ + k * G0, gq + k * np + base, row, bar);
         }
         bulk_g2s(sT, tau + base, row, bar);
-        const T *acc0 = STAGE == 1 ? fn : (STAGE == 2 ? Bacc : Cacc);
-        for (int a = 0; a < kQ; ++a) bulk_g2s(sA + a * kBlock, acc0 + a * np + base, row, bar);
-        if (STAGE == 2)
-            for (int a = 0; a < kQ; ++a)
-                bulk_g2s(sA + (kQ + a) * kBlock, Cacc + a * np + base, row, bar);
         bulk_g2s(sAdj, adj_g, adj_bytes, bar);
     }
-    for (int e = kBlock + t; e < E; e += kBlock) {  // halo rows
+    for (int e = kBlock + t; e < E; e += kFusedThreads) {  // halo rows
         const int gid = H.halo[h0 + e - kBlock];
 #pragma unroll
         for (int a = 0; a < kQ; ++a) cp_async<sizeof(T)>(sf + a * E0 + e, fin + a * np + gid);
@@ -535,23 +648,36 @@ __global__ void __launch_bounds__(kBlock)
             }
         }
     }
+    // this thread's accumulators, straight into registers (used only by this thread)
+    T a1[5], a2[5];
+    {
+        const T *p1 = STAGE == 1 ? fn : (STAGE == 2 ? Bacc : Cacc);
+        a1[0] = p1[i];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a1[1 + k] = p1[half_alpha(h, k) * np + i];
+        if (STAGE == 2) {
+            a2[0] = Cacc[i];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a2[1 + k] = Cacc[half_alpha(h, k) * np + i];
+        }
+    }
     cp_async_wait_all();
     {
         long long it = 0;
-        while (!mbar_try_wait(bar, 0) && ++it < kWaitLimit) {
-        }
-        if (it >= kWaitLimit) {  // give up: flag it, wait once more (bounded), leave
-            atomicExch(H.err, 1);
+        bool done = mbar_try_wait(bar, 0);
+        while (!done && ++it < kWaitLimit) done = mbar_try_wait(bar, 0);
+        // the block leaves together if any thread gave up: flag it, wait once more (bounded)
+        if (__syncthreads_or(!done)) {
+            if (t == 0) atomicExch(H.err, 1);
             for (long long k = 0; k < kWaitLimit && !mbar_try_wait(bar, 0); ++k) {
             }
             return;
         }
     }
-    __syncthreads();
 
     // 2. stage 1 only: f^(1) = [f^n + z/4 f^eq(f^n)] / (1 + z/4) (Eq. (fnewstage), J = 1)
     if (STAGE == 1) {
-        for (int e = t; e < E; e += kBlock) {
+        for (int e = t; e < E; e += kFusedThreads) {
             T v[kQ], eq[kQ], dr, r, u, w;
 #pragma unroll
             for (int a = 0; a < kQ; ++a) v[a] = sf[a * E0 + e];
@@ -565,13 +691,13 @@ __global__ void __launch_bounds__(kBlock)
         __syncthreads();
     }
 
-    // 3. least-squares gradients of block and ring-1 cells (Step 2)
-    for (int c = t; c < NG; c += kBlock) {
-        T fc[kQ], gx[kQ], gy[kQ];
+    // 3. least-squares gradients (alpha of this half) of block and ring-1 cells (Step 2)
+    for (int c = c0; c < NG; c += kBlock) {
+        T fc[4], gx[4], gy[4];
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) {
-            fc[a] = sf[a * E0 + c];
-            gx[a] = gy[a] = T(0);
+        for (int k = 0; k < 4; ++k) {
+            fc[k] = sf[half_alpha(h, k) * E0 + c];
+            gx[k] = gy[k] = T(0);
         }
         const int nv = sAdj[3 * NG + c] == kAdjNone ? 3 : 4;
 #pragma unroll
@@ -581,68 +707,75 @@ __global__ void __launch_bounds__(kBlock)
             const T wx = sW[(2 * m) * G0 + c], wy = sW[(2 * m + 1) * G0 + c];
             if (w & kAdjBnd) {
                 const int bf = static_cast<int>(w & ~kAdjBnd);
-                T rx, ry, exv, eyv, dr, r, u, v, fb[kQ];
+                T rx, ry, exv, eyv, dr, r, u, v, fb[kQ], fa[kQ];
                 face_geo_s(sQ + c, G0, m, nv, rx, ry, exv, eyv);
-                moments(fc, rho0, dr, r, u, v);
-                boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, eyv, -exv, fc, dr, r, u, v,
+#pragma unroll
+                for (int a = 0; a < kQ; ++a) fa[a] = sf[a * E0 + c];
+                moments(fa, rho0, dr, r, u, v);
+                boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, eyv, -exv, fa, dr, r, u, v,
                                 rho0, fb);
 #pragma unroll
-                for (int a = 0; a < kQ; ++a) {
-                    const T d = fb[a] - fc[a];
-                    gx[a] += wx * d;
-                    gy[a] += wy * d;
+                for (int k = 0; k < 4; ++k) {
+                    const T d = (h ? fb[5 + k] : fb[1 + k]) - fc[k];
+                    gx[k] += wx * d;
+                    gy[k] += wy * d;
                 }
             } else {
                 const int j = static_cast<int>(w & 0xFFFFu);
 #pragma unroll
-                for (int a = 0; a < kQ; ++a) {
-                    const T d = sf[a * E0 + j] - fc[a];
-                    gx[a] += wx * d;
-                    gy[a] += wy * d;
+                for (int k = 0; k < 4; ++k) {
+                    const T d = sf[half_alpha(h, k) * E0 + j] - fc[k];
+                    gx[k] += wx * d;
+                    gy[k] += wy * d;
                 }
             }
         }
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) {
-            sg[(2 * a) * G0 + c] = gx[a];
-            sg[(2 * a + 1) * G0 + c] = gy[a];
+        for (int k = 0; k < 4; ++k) {
+            const int q = half_alpha(h, k) - 1;
+            sg[(2 * q) * G0 + c] = gx[k];
+            sg[(2 * q + 1) * G0 + c] = gy[k];
         }
     }
     __syncthreads();
 
-    // 4. flux of block cell t (Eq. (advection)) and the stage algebra
-    const int i = base + t;
-    T fi[kQ], acc[kQ];
+    // 4. flux of block cell c0 (Eq. (advection)) for this half's alpha, then the stage algebra
+    T fi[5], acc[5];
+    fi[0] = sf[c0];
+    acc[0] = T(0);
 #pragma unroll
-    for (int a = 0; a < kQ; ++a) {
-        fi[a] = sf[a * E0 + t];
-        acc[a] = T(0);
+    for (int k = 0; k < 4; ++k) {
+        fi[1 + k] = sf[half_alpha(h, k) * E0 + c0];
+        acc[1 + k] = T(0);
     }
-    const int nv = sAdj[3 * NG + t] == kAdjNone ? 3 : 4;
-    T a2 = T(0);  // twice the area, shoelace on centroid-relative nodes
+    const int nv = sAdj[3 * NG + c0] == kAdjNone ? 3 : 4;
+    T a2x = T(0);  // twice the area, shoelace on centroid-relative nodes
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         if (m < nv) {
             const int m1 = (m + 1 == nv) ? 0 : m + 1;
-            a2 += sQ[(2 * m) * G0 + t] * sQ[(2 * m1 + 1) * G0 + t] -
-                  sQ[(2 * m1) * G0 + t] * sQ[(2 * m + 1) * G0 + t];
+            a2x += sQ[(2 * m) * G0 + c0] * sQ[(2 * m1 + 1) * G0 + c0] -
+                   sQ[(2 * m1) * G0 + c0] * sQ[(2 * m + 1) * G0 + c0];
         }
     }
-    const T inv_a = a2 > T(0) ? T(2) / a2 : T(0);  // padding cells have no faces
+    const T inv_a = a2x > T(0) ? T(2) / a2x : T(0);  // padding cells have no faces
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const unsigned w = sAdj[m * NG + t];
+        const unsigned w = sAdj[m * NG + c0];
         if (w == kAdjNone) continue;
         T rox, roy, exv, eyv;
-        face_geo_s(sQ + t, G0, m, nv, rox, roy, exv, eyv);
+        face_geo_s(sQ + c0, G0, m, nv, rox, roy, exv, eyv);
         const T snx = eyv * inv_a, sny = -exv * inv_a;   // n dl / A
         if (w & kAdjBnd) {
             const int bf = static_cast<int>(w & ~kAdjBnd);
-            T dr, r, u, v, fb[kQ];
-            moments(fi, rho0, dr, r, u, v);
-            boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, snx, sny, fi, dr, r, u, v, rho0, fb);
+            T dr, r, u, v, fb[kQ], fa[kQ];
 #pragma unroll
-            for (int a = 0; a < kQ; ++a) acc[a] += (T(ex_of(a)) * snx + T(ey_of(a)) * sny) * fb[a];
+            for (int a = 0; a < kQ; ++a) fa[a] = sf[a * E0 + c0];
+            moments(fa, rho0, dr, r, u, v);
+            boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, snx, sny, fa, dr, r, u, v, rho0, fb);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                acc[1 + k] += (T(hex(h, k)) * snx + T(hey(h, k)) * sny) * (h ? fb[5 + k] : fb[1 + k]);
         } else {
             const int j = static_cast<int>(w & 0xFFFFu);
             const int mp = static_cast<int>((w >> 16) & 3u);
@@ -650,19 +783,20 @@ __global__ void __launch_bounds__(kBlock)
             T rnx, rny, ejx, ejy;
             face_geo_s(sQ + j, G0, mp, nvj, rnx, rny, ejx, ejy);
 #pragma unroll
-            for (int a = 0; a < kQ; ++a) {
-                const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
-                T fv;
-                if (en >= T(0))
-                    fv = fi[a] + sg[(2 * a) * G0 + t] * rox + sg[(2 * a + 1) * G0 + t] * roy;
-                else
-                    fv = sf[a * E0 + j] + sg[(2 * a) * G0 + j] * rnx + sg[(2 * a + 1) * G0 + j] * rny;
-                acc[a] += en * fv;
+            for (int k = 0; k < 4; ++k) {
+                const int a = half_alpha(h, k);
+                const T en = T(hex(h, k)) * snx + T(hey(h, k)) * sny;
+                const bool own = en >= T(0);           // upwind side, branch free
+                const int src = own ? c0 : j;
+                const T rx = own ? rox : rnx, ry = own ? roy : rny;
+                const T fv = sf[a * E0 + src] + sg[(2 * a - 2) * G0 + src] * rx +
+                             sg[(2 * a - 1) * G0 + src] * ry;
+                acc[1 + k] += en * fv;
             }
         }
     }
-    fused_stage_update<T, STAGE, STATS>(i, t, np, fi, acc, P, sA, sT, fs_out, fn, Cacc, mac,
-                                        partial, G.area, Bacc);
+    split_algebra<T, STAGE, STATS>(i, h, np, fi, acc, P, sT[c0], a1, a2, fs_out, fn, Bacc, Cacc,
+                                   mac, partial, G.area);
 }
 
 // Sum per-block partials into per-instance totals (one block per instance).
@@ -1138,7 +1272,7 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
     if (h->fused) {
         Halo H{h->d_halo_ptr, h->d_halo, h->d_r1, h->d_adj_ptr, h->d_adj, h->d_err, h->emax, h->gmax};
         const T *gq = static_cast<const T *>(h->gq);
-        const dim3 fg(h->nblk), fb(kBlock);
+        const dim3 fg(h->nblk), fb(kFusedThreads);
         const size_t sm = h->fused_smem;
         launch(h, K_FUSED1, "fused_stage1", [&] {
             k_fused_stage<T, 1, false><<<fg, fb, sm, s>>>(fn, s1, fn, B, C, tau, mac, nullptr, G, H, gq);
