@@ -439,143 +439,15 @@ __device__ __forceinline__ void face_geo_s(const T *q, int ld, int m, int nv, T 
     eyv = y1 - y0;
 }
 
-// ---- two threads per cell: lanes l and l ^ 16 of a warp own the same cell; half h = 0 takes
-// the axis velocities alpha = 1..4, half h = 1 the diagonals alpha = 5..8.  alpha = 0 has
-// e = 0, so it carries no flux and needs no gradient; its local algebra is done by both halves
-// (identically) and stored by half 0.  Per-thread arrays of 5 entries hold [alpha = 0, then the
-// half's four alpha].
-constexpr int kFusedThreads = 2 * kBlock;
-
-__device__ __forceinline__ int half_alpha(int h, int k) { return 1 + 4 * h + k; }  // k = 0..3
-__device__ __forceinline__ int hex(int h, int k) {  // e_x of half_alpha(h, k)
-    return h ? ((k == 0 || k == 3) ? 1 : -1) : (k == 0 ? 1 : (k == 2 ? -1 : 0));
-}
-__device__ __forceinline__ int hey(int h, int k) {
-    return h ? (k < 2 ? 1 : -1) : (k == 1 ? 1 : (k == 3 ? -1 : 0));
-}
-template <class T>
-__device__ __forceinline__ T hw(int h) { return h ? T(1.0 / 36.0) : T(1.0 / 9.0); }
-
-// Moments of a split deviation vector d[5] (see above); both halves get identical results.
-template <class T>
-__device__ __forceinline__ void moments_split(const T *d, int h, T rho0, T &drho, T &rho, T &u,
-                                              T &v) {
-    T s = 0, jx = 0, jy = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        s += d[1 + k];
-        jx += T(hex(h, k)) * d[1 + k];
-        jy += T(hey(h, k)) * d[1 + k];
-    }
-    s += __shfl_xor_sync(0xffffffffu, s, 16);
-    jx += __shfl_xor_sync(0xffffffffu, jx, 16);
-    jy += __shfl_xor_sync(0xffffffffu, jy, 16);
-    s += d[0];
-    drho = s;
-    rho = rho0 + s;
-    u = jx / rho;
-    v = jy / rho;
-}
-
-template <class T>
-__device__ __forceinline__ void feq_split(int h, T drho, T rho, T u, T v, T *eq) {
-    const T uu = T(1.5) * (u * u + v * v);
-    eq[0] = T(4.0 / 9.0) * (drho + rho * (-uu));
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const T eu = T(hex(h, k)) * u + T(hey(h, k)) * v;
-        eq[1 + k] = hw<T>(h) * (drho + rho * (T(3) * eu + T(4.5) * eu * eu - uu));
-    }
-}
-
-// Local stage algebra on split vectors (same arithmetic as stage_algebra).  a1 / a2 hold the
-// accumulators of this thread's alpha (f^n | B, C | C); outputs are written for the half's
-// alpha, and alpha = 0 by half 0.
-template <class T, int STAGE, bool STATS>
-__device__ __forceinline__ void split_algebra(int i, int h, size_t np, const T *fi, const T *acc,
-                                              const InstParam &P, T t_i, const T *a1,
-                                              const T *a2, T *__restrict__ fs_out,
-                                              T *__restrict__ fn, T *__restrict__ Bacc,
-                                              T *__restrict__ Cacc, T *__restrict__ mac,
-                                              double *__restrict__ partial,
-                                              const T *__restrict__ area) {
-    const T rho0 = T(P.rho0);
-    const T dt = T(P.dt);
-    auto row = [&](int k) { return k == 0 ? 0 : half_alpha(h, k - 1); };
-    if (STAGE == 1) {
-        T eq[5], X[5], gc1[5], f2[5], dr, r, u, v;
-        moments_split(a1, h, rho0, dr, r, u, v);
-        feq_split(h, dr, r, u, v, eq);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            gc1[k] = (eq[k] - fi[k]) / t_i;
-            X[k] = a1[k] - T(0.5) * dt * acc[k];
-        }
-        moments_split(X, h, rho0, dr, r, u, v);
-        feq_split(h, dr, r, u, v, eq);
-        const T zq = dt / t_i * T(0.25);
-        const T inv = T(1) / (T(1) + zq);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            f2[k] = (X[k] + zq * eq[k]) * inv;
-            const T gc2 = (eq[k] - f2[k]) / t_i;
-            if (k > 0 || h == 0) {
-                Bacc[row(k) * np + i] = X[k] + dt / T(3) * (gc1[k] + gc2);
-                Cacc[row(k) * np + i] = dt / T(6) * acc[k];
-                fs_out[row(k) * np + i] = f2[k];
-            }
-        }
-    } else if (STAGE == 2) {
-        T X[5], eq[5], dr, r, u, v;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) X[k] = a1[k] - T(0.5) * dt * acc[k];
-        moments_split(X, h, rho0, dr, r, u, v);
-        feq_split(h, dr, r, u, v, eq);
-        const T zt = dt / t_i / T(3);
-        const T inv = T(1) / (T(1) + zt);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            if (k > 0 || h == 0) {
-                fs_out[row(k) * np + i] = (X[k] + zt * eq[k]) * inv;
-                Cacc[row(k) * np + i] = a2[k] + dt / T(6) * acc[k];
-            }
-        }
-    } else {
-        T fnew[5], dr, r, u, v;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            fnew[k] = fi[k] + a1[k] - dt / T(3) * acc[k];
-            if (k > 0 || h == 0) fn[row(k) * np + i] = fnew[k];
-        }
-        moments_split(fnew, h, rho0, dr, r, u, v);
-        if (STATS) {
-            double sv[4] = {0, 0, 0, 0};
-            if (h == 0) {
-                const double uo = double(mac[1 * np + i]), vo = double(mac[2 * np + i]);
-                const double un = double(u), vn = double(v);
-                const bool bad = !(isfinite(un) && isfinite(vn) && isfinite(double(r)));
-                sv[0] = (un - uo) * (un - uo) + (vn - vo) * (vn - vo);
-                sv[1] = un * un + vn * vn;
-                sv[2] = double(r) * double(area[i]);
-                sv[3] = bad ? 1.0 : 0.0;
-            }
-            block_sum<4, kFusedThreads>(sv, partial + 4 * blockIdx.x);
-        }
-        if (h == 0) {
-            mac[0 * np + i] = r;
-            mac[1 * np + i] = u;
-            mac[2 * np + i] = v;
-        }
-    }
-}
-
 // Shared-memory layout of the fused kernel (element offsets, every row 16-byte aligned):
 //   sf  [9][emax]   f^(J) of block, ring-1 and ring-2 cells
 //   sg  [16][gmax]  gradients (alpha = 1..8) of block and ring-1 cells
 //   sW  [8][gmax]   least-squares weights of block and ring-1 cells
-//   sQ  [8][gmax]   node positions of block and ring-1 cells
+//   sR  [8][gmax]   face midpoint minus centroid, per face slot, of block and ring-1 cells
 //   sT  [emax]      tau of staged cells
 //   adj [4 gmax] words, then one 8-byte mbarrier
+constexpr int kFusedThreads = kBlock;
+
 template <class T>
 struct FusedSmem {
     static __host__ __device__ size_t elems(int emax, int gmax) {
@@ -586,33 +458,31 @@ struct FusedSmem {
     }
 };
 
-// One IMEX stage for a block of kBlock cells, two threads per cell.  Staging: the block's own
+// One IMEX stage for a block of kBlock cells, one thread per cell.  Staging: the block's own
 // rows (contiguous in every SoA array) arrive by bulk copies on one mbarrier; halo rows are
-// gathered with cp.async; each thread's accumulators are loaded into registers; nothing is
-// waited for until everything has been issued.  Then: stage-1 relaxation f^n -> f^(1) in
-// shared memory, least-squares gradients of block + ring-1 cells, and per block cell the flux
-// of Eq. (advection) and the local stage algebra.  No gradient array goes through HBM.
+// gathered with cp.async; each thread's accumulators and face normals go straight into
+// registers; nothing is waited for until everything has been issued.  Then: stage-1
+// relaxation f^n -> f^(1) in shared memory, least-squares gradients of block + ring-1 cells,
+// and per block cell the flux of Eq. (advection) and the local stage algebra.  No gradient
+// array goes through HBM.  alpha = 0 has e = 0: no gradient and no flux.
 template <class T, int STAGE, bool STATS>
-__global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(kFusedThreads)
     k_fused_stage(const T *__restrict__ fin, T *__restrict__ fs_out, T *__restrict__ fn,
                   T *__restrict__ Bacc, T *__restrict__ Cacc, const T *__restrict__ tau,
-                  T *__restrict__ mac, double *__restrict__ partial, Geo<T> G, Halo H,
-                  const T *__restrict__ gq) {
+                  T *__restrict__ mac, double *__restrict__ partial, Geo<T> G, Halo H) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int E0 = H.emax, G0 = H.gmax;
     T *sf = reinterpret_cast<T *>(smem_raw);
     T *sg = sf + kQ * E0;
     T *sW = sg + 16 * G0;
-    T *sQ = sW + 8 * G0;
-    T *sT = sQ + 8 * G0;
+    T *sR = sW + 8 * G0;
+    T *sT = sR + 8 * G0;
     unsigned *sAdj = reinterpret_cast<unsigned *>(sT + E0);
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(sAdj + 4 * G0);
 
     const int b = blockIdx.x, t = threadIdx.x;
-    const int c0 = (t >> 5) * 16 + (t & 15);   // this thread's block cell
-    const int h = (t >> 4) & 1;                  // this thread's half of the velocities
     const int base = b * kBlock;
-    const int i = base + c0;
+    const int i = base + t;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[2 * b]];
     const T rho0 = T(P.rho0);
@@ -630,7 +500,7 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? 2 : 1)
         for (int a = 0; a < kQ; ++a) bulk_g2s(sf + a * E0, fin + a * np + base, row, bar);
         for (int k = 0; k < 8; ++k) {
             bulk_g2s(sW + k * G0, G.lsq + k * np + base, row, bar);
-            bulk_g2s(sQ + k * G0, gq + k * np + base, row, bar);
+            bulk_g2s(sR + k * G0, G.rown + k * np + base, row, bar);
         }
         bulk_g2s(sT, tau + base, row, bar);
         bulk_g2s(sAdj, adj_g, adj_bytes, bar);
@@ -644,22 +514,22 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? 2 : 1)
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 cp_async<sizeof(T)>(sW + k * G0 + e, G.lsq + k * np + gid);
-                cp_async<sizeof(T)>(sQ + k * G0 + e, gq + k * np + gid);
+                cp_async<sizeof(T)>(sR + k * G0 + e, G.rown + k * np + gid);
             }
         }
     }
-    // this thread's accumulators, straight into registers (used only by this thread)
-    T a1[5], a2[5];
+    // this thread's accumulators and face normals (n dl / A), straight into registers
+    T a1[kQ], a2[kQ], sn[8];
     {
         const T *p1 = STAGE == 1 ? fn : (STAGE == 2 ? Bacc : Cacc);
-        a1[0] = p1[i];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a1[1 + k] = p1[half_alpha(h, k) * np + i];
+        for (int a = 0; a < kQ; ++a) a1[a] = p1[a * np + i];
         if (STAGE == 2) {
-            a2[0] = Cacc[i];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) a2[1 + k] = Cacc[half_alpha(h, k) * np + i];
+            for (int a = 0; a < kQ; ++a) a2[a] = Cacc[a * np + i];
         }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sn[k] = G.sn[k * np + i];
     }
     cp_async_wait_all();
     {
@@ -691,15 +561,14 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? 2 : 1)
         __syncthreads();
     }
 
-    // 3. least-squares gradients (alpha of this half) of block and ring-1 cells (Step 2)
-    for (int c = c0; c < NG; c += kBlock) {
-        T fc[4], gx[4], gy[4];
+    // 3. least-squares gradients (alpha = 1..8) of block and ring-1 cells (Step 2)
+    for (int c = t; c < NG; c += kFusedThreads) {
+        T fc[kQ], gx[kQ], gy[kQ];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            fc[k] = sf[half_alpha(h, k) * E0 + c];
-            gx[k] = gy[k] = T(0);
+        for (int a = 0; a < kQ; ++a) {
+            fc[a] = sf[a * E0 + c];
+            gx[a] = gy[a] = T(0);
         }
-        const int nv = sAdj[3 * NG + c] == kAdjNone ? 3 : 4;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const unsigned w = sAdj[m * NG + c];
@@ -707,96 +576,75 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? 2 : 1)
             const T wx = sW[(2 * m) * G0 + c], wy = sW[(2 * m + 1) * G0 + c];
             if (w & kAdjBnd) {
                 const int bf = static_cast<int>(w & ~kAdjBnd);
-                T rx, ry, exv, eyv, dr, r, u, v, fb[kQ], fa[kQ];
-                face_geo_s(sQ + c, G0, m, nv, rx, ry, exv, eyv);
+                // outward face normal (n dl / A) for the far-field upwind choice
+                const int gid = c < kBlock ? base + c : H.halo[h0 + c - kBlock];
+                const T nx = G.sn[(2 * m) * np + gid], ny = G.sn[(2 * m + 1) * np + gid];
+                T dr, r, u, v, fb[kQ];
+                moments(fc, rho0, dr, r, u, v);
+                boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, nx, ny, fc, dr, r, u, v, rho0,
+                                fb);
 #pragma unroll
-                for (int a = 0; a < kQ; ++a) fa[a] = sf[a * E0 + c];
-                moments(fa, rho0, dr, r, u, v);
-                boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, eyv, -exv, fa, dr, r, u, v,
-                                rho0, fb);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const T d = (h ? fb[5 + k] : fb[1 + k]) - fc[k];
-                    gx[k] += wx * d;
-                    gy[k] += wy * d;
+                for (int a = 1; a < kQ; ++a) {
+                    const T d = fb[a] - fc[a];
+                    gx[a] += wx * d;
+                    gy[a] += wy * d;
                 }
             } else {
                 const int j = static_cast<int>(w & 0xFFFFu);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const T d = sf[half_alpha(h, k) * E0 + j] - fc[k];
-                    gx[k] += wx * d;
-                    gy[k] += wy * d;
+                for (int a = 1; a < kQ; ++a) {
+                    const T d = sf[a * E0 + j] - fc[a];
+                    gx[a] += wx * d;
+                    gy[a] += wy * d;
                 }
             }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int q = half_alpha(h, k) - 1;
-            sg[(2 * q) * G0 + c] = gx[k];
-            sg[(2 * q + 1) * G0 + c] = gy[k];
+        for (int a = 1; a < kQ; ++a) {
+            sg[(2 * a - 2) * G0 + c] = gx[a];
+            sg[(2 * a - 1) * G0 + c] = gy[a];
         }
     }
     __syncthreads();
 
-    // 4. flux of block cell c0 (Eq. (advection)) for this half's alpha, then the stage algebra
-    T fi[5], acc[5];
-    fi[0] = sf[c0];
-    acc[0] = T(0);
+    // 4. flux of block cell t (Eq. (advection)), then the stage algebra
+    T fi[kQ], acc[kQ];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        fi[1 + k] = sf[half_alpha(h, k) * E0 + c0];
-        acc[1 + k] = T(0);
+    for (int a = 0; a < kQ; ++a) {
+        fi[a] = sf[a * E0 + t];
+        acc[a] = T(0);
     }
-    const int nv = sAdj[3 * NG + c0] == kAdjNone ? 3 : 4;
-    T a2x = T(0);  // twice the area, shoelace on centroid-relative nodes
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        if (m < nv) {
-            const int m1 = (m + 1 == nv) ? 0 : m + 1;
-            a2x += sQ[(2 * m) * G0 + c0] * sQ[(2 * m1 + 1) * G0 + c0] -
-                   sQ[(2 * m1) * G0 + c0] * sQ[(2 * m + 1) * G0 + c0];
-        }
-    }
-    const T inv_a = a2x > T(0) ? T(2) / a2x : T(0);  // padding cells have no faces
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const unsigned w = sAdj[m * NG + c0];
+        const unsigned w = sAdj[m * NG + t];
         if (w == kAdjNone) continue;
-        T rox, roy, exv, eyv;
-        face_geo_s(sQ + c0, G0, m, nv, rox, roy, exv, eyv);
-        const T snx = eyv * inv_a, sny = -exv * inv_a;   // n dl / A
+        const T snx = sn[2 * m], sny = sn[2 * m + 1];
         if (w & kAdjBnd) {
             const int bf = static_cast<int>(w & ~kAdjBnd);
-            T dr, r, u, v, fb[kQ], fa[kQ];
+            T dr, r, u, v, fb[kQ];
+            moments(fi, rho0, dr, r, u, v);
+            boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, snx, sny, fi, dr, r, u, v, rho0, fb);
 #pragma unroll
-            for (int a = 0; a < kQ; ++a) fa[a] = sf[a * E0 + c0];
-            moments(fa, rho0, dr, r, u, v);
-            boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, snx, sny, fa, dr, r, u, v, rho0, fb);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                acc[1 + k] += (T(hex(h, k)) * snx + T(hey(h, k)) * sny) * (h ? fb[5 + k] : fb[1 + k]);
+            for (int a = 1; a < kQ; ++a) acc[a] += (T(ex_of(a)) * snx + T(ey_of(a)) * sny) * fb[a];
         } else {
             const int j = static_cast<int>(w & 0xFFFFu);
             const int mp = static_cast<int>((w >> 16) & 3u);
-            const int nvj = (w >> 18) & 1u ? 3 : 4;
-            T rnx, rny, ejx, ejy;
-            face_geo_s(sQ + j, G0, mp, nvj, rnx, rny, ejx, ejy);
+            const T rox = sR[(2 * m) * G0 + t], roy = sR[(2 * m + 1) * G0 + t];
+            const T rnx = sR[(2 * mp) * G0 + j], rny = sR[(2 * mp + 1) * G0 + j];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int a = half_alpha(h, k);
-                const T en = T(hex(h, k)) * snx + T(hey(h, k)) * sny;
+            for (int a = 1; a < kQ; ++a) {
+                const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
                 const bool own = en >= T(0);           // upwind side, branch free
-                const int src = own ? c0 : j;
+                const int src = own ? t : j;
                 const T rx = own ? rox : rnx, ry = own ? roy : rny;
                 const T fv = sf[a * E0 + src] + sg[(2 * a - 2) * G0 + src] * rx +
                              sg[(2 * a - 1) * G0 + src] * ry;
-                acc[1 + k] += en * fv;
+                acc[a] += en * fv;
             }
         }
     }
-    split_algebra<T, STAGE, STATS>(i, h, np, fi, acc, P, sT[c0], a1, a2, fs_out, fn, Bacc, Cacc,
-                                   mac, partial, G.area);
+    stage_algebra<T, STAGE, STATS, kFusedThreads>(i, np, fi, acc, P, sT[t], a1, 1, 0, a2, 1, 0,
+                                                  fs_out, fn, Bacc, Cacc, mac, partial, G.area);
 }
 
 // Sum per-block partials into per-instance totals (one block per instance).
@@ -1271,25 +1119,24 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
     }
     if (h->fused) {
         Halo H{h->d_halo_ptr, h->d_halo, h->d_r1, h->d_adj_ptr, h->d_adj, h->d_err, h->emax, h->gmax};
-        const T *gq = static_cast<const T *>(h->gq);
         const dim3 fg(h->nblk), fb(kFusedThreads);
         const size_t sm = h->fused_smem;
         launch(h, K_FUSED1, "fused_stage1", [&] {
-            k_fused_stage<T, 1, false><<<fg, fb, sm, s>>>(fn, s1, fn, B, C, tau, mac, nullptr, G, H, gq);
+            k_fused_stage<T, 1, false><<<fg, fb, sm, s>>>(fn, s1, fn, B, C, tau, mac, nullptr, G, H);
         });
         launch(h, K_FUSED2, "fused_stage2", [&] {
-            k_fused_stage<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, H, gq);
+            k_fused_stage<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, H);
         });
         if (stats) {
             launch(h, K_FUSED3, "fused_stage3", [&] {
-                k_fused_stage<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, H, gq);
+                k_fused_stage<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, H);
             });
             launch(h, K_REDUCE, "reduce", [&] {
                 k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->d_inst_blk0, h->d_inst_sums);
             });
         } else {
             launch(h, K_FUSED3, "fused_stage3", [&] {
-                k_fused_stage<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, H, gq);
+                k_fused_stage<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, H);
             });
         }
         return;
@@ -1512,7 +1359,6 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
     if ((rc = upload_as<T>(h, &h->bval, bval))) return rc;
     if ((rc = upload_as<T>(h, &h->bnrm, bnrm))) return rc;
     if ((rc = upload_as<T>(h, &h->blen, blen))) return rc;
-    if ((rc = upload_as<T>(h, &h->gq, gq))) return rc;
     if (h->fused && (rc = build_halos<T>(h, nbr, back, nface))) return rc;
     {
         std::vector<double> kt(k0), wt(w0);
