@@ -145,20 +145,25 @@ __device__ __forceinline__ void store9(T *__restrict__ f, size_t np, int i, cons
 // ------------------------------------------------------------------ stage 1 (local)
 // f^(1) = [f^n + (dt/tau)(1/4) f^eq(rho^n, u^n)] / (1 + (dt/tau)/4): Eq. (fnewstage), J = 1.
 template <class T>
+__device__ __forceinline__ void relax9(T *f, T rho0, T dt, T tau_i) {
+    T eq[kQ], dr, r, u, v;
+    moments(f, rho0, dr, r, u, v);
+    feq_dev(dr, r, u, v, eq);
+    const T zq = dt / tau_i * T(0.25);
+    const T inv = T(1) / (T(1) + zq);
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) f[a] = (f[a] + zq * eq[a]) * inv;
+}
+
+template <class T>
 __global__ void __launch_bounds__(kTile) k_stage1(const T *__restrict__ fn, T *__restrict__ fs,
                                                   const T *__restrict__ tau, Geo<T> G) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
-    const T rho0 = T(P.rho0);
-    T f[kQ], eq[kQ], dr, r, u, v;
+    T f[kQ];
     load9(fn, np, i, f);
-    moments(f, rho0, dr, r, u, v);
-    feq_dev(dr, r, u, v, eq);
-    const T zq = T(P.dt) / tau[i] * T(0.25);
-    const T inv = T(1) / (T(1) + zq);
-#pragma unroll
-    for (int a = 0; a < kQ; ++a) f[a] = (f[a] + zq * eq[a]) * inv;
+    relax9(f, T(P.rho0), T(P.dt), tau[i]);
     store9(fs, np, i, f);
 }
 
@@ -232,29 +237,42 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *out) {
 //   J = 3: f^{n+1} = f^(3) + C + dt/3 Gamma^a(3) (Eq. (imextwo)); macros; FP64 partial sums
 // The accumulator inputs are read through (pointer, row stride, column): a1 is f^n (J = 1),
 // B (J = 2) or C (J = 3); a2 is C (J = 2).  Outputs go to global memory at cell i.
-template <class T, int STAGE, bool STATS, int NT>
+//   FN_FROM_F1: f^n is not read but recovered from f^(1) = [f^n + z/4 f^eq] / (1 + z/4) as
+//   f^n = f^(1) - dt/4 Gamma^c(1) (same moments, so f^eq(1) follows from f^(1));
+//   frel (if given): at J = 3, laminar instances also store f^(1) of the next step.
+template <class T, int STAGE, bool STATS, int NT, bool FN_FROM_F1 = false>
 __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, const T *acc,
                                               const InstParam &P, T t_i, const T *a1, size_t ld1,
                                               int c1, const T *a2, size_t ld2, int c2,
                                               T *__restrict__ fs_out, T *__restrict__ fn,
                                               T *__restrict__ Bacc, T *__restrict__ Cacc,
                                               T *__restrict__ mac, double *__restrict__ partial,
-                                              const T *__restrict__ area) {
+                                              const T *__restrict__ area,
+                                              T *__restrict__ frel = nullptr) {
     const T rho0 = T(P.rho0);
     const T dt = T(P.dt);
     if (STAGE == 1) {
         // fi = f^(1); f^n, Gamma^c(1) from f^n and f^(1)
         T f0[kQ], eq[kQ], X[kQ], dr, r, u, v;
-#pragma unroll
-        for (int a = 0; a < kQ; ++a) f0[a] = a1[a * ld1 + c1];
-        moments(f0, rho0, dr, r, u, v);
-        feq_dev(dr, r, u, v, eq);
         T gc1[kQ];
+        if (FN_FROM_F1) {
+            moments(fi, rho0, dr, r, u, v);
+            feq_dev(dr, r, u, v, eq);
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) {
-            gc1[a] = (eq[a] - fi[a]) / t_i;
-            X[a] = f0[a] - T(0.5) * dt * acc[a];
+            for (int a = 0; a < kQ; ++a) {
+                gc1[a] = (eq[a] - fi[a]) / t_i;
+                f0[a] = fi[a] - T(0.25) * dt * gc1[a];
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) f0[a] = a1[a * ld1 + c1];
+            moments(f0, rho0, dr, r, u, v);
+            feq_dev(dr, r, u, v, eq);
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) gc1[a] = (eq[a] - fi[a]) / t_i;
         }
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) X[a] = f0[a] - T(0.5) * dt * acc[a];
         moments(X, rho0, dr, r, u, v);
         feq_dev(dr, r, u, v, eq);
         const T zq = dt / t_i * T(0.25);
@@ -299,6 +317,10 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
         mac[0 * np + i] = r;
         mac[1 * np + i] = u;
         mac[2 * np + i] = v;
+        if (frel != nullptr && !P.sst) {  // laminar: tau is constant, relax for the next step
+            relax9(fnew, rho0, dt, t_i);
+            store9(frel, np, i, fnew);
+        }
     }
 }
 
@@ -444,14 +466,13 @@ __device__ __forceinline__ void face_geo_s(const T *q, int ld, int m, int nv, T 
 //   sg  [16][gmax]  gradients (alpha = 1..8) of block and ring-1 cells
 //   sW  [8][gmax]   least-squares weights of block and ring-1 cells
 //   sR  [8][gmax]   face midpoint minus centroid, per face slot, of block and ring-1 cells
-//   sT  [emax]      tau of staged cells
 //   adj [4 gmax] words, then one 8-byte mbarrier
 constexpr int kFusedThreads = kBlock;
 
 template <class T>
 struct FusedSmem {
     static __host__ __device__ size_t elems(int emax, int gmax) {
-        return size_t(kQ) * emax + 16u * gmax + 16u * gmax + emax;
+        return size_t(kQ) * emax + 16u * gmax + 16u * gmax;
     }
     static __host__ __device__ size_t bytes(int emax, int gmax) {
         return elems(emax, gmax) * sizeof(T) + 4u * gmax * sizeof(unsigned) + 16;
@@ -460,24 +481,26 @@ struct FusedSmem {
 
 // One IMEX stage for a block of kBlock cells, one thread per cell.  Staging: the block's own
 // rows (contiguous in every SoA array) arrive by bulk copies on one mbarrier; halo rows are
-// gathered with cp.async; each thread's accumulators and face normals go straight into
-// registers; nothing is waited for until everything has been issued.  Then: stage-1
-// relaxation f^n -> f^(1) in shared memory, least-squares gradients of block + ring-1 cells,
-// and per block cell the flux of Eq. (advection) and the local stage algebra.  No gradient
-// array goes through HBM.  alpha = 0 has e = 0: no gradient and no flux.
+// gathered with cp.async; each thread's accumulators, tau and face normals go straight into
+// registers; nothing is waited for until everything has been issued.  Then: least-squares
+// gradients of block + ring-1 cells, and per block cell the flux of Eq. (advection) and the
+// local stage algebra.  No gradient array goes through HBM.  alpha = 0 has e = 0: no gradient
+// and no flux.  Stage 1 stages f^(1), which the previous step (laminar instances) or the SST
+// update (turbulent instances, with the new tau) has already relaxed from f^n; stage 3 writes
+// f^(1) of the next step for laminar instances into frel.
 template <class T, int STAGE, bool STATS>
 __global__ void __launch_bounds__(kFusedThreads)
     k_fused_stage(const T *__restrict__ fin, T *__restrict__ fs_out, T *__restrict__ fn,
                   T *__restrict__ Bacc, T *__restrict__ Cacc, const T *__restrict__ tau,
-                  T *__restrict__ mac, double *__restrict__ partial, Geo<T> G, Halo H) {
+                  T *__restrict__ mac, double *__restrict__ partial, Geo<T> G, Halo H,
+                  T *__restrict__ frel) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int E0 = H.emax, G0 = H.gmax;
     T *sf = reinterpret_cast<T *>(smem_raw);
     T *sg = sf + kQ * E0;
     T *sW = sg + 16 * G0;
     T *sR = sW + 8 * G0;
-    T *sT = sR + 8 * G0;
-    unsigned *sAdj = reinterpret_cast<unsigned *>(sT + E0);
+    unsigned *sAdj = reinterpret_cast<unsigned *>(sR + 8 * G0);
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(sAdj + 4 * G0);
 
     const int b = blockIdx.x, t = threadIdx.x;
@@ -496,20 +519,18 @@ __global__ void __launch_bounds__(kFusedThreads)
     if (t == 0) {
         constexpr unsigned row = kBlock * sizeof(T);
         const unsigned adj_bytes = 4u * NG * sizeof(unsigned);
-        mbar_expect_tx(bar, row * (kQ + 8 + 8 + 1) + adj_bytes);
+        mbar_expect_tx(bar, row * (kQ + 8 + 8) + adj_bytes);
         for (int a = 0; a < kQ; ++a) bulk_g2s(sf + a * E0, fin + a * np + base, row, bar);
         for (int k = 0; k < 8; ++k) {
             bulk_g2s(sW + k * G0, G.lsq + k * np + base, row, bar);
             bulk_g2s(sR + k * G0, G.rown + k * np + base, row, bar);
         }
-        bulk_g2s(sT, tau + base, row, bar);
         bulk_g2s(sAdj, adj_g, adj_bytes, bar);
     }
     for (int e = kBlock + t; e < E; e += kFusedThreads) {  // halo rows
         const int gid = H.halo[h0 + e - kBlock];
 #pragma unroll
         for (int a = 0; a < kQ; ++a) cp_async<sizeof(T)>(sf + a * E0 + e, fin + a * np + gid);
-        if (STAGE == 1) cp_async<sizeof(T)>(sT + e, tau + gid);
         if (e < NG) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -518,12 +539,15 @@ __global__ void __launch_bounds__(kFusedThreads)
             }
         }
     }
-    // this thread's accumulators and face normals (n dl / A), straight into registers
+    // this thread's accumulators, tau and face normals (n dl / A), straight into registers
     T a1[kQ], a2[kQ], sn[8];
+    const T tau_i = tau[i];
     {
-        const T *p1 = STAGE == 1 ? fn : (STAGE == 2 ? Bacc : Cacc);
+        if (STAGE != 1) {
+            const T *p1 = STAGE == 2 ? Bacc : Cacc;
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) a1[a] = p1[a * np + i];
+            for (int a = 0; a < kQ; ++a) a1[a] = p1[a * np + i];
+        }
         if (STAGE == 2) {
 #pragma unroll
             for (int a = 0; a < kQ; ++a) a2[a] = Cacc[a * np + i];
@@ -545,23 +569,7 @@ __global__ void __launch_bounds__(kFusedThreads)
         }
     }
 
-    // 2. stage 1 only: f^(1) = [f^n + z/4 f^eq(f^n)] / (1 + z/4) (Eq. (fnewstage), J = 1)
-    if (STAGE == 1) {
-        for (int e = t; e < E; e += kFusedThreads) {
-            T v[kQ], eq[kQ], dr, r, u, w;
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) v[a] = sf[a * E0 + e];
-            moments(v, rho0, dr, r, u, w);
-            feq_dev(dr, r, u, w, eq);
-            const T zq = T(P.dt) / sT[e] * T(0.25);
-            const T inv = T(1) / (T(1) + zq);
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) sf[a * E0 + e] = (v[a] + zq * eq[a]) * inv;
-        }
-        __syncthreads();
-    }
-
-    // 3. least-squares gradients (alpha = 1..8) of block and ring-1 cells (Step 2)
+    // 2. least-squares gradients (alpha = 1..8) of block and ring-1 cells (Step 2)
     for (int c = t; c < NG; c += kFusedThreads) {
         T fc[kQ], gx[kQ], gy[kQ];
 #pragma unroll
@@ -607,7 +615,7 @@ __global__ void __launch_bounds__(kFusedThreads)
     }
     __syncthreads();
 
-    // 4. flux of block cell t (Eq. (advection)), then the stage algebra
+    // 3. flux of block cell t (Eq. (advection)), then the stage algebra
     T fi[kQ], acc[kQ];
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
@@ -643,8 +651,9 @@ __global__ void __launch_bounds__(kFusedThreads)
             }
         }
     }
-    stage_algebra<T, STAGE, STATS, kFusedThreads>(i, np, fi, acc, P, sT[t], a1, 1, 0, a2, 1, 0,
-                                                  fs_out, fn, Bacc, Cacc, mac, partial, G.area);
+    stage_algebra<T, STAGE, STATS, kFusedThreads, true>(i, np, fi, acc, P, tau_i, a1, 1, 0, a2, 1,
+                                                        0, fs_out, fn, Bacc, Cacc, mac, partial,
+                                                        G.area, frel);
 }
 
 // Sum per-block partials into per-instance totals (one block per instance).
@@ -753,7 +762,8 @@ __global__ void __launch_bounds__(kTile)
     k_sst_update(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
                  const T *__restrict__ nut, const T *__restrict__ grads,
                  const T *__restrict__ f1a, T *__restrict__ k_out, T *__restrict__ w_out,
-                 T *__restrict__ nut_out, T *__restrict__ tau, Geo<T> G) {
+                 T *__restrict__ nut_out, T *__restrict__ tau, Geo<T> G,
+                 const T *__restrict__ fn, T *__restrict__ frel) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -845,7 +855,14 @@ __global__ void __launch_bounds__(kTile)
     k_out[i] = kn;
     w_out[i] = wn;
     nut_out[i] = ntn;
-    tau[i] = (nu + ntn) / T(kCs2);
+    const T tnew = (nu + ntn) / T(kCs2);
+    tau[i] = tnew;
+    if (frel != nullptr) {  // fused path: stage 1's f^(1) with the new relaxation time
+        T f[kQ];
+        load9(fn, np, i, f);
+        relax9(f, T(P.rho0), dt, tnew);
+        store9(frel, np, i, f);
+    }
 }
 
 // ------------------------------------------------------------------ state I/O kernels
@@ -998,6 +1015,7 @@ struct fvlbm_handle {
     void *area = nullptr, *wdist = nullptr, *bval = nullptr, *bnrm = nullptr, *blen = nullptr;
     void *fn = nullptr, *s0 = nullptr, *s1 = nullptr, *bacc = nullptr, *cacc = nullptr;
     void *grad = nullptr, *tau = nullptr, *mac = nullptr;
+    void *frel = nullptr;   // fused path: f^(1) of the coming step (relaxed f^n)
     void *kk[2] = {nullptr, nullptr}, *ww[2] = {nullptr, nullptr}, *nut[2] = {nullptr, nullptr};
     void *sgrad = nullptr, *f1 = nullptr;
     int turb = 0;  // which of the k/omega/nu_t ping-pong buffers is current
@@ -1113,30 +1131,32 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         T *sg = static_cast<T *>(h->sgrad), *f1 = static_cast<T *>(h->f1);
         launch(h, K_SST_GRAD, "sst_grad", [&] { k_sst_grad<T><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G); });
         launch(h, K_SST_UPDATE, "sst_update", [&] {
-            k_sst_update<T><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G);
+            k_sst_update<T><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn,
+                                                   h->fused ? static_cast<T *>(h->frel) : nullptr);
         });
         h->turb = n;
     }
     if (h->fused) {
         Halo H{h->d_halo_ptr, h->d_halo, h->d_r1, h->d_adj_ptr, h->d_adj, h->d_err, h->emax, h->gmax};
         const dim3 fg(h->nblk), fb(kFusedThreads);
+        T *fr = static_cast<T *>(h->frel);
         const size_t sm = h->fused_smem;
         launch(h, K_FUSED1, "fused_stage1", [&] {
-            k_fused_stage<T, 1, false><<<fg, fb, sm, s>>>(fn, s1, fn, B, C, tau, mac, nullptr, G, H);
+            k_fused_stage<T, 1, false><<<fg, fb, sm, s>>>(fr, s1, fn, B, C, tau, mac, nullptr, G, H, fr);
         });
         launch(h, K_FUSED2, "fused_stage2", [&] {
-            k_fused_stage<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, H);
+            k_fused_stage<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, H, fr);
         });
         if (stats) {
             launch(h, K_FUSED3, "fused_stage3", [&] {
-                k_fused_stage<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, H);
+                k_fused_stage<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, H, fr);
             });
             launch(h, K_REDUCE, "reduce", [&] {
                 k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->d_inst_blk0, h->d_inst_sums);
             });
         } else {
             launch(h, K_FUSED3, "fused_stage3", [&] {
-                k_fused_stage<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, H);
+                k_fused_stage<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, H, fr);
             });
         }
         return;
@@ -1277,12 +1297,21 @@ int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<
     return FVLBM_OK;
 }
 
+// f^(1) of the coming step from the current f^n and tau, for every cell (after create and
+// set_f); the fused stage-1 kernel reads it.
+template <class T>
+void relax_all(fvlbm_handle *h) {
+    k_stage1<T><<<h->ntiles, kTile, 0, h->stream>>>(static_cast<const T *>(h->fn),
+                                                   static_cast<T *>(h->frel),
+                                                   static_cast<const T *>(h->tau), geo_of<T>(h));
+}
+
 template <class T>
 int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
     const size_t np = h->np;
     int rc;
     const size_t ts = sizeof(T);
-    for (void **p : {&h->fn, &h->s0, &h->s1, &h->bacc, &h->cacc})
+    for (void **p : {&h->fn, &h->s0, &h->s1, &h->bacc, &h->cacc, &h->frel})
         if ((rc = dalloc(h, p, kQ * np * ts))) return rc;
     if ((rc = dalloc(h, &h->grad, 2 * kQ * np * ts))) return rc;
     if ((rc = dalloc(h, &h->tau, np * ts))) return rc;
@@ -1382,6 +1411,8 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
     Geo<T> G = geo_of<T>(h);
     k_init_state<T><<<h->ntiles, kTile, 0, h->stream>>>(static_cast<T *>(h->fn), static_cast<T *>(h->mac),
                                                        d_init, d_init + np, d_init + 2 * np, G);
+    CK(cudaGetLastError());
+    relax_all<T>(h);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     return FVLBM_OK;
@@ -1617,12 +1648,15 @@ int fvlbm_set_f(fvlbm_handle *h, int instance, const double *f) {
     CK(cudaMemcpyAsync(h->d_io, f, sizeof(double) * kQ * I.nc, cudaMemcpyHostToDevice, h->stream));
     const int po = perm_offset(h, instance);
     const int nb = (I.nc + 255) / 256;
-    if (h->precision == FVLBM_FP64)
+    if (h->precision == FVLBM_FP64) {
         k_scatter_f<double><<<nb, 256, 0, h->stream>>>(static_cast<double *>(h->fn), static_cast<double *>(h->mac),
                                                        h->d_perm + po, I.cell_off, I.nc, I.rho0, h->np, h->d_io);
-    else
+        relax_all<double>(h);
+    } else {
         k_scatter_f<float><<<nb, 256, 0, h->stream>>>(static_cast<float *>(h->fn), static_cast<float *>(h->mac),
                                                       h->d_perm + po, I.cell_off, I.nc, I.rho0, h->np, h->d_io);
+        relax_all<float>(h);
+    }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     return FVLBM_OK;
