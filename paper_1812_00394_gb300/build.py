@@ -28,8 +28,22 @@ def _nvcc() -> str:
     return cand
 
 
+def _stamp() -> str:
+    return os.path.join(BUILD, "config.txt")
+
+
+def _config() -> str:
+    return f"FVLBM_FUSED_BLOCK={os.environ.get('FVLBM_FUSED_BLOCK', '')}"
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
+        return True
+    try:
+        with open(_stamp()) as fh:
+            if fh.read() != _config():
+                return True
+    except OSError:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(INCLUDE, "fvlbm.h"),
@@ -44,6 +58,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     inc = ["-I", INCLUDE, "-I", CSRC]
+    fb = os.environ.get("FVLBM_FUSED_BLOCK")   # optional build-time tuning of the fused block
+    if fb:
+        inc += [f"-DFVLBM_FUSED_BLOCK={int(fb)}"]
     host_o = os.path.join(BUILD, "fvlbm_host.o")
     dev_o = os.path.join(BUILD, "fvlbm_kernels.o")
     na_o = os.path.join(BUILD, "fvlbm_noalloc.o")
@@ -69,6 +86,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     subprocess.check_call([nvcc, ARCH, "-shared", "-Xcompiler", "-fopenmp", host_o, dev_o, na_o,
                            "-o", tmp])
     os.replace(tmp, LIB)
+    with open(_stamp(), "w") as fh:
+        fh.write(_config())
     return LIB
 
 

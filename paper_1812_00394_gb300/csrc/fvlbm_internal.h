@@ -12,8 +12,13 @@ namespace fvlbm {
 
 constexpr int kQ = 9;          // D2Q9
 constexpr int kTile = 128;     // cells per thread block of the per-cell kernels
-constexpr int kBlock = 256;    // cells per block of the fused stage kernel (= 2 tiles);
-                               // instances are padded to a multiple of kBlock
+#ifndef FVLBM_FUSED_BLOCK
+#define FVLBM_FUSED_BLOCK 256
+#endif
+constexpr int kBlock = FVLBM_FUSED_BLOCK;  // cells per block of the fused stage kernel (a
+                                           // multiple of kTile); instances are padded to a
+                                           // multiple of kBlock
+static_assert(kBlock % kTile == 0, "fused block must be a whole number of tiles");
 constexpr int kNone = INT32_MIN;  // empty face slot (triangles have 3 faces, padding cells 0)
 
 // One instance after preprocessing, in the library's internal cell order (Hilbert order of the

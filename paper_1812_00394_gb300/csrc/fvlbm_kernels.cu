@@ -89,8 +89,9 @@ __device__ __forceinline__ void moments(const T *d, T rho0, T &drho, T &rho, T &
     }
     drho = s;
     rho = rho0 + s;
-    u = jx / rho;
-    v = jy / rho;
+    const T ir = T(1) / rho;
+    u = jx * ir;
+    v = jy * ir;
 }
 
 // Equilibrium deviation f^eq(rho, u) - w rho0 = w [drho + rho (3 e.u + 4.5 (e.u)^2 - 1.5 u.u)].
@@ -251,6 +252,8 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
                                               T *__restrict__ frel = nullptr) {
     const T rho0 = T(P.rho0);
     const T dt = T(P.dt);
+    const T itau = T(1) / t_i;          // one division per cell, products below
+    const T dt3 = dt * T(1.0 / 3.0), dt6 = dt * T(1.0 / 6.0);
     if (STAGE == 1) {
         // fi = f^(1); f^n, Gamma^c(1) from f^n and f^(1)
         T f0[kQ], eq[kQ], X[kQ], dr, r, u, v;
@@ -260,7 +263,7 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
             feq_dev(dr, r, u, v, eq);
 #pragma unroll
             for (int a = 0; a < kQ; ++a) {
-                gc1[a] = (eq[a] - fi[a]) / t_i;
+                gc1[a] = (eq[a] - fi[a]) * itau;
                 f0[a] = fi[a] - T(0.25) * dt * gc1[a];
             }
         } else {
@@ -269,21 +272,21 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
             moments(f0, rho0, dr, r, u, v);
             feq_dev(dr, r, u, v, eq);
 #pragma unroll
-            for (int a = 0; a < kQ; ++a) gc1[a] = (eq[a] - fi[a]) / t_i;
+            for (int a = 0; a < kQ; ++a) gc1[a] = (eq[a] - fi[a]) * itau;
         }
 #pragma unroll
         for (int a = 0; a < kQ; ++a) X[a] = f0[a] - T(0.5) * dt * acc[a];
         moments(X, rho0, dr, r, u, v);
         feq_dev(dr, r, u, v, eq);
-        const T zq = dt / t_i * T(0.25);
+        const T zq = dt * itau * T(0.25);
         const T inv = T(1) / (T(1) + zq);
         T f2[kQ];
 #pragma unroll
         for (int a = 0; a < kQ; ++a) {
             f2[a] = (X[a] + zq * eq[a]) * inv;
-            const T gc2 = (eq[a] - f2[a]) / t_i;
-            Bacc[a * np + i] = X[a] + dt / T(3) * (gc1[a] + gc2);
-            Cacc[a * np + i] = dt / T(6) * acc[a];
+            const T gc2 = (eq[a] - f2[a]) * itau;
+            Bacc[a * np + i] = X[a] + dt3 * (gc1[a] + gc2);
+            Cacc[a * np + i] = dt6 * acc[a];
         }
         store9(fs_out, np, i, f2);
     } else if (STAGE == 2) {
@@ -292,18 +295,18 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
         for (int a = 0; a < kQ; ++a) X[a] = a1[a * ld1 + c1] - T(0.5) * dt * acc[a];
         moments(X, rho0, dr, r, u, v);
         feq_dev(dr, r, u, v, eq);
-        const T zt = dt / t_i / T(3);
+        const T zt = dt3 * itau;
         const T inv = T(1) / (T(1) + zt);
 #pragma unroll
         for (int a = 0; a < kQ; ++a) {
             f3[a] = (X[a] + zt * eq[a]) * inv;
-            Cacc[a * np + i] = a2[a * ld2 + c2] + dt / T(6) * acc[a];
+            Cacc[a * np + i] = a2[a * ld2 + c2] + dt6 * acc[a];
         }
         store9(fs_out, np, i, f3);
     } else {
         T fnew[kQ], dr, r, u, v;
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) fnew[a] = fi[a] + a1[a * ld1 + c1] - dt / T(3) * acc[a];
+        for (int a = 0; a < kQ; ++a) fnew[a] = fi[a] + a1[a * ld1 + c1] - dt3 * acc[a];
         store9(fn, np, i, fnew);
         moments(fnew, rho0, dr, r, u, v);
         if (STATS) {
@@ -489,7 +492,7 @@ struct FusedSmem {
 // update (turbulent instances, with the new tau) has already relaxed from f^n; stage 3 writes
 // f^(1) of the next step for laminar instances into frel.
 template <class T, int STAGE, bool STATS>
-__global__ void __launch_bounds__(kFusedThreads)
+__global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedThreads) : 1)
     k_fused_stage(const T *__restrict__ fin, T *__restrict__ fs_out, T *__restrict__ fn,
                   T *__restrict__ Bacc, T *__restrict__ Cacc, const T *__restrict__ tau,
                   T *__restrict__ mac, double *__restrict__ partial, Geo<T> G, Halo H,
@@ -507,7 +510,7 @@ __global__ void __launch_bounds__(kFusedThreads)
     const int base = b * kBlock;
     const int i = base + t;
     const size_t np = G.np;
-    const InstParam P = G.ip[G.tile_inst[2 * b]];
+    const InstParam P = G.ip[G.tile_inst[b * (kBlock / kTile)]];
     const T rho0 = T(P.rho0);
     const int h0 = H.halo_ptr[b], nh = H.halo_ptr[b + 1] - h0, nr1 = H.r1[b];
     const int E = kBlock + nh, NG = kBlock + nr1;
@@ -1503,7 +1506,7 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     if ((rc = upload_raw(h.get(), &h->d_inst_tile0, inst_tile0))) { free_all(h.get()); return rc; }
     {
         std::vector<int> inst_blk0(inst_tile0.size());
-        for (size_t q = 0; q < inst_tile0.size(); ++q) inst_blk0[q] = inst_tile0[q] / 2;
+        for (size_t q = 0; q < inst_tile0.size(); ++q) inst_blk0[q] = inst_tile0[q] / (kBlock / kTile);
         if ((rc = upload_raw(h.get(), &h->d_inst_blk0, inst_blk0))) { free_all(h.get()); return rc; }
     }
     if ((rc = upload_raw(h.get(), &h->d_ip, ip))) { free_all(h.get()); return rc; }
