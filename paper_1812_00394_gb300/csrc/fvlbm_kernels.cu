@@ -468,14 +468,13 @@ __device__ __forceinline__ void face_geo_s(const T *q, int ld, int m, int nv, T 
 //   sf  [9][emax]   f^(J) of block, ring-1 and ring-2 cells
 //   sg  [16][gmax]  gradients (alpha = 1..8) of block and ring-1 cells
 //   sW  [8][gmax]   least-squares weights of block and ring-1 cells
-//   sR  [8][gmax]   face midpoint minus centroid, per face slot, of block and ring-1 cells
 //   adj [4 gmax] words, then one 8-byte mbarrier
 constexpr int kFusedThreads = kBlock;
 
 template <class T>
 struct FusedSmem {
     static __host__ __device__ size_t elems(int emax, int gmax) {
-        return size_t(kQ) * emax + 16u * gmax + 16u * gmax;
+        return size_t(kQ) * emax + 16u * gmax + 8u * gmax;
     }
     static __host__ __device__ size_t bytes(int emax, int gmax) {
         return elems(emax, gmax) * sizeof(T) + 4u * gmax * sizeof(unsigned) + 16;
@@ -502,8 +501,7 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
     T *sf = reinterpret_cast<T *>(smem_raw);
     T *sg = sf + kQ * E0;
     T *sW = sg + 16 * G0;
-    T *sR = sW + 8 * G0;
-    unsigned *sAdj = reinterpret_cast<unsigned *>(sR + 8 * G0);
+    unsigned *sAdj = reinterpret_cast<unsigned *>(sW + 8 * G0);
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(sAdj + 4 * G0);
 
     const int b = blockIdx.x, t = threadIdx.x;
@@ -522,12 +520,9 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
     if (t == 0) {
         constexpr unsigned row = kBlock * sizeof(T);
         const unsigned adj_bytes = 4u * NG * sizeof(unsigned);
-        mbar_expect_tx(bar, row * (kQ + 8 + 8) + adj_bytes);
+        mbar_expect_tx(bar, row * (kQ + 8) + adj_bytes);
         for (int a = 0; a < kQ; ++a) bulk_g2s(sf + a * E0, fin + a * np + base, row, bar);
-        for (int k = 0; k < 8; ++k) {
-            bulk_g2s(sW + k * G0, G.lsq + k * np + base, row, bar);
-            bulk_g2s(sR + k * G0, G.rown + k * np + base, row, bar);
-        }
+        for (int k = 0; k < 8; ++k) bulk_g2s(sW + k * G0, G.lsq + k * np + base, row, bar);
         bulk_g2s(sAdj, adj_g, adj_bytes, bar);
     }
     for (int e = kBlock + t; e < E; e += kFusedThreads) {  // halo rows
@@ -536,10 +531,7 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
         for (int a = 0; a < kQ; ++a) cp_async<sizeof(T)>(sf + a * E0 + e, fin + a * np + gid);
         if (e < NG) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                cp_async<sizeof(T)>(sW + k * G0 + e, G.lsq + k * np + gid);
-                cp_async<sizeof(T)>(sR + k * G0 + e, G.rown + k * np + gid);
-            }
+            for (int k = 0; k < 8; ++k) cp_async<sizeof(T)>(sW + k * G0 + e, G.lsq + k * np + gid);
         }
     }
     // this thread's accumulators, tau and face normals (n dl / A), straight into registers
@@ -639,9 +631,9 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
             for (int a = 1; a < kQ; ++a) acc[a] += (T(ex_of(a)) * snx + T(ey_of(a)) * sny) * fb[a];
         } else {
             const int j = static_cast<int>(w & 0xFFFFu);
-            const int mp = static_cast<int>((w >> 16) & 3u);
-            const T rox = sR[(2 * m) * G0 + t], roy = sR[(2 * m + 1) * G0 + t];
-            const T rnx = sR[(2 * mp) * G0 + j], rny = sR[(2 * mp + 1) * G0 + j];
+            // face offsets from this cell's and from the neighbour's centroid (precomputed)
+            const T rox = G.rown[(2 * m) * np + i], roy = G.rown[(2 * m + 1) * np + i];
+            const T rnx = G.rnbr[(2 * m) * np + i], rny = G.rnbr[(2 * m + 1) * np + i];
 #pragma unroll
             for (int a = 1; a < kQ; ++a) {
                 const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
