@@ -663,60 +663,49 @@ __global__ void k_reduce_instances(const double *__restrict__ partial,
 }
 
 // ------------------------------------------------------------------ SST (Step 1)
-// Gradients of u, v, k, omega (least squares with boundary values), the limited k / omega
-// gradients used for upwind face values, and the blending function f1.
+// ---- per-cell SST arithmetic, shared by the two-pass and the fused kernels
+// Boundary values of (u, v, k, omega) on boundary face b of a cell with values (ui, vi, ki, wi)
+// and wall distance di (Menter 1994 boundary conditions; wall omega = 60 nu / (beta1 d^2)).
 template <class T>
-__global__ void __launch_bounds__(kTile)
-    k_sst_grad(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
-               T *__restrict__ grads, T *__restrict__ f1out, Geo<T> G) {
-    const int i = blockIdx.x * kTile + threadIdx.x;
-    const size_t np = G.np;
-    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
-    if (!P.sst) return;  // laminar instance: tau stays nu / cs^2
-    const T nu = T(P.nu);
-    const T ui = mac[np + i], vi = mac[2 * np + i], ki = kk[i], wi = ww[i];
-    const T di = G.wdist[i];
-    T g[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // du/dx du/dy dv/dx dv/dy dk/dx dk/dy dw/dx dw/dy
-    T kq[4], wq[4];                       // face-neighbour (or boundary) values of k, omega
+__device__ __forceinline__ void sst_bvals(const Geo<T> &G, int b, T nu, T ui, T vi, T ki, T wi,
+                                          T di, T &ub, T &vb, T &kb, T &wb) {
+    const int t = G.btype[b];
+    if (t == FVLBM_BC_WALL) {
+        ub = G.bval[1 * G.nbt + b]; vb = G.bval[2 * G.nbt + b]; kb = T(0);
+        wb = T(60) * nu / (T(kB1) * di * di);
+    } else if (t == FVLBM_BC_OUTLET) {
+        ub = ui; vb = vi; kb = ki; wb = wi;
+    } else {
+        ub = G.bval[1 * G.nbt + b]; vb = G.bval[2 * G.nbt + b];
+        kb = G.bval[3 * G.nbt + b]; wb = G.bval[4 * G.nbt + b];
+    }
+}
+
+// Gradients of u, v, k, omega (least squares; face data q[m] = neighbour or boundary values,
+// has[m] = face present), Barth-Jespersen limited k / omega gradients for the upwind face
+// values, and the blending function f1 = tanh(arg1^4) (Sec. 2, kinematic form).
+template <class T>
+__device__ __forceinline__ void sst_cell_grad(T ki, T wi, T di, T nu, const bool *has,
+                                              const T (*q)[4], const T *W, const T *R,
+                                              const T *uvkw_i, T *g, T *lg, T &f1) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) g[c] = T(0);
+    T kq[4], wq[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         kq[m] = ki;
         wq[m] = wi;
-        const int nb = G.nbr[m * np + i];
-        if (nb == kNone) continue;
-        T du, dv, dk, dw;
-        if (nb >= 0) {
-            du = mac[np + nb] - ui;
-            dv = mac[2 * np + nb] - vi;
-            dk = kk[nb] - ki;
-            dw = ww[nb] - wi;
-        } else {
-            const int b = -nb - 1;
-            const int t = G.btype[b];
-            T ub, vb, kb, wb;
-            if (t == FVLBM_BC_WALL) {
-                ub = G.bval[1 * G.nbt + b]; vb = G.bval[2 * G.nbt + b]; kb = T(0);
-                wb = T(60) * nu / (T(kB1) * di * di);
-            } else if (t == FVLBM_BC_OUTLET) {
-                ub = ui; vb = vi; kb = ki; wb = wi;
-            } else {
-                ub = G.bval[1 * G.nbt + b]; vb = G.bval[2 * G.nbt + b];
-                kb = G.bval[3 * G.nbt + b]; wb = G.bval[4 * G.nbt + b];
-            }
-            du = ub - ui; dv = vb - vi; dk = kb - ki; dw = wb - wi;
-        }
+        if (!has[m]) continue;
+        const T du = q[m][0] - uvkw_i[0], dv = q[m][1] - uvkw_i[1];
+        const T dk = q[m][2] - ki, dw = q[m][3] - wi;
         kq[m] = ki + dk;
         wq[m] = wi + dw;
-        const T wx = G.lsq[(2 * m) * np + i], wy = G.lsq[(2 * m + 1) * np + i];
+        const T wx = W[2 * m], wy = W[2 * m + 1];
         g[0] += wx * du; g[1] += wy * du;
         g[2] += wx * dv; g[3] += wy * dv;
         g[4] += wx * dk; g[5] += wy * dk;
         g[6] += wx * dw; g[7] += wy * dw;
     }
-#pragma unroll
-    for (int c = 0; c < 8; ++c) grads[c * np + i] = g[c];
-    // Barth-Jespersen limiters of the k and omega reconstructions (second-order upwind on
-    // unstructured cells): face values stay within the local min / max
     T klo = ki, khi = ki, wlo = wi, whi = wi;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -726,19 +715,18 @@ __global__ void __launch_bounds__(kTile)
     T pk = T(1), pw = T(1);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        if (G.nbr[m * np + i] == kNone) continue;
-        const T rx = G.rown[(2 * m) * np + i], ry = G.rown[(2 * m + 1) * np + i];
+        if (!has[m]) continue;
+        const T rx = R[2 * m], ry = R[2 * m + 1];
         const T dkf = g[4] * rx + g[5] * ry, dwf = g[6] * rx + g[7] * ry;
         if (dkf > T(0)) pk = fmin(pk, (khi - ki) / dkf);
         else if (dkf < T(0)) pk = fmin(pk, (klo - ki) / dkf);
         if (dwf > T(0)) pw = fmin(pw, (whi - wi) / dwf);
         else if (dwf < T(0)) pw = fmin(pw, (wlo - wi) / dwf);
     }
-    grads[8 * np + i] = pk * g[4];
-    grads[9 * np + i] = pk * g[5];
-    grads[10 * np + i] = pw * g[6];
-    grads[11 * np + i] = pw * g[7];
-    // f1 = tanh(arg1^4) (Sec. 2), kinematic form
+    lg[0] = pk * g[4];
+    lg[1] = pk * g[5];
+    lg[2] = pw * g[6];
+    lg[3] = pw * g[7];
     T cd = T(2 * kSw2) / wi * (g[4] * g[6] + g[5] * g[7]);
     cd = cd > T(1e-20) ? cd : T(1e-20);
     const T a = sqrt(ki) / (T(kBstar) * wi * di);
@@ -746,84 +734,65 @@ __global__ void __launch_bounds__(kTile)
     const T c = T(4 * kSw2) * ki / (cd * di * di);
     const T arg1 = fmin(fmax(a, bb), c);
     const T a2 = arg1 * arg1;
-    f1out[i] = tanh(a2 * a2);
+    f1 = tanh(a2 * a2);
 }
 
-// Face convection (limited second-order upwind, mean face velocity) and central diffusion (mean face
-// coefficient) of k and omega, explicit production and cross diffusion, point-implicit
-// destruction; then f2, nu_t = a1 k / max(a1 omega, S f2) and tau = (nu + nu_t)/cs^2.
+// Face data of the k / omega update for one face: the neighbour's (u, v, k, omega), its
+// limited k / omega gradients, f1 and nu_t; or the boundary values.
 template <class T>
-__global__ void __launch_bounds__(kTile)
-    k_sst_update(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
-                 const T *__restrict__ nut, const T *__restrict__ grads,
-                 const T *__restrict__ f1a, T *__restrict__ k_out, T *__restrict__ w_out,
-                 T *__restrict__ nut_out, T *__restrict__ tau, Geo<T> G,
-                 const T *__restrict__ fn, T *__restrict__ frel) {
-    const int i = blockIdx.x * kTile + threadIdx.x;
-    const size_t np = G.np;
-    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
-    if (!P.sst) return;  // laminar instance
+struct SstFace {
+    bool has, bnd;
+    T u, v, k, w;        // neighbour or boundary values
+    T lg[4];             // neighbour limited gradients (interior only)
+    T f1, nut;           // neighbour (interior only)
+    T snx, sny, rox, roy, rnx, rny, dinv;
+};
+
+// Convection (limited second-order upwind, mean face velocity), central diffusion (mean face
+// coefficient), explicit production and cross diffusion, point-implicit destruction; then f2,
+// nu_t = a1 k / max(a1 omega, S f2) and tau = (nu + nu_t)/cs^2.
+template <class T>
+__device__ __forceinline__ void sst_cell_update(const InstParam &P, T ui, T vi, T ki, T wi, T nti,
+                                                T di, const T *g, const T *lgi, T f1,
+                                                const SstFace<T> *F, T &kn, T &wn, T &ntn,
+                                                T &tnew) {
     const T nu = T(P.nu), dt = T(P.dt);
-    const T ui = mac[np + i], vi = mac[2 * np + i], ki = kk[i], wi = ww[i], nti = nut[i];
-    const T di = G.wdist[i];
-    T g[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) g[c] = grads[c * np + i];
-    const T f1 = f1a[i];
     const T sk_i = f1 * T(kSk1) + (T(1) - f1) * T(kSk2);
     const T sw_i = f1 * T(kSw1) + (T(1) - f1) * T(kSw2);
     T ck = 0, cw = 0, dk = 0, dw = 0;
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const int nb = G.nbr[m * np + i];
-        if (nb == kNone) continue;
-        const T snx = G.sn[(2 * m) * np + i], sny = G.sn[(2 * m + 1) * np + i];  // n dl / A
-        const T rox = G.rown[(2 * m) * np + i], roy = G.rown[(2 * m + 1) * np + i];
-        const T kin = ki + grads[8 * np + i] * rox + grads[9 * np + i] * roy;
-        const T win = wi + grads[10 * np + i] * rox + grads[11 * np + i] * roy;
-        const T dinv = G.dinv[m * np + i];
-        // |n dl / A| -> dl / A
-        const T dla = sqrt(snx * snx + sny * sny);
-        if (nb >= 0) {
-            const T uf = T(0.5) * (ui + mac[np + nb]), vf = T(0.5) * (vi + mac[2 * np + nb]);
-            const T un = uf * snx + vf * sny;  // (u_f . n) dl / A
+        const SstFace<T> &f = F[m];
+        if (!f.has) continue;
+        const T kin = ki + lgi[0] * f.rox + lgi[1] * f.roy;
+        const T win = wi + lgi[2] * f.rox + lgi[3] * f.roy;
+        const T dla = sqrt(f.snx * f.snx + f.sny * f.sny);  // |n dl / A| -> dl / A
+        if (!f.bnd) {
+            const T uf = T(0.5) * (ui + f.u), vf = T(0.5) * (vi + f.v);
+            const T un = uf * f.snx + vf * f.sny;  // (u_f . n) dl / A
             T kup, wup;
             if (un >= T(0)) {
                 kup = kin; wup = win;
             } else {
-                const T rnx = G.rnbr[(2 * m) * np + i], rny = G.rnbr[(2 * m + 1) * np + i];
-                kup = kk[nb] + grads[8 * np + nb] * rnx + grads[9 * np + nb] * rny;
-                wup = ww[nb] + grads[10 * np + nb] * rnx + grads[11 * np + nb] * rny;
+                kup = f.k + f.lg[0] * f.rnx + f.lg[1] * f.rny;
+                wup = f.w + f.lg[2] * f.rnx + f.lg[3] * f.rny;
             }
-            const T f1j = f1a[nb], ntj = nut[nb];
-            const T skj = f1j * T(kSk1) + (T(1) - f1j) * T(kSk2);
-            const T swj = f1j * T(kSw1) + (T(1) - f1j) * T(kSw2);
-            const T gkf = T(0.5) * ((nu + sk_i * nti) + (nu + skj * ntj));
-            const T gwf = T(0.5) * ((nu + sw_i * nti) + (nu + swj * ntj));
+            const T skj = f.f1 * T(kSk1) + (T(1) - f.f1) * T(kSk2);
+            const T swj = f.f1 * T(kSw1) + (T(1) - f.f1) * T(kSw2);
+            const T gkf = T(0.5) * ((nu + sk_i * nti) + (nu + skj * f.nut));
+            const T gwf = T(0.5) * ((nu + sw_i * nti) + (nu + swj * f.nut));
             ck += un * kup;
             cw += un * wup;
-            dk += gkf * (kk[nb] - ki) * dinv * dla;
-            dw += gwf * (ww[nb] - wi) * dinv * dla;
+            dk += gkf * (f.k - ki) * f.dinv * dla;
+            dw += gwf * (f.w - wi) * f.dinv * dla;
         } else {
-            const int b = -nb - 1;
-            const int t = G.btype[b];
-            T ub, vb, kb, wb;
-            if (t == FVLBM_BC_WALL) {
-                ub = G.bval[1 * G.nbt + b]; vb = G.bval[2 * G.nbt + b]; kb = T(0);
-                wb = T(60) * nu / (T(kB1) * di * di);
-            } else if (t == FVLBM_BC_OUTLET) {
-                ub = ui; vb = vi; kb = ki; wb = wi;
-            } else {
-                ub = G.bval[1 * G.nbt + b]; vb = G.bval[2 * G.nbt + b];
-                kb = G.bval[3 * G.nbt + b]; wb = G.bval[4 * G.nbt + b];
-            }
-            const T un = ub * snx + vb * sny;
-            const T kup = un >= T(0) ? kin : kb;
-            const T wup = un >= T(0) ? win : wb;
+            const T un = f.u * f.snx + f.v * f.sny;
+            const T kup = un >= T(0) ? kin : f.k;
+            const T wup = un >= T(0) ? win : f.w;
             ck += un * kup;
             cw += un * wup;
-            dk += (nu + sk_i * nti) * (kb - ki) * dinv * dla;
-            dw += (nu + sw_i * nti) * (wb - wi) * dinv * dla;
+            dk += (nu + sk_i * nti) * (f.k - ki) * f.dinv * dla;
+            dw += (nu + sw_i * nti) * (f.w - wi) * f.dinv * dla;
         }
     }
     const T s11 = g[0], s22 = g[3], s12 = T(0.5) * (g[1] + g[2]);
@@ -840,24 +809,266 @@ __global__ void __launch_bounds__(kTile)
     const T rk = -ck + dk + pk;
     const T rw = -cw + dw + pw + cross;
     const T beta = f1 * T(kB1) + (T(1) - f1) * T(kB2);
-    T kn = (ki + dt * rk) / (T(1) + dt * T(kBstar) * wi);
-    T wn = (wi + dt * rw) / (T(1) + dt * beta * wi);
+    kn = (ki + dt * rk) / (T(1) + dt * T(kBstar) * wi);
+    wn = (wi + dt * rw) / (T(1) + dt * beta * wi);
     kn = kn > T(0) ? kn : T(0);
     wn = wn > T(P.omega_min) ? wn : T(P.omega_min);
     const T arg2 = fmax(T(2) * sqrt(kn) / (T(kBstar) * wn * di), T(500) * nu / (wn * di * di));
     const T f2 = tanh(arg2 * arg2);
-    const T ntn = T(kA1) * kn / fmax(T(kA1) * wn, Sabs * f2);
+    ntn = T(kA1) * kn / fmax(T(kA1) * wn, Sabs * f2);
+    tnew = (nu + ntn) / T(kCs2);
+}
+
+// ---- two-pass SST kernels (one thread per cell, neighbours gathered from global memory)
+// Gradients of u, v, k, omega, the limited k / omega gradients and f1.
+template <class T>
+__global__ void __launch_bounds__(kTile)
+    k_sst_grad(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
+               T *__restrict__ grads, T *__restrict__ f1out, Geo<T> G) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
+    if (!P.sst) return;  // laminar instance: tau stays nu / cs^2
+    const T nu = T(P.nu);
+    const T own[4] = {mac[np + i], mac[2 * np + i], kk[i], ww[i]};
+    const T di = G.wdist[i];
+    bool has[4];
+    T q[4][4], W[8], R[8];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int nb = G.nbr[m * np + i];
+        has[m] = nb != kNone;
+        W[2 * m] = G.lsq[(2 * m) * np + i];
+        W[2 * m + 1] = G.lsq[(2 * m + 1) * np + i];
+        R[2 * m] = G.rown[(2 * m) * np + i];
+        R[2 * m + 1] = G.rown[(2 * m + 1) * np + i];
+        if (nb == kNone) continue;
+        if (nb >= 0) {
+            q[m][0] = mac[np + nb]; q[m][1] = mac[2 * np + nb]; q[m][2] = kk[nb]; q[m][3] = ww[nb];
+        } else {
+            sst_bvals(G, -nb - 1, nu, own[0], own[1], own[2], own[3], di, q[m][0], q[m][1], q[m][2],
+                      q[m][3]);
+        }
+    }
+    T g[8], lg[4], f1;
+    sst_cell_grad(own[2], own[3], di, nu, has, q, W, R, own, g, lg, f1);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) grads[c * np + i] = g[c];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) grads[(8 + c) * np + i] = lg[c];
+    f1out[i] = f1;
+}
+
+// The k / omega update and the new relaxation time (and, on the fused path, f^(1)).
+template <class T>
+__global__ void __launch_bounds__(kTile)
+    k_sst_update(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
+                 const T *__restrict__ nut, const T *__restrict__ grads,
+                 const T *__restrict__ f1a, T *__restrict__ k_out, T *__restrict__ w_out,
+                 T *__restrict__ nut_out, T *__restrict__ tau, Geo<T> G,
+                 const T *__restrict__ fn, T *__restrict__ frel) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
+    if (!P.sst) return;  // laminar instance
+    const T nu = T(P.nu);
+    const T ui = mac[np + i], vi = mac[2 * np + i], ki = kk[i], wi = ww[i], nti = nut[i];
+    const T di = G.wdist[i];
+    T g[8], lgi[4];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) g[c] = grads[c * np + i];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) lgi[c] = grads[(8 + c) * np + i];
+    SstFace<T> F[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int nb = G.nbr[m * np + i];
+        SstFace<T> &f = F[m];
+        f.has = nb != kNone;
+        if (!f.has) continue;
+        f.bnd = nb < 0;
+        f.snx = G.sn[(2 * m) * np + i]; f.sny = G.sn[(2 * m + 1) * np + i];
+        f.rox = G.rown[(2 * m) * np + i]; f.roy = G.rown[(2 * m + 1) * np + i];
+        f.dinv = G.dinv[m * np + i];
+        if (nb >= 0) {
+            f.u = mac[np + nb]; f.v = mac[2 * np + nb]; f.k = kk[nb]; f.w = ww[nb];
+            f.rnx = G.rnbr[(2 * m) * np + i]; f.rny = G.rnbr[(2 * m + 1) * np + i];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) f.lg[c] = grads[(8 + c) * np + nb];
+            f.f1 = f1a[nb];
+            f.nut = nut[nb];
+        } else {
+            sst_bvals(G, -nb - 1, nu, ui, vi, ki, wi, di, f.u, f.v, f.k, f.w);
+        }
+    }
+    T kn, wn, ntn, tnew;
+    sst_cell_update(P, ui, vi, ki, wi, nti, di, g, lgi, f1a[i], F, kn, wn, ntn, tnew);
     k_out[i] = kn;
     w_out[i] = wn;
     nut_out[i] = ntn;
-    const T tnew = (nu + ntn) / T(kCs2);
     tau[i] = tnew;
     if (frel != nullptr) {  // fused path: stage 1's f^(1) with the new relaxation time
         T f[kQ];
         load9(fn, np, i, f);
-        relax9(f, T(P.rho0), dt, tnew);
+        relax9(f, T(P.rho0), T(P.dt), tnew);
         store9(frel, np, i, f);
     }
+}
+
+// ------------------------------------------------------------------ fused SST kernel
+// Step 1 for one block of kBlock cells of an SST instance (laminar blocks return at once):
+// u, v, k, omega, nu_t of the block and both halo rings, the least-squares weights and wall
+// distances of block + ring-1 cells are staged asynchronously (bulk copies + cp.async); then
+// gradients, limited gradients and f1 of block + ring-1 cells go to shared memory; then each
+// block cell updates k, omega, nu_t and tau, and relaxes f^n to stage 1's f^(1) with the new
+// tau.  Same per-cell arithmetic as k_sst_grad / k_sst_update.
+//   sv  [5][emax]   u, v, k, omega, nu_t
+//   sG  [13][gmax]  8 gradients, 4 limited gradients, f1
+//   sW  [8][gmax]   least-squares weights;  sD [gmax] wall distance
+//   adj [4 gmax] words, then one 8-byte mbarrier
+template <class T>
+struct SstSmem {
+    static __host__ __device__ size_t bytes(int emax, int gmax) {
+        return (size_t(5) * emax + 22u * gmax) * sizeof(T) + 4u * gmax * sizeof(unsigned) + 16;
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kBlock)
+    k_sst_fused(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
+                const T *__restrict__ nut, T *__restrict__ k_out, T *__restrict__ w_out,
+                T *__restrict__ nut_out, T *__restrict__ tau, const T *__restrict__ fn,
+                T *__restrict__ frel, Geo<T> G, Halo H) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int b = blockIdx.x, t = threadIdx.x;
+    const InstParam P = G.ip[G.tile_inst[b * (kBlock / kTile)]];
+    if (!P.sst) return;  // the whole block belongs to one laminar instance
+    const int E0 = H.emax, G0 = H.gmax;
+    T *sv = reinterpret_cast<T *>(smem_raw);
+    T *sG = sv + 5 * E0;
+    T *sW = sG + 13 * G0;
+    T *sD = sW + 8 * G0;
+    unsigned *sAdj = reinterpret_cast<unsigned *>(sD + G0);
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(sAdj + 4 * G0);
+    const int base = b * kBlock;
+    const int i = base + t;
+    const size_t np = G.np;
+    const T nu = T(P.nu);
+    const int h0 = H.halo_ptr[b], nh = H.halo_ptr[b + 1] - h0, nr1 = H.r1[b];
+    const int E = kBlock + nh, NG = kBlock + nr1;
+    const unsigned *__restrict__ adj_g = H.adj + 4 * static_cast<size_t>(H.adj_ptr[b]);
+    const T *rows[5] = {mac + np, mac + 2 * np, kk, ww, nut};
+
+    if (t == 0) mbar_init(bar);
+    __syncthreads();
+    if (t == 0) {
+        constexpr unsigned row = kBlock * sizeof(T);
+        const unsigned adj_bytes = 4u * NG * sizeof(unsigned);
+        mbar_expect_tx(bar, row * (5 + 8 + 1) + adj_bytes);
+        for (int c = 0; c < 5; ++c) bulk_g2s(sv + c * E0, rows[c] + base, row, bar);
+        for (int k = 0; k < 8; ++k) bulk_g2s(sW + k * G0, G.lsq + k * np + base, row, bar);
+        bulk_g2s(sD, G.wdist + base, row, bar);
+        bulk_g2s(sAdj, adj_g, adj_bytes, bar);
+    }
+    for (int e = kBlock + t; e < E; e += kBlock) {
+        const int gid = H.halo[h0 + e - kBlock];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) cp_async<sizeof(T)>(sv + c * E0 + e, rows[c] + gid);
+        if (e < NG) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) cp_async<sizeof(T)>(sW + k * G0 + e, G.lsq + k * np + gid);
+            cp_async<sizeof(T)>(sD + e, G.wdist + gid);
+        }
+    }
+    cp_async_wait_all();
+    {
+        long long it = 0;
+        bool done = mbar_try_wait(bar, 0);
+        while (!done && ++it < kWaitLimit) done = mbar_try_wait(bar, 0);
+        if (__syncthreads_or(!done)) {
+            if (t == 0) atomicExch(H.err, 1);
+            for (long long k = 0; k < kWaitLimit && !mbar_try_wait(bar, 0); ++k) {
+            }
+            return;
+        }
+    }
+
+    // gradients, limited gradients and f1 of block + ring-1 cells
+    for (int c = t; c < NG; c += kBlock) {
+        const int gid = c < kBlock ? base + c : H.halo[h0 + c - kBlock];
+        const T own[4] = {sv[c], sv[E0 + c], sv[2 * E0 + c], sv[3 * E0 + c]};
+        const T di = sD[c];
+        bool has[4];
+        T q[4][4], W[8], R[8];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const unsigned w = sAdj[m * NG + c];
+            has[m] = w != kAdjNone;
+            W[2 * m] = sW[(2 * m) * G0 + c];
+            W[2 * m + 1] = sW[(2 * m + 1) * G0 + c];
+            R[2 * m] = G.rown[(2 * m) * np + gid];
+            R[2 * m + 1] = G.rown[(2 * m + 1) * np + gid];
+            if (!has[m]) continue;
+            if (w & kAdjBnd) {
+                sst_bvals(G, static_cast<int>(w & ~kAdjBnd), nu, own[0], own[1], own[2], own[3], di,
+                          q[m][0], q[m][1], q[m][2], q[m][3]);
+            } else {
+                const int j = static_cast<int>(w & 0xFFFFu);
+#pragma unroll
+                for (int c2 = 0; c2 < 4; ++c2) q[m][c2] = sv[c2 * E0 + j];
+            }
+        }
+        T g[8], lg[4], f1;
+        sst_cell_grad(own[2], own[3], di, nu, has, q, W, R, own, g, lg, f1);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sG[k * G0 + c] = g[k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sG[(8 + k) * G0 + c] = lg[k];
+        sG[12 * G0 + c] = f1;
+    }
+    __syncthreads();
+
+    // update of block cell t
+    const T ui = sv[t], vi = sv[E0 + t], ki = sv[2 * E0 + t], wi = sv[3 * E0 + t];
+    const T nti = sv[4 * E0 + t], di = sD[t];
+    T g[8], lgi[4];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) g[k] = sG[k * G0 + t];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) lgi[k] = sG[(8 + k) * G0 + t];
+    SstFace<T> F[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const unsigned w = sAdj[m * NG + t];
+        SstFace<T> &f = F[m];
+        f.has = w != kAdjNone;
+        if (!f.has) continue;
+        f.bnd = (w & kAdjBnd) != 0;
+        f.snx = G.sn[(2 * m) * np + i]; f.sny = G.sn[(2 * m + 1) * np + i];
+        f.rox = G.rown[(2 * m) * np + i]; f.roy = G.rown[(2 * m + 1) * np + i];
+        f.dinv = G.dinv[m * np + i];
+        if (!f.bnd) {
+            const int j = static_cast<int>(w & 0xFFFFu);
+            f.u = sv[j]; f.v = sv[E0 + j]; f.k = sv[2 * E0 + j]; f.w = sv[3 * E0 + j];
+            f.rnx = G.rnbr[(2 * m) * np + i]; f.rny = G.rnbr[(2 * m + 1) * np + i];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f.lg[k] = sG[(8 + k) * G0 + j];
+            f.f1 = sG[12 * G0 + j];
+            f.nut = sv[4 * E0 + j];
+        } else {
+            sst_bvals(G, static_cast<int>(w & ~kAdjBnd), nu, ui, vi, ki, wi, di, f.u, f.v, f.k, f.w);
+        }
+    }
+    T kn, wn, ntn, tnew;
+    sst_cell_update(P, ui, vi, ki, wi, nti, di, g, lgi, sG[12 * G0 + t], F, kn, wn, ntn, tnew);
+    k_out[i] = kn;
+    w_out[i] = wn;
+    nut_out[i] = ntn;
+    tau[i] = tnew;
+    T f[kQ];
+    load9(fn, np, i, f);
+    relax9(f, T(P.rho0), T(P.dt), tnew);
+    store9(frel, np, i, f);
 }
 
 // ------------------------------------------------------------------ state I/O kernels
@@ -1000,7 +1211,7 @@ struct fvlbm_handle {
     // fused path: per-block halo lists and local adjacency
     bool fused = false;
     int nblk = 0, emax = 0, gmax = 0;
-    size_t fused_smem = 0;
+    size_t fused_smem = 0, sst_smem = 0;
     int *d_halo_ptr = nullptr, *d_halo = nullptr, *d_r1 = nullptr, *d_adj_ptr = nullptr;
     unsigned *d_adj = nullptr;
     int *d_err = nullptr;   // device error flag (a staging wait gave up)
@@ -1106,7 +1317,7 @@ void launch(fvlbm_handle *h, int id, const char *name, F &&fn) {
 
 enum KernelId {
     K_SST_GRAD, K_SST_UPDATE, K_STAGE1, K_GRAD, K_FLUX1, K_FLUX2, K_FLUX3, K_REDUCE,
-    K_FUSED1, K_FUSED2, K_FUSED3
+    K_FUSED1, K_FUSED2, K_FUSED3, K_SST_FUSED
 };
 
 template <class T>
@@ -1124,11 +1335,18 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         T *kn = static_cast<T *>(h->kk[n]), *wn = static_cast<T *>(h->ww[n]);
         T *nn = static_cast<T *>(h->nut[n]);
         T *sg = static_cast<T *>(h->sgrad), *f1 = static_cast<T *>(h->f1);
-        launch(h, K_SST_GRAD, "sst_grad", [&] { k_sst_grad<T><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G); });
-        launch(h, K_SST_UPDATE, "sst_update", [&] {
-            k_sst_update<T><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn,
-                                                   h->fused ? static_cast<T *>(h->frel) : nullptr);
-        });
+        if (h->fused) {
+            Halo H{h->d_halo_ptr, h->d_halo, h->d_r1, h->d_adj_ptr, h->d_adj, h->d_err, h->emax, h->gmax};
+            launch(h, K_SST_FUSED, "sst_fused", [&] {
+                k_sst_fused<T><<<h->nblk, kBlock, h->sst_smem, s>>>(mac, kc, wc, nc, kn, wn, nn, tau, fn,
+                                                                   static_cast<T *>(h->frel), G, H);
+            });
+        } else {
+            launch(h, K_SST_GRAD, "sst_grad", [&] { k_sst_grad<T><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G); });
+            launch(h, K_SST_UPDATE, "sst_update", [&] {
+                k_sst_update<T><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn, nullptr);
+            });
+        }
         h->turb = n;
     }
     if (h->fused) {
@@ -1187,7 +1405,9 @@ void enqueue(fvlbm_handle *h, bool stats) {
         enqueue_step<float>(h, stats);
 }
 
-int launches_per_step(const fvlbm_handle *h) { return (h->sst ? 2 : 0) + (h->fused ? 3 : 7); }
+int launches_per_step(const fvlbm_handle *h) {
+    return (h->sst ? (h->fused ? 1 : 2) : 0) + (h->fused ? 3 : 7);
+}
 
 // Capture `nsteps` plain steps into an executable graph.  A replay always starts from the
 // k / omega / nu_t ping-pong parity the graph was captured with, and an even step count ends
@@ -1267,13 +1487,15 @@ int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<
     emax = (emax + 3) / 4 * 4;  // 16-byte aligned shared-memory rows
     gmax = (gmax + 3) / 4 * 4;
     const size_t smem = FusedSmem<T>::bytes(emax, gmax);
-    if (emax >= 65536 || smem > static_cast<size_t>(kFusedSmemCap)) {
+    if (emax >= 65536 || std::max(smem, SstSmem<T>::bytes(emax, gmax)) >
+                             static_cast<size_t>(kFusedSmemCap)) {
         h->fused = false;
         return FVLBM_OK;
     }
     h->emax = emax;
     h->gmax = gmax;
     h->fused_smem = smem;
+    h->sst_smem = SstSmem<T>::bytes(emax, gmax);
     int rc;
     if ((rc = upload_raw(h, &h->d_halo_ptr, halo_ptr))) return rc;
     if (halo.empty()) halo.push_back(0);
@@ -1289,6 +1511,7 @@ int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<
     CK(cudaFuncSetAttribute(k_fused_stage<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     CK(cudaFuncSetAttribute(k_fused_stage<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     CK(cudaFuncSetAttribute(k_fused_stage<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    CK(cudaFuncSetAttribute(k_sst_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     return FVLBM_OK;
 }
 
