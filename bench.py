@@ -345,6 +345,7 @@ def _kernel_bytes(kname, prec, cells, sst_cells):
         "fused_stage1": 9 + 1 + 27,                # f^n, tau -> f2, B, C (gradient in smem)
         "fused_stage2": 9 + 18 + 1 + 18,           # f2, B, C, tau -> f3, C
         "fused_stage3": 9 + 9 + 1 + 12,            # f3, C, tau -> f^{n+1}, macros
+        "sst_fused": 5 + 4 + 9 + 9,                # u, v, k, w, nu_t -> k, w, nu_t, tau; f^n -> f^(1)
     }[kname]
     n = sst_cells if kname.startswith("sst") else cells
     return n * (words * w + idx)
