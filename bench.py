@@ -341,11 +341,10 @@ def _kernel_bytes(kname, prec, cells, sst_cells):
         "flux_stage2": 9 + 18 + 18 + 1 + 18,       # f2, g, B, C, tau -> f3, C
         "flux_stage3": 9 + 18 + 9 + 1 + 9 + 3,     # f3, g, C, tau -> f^{n+1}, macros
         "sst_grad": 3 + 2 + 1 + 12 + 1,
-        "sst_update": 3 + 3 + 12 + 1 + 4,
+        "sst_update": 3 + 3 + 12 + 1 + 4 + 9 + 9,  # + f^n -> f^(1) (fused path)
         "fused_stage1": 9 + 1 + 27,                # f^n, tau -> f2, B, C (gradient in smem)
         "fused_stage2": 9 + 18 + 1 + 18,           # f2, B, C, tau -> f3, C
         "fused_stage3": 9 + 9 + 1 + 12,            # f3, C, tau -> f^{n+1}, macros
-        "sst_fused": 5 + 4 + 9 + 9,                # u, v, k, w, nu_t -> k, w, nu_t, tau; f^n -> f^(1)
     }[kname]
     n = sst_cells if kname.startswith("sst") else cells
     return n * (words * w + idx)

@@ -915,162 +915,6 @@ __global__ void __launch_bounds__(kTile)
     }
 }
 
-// ------------------------------------------------------------------ fused SST kernel
-// Step 1 for one block of kBlock cells of an SST instance (laminar blocks return at once):
-// u, v, k, omega, nu_t of the block and both halo rings, the least-squares weights and wall
-// distances of block + ring-1 cells are staged asynchronously (bulk copies + cp.async); then
-// gradients, limited gradients and f1 of block + ring-1 cells go to shared memory; then each
-// block cell updates k, omega, nu_t and tau, and relaxes f^n to stage 1's f^(1) with the new
-// tau.  Same per-cell arithmetic as k_sst_grad / k_sst_update.
-//   sv  [5][emax]   u, v, k, omega, nu_t
-//   sG  [13][gmax]  8 gradients, 4 limited gradients, f1
-//   sW  [8][gmax]   least-squares weights;  sD [gmax] wall distance
-//   adj [4 gmax] words, then one 8-byte mbarrier
-template <class T>
-struct SstSmem {
-    static __host__ __device__ size_t bytes(int emax, int gmax) {
-        return (size_t(5) * emax + 22u * gmax) * sizeof(T) + 4u * gmax * sizeof(unsigned) + 16;
-    }
-};
-
-template <class T>
-__global__ void __launch_bounds__(kBlock)
-    k_sst_fused(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
-                const T *__restrict__ nut, T *__restrict__ k_out, T *__restrict__ w_out,
-                T *__restrict__ nut_out, T *__restrict__ tau, const T *__restrict__ fn,
-                T *__restrict__ frel, Geo<T> G, Halo H) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int b = blockIdx.x, t = threadIdx.x;
-    const InstParam P = G.ip[G.tile_inst[b * (kBlock / kTile)]];
-    if (!P.sst) return;  // the whole block belongs to one laminar instance
-    const int E0 = H.emax, G0 = H.gmax;
-    T *sv = reinterpret_cast<T *>(smem_raw);
-    T *sG = sv + 5 * E0;
-    T *sW = sG + 13 * G0;
-    T *sD = sW + 8 * G0;
-    unsigned *sAdj = reinterpret_cast<unsigned *>(sD + G0);
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(sAdj + 4 * G0);
-    const int base = b * kBlock;
-    const int i = base + t;
-    const size_t np = G.np;
-    const T nu = T(P.nu);
-    const int h0 = H.halo_ptr[b], nh = H.halo_ptr[b + 1] - h0, nr1 = H.r1[b];
-    const int E = kBlock + nh, NG = kBlock + nr1;
-    const unsigned *__restrict__ adj_g = H.adj + 4 * static_cast<size_t>(H.adj_ptr[b]);
-    const T *rows[5] = {mac + np, mac + 2 * np, kk, ww, nut};
-
-    if (t == 0) mbar_init(bar);
-    __syncthreads();
-    if (t == 0) {
-        constexpr unsigned row = kBlock * sizeof(T);
-        const unsigned adj_bytes = 4u * NG * sizeof(unsigned);
-        mbar_expect_tx(bar, row * (5 + 8 + 1) + adj_bytes);
-        for (int c = 0; c < 5; ++c) bulk_g2s(sv + c * E0, rows[c] + base, row, bar);
-        for (int k = 0; k < 8; ++k) bulk_g2s(sW + k * G0, G.lsq + k * np + base, row, bar);
-        bulk_g2s(sD, G.wdist + base, row, bar);
-        bulk_g2s(sAdj, adj_g, adj_bytes, bar);
-    }
-    for (int e = kBlock + t; e < E; e += kBlock) {
-        const int gid = H.halo[h0 + e - kBlock];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) cp_async<sizeof(T)>(sv + c * E0 + e, rows[c] + gid);
-        if (e < NG) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) cp_async<sizeof(T)>(sW + k * G0 + e, G.lsq + k * np + gid);
-            cp_async<sizeof(T)>(sD + e, G.wdist + gid);
-        }
-    }
-    cp_async_wait_all();
-    {
-        long long it = 0;
-        bool done = mbar_try_wait(bar, 0);
-        while (!done && ++it < kWaitLimit) done = mbar_try_wait(bar, 0);
-        if (__syncthreads_or(!done)) {
-            if (t == 0) atomicExch(H.err, 1);
-            for (long long k = 0; k < kWaitLimit && !mbar_try_wait(bar, 0); ++k) {
-            }
-            return;
-        }
-    }
-
-    // gradients, limited gradients and f1 of block + ring-1 cells
-    for (int c = t; c < NG; c += kBlock) {
-        const int gid = c < kBlock ? base + c : H.halo[h0 + c - kBlock];
-        const T own[4] = {sv[c], sv[E0 + c], sv[2 * E0 + c], sv[3 * E0 + c]};
-        const T di = sD[c];
-        bool has[4];
-        T q[4][4], W[8], R[8];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const unsigned w = sAdj[m * NG + c];
-            has[m] = w != kAdjNone;
-            W[2 * m] = sW[(2 * m) * G0 + c];
-            W[2 * m + 1] = sW[(2 * m + 1) * G0 + c];
-            R[2 * m] = G.rown[(2 * m) * np + gid];
-            R[2 * m + 1] = G.rown[(2 * m + 1) * np + gid];
-            if (!has[m]) continue;
-            if (w & kAdjBnd) {
-                sst_bvals(G, static_cast<int>(w & ~kAdjBnd), nu, own[0], own[1], own[2], own[3], di,
-                          q[m][0], q[m][1], q[m][2], q[m][3]);
-            } else {
-                const int j = static_cast<int>(w & 0xFFFFu);
-#pragma unroll
-                for (int c2 = 0; c2 < 4; ++c2) q[m][c2] = sv[c2 * E0 + j];
-            }
-        }
-        T g[8], lg[4], f1;
-        sst_cell_grad(own[2], own[3], di, nu, has, q, W, R, own, g, lg, f1);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) sG[k * G0 + c] = g[k];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sG[(8 + k) * G0 + c] = lg[k];
-        sG[12 * G0 + c] = f1;
-    }
-    __syncthreads();
-
-    // update of block cell t
-    const T ui = sv[t], vi = sv[E0 + t], ki = sv[2 * E0 + t], wi = sv[3 * E0 + t];
-    const T nti = sv[4 * E0 + t], di = sD[t];
-    T g[8], lgi[4];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) g[k] = sG[k * G0 + t];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) lgi[k] = sG[(8 + k) * G0 + t];
-    SstFace<T> F[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const unsigned w = sAdj[m * NG + t];
-        SstFace<T> &f = F[m];
-        f.has = w != kAdjNone;
-        if (!f.has) continue;
-        f.bnd = (w & kAdjBnd) != 0;
-        f.snx = G.sn[(2 * m) * np + i]; f.sny = G.sn[(2 * m + 1) * np + i];
-        f.rox = G.rown[(2 * m) * np + i]; f.roy = G.rown[(2 * m + 1) * np + i];
-        f.dinv = G.dinv[m * np + i];
-        if (!f.bnd) {
-            const int j = static_cast<int>(w & 0xFFFFu);
-            f.u = sv[j]; f.v = sv[E0 + j]; f.k = sv[2 * E0 + j]; f.w = sv[3 * E0 + j];
-            f.rnx = G.rnbr[(2 * m) * np + i]; f.rny = G.rnbr[(2 * m + 1) * np + i];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) f.lg[k] = sG[(8 + k) * G0 + j];
-            f.f1 = sG[12 * G0 + j];
-            f.nut = sv[4 * E0 + j];
-        } else {
-            sst_bvals(G, static_cast<int>(w & ~kAdjBnd), nu, ui, vi, ki, wi, di, f.u, f.v, f.k, f.w);
-        }
-    }
-    T kn, wn, ntn, tnew;
-    sst_cell_update(P, ui, vi, ki, wi, nti, di, g, lgi, sG[12 * G0 + t], F, kn, wn, ntn, tnew);
-    k_out[i] = kn;
-    w_out[i] = wn;
-    nut_out[i] = ntn;
-    tau[i] = tnew;
-    T f[kQ];
-    load9(fn, np, i, f);
-    relax9(f, T(P.rho0), T(P.dt), tnew);
-    store9(frel, np, i, f);
-}
-
 // ------------------------------------------------------------------ state I/O kernels
 template <class T>
 __global__ void k_init_state(T *__restrict__ fn, T *__restrict__ mac, const double *__restrict__ r0,
@@ -1211,7 +1055,7 @@ struct fvlbm_handle {
     // fused path: per-block halo lists and local adjacency
     bool fused = false;
     int nblk = 0, emax = 0, gmax = 0;
-    size_t fused_smem = 0, sst_smem = 0;
+    size_t fused_smem = 0;
     int *d_halo_ptr = nullptr, *d_halo = nullptr, *d_r1 = nullptr, *d_adj_ptr = nullptr;
     unsigned *d_adj = nullptr;
     int *d_err = nullptr;   // device error flag (a staging wait gave up)
@@ -1317,7 +1161,7 @@ void launch(fvlbm_handle *h, int id, const char *name, F &&fn) {
 
 enum KernelId {
     K_SST_GRAD, K_SST_UPDATE, K_STAGE1, K_GRAD, K_FLUX1, K_FLUX2, K_FLUX3, K_REDUCE,
-    K_FUSED1, K_FUSED2, K_FUSED3, K_SST_FUSED
+    K_FUSED1, K_FUSED2, K_FUSED3
 };
 
 template <class T>
@@ -1335,18 +1179,11 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         T *kn = static_cast<T *>(h->kk[n]), *wn = static_cast<T *>(h->ww[n]);
         T *nn = static_cast<T *>(h->nut[n]);
         T *sg = static_cast<T *>(h->sgrad), *f1 = static_cast<T *>(h->f1);
-        if (h->fused) {
-            Halo H{h->d_halo_ptr, h->d_halo, h->d_r1, h->d_adj_ptr, h->d_adj, h->d_err, h->emax, h->gmax};
-            launch(h, K_SST_FUSED, "sst_fused", [&] {
-                k_sst_fused<T><<<h->nblk, kBlock, h->sst_smem, s>>>(mac, kc, wc, nc, kn, wn, nn, tau, fn,
-                                                                   static_cast<T *>(h->frel), G, H);
-            });
-        } else {
-            launch(h, K_SST_GRAD, "sst_grad", [&] { k_sst_grad<T><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G); });
-            launch(h, K_SST_UPDATE, "sst_update", [&] {
-                k_sst_update<T><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn, nullptr);
-            });
-        }
+        launch(h, K_SST_GRAD, "sst_grad", [&] { k_sst_grad<T><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G); });
+        launch(h, K_SST_UPDATE, "sst_update", [&] {
+            k_sst_update<T><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn,
+                                                   h->fused ? static_cast<T *>(h->frel) : nullptr);
+        });
         h->turb = n;
     }
     if (h->fused) {
@@ -1405,9 +1242,7 @@ void enqueue(fvlbm_handle *h, bool stats) {
         enqueue_step<float>(h, stats);
 }
 
-int launches_per_step(const fvlbm_handle *h) {
-    return (h->sst ? (h->fused ? 1 : 2) : 0) + (h->fused ? 3 : 7);
-}
+int launches_per_step(const fvlbm_handle *h) { return (h->sst ? 2 : 0) + (h->fused ? 3 : 7); }
 
 // Capture `nsteps` plain steps into an executable graph.  A replay always starts from the
 // k / omega / nu_t ping-pong parity the graph was captured with, and an even step count ends
@@ -1487,15 +1322,13 @@ int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<
     emax = (emax + 3) / 4 * 4;  // 16-byte aligned shared-memory rows
     gmax = (gmax + 3) / 4 * 4;
     const size_t smem = FusedSmem<T>::bytes(emax, gmax);
-    if (emax >= 65536 || std::max(smem, SstSmem<T>::bytes(emax, gmax)) >
-                             static_cast<size_t>(kFusedSmemCap)) {
+    if (emax >= 65536 || smem > static_cast<size_t>(kFusedSmemCap)) {
         h->fused = false;
         return FVLBM_OK;
     }
     h->emax = emax;
     h->gmax = gmax;
     h->fused_smem = smem;
-    h->sst_smem = SstSmem<T>::bytes(emax, gmax);
     int rc;
     if ((rc = upload_raw(h, &h->d_halo_ptr, halo_ptr))) return rc;
     if (halo.empty()) halo.push_back(0);
@@ -1511,7 +1344,6 @@ int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<
     CK(cudaFuncSetAttribute(k_fused_stage<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     CK(cudaFuncSetAttribute(k_fused_stage<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     CK(cudaFuncSetAttribute(k_fused_stage<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    CK(cudaFuncSetAttribute(k_sst_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
     return FVLBM_OK;
 }
 
