@@ -109,7 +109,7 @@ class ClockSampler:
 def make_workload(name: str, rank: int = 0):
     from paper_1812_00394_gb300 import meshgen as mg
     if name == "sweep":
-        return mg.batched_sweep(seed=5 + 7919 * rank)
+        return mg.batched_sweep(seed=rank_seed(rank))
     if name == "delaunay40k":
         return [mg.cavity_delaunay(re=1000.0, z=5.0, seed=2 + rank)]
     if name == "cavity64":
@@ -195,12 +195,27 @@ def _time_steps(torch, solver, stream, steps, dist, world):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = start.elapsed_time(stop)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    return ms
+    return max_over_ranks(torch, dist, world, start.elapsed_time(stop), device="cuda")
+
+
+def max_over_ranks(torch, dist, world: int, value: float, device: str = "cuda") -> float:
+    """The slowest rank's time (all ranks get it); a no-op for one rank.  This is the only
+    collective of the multi-GPU run: instances are sharded by rank and never exchange data."""
+    if world <= 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Seed of rank r's own copy of the sweep (weak scaling: every rank a full, distinct sweep)."""
+    return 5 + 7919 * rank
+
+
+def aggregate_rate(cells_per_rank: int, world: int, steps: int, ms_max: float) -> float:
+    """Whole-job Mcell-steps/s: the cells all ranks advanced over the slowest rank's time."""
+    return cells_per_rank * world * steps / (ms_max * 1e-3) / 1e6
 
 
 def _vel(fields):
@@ -241,12 +256,20 @@ def run_ours(args):
                 ms = _time_steps(torch, s, stream, args.steps, dist, world)
             results[tag] = {"ms": ms, "clocks": clk.summary()}
         solvers[tag] = s
+    # the explicit Euler comparison scheme (Sec. 3.1 / 4.1) on the same workload, FP32: cost per
+    # step (its stable dt is < 2 tau, the IMEX one is not limited by tau)
+    with torch.cuda.stream(stream):
+        se = fvlbm.Solver(cases, precision=fvlbm.FVLBM_FP32_DEV, device=dev,
+                          stream=stream.cuda_stream, scheme=fvlbm.SCHEME_EULER)
+        se.step(args.warmup)
+        ms_euler = _time_steps(torch, se, stream, args.steps, dist, world)
+        se.close()
     setup_s = time.perf_counter() - t_setup
 
     ms32 = results["f32"]["ms"]
-    value = total_cells * world * args.steps / (ms32 * 1e-3) / 1e6
+    value = aggregate_rate(total_cells, world, args.steps, ms32)
     ms64 = results["f64"]["ms"]
-    value64 = total_cells * world * args.steps / (ms64 * 1e-3) / 1e6
+    value64 = aggregate_rate(total_cells, world, args.steps, ms64)
 
     # FP32 vs FP64 (both GPU, same number of steps) on every cell of the workload
     s32, s64 = solvers["f32"], solvers["f64"]
@@ -294,6 +317,9 @@ def run_ours(args):
                        "parallelism": f"{world} process(es), one per GPU, each its own sweep"},
             "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / args.steps,
                            "speedup_fp32_over_fp64": value / value64},
+            "explicit_euler_fp32": {"ms_per_step": ms_euler / args.steps,
+                                    "imex_over_euler_cost_per_step": ms32 / ms_euler,
+                                    "note": "comparison scheme of Sec. 4.1: stable only for dt < 2 tau"},
             "error": {"fp32_vs_fp64_gpu_velocity_rel_l2": l2_32_64, **err},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm, "traffic": None,

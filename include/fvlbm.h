@@ -92,6 +92,11 @@ typedef struct {
     const double *omega_init;  /* [n_cells] or NULL (1) */
     int kernel_path;           /* 0: fused stage kernels with shared-memory halo staging
                                   (default); 1: two-pass kernels (gradient array in HBM) */
+    int scheme;                /* 0: three-stage IMEX Runge-Kutta of Sec. 3.1 (default);
+                                  1: explicit Euler f^{n+1} = f^n + dt (Gamma^a + Gamma^c), the
+                                  original scheme that Sec. 3.1 and Sec. 4.1 compare against
+                                  (stable only for dt < 2 tau).  All instances of a batch share
+                                  it. */
 } fvlbm_params;
 
 typedef struct {

@@ -18,6 +18,7 @@
  *   sst_update()     Sec. 2 (k-omega SST), discretised per Eq. (SSTequint); tau by
  *                    Eq. (turbtau); coupled once per step before the stages (Step 1)
  *   forces()         momentum flux through wall faces -> C_D, C_L, Cp (Sec. 4.3 table)
+ *   euler_step()     the explicit Euler scheme of Part I, for the comparison of Sec. 4.1
  *
  * Where Part I (not available) or the text is silent, the reading taken is stated beside the
  * code; each is listed with its reason in the design notes of this repository.
@@ -76,6 +77,7 @@ typedef struct oracle {
     double *bxm, *bym, *bnx, *bny, *blen;
     double nu, rho0, dt, uref, lref, alpha_deg;
     int sst;
+    int scheme;                  /* 0: IMEX Runge-Kutta (Part II); 1: explicit Euler (Part I) */
     double *f;                   /* [nc * Q], cell-major */
     double *rho, *ux, *uy, *k, *om, *nut, *tau;
     double residual, moment_defect;
@@ -140,7 +142,7 @@ static void *xcalloc(size_t n, size_t s) { return calloc(n ? n : 1, s); }
 
 void oracle_destroy(oracle *o);
 
-/* params: [nu, rho0, dt, cfl, sst, uref, lref, alpha_deg] */
+/* params: [nu, rho0, dt, cfl, sst, uref, lref, alpha_deg, scheme] */
 oracle *oracle_create(int n_nodes, const double *xy, int n_cells, const int *cell_ptr,
                       const int *cell_nodes, int n_bedges, const int *bedge_nodes,
                       const int *bedge_type, const double *bedge_val, int n_periodic,
@@ -161,6 +163,7 @@ oracle *oracle_create(int n_nodes, const double *xy, int n_cells, const int *cel
     o->uref = params[5];
     o->lref = params[6];
     o->alpha_deg = params[7];
+    o->scheme = (int)params[8];
 
     o->nface = (int *)xcalloc(nc, sizeof(int));
     o->face = (oface *)xcalloc((size_t)nc * 4, sizeof(oface));
@@ -676,6 +679,8 @@ static void sst_update(oracle *o)
  *   Gamma^c(J) = -(f^(J) - f^eq(J)) / tau                                 Eq. (collision)
  *   Gamma^a(J) = convection of f^(J)                                      Eq. (advection)
  * then f^{n+1} = f^n + dt sum nt_J Gamma^a(J) + dt sum n_J Gamma^c(J)      Eq. (imextwo). */
+static int finish_step(oracle *o);
+
 static int imex_step(oracle *o)
 {
     int nc = o->nc;
@@ -724,7 +729,13 @@ static int imex_step(oracle *o)
         o->f[q] = s;
     }
     o->moment_defect = defect;
-    /* Step 7: macros; velocity residual e (reading: relative L2 change of u over the step) */
+    return finish_step(o);
+}
+
+/* Step 7: macros; velocity residual e (reading: relative L2 change of u over the step). */
+static int finish_step(oracle *o)
+{
+    int nc = o->nc;
     double num = 0.0, den = 0.0;
     int bad = 0;
     for (int i = 0; i < nc; i++) {
@@ -742,11 +753,35 @@ static int imex_step(oracle *o)
     return bad ? -1 : 0;
 }
 
+/* Explicit Euler FVLBM (the original scheme of Part I that the IMEX method replaces; Sec. 3.1
+ * states its collision limit dt < 2 tau, Sec. 4.1 compares the two):
+ * f^{n+1} = f^n + dt [Gamma^a(f^n) + Gamma^c(f^n)], Eqs. (semibgk), (advection), (collision). */
+static int euler_step(oracle *o)
+{
+    int nc = o->nc;
+    double dt = o->dt;
+    if (o->sst) sst_update(o);
+    else
+        for (int i = 0; i < nc; i++) o->tau[i] = o->nu / CS2;
+    convection(o, o->f, o->ga[0]);
+    for (int i = 0; i < nc; i++) {
+        double *f = &o->f[(size_t)i * Q];
+        double r, u, v, eq[Q];
+        moments(f, &r, &u, &v);
+        oracle_feq(r, u, v, eq);
+        for (int a = 0; a < Q; a++) {
+            double gc = -(f[a] - eq[a]) / o->tau[i];
+            f[a] = f[a] + dt * (o->ga[0][(size_t)i * Q + a] + gc);
+        }
+    }
+    return finish_step(o);
+}
+
 /* ------------------------------------------------------------------ public entry points */
 int oracle_step(oracle *o, int n)
 {
     for (int s = 0; s < n; s++)
-        if (imex_step(o) != 0) return -1;
+        if ((o->scheme == 1 ? euler_step(o) : imex_step(o)) != 0) return -1;
     return 0;
 }
 

@@ -90,14 +90,15 @@ class Oracle:
     """One oracle instance for a ``meshgen.Case``; arrays are in the mesh's cell order and
     f is cell-major [n_cells, 9]."""
 
-    def __init__(self, case, dt: float | None = None, sst: bool | None = None):
+    def __init__(self, case, dt: float | None = None, sst: bool | None = None,
+                 scheme: int = 0):
         lib = _load()
         m = case.mesh.normalized()
         rho, u, v, k, w = case.init_arrays()
         self._keep = (m, rho, u, v, k, w)
         params = np.array([case.nu, case.rho0, case.dt if dt is None else dt, case.cfl,
                            float(case.sst if sst is None else sst), case.uref, case.lref,
-                           case.alpha_deg], np.float64)
+                           case.alpha_deg, float(scheme)], np.float64)
         self._h = lib.oracle_create(m.n_nodes, m.xy.ravel(), m.n_cells, m.cell_ptr, m.cell_nodes,
                                     m.n_bedges, m.bedge_nodes.ravel(), m.bedge_type,
                                     m.bedge_val.ravel(), m.periodic_pairs.shape[0],

@@ -236,6 +236,7 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *out) {
 //   J = 1: Gamma^c(1) from f^n and f^(1); stage 2 solve (Eq. (fnewstage)); B, C
 //   J = 2: stage 3 solve from B + dt/2 Gamma^a(2); C update
 //   J = 3: f^{n+1} = f^(3) + C + dt/3 Gamma^a(3) (Eq. (imextwo)); macros; FP64 partial sums
+//   J = 4: explicit Euler comparison scheme, f^{n+1} = f^n + dt (Gamma^a + Gamma^c), into fs_out
 // The accumulator inputs are read through (pointer, row stride, column): a1 is f^n (J = 1),
 // B (J = 2) or C (J = 3); a2 is C (J = 2).  Outputs go to global memory at cell i.
 //   FN_FROM_F1: f^n is not read but recovered from f^(1) = [f^n + z/4 f^eq] / (1 + z/4) as
@@ -303,6 +304,26 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
             Cacc[a * np + i] = a2[a * ld2 + c2] + dt6 * acc[a];
         }
         store9(fs_out, np, i, f3);
+    } else if (STAGE == 4) {
+        // explicit Euler (comparison scheme): f^{n+1} = f^n + dt [Gamma^a + Gamma^c](f^n)
+        T eq[kQ], fnew[kQ], dr, r, u, v;
+        moments(fi, rho0, dr, r, u, v);
+        feq_dev(dr, r, u, v, eq);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) fnew[a] = fi[a] + dt * (-acc[a] + (eq[a] - fi[a]) * itau);
+        store9(fs_out, np, i, fnew);
+        moments(fnew, rho0, dr, r, u, v);
+        if (STATS) {
+            const double uo = double(mac[1 * np + i]), vo = double(mac[2 * np + i]);
+            const double un = double(u), vn = double(v);
+            const bool bad = !(isfinite(un) && isfinite(vn) && isfinite(double(r)));
+            double s[4] = {(un - uo) * (un - uo) + (vn - vo) * (vn - vo), un * un + vn * vn,
+                           double(r) * double(area[i]), bad ? 1.0 : 0.0};
+            block_sum<4, NT>(s, partial + 4 * blockIdx.x);
+        }
+        mac[0 * np + i] = r;
+        mac[1 * np + i] = u;
+        mac[2 * np + i] = v;
     } else {
         T fnew[kQ], dr, r, u, v;
 #pragma unroll
@@ -1054,6 +1075,7 @@ struct fvlbm_handle {
     int *d_perm = nullptr, *d_inst_tile0 = nullptr, *d_inst_blk0 = nullptr;
     // fused path: per-block halo lists and local adjacency
     bool fused = false;
+    int scheme = 0;   // 0: IMEX Runge-Kutta; 1: explicit Euler (comparison scheme)
     int nblk = 0, emax = 0, gmax = 0;
     size_t fused_smem = 0;
     int *d_halo_ptr = nullptr, *d_halo = nullptr, *d_r1 = nullptr, *d_adj_ptr = nullptr;
@@ -1161,7 +1183,7 @@ void launch(fvlbm_handle *h, int id, const char *name, F &&fn) {
 
 enum KernelId {
     K_SST_GRAD, K_SST_UPDATE, K_STAGE1, K_GRAD, K_FLUX1, K_FLUX2, K_FLUX3, K_REDUCE,
-    K_FUSED1, K_FUSED2, K_FUSED3
+    K_FUSED1, K_FUSED2, K_FUSED3, K_EULER
 };
 
 template <class T>
@@ -1185,6 +1207,23 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
                                                    h->fused ? static_cast<T *>(h->frel) : nullptr);
         });
         h->turb = n;
+    }
+    if (h->scheme == 1) {  // explicit Euler: gradient, flux + collision into s0, copy back
+        launch(h, K_GRAD, "grad_f", [&] { k_grad<T><<<grid, block, 0, s>>>(fn, g, G); });
+        if (stats) {
+            launch(h, K_EULER, "euler", [&] {
+                k_flux_stage<T, 4, true><<<grid, block, 0, s>>>(fn, g, s0, fn, B, C, tau, mac, h->d_partial, G);
+            });
+            launch(h, K_REDUCE, "reduce", [&] {
+                k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->d_inst_tile0, h->d_inst_sums);
+            });
+        } else {
+            launch(h, K_EULER, "euler", [&] {
+                k_flux_stage<T, 4, false><<<grid, block, 0, s>>>(fn, g, s0, fn, B, C, tau, mac, nullptr, G);
+            });
+        }
+        cudaMemcpyAsync(fn, s0, sizeof(T) * kQ * static_cast<size_t>(h->np), cudaMemcpyDeviceToDevice, s);
+        return;
     }
     if (h->fused) {
         Halo H{h->d_halo_ptr, h->d_halo, h->d_r1, h->d_adj_ptr, h->d_adj, h->d_err, h->emax, h->gmax};
@@ -1242,7 +1281,9 @@ void enqueue(fvlbm_handle *h, bool stats) {
         enqueue_step<float>(h, stats);
 }
 
-int launches_per_step(const fvlbm_handle *h) { return (h->sst ? 2 : 0) + (h->fused ? 3 : 7); }
+int launches_per_step(const fvlbm_handle *h) {
+    return (h->sst ? 2 : 0) + (h->scheme == 1 ? 2 : (h->fused ? 3 : 7));
+}
 
 // Capture `nsteps` plain steps into an executable graph.  A replay always starts from the
 // k / omega / nu_t ping-pong parity the graph was captured with, and an even step count ends
@@ -1484,7 +1525,8 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     int sst = 0;
     if (prec != FVLBM_FP64 && prec != FVLBM_FP32_DEV) return FVLBM_ERR_BAD_PARAM;
     for (int q = 0; q < n; ++q) {
-        if (params[q].precision != prec) return FVLBM_ERR_BAD_PARAM;
+        if (params[q].precision != prec || params[q].scheme != params[0].scheme)
+            return FVLBM_ERR_BAD_PARAM;
         sst |= params[q].sst ? 1 : 0;
     }
     std::vector<std::unique_ptr<Prepared>> prep(n);
@@ -1507,7 +1549,9 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     CK(cudaSetDevice(device));
     h->precision = prec;
     h->sst = sst != 0;
-    h->fused = params[0].kernel_path == 0;
+    h->scheme = params[0].scheme;
+    if (h->scheme != 0 && h->scheme != 1) return FVLBM_ERR_BAD_PARAM;
+    h->fused = params[0].kernel_path == 0 && h->scheme == 0;
     h->ninst = n;
     int cell_off = 0, bface_off = 0;
     std::vector<int> tile_inst, inst_tile0;

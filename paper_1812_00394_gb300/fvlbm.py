@@ -18,6 +18,8 @@ FVLBM_OK = 0
 FVLBM_ERR_DIVERGED = -6
 FVLBM_FP64 = 0
 FVLBM_FP32_DEV = 1
+SCHEME_IMEX = 0
+SCHEME_EULER = 1
 Q = 9
 
 
@@ -43,7 +45,7 @@ class fvlbm_params(C.Structure):
                 ("sst", C.c_int), ("precision", C.c_int), ("uref", C.c_double),
                 ("lref", C.c_double), ("alpha_deg", C.c_double), ("rho_init", C.c_void_p),
                 ("u_init", C.c_void_p), ("v_init", C.c_void_p), ("k_init", C.c_void_p),
-                ("omega_init", C.c_void_p), ("kernel_path", C.c_int)]
+                ("omega_init", C.c_void_p), ("kernel_path", C.c_int), ("scheme", C.c_int)]
 
 
 class fvlbm_stats(C.Structure):
@@ -226,7 +228,7 @@ def fvlbm_strerror(code: int) -> str:
 class _Pack:
     """Keeps the numpy arrays alive that a (mesh, bc, params) triple points into."""
 
-    def __init__(self, case, precision: int, kernel_path: int = 0):
+    def __init__(self, case, precision: int, kernel_path: int = 0, scheme: int = 0):
         m = case.mesh.normalized()
         rho, u, v, k, w = case.init_arrays()
         self.keep = (m, rho, u, v, k, w)
@@ -235,17 +237,17 @@ class _Pack:
                            m.periodic_pairs.shape[0], _p(m.periodic_pairs), _p(m.periodic_shift))
         self.params = fvlbm_params(case.nu, case.rho0, case.dt, case.cfl, int(bool(case.sst)),
                                    precision, case.uref, case.lref, case.alpha_deg, _p(rho), _p(u),
-                                   _p(v), _p(k), _p(w), kernel_path)
+                                   _p(v), _p(k), _p(w), kernel_path, scheme)
 
 
 class Solver:
     """One handle over one case or a batch of cases (``meshgen.Case``)."""
 
     def __init__(self, cases, precision: int = FVLBM_FP64, device: int = -1,
-                 stream: int | None = None, kernel_path: int = 0):
+                 stream: int | None = None, kernel_path: int = 0, scheme: int = 0):
         if not isinstance(cases, (list, tuple)):
             cases = [cases]
-        packs = [_Pack(c, precision, kernel_path) for c in cases]
+        packs = [_Pack(c, precision, kernel_path, scheme) for c in cases]
         if len(packs) == 1:
             self.h = fvlbm_create(packs[0].mesh, packs[0].bc, packs[0].params, device, stream)
         else:

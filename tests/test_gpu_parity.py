@@ -231,3 +231,38 @@ def test_handles_with_different_halo_sizes_coexist():
     small.close()
     big.step(3, stats=True)
     assert np.isfinite(big.fields()["u"]).all()
+
+
+# ----------------------------------------------------------------- explicit Euler comparison
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-10), (FP32, 1e-5)])
+def test_euler_scheme_parity(prec, tol):
+    """The explicit Euler comparison scheme (Part I) against the oracle's, laminar and SST."""
+    for case in (mg.Case(mg.couette_channel(16, 24, kind="tri", jitter=0.2, seed=6), nu=0.02,
+                         cfl=0.4), mg.bfs_hybrid(n_target=2500)):
+        tau = case.nu / (1.0 / 3.0)
+        if case.sst:
+            case.dt, case.cfl = 1.5 * tau, 0.0      # explicit collision limit dt < 2 tau
+        s = fvlbm.Solver(case, precision=prec, device=0, scheme=fvlbm.SCHEME_EULER)
+        o = Oracle(case, scheme=1)
+        s.step(6)
+        o.step(6)
+        assert _rel_max(s.get_f(), o.get_f()) < tol, case.name
+
+
+def test_explicit_collision_limit_vs_imex():
+    """Sec. 3.1 / 4.1: the explicit scheme needs dt < 2 tau; the IMEX scheme does not.  On the
+    same cavity the explicit run at dt = 1.8 tau stays bounded and at dt = 2.4 tau blows up,
+    while IMEX runs stably at 2.4 tau and at 30 tau."""
+    def run(z, scheme, steps=300):
+        base = mg.cavity_quad(24, re=1000.0)
+        nu = base.nu                       # tau = 3e-4: even dt = 30 tau keeps convective CFL < 0.5
+        tau = nu / (1.0 / 3.0)
+        case = mg.Case(base.mesh, nu=nu, dt=z * tau, rho=base.rho, uref=0.1)
+        s = fvlbm.Solver(case, precision=FP64, device=0, scheme=scheme)
+        st = s.step(steps, stats=True)
+        return st["diverged"] == 1 or not np.isfinite(st["residual"]) or \
+            np.abs(s.fields()["u"]).max() > 1.0
+    assert not run(1.8, fvlbm.SCHEME_EULER)
+    assert run(2.4, fvlbm.SCHEME_EULER)
+    assert not run(2.4, fvlbm.SCHEME_IMEX)
+    assert not run(30.0, fvlbm.SCHEME_IMEX, steps=100)

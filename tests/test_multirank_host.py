@@ -1,0 +1,63 @@
+"""Host logic of the multi-GPU benchmark path on CPU: two gloo ranks.
+
+Each rank advances its own seeded copy of the sweep (weak scaling, no data exchange); the only
+collective is the max over ranks of the timed region.  Here the ranks use the gloo backend and
+the oracle-free host pieces of bench.py.
+"""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # a rank-dependent "elapsed time": the reported value must be the slowest rank's
+        ms = 10.0 + 5.0 * rank
+        got = bench.max_over_ranks(torch, dist, world, ms, device="cpu")
+        seed = bench.rank_seed(rank)
+        seeds = [None] * world
+        dist.all_gather_object(seeds, seed)
+        out[rank] = (got, seeds)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_max_time_and_distinct_seeds():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.start_processes(_worker, args=(world, port, out), nprocs=world, start_method="spawn")
+        res = dict(out)
+    assert res[0][0] == res[1][0] == 15.0            # max over ranks, seen by every rank
+    assert len(set(res[0][1])) == world               # every rank its own sweep
+
+
+def test_single_rank_is_identity_and_rate():
+    assert bench.max_over_ranks(torch, None, 1, 3.5) == 3.5
+    # 1000 cells, 2 ranks, 10 steps in 2 ms -> 10 Mcell-steps/s
+    assert abs(bench.aggregate_rate(1000, 2, 10, 2.0) - 10.0) < 1e-12
+
+
+@pytest.mark.parametrize("rank", [0, 1, 3])
+def test_rank_workloads_differ_but_are_seeded(rank):
+    from paper_1812_00394_gb300 import meshgen as mg
+    a = mg.batched_sweep(seed=bench.rank_seed(rank), scale=0.02, n_cavity=2, n_bfs=0, n_naca=0)
+    b = mg.batched_sweep(seed=bench.rank_seed(rank), scale=0.02, n_cavity=2, n_bfs=0, n_naca=0)
+    assert [c.mesh.n_cells for c in a] == [c.mesh.n_cells for c in b]
+    assert all((x.mesh.xy == y.mesh.xy).all() for x, y in zip(a, b))

@@ -298,3 +298,30 @@ def test_sst_with_zero_k_is_laminar():
     b.step(20)
     assert np.array_equal(a.get_f(), b.get_f())
     assert np.all(b.fields()["nut"] == 0.0)
+
+
+# ----------------------------------------------------------------- explicit Euler (Part I)
+@pytest.mark.parametrize("z", [0.5, 1.5, 2.5])
+def test_euler_relaxation_factor(z):
+    """The explicit scheme of Part I multiplies f^neq of a uniform field by 1 - z per step: it is
+    stable only for dt < 2 tau (Sec. 3.1), which the IMEX tableau removes (R(z) -> 0)."""
+    m = _box_at_rest()
+    dt = 0.01
+    o = Oracle(mg.Case(m, nu=CS2 * dt / z, dt=dt), scheme=1)
+    eq = feq(1.0, 0.0, 0.0)
+    delta = 1e-3 * eq * (EX ** 2 - EY ** 2)
+    o.set_f(np.tile(eq + delta, (o.n_cells, 1)))
+    o.step(1)
+    np.testing.assert_allclose(o.get_f() - eq, np.tile((1 - z) * delta, (o.n_cells, 1)),
+                               rtol=0, atol=1e-16 * (10 + z))
+
+
+def test_euler_couette_matches_imex_steady_state():
+    """Both integrators have the same steady state (the spatial operator is shared): Couette
+    flow (CFL 0.5, dt = 0.28 tau) converges to u = U y / H with the explicit scheme too."""
+    U, H, nu = 0.1, 1.0, 0.05
+    m = mg.couette_channel(4, 8, U=U, H=H, Lx=1.0)
+    o = Oracle(mg.Case(m, nu=nu, cfl=0.5, uref=U), scheme=1)
+    o.step(int(3 * H * H / nu / o.dt))
+    g, fl = o.geometry(), o.fields()
+    assert np.abs(fl["u"] - U * g["cy"] / H).max() < 1e-9
