@@ -289,6 +289,7 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
     P.gq.assign(8 * np, 0.0);
     P.sn.assign(8 * np, 0.0);
     P.lsq.assign(8 * np, 0.0);
+    P.dvec.assign(8 * np, 0.0);
     P.rown.assign(8 * np, 0.0);
     P.rnbr.assign(8 * np, 0.0);
     P.dinv.assign(4 * np, 0.0);
@@ -336,6 +337,8 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
             return FVLBM_ERR_BAD_MESH;
         }
         for (int l = 0; l < nv; ++l) {
+            P.dvec[(2 * l) * np + k] = dx[l];
+            P.dvec[(2 * l + 1) * np + k] = dy[l];
             P.lsq[(2 * l) * np + k] = (myy * dx[l] - mxy * dy[l]) / det;
             P.lsq[(2 * l + 1) * np + k] = (mxx * dy[l] - mxy * dx[l]) / det;
         }

@@ -38,6 +38,8 @@ struct Prepared {
                                 //         face m joins nodes m and (m + 1) mod nface
     std::vector<double> sn;     // [8 np]  n * Delta l / A of face m, out of the cell
     std::vector<double> lsq;    // [8 np]  least-squares weight W_m = M^{-1} d_m
+    std::vector<double> dvec;   // [8 np]  d_m: neighbour centroid (+ shift) or face midpoint,
+                                //         minus own centroid
     std::vector<double> rown;   // [8 np]  face midpoint - own centroid
     std::vector<double> rnbr;   // [8 np]  face midpoint - (neighbour centroid + periodic shift)
     std::vector<double> dinv;   // [4 np]  1 / |d_m| (SST central diffusion distance)

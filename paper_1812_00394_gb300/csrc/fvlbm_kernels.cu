@@ -430,6 +430,17 @@ struct Halo {
     int emax, gmax;                     // smem row strides: max ext cells, max gradient cells
 };
 
+// Compact geometry of the fused kernels: per cell the node positions relative to the centroid
+// (gq, face m joins nodes m and m+1) and, per face slot, d_m = neighbour centroid (periodic
+// shift included) or face midpoint, minus the own centroid.  Everything else is derived:
+// area and n dl / A from gq, the face offset r_m = face midpoint - centroid from gq, the
+// neighbour's offset r_m - d_m, and the least-squares weights M^{-1} d_m.
+template <class T>
+struct CompactGeo {
+    const T *__restrict__ gq;    // [8 np]
+    const T *__restrict__ dv;    // [8 np]
+};
+
 // ---- asynchronous staging primitives (sm_90+ bulk copy engine and cp.async)
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -488,7 +499,7 @@ __device__ __forceinline__ void face_geo_s(const T *q, int ld, int m, int nv, T 
 // Shared-memory layout of the fused kernel (element offsets, every row 16-byte aligned):
 //   sf  [9][emax]   f^(J) of block, ring-1 and ring-2 cells
 //   sg  [16][gmax]  gradients (alpha = 1..8) of block and ring-1 cells
-//   sW  [8][gmax]   least-squares weights of block and ring-1 cells
+//   sD  [8][gmax]   neighbour-centroid offsets d_m of block and ring-1 cells
 //   adj [4 gmax] words, then one 8-byte mbarrier
 constexpr int kFusedThreads = kBlock;
 
@@ -516,13 +527,13 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
     k_fused_stage(const T *__restrict__ fin, T *__restrict__ fs_out, T *__restrict__ fn,
                   T *__restrict__ Bacc, T *__restrict__ Cacc, const T *__restrict__ tau,
                   T *__restrict__ mac, double *__restrict__ partial, Geo<T> G, Halo H,
-                  T *__restrict__ frel) {
+                  T *__restrict__ frel, CompactGeo<T> CG) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int E0 = H.emax, G0 = H.gmax;
     T *sf = reinterpret_cast<T *>(smem_raw);
     T *sg = sf + kQ * E0;
-    T *sW = sg + 16 * G0;
-    unsigned *sAdj = reinterpret_cast<unsigned *>(sW + 8 * G0);
+    T *sD = sg + 16 * G0;
+    unsigned *sAdj = reinterpret_cast<unsigned *>(sD + 8 * G0);
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(sAdj + 4 * G0);
 
     const int b = blockIdx.x, t = threadIdx.x;
@@ -543,7 +554,7 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
         const unsigned adj_bytes = 4u * NG * sizeof(unsigned);
         mbar_expect_tx(bar, row * (kQ + 8) + adj_bytes);
         for (int a = 0; a < kQ; ++a) bulk_g2s(sf + a * E0, fin + a * np + base, row, bar);
-        for (int k = 0; k < 8; ++k) bulk_g2s(sW + k * G0, G.lsq + k * np + base, row, bar);
+        for (int k = 0; k < 8; ++k) bulk_g2s(sD + k * G0, CG.dv + k * np + base, row, bar);
         bulk_g2s(sAdj, adj_g, adj_bytes, bar);
     }
     for (int e = kBlock + t; e < E; e += kFusedThreads) {  // halo rows
@@ -552,11 +563,11 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
         for (int a = 0; a < kQ; ++a) cp_async<sizeof(T)>(sf + a * E0 + e, fin + a * np + gid);
         if (e < NG) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) cp_async<sizeof(T)>(sW + k * G0 + e, G.lsq + k * np + gid);
+            for (int k = 0; k < 8; ++k) cp_async<sizeof(T)>(sD + k * G0 + e, CG.dv + k * np + gid);
         }
     }
-    // this thread's accumulators, tau and face normals (n dl / A), straight into registers
-    T a1[kQ], a2[kQ], sn[8];
+    // this thread's accumulators, tau and node positions, straight into registers
+    T a1[kQ], a2[kQ], q[8];
     const T tau_i = tau[i];
     {
         if (STAGE != 1) {
@@ -569,7 +580,7 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
             for (int a = 0; a < kQ; ++a) a2[a] = Cacc[a * np + i];
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) sn[k] = G.sn[k * np + i];
+        for (int k = 0; k < 8; ++k) q[k] = CG.gq[k * np + i];
     }
     cp_async_wait_all();
     {
@@ -593,11 +604,23 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
             fc[a] = sf[a * E0 + c];
             gx[a] = gy[a] = T(0);
         }
+        // least-squares matrix M = sum_m d_m d_m^T of this cell, inverted once
+        T mxx = 0, mxy = 0, myy = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            if (sAdj[m * NG + c] == kAdjNone) continue;
+            const T dx = sD[(2 * m) * G0 + c], dy = sD[(2 * m + 1) * G0 + c];
+            mxx += dx * dx;
+            mxy += dx * dy;
+            myy += dy * dy;
+        }
+        const T idet = T(1) / (mxx * myy - mxy * mxy);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const unsigned w = sAdj[m * NG + c];
             if (w == kAdjNone) continue;
-            const T wx = sW[(2 * m) * G0 + c], wy = sW[(2 * m + 1) * G0 + c];
+            const T dx = sD[(2 * m) * G0 + c], dy = sD[(2 * m + 1) * G0 + c];
+            const T wx = (myy * dx - mxy * dy) * idet, wy = (mxx * dy - mxy * dx) * idet;
             if (w & kAdjBnd) {
                 const int bf = static_cast<int>(w & ~kAdjBnd);
                 // outward face normal (n dl / A) for the far-field upwind choice
@@ -638,11 +661,22 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
         fi[a] = sf[a * E0 + t];
         acc[a] = T(0);
     }
+    const bool tri = sAdj[3 * NG + t] == kAdjNone;
+    // end node of face m (m compile-time): node m + 1, wrapping to node 0 after the last face
+    auto end_x = [&](int m) { return m == 3 ? q[0] : (m == 2 && tri ? q[0] : q[2 * m + 2]); };
+    auto end_y = [&](int m) { return m == 3 ? q[1] : (m == 2 && tri ? q[1] : q[2 * m + 3]); };
+    T a2x = T(0);  // twice the area (shoelace on centroid-relative nodes)
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        if (m < 3 || !tri) a2x += q[2 * m] * end_y(m) - end_x(m) * q[2 * m + 1];
+    const T inv_a = a2x > T(0) ? T(2) / a2x : T(0);  // padding cells have no faces
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const unsigned w = sAdj[m * NG + t];
         if (w == kAdjNone) continue;
-        const T snx = sn[2 * m], sny = sn[2 * m + 1];
+        const T x1 = end_x(m), y1 = end_y(m);
+        const T snx = (y1 - q[2 * m + 1]) * inv_a;   // n dl / A
+        const T sny = -(x1 - q[2 * m]) * inv_a;
         if (w & kAdjBnd) {
             const int bf = static_cast<int>(w & ~kAdjBnd);
             T dr, r, u, v, fb[kQ];
@@ -652,9 +686,9 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
             for (int a = 1; a < kQ; ++a) acc[a] += (T(ex_of(a)) * snx + T(ey_of(a)) * sny) * fb[a];
         } else {
             const int j = static_cast<int>(w & 0xFFFFu);
-            // face offsets from this cell's and from the neighbour's centroid (precomputed)
-            const T rox = G.rown[(2 * m) * np + i], roy = G.rown[(2 * m + 1) * np + i];
-            const T rnx = G.rnbr[(2 * m) * np + i], rny = G.rnbr[(2 * m + 1) * np + i];
+            // face offsets from this cell's centroid and from the neighbour's
+            const T rox = T(0.5) * (q[2 * m] + x1), roy = T(0.5) * (q[2 * m + 1] + y1);
+            const T rnx = rox - sD[(2 * m) * G0 + t], rny = roy - sD[(2 * m + 1) * G0 + t];
 #pragma unroll
             for (int a = 1; a < kQ; ++a) {
                 const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
@@ -1081,7 +1115,8 @@ struct fvlbm_handle {
     int *d_halo_ptr = nullptr, *d_halo = nullptr, *d_r1 = nullptr, *d_adj_ptr = nullptr;
     unsigned *d_adj = nullptr;
     int *d_err = nullptr;   // device error flag (a staging wait gave up)
-    void *gq = nullptr;
+    void *gq = nullptr;     // fused path: node positions minus centroid [8 np]
+    void *dvec = nullptr;   // fused path: neighbour-centroid offsets d_m [8 np]
     InstParam *d_ip = nullptr;
     void *sn = nullptr, *lsq = nullptr, *rown = nullptr, *rnbr = nullptr, *dinv = nullptr;
     void *area = nullptr, *wdist = nullptr, *bval = nullptr, *bnrm = nullptr, *blen = nullptr;
@@ -1229,23 +1264,24 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         Halo H{h->d_halo_ptr, h->d_halo, h->d_r1, h->d_adj_ptr, h->d_adj, h->d_err, h->emax, h->gmax};
         const dim3 fg(h->nblk), fb(kFusedThreads);
         T *fr = static_cast<T *>(h->frel);
+        const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
         const size_t sm = h->fused_smem;
         launch(h, K_FUSED1, "fused_stage1", [&] {
-            k_fused_stage<T, 1, false><<<fg, fb, sm, s>>>(fr, s1, fn, B, C, tau, mac, nullptr, G, H, fr);
+            k_fused_stage<T, 1, false><<<fg, fb, sm, s>>>(fr, s1, fn, B, C, tau, mac, nullptr, G, H, fr, CG);
         });
         launch(h, K_FUSED2, "fused_stage2", [&] {
-            k_fused_stage<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, H, fr);
+            k_fused_stage<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, H, fr, CG);
         });
         if (stats) {
             launch(h, K_FUSED3, "fused_stage3", [&] {
-                k_fused_stage<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, H, fr);
+                k_fused_stage<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, H, fr, CG);
             });
             launch(h, K_REDUCE, "reduce", [&] {
                 k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->d_inst_blk0, h->d_inst_sums);
             });
         } else {
             launch(h, K_FUSED3, "fused_stage3", [&] {
-                k_fused_stage<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, H, fr);
+                k_fused_stage<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, H, fr, CG);
             });
         }
         return;
@@ -1417,7 +1453,7 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
     // geometry, concatenated over instances with neighbour / boundary ids offset
     std::vector<int> nbr(4 * np, kNone), back(4 * np, -1), nface(np, 0);
     std::vector<int> btype(h->nbt), bowner(h->nbt), perm;
-    std::vector<double> gq(8 * np, 0);
+    std::vector<double> gq(8 * np, 0), dvec(8 * np, 0);
     std::vector<double> sn(8 * np, 0), lsq(8 * np, 0), rown(8 * np, 0), rnbr(8 * np, 0);
     std::vector<double> dinv(4 * np, 0), area(np, 0), wdist(np, 1e30);
     std::vector<double> bval(5 * static_cast<size_t>(h->nbt)), bnrm(2 * static_cast<size_t>(h->nbt));
@@ -1441,6 +1477,7 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
                 rown[c * np + o + k] = p.rown[c * pn + k];
                 rnbr[c * np + o + k] = p.rnbr[c * pn + k];
                 gq[c * np + o + k] = p.gq[c * pn + k];
+                dvec[c * np + o + k] = p.dvec[c * pn + k];
             }
         for (size_t k = 0; k < pn; ++k) nface[o + k] = p.nface[k];
         for (size_t k = 0; k < pn; ++k) {
@@ -1479,6 +1516,10 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
     if ((rc = upload_as<T>(h, &h->bval, bval))) return rc;
     if ((rc = upload_as<T>(h, &h->bnrm, bnrm))) return rc;
     if ((rc = upload_as<T>(h, &h->blen, blen))) return rc;
+    if (h->fused) {
+        if ((rc = upload_as<T>(h, &h->gq, gq))) return rc;
+        if ((rc = upload_as<T>(h, &h->dvec, dvec))) return rc;
+    }
     if (h->fused && (rc = build_halos<T>(h, nbr, back, nface))) return rc;
     {
         std::vector<double> kt(k0), wt(w0);
