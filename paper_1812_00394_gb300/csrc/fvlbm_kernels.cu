@@ -876,10 +876,52 @@ __device__ __forceinline__ void sst_cell_update(const InstParam &P, T ui, T vi, 
 
 // ---- two-pass SST kernels (one thread per cell, neighbours gathered from global memory)
 // Gradients of u, v, k, omega, the limited k / omega gradients and f1.
+// Face geometry of cell i from the compact arrays (node positions gq, offsets d): face offset
+// r_m, outward n dl / A, neighbour offset r_m - d_m, 1 / |d_m| and the least-squares weights.
 template <class T>
+__device__ __forceinline__ void compact_face_geo(const CompactGeo<T> &CG, size_t np, int i,
+                                                 const bool *has, T *R, T *SN, T *RN, T *DI,
+                                                 T *W) {
+    T q[8], d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        q[k] = CG.gq[k * np + i];
+        d[k] = CG.dv[k * np + i];
+    }
+    const bool tri = !has[3];
+    auto end_x = [&](int m) { return m == 3 ? q[0] : (m == 2 && tri ? q[0] : q[2 * m + 2]); };
+    auto end_y = [&](int m) { return m == 3 ? q[1] : (m == 2 && tri ? q[1] : q[2 * m + 3]); };
+    T a2x = T(0), mxx = 0, mxy = 0, myy = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (m < 3 || !tri) a2x += q[2 * m] * end_y(m) - end_x(m) * q[2 * m + 1];
+        if (has[m]) {
+            mxx += d[2 * m] * d[2 * m];
+            mxy += d[2 * m] * d[2 * m + 1];
+            myy += d[2 * m + 1] * d[2 * m + 1];
+        }
+    }
+    const T inv_a = a2x > T(0) ? T(2) / a2x : T(0);
+    const T idet = T(1) / (mxx * myy - mxy * mxy);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const T x1 = end_x(m), y1 = end_y(m);
+        R[2 * m] = T(0.5) * (q[2 * m] + x1);
+        R[2 * m + 1] = T(0.5) * (q[2 * m + 1] + y1);
+        SN[2 * m] = (y1 - q[2 * m + 1]) * inv_a;
+        SN[2 * m + 1] = -(x1 - q[2 * m]) * inv_a;
+        RN[2 * m] = R[2 * m] - d[2 * m];
+        RN[2 * m + 1] = R[2 * m + 1] - d[2 * m + 1];
+        DI[m] = has[m] ? T(1) / sqrt(d[2 * m] * d[2 * m] + d[2 * m + 1] * d[2 * m + 1]) : T(0);
+        W[2 * m] = (myy * d[2 * m] - mxy * d[2 * m + 1]) * idet;
+        W[2 * m + 1] = (mxx * d[2 * m + 1] - mxy * d[2 * m]) * idet;
+    }
+}
+
+template <class T, bool COMPACT>
 __global__ void __launch_bounds__(kTile)
     k_sst_grad(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
-               T *__restrict__ grads, T *__restrict__ f1out, Geo<T> G) {
+               T *__restrict__ grads, T *__restrict__ f1out, Geo<T> G, CompactGeo<T> CG) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -888,15 +930,28 @@ __global__ void __launch_bounds__(kTile)
     const T own[4] = {mac[np + i], mac[2 * np + i], kk[i], ww[i]};
     const T di = G.wdist[i];
     bool has[4];
+    int nbs[4];
     T q[4][4], W[8], R[8];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const int nb = G.nbr[m * np + i];
-        has[m] = nb != kNone;
-        W[2 * m] = G.lsq[(2 * m) * np + i];
-        W[2 * m + 1] = G.lsq[(2 * m + 1) * np + i];
-        R[2 * m] = G.rown[(2 * m) * np + i];
-        R[2 * m + 1] = G.rown[(2 * m + 1) * np + i];
+        nbs[m] = G.nbr[m * np + i];
+        has[m] = nbs[m] != kNone;
+    }
+    if (COMPACT) {
+        T SN[8], RN[8], DI[4];
+        compact_face_geo(CG, np, i, has, R, SN, RN, DI, W);
+    } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            W[2 * m] = G.lsq[(2 * m) * np + i];
+            W[2 * m + 1] = G.lsq[(2 * m + 1) * np + i];
+            R[2 * m] = G.rown[(2 * m) * np + i];
+            R[2 * m + 1] = G.rown[(2 * m + 1) * np + i];
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int nb = nbs[m];
         if (nb == kNone) continue;
         if (nb >= 0) {
             q[m][0] = mac[np + nb]; q[m][1] = mac[2 * np + nb]; q[m][2] = kk[nb]; q[m][3] = ww[nb];
@@ -915,13 +970,13 @@ __global__ void __launch_bounds__(kTile)
 }
 
 // The k / omega update and the new relaxation time (and, on the fused path, f^(1)).
-template <class T>
+template <class T, bool COMPACT>
 __global__ void __launch_bounds__(kTile)
     k_sst_update(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
                  const T *__restrict__ nut, const T *__restrict__ grads,
                  const T *__restrict__ f1a, T *__restrict__ k_out, T *__restrict__ w_out,
                  T *__restrict__ nut_out, T *__restrict__ tau, Geo<T> G,
-                 const T *__restrict__ fn, T *__restrict__ frel) {
+                 const T *__restrict__ fn, T *__restrict__ frel, CompactGeo<T> CG) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -935,19 +990,40 @@ __global__ void __launch_bounds__(kTile)
 #pragma unroll
     for (int c = 0; c < 4; ++c) lgi[c] = grads[(8 + c) * np + i];
     SstFace<T> F[4];
+    int nbs[4];
+    bool has[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-        const int nb = G.nbr[m * np + i];
+        nbs[m] = G.nbr[m * np + i];
+        has[m] = nbs[m] != kNone;
+    }
+    T R[8], SN[8], RN[8], DI[4];
+    if (COMPACT) {
+        T W[8];
+        compact_face_geo(CG, np, i, has, R, SN, RN, DI, W);
+    } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            if (!has[m]) continue;
+            SN[2 * m] = G.sn[(2 * m) * np + i]; SN[2 * m + 1] = G.sn[(2 * m + 1) * np + i];
+            R[2 * m] = G.rown[(2 * m) * np + i]; R[2 * m + 1] = G.rown[(2 * m + 1) * np + i];
+            RN[2 * m] = G.rnbr[(2 * m) * np + i]; RN[2 * m + 1] = G.rnbr[(2 * m + 1) * np + i];
+            DI[m] = G.dinv[m * np + i];
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int nb = nbs[m];
         SstFace<T> &f = F[m];
-        f.has = nb != kNone;
+        f.has = has[m];
         if (!f.has) continue;
         f.bnd = nb < 0;
-        f.snx = G.sn[(2 * m) * np + i]; f.sny = G.sn[(2 * m + 1) * np + i];
-        f.rox = G.rown[(2 * m) * np + i]; f.roy = G.rown[(2 * m + 1) * np + i];
-        f.dinv = G.dinv[m * np + i];
+        f.snx = SN[2 * m]; f.sny = SN[2 * m + 1];
+        f.rox = R[2 * m]; f.roy = R[2 * m + 1];
+        f.dinv = DI[m];
         if (nb >= 0) {
             f.u = mac[np + nb]; f.v = mac[2 * np + nb]; f.k = kk[nb]; f.w = ww[nb];
-            f.rnx = G.rnbr[(2 * m) * np + i]; f.rny = G.rnbr[(2 * m + 1) * np + i];
+            f.rnx = RN[2 * m]; f.rny = RN[2 * m + 1];
 #pragma unroll
             for (int c = 0; c < 4; ++c) f.lg[c] = grads[(8 + c) * np + nb];
             f.f1 = f1a[nb];
@@ -1236,11 +1312,24 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         T *kn = static_cast<T *>(h->kk[n]), *wn = static_cast<T *>(h->ww[n]);
         T *nn = static_cast<T *>(h->nut[n]);
         T *sg = static_cast<T *>(h->sgrad), *f1 = static_cast<T *>(h->f1);
-        launch(h, K_SST_GRAD, "sst_grad", [&] { k_sst_grad<T><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G); });
-        launch(h, K_SST_UPDATE, "sst_update", [&] {
-            k_sst_update<T><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn,
-                                                   h->fused ? static_cast<T *>(h->frel) : nullptr);
-        });
+        const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
+        if (h->fused) {  // compact geometry, and stage 1's f^(1) with the new tau
+            launch(h, K_SST_GRAD, "sst_grad", [&] {
+                k_sst_grad<T, true><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG);
+            });
+            launch(h, K_SST_UPDATE, "sst_update", [&] {
+                k_sst_update<T, true><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn,
+                                                             static_cast<T *>(h->frel), CG);
+            });
+        } else {
+            launch(h, K_SST_GRAD, "sst_grad", [&] {
+                k_sst_grad<T, false><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG);
+            });
+            launch(h, K_SST_UPDATE, "sst_update", [&] {
+                k_sst_update<T, false><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn,
+                                                              nullptr, CG);
+            });
+        }
         h->turb = n;
     }
     if (h->scheme == 1) {  // explicit Euler: gradient, flux + collision into s0, copy back

@@ -93,3 +93,18 @@ def test_splitmix64_reference_values():
     words = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
     expect = np.array([2.0 * ((w >> 11) * 2.0 ** -53) - 1.0 for w in words])
     assert np.array_equal(u, expect)
+
+
+def test_rejects_empty_mesh():
+    m = mg.Mesh(np.zeros((3, 2)), np.zeros(1, np.int32), np.zeros(0, np.int32),
+                np.zeros((0, 2), np.int32), np.zeros(0, np.int32), np.zeros((0, 5)))
+    assert _create(mg.Case(m, nu=1e-3, dt=1e-3)) == -1
+
+
+def test_rejects_polygon_with_five_nodes():
+    xy = np.array([[0, 0], [1, 0], [1.5, 0.8], [0.5, 1.4], [-0.4, 0.8]], float)
+    cells = np.arange(5, dtype=np.int32)
+    bn = np.stack([np.arange(5), (np.arange(5) + 1) % 5], 1).astype(np.int32)
+    m = mg.Mesh(xy, np.array([0, 5], np.int32), cells, bn, np.zeros(5, np.int32),
+                np.tile([1.0, 0, 0, 0, 0], (5, 1)))
+    assert _create(mg.Case(m, nu=1e-3, dt=1e-3)) == -1

@@ -266,3 +266,38 @@ def test_explicit_collision_limit_vs_imex():
     assert run(2.4, fvlbm.SCHEME_EULER)
     assert not run(2.4, fvlbm.SCHEME_IMEX)
     assert not run(30.0, fvlbm.SCHEME_IMEX, steps=100)
+
+
+# ----------------------------------------------------------------- degenerate and ragged inputs
+def _single_triangle(lid=0.1):
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.3, 0.9]])
+    bn = np.array([[0, 1], [1, 2], [2, 0]], np.int32)
+    bv = np.tile([1.0, 0.0, 0.0, 0.0, 0.0], (3, 1))
+    bv[1, 1] = lid                                 # one moving wall
+    m = mg.Mesh(xy, np.array([0, 3], np.int32), np.arange(3, dtype=np.int32), bn,
+                np.zeros(3, np.int32), bv).normalized()
+    return mg.Case(m, nu=0.01, cfl=0.4)
+
+
+@pytest.mark.parametrize("path", [0, 1], ids=["fused", "twopass"])
+def test_single_cell_mesh(path):
+    """One triangle with three wall faces (one moving): a block of 255 padding cells and one
+    real cell."""
+    case = _single_triangle()
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=path)
+    o = Oracle(case)
+    s.step(10)
+    o.step(10)
+    assert _rel_max(s.get_f(), o.get_f()) < 1e-12
+
+
+def test_batch_with_tiny_and_ragged_instances():
+    """Instances of 1, 7 x 7 jittered quads and a ~3k Delaunay cavity in one FP32 handle."""
+    cases = [_single_triangle(), mg.cavity_quad(7, re=50.0, jitter=0.2, seed=3),
+             mg.cavity_delaunay(h_boundary=1 / 40, n_target=3000, re=500.0, cfl=0.5, seed=12)]
+    s = fvlbm.Solver(cases, precision=FP32, device=0)
+    s.step(20)
+    for i, c in enumerate(cases):
+        o = Oracle(c)
+        o.step(20)
+        assert _rel_max(s.get_f(i), o.get_f()) < 1e-5, c.name
