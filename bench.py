@@ -251,10 +251,11 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             s = fvlbm.Solver(cases, precision=prec, device=dev, stream=stream.cuda_stream)
             s.step(args.warmup)
+            tuned = s.autotune(3)            # kernel configuration chosen by measurement
             torch.cuda.synchronize()
             with ClockSampler(dev) as clk:
                 ms = _time_steps(torch, s, stream, args.steps, dist, world)
-            results[tag] = {"ms": ms, "clocks": clk.summary()}
+            results[tag] = {"ms": ms, "clocks": clk.summary(), "autotune": tuned}
         solvers[tag] = s
     # the explicit Euler comparison scheme (Sec. 3.1 / 4.1) on the same workload, FP32: cost per
     # step (its stable dt is < 2 tau, the IMEX one is not limited by tau)
@@ -329,6 +330,10 @@ def run_ours(args):
             "step_roofline": {"bytes_per_cell_step": step_bytes / total_cells,
                               "achieved": step_gbs, "peak": hbm, "unit": "GB/s",
                               "frac": step_gbs / hbm, "peak_kind": peak_kind},
+            "autotune": {"fp32": {"chosen": results["f32"]["autotune"][0],
+                                  "ms_per_step": results["f32"]["autotune"][1]},
+                         "fp64": {"chosen": results["f64"]["autotune"][0],
+                                  "ms_per_step": results["f64"]["autotune"][1]}},
             "kernels": {k: {"avg_ms": v["ms"] / v["launches"], "launches": v["launches"]}
                         for k, v in prof.items()},
             "cpu_baseline": cpu,

@@ -159,6 +159,16 @@ int fvlbm_footprint(fvlbm_handle *h, long long *device_bytes, int *launches_per_
 int fvlbm_profile_kernels(fvlbm_handle *h, int n_steps, int max_kernels, char *names,
                           double *ms, int *launches);
 
+/* Kernel autotuner (not in the paper).  Times trial_steps steps of each kernel configuration the
+ * handle supports -- 0: fused stages with 256-cell blocks, 1: fused stages with 128-cell blocks,
+ * 2: two-pass kernels -- on a snapshot of the current state, restores the state exactly, and
+ * keeps the fastest for all later steps.  *chosen (may be NULL) receives the configuration and
+ * ms_per_step[3] (may be NULL) the measured milliseconds per step, -1 for configurations not
+ * available (a block's halo too large for shared memory, kernel_path 1, or the explicit
+ * scheme).  Allocates a temporary snapshot of the state (about 28 words per cell) and
+ * synchronises the stream.  Errors: BAD_PARAM, OOM, CUDA. */
+int fvlbm_autotune(fvlbm_handle *h, int trial_steps, int *chosen, double *ms_per_step);
+
 void fvlbm_destroy(fvlbm_handle *h);
 const char *fvlbm_strerror(int code);
 

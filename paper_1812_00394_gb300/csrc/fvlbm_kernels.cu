@@ -501,7 +501,6 @@ __device__ __forceinline__ void face_geo_s(const T *q, int ld, int m, int nv, T 
 //   sg  [16][gmax]  gradients (alpha = 1..8) of block and ring-1 cells
 //   sD  [8][gmax]   neighbour-centroid offsets d_m of block and ring-1 cells
 //   adj [4 gmax] words, then one 8-byte mbarrier
-constexpr int kFusedThreads = kBlock;
 
 template <class T>
 struct FusedSmem {
@@ -513,7 +512,7 @@ struct FusedSmem {
     }
 };
 
-// One IMEX stage for a block of kBlock cells, one thread per cell.  Staging: the block's own
+// One IMEX stage for a block of BLK cells (BLK = 128 or 256), one thread per cell.  Staging: the block's own
 // rows (contiguous in every SoA array) arrive by bulk copies on one mbarrier; halo rows are
 // gathered with cp.async; each thread's accumulators, tau and face normals go straight into
 // registers; nothing is waited for until everything has been issued.  Then: least-squares
@@ -522,8 +521,8 @@ struct FusedSmem {
 // and no flux.  Stage 1 stages f^(1), which the previous step (laminar instances) or the SST
 // update (turbulent instances, with the new tau) has already relaxed from f^n; stage 3 writes
 // f^(1) of the next step for laminar instances into frel.
-template <class T, int STAGE, bool STATS>
-__global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedThreads) : 1)
+template <class T, int STAGE, bool STATS, int BLK>
+__global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
     k_fused_stage(const T *__restrict__ fin, T *__restrict__ fs_out, T *__restrict__ fn,
                   T *__restrict__ Bacc, T *__restrict__ Cacc, const T *__restrict__ tau,
                   T *__restrict__ mac, double *__restrict__ partial, Geo<T> G, Halo H,
@@ -537,28 +536,28 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(sAdj + 4 * G0);
 
     const int b = blockIdx.x, t = threadIdx.x;
-    const int base = b * kBlock;
+    const int base = b * BLK;
     const int i = base + t;
     const size_t np = G.np;
-    const InstParam P = G.ip[G.tile_inst[b * (kBlock / kTile)]];
+    const InstParam P = G.ip[G.tile_inst[b * (BLK / kTile)]];
     const T rho0 = T(P.rho0);
     const int h0 = H.halo_ptr[b], nh = H.halo_ptr[b + 1] - h0, nr1 = H.r1[b];
-    const int E = kBlock + nh, NG = kBlock + nr1;
+    const int E = BLK + nh, NG = BLK + nr1;
     const unsigned *__restrict__ adj_g = H.adj + 4 * static_cast<size_t>(H.adj_ptr[b]);
 
     // 1. issue every copy of the block's data, then wait once
     if (t == 0) mbar_init(bar);
     __syncthreads();
     if (t == 0) {
-        constexpr unsigned row = kBlock * sizeof(T);
+        constexpr unsigned row = BLK * sizeof(T);
         const unsigned adj_bytes = 4u * NG * sizeof(unsigned);
         mbar_expect_tx(bar, row * (kQ + 8) + adj_bytes);
         for (int a = 0; a < kQ; ++a) bulk_g2s(sf + a * E0, fin + a * np + base, row, bar);
         for (int k = 0; k < 8; ++k) bulk_g2s(sD + k * G0, CG.dv + k * np + base, row, bar);
         bulk_g2s(sAdj, adj_g, adj_bytes, bar);
     }
-    for (int e = kBlock + t; e < E; e += kFusedThreads) {  // halo rows
-        const int gid = H.halo[h0 + e - kBlock];
+    for (int e = BLK + t; e < E; e += BLK) {  // halo rows
+        const int gid = H.halo[h0 + e - BLK];
 #pragma unroll
         for (int a = 0; a < kQ; ++a) cp_async<sizeof(T)>(sf + a * E0 + e, fin + a * np + gid);
         if (e < NG) {
@@ -597,7 +596,7 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
     }
 
     // 2. least-squares gradients (alpha = 1..8) of block and ring-1 cells (Step 2)
-    for (int c = t; c < NG; c += kFusedThreads) {
+    for (int c = t; c < NG; c += BLK) {
         T fc[kQ], gx[kQ], gy[kQ];
 #pragma unroll
         for (int a = 0; a < kQ; ++a) {
@@ -624,7 +623,7 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
             if (w & kAdjBnd) {
                 const int bf = static_cast<int>(w & ~kAdjBnd);
                 // outward face normal (n dl / A) for the far-field upwind choice
-                const int gid = c < kBlock ? base + c : H.halo[h0 + c - kBlock];
+                const int gid = c < BLK ? base + c : H.halo[h0 + c - BLK];
                 const T nx = G.sn[(2 * m) * np + gid], ny = G.sn[(2 * m + 1) * np + gid];
                 T dr, r, u, v, fb[kQ];
                 moments(fc, rho0, dr, r, u, v);
@@ -701,7 +700,7 @@ __global__ void __launch_bounds__(kFusedThreads, sizeof(T) == 4 ? (768 / kFusedT
             }
         }
     }
-    stage_algebra<T, STAGE, STATS, kFusedThreads, true>(i, np, fi, acc, P, tau_i, a1, 1, 0, a2, 1,
+    stage_algebra<T, STAGE, STATS, BLK, true>(i, np, fi, acc, P, tau_i, a1, 1, 0, a2, 1,
                                                         0, fs_out, fn, Bacc, Cacc, mac, partial,
                                                         G.area, frel);
 }
@@ -1182,14 +1181,19 @@ struct fvlbm_handle {
     std::vector<void *> allocs;
     // device arrays (element type T = double or float; stored as void*)
     int *d_nbr = nullptr, *d_tile_inst = nullptr, *d_btype = nullptr, *d_bowner = nullptr;
-    int *d_perm = nullptr, *d_inst_tile0 = nullptr, *d_inst_blk0 = nullptr;
-    // fused path: per-block halo lists and local adjacency
-    bool fused = false;
-    int scheme = 0;   // 0: IMEX Runge-Kutta; 1: explicit Euler (comparison scheme)
-    int nblk = 0, emax = 0, gmax = 0;
-    size_t fused_smem = 0;
-    int *d_halo_ptr = nullptr, *d_halo = nullptr, *d_r1 = nullptr, *d_adj_ptr = nullptr;
-    unsigned *d_adj = nullptr;
+    int *d_perm = nullptr, *d_inst_tile0 = nullptr;
+    // fused path: per-block halo lists and local adjacency, for each fused block size
+    struct HaloSet {
+        bool ok = false;
+        int blk = 0, nblk = 0, emax = 0, gmax = 0;
+        size_t smem = 0;
+        int *d_halo_ptr = nullptr, *d_halo = nullptr, *d_r1 = nullptr, *d_adj_ptr = nullptr;
+        int *d_inst_blk0 = nullptr;
+        unsigned *d_adj = nullptr;
+    } hs[2];                // [0]: 256-cell blocks, [1]: 128-cell blocks
+    bool fused = false;     // fused kernels available (IMEX scheme, kernel_path 0)
+    int config = 2;         // 0: fused 256, 1: fused 128, 2: two-pass (see fvlbm_autotune)
+    int scheme = 0;         // 0: IMEX Runge-Kutta; 1: explicit Euler (comparison scheme)
     int *d_err = nullptr;   // device error flag (a staging wait gave up)
     void *gq = nullptr;     // fused path: node positions minus centroid [8 np]
     void *dvec = nullptr;   // fused path: neighbour-centroid offsets d_m [8 np]
@@ -1297,6 +1301,40 @@ enum KernelId {
     K_FUSED1, K_FUSED2, K_FUSED3, K_EULER
 };
 
+// The three fused stages with BLK-cell blocks (halo set S).
+template <class T, int BLK>
+void enqueue_fused(fvlbm_handle *h, bool stats, const fvlbm_handle::HaloSet &S) {
+    Geo<T> G = geo_of<T>(h);
+    cudaStream_t s = h->stream;
+    T *fn = static_cast<T *>(h->fn), *s0 = static_cast<T *>(h->s0), *s1 = static_cast<T *>(h->s1);
+    T *B = static_cast<T *>(h->bacc), *C = static_cast<T *>(h->cacc);
+    T *tau = static_cast<T *>(h->tau), *mac = static_cast<T *>(h->mac);
+    T *fr = static_cast<T *>(h->frel);
+    const Halo H{S.d_halo_ptr, S.d_halo, S.d_r1, S.d_adj_ptr, S.d_adj, h->d_err, S.emax, S.gmax};
+    const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
+    const dim3 fg(S.nblk), fb(BLK);
+    const size_t sm = S.smem;
+    launch(h, K_FUSED1, "fused_stage1", [&] {
+        k_fused_stage<T, 1, false, BLK><<<fg, fb, sm, s>>>(fr, s1, fn, B, C, tau, mac, nullptr, G, H, fr, CG);
+    });
+    launch(h, K_FUSED2, "fused_stage2", [&] {
+        k_fused_stage<T, 2, false, BLK><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, H, fr, CG);
+    });
+    if (stats) {
+        launch(h, K_FUSED3, "fused_stage3", [&] {
+            k_fused_stage<T, 3, true, BLK><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, H, fr,
+                                                              CG);
+        });
+        launch(h, K_REDUCE, "reduce", [&] {
+            k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, S.d_inst_blk0, h->d_inst_sums);
+        });
+    } else {
+        launch(h, K_FUSED3, "fused_stage3", [&] {
+            k_fused_stage<T, 3, false, BLK><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, H, fr, CG);
+        });
+    }
+}
+
 template <class T>
 void enqueue_step(fvlbm_handle *h, bool stats) {
     Geo<T> G = geo_of<T>(h);
@@ -1313,7 +1351,7 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         T *nn = static_cast<T *>(h->nut[n]);
         T *sg = static_cast<T *>(h->sgrad), *f1 = static_cast<T *>(h->f1);
         const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
-        if (h->fused) {  // compact geometry, and stage 1's f^(1) with the new tau
+        if (h->config != 2) {  // compact geometry, and stage 1's f^(1) with the new tau
             launch(h, K_SST_GRAD, "sst_grad", [&] {
                 k_sst_grad<T, true><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG);
             });
@@ -1349,30 +1387,12 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         cudaMemcpyAsync(fn, s0, sizeof(T) * kQ * static_cast<size_t>(h->np), cudaMemcpyDeviceToDevice, s);
         return;
     }
-    if (h->fused) {
-        Halo H{h->d_halo_ptr, h->d_halo, h->d_r1, h->d_adj_ptr, h->d_adj, h->d_err, h->emax, h->gmax};
-        const dim3 fg(h->nblk), fb(kFusedThreads);
-        T *fr = static_cast<T *>(h->frel);
-        const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
-        const size_t sm = h->fused_smem;
-        launch(h, K_FUSED1, "fused_stage1", [&] {
-            k_fused_stage<T, 1, false><<<fg, fb, sm, s>>>(fr, s1, fn, B, C, tau, mac, nullptr, G, H, fr, CG);
-        });
-        launch(h, K_FUSED2, "fused_stage2", [&] {
-            k_fused_stage<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, H, fr, CG);
-        });
-        if (stats) {
-            launch(h, K_FUSED3, "fused_stage3", [&] {
-                k_fused_stage<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, H, fr, CG);
-            });
-            launch(h, K_REDUCE, "reduce", [&] {
-                k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->d_inst_blk0, h->d_inst_sums);
-            });
-        } else {
-            launch(h, K_FUSED3, "fused_stage3", [&] {
-                k_fused_stage<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, H, fr, CG);
-            });
-        }
+    if (h->config == 0) {
+        enqueue_fused<T, 256>(h, stats, h->hs[0]);
+        return;
+    }
+    if (h->config == 1) {
+        enqueue_fused<T, 128>(h, stats, h->hs[1]);
         return;
     }
     launch(h, K_STAGE1, "stage1", [&] { k_stage1<T><<<grid, block, 0, s>>>(fn, s0, tau, G); });
@@ -1407,7 +1427,7 @@ void enqueue(fvlbm_handle *h, bool stats) {
 }
 
 int launches_per_step(const fvlbm_handle *h) {
-    return (h->sst ? 2 : 0) + (h->scheme == 1 ? 2 : (h->fused ? 3 : 7));
+    return (h->sst ? 2 : 0) + (h->scheme == 1 ? 2 : (h->config != 2 ? 3 : 7));
 }
 
 // Capture `nsteps` plain steps into an executable graph.  A replay always starts from the
@@ -1427,25 +1447,27 @@ int build_graph(fvlbm_handle *h, int nsteps, cudaGraphExec_t *out) {
     return FVLBM_OK;
 }
 
-// Per block of kBlock cells: ring-1 and ring-2 halo lists and the local adjacency of block and
-// ring-1 cells.  Falls back to the two-pass kernels (h->fused = false) when a block's halo does
-// not fit the 16-bit local index or the shared-memory budget.
+// Per block of blk cells: ring-1 and ring-2 halo lists and the local adjacency of block and
+// ring-1 cells.  The set is marked unusable (ok = false) when a block's halo does not fit the
+// 16-bit local index or the shared-memory budget; the two-pass kernels then serve.
 template <class T>
-int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<int> &back,
-                const std::vector<int> &nface) {
+int build_halos(fvlbm_handle *h, fvlbm_handle::HaloSet &S, int blk, const std::vector<int> &nbr,
+                const std::vector<int> &back, const std::vector<int> &nface,
+                const std::vector<int> &inst_tile0) {
     const size_t np = h->np;
-    h->nblk = static_cast<int>(np / kBlock);
+    S.blk = blk;
+    S.nblk = static_cast<int>(np / blk);
     std::vector<int> local(np, -1), halo_ptr(1, 0), halo, r1n, adj_ptr(1, 0);
     std::vector<unsigned> adj;
     int emax = 0, gmax = 0;
     std::vector<int> ring1, ring2;
-    for (int b = 0; b < h->nblk; ++b) {
-        const int base = b * kBlock;
-        for (int c = 0; c < kBlock; ++c) local[base + c] = c;
+    for (int b = 0; b < S.nblk; ++b) {
+        const int base = b * blk;
+        for (int c = 0; c < blk; ++c) local[base + c] = c;
         ring1.clear();
         ring2.clear();
-        int next = kBlock;
-        for (int c = 0; c < kBlock; ++c)
+        int next = blk;
+        for (int c = 0; c < blk; ++c)
             for (int m = 0; m < 4; ++m) {
                 const int v = nbr[m * np + base + c];
                 if (v >= 0 && local[v] < 0) { local[v] = next++; ring1.push_back(v); }
@@ -1455,7 +1477,7 @@ int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<
                 const int v = nbr[m * np + g];
                 if (v >= 0 && local[v] < 0) { local[v] = next++; ring2.push_back(v); }
             }
-        const int E = next, NG = kBlock + static_cast<int>(ring1.size());
+        const int E = next, NG = blk + static_cast<int>(ring1.size());
         emax = std::max(emax, E);
         gmax = std::max(gmax, NG);
         halo.insert(halo.end(), ring1.begin(), ring1.end());
@@ -1465,7 +1487,7 @@ int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<
         const size_t a0 = adj.size();
         adj.resize(a0 + 4 * static_cast<size_t>(NG), kAdjNone);
         for (int c = 0; c < NG; ++c) {
-            const int g = c < kBlock ? base + c : ring1[c - kBlock];
+            const int g = c < blk ? base + c : ring1[c - blk];
             for (int m = 0; m < 4; ++m) {
                 const int v = nbr[m * np + g];
                 unsigned w = kAdjNone;
@@ -1481,35 +1503,42 @@ int build_halos(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<
             }
         }
         adj_ptr.push_back(adj_ptr.back() + NG);
-        for (int c = 0; c < kBlock; ++c) local[base + c] = -1;
+        for (int c = 0; c < blk; ++c) local[base + c] = -1;
         for (int g : ring1) local[g] = -1;
         for (int g : ring2) local[g] = -1;
     }
     emax = (emax + 3) / 4 * 4;  // 16-byte aligned shared-memory rows
     gmax = (gmax + 3) / 4 * 4;
     const size_t smem = FusedSmem<T>::bytes(emax, gmax);
-    if (emax >= 65536 || smem > static_cast<size_t>(kFusedSmemCap)) {
-        h->fused = false;
-        return FVLBM_OK;
-    }
-    h->emax = emax;
-    h->gmax = gmax;
-    h->fused_smem = smem;
+    if (emax >= 65536 || smem > static_cast<size_t>(kFusedSmemCap)) return FVLBM_OK;  // not usable
+    S.emax = emax;
+    S.gmax = gmax;
+    S.smem = smem;
     int rc;
-    if ((rc = upload_raw(h, &h->d_halo_ptr, halo_ptr))) return rc;
+    std::vector<int> inst_blk0(inst_tile0.size());
+    for (size_t q = 0; q < inst_tile0.size(); ++q) inst_blk0[q] = inst_tile0[q] / (blk / kTile);
+    if ((rc = upload_raw(h, &S.d_inst_blk0, inst_blk0))) return rc;
+    if ((rc = upload_raw(h, &S.d_halo_ptr, halo_ptr))) return rc;
     if (halo.empty()) halo.push_back(0);
-    if ((rc = upload_raw(h, &h->d_halo, halo))) return rc;
-    if ((rc = upload_raw(h, &h->d_r1, r1n))) return rc;
-    if ((rc = upload_raw(h, &h->d_adj_ptr, adj_ptr))) return rc;
-    if ((rc = upload_raw(h, &h->d_adj, adj))) return rc;
-    if ((rc = upload_raw(h, &h->d_err, std::vector<int>(1, 0)))) return rc;
+    if ((rc = upload_raw(h, &S.d_halo, halo))) return rc;
+    if ((rc = upload_raw(h, &S.d_r1, r1n))) return rc;
+    if ((rc = upload_raw(h, &S.d_adj_ptr, adj_ptr))) return rc;
+    if ((rc = upload_raw(h, &S.d_adj, adj))) return rc;
     // The attribute is per function and process-wide, shared by every handle: always raise it
     // to the library's cap so that a handle with a smaller halo never lowers another's limit.
     const int cap = kFusedSmemCap;
-    CK(cudaFuncSetAttribute(k_fused_stage<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    CK(cudaFuncSetAttribute(k_fused_stage<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    CK(cudaFuncSetAttribute(k_fused_stage<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-    CK(cudaFuncSetAttribute(k_fused_stage<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    if (blk == 256) {
+        CK(cudaFuncSetAttribute(k_fused_stage<T, 1, false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+        CK(cudaFuncSetAttribute(k_fused_stage<T, 2, false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+        CK(cudaFuncSetAttribute(k_fused_stage<T, 3, false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+        CK(cudaFuncSetAttribute(k_fused_stage<T, 3, true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    } else {
+        CK(cudaFuncSetAttribute(k_fused_stage<T, 1, false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+        CK(cudaFuncSetAttribute(k_fused_stage<T, 2, false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+        CK(cudaFuncSetAttribute(k_fused_stage<T, 3, false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+        CK(cudaFuncSetAttribute(k_fused_stage<T, 3, true, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+    }
+    S.ok = true;
     return FVLBM_OK;
 }
 
@@ -1523,7 +1552,8 @@ void relax_all(fvlbm_handle *h) {
 }
 
 template <class T>
-int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
+int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
+                   const std::vector<int> &inst_tile0) {
     const size_t np = h->np;
     int rc;
     const size_t ts = sizeof(T);
@@ -1607,9 +1637,15 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P) {
     if ((rc = upload_as<T>(h, &h->blen, blen))) return rc;
     if (h->fused) {
         if ((rc = upload_as<T>(h, &h->gq, gq))) return rc;
+        if ((rc = upload_raw(h, &h->d_err, std::vector<int>(1, 0)))) return rc;
         if ((rc = upload_as<T>(h, &h->dvec, dvec))) return rc;
     }
-    if (h->fused && (rc = build_halos<T>(h, nbr, back, nface))) return rc;
+    if (h->fused) {
+        if ((rc = build_halos<T>(h, h->hs[0], 256, nbr, back, nface, inst_tile0))) return rc;
+        if ((rc = build_halos<T>(h, h->hs[1], 128, nbr, back, nface, inst_tile0))) return rc;
+        h->config = h->hs[0].ok ? 0 : (h->hs[1].ok ? 1 : 2);
+        if (h->config == 2) h->fused = false;
+    }
     {
         std::vector<double> kt(k0), wt(w0);
         void *tmp = nullptr;
@@ -1725,18 +1761,15 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     int rc;
     if ((rc = upload_raw(h.get(), &h->d_tile_inst, tile_inst))) { free_all(h.get()); return rc; }
     if ((rc = upload_raw(h.get(), &h->d_inst_tile0, inst_tile0))) { free_all(h.get()); return rc; }
-    {
-        std::vector<int> inst_blk0(inst_tile0.size());
-        for (size_t q = 0; q < inst_tile0.size(); ++q) inst_blk0[q] = inst_tile0[q] / (kBlock / kTile);
-        if ((rc = upload_raw(h.get(), &h->d_inst_blk0, inst_blk0))) { free_all(h.get()); return rc; }
-    }
+
     if ((rc = upload_raw(h.get(), &h->d_ip, ip))) { free_all(h.get()); return rc; }
     if ((rc = dalloc(h.get(), reinterpret_cast<void **>(&h->d_partial), 4 * sizeof(double) * h->ntiles)) ||
         (rc = dalloc(h.get(), reinterpret_cast<void **>(&h->d_inst_sums), 4 * sizeof(double) * n))) {
         free_all(h.get());
         return rc;
     }
-    rc = prec == FVLBM_FP64 ? allocate_state<double>(h.get(), P) : allocate_state<float>(h.get(), P);
+    rc = prec == FVLBM_FP64 ? allocate_state<double>(h.get(), P, inst_tile0)
+                            : allocate_state<float>(h.get(), P, inst_tile0);
     if (rc) {
         free_all(h.get());
         return rc;
@@ -2003,6 +2036,83 @@ int fvlbm_profile_kernels(fvlbm_handle *h, int n_steps, int max_kernels, char *n
         ++nk;
     }
     return std::min(nk, max_kernels);
+}
+
+int fvlbm_autotune(fvlbm_handle *h, int trial_steps, int *chosen, double *ms_per_step) {
+    if (!h || trial_steps <= 0) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    if (ms_per_step)
+        for (int c = 0; c < 3; ++c) ms_per_step[c] = -1.0;
+    if (h->scheme != 0 || (!h->hs[0].ok && !h->hs[1].ok)) {  // nothing to choose
+        if (chosen) *chosen = h->config;
+        return FVLBM_OK;
+    }
+    // snapshot of the state a step reads (the rest is scratch)
+    const size_t np = h->np, ts = h->precision == FVLBM_FP64 ? sizeof(double) : sizeof(float);
+    std::vector<std::pair<void *, size_t>> st = {
+        {h->fn, kQ * np * ts}, {h->frel, kQ * np * ts}, {h->mac, 3 * np * ts}, {h->tau, np * ts}};
+    for (int b = 0; b < 2; ++b) {
+        st.push_back({h->kk[b], np * ts});
+        st.push_back({h->ww[b], np * ts});
+        st.push_back({h->nut[b], np * ts});
+    }
+    size_t total = 0;
+    for (auto &e : st) total += e.second;
+    char *snap = nullptr;
+    CK(cudaMalloc(reinterpret_cast<void **>(&snap), total));
+    auto copy_all = [&](bool save) {
+        size_t off = 0;
+        for (auto &e : st) {
+            if (save)
+                cudaMemcpyAsync(snap + off, e.first, e.second, cudaMemcpyDeviceToDevice, h->stream);
+            else
+                cudaMemcpyAsync(e.first, snap + off, e.second, cudaMemcpyDeviceToDevice, h->stream);
+            off += e.second;
+        }
+    };
+    copy_all(true);
+    const int turb0 = h->turb;
+    const long long steps0 = h->steps;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e300;
+    int best_c = h->config;
+    cudaError_t err = cudaSuccess;
+    for (int c = 0; c < 3 && err == cudaSuccess; ++c) {
+        if (c < 2 && !h->hs[c].ok) continue;
+        h->config = c;
+        for (int k = 0; k < 2; ++k) enqueue(h, false);  // warm-up
+        cudaEventRecord(e0, h->stream);
+        for (int k = 0; k < trial_steps; ++k) enqueue(h, false);
+        cudaEventRecord(e1, h->stream);
+        err = cudaStreamSynchronize(h->stream);
+        float ms = 0.f;
+        if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        const double per = double(ms) / trial_steps;
+        if (ms_per_step) ms_per_step[c] = per;
+        if (per < best) {
+            best = per;
+            best_c = c;
+        }
+        copy_all(false);
+        h->turb = turb0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+    cudaFree(snap);
+    h->config = best_c;
+    h->steps = steps0;
+    for (int k = 0; k < 3; ++k)  // captured graphs bake the old configuration
+        if (h->graph[k]) {
+            cudaGraphExecDestroy(h->graph[k]);
+            h->graph[k] = nullptr;
+        }
+    if (chosen) *chosen = best_c;
+    if (err != cudaSuccess) return cuda_fail(err);
+    CK(cudaGetLastError());
+    return FVLBM_OK;
 }
 
 void fvlbm_destroy(fvlbm_handle *h) {

@@ -55,7 +55,7 @@ class fvlbm_stats(C.Structure):
 
 EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "fvlbm_get_f",
            "fvlbm_set_f", "fvlbm_get_fields", "fvlbm_info", "fvlbm_footprint",
-           "fvlbm_profile_kernels", "fvlbm_destroy", "fvlbm_strerror",
+           "fvlbm_profile_kernels", "fvlbm_autotune", "fvlbm_destroy", "fvlbm_strerror",
            "fvlbm_stats_reduce_static"]
 
 _lib = None
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_info.argtypes = [vp, i, P(i), P(i), P(d)]
     lib.fvlbm_footprint.argtypes = [vp, P(C.c_longlong), P(i)]
     lib.fvlbm_profile_kernels.argtypes = [vp, i, i, vp, vp, vp]
+    lib.fvlbm_autotune.argtypes = [vp, i, P(i), vp]
     lib.fvlbm_destroy.argtypes = [vp]
     lib.fvlbm_destroy.restype = None
     lib.fvlbm_strerror.argtypes = [i]
@@ -215,6 +216,16 @@ def fvlbm_stats_reduce_static(u_old: int, v_old: int, u_new: int, v_new: int, rh
                                             stream), "fvlbm_stats_reduce_static")
 
 
+def fvlbm_autotune(h, trial_steps: int = 5):
+    """Time the available kernel configurations on a snapshot and keep the fastest.
+    Returns (chosen, {name: ms_per_step})."""
+    chosen = C.c_int()
+    ms = np.zeros(3)
+    _check(load().fvlbm_autotune(h, int(trial_steps), C.byref(chosen), _p(ms)), "fvlbm_autotune")
+    names = ("fused256", "fused128", "twopass")
+    return names[chosen.value], {names[k]: float(ms[k]) for k in range(3) if ms[k] >= 0}
+
+
 def fvlbm_destroy(h) -> None:
     if h:
         load().fvlbm_destroy(h)
@@ -284,6 +295,9 @@ class Solver:
 
     def footprint(self):
         return fvlbm_footprint(self.h)
+
+    def autotune(self, trial_steps: int = 5):
+        return fvlbm_autotune(self.h, trial_steps)
 
     def profile_kernels(self, n_steps: int) -> dict:
         return fvlbm_profile_kernels(self.h, n_steps)

@@ -301,3 +301,27 @@ def test_batch_with_tiny_and_ragged_instances():
         o = Oracle(c)
         o.step(20)
         assert _rel_max(s.get_f(i), o.get_f()) < 1e-5, c.name
+
+
+# ----------------------------------------------------------------- autotuner
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_autotune_restores_state_and_keeps_parity(prec):
+    """fvlbm_autotune times every kernel configuration on a snapshot, restores the state bit for
+    bit, and the chosen configuration still matches the oracle."""
+    cases = [mg.naca0012_cmesh(n_target=5000, alpha_deg=4.0), mg.cavity_quad(30, re=400.0)]
+    s = fvlbm.Solver(cases, precision=prec, device=0)
+    s.step(3)
+    before = [s.get_f(i) for i in range(2)]
+    om = s.fields(0)["omega"]
+    chosen, times = s.autotune(3)
+    assert chosen in ("fused256", "fused128", "twopass")
+    assert set(times) >= {"twopass"} and all(t > 0 for t in times.values())
+    for i in range(2):
+        assert np.array_equal(s.get_f(i), before[i])
+    assert np.array_equal(s.fields(0)["omega"], om)
+    s.step(4)
+    tol = 1e-10 if prec == FP64 else 1e-5
+    for i, c in enumerate(cases):
+        o = Oracle(c)
+        o.step(7)
+        assert _rel_max(s.get_f(i), o.get_f()) < tol, (chosen, c.name)
