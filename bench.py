@@ -413,31 +413,27 @@ def _oracle_errors(cases, fvlbm, dev, stream, torch, nsteps):
 
 
 def _e2e(torch, fvlbm, solver, stream, args, world, dist):
-    """Same metric through the public API with host buffers: per step, fvlbm_set_f of every
-    instance from pinned host memory, one fvlbm_step, fvlbm_get_fields (u, v) back."""
-    n = solver.n
-    cells = solver.cells
-    host_f = [torch.empty((cells[i], 9), dtype=torch.float64, pin_memory=True).numpy()
-              for i in range(n)]
-    for i in range(n):
-        host_f[i][:] = solver.get_f(i)
-    lib = fvlbm.load()
+    """Same metric through the public API with host buffers: per step, one fvlbm_set_f of the
+    whole state (all instances, FVLBM_ALL_INSTANCES) from pinned host memory, one fvlbm_step,
+    and one fvlbm_get_fields of u and v back to pinned host memory."""
     import ctypes as C
-    outs = [[torch.empty(cells[i], dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
-            for i in range(n)]
-    k = max(2, min(args.steps // 10, 10))
+    total = fvlbm.fvlbm_info(solver.h, -1)[0]
+    host_f = torch.empty((total, 9), dtype=torch.float64, pin_memory=True).numpy()
+    host_f[:] = fvlbm.fvlbm_get_f(solver.h, -1)
+    u = torch.empty(total, dtype=torch.float64, pin_memory=True).numpy()
+    v = torch.empty(total, dtype=torch.float64, pin_memory=True).numpy()
+    lib = fvlbm.load()
+    k = max(3, min(args.steps // 10, 20))
 
     def one_step():
-        for i in range(n):
-            rc = lib.fvlbm_set_f(solver.h, i, host_f[i].ctypes.data_as(C.c_void_p))
-            if rc:
-                raise fvlbm.FvlbmError(rc, "fvlbm_set_f")
+        rc = lib.fvlbm_set_f(solver.h, -1, host_f.ctypes.data_as(C.c_void_p))
+        if rc:
+            raise fvlbm.FvlbmError(rc, "fvlbm_set_f")
         solver.step(1)
-        for i in range(n):
-            rc = lib.fvlbm_get_fields(solver.h, i, None, outs[i][0].ctypes.data_as(C.c_void_p),
-                                      outs[i][1].ctypes.data_as(C.c_void_p), None, None, None)
-            if rc:
-                raise fvlbm.FvlbmError(rc, "fvlbm_get_fields")
+        rc = lib.fvlbm_get_fields(solver.h, -1, None, u.ctypes.data_as(C.c_void_p),
+                                  v.ctypes.data_as(C.c_void_p), None, None, None)
+        if rc:
+            raise fvlbm.FvlbmError(rc, "fvlbm_get_fields")
     with torch.cuda.stream(stream):
         one_step()
         torch.cuda.synchronize()
@@ -448,33 +444,11 @@ def _e2e(torch, fvlbm, solver, stream, args, world, dist):
             one_step()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-    total = sum(cells)
+    if world > 1:
+        el = max_over_ranks(torch, dist, world, el, device="cuda")
     return {"value": total * world / (el / k) / 1e6, "unit": UNIT,
             "h2d_bytes_per_step": int(total * 9 * 8), "d2h_bytes_per_step": int(total * 2 * 8),
             "steps": k, "ms_per_step": el / k * 1e3}
-
-
-def run_profile_mode(args):
-    """Minimal run for ncu: one solver, warmup + steps, nothing else (launch list / capture)."""
-    import torch
-    from paper_1812_00394_gb300 import fvlbm
-    torch.cuda.set_device(0)
-    cases = make_workload(args.workload)
-    prec = fvlbm.FVLBM_FP32_DEV if args.precision == "fp32" else fvlbm.FVLBM_FP64
-    s = fvlbm.Solver(cases, precision=prec, device=0)
-    s.step(args.warmup)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    s.step(args.steps)
-    st = s.step(0, stats=False)
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    _, lps = s.footprint()
-    print(json.dumps({"mode": "profile", "workload": args.workload, "precision": args.precision,
-                      "cells": sum(c.mesh.n_cells for c in cases), "launches_per_step": lps,
-                      "warmup": args.warmup, "steps": args.steps, "wall_s": el, "st": st}))
-    s.close()
-    return 0
 
 
 def main():

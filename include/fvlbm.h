@@ -140,13 +140,16 @@ int fvlbm_step(fvlbm_handle *h, int n_steps, fvlbm_stats *stats);
 int fvlbm_forces(fvlbm_handle *h, int instance, double *out, double *cp);
 
 /* Host copies of the state of `instance` in input cell order (absolute f, FP64 on output).
- * Any pointer may be NULL.  Synchronise the stream. */
+ * instance = FVLBM_ALL_INSTANCES (-1) addresses every instance at once: arrays are the
+ * instances' arrays concatenated in instance order (one copy and one kernel per call).
+ * Any pointer of get_fields may be NULL.  Synchronise the stream. */
+#define FVLBM_ALL_INSTANCES (-1)
 int fvlbm_get_f(fvlbm_handle *h, int instance, double *f);
 int fvlbm_set_f(fvlbm_handle *h, int instance, const double *f);
 int fvlbm_get_fields(fvlbm_handle *h, int instance, double *rho, double *u, double *v,
                      double *k, double *omega, double *nut);
 
-/* Sizes and the time step actually used. */
+/* Sizes and the time step actually used (instance -1: totals over all instances, dt = 0). */
 int fvlbm_info(fvlbm_handle *h, int instance, int *n_cells, int *n_bedges, double *dt);
 
 /* Bytes of device memory the handle holds, and the number of kernel launches one step issues. */

@@ -1146,6 +1146,60 @@ __global__ void k_wall_forces(const T *__restrict__ fn, const int *__restrict__ 
     out[2 * nbi + q] = (kCs2 * double(r) - kCs2 * rho0) / (0.5 * rho0 * uref * uref);
 }
 
+// All instances at once: output position j (instances concatenated in input order, cells in
+// input order within each) maps to internal cell map[j].
+template <class T>
+__global__ void k_gather_f_all(const T *__restrict__ f, const int *__restrict__ map, int total,
+                               size_t np, const int *__restrict__ tile_inst,
+                               const InstParam *__restrict__ ip, double *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= total) return;
+    const int i = map[j];
+    const double rho0 = ip[tile_inst[i / kTile]].rho0;
+    for (int a = 0; a < kQ; ++a) {
+        const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        out[static_cast<size_t>(j) * kQ + a] = double(f[a * np + i]) + wa * rho0;
+    }
+}
+
+template <class T>
+__global__ void k_scatter_f_all(T *__restrict__ f, T *__restrict__ mac, const int *__restrict__ map,
+                                int total, size_t np, const int *__restrict__ tile_inst,
+                                const InstParam *__restrict__ ip, const double *__restrict__ in) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= total) return;
+    const int i = map[j];
+    const double rho0 = ip[tile_inst[i / kTile]].rho0;
+    T d[kQ];
+    for (int a = 0; a < kQ; ++a) {
+        const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        d[a] = T(in[static_cast<size_t>(j) * kQ + a] - wa * rho0);
+        f[a * np + i] = d[a];
+    }
+    T dr, r, u, v;
+    moments(d, T(rho0), dr, r, u, v);
+    mac[i] = r;
+    mac[np + i] = u;
+    mac[2 * np + i] = v;
+}
+
+template <class T>
+__global__ void k_gather_fields_all(const T *__restrict__ mac, const T *__restrict__ kk,
+                                    const T *__restrict__ ww, const T *__restrict__ nut,
+                                    const int *__restrict__ map, int total, size_t np,
+                                    double *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= total) return;
+    const int i = map[j];
+    const size_t n = total;
+    out[0 * n + j] = double(mac[i]);
+    out[1 * n + j] = double(mac[np + i]);
+    out[2 * n + j] = double(mac[2 * np + i]);
+    out[3 * n + j] = double(kk[i]);
+    out[4 * n + j] = double(ww[i]);
+    out[5 * n + j] = double(nut[i]);
+}
+
 }  // namespace fvlbm
 
 // ==================================================================== handle and C ABI
@@ -1182,6 +1236,8 @@ struct fvlbm_handle {
     // device arrays (element type T = double or float; stored as void*)
     int *d_nbr = nullptr, *d_tile_inst = nullptr, *d_btype = nullptr, *d_bowner = nullptr;
     int *d_perm = nullptr, *d_inst_tile0 = nullptr;
+    int *d_all_map = nullptr;   // output position (all instances) -> internal cell
+    int total_nc = 0, total_nb = 0;
     // fused path: per-block halo lists and local adjacency, for each fused block size
     struct HaloSet {
         bool ok = false;
@@ -1625,6 +1681,18 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
     if ((rc = upload_raw(h, &h->d_btype, btype))) return rc;
     if ((rc = upload_raw(h, &h->d_bowner, bowner))) return rc;
     if ((rc = upload_raw(h, &h->d_perm, perm))) return rc;
+    {
+        std::vector<int> map;
+        int out_off = 0;
+        for (int q = 0; q < h->ninst; ++q) {
+            const Prepared &p = *P[q];
+            map.resize(out_off + p.nc);
+            for (int k = 0; k < p.nc; ++k) map[out_off + p.perm[k]] = h->inst[q].cell_off + k;
+            out_off += p.nc;
+        }
+        h->total_nc = out_off;
+        if ((rc = upload_raw(h, &h->d_all_map, map))) return rc;
+    }
     if ((rc = upload_as<T>(h, &h->sn, sn))) return rc;
     if ((rc = upload_as<T>(h, &h->lsq, lsq))) return rc;
     if ((rc = upload_as<T>(h, &h->rown, rown))) return rc;
@@ -1877,8 +1945,24 @@ int fvlbm_step(fvlbm_handle *h, int n_steps, fvlbm_stats *stats) {
 }
 
 int fvlbm_get_f(fvlbm_handle *h, int instance, double *f) {
-    if (!h || instance < 0 || instance >= h->ninst || !f) return FVLBM_ERR_BAD_PARAM;
+    if (!h || instance < -1 || instance >= h->ninst || !f) return FVLBM_ERR_BAD_PARAM;
     CK(cudaSetDevice(h->device));
+    if (instance == -1) {
+        const int n = h->total_nc;
+        int rc = io_buffer(h, sizeof(double) * kQ * n);
+        if (rc) return rc;
+        const int nb = (n + 255) / 256;
+        if (h->precision == FVLBM_FP64)
+            k_gather_f_all<double><<<nb, 256, 0, h->stream>>>(static_cast<double *>(h->fn), h->d_all_map, n,
+                                                              h->np, h->d_tile_inst, h->d_ip, h->d_io);
+        else
+            k_gather_f_all<float><<<nb, 256, 0, h->stream>>>(static_cast<float *>(h->fn), h->d_all_map, n,
+                                                             h->np, h->d_tile_inst, h->d_ip, h->d_io);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(f, h->d_io, sizeof(double) * kQ * n, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return FVLBM_OK;
+    }
     const InstInfo &I = h->inst[instance];
     int rc = io_buffer(h, sizeof(double) * kQ * I.nc);
     if (rc) return rc;
@@ -1897,8 +1981,29 @@ int fvlbm_get_f(fvlbm_handle *h, int instance, double *f) {
 }
 
 int fvlbm_set_f(fvlbm_handle *h, int instance, const double *f) {
-    if (!h || instance < 0 || instance >= h->ninst || !f) return FVLBM_ERR_BAD_PARAM;
+    if (!h || instance < -1 || instance >= h->ninst || !f) return FVLBM_ERR_BAD_PARAM;
     CK(cudaSetDevice(h->device));
+    if (instance == -1) {
+        const int n = h->total_nc;
+        int rc = io_buffer(h, sizeof(double) * kQ * n);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(h->d_io, f, sizeof(double) * kQ * n, cudaMemcpyHostToDevice, h->stream));
+        const int nb = (n + 255) / 256;
+        if (h->precision == FVLBM_FP64) {
+            k_scatter_f_all<double><<<nb, 256, 0, h->stream>>>(static_cast<double *>(h->fn),
+                                                               static_cast<double *>(h->mac), h->d_all_map, n,
+                                                               h->np, h->d_tile_inst, h->d_ip, h->d_io);
+            relax_all<double>(h);
+        } else {
+            k_scatter_f_all<float><<<nb, 256, 0, h->stream>>>(static_cast<float *>(h->fn),
+                                                              static_cast<float *>(h->mac), h->d_all_map, n,
+                                                              h->np, h->d_tile_inst, h->d_ip, h->d_io);
+            relax_all<float>(h);
+        }
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->stream));
+        return FVLBM_OK;
+    }
     const InstInfo &I = h->inst[instance];
     int rc = io_buffer(h, sizeof(double) * kQ * I.nc);
     if (rc) return rc;
@@ -1921,8 +2026,31 @@ int fvlbm_set_f(fvlbm_handle *h, int instance, const double *f) {
 
 int fvlbm_get_fields(fvlbm_handle *h, int instance, double *rho, double *u, double *v, double *k,
                      double *omega, double *nut) {
-    if (!h || instance < 0 || instance >= h->ninst) return FVLBM_ERR_BAD_PARAM;
+    if (!h || instance < -1 || instance >= h->ninst) return FVLBM_ERR_BAD_PARAM;
     CK(cudaSetDevice(h->device));
+    if (instance == -1) {
+        const size_t n = h->total_nc;
+        int rc = io_buffer(h, sizeof(double) * 6 * n);
+        if (rc) return rc;
+        const int nb = static_cast<int>((n + 255) / 256);
+        const int c = h->turb;
+        if (h->precision == FVLBM_FP64)
+            k_gather_fields_all<double><<<nb, 256, 0, h->stream>>>(
+                static_cast<double *>(h->mac), static_cast<double *>(h->kk[c]), static_cast<double *>(h->ww[c]),
+                static_cast<double *>(h->nut[c]), h->d_all_map, static_cast<int>(n), h->np, h->d_io);
+        else
+            k_gather_fields_all<float><<<nb, 256, 0, h->stream>>>(
+                static_cast<float *>(h->mac), static_cast<float *>(h->kk[c]), static_cast<float *>(h->ww[c]),
+                static_cast<float *>(h->nut[c]), h->d_all_map, static_cast<int>(n), h->np, h->d_io);
+        CK(cudaGetLastError());
+        double *dst[6] = {rho, u, v, k, omega, nut};
+        for (int q = 0; q < 6; ++q)
+            if (dst[q])
+                CK(cudaMemcpyAsync(dst[q], h->d_io + q * n, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                   h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return FVLBM_OK;
+    }
     const InstInfo &I = h->inst[instance];
     const size_t n = I.nc;
     int rc = io_buffer(h, sizeof(double) * 6 * n);
@@ -1987,7 +2115,15 @@ int fvlbm_forces(fvlbm_handle *h, int instance, double *out, double *cp) {
 }
 
 int fvlbm_info(fvlbm_handle *h, int instance, int *n_cells, int *n_bedges, double *dt) {
-    if (!h || instance < 0 || instance >= h->ninst) return FVLBM_ERR_BAD_PARAM;
+    if (!h || instance < -1 || instance >= h->ninst) return FVLBM_ERR_BAD_PARAM;
+    if (instance == -1) {  // totals over all instances
+        int nbe = 0;
+        for (const auto &I : h->inst) nbe += I.n_bedges_in;
+        if (n_cells) *n_cells = h->total_nc;
+        if (n_bedges) *n_bedges = nbe;
+        if (dt) *dt = 0.0;
+        return FVLBM_OK;
+    }
     const InstInfo &I = h->inst[instance];
     if (n_cells) *n_cells = I.nc;
     if (n_bedges) *n_bedges = I.n_bedges_in;

@@ -325,3 +325,20 @@ def test_autotune_restores_state_and_keeps_parity(prec):
         o = Oracle(c)
         o.step(7)
         assert _rel_max(s.get_f(i), o.get_f()) < tol, (chosen, c.name)
+
+
+def test_all_instances_io_matches_per_instance():
+    """instance = -1 reads and writes every instance at once, concatenated in order."""
+    cases = [mg.cavity_quad(9, re=100.0), mg.bfs_hybrid(n_target=1500), mg.cavity_quad(5)]
+    s = fvlbm.Solver(cases, precision=FP32, device=0)
+    s.step(3)
+    allf = fvlbm.fvlbm_get_f(s.h, -1)
+    parts = [s.get_f(i) for i in range(3)]
+    assert np.array_equal(allf, np.concatenate(parts))
+    allv = fvlbm.fvlbm_get_fields(s.h, -1)
+    for key in ("u", "omega"):
+        assert np.array_equal(allv[key], np.concatenate([s.fields(i)[key] for i in range(3)]))
+    new = allf * (1 + 1e-4 * mg.splitmix64_uniform(9, allf.size).reshape(allf.shape))
+    fvlbm.fvlbm_set_f(s.h, -1, new)
+    np.testing.assert_allclose(s.get_f(1), new[parts[0].shape[0]:parts[0].shape[0] + parts[1].shape[0]],
+                               rtol=0, atol=1e-7)
