@@ -54,6 +54,10 @@ extern "C" {
 /* storage precision of the distribution functions */
 #define FVLBM_FP64 0          /* f and all arithmetic in double */
 #define FVLBM_FP32_DEV 1      /* f - w_alpha rho0 stored and computed in float; reductions FP64 */
+#define FVLBM_FP64_TANGENT 2  /* FP64 plus the forward-mode tangent: every stored and computed
+                                 number is a pair (value, derivative with respect to one scalar
+                                 parameter p); see fvlbm_tangent_seed.  Runs the two-pass
+                                 kernels at about twice the FP64 cost. */
 
 /* Unstructured 2-D mesh: triangles and quadrilaterals, nodes counter-clockwise. */
 typedef struct {
@@ -82,7 +86,7 @@ typedef struct {
     double dt;                 /* time step; if <= 0, dt = cfl / (max upwind outflow rate) */
     double cfl;
     int sst;                   /* 1: k-omega SST eddy viscosity; 0: laminar */
-    int precision;             /* FVLBM_FP64 or FVLBM_FP32_DEV */
+    int precision;             /* FVLBM_FP64, FVLBM_FP32_DEV or FVLBM_FP64_TANGENT */
     double uref, lref;         /* reference speed and length (C_D, C_L, Cp, omega floor) */
     double alpha_deg;          /* free-stream angle for C_D / C_L */
     const double *rho_init;    /* [n_cells] or NULL (rho0) */
@@ -171,6 +175,48 @@ int fvlbm_profile_kernels(fvlbm_handle *h, int n_steps, int max_kernels, char *n
  * scheme).  Allocates a temporary snapshot of the state (about 28 words per cell) and
  * synchronises the stream.  Errors: BAD_PARAM, OOM, CUDA. */
 int fvlbm_autotune(fvlbm_handle *h, int trial_steps, int *chosen, double *ms_per_step);
+
+/* ---------------------------------------------------------------------------------------------
+ * Forward-mode tangent (no counterpart in the paper's Part II; the shape-design use of the solver
+ * that its conclusion points to needs derivatives of C_D and C_L).  Valid on handles created with
+ * precision FVLBM_FP64_TANGENT, else FVLBM_ERR_NOT_SUPPORTED.
+ *
+ * Such a handle advances, with every step, the values of the FP64 step AND their derivatives
+ * with respect to one scalar parameter p, by the chain rule through each operation of the
+ * discrete step (Steps 1-7 of Sec. 3.2: gradient, upwind face values, boundary values, the
+ * closed-form implicit collision, the SST update and tau = (nu + nu_t) / c_s^2).  Where the step
+ * is not differentiable (upwind switch on e.n = 0, limiter and clip branches, the nu_t limiter's
+ * min), the derivative of the branch the value takes is carried.  The values equal those of an
+ * FVLBM_FP64 handle with kernel_path 1 up to rounding (the compiler may fuse multiply-adds
+ * differently).
+ *
+ * fvlbm_tangent_seed sets dp of the inputs p acts on, for `instance` (FVLBM_ALL_INSTANCES is not
+ * accepted):
+ *   dbedge_val  [5 * n_bedges] in boundary-edge input order: d(rho_b, u_b, v_b, k_b, omega_b)/dp,
+ *               e.g. for p = free-stream angle alpha (radians) with u_b = U cos alpha,
+ *               v_b = U sin alpha: (0, -v_b, u_b, 0, 0) on far-field edges.  NULL = unchanged.
+ *   df          [n_cells * 9] cell-major like fvlbm_set_f: df/dp of the current state.  NULL =
+ *               unchanged.  fvlbm_set_f resets the derivative of f it writes to 0.
+ * The derivatives of k, omega and nu_t start at 0 at create.
+ *
+ * fvlbm_get_f_tangent: df/dp of the current state, layout of fvlbm_get_f.
+ * fvlbm_forces_tangent: out[4] as fvlbm_forces and dout[4] = d(Fx, Fy, C_D, C_L)/dp.  dalpha is
+ *   d(alpha)/dp in radians (1 when p is alpha in radians, 0 when alpha does not depend on p): it
+ *   adds the derivative of the projection of (Fx, Fy) onto the drag and lift directions.
+ * All three synchronise the stream.  Errors: BAD_PARAM, NOT_SUPPORTED, CUDA. */
+int fvlbm_tangent_seed(fvlbm_handle *h, int instance, const double *dbedge_val, const double *df);
+int fvlbm_get_f_tangent(fvlbm_handle *h, int instance, double *df);
+
+/* Shape derivatives: dxy [2 * n_nodes] = d(x, y)/dp of every mesh node of `instance` (for example
+ * a wall-normal displacement of one wall node).  Recomputes the instance's geometry on the host
+ * with these derivatives (areas, normals and face lengths, centroids, least-squares weights,
+ * face offsets, wall distance d) and stores d(geometry)/dp beside the values; the values and
+ * the cell order do not change (FVLBM_ERR_NOT_SUPPORTED if the perturbed preprocessing would
+ * reorder cells).  The time step stays the one fixed at create, so the derivative is the one at
+ * fixed dt: for a dt derived from cfl it omits dt's own dependence on the geometry.  dxy = 0
+ * clears the shape seed.  Synchronises.  Errors: BAD_PARAM, NOT_SUPPORTED, BAD_MESH, CUDA. */
+int fvlbm_tangent_seed_nodes(fvlbm_handle *h, int instance, const double *dxy);
+int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *out, double *dout);
 
 void fvlbm_destroy(fvlbm_handle *h);
 const char *fvlbm_strerror(int code);

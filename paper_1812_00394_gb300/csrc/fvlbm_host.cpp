@@ -42,28 +42,31 @@ inline uint64_t hilbert_key(uint64_t x, uint64_t y) {
     return d;
 }
 
-double point_segment(double px, double py, double ax, double ay, double bx, double by) {
-    const double ex = bx - ax, ey = by - ay;
-    const double L2 = ex * ex + ey * ey;
-    double t = L2 > 0 ? ((px - ax) * ex + (py - ay) * ey) / L2 : 0.0;
-    t = std::min(1.0, std::max(0.0, t));
-    const double dx = ax + t * ex - px, dy = ay + t * ey - py;
-    return std::sqrt(dx * dx + dy * dy);
+template <class S>
+S point_segment(S px, S py, S ax, S ay, S bx, S by) {
+    const S ex = bx - ax, ey = by - ay;
+    const S L2 = ex * ex + ey * ey;
+    S t = L2 > S(0.0) ? ((px - ax) * ex + (py - ay) * ey) / L2 : S(0.0);
+    t = smin(S(1.0), smax(S(0.0), t));
+    const S dx = ax + t * ex - px, dy = ay + t * ey - py;
+    return sqrt(dx * dx + dy * dy);
 }
 
+template <class S>
 struct FaceGeo {
     int nbr = kNone;        // neighbour input cell id, or -(b+1) boundary edge, or kNone
     int back = -1;          // local slot of this face in the neighbour's face list
-    double nx = 0, ny = 0;  // unit outward normal
-    double len = 0;
-    double xm = 0, ym = 0;
+    S nx = 0, ny = 0;       // unit outward normal
+    S len = 0;
+    S xm = 0, ym = 0;
     double sx = 0, sy = 0;  // neighbour centroid offset (periodic shift as seen from here)
 };
 
 }  // namespace
 
-int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params &p,
-                     Prepared *out, std::string *why) {
+template <class S>
+int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params &p, const S *xy,
+                       PreparedT<S> *out, std::string *why) {
     const int nc = m.n_cells;
     if (nc <= 0 || m.n_nodes <= 0 || !m.xy || !m.cell_ptr || !m.cell_nodes) {
         *why = "empty mesh";
@@ -73,9 +76,12 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
         *why = "need nu > 0, rho0 > 0 and dt > 0 or cfl > 0";
         return FVLBM_ERR_BAD_PARAM;
     }
-    const double *xy = m.xy;
-    std::vector<double> cx(nc), cy(nc), area(nc);
-    std::vector<FaceGeo> face(static_cast<size_t>(nc) * 4);
+    if (!xy) {
+        *why = "empty mesh";
+        return FVLBM_ERR_BAD_MESH;
+    }
+    std::vector<S> cx(nc), cy(nc), area(nc);
+    std::vector<FaceGeo<S>> face(static_cast<size_t>(nc) * 4);
     std::unordered_map<uint64_t, Side> open;
     open.reserve(static_cast<size_t>(nc) * 3);
     for (int i = 0; i < nc; ++i) {
@@ -93,33 +99,33 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
         }
         // polygon area and centroid, relative to node 0 of the cell for accuracy on small cells
         const int n0 = m.cell_nodes[p0];
-        const double ox = xy[2 * n0], oy = xy[2 * n0 + 1];
-        double a2 = 0, mx = 0, my = 0;
+        const S ox = xy[2 * n0], oy = xy[2 * n0 + 1];
+        S a2 = 0, mx = 0, my = 0;
         for (int l = 0; l < nv; ++l) {
             const int a = m.cell_nodes[p0 + l], b = m.cell_nodes[p0 + (l + 1) % nv];
-            const double x0 = xy[2 * a] - ox, y0 = xy[2 * a + 1] - oy;
-            const double x1 = xy[2 * b] - ox, y1 = xy[2 * b + 1] - oy;
-            const double c = x0 * y1 - x1 * y0;
+            const S x0 = xy[2 * a] - ox, y0 = xy[2 * a + 1] - oy;
+            const S x1 = xy[2 * b] - ox, y1 = xy[2 * b + 1] - oy;
+            const S c = x0 * y1 - x1 * y0;
             a2 += c;
             mx += (x0 + x1) * c;
             my += (y0 + y1) * c;
         }
-        if (!(a2 > 0.0)) {
+        if (!(a2 > S(0.0))) {
             *why = "cell " + std::to_string(i) + " has non-positive area (nodes must be CCW)";
             return FVLBM_ERR_BAD_MESH;
         }
-        area[i] = 0.5 * a2;
-        cx[i] = ox + mx / (3.0 * a2);
-        cy[i] = oy + my / (3.0 * a2);
+        area[i] = S(0.5) * a2;
+        cx[i] = ox + mx / (S(3.0) * a2);
+        cy[i] = oy + my / (S(3.0) * a2);
         for (int l = 0; l < nv; ++l) {
             const int a = m.cell_nodes[p0 + l], b = m.cell_nodes[p0 + (l + 1) % nv];
-            const double ex = xy[2 * b] - xy[2 * a], ey = xy[2 * b + 1] - xy[2 * a + 1];
-            FaceGeo &F = face[4 * static_cast<size_t>(i) + l];
-            F.len = std::sqrt(ex * ex + ey * ey);
+            const S ex = xy[2 * b] - xy[2 * a], ey = xy[2 * b + 1] - xy[2 * a + 1];
+            FaceGeo<S> &F = face[4 * static_cast<size_t>(i) + l];
+            F.len = sqrt(ex * ex + ey * ey);
             F.nx = ey / F.len;
             F.ny = -ex / F.len;
-            F.xm = 0.5 * (xy[2 * a] + xy[2 * b]);
-            F.ym = 0.5 * (xy[2 * a + 1] + xy[2 * b + 1]);
+            F.xm = S(0.5) * (xy[2 * a] + xy[2 * b]);
+            F.ym = S(0.5) * (xy[2 * a + 1] + xy[2 * b + 1]);
             const uint64_t id = edge_id(a, b);
             auto it = open.find(id);
             if (it == open.end()) {
@@ -129,7 +135,7 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
                     *why = "edge shared by more than two cells";
                     return FVLBM_ERR_BAD_MESH;
                 }
-                FaceGeo &G = face[4 * static_cast<size_t>(it->second.cell) + it->second.local];
+                FaceGeo<S> &G = face[4 * static_cast<size_t>(it->second.cell) + it->second.local];
                 F.nbr = it->second.cell;
                 F.back = it->second.local;
                 G.nbr = i;
@@ -164,8 +170,8 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
             return FVLBM_ERR_BAD_BC;
         }
         const double sx = bc.periodic_shift[2 * q], sy = bc.periodic_shift[2 * q + 1];
-        FaceGeo &A = face[4 * static_cast<size_t>(bside[ea].cell) + bside[ea].local];
-        FaceGeo &B = face[4 * static_cast<size_t>(bside[eb].cell) + bside[eb].local];
+        FaceGeo<S> &A = face[4 * static_cast<size_t>(bside[ea].cell) + bside[ea].local];
+        FaceGeo<S> &B = face[4 * static_cast<size_t>(bside[eb].cell) + bside[eb].local];
         A.nbr = bside[eb].cell;
         A.back = bside[eb].local;
         A.sx = -sx;
@@ -184,7 +190,7 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
     for (int i = 0; i < nc; ++i) {
         const int nv = m.cell_ptr[i + 1] - m.cell_ptr[i];
         for (int l = 0; l < nv; ++l) {
-            const FaceGeo &F = face[4 * static_cast<size_t>(i) + l];
+            const FaceGeo<S> &F = face[4 * static_cast<size_t>(i) + l];
             if (F.nbr == kNone) {
                 *why = "cell " + std::to_string(i) + " has an open edge with no boundary record";
                 return FVLBM_ERR_BAD_BC;
@@ -199,17 +205,17 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
 
     // Renumbering: Hilbert order of the centroids (32-bit resolution per axis, so that even
     // wall cells of 1e-6 chord on a 40-chord domain get distinct keys) seeds the block growth
-    double x0 = cx[0], x1 = cx[0], y0 = cy[0], y1 = cy[0];
+    double x0 = value_of(cx[0]), x1 = x0, y0 = value_of(cy[0]), y1 = y0;
     for (int i = 0; i < nc; ++i) {
-        x0 = std::min(x0, cx[i]); x1 = std::max(x1, cx[i]);
-        y0 = std::min(y0, cy[i]); y1 = std::max(y1, cy[i]);
+        x0 = std::min(x0, value_of(cx[i])); x1 = std::max(x1, value_of(cx[i]));
+        y0 = std::min(y0, value_of(cy[i])); y1 = std::max(y1, value_of(cy[i]));
     }
     const double span = std::max(x1 - x0, y1 - y0) + 1e-300;
     const double qmax = 4294967295.0;
     std::vector<std::pair<uint64_t, int>> key(nc);
     for (int i = 0; i < nc; ++i) {
-        const uint64_t qx = static_cast<uint64_t>(std::min(qmax, (cx[i] - x0) / span * qmax));
-        const uint64_t qy = static_cast<uint64_t>(std::min(qmax, (cy[i] - y0) / span * qmax));
+        const uint64_t qx = static_cast<uint64_t>(std::min(qmax, (value_of(cx[i]) - x0) / span * qmax));
+        const uint64_t qy = static_cast<uint64_t>(std::min(qmax, (value_of(cy[i]) - y0) / span * qmax));
         key[i] = {hilbert_key(qx, qy), i};
     }
     std::stable_sort(key.begin(), key.end(),
@@ -248,8 +254,8 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
         }
         for (int k = 0; k < nc; ++k) key[k].second = order[k];
     }
-    Prepared &P = *out;
-    P = Prepared();
+    PreparedT<S> &P = *out;
+    P = PreparedT<S>();
     P.nc = nc;
     P.np = (nc + kBlock - 1) / kBlock * kBlock;
     P.n_bedges_in = nbe;
@@ -274,7 +280,7 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
     P.blen.resize(P.nb);
     for (int f = 0; f < P.nb; ++f) {
         const int b = P.bedge_of[f];
-        const FaceGeo &F = face[4 * static_cast<size_t>(bside[b].cell) + bside[b].local];
+        const FaceGeo<S> &F = face[4 * static_cast<size_t>(bside[b].cell) + bside[b].local];
         P.bowner[f] = inv[bside[b].cell];
         P.btype[f] = bc.bedge_type[b];
         for (int c = 0; c < 5; ++c) P.bval[5 * f + c] = bc.bedge_val[5 * b + c];
@@ -286,15 +292,15 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
     P.nbr.assign(4 * np, kNone);
     P.back.assign(4 * np, -1);
     P.nface.assign(np, 0);
-    P.gq.assign(8 * np, 0.0);
-    P.sn.assign(8 * np, 0.0);
-    P.lsq.assign(8 * np, 0.0);
-    P.dvec.assign(8 * np, 0.0);
-    P.rown.assign(8 * np, 0.0);
-    P.rnbr.assign(8 * np, 0.0);
-    P.dinv.assign(4 * np, 0.0);
-    P.area.assign(np, 0.0);
-    P.wdist.assign(np, 1e30);
+    P.gq.assign(8 * np, S(0.0));
+    P.sn.assign(8 * np, S(0.0));
+    P.lsq.assign(8 * np, S(0.0));
+    P.dvec.assign(8 * np, S(0.0));
+    P.rown.assign(8 * np, S(0.0));
+    P.rnbr.assign(8 * np, S(0.0));
+    P.dinv.assign(4 * np, S(0.0));
+    P.area.assign(np, S(0.0));
+    P.wdist.assign(np, S(1e30));
     for (int k = 0; k < nc; ++k) {
         const int i = P.perm[k];
         const int nv = m.cell_ptr[i + 1] - m.cell_ptr[i];
@@ -305,12 +311,12 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
             P.gq[(2 * l) * np + k] = xy[2 * a] - cx[i];
             P.gq[(2 * l + 1) * np + k] = xy[2 * a + 1] - cy[i];
         }
-        double dx[4], dy[4];
-        double mxx = 0, mxy = 0, myy = 0;
+        S dx[4], dy[4];
+        S mxx = 0, mxy = 0, myy = 0;
         for (int l = 0; l < nv; ++l) {
-            const FaceGeo &F = face[4 * static_cast<size_t>(i) + l];
+            const FaceGeo<S> &F = face[4 * static_cast<size_t>(i) + l];
             if (F.nbr >= 0) {
-                const double xj = cx[F.nbr] + F.sx, yj = cy[F.nbr] + F.sy;
+                const S xj = cx[F.nbr] + F.sx, yj = cy[F.nbr] + F.sy;
                 P.nbr[l * np + k] = inv[F.nbr];
                 P.back[l * np + k] = F.back;
                 dx[l] = xj - cx[i];
@@ -326,13 +332,13 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
             P.sn[(2 * l + 1) * np + k] = F.ny * F.len / area[i];
             P.rown[(2 * l) * np + k] = F.xm - cx[i];
             P.rown[(2 * l + 1) * np + k] = F.ym - cy[i];
-            P.dinv[l * np + k] = 1.0 / std::sqrt(dx[l] * dx[l] + dy[l] * dy[l]);
+            P.dinv[l * np + k] = S(1.0) / sqrt(dx[l] * dx[l] + dy[l] * dy[l]);
             mxx += dx[l] * dx[l];
             mxy += dx[l] * dy[l];
             myy += dy[l] * dy[l];
         }
-        const double det = mxx * myy - mxy * mxy;
-        if (!(det > 0.0)) {
+        const S det = mxx * myy - mxy * mxy;
+        if (!(det > S(0.0))) {
             *why = "degenerate least-squares stencil at cell " + std::to_string(i);
             return FVLBM_ERR_BAD_MESH;
         }
@@ -351,11 +357,11 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
 #pragma omp parallel for schedule(static)
         for (int k = 0; k < nc; ++k) {
             const int i = P.perm[k];
-            double best = 1e300;
+            S best = 1e300;
             for (int b : walls) {
                 const int a0 = bc.bedge_nodes[2 * b], a1 = bc.bedge_nodes[2 * b + 1];
-                best = std::min(best, point_segment(cx[i], cy[i], xy[2 * a0], xy[2 * a0 + 1],
-                                                    xy[2 * a1], xy[2 * a1 + 1]));
+                best = smin(best, point_segment(cx[i], cy[i], xy[2 * a0], xy[2 * a0 + 1],
+                                                xy[2 * a1], xy[2 * a1 + 1]));
             }
             P.wdist[k] = best;
         }
@@ -372,11 +378,11 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
             for (int a = 1; a < kQ; ++a) {
                 double s = 0.0;
                 for (int l = 0; l < nv; ++l) {
-                    const FaceGeo &F = face[4 * static_cast<size_t>(i) + l];
-                    const double en = ex[a] * F.nx + ey[a] * F.ny;
-                    if (en > 0.0) s += en * F.len;
+                    const FaceGeo<S> &F = face[4 * static_cast<size_t>(i) + l];
+                    const double en = ex[a] * value_of(F.nx) + ey[a] * value_of(F.ny);
+                    if (en > 0.0) s += en * value_of(F.len);
                 }
-                rate = std::max(rate, s / area[i]);
+                rate = std::max(rate, s / value_of(area[i]));
             }
         }
         P.dt = p.cfl / rate;
@@ -397,5 +403,10 @@ int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params
     }
     return FVLBM_OK;
 }
+
+template int prepare_instance_t<double>(const fvlbm_mesh &, const fvlbm_bc &, const fvlbm_params &,
+                                        const double *, PreparedT<double> *, std::string *);
+template int prepare_instance_t<Dual>(const fvlbm_mesh &, const fvlbm_bc &, const fvlbm_params &,
+                                      const Dual *, PreparedT<Dual> *, std::string *);
 
 }  // namespace fvlbm

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "fvlbm.h"
+#include "fvlbm_dual.h"
 
 namespace fvlbm {
 
@@ -24,8 +25,10 @@ constexpr int kNone = INT32_MIN;  // empty face slot (triangles have 3 faces, pa
 // One instance after preprocessing, in the library's internal cell order (Hilbert order of the
 // cell centroids), padded with inert cells (no faces, zero area) to a multiple of kBlock.
 // Face slot m of cell i is stored at [m * np + i] (vectors: [(2 m + c) * np + i]) so that one
-// thread per cell reads every array with unit stride.
-struct Prepared {
+// thread per cell reads every array with unit stride.  S is the scalar of the geometry: double,
+// or Dual when the derivative of the geometry with respect to node positions is wanted.
+template <class S>
+struct PreparedT {
     int nc = 0;                 // real cells
     int np = 0;                 // padded cells
     int nb = 0;                 // boundary faces (non-periodic boundary edges)
@@ -34,31 +37,46 @@ struct Prepared {
     std::vector<int> nbr;       // [4 np]  neighbour internal id, -(b+1) for boundary face b, kNone
     std::vector<int> back;      // [4 np]  face slot of this face in the neighbour's list (or -1)
     std::vector<int> nface;     // [np]    3 or 4 (0 for padding cells)
-    std::vector<double> gq;     // [8 np]  node k position minus centroid (x, y) for k < nface;
+    std::vector<S> gq;     // [8 np]  node k position minus centroid (x, y) for k < nface;
                                 //         face m joins nodes m and (m + 1) mod nface
-    std::vector<double> sn;     // [8 np]  n * Delta l / A of face m, out of the cell
-    std::vector<double> lsq;    // [8 np]  least-squares weight W_m = M^{-1} d_m
-    std::vector<double> dvec;   // [8 np]  d_m: neighbour centroid (+ shift) or face midpoint,
+    std::vector<S> sn;     // [8 np]  n * Delta l / A of face m, out of the cell
+    std::vector<S> lsq;    // [8 np]  least-squares weight W_m = M^{-1} d_m
+    std::vector<S> dvec;   // [8 np]  d_m: neighbour centroid (+ shift) or face midpoint,
                                 //         minus own centroid
-    std::vector<double> rown;   // [8 np]  face midpoint - own centroid
-    std::vector<double> rnbr;   // [8 np]  face midpoint - (neighbour centroid + periodic shift)
-    std::vector<double> dinv;   // [4 np]  1 / |d_m| (SST central diffusion distance)
-    std::vector<double> area;   // [np]    0 for padding cells
-    std::vector<double> wdist;  // [np]    distance to the nearest wall face (1e30 if none)
+    std::vector<S> rown;   // [8 np]  face midpoint - own centroid
+    std::vector<S> rnbr;   // [8 np]  face midpoint - (neighbour centroid + periodic shift)
+    std::vector<S> dinv;   // [4 np]  1 / |d_m| (SST central diffusion distance)
+    std::vector<S> area;   // [np]    0 for padding cells
+    std::vector<S> wdist;  // [np]    distance to the nearest wall face (1e30 if none)
     // boundary faces, ordered by input boundary-edge index (periodic edges dropped)
     std::vector<int> bowner;    // internal owner cell
     std::vector<int> btype;     // FVLBM_BC_*
     std::vector<double> bval;   // [5 nb] rho_b, u_b, v_b, k_b, omega_b
-    std::vector<double> bnrm;   // [2 nb] unit normal out of the fluid
-    std::vector<double> blen;   // [nb]
+    std::vector<S> bnrm;   // [2 nb] unit normal out of the fluid
+    std::vector<S> blen;   // [nb]
     std::vector<int> bedge_of;  // [nb] input boundary-edge index of each boundary face
     double dt = 0.0;
     std::vector<double> rho_i, u_i, v_i, k_i, w_i;  // initial fields, internal order [np]
 };
 
-// Validates and preprocesses one (mesh, bc, params) triple.  Returns FVLBM_OK or an error
-// code, with a message in *why.
-int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params &p,
-                     Prepared *out, std::string *why);
+using Prepared = PreparedT<double>;
+
+// Validates and preprocesses one (mesh, bc, params) triple, with node positions xy (the mesh's
+// own, or the same positions carrying derivatives).  Returns FVLBM_OK or an error code, with a
+// message in *why.  The cell order and the time step depend on the values only.
+template <class S>
+int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params &p, const S *xy,
+                       PreparedT<S> *out, std::string *why);
+extern template int prepare_instance_t<double>(const fvlbm_mesh &, const fvlbm_bc &,
+                                               const fvlbm_params &, const double *,
+                                               PreparedT<double> *, std::string *);
+extern template int prepare_instance_t<Dual>(const fvlbm_mesh &, const fvlbm_bc &,
+                                             const fvlbm_params &, const Dual *, PreparedT<Dual> *,
+                                             std::string *);
+
+inline int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params &p,
+                            Prepared *out, std::string *why) {
+    return prepare_instance_t<double>(m, bc, p, m.xy, out, why);
+}
 
 }  // namespace fvlbm

@@ -30,8 +30,10 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <type_traits>
 #include <vector>
 
+#include "fvlbm_dual.h"
 #include "fvlbm_internal.h"
 
 namespace fvlbm {
@@ -1115,7 +1117,8 @@ __global__ void k_gather_fields(const T *__restrict__ mac, const T *__restrict__
     out[5 * n + dst] = double(nut[off + k]);
 }
 
-// Per wall face momentum flux and Cp (FP64): out[3][nb_inst] = fx, fy, cp.
+// Per wall face momentum flux and Cp (FP64): out[5][nb_inst] = fx, fy, cp, dfx/dp, dfy/dp (the
+// last two are 0 except for the tangent type).
 template <class T>
 __global__ void k_wall_forces(const T *__restrict__ fn, const int *__restrict__ bowner,
                              const T *__restrict__ bnrm, const T *__restrict__ blen, int b0,
@@ -1125,7 +1128,7 @@ __global__ void k_wall_forces(const T *__restrict__ fn, const int *__restrict__ 
     if (q >= nbi) return;
     const int b = b0 + q;
     const size_t np = G.np;
-    out[q] = out[nbi + q] = out[2 * nbi + q] = 0.0;
+    out[q] = out[nbi + q] = out[2 * nbi + q] = out[3 * nbi + q] = out[4 * nbi + q] = 0.0;
     if (G.btype[b] != FVLBM_BC_WALL) return;
     const int i = bowner[b];
     T fi[kQ], fb[kQ], dr, r, u, v;
@@ -1133,16 +1136,22 @@ __global__ void k_wall_forces(const T *__restrict__ fn, const int *__restrict__ 
     moments(fi, T(rho0), dr, r, u, v);
     const T nx = bnrm[b], ny = bnrm[G.nbt + b];
     boundary_values(G.btype[b], G.bval + b, 0, G.nbt, nx, ny, fi, dr, r, u, v, T(rho0), fb);
-    double fx = 0, fy = 0;
+    double fx = 0, fy = 0, dfx = 0, dfy = 0;
     for (int a = 0; a < kQ; ++a) {
         const double en = double(ex_of(a)) * double(nx) + double(ey_of(a)) * double(ny);
         const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
         const double m = en * (double(fb[a]) + wa * rho0) * double(blen[b]);
+        // derivative: f_bc, the normal and the length may all depend on p
+        const double dm = tangent_of((T(ex_of(a)) * nx + T(ey_of(a)) * ny) * (fb[a] + T(wa * rho0)) * blen[b]);
         fx += ex_of(a) * m;
         fy += ey_of(a) * m;
+        dfx += ex_of(a) * dm;
+        dfy += ey_of(a) * dm;
     }
     out[q] = fx;
     out[nbi + q] = fy;
+    out[3 * nbi + q] = dfx;
+    out[4 * nbi + q] = dfy;
     out[2 * nbi + q] = (kCs2 * double(r) - kCs2 * rho0) / (0.5 * rho0 * uref * uref);
 }
 
@@ -1200,6 +1209,34 @@ __global__ void k_gather_fields_all(const T *__restrict__ mac, const T *__restri
     out[5 * n + j] = double(nut[i]);
 }
 
+// Tangent seed: df/dp of instance cells (off + k) from in[perm[k] * 9 + a]; the macros are
+// recomputed from the seeded f so that their derivatives agree.
+__global__ void k_seed_df(Dual *__restrict__ f, Dual *__restrict__ mac, const int *__restrict__ perm,
+                          int off, int nc, double rho0, size_t np, const double *__restrict__ in) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nc) return;
+    const int src = perm[k];
+    Dual d[kQ];
+    for (int a = 0; a < kQ; ++a) {
+        d[a] = f[a * np + off + k];
+        d[a].d = in[static_cast<size_t>(src) * kQ + a];
+        f[a * np + off + k] = d[a];
+    }
+    Dual dr, r, u, v;
+    moments(d, Dual(rho0), dr, r, u, v);
+    mac[off + k] = r;
+    mac[np + off + k] = u;
+    mac[2 * np + off + k] = v;
+}
+
+__global__ void k_gather_df(const Dual *__restrict__ f, const int *__restrict__ perm, int off, int nc,
+                            size_t np, double *__restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nc) return;
+    const int dst = perm[k];
+    for (int a = 0; a < kQ; ++a) out[static_cast<size_t>(dst) * kQ + a] = f[a * np + off + k].d;
+}
+
 }  // namespace fvlbm
 
 // ==================================================================== handle and C ABI
@@ -1207,11 +1244,20 @@ using namespace fvlbm;
 
 namespace {
 
+// Copy of one instance's input mesh, kept by tangent handles so that the geometry can be
+// differentiated with respect to node positions after create.
+struct MeshCopy {
+    std::vector<double> xy, bval, pshift;
+    std::vector<int> cell_ptr, cell_nodes, bnodes, btype, ppairs, perm;
+    fvlbm_params params{};
+};
+
 struct InstInfo {
-    int nc, np, nb, n_bedges_in, sst;
+    int nc, np, nb, n_bedges_in, sst, n_nodes;
     int cell_off, tile_off, bface_off;
     double dt, rho0, uref, lref, alpha_deg, nu;
     std::vector<int> bedge_of;   // boundary face -> input edge (local)
+    std::shared_ptr<MeshCopy> mesh;  // tangent handles only
 };
 
 struct KernelTimer {
@@ -1276,6 +1322,22 @@ struct fvlbm_handle {
 namespace {
 
 constexpr int kGraphSteps = 16;
+
+// Runs f with a value of the element type of the handle's precision (double, float or the
+// tangent Dual) so that one generic body serves every precision.
+template <class F>
+void dispatch(int precision, F &&f) {
+    if (precision == FVLBM_FP64)
+        f(double(0));
+    else if (precision == FVLBM_FP32_DEV)
+        f(float(0));
+    else
+        f(Dual());
+}
+
+// The fused stage kernels exist for double and float; the tangent type runs the two-pass kernels.
+template <class T>
+constexpr bool kHasFused = !std::is_same<T, Dual>::value;
 
 int cuda_fail(cudaError_t e) {
     if (e == cudaErrorMemoryAllocation) return FVLBM_ERR_OOM;
@@ -1407,15 +1469,18 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         T *nn = static_cast<T *>(h->nut[n]);
         T *sg = static_cast<T *>(h->sgrad), *f1 = static_cast<T *>(h->f1);
         const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
-        if (h->config != 2) {  // compact geometry, and stage 1's f^(1) with the new tau
-            launch(h, K_SST_GRAD, "sst_grad", [&] {
-                k_sst_grad<T, true><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG);
-            });
-            launch(h, K_SST_UPDATE, "sst_update", [&] {
-                k_sst_update<T, true><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn,
-                                                             static_cast<T *>(h->frel), CG);
-            });
-        } else {
+        if constexpr (kHasFused<T>) {
+            if (h->config != 2) {  // compact geometry, and stage 1's f^(1) with the new tau
+                launch(h, K_SST_GRAD, "sst_grad", [&] {
+                    k_sst_grad<T, true><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG);
+                });
+                launch(h, K_SST_UPDATE, "sst_update", [&] {
+                    k_sst_update<T, true><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G,
+                                                                 fn, static_cast<T *>(h->frel), CG);
+                });
+            }
+        }
+        if (h->config == 2) {
             launch(h, K_SST_GRAD, "sst_grad", [&] {
                 k_sst_grad<T, false><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG);
             });
@@ -1443,13 +1508,15 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         cudaMemcpyAsync(fn, s0, sizeof(T) * kQ * static_cast<size_t>(h->np), cudaMemcpyDeviceToDevice, s);
         return;
     }
-    if (h->config == 0) {
-        enqueue_fused<T, 256>(h, stats, h->hs[0]);
-        return;
-    }
-    if (h->config == 1) {
-        enqueue_fused<T, 128>(h, stats, h->hs[1]);
-        return;
+    if constexpr (kHasFused<T>) {
+        if (h->config == 0) {
+            enqueue_fused<T, 256>(h, stats, h->hs[0]);
+            return;
+        }
+        if (h->config == 1) {
+            enqueue_fused<T, 128>(h, stats, h->hs[1]);
+            return;
+        }
     }
     launch(h, K_STAGE1, "stage1", [&] { k_stage1<T><<<grid, block, 0, s>>>(fn, s0, tau, G); });
     launch(h, K_GRAD, "grad_f", [&] { k_grad<T><<<grid, block, 0, s>>>(s0, g, G); });
@@ -1476,10 +1543,10 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
 }
 
 void enqueue(fvlbm_handle *h, bool stats) {
-    if (h->precision == FVLBM_FP64)
-        enqueue_step<double>(h, stats);
-    else
-        enqueue_step<float>(h, stats);
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        enqueue_step<T>(h, stats);
+    });
 }
 
 int launches_per_step(const fvlbm_handle *h) {
@@ -1708,11 +1775,13 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
         if ((rc = upload_raw(h, &h->d_err, std::vector<int>(1, 0)))) return rc;
         if ((rc = upload_as<T>(h, &h->dvec, dvec))) return rc;
     }
-    if (h->fused) {
-        if ((rc = build_halos<T>(h, h->hs[0], 256, nbr, back, nface, inst_tile0))) return rc;
-        if ((rc = build_halos<T>(h, h->hs[1], 128, nbr, back, nface, inst_tile0))) return rc;
-        h->config = h->hs[0].ok ? 0 : (h->hs[1].ok ? 1 : 2);
-        if (h->config == 2) h->fused = false;
+    if constexpr (kHasFused<T>) {
+        if (h->fused) {
+            if ((rc = build_halos<T>(h, h->hs[0], 256, nbr, back, nface, inst_tile0))) return rc;
+            if ((rc = build_halos<T>(h, h->hs[1], 128, nbr, back, nface, inst_tile0))) return rc;
+            h->config = h->hs[0].ok ? 0 : (h->hs[1].ok ? 1 : 2);
+            if (h->config == 2) h->fused = false;
+        }
     }
     {
         std::vector<double> kt(k0), wt(w0);
@@ -1757,7 +1826,8 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     *out = nullptr;
     const int prec = params[0].precision;
     int sst = 0;
-    if (prec != FVLBM_FP64 && prec != FVLBM_FP32_DEV) return FVLBM_ERR_BAD_PARAM;
+    if (prec != FVLBM_FP64 && prec != FVLBM_FP32_DEV && prec != FVLBM_FP64_TANGENT)
+        return FVLBM_ERR_BAD_PARAM;
     for (int q = 0; q < n; ++q) {
         if (params[q].precision != prec || params[q].scheme != params[0].scheme)
             return FVLBM_ERR_BAD_PARAM;
@@ -1785,7 +1855,7 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     h->sst = sst != 0;
     h->scheme = params[0].scheme;
     if (h->scheme != 0 && h->scheme != 1) return FVLBM_ERR_BAD_PARAM;
-    h->fused = params[0].kernel_path == 0 && h->scheme == 0;
+    h->fused = params[0].kernel_path == 0 && h->scheme == 0 && prec != FVLBM_FP64_TANGENT;
     h->ninst = n;
     int cell_off = 0, bface_off = 0;
     std::vector<int> tile_inst, inst_tile0;
@@ -1808,6 +1878,28 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
         I.alpha_deg = params[q].alpha_deg;
         I.nu = params[q].nu;
         I.bedge_of = p.bedge_of;
+        I.n_nodes = meshes[q].n_nodes;
+        if (prec == FVLBM_FP64_TANGENT) {
+            const fvlbm_mesh &M = meshes[q];
+            const fvlbm_bc &B = bcs[q];
+            auto mc = std::make_shared<MeshCopy>();
+            mc->xy.assign(M.xy, M.xy + 2 * static_cast<size_t>(M.n_nodes));
+            mc->cell_ptr.assign(M.cell_ptr, M.cell_ptr + M.n_cells + 1);
+            mc->cell_nodes.assign(M.cell_nodes, M.cell_nodes + M.cell_ptr[M.n_cells]);
+            mc->bnodes.assign(B.bedge_nodes, B.bedge_nodes + 2 * static_cast<size_t>(B.n_bedges));
+            mc->btype.assign(B.bedge_type, B.bedge_type + B.n_bedges);
+            mc->bval.assign(B.bedge_val, B.bedge_val + 5 * static_cast<size_t>(B.n_bedges));
+            if (B.n_periodic > 0) {
+                mc->ppairs.assign(B.periodic_pairs, B.periodic_pairs + 2 * static_cast<size_t>(B.n_periodic));
+                mc->pshift.assign(B.periodic_shift, B.periodic_shift + 2 * static_cast<size_t>(B.n_periodic));
+            }
+            mc->perm = p.perm;
+            mc->params = params[q];
+            mc->params.rho_init = mc->params.u_init = mc->params.v_init = nullptr;
+            mc->params.k_init = mc->params.omega_init = nullptr;
+            mc->params.dt = p.dt;  // the time step is held fixed under differentiation
+            I.mesh = mc;
+        }
         inst_tile0.push_back(I.tile_off);
         for (int t = 0; t < p.np / kTile; ++t) tile_inst.push_back(q);
         ip[q] = InstParam{p.dt, params[q].nu, params[q].rho0,
@@ -1836,8 +1928,7 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
         free_all(h.get());
         return rc;
     }
-    rc = prec == FVLBM_FP64 ? allocate_state<double>(h.get(), P, inst_tile0)
-                            : allocate_state<float>(h.get(), P, inst_tile0);
+    dispatch(prec, [&](auto z_) { rc = allocate_state<decltype(z_)>(h.get(), P, inst_tile0); });
     if (rc) {
         free_all(h.get());
         return rc;
@@ -1864,6 +1955,55 @@ int perm_offset(const fvlbm_handle *h, int instance) {
     int o = 0;
     for (int q = 0; q < instance; ++q) o += h->inst[q].nc;
     return o;
+}
+
+// Wall force and coefficients of one instance; dout (may be NULL) receives their derivatives
+// (tangent handles), dalpha the derivative of the free-stream angle in radians.
+int forces_impl(fvlbm_handle *h, int instance, double dalpha, double *out, double *dout, double *cp) {
+    if (!h || instance < 0 || instance >= h->ninst || !out) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    const InstInfo &I = h->inst[instance];
+    const int nbi = I.nb;
+    int rc = io_buffer(h, sizeof(double) * 5 * std::max(nbi, 1));
+    if (rc) return rc;
+    if (nbi > 0) {
+        const int nb = (nbi + 255) / 256;
+        dispatch(h->precision, [&](auto z_) {
+            using T = decltype(z_);
+            k_wall_forces<T><<<nb, 256, 0, h->stream>>>(
+                static_cast<T *>(h->fn), h->d_bowner, static_cast<T *>(h->bnrm),
+                static_cast<T *>(h->blen), I.bface_off, nbi, I.rho0, I.uref, geo_of<T>(h), h->d_io);
+        });
+        CK(cudaGetLastError());
+    }
+    std::vector<double> host(5 * static_cast<size_t>(std::max(nbi, 1)));
+    CK(cudaMemcpyAsync(host.data(), h->d_io, host.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double fx = 0, fy = 0, dfx = 0, dfy = 0;
+    if (cp)
+        for (int b = 0; b < I.n_bedges_in; ++b) cp[b] = 0.0;
+    for (int b = 0; b < nbi; ++b) {
+        fx += host[b];
+        fy += host[nbi + b];
+        dfx += host[3 * nbi + b];
+        dfy += host[4 * nbi + b];
+        if (cp) cp[I.bedge_of[b]] = host[2 * nbi + b];
+    }
+    const double q = 0.5 * I.rho0 * I.uref * I.uref;
+    const double al = I.alpha_deg * M_PI / 180.0;
+    out[0] = fx;
+    out[1] = fy;
+    out[2] = (fx * std::cos(al) + fy * std::sin(al)) / (q * I.lref);
+    out[3] = (-fx * std::sin(al) + fy * std::cos(al)) / (q * I.lref);
+    if (dout) {
+        // C_D = (Fx cos a + Fy sin a) / (q l), C_L = (-Fx sin a + Fy cos a) / (q l)
+        const double ca = std::cos(al), sa = std::sin(al);
+        dout[0] = dfx;
+        dout[1] = dfy;
+        dout[2] = (dfx * ca + dfy * sa + dalpha * (-fx * sa + fy * ca)) / (q * I.lref);
+        dout[3] = (-dfx * sa + dfy * ca - dalpha * (fx * ca + fy * sa)) / (q * I.lref);
+    }
+    return FVLBM_OK;
 }
 
 }  // namespace
@@ -1952,12 +2092,11 @@ int fvlbm_get_f(fvlbm_handle *h, int instance, double *f) {
         int rc = io_buffer(h, sizeof(double) * kQ * n);
         if (rc) return rc;
         const int nb = (n + 255) / 256;
-        if (h->precision == FVLBM_FP64)
-            k_gather_f_all<double><<<nb, 256, 0, h->stream>>>(static_cast<double *>(h->fn), h->d_all_map, n,
+        dispatch(h->precision, [&](auto z_) {
+            using T = decltype(z_);
+            k_gather_f_all<T><<<nb, 256, 0, h->stream>>>(static_cast<T *>(h->fn), h->d_all_map, n,
                                                               h->np, h->d_tile_inst, h->d_ip, h->d_io);
-        else
-            k_gather_f_all<float><<<nb, 256, 0, h->stream>>>(static_cast<float *>(h->fn), h->d_all_map, n,
-                                                             h->np, h->d_tile_inst, h->d_ip, h->d_io);
+        });
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(f, h->d_io, sizeof(double) * kQ * n, cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
@@ -1968,12 +2107,11 @@ int fvlbm_get_f(fvlbm_handle *h, int instance, double *f) {
     if (rc) return rc;
     const int po = perm_offset(h, instance);
     const int nb = (I.nc + 255) / 256;
-    if (h->precision == FVLBM_FP64)
-        k_gather_f<double><<<nb, 256, 0, h->stream>>>(static_cast<double *>(h->fn), h->d_perm + po,
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        k_gather_f<T><<<nb, 256, 0, h->stream>>>(static_cast<T *>(h->fn), h->d_perm + po,
                                                       I.cell_off, I.nc, I.rho0, h->np, h->d_io);
-    else
-        k_gather_f<float><<<nb, 256, 0, h->stream>>>(static_cast<float *>(h->fn), h->d_perm + po,
-                                                     I.cell_off, I.nc, I.rho0, h->np, h->d_io);
+    });
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(f, h->d_io, sizeof(double) * kQ * I.nc, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -1989,17 +2127,13 @@ int fvlbm_set_f(fvlbm_handle *h, int instance, const double *f) {
         if (rc) return rc;
         CK(cudaMemcpyAsync(h->d_io, f, sizeof(double) * kQ * n, cudaMemcpyHostToDevice, h->stream));
         const int nb = (n + 255) / 256;
-        if (h->precision == FVLBM_FP64) {
-            k_scatter_f_all<double><<<nb, 256, 0, h->stream>>>(static_cast<double *>(h->fn),
-                                                               static_cast<double *>(h->mac), h->d_all_map, n,
+        dispatch(h->precision, [&](auto z_) {
+            using T = decltype(z_);
+            k_scatter_f_all<T><<<nb, 256, 0, h->stream>>>(static_cast<T *>(h->fn),
+                                                               static_cast<T *>(h->mac), h->d_all_map, n,
                                                                h->np, h->d_tile_inst, h->d_ip, h->d_io);
-            relax_all<double>(h);
-        } else {
-            k_scatter_f_all<float><<<nb, 256, 0, h->stream>>>(static_cast<float *>(h->fn),
-                                                              static_cast<float *>(h->mac), h->d_all_map, n,
-                                                              h->np, h->d_tile_inst, h->d_ip, h->d_io);
-            relax_all<float>(h);
-        }
+            relax_all<T>(h);
+        });
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(h->stream));
         return FVLBM_OK;
@@ -2010,15 +2144,12 @@ int fvlbm_set_f(fvlbm_handle *h, int instance, const double *f) {
     CK(cudaMemcpyAsync(h->d_io, f, sizeof(double) * kQ * I.nc, cudaMemcpyHostToDevice, h->stream));
     const int po = perm_offset(h, instance);
     const int nb = (I.nc + 255) / 256;
-    if (h->precision == FVLBM_FP64) {
-        k_scatter_f<double><<<nb, 256, 0, h->stream>>>(static_cast<double *>(h->fn), static_cast<double *>(h->mac),
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        k_scatter_f<T><<<nb, 256, 0, h->stream>>>(static_cast<T *>(h->fn), static_cast<T *>(h->mac),
                                                        h->d_perm + po, I.cell_off, I.nc, I.rho0, h->np, h->d_io);
-        relax_all<double>(h);
-    } else {
-        k_scatter_f<float><<<nb, 256, 0, h->stream>>>(static_cast<float *>(h->fn), static_cast<float *>(h->mac),
-                                                      h->d_perm + po, I.cell_off, I.nc, I.rho0, h->np, h->d_io);
-        relax_all<float>(h);
-    }
+        relax_all<T>(h);
+    });
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     return FVLBM_OK;
@@ -2034,14 +2165,12 @@ int fvlbm_get_fields(fvlbm_handle *h, int instance, double *rho, double *u, doub
         if (rc) return rc;
         const int nb = static_cast<int>((n + 255) / 256);
         const int c = h->turb;
-        if (h->precision == FVLBM_FP64)
-            k_gather_fields_all<double><<<nb, 256, 0, h->stream>>>(
-                static_cast<double *>(h->mac), static_cast<double *>(h->kk[c]), static_cast<double *>(h->ww[c]),
-                static_cast<double *>(h->nut[c]), h->d_all_map, static_cast<int>(n), h->np, h->d_io);
-        else
-            k_gather_fields_all<float><<<nb, 256, 0, h->stream>>>(
-                static_cast<float *>(h->mac), static_cast<float *>(h->kk[c]), static_cast<float *>(h->ww[c]),
-                static_cast<float *>(h->nut[c]), h->d_all_map, static_cast<int>(n), h->np, h->d_io);
+        dispatch(h->precision, [&](auto z_) {
+            using T = decltype(z_);
+            k_gather_fields_all<T><<<nb, 256, 0, h->stream>>>(
+                static_cast<T *>(h->mac), static_cast<T *>(h->kk[c]), static_cast<T *>(h->ww[c]),
+                static_cast<T *>(h->nut[c]), h->d_all_map, static_cast<int>(n), h->np, h->d_io);
+        });
         CK(cudaGetLastError());
         double *dst[6] = {rho, u, v, k, omega, nut};
         for (int q = 0; q < 6; ++q)
@@ -2058,14 +2187,12 @@ int fvlbm_get_fields(fvlbm_handle *h, int instance, double *rho, double *u, doub
     const int po = perm_offset(h, instance);
     const int nb = (I.nc + 255) / 256;
     const int c = h->turb;
-    if (h->precision == FVLBM_FP64)
-        k_gather_fields<double><<<nb, 256, 0, h->stream>>>(
-            static_cast<double *>(h->mac), static_cast<double *>(h->kk[c]), static_cast<double *>(h->ww[c]),
-            static_cast<double *>(h->nut[c]), h->d_perm + po, I.cell_off, I.nc, h->np, h->d_io);
-    else
-        k_gather_fields<float><<<nb, 256, 0, h->stream>>>(
-            static_cast<float *>(h->mac), static_cast<float *>(h->kk[c]), static_cast<float *>(h->ww[c]),
-            static_cast<float *>(h->nut[c]), h->d_perm + po, I.cell_off, I.nc, h->np, h->d_io);
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        k_gather_fields<T><<<nb, 256, 0, h->stream>>>(
+            static_cast<T *>(h->mac), static_cast<T *>(h->kk[c]), static_cast<T *>(h->ww[c]),
+            static_cast<T *>(h->nut[c]), h->d_perm + po, I.cell_off, I.nc, h->np, h->d_io);
+    });
     CK(cudaGetLastError());
     double *dst[6] = {rho, u, v, k, omega, nut};
     for (int q = 0; q < 6; ++q)
@@ -2076,42 +2203,119 @@ int fvlbm_get_fields(fvlbm_handle *h, int instance, double *rho, double *u, doub
 }
 
 int fvlbm_forces(fvlbm_handle *h, int instance, double *out, double *cp) {
-    if (!h || instance < 0 || instance >= h->ninst || !out) return FVLBM_ERR_BAD_PARAM;
+    return forces_impl(h, instance, 0.0, out, nullptr, cp);
+}
+
+int fvlbm_tangent_seed(fvlbm_handle *h, int instance, const double *dbedge_val, const double *df) {
+    if (!h || instance < 0 || instance >= h->ninst) return FVLBM_ERR_BAD_PARAM;
+    if (h->precision != FVLBM_FP64_TANGENT) return FVLBM_ERR_NOT_SUPPORTED;
     CK(cudaSetDevice(h->device));
     const InstInfo &I = h->inst[instance];
-    const int nbi = I.nb;
-    int rc = io_buffer(h, sizeof(double) * 3 * std::max(nbi, 1));
-    if (rc) return rc;
-    if (nbi > 0) {
-        const int nb = (nbi + 255) / 256;
-        if (h->precision == FVLBM_FP64)
-            k_wall_forces<double><<<nb, 256, 0, h->stream>>>(
-                static_cast<double *>(h->fn), h->d_bowner, static_cast<double *>(h->bnrm),
-                static_cast<double *>(h->blen), I.bface_off, nbi, I.rho0, I.uref, geo_of<double>(h), h->d_io);
-        else
-            k_wall_forces<float><<<nb, 256, 0, h->stream>>>(
-                static_cast<float *>(h->fn), h->d_bowner, static_cast<float *>(h->bnrm),
-                static_cast<float *>(h->blen), I.bface_off, nbi, I.rho0, I.uref, geo_of<float>(h), h->d_io);
+    if (dbedge_val && I.nb > 0) {
+        // boundary values are field-major [5][nbt]; the instance's faces are one run per field
+        std::vector<Dual> bv(static_cast<size_t>(5) * I.nb);
+        Dual *dev = static_cast<Dual *>(h->bval);
+        for (int c = 0; c < 5; ++c)
+            CK(cudaMemcpyAsync(bv.data() + static_cast<size_t>(c) * I.nb,
+                               dev + static_cast<size_t>(c) * h->nbt + I.bface_off, sizeof(Dual) * I.nb,
+                               cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int b = 0; b < I.nb; ++b)
+            for (int c = 0; c < 5; ++c)
+                bv[static_cast<size_t>(c) * I.nb + b].d = dbedge_val[5 * static_cast<size_t>(I.bedge_of[b]) + c];
+        for (int c = 0; c < 5; ++c)
+            CK(cudaMemcpyAsync(dev + static_cast<size_t>(c) * h->nbt + I.bface_off,
+                               bv.data() + static_cast<size_t>(c) * I.nb, sizeof(Dual) * I.nb,
+                               cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    if (df && I.nc > 0) {
+        const size_t bytes = sizeof(double) * kQ * static_cast<size_t>(I.nc);
+        int rc = io_buffer(h, bytes);
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(h->d_io, df, bytes, cudaMemcpyHostToDevice, h->stream));
+        const int nb = (I.nc + 255) / 256;
+        k_seed_df<<<nb, 256, 0, h->stream>>>(static_cast<Dual *>(h->fn), static_cast<Dual *>(h->mac),
+                                             h->d_perm + perm_offset(h, instance), I.cell_off, I.nc, I.rho0,
+                                             h->np, h->d_io);
         CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->stream));
     }
-    std::vector<double> host(3 * static_cast<size_t>(std::max(nbi, 1)));
-    CK(cudaMemcpyAsync(host.data(), h->d_io, host.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    double fx = 0, fy = 0;
-    if (cp)
-        for (int b = 0; b < I.n_bedges_in; ++b) cp[b] = 0.0;
-    for (int b = 0; b < nbi; ++b) {
-        fx += host[b];
-        fy += host[nbi + b];
-        if (cp) cp[I.bedge_of[b]] = host[2 * nbi + b];
-    }
-    const double q = 0.5 * I.rho0 * I.uref * I.uref;
-    const double al = I.alpha_deg * M_PI / 180.0;
-    out[0] = fx;
-    out[1] = fy;
-    out[2] = (fx * std::cos(al) + fy * std::sin(al)) / (q * I.lref);
-    out[3] = (-fx * std::sin(al) + fy * std::cos(al)) / (q * I.lref);
     return FVLBM_OK;
+}
+
+int fvlbm_tangent_seed_nodes(fvlbm_handle *h, int instance, const double *dxy) {
+    if (!h || instance < 0 || instance >= h->ninst || !dxy) return FVLBM_ERR_BAD_PARAM;
+    if (h->precision != FVLBM_FP64_TANGENT) return FVLBM_ERR_NOT_SUPPORTED;
+    CK(cudaSetDevice(h->device));
+    const InstInfo &I = h->inst[instance];
+    const MeshCopy &mc = *I.mesh;
+    // the instance's preprocessing again, on node positions that carry d(x, y)/dp
+    std::vector<Dual> xyd(mc.xy.size());
+    for (size_t k = 0; k < xyd.size(); ++k) xyd[k] = Dual(mc.xy[k], dxy[k]);
+    const fvlbm_mesh M{I.n_nodes, mc.xy.data(), I.nc, mc.cell_ptr.data(), mc.cell_nodes.data()};
+    const int nbe = static_cast<int>(mc.btype.size());
+    const fvlbm_bc B{nbe, mc.bnodes.data(), mc.btype.data(), mc.bval.data(),
+                     static_cast<int>(mc.ppairs.size() / 2), mc.ppairs.data(), mc.pshift.data()};
+    PreparedT<Dual> D;
+    std::string why;
+    const int rc = prepare_instance_t<Dual>(M, B, mc.params, xyd.data(), &D, &why);
+    if (rc) {
+        fprintf(stderr, "fvlbm_tangent_seed_nodes: %s\n", why.c_str());
+        return rc;
+    }
+    if (D.perm != mc.perm || D.np != I.np || D.nb != I.nb) return FVLBM_ERR_NOT_SUPPORTED;
+    // Derivative parts into the device arrays.  dst holds ncomp runs of n values at
+    // dst[c * stride + off]; get(c, k) is the Dual of component c, item k.
+    const size_t np = h->np, nbt = h->nbt;
+    auto put = [&](void *dst, int ncomp, size_t stride, size_t off, size_t n, auto get) -> int {
+        if (n == 0) return FVLBM_OK;
+        std::vector<Dual> run(n);
+        Dual *dev = static_cast<Dual *>(dst);
+        for (int c = 0; c < ncomp; ++c) {
+            CK(cudaMemcpy(run.data(), dev + c * stride + off, n * sizeof(Dual), cudaMemcpyDeviceToHost));
+            for (size_t k = 0; k < n; ++k) run[k].d = get(c, k).d;
+            CK(cudaMemcpy(dev + c * stride + off, run.data(), n * sizeof(Dual), cudaMemcpyHostToDevice));
+        }
+        return FVLBM_OK;
+    };
+    CK(cudaStreamSynchronize(h->stream));
+    const size_t pn = I.np, co = I.cell_off, nb = I.nb, bo = I.bface_off;
+    int e = 0;
+    e = e ? e : put(h->sn, 8, np, co, pn, [&](int c, size_t k) { return D.sn[c * pn + k]; });
+    e = e ? e : put(h->lsq, 8, np, co, pn, [&](int c, size_t k) { return D.lsq[c * pn + k]; });
+    e = e ? e : put(h->rown, 8, np, co, pn, [&](int c, size_t k) { return D.rown[c * pn + k]; });
+    e = e ? e : put(h->rnbr, 8, np, co, pn, [&](int c, size_t k) { return D.rnbr[c * pn + k]; });
+    e = e ? e : put(h->dinv, 4, np, co, pn, [&](int c, size_t k) { return D.dinv[c * pn + k]; });
+    e = e ? e : put(h->area, 1, np, co, pn, [&](int, size_t k) { return D.area[k]; });
+    e = e ? e : put(h->wdist, 1, np, co, pn, [&](int, size_t k) { return D.wdist[k]; });
+    e = e ? e : put(h->bnrm, 2, nbt, bo, nb, [&](int c, size_t f) { return D.bnrm[2 * f + c]; });
+    e = e ? e : put(h->blen, 1, nbt, bo, nb, [&](int, size_t f) { return D.blen[f]; });
+    return e;
+}
+
+int fvlbm_get_f_tangent(fvlbm_handle *h, int instance, double *df) {
+    if (!h || instance < 0 || instance >= h->ninst || !df) return FVLBM_ERR_BAD_PARAM;
+    if (h->precision != FVLBM_FP64_TANGENT) return FVLBM_ERR_NOT_SUPPORTED;
+    CK(cudaSetDevice(h->device));
+    const InstInfo &I = h->inst[instance];
+    if (I.nc == 0) return FVLBM_OK;
+    const size_t bytes = sizeof(double) * kQ * static_cast<size_t>(I.nc);
+    int rc = io_buffer(h, bytes);
+    if (rc) return rc;
+    const int nb = (I.nc + 255) / 256;
+    k_gather_df<<<nb, 256, 0, h->stream>>>(static_cast<const Dual *>(h->fn), h->d_perm + perm_offset(h, instance),
+                                           I.cell_off, I.nc, h->np, h->d_io);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(df, h->d_io, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FVLBM_OK;
+}
+
+int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *out, double *dout) {
+    if (!h || !dout) return FVLBM_ERR_BAD_PARAM;
+    if (h->precision != FVLBM_FP64_TANGENT) return FVLBM_ERR_NOT_SUPPORTED;
+    return forces_impl(h, instance, dalpha, out, dout, nullptr);
 }
 
 int fvlbm_info(fvlbm_handle *h, int instance, int *n_cells, int *n_bedges, double *dt) {
@@ -2184,7 +2388,9 @@ int fvlbm_autotune(fvlbm_handle *h, int trial_steps, int *chosen, double *ms_per
         return FVLBM_OK;
     }
     // snapshot of the state a step reads (the rest is scratch)
-    const size_t np = h->np, ts = h->precision == FVLBM_FP64 ? sizeof(double) : sizeof(float);
+    size_t ts = 0;
+    dispatch(h->precision, [&](auto z_) { ts = sizeof(z_); });
+    const size_t np = h->np;
     std::vector<std::pair<void *, size_t>> st = {
         {h->fn, kQ * np * ts}, {h->frel, kQ * np * ts}, {h->mac, 3 * np * ts}, {h->tau, np * ts}};
     for (int b = 0; b < 2; ++b) {

@@ -15,9 +15,12 @@ import numpy as np
 from . import build as _build
 
 FVLBM_OK = 0
+FVLBM_ERR_BAD_PARAM = -3
 FVLBM_ERR_DIVERGED = -6
+FVLBM_ERR_NOT_SUPPORTED = -7
 FVLBM_FP64 = 0
 FVLBM_FP32_DEV = 1
+FVLBM_FP64_TANGENT = 2
 SCHEME_IMEX = 0
 SCHEME_EULER = 1
 Q = 9
@@ -89,6 +92,10 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_footprint.argtypes = [vp, P(C.c_longlong), P(i)]
     lib.fvlbm_profile_kernels.argtypes = [vp, i, i, vp, vp, vp]
     lib.fvlbm_autotune.argtypes = [vp, i, P(i), vp]
+    lib.fvlbm_tangent_seed.argtypes = [vp, i, vp, vp]
+    lib.fvlbm_get_f_tangent.argtypes = [vp, i, vp]
+    lib.fvlbm_tangent_seed_nodes.argtypes = [vp, i, vp]
+    lib.fvlbm_forces_tangent.argtypes = [vp, i, d, vp, vp]
     lib.fvlbm_destroy.argtypes = [vp]
     lib.fvlbm_destroy.restype = None
     lib.fvlbm_strerror.argtypes = [i]
@@ -226,6 +233,37 @@ def fvlbm_autotune(h, trial_steps: int = 5):
     return names[chosen.value], {names[k]: float(ms[k]) for k in range(3) if ms[k] >= 0}
 
 
+def fvlbm_tangent_seed(h, instance: int, dbedge_val: np.ndarray | None = None,
+                       df: np.ndarray | None = None) -> None:
+    """Seed d/dp of the boundary values ([n_bedges, 5], input edge order) and/or of f
+    ([n_cells, 9]) on a FVLBM_FP64_TANGENT handle."""
+    bv = None if dbedge_val is None else np.ascontiguousarray(dbedge_val, np.float64)
+    f = None if df is None else np.ascontiguousarray(df, np.float64)
+    _check(load().fvlbm_tangent_seed(h, instance, _p(bv), _p(f)), "fvlbm_tangent_seed")
+
+
+def fvlbm_tangent_seed_nodes(h, instance: int, dxy: np.ndarray) -> None:
+    """Seed d(x, y)/dp of every mesh node ([n_nodes, 2]) on a FVLBM_FP64_TANGENT handle."""
+    d = np.ascontiguousarray(dxy, np.float64)
+    _check(load().fvlbm_tangent_seed_nodes(h, instance, _p(d)), "fvlbm_tangent_seed_nodes")
+
+
+def fvlbm_get_f_tangent(h, instance: int = 0) -> np.ndarray:
+    n, _, _ = fvlbm_info(h, instance)
+    df = np.empty((n, Q))
+    _check(load().fvlbm_get_f_tangent(h, instance, _p(df)), "fvlbm_get_f_tangent")
+    return df
+
+
+def fvlbm_forces_tangent(h, instance: int = 0, dalpha: float = 0.0) -> tuple[dict, dict]:
+    """(forces, d forces / dp); dalpha = d(alpha in radians)/dp."""
+    out, dout = np.zeros(4), np.zeros(4)
+    _check(load().fvlbm_forces_tangent(h, instance, float(dalpha), _p(out), _p(dout)),
+           "fvlbm_forces_tangent")
+    keys = ("fx", "fy", "cd", "cl")
+    return dict(zip(keys, out)), dict(zip(keys, dout))
+
+
 def fvlbm_destroy(h) -> None:
     if h:
         load().fvlbm_destroy(h)
@@ -301,3 +339,15 @@ class Solver:
 
     def profile_kernels(self, n_steps: int) -> dict:
         return fvlbm_profile_kernels(self.h, n_steps)
+
+    def tangent_seed(self, dbedge_val=None, df=None, i: int = 0) -> None:
+        fvlbm_tangent_seed(self.h, i, dbedge_val, df)
+
+    def tangent_seed_nodes(self, dxy, i: int = 0) -> None:
+        fvlbm_tangent_seed_nodes(self.h, i, dxy)
+
+    def get_f_tangent(self, i: int = 0) -> np.ndarray:
+        return fvlbm_get_f_tangent(self.h, i)
+
+    def forces_tangent(self, i: int = 0, dalpha: float = 0.0):
+        return fvlbm_forces_tangent(self.h, i, dalpha)
