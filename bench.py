@@ -451,6 +451,30 @@ def _e2e(torch, fvlbm, solver, stream, args, world, dist):
             "steps": k, "ms_per_step": el / k * 1e3}
 
 
+def run_profile_mode(args):
+    """Minimal run for ncu: one solver, warmup + steps, nothing else (launch list / capture)."""
+    import torch
+    from paper_1812_00394_gb300 import fvlbm
+    torch.cuda.set_device(0)
+    cases = make_workload(args.workload)
+    prec = fvlbm.FVLBM_FP32_DEV if args.precision == "fp32" else fvlbm.FVLBM_FP64
+    s = fvlbm.Solver(cases, precision=prec, device=0, kernel_path=args.kernel_path)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    st = s.step(0, stats=False)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    _, lps = s.footprint()
+    print(json.dumps({"mode": "profile", "workload": args.workload, "precision": args.precision,
+                      "kernel_path": args.kernel_path,
+                      "cells": sum(c.mesh.n_cells for c in cases), "launches_per_step": lps,
+                      "warmup": args.warmup, "steps": args.steps, "wall_s": el, "st": st}))
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -465,6 +489,8 @@ def main():
     ap.add_argument("--profile-mode", action="store_true",
                     help="only build the workload and run warmup + steps (for ncu)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--kernel-path", type=int, default=0, choices=[0, 1],
+                    help="profile mode: 0 fused stage kernels, 1 two-pass kernels")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -61,3 +61,9 @@ def test_rank_workloads_differ_but_are_seeded(rank):
     b = mg.batched_sweep(seed=bench.rank_seed(rank), scale=0.02, n_cavity=2, n_bfs=0, n_naca=0)
     assert [c.mesh.n_cells for c in a] == [c.mesh.n_cells for c in b]
     assert all((x.mesh.xy == y.mesh.xy).all() for x, y in zip(a, b))
+
+
+def test_bench_entry_points_exist():
+    """Every mode main() dispatches to is defined (the ncu profile mode included)."""
+    for name in ("run_ours", "run_reference", "run_profile_mode"):
+        assert callable(getattr(bench, name)), name
