@@ -49,6 +49,18 @@ template <class T>
 __device__ __forceinline__ T w_of(int a) {
     return a == 0 ? T(4.0 / 9.0) : (a < 5 ? T(1.0 / 9.0) : T(1.0 / 36.0));
 }
+// e_alpha . (x, y) for a compile-time alpha (unrolled loops): the components are 0 or +-1, so
+// the product is a sign change, a sum or a difference; writing it out keeps the compiler from
+// issuing the multiplications by 0 that IEEE semantics would otherwise force.
+template <class T>
+__device__ __forceinline__ T edot(int a, T x, T y) {
+    const int cx = ex_of(a), cy = ey_of(a);
+    if (cx == 0 && cy == 0) return T(0);
+    if (cx == 0) return cy > 0 ? y : -y;
+    if (cy == 0) return cx > 0 ? x : -x;
+    const T xs = cx > 0 ? x : -x;
+    return cy > 0 ? xs + y : xs - y;
+}
 
 // SST constants (Sec. 2)
 constexpr double kA1 = 0.31, kBstar = 0.09, kKappa = 0.41;
@@ -86,8 +98,10 @@ __device__ __forceinline__ void moments(const T *d, T rho0, T &drho, T &rho, T &
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
         s += d[a];
-        jx += T(ex_of(a)) * d[a];
-        jy += T(ey_of(a)) * d[a];
+        if (ex_of(a) > 0) jx += d[a];
+        if (ex_of(a) < 0) jx -= d[a];
+        if (ey_of(a) > 0) jy += d[a];
+        if (ey_of(a) < 0) jy -= d[a];
     }
     drho = s;
     rho = rho0 + s;
@@ -102,7 +116,7 @@ __device__ __forceinline__ void feq_dev(T drho, T rho, T u, T v, T *eq) {
     const T uu = T(1.5) * (u * u + v * v);
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
-        const T eu = T(ex_of(a)) * u + T(ey_of(a)) * v;
+        const T eu = edot<T>(a, u, v);
         eq[a] = w_of<T>(a) * (drho + rho * (T(3) * eu + T(4.5) * eu * eu - uu));
     }
 }
@@ -128,7 +142,7 @@ __device__ __forceinline__ void boundary_values(int type, const T *__restrict__ 
         feq_dev(rb - rho0, rb, ub, vb, eqB);
 #pragma unroll
         for (int a = 0; a < kQ; ++a) {
-            const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
+            const T en = edot<T>(a, snx, sny);
             out[a] = en < T(0) ? eqB[a] : fP[a];
         }
     }
@@ -390,7 +404,7 @@ __global__ void __launch_bounds__(kTile)
             const T rnx = G.rnbr[(2 * m) * np + i], rny = G.rnbr[(2 * m + 1) * np + i];
 #pragma unroll
             for (int a = 0; a < kQ; ++a) {
-                const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
+                const T en = edot<T>(a, snx, sny);
                 T fv;
                 if (en >= T(0))
                     fv = fi[a] + g[(2 * a) * np + i] * rox + g[(2 * a + 1) * np + i] * roy;
@@ -404,7 +418,7 @@ __global__ void __launch_bounds__(kTile)
             moments(fi, rho0, dr, r, u, v);
             boundary_values(G.btype[b], G.bval + b, 0, G.nbt, snx, sny, fi, dr, r, u, v, rho0, fb);
 #pragma unroll
-            for (int a = 0; a < kQ; ++a) acc[a] += (T(ex_of(a)) * snx + T(ey_of(a)) * sny) * fb[a];
+            for (int a = 0; a < kQ; ++a) acc[a] += edot<T>(a, snx, sny) * fb[a];
         }
     }
     stage_update<T, STAGE, STATS, kTile>(i, np, fi, acc, P, fs_out, fn, Bacc, Cacc, tau, mac, partial,
@@ -684,7 +698,7 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
             moments(fi, rho0, dr, r, u, v);
             boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, snx, sny, fi, dr, r, u, v, rho0, fb);
 #pragma unroll
-            for (int a = 1; a < kQ; ++a) acc[a] += (T(ex_of(a)) * snx + T(ey_of(a)) * sny) * fb[a];
+            for (int a = 1; a < kQ; ++a) acc[a] += edot<T>(a, snx, sny) * fb[a];
         } else {
             const int j = static_cast<int>(w & 0xFFFFu);
             // face offsets from this cell's centroid and from the neighbour's
@@ -692,7 +706,7 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
             const T rnx = rox - sD[(2 * m) * G0 + t], rny = roy - sD[(2 * m + 1) * G0 + t];
 #pragma unroll
             for (int a = 1; a < kQ; ++a) {
-                const T en = T(ex_of(a)) * snx + T(ey_of(a)) * sny;
+                const T en = edot<T>(a, snx, sny);
                 const bool own = en >= T(0);           // upwind side, branch free
                 const int src = own ? t : j;
                 const T rx = own ? rox : rnx, ry = own ? roy : rny;
