@@ -76,6 +76,7 @@ typedef struct oracle {
     double *bval;                /* [nb * 5]: rho_b, u_b, v_b, k_b, omega_b */
     double *bxm, *bym, *bnx, *bny, *blen;
     double nu, rho0, dt, uref, lref, alpha_deg;
+    double *dtc;                 /* local time stepping: dt of each cell (NULL: dt everywhere) */
     int sst;
     int scheme;                  /* 0: IMEX Runge-Kutta (Part II); 1: explicit Euler (Part I) */
     double *f;                   /* [nc * Q], cell-major */
@@ -86,6 +87,9 @@ typedef struct oracle {
     double *fn, *fst, *ga[3], *gc[3], *gradf, *fbc, *feqs, *X;
     double *gu, *gv, *gk, *gw, *rk, *rw, *f1, *Sabs;
 } oracle;
+
+/* Time step of cell i: its own under local time stepping, else the global one. */
+static double cell_dt(const struct oracle *o, int i) { return o->dtc ? o->dtc[i] : o->dt; }
 
 /* ------------------------------------------------------------------ equilibrium */
 /* f^eq_alpha(rho, u) = w_alpha rho [1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u]: the second-order
@@ -142,7 +146,7 @@ static void *xcalloc(size_t n, size_t s) { return calloc(n ? n : 1, s); }
 
 void oracle_destroy(oracle *o);
 
-/* params: [nu, rho0, dt, cfl, sst, uref, lref, alpha_deg, scheme] */
+/* params: [nu, rho0, dt, cfl, sst, uref, lref, alpha_deg, scheme, local_dt] */
 oracle *oracle_create(int n_nodes, const double *xy, int n_cells, const int *cell_ptr,
                       const int *cell_nodes, int n_bedges, const int *bedge_nodes,
                       const int *bedge_type, const double *bedge_val, int n_periodic,
@@ -164,6 +168,11 @@ oracle *oracle_create(int n_nodes, const double *xy, int n_cells, const int *cel
     o->lref = params[6];
     o->alpha_deg = params[7];
     o->scheme = (int)params[8];
+    int local_dt = params[9] != 0.0;
+    if (local_dt && !(cfl > 0.0)) { /* local steps are CFL * the cell's limit: need a CFL */
+        free(o);
+        return NULL;
+    }
 
     o->nface = (int *)xcalloc(nc, sizeof(int));
     o->face = (oface *)xcalloc((size_t)nc * 4, sizeof(oface));
@@ -329,10 +338,16 @@ oracle *oracle_create(int n_nodes, const double *xy, int n_cells, const int *cel
         o->tau[i] = (o->nu + o->nut[i]) / CS2;
     }
 
-    /* time step: given, or CFL * (forward-Euler upwind limit) when dt <= 0 */
-    if (o->dt <= 0.0) {
+    /* time step: given, or CFL * (forward-Euler upwind limit) when dt <= 0.  The limit of cell
+     * i is 1 / max_alpha sum_m max(e_alpha . n_m, 0) Delta l_m / A_i; the global step takes the
+     * smallest over the cells.  Local time stepping (steady-state acceleration, not in the
+     * paper) gives every cell its own dt_i = CFL * limit_i instead; dt then reports the
+     * smallest of them, which is the global step. */
+    if (o->dt <= 0.0 || local_dt) {
+        if (local_dt) o->dtc = (double *)xcalloc(nc, sizeof(double));
         double lim = 0.0;
-        for (int i = 0; i < nc; i++)
+        for (int i = 0; i < nc; i++) {
+            double rate = 0.0;
             for (int a = 0; a < Q; a++) {
                 double s = 0.0;
                 for (int l = 0; l < o->nface[i]; l++) {
@@ -341,8 +356,11 @@ oracle *oracle_create(int n_nodes, const double *xy, int n_cells, const int *cel
                     if (en > 0) s += en * F->len;
                 }
                 s /= o->area[i];
-                if (s > lim) lim = s;
+                if (s > rate) rate = s;
             }
+            if (rate > lim) lim = rate;
+            if (local_dt) o->dtc[i] = cfl / rate;
+        }
         o->dt = cfl / lim;
     }
     return o;
@@ -357,7 +375,7 @@ void oracle_destroy(oracle *o)
     free(o->f); free(o->fn); free(o->fst); free(o->feqs); free(o->X);
     for (int J = 0; J < 3; J++) { free(o->ga[J]); free(o->gc[J]); }
     free(o->gradf); free(o->fbc);
-    free(o->rho); free(o->ux); free(o->uy); free(o->k); free(o->om); free(o->nut); free(o->tau);
+    free(o->rho); free(o->ux); free(o->uy); free(o->k); free(o->om); free(o->nut); free(o->tau); free(o->dtc);
     free(o->gu); free(o->gv); free(o->gk); free(o->gw); free(o->rk); free(o->rw);
     free(o->f1); free(o->Sabs);
     free(o);
@@ -658,8 +676,9 @@ static void sst_update(oracle *o)
     for (int i = 0; i < nc; i++) {
         double f1 = o->f1[i];
         double beta = f1 * B1 + (1.0 - f1) * B2;
-        double kn = (o->k[i] + o->dt * o->rk[i]) / (1.0 + o->dt * BSTAR * o->om[i]);
-        double wn = (o->om[i] + o->dt * o->rw[i]) / (1.0 + o->dt * beta * o->om[i]);
+        double dt = cell_dt(o, i);
+        double kn = (o->k[i] + dt * o->rk[i]) / (1.0 + dt * BSTAR * o->om[i]);
+        double wn = (o->om[i] + dt * o->rw[i]) / (1.0 + dt * beta * o->om[i]);
         o->k[i] = kn > 0.0 ? kn : 0.0;
         o->om[i] = wn > wmin ? wn : wmin;
     }
@@ -685,7 +704,6 @@ static int imex_step(oracle *o)
 {
     int nc = o->nc;
     size_t nq = (size_t)nc * Q;
-    double dt = o->dt;
     if (o->sst) sst_update(o); /* Step 1 */
     else
         for (int i = 0; i < nc; i++) o->tau[i] = o->nu / CS2;
@@ -694,6 +712,7 @@ static int imex_step(oracle *o)
     for (int J = 0; J < 3; J++) {
         for (int i = 0; i < nc; i++) {
             double tau = o->tau[i];
+            double dt = cell_dt(o, i);
             double *X = &o->X[(size_t)i * Q];
             const double *fn = &o->fn[(size_t)i * Q];
             for (int a = 0; a < Q; a++) {
@@ -724,6 +743,7 @@ static int imex_step(oracle *o)
         convection(o, o->fst, o->ga[J]); /* Step 2 for the next stage / the final update */
     }
     for (size_t q = 0; q < nq; q++) {
+        double dt = cell_dt(o, (int)(q / Q));
         double s = o->fn[q];
         for (int J = 0; J < 3; J++) s += dt * (NT[J] * o->ga[J][q] + NI[J] * o->gc[J][q]);
         o->f[q] = s;
@@ -759,12 +779,12 @@ static int finish_step(oracle *o)
 static int euler_step(oracle *o)
 {
     int nc = o->nc;
-    double dt = o->dt;
     if (o->sst) sst_update(o);
     else
         for (int i = 0; i < nc; i++) o->tau[i] = o->nu / CS2;
     convection(o, o->f, o->ga[0]);
     for (int i = 0; i < nc; i++) {
+        double dt = cell_dt(o, i);
         double *f = &o->f[(size_t)i * Q];
         double r, u, v, eq[Q];
         moments(f, &r, &u, &v);
@@ -787,6 +807,12 @@ int oracle_step(oracle *o, int n)
 
 int oracle_n_cells(const oracle *o) { return o->nc; }
 double oracle_dt(const oracle *o) { return o->dt; }
+
+/* dt of every cell (the global dt everywhere unless local time stepping is on). */
+void oracle_dt_cells(const oracle *o, double *out)
+{
+    for (int i = 0; i < o->nc; i++) out[i] = cell_dt(o, i);
+}
 double oracle_residual(const oracle *o) { return o->residual; }
 double oracle_moment_defect(const oracle *o) { return o->moment_defect; }
 

@@ -55,6 +55,7 @@ def _load():
         for name in ("oracle_dt", "oracle_residual", "oracle_moment_defect", "oracle_mass"):
             getattr(lib, name).argtypes = [vp]
             getattr(lib, name).restype = C.c_double
+        lib.oracle_dt_cells.argtypes = [vp, _D]
         lib.oracle_n_cells.argtypes = [vp]
         lib.oracle_n_cells.restype = C.c_int
         lib.oracle_get_f.argtypes = [vp, _D]
@@ -98,7 +99,7 @@ class Oracle:
         self._keep = (m, rho, u, v, k, w)
         params = np.array([case.nu, case.rho0, case.dt if dt is None else dt, case.cfl,
                            float(case.sst if sst is None else sst), case.uref, case.lref,
-                           case.alpha_deg, float(scheme)], np.float64)
+                           case.alpha_deg, float(scheme), float(case.local_dt)], np.float64)
         self._h = lib.oracle_create(m.n_nodes, m.xy.ravel(), m.n_cells, m.cell_ptr, m.cell_nodes,
                                     m.n_bedges, m.bedge_nodes.ravel(), m.bedge_type,
                                     m.bedge_val.ravel(), m.periodic_pairs.shape[0],
@@ -119,6 +120,12 @@ class Oracle:
     @property
     def dt(self) -> float:
         return self.lib.oracle_dt(self._h)
+
+    def dt_cells(self) -> np.ndarray:
+        """dt of every cell (the global dt unless the case asks for local time stepping)."""
+        out = np.zeros(self.n_cells)
+        self.lib.oracle_dt_cells(self._h, out)
+        return out
 
     def step(self, n: int = 1) -> None:
         if self.lib.oracle_step(self._h, int(n)) != 0:

@@ -110,6 +110,7 @@ class Case:
     k: np.ndarray | None = None
     omega: np.ndarray | None = None
     name: str = ""
+    local_dt: bool = False   # local time stepping dt_i = cfl * limit_i (steady runs only)
 
     @property
     def tau(self) -> float:
@@ -233,10 +234,17 @@ def periodic_box(n: int, kind: str = "quad", jitter: float = 0.0, seed: int = 0,
 
 
 def couette_channel(nx: int, ny: int, U: float = 0.1, H: float = 1.0, Lx: float = 1.0,
-                    kind: str = "quad", jitter: float = 0.0, seed: int = 0) -> Mesh:
-    """Channel periodic in x; bottom wall at rest, top wall moving at (U, 0)."""
+                    kind: str = "quad", jitter: float = 0.0, seed: int = 0,
+                    stretch: float = 1.0) -> Mesh:
+    """Channel periodic in x; bottom wall at rest, top wall moving at (U, 0).  ``stretch`` > 1
+    grows the row heights geometrically from the bottom wall by that ratio per row."""
     xs = np.linspace(0.0, Lx, nx + 1)
-    ys = np.linspace(0.0, H, ny + 1)
+    if stretch == 1.0:
+        ys = np.linspace(0.0, H, ny + 1)
+    else:
+        hs = stretch ** np.arange(ny)
+        ys = np.concatenate([[0.0], np.cumsum(hs)]) * (H / hs.sum())
+        ys[-1] = H
     xy, cells, sides = quad_grid(xs, ys, jitter, seed)
     cells_out = split_quads(cells) if kind == "tri" else cells
     bn = np.concatenate([sides["bottom"], sides["top"], sides["left"], sides["right"]])

@@ -5,6 +5,7 @@ invariant of the lattice or of the scheme, a textbook flow, or a value printed i
 (golden fixtures under tests/golden/).  A plausible slip anywhere in the oracle -- a dropped
 term, a wrong sign, a swapped tableau entry, a transposed gradient -- fails one of them.
 """
+import dataclasses
 import json
 import math
 import os
@@ -325,3 +326,104 @@ def test_euler_couette_matches_imex_steady_state():
     o.step(int(3 * H * H / nu / o.dt))
     g, fl = o.geometry(), o.fields()
     assert np.abs(fl["u"] - U * g["cy"] / H).max() < 1e-9
+
+
+# ----------------------------------------------------------------- local time stepping
+def test_local_dt_closed_form_on_rectangles():
+    """Local time stepping (steady-state acceleration, not in the paper): dt_i = CFL * limit_i
+    with limit_i = 1 / max_alpha sum_m max(e_alpha . n_m, 0) dl_m / A_i.  On an hx x hy
+    rectangle the maximum is the diagonal velocity, 1/hx + 1/hy, so dt_i = CFL hx hy/(hx + hy);
+    the global dt is the smallest dt_i."""
+    m = mg.couette_channel(5, 9, stretch=1.4)
+    cfl = 0.7
+    o = Oracle(mg.Case(m, nu=0.01, cfl=cfl, local_dt=True))
+    P = m.xy[m.cell_nodes.reshape(-1, 4)]
+    hx = P[:, :, 0].max(1) - P[:, :, 0].min(1)
+    hy = P[:, :, 1].max(1) - P[:, :, 1].min(1)
+    want = cfl * hx * hy / (hx + hy)
+    np.testing.assert_allclose(o.dt_cells(), want, rtol=1e-13, atol=0)
+    assert o.dt == o.dt_cells().min()
+    assert want.max() / want.min() > 5        # the stretching really spreads the steps
+    g = Oracle(mg.Case(m, nu=0.01, cfl=cfl))
+    assert g.dt == o.dt and np.all(g.dt_cells() == g.dt)
+
+
+def _separate_boxes(sides):
+    """Disconnected closed square cells of the given side lengths, all edges walls at rest."""
+    xy, cells, bn = [], [], []
+    x0 = 0.0
+    for k, h in enumerate(sides):
+        xy += [(x0, 0.0), (x0 + h, 0.0), (x0 + h, h), (x0, h)]
+        c = [4 * k, 4 * k + 1, 4 * k + 2, 4 * k + 3]
+        cells.append(c)
+        bn += [(c[0], c[1]), (c[1], c[2]), (c[2], c[3]), (c[3], c[0])]
+        x0 += h + 0.5
+    nb = len(bn)
+    bv = np.zeros((nb, 5))
+    bv[:, 0] = 1.0
+    return mg.Mesh(np.array(xy), np.arange(len(sides) + 1, dtype=np.int32) * 4,
+                   np.array(cells, np.int32).ravel(), np.array(bn, np.int32),
+                   np.zeros(nb, np.int32), bv).normalized()
+
+
+def test_local_dt_relaxation_factor_per_cell():
+    """Isolated closed cells of different sizes holding a uniform non-equilibrium field
+    (Gamma^a = 0 in each): with local time steps every cell multiplies its non-equilibrium
+    part by R(z_i), z_i = dt_i / tau, the stability function of the printed tableau at its
+    own step, and dt_i = CFL h_i / 2 for a square of side h_i."""
+    sides = [0.05, 0.1, 0.3, 1.0]
+    m = _separate_boxes(sides)
+    nu, cfl = 2e-4, 2.0
+    o = Oracle(mg.Case(m, nu=nu, cfl=cfl, local_dt=True))
+    dti = o.dt_cells()
+    np.testing.assert_allclose(dti, cfl * np.array(sides) / 2, rtol=1e-14)
+    eq = feq(1.0, 0.0, 0.0)
+    delta = 1e-3 * eq * (EX ** 2 - EY ** 2)
+    o.set_f(np.tile(eq + delta, (o.n_cells, 1)))
+    o.step(1)
+    f1 = o.get_f()
+    for i in range(o.n_cells):
+        z = dti[i] / (nu / CS2)
+        R = _relaxation_factor_from_tableau(z)
+        np.testing.assert_allclose(f1[i] - eq, R * delta, rtol=0, atol=1e-16 * (10 + z))
+
+
+def test_local_dt_on_uniform_mesh_matches_global():
+    """On a uniform quad mesh every cell has the same limit, so local stepping is the global
+    step (up to the last bit of each cell's own limit)."""
+    case = mg.cavity_quad(12, re=400.0)
+    a = Oracle(case)
+    b = Oracle(dataclasses.replace(case, local_dt=True))
+    assert np.abs(b.dt_cells() / a.dt - 1).max() < 1e-14
+    a.step(10)
+    b.step(10)
+    assert np.abs(a.get_f() - b.get_f()).max() < 1e-13
+
+
+def test_local_dt_needs_cfl():
+    m = _box_at_rest(4)
+    with pytest.raises(ValueError):
+        Oracle(mg.Case(m, nu=1e-3, dt=1e-3, local_dt=True))
+
+
+def test_local_dt_accelerates_steady_couette():
+    """Stretched Couette channel (row heights x1.25 per row, 16 rows): the global step is set
+    by the thinnest row; local steps let every row move at its own limit.  Both reach a steady
+    state; local stepping needs several times fewer steps, and its steady profile differs from
+    the global one only at the level of the scheme's own dependence on the step (the IMEX
+    fixed point moves with dt; 2.1e-5 U here)."""
+    U, H, nu = 0.1, 1.0, 0.02
+    m = mg.couette_channel(4, 16, U=U, H=H, stretch=1.25)
+    out = {}
+    for local in (False, True):
+        o = Oracle(mg.Case(m, nu=nu, cfl=0.5, uref=U, local_dt=local))
+        n = 0
+        while o.residual() > 1e-12 or n == 0:
+            o.step(500)
+            n += 500
+            assert n <= 40000
+        out[local] = (n, o.fields()["u"], o.geometry()["cy"])
+    (ng, ug, cy), (nl, ul, _) = out[False], out[True]
+    assert np.abs(ug - U * cy / H).max() < 1e-8 * U       # global: the exact linear profile
+    assert nl * 5 < ng
+    assert np.abs(ul - ug).max() < 5e-5 * U
