@@ -101,6 +101,14 @@ typedef struct {
                                   original scheme that Sec. 3.1 and Sec. 4.1 compare against
                                   (stable only for dt < 2 tau).  All instances of a batch share
                                   it. */
+    int local_dt;              /* 1: local time stepping (not in the paper; for steady runs):
+                                  every cell advances with its own dt_i = cfl * its convective
+                                  limit 1 / max_alpha sum_m max(e_alpha . n_m, 0) dl_m / A_i,
+                                  in the stages, the implicit collision and the SST update.
+                                  Not time accurate; the steady state moves with the steps at
+                                  the level of the scheme's own dt dependence.  Needs cfl > 0
+                                  (dt is ignored); fvlbm_info reports the smallest dt_i.
+                                  0: one dt per instance (default). */
 } fvlbm_params;
 
 typedef struct {

@@ -76,6 +76,10 @@ int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_para
         *why = "need nu > 0, rho0 > 0 and dt > 0 or cfl > 0";
         return FVLBM_ERR_BAD_PARAM;
     }
+    if (p.local_dt && !(p.cfl > 0.0)) {
+        *why = "local time stepping needs cfl > 0";
+        return FVLBM_ERR_BAD_PARAM;
+    }
     if (!xy) {
         *why = "empty mesh";
         return FVLBM_ERR_BAD_MESH;
@@ -367,11 +371,13 @@ int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_para
         }
     }
     // time step: dt, or cfl over the largest upwind outflow rate max_i max_alpha
-    // sum_m max(e_alpha . n_m, 0) Delta l_m / A_i (forward-Euler limit of first-order upwind)
+    // sum_m max(e_alpha . n_m, 0) Delta l_m / A_i (forward-Euler limit of first-order upwind).
+    // Local time stepping keeps each cell's own cfl / rate_i (steady-state acceleration).
     P.dt = p.dt;
-    if (P.dt <= 0.0) {
+    if (P.dt <= 0.0 || p.local_dt) {
         static const int ex[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
         static const int ey[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+        std::vector<double> rate_in(nc, 0.0);  // per input cell
         double rate = 0.0;
         for (int i = 0; i < nc; ++i) {
             const int nv = m.cell_ptr[i + 1] - m.cell_ptr[i];
@@ -382,10 +388,15 @@ int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_para
                     const double en = ex[a] * value_of(F.nx) + ey[a] * value_of(F.ny);
                     if (en > 0.0) s += en * value_of(F.len);
                 }
-                rate = std::max(rate, s / value_of(area[i]));
+                rate_in[i] = std::max(rate_in[i], s / value_of(area[i]));
             }
+            rate = std::max(rate, rate_in[i]);
         }
         P.dt = p.cfl / rate;
+        if (p.local_dt) {
+            P.dt_cell.assign(np, P.dt);  // padding cells: any positive step
+            for (int k = 0; k < nc; ++k) P.dt_cell[k] = p.cfl / rate_in[P.perm[k]];
+        }
     }
     // initial fields in internal order (padding cells at rest with rho0)
     P.rho_i.assign(np, p.rho0);

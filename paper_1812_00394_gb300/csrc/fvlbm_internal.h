@@ -55,7 +55,8 @@ struct PreparedT {
     std::vector<S> bnrm;   // [2 nb] unit normal out of the fluid
     std::vector<S> blen;   // [nb]
     std::vector<int> bedge_of;  // [nb] input boundary-edge index of each boundary face
-    double dt = 0.0;
+    double dt = 0.0;            // the instance's step (local stepping: the smallest dt_i)
+    std::vector<double> dt_cell;  // [np] local time stepping: dt_i of each cell; empty otherwise
     std::vector<double> rho_i, u_i, v_i, k_i, w_i;  // initial fields, internal order [np]
 };
 

@@ -87,8 +87,15 @@ struct Geo {
     const InstParam *__restrict__ ip;
     const int *__restrict__ btype;  // [nbt]
     const T *__restrict__ bval;     // [5 nbt] field-major: bval[c * nbt + b]
+    const T *__restrict__ dtc;      // [np] local time step of each cell, or NULL (global dt)
     int np, nbt;
 };
+
+// Time step of cell i: its own under local time stepping, else the instance's.
+template <class T>
+__device__ __forceinline__ T cell_dt(const Geo<T> &G, const InstParam &P, int i) {
+    return G.dtc != nullptr ? G.dtc[i] : T(P.dt);
+}
 
 // ------------------------------------------------------------------ cell algebra
 // Moments of a deviation vector d = f - w rho0: drho = sum d, rho = rho0 + drho, u = sum e d / rho.
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(kTile) k_stage1(const T *__restrict__ fn, T *_
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
     T f[kQ];
     load9(fn, np, i, f);
-    relax9(f, T(P.rho0), T(P.dt), tau[i]);
+    relax9(f, T(P.rho0), cell_dt(G, P, i), tau[i]);
     store9(fs, np, i, f);
 }
 
@@ -260,7 +267,7 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *out) {
 //   frel (if given): at J = 3, laminar instances also store f^(1) of the next step.
 template <class T, int STAGE, bool STATS, int NT, bool FN_FROM_F1 = false>
 __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, const T *acc,
-                                              const InstParam &P, T t_i, const T *a1, size_t ld1,
+                                              const InstParam &P, T t_i, T dt_i, const T *a1, size_t ld1,
                                               int c1, const T *a2, size_t ld2, int c2,
                                               T *__restrict__ fs_out, T *__restrict__ fn,
                                               T *__restrict__ Bacc, T *__restrict__ Cacc,
@@ -268,7 +275,7 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
                                               const T *__restrict__ area,
                                               T *__restrict__ frel = nullptr) {
     const T rho0 = T(P.rho0);
-    const T dt = T(P.dt);
+    const T dt = dt_i;
     const T itau = T(1) / t_i;          // one division per cell, products below
     const T dt3 = dt * T(1.0 / 3.0), dt6 = dt * T(1.0 / 6.0);
     if (STAGE == 1) {
@@ -371,9 +378,9 @@ __device__ __forceinline__ void stage_update(int i, size_t np, const T *fi, cons
                                              T *__restrict__ fn, T *__restrict__ Bacc,
                                              T *__restrict__ Cacc, const T *__restrict__ tau,
                                              T *__restrict__ mac, double *__restrict__ partial,
-                                             const T *__restrict__ area) {
+                                             const T *__restrict__ area, T dt_i) {
     const T *a1 = STAGE == 1 ? fn : (STAGE == 2 ? Bacc : Cacc);
-    stage_algebra<T, STAGE, STATS, NT>(i, np, fi, acc, P, tau[i], a1, np, i, Cacc, np, i, fs_out,
+    stage_algebra<T, STAGE, STATS, NT>(i, np, fi, acc, P, tau[i], dt_i, a1, np, i, Cacc, np, i, fs_out,
                                        fn, Bacc, Cacc, mac, partial, area);
 }
 
@@ -422,7 +429,7 @@ __global__ void __launch_bounds__(kTile)
         }
     }
     stage_update<T, STAGE, STATS, kTile>(i, np, fi, acc, P, fs_out, fn, Bacc, Cacc, tau, mac, partial,
-                                         G.area);
+                                         G.area, cell_dt(G, P, i));
 }
 
 // ------------------------------------------------------------------ fused stage kernel
@@ -716,7 +723,7 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
             }
         }
     }
-    stage_algebra<T, STAGE, STATS, BLK, true>(i, np, fi, acc, P, tau_i, a1, 1, 0, a2, 1,
+    stage_algebra<T, STAGE, STATS, BLK, true>(i, np, fi, acc, P, tau_i, cell_dt(G, P, i), a1, 1, 0, a2, 1,
                                                         0, fs_out, fn, Bacc, Cacc, mac, partial,
                                                         G.area, frel);
 }
@@ -822,11 +829,11 @@ struct SstFace {
 // coefficient), explicit production and cross diffusion, point-implicit destruction; then f2,
 // nu_t = a1 k / max(a1 omega, S f2) and tau = (nu + nu_t)/cs^2.
 template <class T>
-__device__ __forceinline__ void sst_cell_update(const InstParam &P, T ui, T vi, T ki, T wi, T nti,
-                                                T di, const T *g, const T *lgi, T f1,
+__device__ __forceinline__ void sst_cell_update(const InstParam &P, T dt, T ui, T vi, T ki, T wi,
+                                                T nti, T di, const T *g, const T *lgi, T f1,
                                                 const SstFace<T> *F, T &kn, T &wn, T &ntn,
                                                 T &tnew) {
-    const T nu = T(P.nu), dt = T(P.dt);
+    const T nu = T(P.nu);
     const T sk_i = f1 * T(kSk1) + (T(1) - f1) * T(kSk2);
     const T sw_i = f1 * T(kSw1) + (T(1) - f1) * T(kSw2);
     T ck = 0, cw = 0, dk = 0, dw = 0;
@@ -1048,7 +1055,8 @@ __global__ void __launch_bounds__(kTile)
         }
     }
     T kn, wn, ntn, tnew;
-    sst_cell_update(P, ui, vi, ki, wi, nti, di, g, lgi, f1a[i], F, kn, wn, ntn, tnew);
+    const T dt_i = cell_dt(G, P, i);
+    sst_cell_update(P, dt_i, ui, vi, ki, wi, nti, di, g, lgi, f1a[i], F, kn, wn, ntn, tnew);
     k_out[i] = kn;
     w_out[i] = wn;
     nut_out[i] = ntn;
@@ -1056,7 +1064,7 @@ __global__ void __launch_bounds__(kTile)
     if (frel != nullptr) {  // fused path: stage 1's f^(1) with the new relaxation time
         T f[kQ];
         load9(fn, np, i, f);
-        relax9(f, T(P.rho0), T(P.dt), tnew);
+        relax9(f, T(P.rho0), dt_i, tnew);
         store9(frel, np, i, f);
     }
 }
@@ -1319,6 +1327,7 @@ struct fvlbm_handle {
     void *fn = nullptr, *s0 = nullptr, *s1 = nullptr, *bacc = nullptr, *cacc = nullptr;
     void *grad = nullptr, *tau = nullptr, *mac = nullptr;
     void *frel = nullptr;   // fused path: f^(1) of the coming step (relaxed f^n)
+    void *dtc = nullptr;    // local time stepping: dt of each cell (NULL: every instance global)
     void *kk[2] = {nullptr, nullptr}, *ww[2] = {nullptr, nullptr}, *nut[2] = {nullptr, nullptr};
     void *sgrad = nullptr, *f1 = nullptr;
     int turb = 0;  // which of the k/omega/nu_t ping-pong buffers is current
@@ -1379,6 +1388,7 @@ Geo<T> geo_of(const fvlbm_handle *h) {
     G.ip = h->d_ip;
     G.btype = h->d_btype;
     G.bval = static_cast<const T *>(h->bval);
+    G.dtc = static_cast<const T *>(h->dtc);
     G.np = h->np;
     G.nbt = h->nbt;
     return G;
@@ -1784,6 +1794,17 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
     if ((rc = upload_as<T>(h, &h->bval, bval))) return rc;
     if ((rc = upload_as<T>(h, &h->bnrm, bnrm))) return rc;
     if ((rc = upload_as<T>(h, &h->blen, blen))) return rc;
+    bool any_local = false;
+    for (const Prepared *p : P) any_local |= !p->dt_cell.empty();
+    if (any_local) {  // local time stepping: every cell's step (global instances: their dt)
+        std::vector<double> dtc(np, 1.0);
+        for (int q = 0; q < h->ninst; ++q) {
+            const Prepared &p = *P[q];
+            for (int k = 0; k < p.np; ++k)
+                dtc[h->inst[q].cell_off + k] = p.dt_cell.empty() ? p.dt : p.dt_cell[k];
+        }
+        if ((rc = upload_as<T>(h, &h->dtc, dtc))) return rc;
+    }
     if (h->fused) {
         if ((rc = upload_as<T>(h, &h->gq, gq))) return rc;
         if ((rc = upload_raw(h, &h->d_err, std::vector<int>(1, 0)))) return rc;

@@ -48,7 +48,8 @@ class fvlbm_params(C.Structure):
                 ("sst", C.c_int), ("precision", C.c_int), ("uref", C.c_double),
                 ("lref", C.c_double), ("alpha_deg", C.c_double), ("rho_init", C.c_void_p),
                 ("u_init", C.c_void_p), ("v_init", C.c_void_p), ("k_init", C.c_void_p),
-                ("omega_init", C.c_void_p), ("kernel_path", C.c_int), ("scheme", C.c_int)]
+                ("omega_init", C.c_void_p), ("kernel_path", C.c_int), ("scheme", C.c_int),
+                ("local_dt", C.c_int)]
 
 
 class fvlbm_stats(C.Structure):
@@ -286,7 +287,8 @@ class _Pack:
                            m.periodic_pairs.shape[0], _p(m.periodic_pairs), _p(m.periodic_shift))
         self.params = fvlbm_params(case.nu, case.rho0, case.dt, case.cfl, int(bool(case.sst)),
                                    precision, case.uref, case.lref, case.alpha_deg, _p(rho), _p(u),
-                                   _p(v), _p(k), _p(w), kernel_path, scheme)
+                                   _p(v), _p(k), _p(w), kernel_path, scheme,
+                                   int(bool(getattr(case, "local_dt", False))))
 
 
 class Solver:
