@@ -70,7 +70,8 @@ constexpr double kCs2 = 1.0 / 3.0;
 
 struct InstParam {
     double dt, nu, rho0, omega_min;
-    int sst;  // 1: k-omega SST instance; 0: laminar (SST kernels skip its tiles)
+    int sst;    // 1: k-omega SST instance; 0: laminar (SST kernels skip its tiles)
+    int local;  // 1: local time stepping (cell steps in Geo::dtc)
 };
 
 template <class T>
@@ -262,9 +263,14 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *out) {
 //   J = 4: explicit Euler comparison scheme, f^{n+1} = f^n + dt (Gamma^a + Gamma^c), into fs_out
 // The accumulator inputs are read through (pointer, row stride, column): a1 is f^n (J = 1),
 // B (J = 2) or C (J = 3); a2 is C (J = 2).  Outputs go to global memory at cell i.
-//   FN_FROM_F1: f^n is not read but recovered from f^(1) = [f^n + z/4 f^eq] / (1 + z/4) as
-//   f^n = f^(1) - dt/4 Gamma^c(1) (same moments, so f^eq(1) follows from f^(1));
+//   FN_FROM_F1: unless fn_in_a1, f^n is not read but recovered from f^(1) = [f^n + z/4 f^eq] /
+//   (1 + z/4) as f^n = f^(1) - dt/4 Gamma^c(1) (same moments, so f^eq(1) follows from f^(1));
+//   the recovery multiplies the rounding of f^(1) by z/4, so callers with large z (local time
+//   steps) pass f^n in a1 instead;
 //   frel (if given): at J = 3, laminar instances also store f^(1) of the next step.
+// The collision terms are formed from differences that are not scaled by z: with
+// f^(J) = (X + zJ f^eq) / (1 + zJ), dt Gamma^c(J) = dt/tau (f^eq - X) / (1 + zJ) exactly, so a
+// rounding of X or f^eq is multiplied by dt/tau / (1 + zJ) <= 1/m_JJ instead of dt/tau.
 template <class T, int STAGE, bool STATS, int NT, bool FN_FROM_F1 = false>
 __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, const T *acc,
                                               const InstParam &P, T t_i, T dt_i, const T *a1, size_t ld1,
@@ -273,43 +279,47 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
                                               T *__restrict__ Bacc, T *__restrict__ Cacc,
                                               T *__restrict__ mac, double *__restrict__ partial,
                                               const T *__restrict__ area,
-                                              T *__restrict__ frel = nullptr) {
+                                              T *__restrict__ frel = nullptr,
+                                              bool fn_in_a1 = false) {
     const T rho0 = T(P.rho0);
     const T dt = dt_i;
     const T itau = T(1) / t_i;          // one division per cell, products below
     const T dt3 = dt * T(1.0 / 3.0), dt6 = dt * T(1.0 / 6.0);
     if (STAGE == 1) {
-        // fi = f^(1); f^n, Gamma^c(1) from f^n and f^(1)
+        // fi = f^(1); f^n and dt Gamma^c(1)
         T f0[kQ], eq[kQ], X[kQ], dr, r, u, v;
-        T gc1[kQ];
-        if (FN_FROM_F1) {
+        T dgc1[kQ];
+        const T z = dt * itau;
+        const T zq = z * T(0.25);
+        const T inv = T(1) / (T(1) + zq);
+        if (FN_FROM_F1 && !fn_in_a1) {
             moments(fi, rho0, dr, r, u, v);
             feq_dev(dr, r, u, v, eq);
 #pragma unroll
             for (int a = 0; a < kQ; ++a) {
-                gc1[a] = (eq[a] - fi[a]) * itau;
-                f0[a] = fi[a] - T(0.25) * dt * gc1[a];
+                dgc1[a] = (eq[a] - fi[a]) * z;
+                f0[a] = fi[a] - T(0.25) * dgc1[a];
             }
         } else {
 #pragma unroll
             for (int a = 0; a < kQ; ++a) f0[a] = a1[a * ld1 + c1];
             moments(f0, rho0, dr, r, u, v);
             feq_dev(dr, r, u, v, eq);
+            const T s1 = z * inv;  // f^(1) = (f^n + zq f^eq) / (1 + zq)
 #pragma unroll
-            for (int a = 0; a < kQ; ++a) gc1[a] = (eq[a] - fi[a]) * itau;
+            for (int a = 0; a < kQ; ++a) dgc1[a] = (eq[a] - f0[a]) * s1;
         }
 #pragma unroll
         for (int a = 0; a < kQ; ++a) X[a] = f0[a] - T(0.5) * dt * acc[a];
         moments(X, rho0, dr, r, u, v);
         feq_dev(dr, r, u, v, eq);
-        const T zq = dt * itau * T(0.25);
-        const T inv = T(1) / (T(1) + zq);
+        const T s2 = z * inv;
         T f2[kQ];
 #pragma unroll
         for (int a = 0; a < kQ; ++a) {
             f2[a] = (X[a] + zq * eq[a]) * inv;
-            const T gc2 = (eq[a] - f2[a]) * itau;
-            Bacc[a * np + i] = X[a] + dt3 * (gc1[a] + gc2);
+            const T dgc2 = (eq[a] - X[a]) * s2;  // dt Gamma^c(2)
+            Bacc[a * np + i] = X[a] + T(1.0 / 3.0) * (dgc1[a] + dgc2);
             Cacc[a * np + i] = dt6 * acc[a];
         }
         store9(fs_out, np, i, f2);
@@ -591,9 +601,10 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
     // this thread's accumulators, tau and node positions, straight into registers
     T a1[kQ], a2[kQ], q[8];
     const T tau_i = tau[i];
+    const bool fn_in_a1 = STAGE == 1 && P.local;  // local steps: large z, read f^n
     {
-        if (STAGE != 1) {
-            const T *p1 = STAGE == 2 ? Bacc : Cacc;
+        if (STAGE != 1 || fn_in_a1) {
+            const T *p1 = STAGE == 1 ? fn : (STAGE == 2 ? Bacc : Cacc);
 #pragma unroll
             for (int a = 0; a < kQ; ++a) a1[a] = p1[a * np + i];
         }
@@ -725,7 +736,7 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
     }
     stage_algebra<T, STAGE, STATS, BLK, true>(i, np, fi, acc, P, tau_i, cell_dt(G, P, i), a1, 1, 0, a2, 1,
                                                         0, fs_out, fn, Bacc, Cacc, mac, partial,
-                                                        G.area, frel);
+                                                        G.area, frel, fn_in_a1);
 }
 
 // Sum per-block partials into per-instance totals (one block per instance).
@@ -1938,7 +1949,8 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
         inst_tile0.push_back(I.tile_off);
         for (int t = 0; t < p.np / kTile; ++t) tile_inst.push_back(q);
         ip[q] = InstParam{p.dt, params[q].nu, params[q].rho0,
-                          1e-12 * params[q].uref / params[q].lref, params[q].sst ? 1 : 0};
+                          1e-12 * params[q].uref / params[q].lref, params[q].sst ? 1 : 0,
+                          p.dt_cell.empty() ? 0 : 1};
         cell_off += p.np;
         bface_off += p.nb;
         h->inst.push_back(I);

@@ -365,7 +365,7 @@ def test_local_dt_parity_fp64(name, path):
     case = LOCAL_CASES[name]()
     s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=path)
     o = Oracle(case)
-    assert abs(s.dt() - o.dt) <= 1e-15 * o.dt
+    assert abs(s.dt() - o.dt) <= 1e-12 * o.dt   # independent geometry codes, 1e-5-chord cells
     zmax = o.dt_cells().max() / (case.nu / 3.0)
     tol = 1e-10 + 2e-16 * zmax
     for n in (1, 10):
