@@ -263,10 +263,10 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *out) {
 //   J = 4: explicit Euler comparison scheme, f^{n+1} = f^n + dt (Gamma^a + Gamma^c), into fs_out
 // The accumulator inputs are read through (pointer, row stride, column): a1 is f^n (J = 1),
 // B (J = 2) or C (J = 3); a2 is C (J = 2).  Outputs go to global memory at cell i.
-//   FN_FROM_F1: unless fn_in_a1, f^n is not read but recovered from f^(1) = [f^n + z/4 f^eq] /
+//   FN_FROM_F1: unless fn_read, f^n is not read but recovered from f^(1) = [f^n + z/4 f^eq] /
 //   (1 + z/4) as f^n = f^(1) - dt/4 Gamma^c(1) (same moments, so f^eq(1) follows from f^(1));
-//   the recovery multiplies the rounding of f^(1) by z/4, so callers with large z (local time
-//   steps) pass f^n in a1 instead;
+//   the recovery multiplies the rounding of f^(1) by z/4, so with large z (local time steps)
+//   the caller sets fn_read and f^n is read from fn at cell i instead;
 //   frel (if given): at J = 3, laminar instances also store f^(1) of the next step.
 // The collision terms are formed from differences that are not scaled by z: with
 // f^(J) = (X + zJ f^eq) / (1 + zJ), dt Gamma^c(J) = dt/tau (f^eq - X) / (1 + zJ) exactly, so a
@@ -280,7 +280,7 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
                                               T *__restrict__ mac, double *__restrict__ partial,
                                               const T *__restrict__ area,
                                               T *__restrict__ frel = nullptr,
-                                              bool fn_in_a1 = false) {
+                                              bool fn_read = false) {
     const T rho0 = T(P.rho0);
     const T dt = dt_i;
     const T itau = T(1) / t_i;          // one division per cell, products below
@@ -292,7 +292,7 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
         const T z = dt * itau;
         const T zq = z * T(0.25);
         const T inv = T(1) / (T(1) + zq);
-        if (FN_FROM_F1 && !fn_in_a1) {
+        if (FN_FROM_F1 && !fn_read) {
             moments(fi, rho0, dr, r, u, v);
             feq_dev(dr, r, u, v, eq);
 #pragma unroll
@@ -302,7 +302,7 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
             }
         } else {
 #pragma unroll
-            for (int a = 0; a < kQ; ++a) f0[a] = a1[a * ld1 + c1];
+            for (int a = 0; a < kQ; ++a) f0[a] = FN_FROM_F1 ? fn[a * np + i] : a1[a * ld1 + c1];
             moments(f0, rho0, dr, r, u, v);
             feq_dev(dr, r, u, v, eq);
             const T s1 = z * inv;  // f^(1) = (f^n + zq f^eq) / (1 + zq)
@@ -601,10 +601,9 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
     // this thread's accumulators, tau and node positions, straight into registers
     T a1[kQ], a2[kQ], q[8];
     const T tau_i = tau[i];
-    const bool fn_in_a1 = STAGE == 1 && P.local;  // local steps: large z, read f^n
     {
-        if (STAGE != 1 || fn_in_a1) {
-            const T *p1 = STAGE == 1 ? fn : (STAGE == 2 ? Bacc : Cacc);
+        if (STAGE != 1) {
+            const T *p1 = STAGE == 2 ? Bacc : Cacc;
 #pragma unroll
             for (int a = 0; a < kQ; ++a) a1[a] = p1[a * np + i];
         }
@@ -736,7 +735,7 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
     }
     stage_algebra<T, STAGE, STATS, BLK, true>(i, np, fi, acc, P, tau_i, cell_dt(G, P, i), a1, 1, 0, a2, 1,
                                                         0, fs_out, fn, Bacc, Cacc, mac, partial,
-                                                        G.area, frel, fn_in_a1);
+                                                        G.area, frel, P.local != 0);  // local steps: read f^n
 }
 
 // Sum per-block partials into per-instance totals (one block per instance).
@@ -2493,6 +2492,11 @@ int fvlbm_autotune(fvlbm_handle *h, int trial_steps, int *chosen, double *ms_per
     cudaFree(snap);
     h->config = best_c;
     h->steps = steps0;
+    // The two-pass kernels do not keep f^(1) of the coming step: if they ran before this call,
+    // the restored snapshot holds a stale one.  Relax it again from f^n for the fused stages
+    // (bitwise what stage 3 writes for laminar instances; SST instances redo it every step).
+    if (best_c != 2 && err == cudaSuccess)
+        dispatch(h->precision, [&](auto z_) { relax_all<decltype(z_)>(h); });
     for (int k = 0; k < 3; ++k)  // captured graphs bake the old configuration
         if (h->graph[k]) {
             cudaGraphExecDestroy(h->graph[k]);

@@ -60,7 +60,8 @@ class fvlbm_stats(C.Structure):
 EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "fvlbm_get_f",
            "fvlbm_set_f", "fvlbm_get_fields", "fvlbm_info", "fvlbm_footprint",
            "fvlbm_profile_kernels", "fvlbm_autotune", "fvlbm_destroy", "fvlbm_strerror",
-           "fvlbm_stats_reduce_static"]
+           "fvlbm_stats_reduce_static", "fvlbm_tangent_seed", "fvlbm_tangent_seed_nodes",
+           "fvlbm_get_f_tangent", "fvlbm_forces_tangent"]
 
 _lib = None
 

@@ -328,6 +328,23 @@ def test_autotune_restores_state_and_keeps_parity(prec):
         assert _rel_max(s.get_f(i), o.get_f()) < tol, (chosen, c.name)
 
 
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_repeated_autotune_between_steps_keeps_parity(prec):
+    """Autotune, step, autotune again, step: whichever configurations are chosen in turn
+    (the two-pass kernels keep no f^(1) for the fused ones), the state follows the oracle."""
+    cases = [mg.cavity_quad(30, re=400.0), mg.naca0012_cmesh(n_target=3000, alpha_deg=2.0)]
+    s = fvlbm.Solver(cases, precision=prec, device=0)
+    picks = []
+    for _ in range(3):
+        picks.append(s.autotune(2)[0])
+        s.step(3)
+    tol = 1e-10 if prec == FP64 else 1e-5
+    for i, c in enumerate(cases):
+        o = Oracle(c)
+        o.step(9)
+        assert _rel_max(s.get_f(i), o.get_f()) < tol, (picks, c.name)
+
+
 def test_all_instances_io_matches_per_instance():
     """instance = -1 reads and writes every instance at once, concatenated in order."""
     cases = [mg.cavity_quad(9, re=100.0), mg.bfs_hybrid(n_target=1500), mg.cavity_quad(5)]
