@@ -77,6 +77,8 @@ typedef struct oracle {
     double *bxm, *bym, *bnx, *bny, *blen;
     double nu, rho0, dt, uref, lref, alpha_deg;
     double *dtc;                 /* local time stepping: dt of each cell (NULL: dt everywhere) */
+    int variant;                 /* reading variants (bit mask): 1 limiter on the gradient of f,
+                                    2 non-orthogonal correction of the SST diffusion */
     int sst;
     int scheme;                  /* 0: IMEX Runge-Kutta (Part II); 1: explicit Euler (Part I) */
     double *f;                   /* [nc * Q], cell-major */
@@ -146,7 +148,7 @@ static void *xcalloc(size_t n, size_t s) { return calloc(n ? n : 1, s); }
 
 void oracle_destroy(oracle *o);
 
-/* params: [nu, rho0, dt, cfl, sst, uref, lref, alpha_deg, scheme, local_dt] */
+/* params: [nu, rho0, dt, cfl, sst, uref, lref, alpha_deg, scheme, local_dt, variant] */
 oracle *oracle_create(int n_nodes, const double *xy, int n_cells, const int *cell_ptr,
                       const int *cell_nodes, int n_bedges, const int *bedge_nodes,
                       const int *bedge_type, const double *bedge_val, int n_periodic,
@@ -169,6 +171,7 @@ oracle *oracle_create(int n_nodes, const double *xy, int n_cells, const int *cel
     o->alpha_deg = params[7];
     o->scheme = (int)params[8];
     int local_dt = params[9] != 0.0;
+    o->variant = (int)params[10];
     if (local_dt && !(cfl > 0.0)) { /* local steps are CFL * the cell's limit: need a CFL */
         free(o);
         return NULL;
@@ -447,6 +450,37 @@ static void boundary_f(const oracle *o, const double *f, double *fbc)
     }
 }
 
+/* Venkatakrishnan limiter of the reconstruction of f (variant 1; a reading of Part I's
+ * reconstruction with a limiter, which Sec. 3.2 does not state): with D1 the distance from f_i
+ * to the max (min) over the cell, its face neighbours and its boundary face values and D2 the
+ * reconstructed increment g . (x_f - x_i) to face m, phi_m = [(D1^2 + e2) D2 + 2 D2^2 D1] /
+ * [D1^2 + 2 D2^2 + D1 D2 + e2] / D2 (1 where D2 = 0), and phi = min_m phi_m.  e2 = (K h)^3
+ * with h = sqrt(A_i) and K = 1 keeps smooth regions unlimited. */
+static double vk_limiter(const oracle *o, int i, const double *phi, int stride,
+                         const double *phib, int bstride, double gx, double gy)
+{
+    double pi = phi[(size_t)i * stride], lo = pi, hi = pi;
+    for (int l = 0; l < o->nface[i]; l++) {
+        const oface *F = &o->face[4 * i + l];
+        double q = F->nbr >= 0 ? phi[(size_t)F->nbr * stride] : phib[(size_t)F->bedge * bstride];
+        if (q < lo) lo = q;
+        if (q > hi) hi = q;
+    }
+    double h = sqrt(o->area[i]);
+    double e2 = h * h * h;
+    double psi = 1.0;
+    for (int l = 0; l < o->nface[i]; l++) {
+        const oface *F = &o->face[4 * i + l];
+        double d2 = gx * (F->xm - o->cx[i]) + gy * (F->ym - o->cy[i]);
+        if (d2 == 0.0) continue;
+        double d1 = d2 > 0.0 ? hi - pi : lo - pi;
+        double r = ((d1 * d1 + e2) * d2 + 2.0 * d2 * d2 * d1) /
+                   (d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + e2) / d2;
+        if (r < psi) psi = r;
+    }
+    return psi;
+}
+
 /* ------------------------------------------------------------------ convection */
 /* Gamma^a_alpha = -(1/A) sum_m [(e_alpha . n) f_{alpha,bc} Delta l]_m, Eq. (advection).
  * Interior face values: upwind by the sign of e_alpha . n (n out of this cell), linear
@@ -460,6 +494,11 @@ static void convection(oracle *o, const double *f, double *ga)
         for (int a = 0; a < Q; a++) {
             double gx, gy;
             lsq_gradient(o, i, f + a, Q, o->fbc + a, Q, &gx, &gy);
+            if (o->variant & 1) {
+                double phi = vk_limiter(o, i, f + a, Q, o->fbc + a, Q, gx, gy);
+                gx *= phi;
+                gy *= phi;
+            }
             o->gradf[((size_t)i * Q + a) * 2] = gx;
             o->gradf[((size_t)i * Q + a) * 2 + 1] = gy;
         }
@@ -645,8 +684,16 @@ static void sst_update(oracle *o)
                 double gwf = 0.5 * ((o->nu + sw[i] * o->nut[i]) + (o->nu + sw[j] * o->nut[j]));
                 ck += un * kup * F->len;
                 cw += un * wup * F->len;
-                dk += gkf * (o->k[j] - o->k[i]) / dist * F->len;
-                dw += gwf * (o->om[j] - o->om[i]) / dist * F->len;
+                double ck_n = (o->k[j] - o->k[i]) / dist, cw_n = (o->om[j] - o->om[i]) / dist;
+                if (o->variant & 2) {
+                    /* non-orthogonal correction (variant 2): grad phi . n = (phi_j - phi_i)/|d|
+                     * + mean grad phi . (n - d/|d|) */
+                    double tx = F->nx - (xj - o->cx[i]) / dist, ty = F->ny - (yj - o->cy[i]) / dist;
+                    ck_n += 0.5 * ((o->gk[2 * i] + o->gk[2 * j]) * tx + (o->gk[2 * i + 1] + o->gk[2 * j + 1]) * ty);
+                    cw_n += 0.5 * ((o->gw[2 * i] + o->gw[2 * j]) * tx + (o->gw[2 * i + 1] + o->gw[2 * j + 1]) * ty);
+                }
+                dk += gkf * ck_n * F->len;
+                dw += gwf * cw_n * F->len;
             } else {
                 const double *ub = &ubc[4 * F->bedge];
                 double un = ub[0] * F->nx + ub[1] * F->ny;
@@ -655,8 +702,14 @@ static void sst_update(oracle *o)
                 double dist = sqrt(rx * rx + ry * ry);
                 ck += un * kup * F->len;
                 cw += un * wup * F->len;
-                dk += (o->nu + sk[i] * o->nut[i]) * (ub[2] - o->k[i]) / dist * F->len;
-                dw += (o->nu + sw[i] * o->nut[i]) * (ub[3] - o->om[i]) / dist * F->len;
+                double ck_n = (ub[2] - o->k[i]) / dist, cw_n = (ub[3] - o->om[i]) / dist;
+                if (o->variant & 2) {
+                    double tx = F->nx - rx / dist, ty = F->ny - ry / dist;
+                    ck_n += o->gk[2 * i] * tx + o->gk[2 * i + 1] * ty;
+                    cw_n += o->gw[2 * i] * tx + o->gw[2 * i + 1] * ty;
+                }
+                dk += (o->nu + sk[i] * o->nut[i]) * ck_n * F->len;
+                dw += (o->nu + sw[i] * o->nut[i]) * cw_n * F->len;
             }
         }
         double f1 = o->f1[i];
@@ -860,6 +913,17 @@ double oracle_mass(const oracle *o)
 }
 
 /* Gradient of a per-cell field phi with boundary values phib (one per boundary edge). */
+/* The limiter value of the f reconstruction (variant 1) for a scalar field phi with boundary
+ * values phib [n_bedges], at its least-squares gradient, per cell (test access). */
+void oracle_limiter(oracle *o, const double *phi, const double *phib, double *psi)
+{
+    for (int i = 0; i < o->nc; i++) {
+        double gx, gy;
+        lsq_gradient(o, i, phi, 1, phib, 1, &gx, &gy);
+        psi[i] = vk_limiter(o, i, phi, 1, phib, 1, gx, gy);
+    }
+}
+
 void oracle_gradient(oracle *o, const double *phi, const double *phib, double *g)
 {
     for (int i = 0; i < o->nc; i++) lsq_gradient(o, i, phi, 1, phib, 1, &g[2 * i], &g[2 * i + 1]);

@@ -56,6 +56,7 @@ def _load():
             getattr(lib, name).argtypes = [vp]
             getattr(lib, name).restype = C.c_double
         lib.oracle_dt_cells.argtypes = [vp, _D]
+        lib.oracle_limiter.argtypes = [vp, _D, _D, _D]
         lib.oracle_n_cells.argtypes = [vp]
         lib.oracle_n_cells.restype = C.c_int
         lib.oracle_get_f.argtypes = [vp, _D]
@@ -99,7 +100,8 @@ class Oracle:
         self._keep = (m, rho, u, v, k, w)
         params = np.array([case.nu, case.rho0, case.dt if dt is None else dt, case.cfl,
                            float(case.sst if sst is None else sst), case.uref, case.lref,
-                           case.alpha_deg, float(scheme), float(case.local_dt)], np.float64)
+                           case.alpha_deg, float(scheme), float(case.local_dt),
+                           float(case.variant)], np.float64)
         self._h = lib.oracle_create(m.n_nodes, m.xy.ravel(), m.n_cells, m.cell_ptr, m.cell_nodes,
                                     m.n_bedges, m.bedge_nodes.ravel(), m.bedge_type,
                                     m.bedge_val.ravel(), m.periodic_pairs.shape[0],
@@ -166,6 +168,13 @@ class Oracle:
         self.lib.oracle_gradient(self._h, np.ascontiguousarray(phi, np.float64),
                                  np.ascontiguousarray(phib, np.float64), g)
         return g.reshape(self.n_cells, 2)
+
+    def limiter(self, phi: np.ndarray, phib: np.ndarray) -> np.ndarray:
+        """Limiter value per cell of the reconstruction of a scalar field (variant 1)."""
+        psi = np.zeros(self.n_cells)
+        self.lib.oracle_limiter(self._h, np.ascontiguousarray(phi, np.float64),
+                                np.ascontiguousarray(phib, np.float64), psi)
+        return psi
 
     def convection(self, f: np.ndarray) -> np.ndarray:
         ga = np.zeros(self.n_cells * Q)

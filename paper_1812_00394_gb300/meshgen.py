@@ -111,6 +111,8 @@ class Case:
     omega: np.ndarray | None = None
     name: str = ""
     local_dt: bool = False   # local time stepping dt_i = cfl * limit_i (steady runs only)
+    variant: int = 0         # reading variants (bit mask): 1 limiter on grad f, 2 SST
+                             # non-orthogonal diffusion correction
 
     @property
     def tau(self) -> float:

@@ -427,3 +427,67 @@ def test_local_dt_accelerates_steady_couette():
     assert np.abs(ug - U * cy / H).max() < 1e-8 * U       # global: the exact linear profile
     assert nl * 5 < ng
     assert np.abs(ul - ug).max() < 5e-5 * U
+
+
+# ----------------------------------------------------------------- reading variants
+def test_limiter_variant_closed_forms():
+    """Variant 1 (Venkatakrishnan limiter on the reconstruction of f, a reading that Sec. 3.2
+    leaves open).  For a linear field on uniform quads an interior face sees an increment D2
+    half of the neighbour difference D1 (ratio 2), where the limiter function is exactly 1 for
+    any smoothing e2; a cell on the x boundary sees its face value as the extremum (ratio 1),
+    where it is (3 D2^2 + e2) / (4 D2^2 + e2) with D2 = b h / 2 and e2 = h^3."""
+    n, b = 10, 0.7
+    m = _box_at_rest(n, "quad", 0.0, 0)
+    o = Oracle(mg.Case(m, nu=1e-3, dt=1e-3))
+    g = o.geometry()
+    phi = 0.3 + b * g["cx"]
+    mid = 0.5 * (m.xy[m.bedge_nodes[:, 0]] + m.xy[m.bedge_nodes[:, 1]])
+    phib = 0.3 + b * mid[:, 0]
+    psi = o.limiter(phi, phib)
+    h = 1.0 / n
+    xb = (g["cx"] < h) | (g["cx"] > 1 - h)
+    np.testing.assert_allclose(psi[~xb], 1.0, rtol=0, atol=1e-14)
+    d2, e2 = b * h / 2, h ** 3
+    np.testing.assert_allclose(psi[xb], (3 * d2 ** 2 + e2) / (4 * d2 ** 2 + e2), rtol=1e-12)
+
+
+def test_limiter_variant_changes_only_when_on():
+    """Variant 1 off is the default path bit for bit; on, a smooth cavity flow changes little
+    (the limiter acts near extrema only)."""
+    case = mg.cavity_quad(16, re=400.0)
+    a, b = Oracle(case), Oracle(dataclasses.replace(case, variant=1))
+    c = Oracle(dataclasses.replace(case, variant=0))
+    for x in (a, b, c):
+        x.step(30)
+    assert np.array_equal(a.get_f(), c.get_f())
+    ua, ub = a.fields()["u"], b.fields()["u"]
+    assert 0 < np.abs(ua - ub).max() < 0.05 * np.abs(ua).max()
+
+
+def test_nonorthogonal_variant_linear_k_has_no_net_diffusion():
+    """Variant 2 (non-orthogonal correction of the SST diffusion): the face-normal gradient
+    (k_j - k_i)/|d| + mean grad k . (n - d/|d|) is exact for a linear k, so with u = 0 the
+    diffusive fluxes of a linear k cancel around every interior cell (up to the variation of
+    the coefficient through nu_t = k / omega ~ 1e-4 nu) and k only decays; without the
+    correction the skewed triangles leave a net flux of the order of nu |grad k| / h."""
+    n = 14
+    xs = np.linspace(0, 1, n + 1)
+    xy, cells, sides = mg.quad_grid(xs, xs, 0.3, 5)
+    cells = mg.split_quads(cells)
+    bn = np.concatenate([sides["bottom"], sides["right"], sides["top"], sides["left"]])
+    bv = np.zeros((bn.shape[0], 5))
+    bv[:, 0] = 1.0
+    m = mg.Mesh(xy, np.arange(cells.shape[0] + 1, dtype=np.int32) * 3, cells.ravel(), bn,
+                np.zeros(bn.shape[0], np.int32), bv).normalized()
+    g = Oracle(mg.Case(m, nu=1e-2, dt=1e-3)).geometry()
+    k = 1e-3 * (1 + g["cx"] + 0.5 * g["cy"])
+    w = np.full(m.n_cells, 1e3)
+    inner = (np.minimum(g["cx"], 1 - g["cx"]) > 2.5 / n) & (np.minimum(g["cy"], 1 - g["cy"]) > 2.5 / n)
+    scale = 1e-2 * 1e-3 * math.hypot(1, 0.5) * n
+    out = {}
+    for var in (0, 2):
+        o = Oracle(mg.Case(m, nu=1e-2, dt=1e-3, sst=True, k=k, omega=w, variant=var))
+        o.step(1)
+        rk = (o.fields()["k"] * (1 + 1e-3 * 0.09 * 1e3) - k) / 1e-3   # point-implicit decay removed
+        out[var] = np.abs(rk[inner]).max() / scale
+    assert out[2] < 1e-3 and out[0] > 1.0, out
