@@ -109,6 +109,14 @@ typedef struct {
                                   the level of the scheme's own dt dependence.  Needs cfl > 0
                                   (dt is ignored); fvlbm_info reports the smallest dt_i.
                                   0: one dt per instance (default). */
+    int variant;               /* readings of points the paper leaves open, as a bit mask
+                                  (0, the default, is the reading the oracle pins):
+                                  1: Venkatakrishnan limiter on the least-squares gradient of f
+                                     before the upwind reconstruction (Sec. 3.2 Step 2 states
+                                     none); runs the two-pass kernels;
+                                  2: non-orthogonal correction of the SST diffusion flux,
+                                     grad phi . n = (phi_j - phi_i)/|d| + mean grad phi .
+                                     (n - d/|d|), instead of the two-point difference alone. */
 } fvlbm_params;
 
 typedef struct {

@@ -70,8 +70,9 @@ constexpr double kCs2 = 1.0 / 3.0;
 
 struct InstParam {
     double dt, nu, rho0, omega_min;
-    int sst;    // 1: k-omega SST instance; 0: laminar (SST kernels skip its tiles)
-    int local;  // 1: local time stepping (cell steps in Geo::dtc)
+    int sst;      // 1: k-omega SST instance; 0: laminar (SST kernels skip its tiles)
+    int local;    // 1: local time stepping (cell steps in Geo::dtc)
+    int variant;  // reading variants: 1 limiter on grad f, 2 SST non-orthogonal correction
 };
 
 template <class T>
@@ -195,16 +196,20 @@ __global__ void __launch_bounds__(kTile) k_stage1(const T *__restrict__ fn, T *_
 // ------------------------------------------------------------------ gradient of f
 // Least-squares cell gradient (Step 2): g_i = sum_m W_m (f_m - f_i), data from face neighbours
 // and, on boundary faces, the boundary value at the face midpoint.
-template <class T>
+template <class T, bool LIMIT>
 __global__ void __launch_bounds__(kTile) k_grad(const T *__restrict__ f, T *__restrict__ g,
                                                 Geo<T> G) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
-    const T rho0 = T(G.ip[G.tile_inst[blockIdx.x]].rho0);
-    T fi[kQ], gx[kQ], gy[kQ];
+    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
+    const T rho0 = T(P.rho0);
+    T fi[kQ], gx[kQ], gy[kQ], lo[kQ], hi[kQ];
     load9(f, np, i, fi);
 #pragma unroll
-    for (int a = 0; a < kQ; ++a) gx[a] = gy[a] = T(0);
+    for (int a = 0; a < kQ; ++a) {
+        gx[a] = gy[a] = T(0);
+        lo[a] = hi[a] = fi[a];
+    }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const int nb = G.nbr[m * np + i];
@@ -213,9 +218,14 @@ __global__ void __launch_bounds__(kTile) k_grad(const T *__restrict__ f, T *__re
         if (nb >= 0) {
 #pragma unroll
             for (int a = 0; a < kQ; ++a) {
-                const T d = f[a * np + nb] - fi[a];
+                const T fm = f[a * np + nb];
+                const T d = fm - fi[a];
                 gx[a] += wx * d;
                 gy[a] += wy * d;
+                if (LIMIT) {
+                    lo[a] = fmin(lo[a], fm);
+                    hi[a] = fmax(hi[a], fm);
+                }
             }
         } else {
             const int b = -nb - 1;
@@ -228,7 +238,41 @@ __global__ void __launch_bounds__(kTile) k_grad(const T *__restrict__ f, T *__re
                 const T d = fb[a] - fi[a];
                 gx[a] += wx * d;
                 gy[a] += wy * d;
+                if (LIMIT) {
+                    lo[a] = fmin(lo[a], fb[a]);
+                    hi[a] = fmax(hi[a], fb[a]);
+                }
             }
+        }
+    }
+    if (LIMIT && (P.variant & 1)) {
+        // Venkatakrishnan limiter (reading variant 1): phi = min over faces of
+        // [(D1^2 + e2) D2 + 2 D2^2 D1] / [D1^2 + 2 D2^2 + D1 D2 + e2] / D2, D2 = g . r_m the
+        // increment to face m, D1 the distance to the max (D2 > 0) or min (D2 < 0) of the cell
+        // and its face data, e2 = A^(3/2).
+        const T ar = G.area[i];
+        const T e2 = ar * sqrt(ar);
+        T phi[kQ];
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) phi[a] = T(1);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            if (G.nbr[m * np + i] == kNone) continue;
+            const T rx = G.rown[(2 * m) * np + i], ry = G.rown[(2 * m + 1) * np + i];
+#pragma unroll
+            for (int a = 1; a < kQ; ++a) {
+                const T d2 = gx[a] * rx + gy[a] * ry;
+                if (d2 == T(0)) continue;
+                const T d1 = d2 > T(0) ? hi[a] - fi[a] : lo[a] - fi[a];
+                const T r = ((d1 * d1 + e2) * d2 + T(2) * d2 * d2 * d1) /
+                            (d1 * d1 + T(2) * d2 * d2 + d1 * d2 + e2) / d2;
+                phi[a] = fmin(phi[a], r);
+            }
+        }
+#pragma unroll
+        for (int a = 1; a < kQ; ++a) {
+            gx[a] *= phi[a];
+            gy[a] *= phi[a];
         }
     }
 #pragma unroll
@@ -831,6 +875,7 @@ struct SstFace {
     bool has, bnd;
     T u, v, k, w;        // neighbour or boundary values
     T lg[4];             // neighbour limited gradients (interior only)
+    T gn[4];             // neighbour gradients of k, omega (non-orthogonal correction only)
     T f1, nut;           // neighbour (interior only)
     T snx, sny, rox, roy, rnx, rny, dinv;
 };
@@ -870,16 +915,31 @@ __device__ __forceinline__ void sst_cell_update(const InstParam &P, T dt, T ui, 
             const T gwf = T(0.5) * ((nu + sw_i * nti) + (nu + swj * f.nut));
             ck += un * kup;
             cw += un * wup;
-            dk += gkf * (f.k - ki) * f.dinv * dla;
-            dw += gwf * (f.w - wi) * f.dinv * dla;
+            T dkn = (f.k - ki) * f.dinv, dwn = (f.w - wi) * f.dinv;
+            if (P.variant & 2) {
+                // non-orthogonal correction (reading variant 2): + mean grad . (n - d/|d|),
+                // d = x_j - x_i = r_own - r_nbr, n the unit face normal
+                const T tx = f.snx / dla - (f.rox - f.rnx) * f.dinv;
+                const T ty = f.sny / dla - (f.roy - f.rny) * f.dinv;
+                dkn += T(0.5) * ((g[4] + f.gn[0]) * tx + (g[5] + f.gn[1]) * ty);
+                dwn += T(0.5) * ((g[6] + f.gn[2]) * tx + (g[7] + f.gn[3]) * ty);
+            }
+            dk += gkf * dkn * dla;
+            dw += gwf * dwn * dla;
         } else {
             const T un = f.u * f.snx + f.v * f.sny;
             const T kup = un >= T(0) ? kin : f.k;
             const T wup = un >= T(0) ? win : f.w;
             ck += un * kup;
             cw += un * wup;
-            dk += (nu + sk_i * nti) * (f.k - ki) * f.dinv * dla;
-            dw += (nu + sw_i * nti) * (f.w - wi) * f.dinv * dla;
+            T dkn = (f.k - ki) * f.dinv, dwn = (f.w - wi) * f.dinv;
+            if (P.variant & 2) {  // d = r_own (face midpoint - centroid)
+                const T tx = f.snx / dla - f.rox * f.dinv, ty = f.sny / dla - f.roy * f.dinv;
+                dkn += g[4] * tx + g[5] * ty;
+                dwn += g[6] * tx + g[7] * ty;
+            }
+            dk += (nu + sk_i * nti) * dkn * dla;
+            dw += (nu + sw_i * nti) * dwn * dla;
         }
     }
     const T s11 = g[0], s22 = g[3], s12 = T(0.5) * (g[1] + g[2]);
@@ -1058,6 +1118,10 @@ __global__ void __launch_bounds__(kTile)
             f.rnx = RN[2 * m]; f.rny = RN[2 * m + 1];
 #pragma unroll
             for (int c = 0; c < 4; ++c) f.lg[c] = grads[(8 + c) * np + nb];
+            if (P.variant & 2) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) f.gn[c] = grads[(4 + c) * np + nb];
+            }
             f.f1 = f1a[nb];
             f.nut = nut[nb];
         } else {
@@ -1328,6 +1392,7 @@ struct fvlbm_handle {
     bool fused = false;     // fused kernels available (IMEX scheme, kernel_path 0)
     int config = 2;         // 0: fused 256, 1: fused 128, 2: two-pass (see fvlbm_autotune)
     int scheme = 0;         // 0: IMEX Runge-Kutta; 1: explicit Euler (comparison scheme)
+    bool limit_f = false;   // an instance uses the limiter variant (two-pass kernels only)
     int *d_err = nullptr;   // device error flag (a staging wait gave up)
     void *gq = nullptr;     // fused path: node positions minus centroid [8 np]
     void *dvec = nullptr;   // fused path: neighbour-centroid offsets d_m [8 np]
@@ -1487,6 +1552,16 @@ void enqueue_fused(fvlbm_handle *h, bool stats, const fvlbm_handle::HaloSet &S) 
     }
 }
 
+// Gradient of f for the two-pass kernels, with the limiter variant when an instance asks for it.
+template <class T>
+void grad_f(const fvlbm_handle *h, dim3 grid, dim3 block, cudaStream_t s, const T *f, T *g,
+            const Geo<T> &G) {
+    if (h->limit_f)
+        k_grad<T, true><<<grid, block, 0, s>>>(f, g, G);
+    else
+        k_grad<T, false><<<grid, block, 0, s>>>(f, g, G);
+}
+
 template <class T>
 void enqueue_step(fvlbm_handle *h, bool stats) {
     Geo<T> G = geo_of<T>(h);
@@ -1526,7 +1601,7 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         h->turb = n;
     }
     if (h->scheme == 1) {  // explicit Euler: gradient, flux + collision into s0, copy back
-        launch(h, K_GRAD, "grad_f", [&] { k_grad<T><<<grid, block, 0, s>>>(fn, g, G); });
+        launch(h, K_GRAD, "grad_f", [&] { grad_f<T>(h, grid, block, s, fn, g, G); });
         if (stats) {
             launch(h, K_EULER, "euler", [&] {
                 k_flux_stage<T, 4, true><<<grid, block, 0, s>>>(fn, g, s0, fn, B, C, tau, mac, h->d_partial, G);
@@ -1553,15 +1628,15 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         }
     }
     launch(h, K_STAGE1, "stage1", [&] { k_stage1<T><<<grid, block, 0, s>>>(fn, s0, tau, G); });
-    launch(h, K_GRAD, "grad_f", [&] { k_grad<T><<<grid, block, 0, s>>>(s0, g, G); });
+    launch(h, K_GRAD, "grad_f", [&] { grad_f<T>(h, grid, block, s, s0, g, G); });
     launch(h, K_FLUX1, "flux_stage1", [&] {
         k_flux_stage<T, 1, false><<<grid, block, 0, s>>>(s0, g, s1, fn, B, C, tau, mac, nullptr, G);
     });
-    launch(h, K_GRAD, "grad_f", [&] { k_grad<T><<<grid, block, 0, s>>>(s1, g, G); });
+    launch(h, K_GRAD, "grad_f", [&] { grad_f<T>(h, grid, block, s, s1, g, G); });
     launch(h, K_FLUX2, "flux_stage2", [&] {
         k_flux_stage<T, 2, false><<<grid, block, 0, s>>>(s1, g, s0, fn, B, C, tau, mac, nullptr, G);
     });
-    launch(h, K_GRAD, "grad_f", [&] { k_grad<T><<<grid, block, 0, s>>>(s0, g, G); });
+    launch(h, K_GRAD, "grad_f", [&] { grad_f<T>(h, grid, block, s, s0, g, G); });
     if (stats) {
         launch(h, K_FLUX3, "flux_stage3", [&] {
             k_flux_stage<T, 3, true><<<grid, block, 0, s>>>(s0, g, s1, fn, B, C, tau, mac, h->d_partial, G);
@@ -1900,7 +1975,9 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     h->sst = sst != 0;
     h->scheme = params[0].scheme;
     if (h->scheme != 0 && h->scheme != 1) return FVLBM_ERR_BAD_PARAM;
-    h->fused = params[0].kernel_path == 0 && h->scheme == 0 && prec != FVLBM_FP64_TANGENT;
+    for (int q = 0; q < n; ++q) h->limit_f |= (params[q].variant & 1) != 0;
+    h->fused = params[0].kernel_path == 0 && h->scheme == 0 && prec != FVLBM_FP64_TANGENT &&
+               !h->limit_f;
     h->ninst = n;
     int cell_off = 0, bface_off = 0;
     std::vector<int> tile_inst, inst_tile0;
@@ -1949,7 +2026,7 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
         for (int t = 0; t < p.np / kTile; ++t) tile_inst.push_back(q);
         ip[q] = InstParam{p.dt, params[q].nu, params[q].rho0,
                           1e-12 * params[q].uref / params[q].lref, params[q].sst ? 1 : 0,
-                          p.dt_cell.empty() ? 0 : 1};
+                          p.dt_cell.empty() ? 0 : 1, params[q].variant};
         cell_off += p.np;
         bface_off += p.nb;
         h->inst.push_back(I);

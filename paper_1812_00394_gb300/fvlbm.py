@@ -49,7 +49,7 @@ class fvlbm_params(C.Structure):
                 ("lref", C.c_double), ("alpha_deg", C.c_double), ("rho_init", C.c_void_p),
                 ("u_init", C.c_void_p), ("v_init", C.c_void_p), ("k_init", C.c_void_p),
                 ("omega_init", C.c_void_p), ("kernel_path", C.c_int), ("scheme", C.c_int),
-                ("local_dt", C.c_int)]
+                ("local_dt", C.c_int), ("variant", C.c_int)]
 
 
 class fvlbm_stats(C.Structure):
@@ -289,7 +289,8 @@ class _Pack:
         self.params = fvlbm_params(case.nu, case.rho0, case.dt, case.cfl, int(bool(case.sst)),
                                    precision, case.uref, case.lref, case.alpha_deg, _p(rho), _p(u),
                                    _p(v), _p(k), _p(w), kernel_path, scheme,
-                                   int(bool(getattr(case, "local_dt", False))))
+                                   int(bool(getattr(case, "local_dt", False))),
+                                   int(getattr(case, "variant", 0)))
 
 
 class Solver:

@@ -434,3 +434,59 @@ def test_local_dt_accelerates_steady_couette_gpu():
     (ng, ug), (nl, ul) = out[False], out[True]
     assert nl * 5 < ng, (nl, ng)
     assert np.abs(ul - ug).max() < 5e-5 * U
+
+
+# ----------------------------------------------------------------- reading variants
+VARIANT_CASES = {
+    "cavity_delaunay": lambda: mg.cavity_delaunay(h_boundary=1 / 30, n_target=2000, re=1000.0,
+                                                  z=5.0, seed=3),
+    "naca_sst": lambda: mg.naca0012_cmesh(n_target=3000, alpha_deg=6.0),
+    "bfs_sst": lambda: mg.bfs_hybrid(n_target=2000),
+}
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("name", sorted(VARIANT_CASES))
+def test_variant_parity_fp64(name, variant):
+    """Reading variants (1: limiter on grad f; 2: non-orthogonal SST diffusion correction;
+    3: both) against the oracle's variants, element by element."""
+    case = dataclasses.replace(VARIANT_CASES[name](), variant=variant)
+    s = fvlbm.Solver(case, precision=FP64, device=0)
+    o = Oracle(case)
+    for n in (1, 10):
+        s.step(n)
+        o.step(n)
+        assert _rel_max(s.get_f(), o.get_f()) < 1e-10, (name, variant, n)
+    if case.sst:
+        fg, fo = s.fields(), o.fields()
+        for key in ("k", "omega", "nut"):
+            assert _rel_max(fg[key], fo[key]) < 1e-9, key
+
+
+def test_variant_limiter_uses_two_pass_and_fp32_parity():
+    """The limiter variant runs the two-pass kernels whatever kernel_path asks for (the
+    autotuner then has nothing to choose); FP32 stays within the FP32 bound."""
+    case = dataclasses.replace(VARIANT_CASES["naca_sst"](), variant=3)
+    s = fvlbm.Solver(case, precision=FP32, device=0, kernel_path=0)
+    chosen, times = s.autotune(2)
+    assert chosen == "twopass" and set(times) == set()
+    o = Oracle(case)
+    s.step(40)
+    o.step(40)
+    assert _vel_l2(s.fields(), o.fields()) < 1e-4
+
+
+def test_variant_sensitivity_is_bounded():
+    """Sensitivity of the wall force to the readings (NACA 0012, SST, 400 steps from the free
+    stream): every variant moves C_L and C_D, and by less than the uncertainty the readings
+    themselves carry (a few per cent of the transient values)."""
+    base = VARIANT_CASES["naca_sst"]()
+    res = {}
+    for v in (0, 1, 2, 3):
+        s = fvlbm.Solver(dataclasses.replace(base, variant=v), precision=FP64, device=0)
+        s.step(400)
+        res[v] = s.forces()
+    for v in (1, 2, 3):
+        for key in ("cl", "cd"):
+            rel = abs(res[v][key] - res[0][key]) / abs(res[0][key])
+            assert 0 < rel < 0.1, (v, key, res[v][key], res[0][key])
