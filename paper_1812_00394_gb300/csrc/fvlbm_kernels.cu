@@ -883,7 +883,7 @@ struct SstFace {
 // Convection (limited second-order upwind, mean face velocity), central diffusion (mean face
 // coefficient), explicit production and cross diffusion, point-implicit destruction; then f2,
 // nu_t = a1 k / max(a1 omega, S f2) and tau = (nu + nu_t)/cs^2.
-template <class T>
+template <class T, bool NONORTH>
 __device__ __forceinline__ void sst_cell_update(const InstParam &P, T dt, T ui, T vi, T ki, T wi,
                                                 T nti, T di, const T *g, const T *lgi, T f1,
                                                 const SstFace<T> *F, T &kn, T &wn, T &ntn,
@@ -916,7 +916,7 @@ __device__ __forceinline__ void sst_cell_update(const InstParam &P, T dt, T ui, 
             ck += un * kup;
             cw += un * wup;
             T dkn = (f.k - ki) * f.dinv, dwn = (f.w - wi) * f.dinv;
-            if (P.variant & 2) {
+            if (NONORTH && (P.variant & 2)) {
                 // non-orthogonal correction (reading variant 2): + mean grad . (n - d/|d|),
                 // d = x_j - x_i = r_own - r_nbr, n the unit face normal
                 const T tx = f.snx / dla - (f.rox - f.rnx) * f.dinv;
@@ -933,7 +933,7 @@ __device__ __forceinline__ void sst_cell_update(const InstParam &P, T dt, T ui, 
             ck += un * kup;
             cw += un * wup;
             T dkn = (f.k - ki) * f.dinv, dwn = (f.w - wi) * f.dinv;
-            if (P.variant & 2) {  // d = r_own (face midpoint - centroid)
+            if (NONORTH && (P.variant & 2)) {  // d = r_own (face midpoint - centroid)
                 const T tx = f.snx / dla - f.rox * f.dinv, ty = f.sny / dla - f.roy * f.dinv;
                 dkn += g[4] * tx + g[5] * ty;
                 dwn += g[6] * tx + g[7] * ty;
@@ -1062,7 +1062,9 @@ __global__ void __launch_bounds__(kTile)
 }
 
 // The k / omega update and the new relaxation time (and, on the fused path, f^(1)).
-template <class T, bool COMPACT>
+// NONORTH compiles the non-orthogonal diffusion correction (reading variant 2) in; without it
+// the kernel keeps the register count (and occupancy) of the default reading.
+template <class T, bool COMPACT, bool NONORTH>
 __global__ void __launch_bounds__(kTile)
     k_sst_update(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
                  const T *__restrict__ nut, const T *__restrict__ grads,
@@ -1118,7 +1120,7 @@ __global__ void __launch_bounds__(kTile)
             f.rnx = RN[2 * m]; f.rny = RN[2 * m + 1];
 #pragma unroll
             for (int c = 0; c < 4; ++c) f.lg[c] = grads[(8 + c) * np + nb];
-            if (P.variant & 2) {
+            if (NONORTH && (P.variant & 2)) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) f.gn[c] = grads[(4 + c) * np + nb];
             }
@@ -1130,7 +1132,7 @@ __global__ void __launch_bounds__(kTile)
     }
     T kn, wn, ntn, tnew;
     const T dt_i = cell_dt(G, P, i);
-    sst_cell_update(P, dt_i, ui, vi, ki, wi, nti, di, g, lgi, f1a[i], F, kn, wn, ntn, tnew);
+    sst_cell_update<T, NONORTH>(P, dt_i, ui, vi, ki, wi, nti, di, g, lgi, f1a[i], F, kn, wn, ntn, tnew);
     k_out[i] = kn;
     w_out[i] = wn;
     nut_out[i] = ntn;
@@ -1393,6 +1395,7 @@ struct fvlbm_handle {
     int config = 2;         // 0: fused 256, 1: fused 128, 2: two-pass (see fvlbm_autotune)
     int scheme = 0;         // 0: IMEX Runge-Kutta; 1: explicit Euler (comparison scheme)
     bool limit_f = false;   // an instance uses the limiter variant (two-pass kernels only)
+    bool nonorth = false;   // an instance uses the non-orthogonal SST diffusion correction
     int *d_err = nullptr;   // device error flag (a staging wait gave up)
     void *gq = nullptr;     // fused path: node positions minus centroid [8 np]
     void *dvec = nullptr;   // fused path: neighbour-centroid offsets d_m [8 np]
@@ -1584,8 +1587,13 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
                     k_sst_grad<T, true><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG);
                 });
                 launch(h, K_SST_UPDATE, "sst_update", [&] {
-                    k_sst_update<T, true><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G,
-                                                                 fn, static_cast<T *>(h->frel), CG);
+                    T *fr = static_cast<T *>(h->frel);
+                    if (h->nonorth)
+                        k_sst_update<T, true, true><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn,
+                                                                           tau, G, fn, fr, CG);
+                    else
+                        k_sst_update<T, true, false><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn,
+                                                                            tau, G, fn, fr, CG);
                 });
             }
         }
@@ -1594,8 +1602,12 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
                 k_sst_grad<T, false><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG);
             });
             launch(h, K_SST_UPDATE, "sst_update", [&] {
-                k_sst_update<T, false><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn,
-                                                              nullptr, CG);
+                if (h->nonorth)
+                    k_sst_update<T, false, true><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn,
+                                                                        tau, G, fn, nullptr, CG);
+                else
+                    k_sst_update<T, false, false><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn,
+                                                                         tau, G, fn, nullptr, CG);
             });
         }
         h->turb = n;
@@ -1975,7 +1987,10 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     h->sst = sst != 0;
     h->scheme = params[0].scheme;
     if (h->scheme != 0 && h->scheme != 1) return FVLBM_ERR_BAD_PARAM;
-    for (int q = 0; q < n; ++q) h->limit_f |= (params[q].variant & 1) != 0;
+    for (int q = 0; q < n; ++q) {
+        h->limit_f |= (params[q].variant & 1) != 0;
+        h->nonorth |= (params[q].variant & 2) != 0;
+    }
     h->fused = params[0].kernel_path == 0 && h->scheme == 0 && prec != FVLBM_FP64_TANGENT &&
                !h->limit_f;
     h->ninst = n;
