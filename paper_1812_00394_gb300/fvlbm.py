@@ -266,6 +266,32 @@ def fvlbm_forces_tangent(h, instance: int = 0, dalpha: float = 0.0) -> tuple[dic
     return dict(zip(keys, out)), dict(zip(keys, dout))
 
 
+def forces_gradient(case, directions, steps: int, device: int = -1):
+    """Derivatives of the wall force of ``case`` after ``steps`` steps along several parameter
+    directions at once: one FVLBM_FP64_TANGENT batch with one instance per direction, so that
+    every kernel launch of a step advances all directions.  Each direction is a dict with any
+    of ``dbedge_val`` ([n_bedges, 5]), ``dxy`` ([n_nodes, 2]), ``df`` ([n_cells, 9]) and
+    ``dalpha`` (d alpha / dp in radians).  Returns (forces, [d forces / dp_k])."""
+    k = len(directions)
+    if k == 0:
+        raise ValueError("forces_gradient needs at least one direction")
+    s = Solver([case] * k, precision=FVLBM_FP64_TANGENT, device=device)
+    for i, d in enumerate(directions):
+        if d.get("dxy") is not None:
+            s.tangent_seed_nodes(d["dxy"], i=i)
+        if d.get("dbedge_val") is not None or d.get("df") is not None:
+            s.tangent_seed(d.get("dbedge_val"), d.get("df"), i=i)
+    s.step(steps)
+    grads = []
+    val = None
+    for i, d in enumerate(directions):
+        v, g = s.forces_tangent(i, float(d.get("dalpha", 0.0)))
+        val = v if val is None else val
+        grads.append(g)
+    s.close()
+    return val, grads
+
+
 def fvlbm_destroy(h) -> None:
     if h:
         load().fvlbm_destroy(h)

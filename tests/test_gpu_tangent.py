@@ -287,3 +287,45 @@ def test_tangent_batch_directions_match_single():
         s.step(20)
         np.testing.assert_allclose(b.get_f_tangent(i), s.get_f_tangent(), rtol=0, atol=1e-12 *
                                    max(np.abs(s.get_f_tangent()).max(), 1e-300))
+
+
+def test_forces_gradient_many_directions_in_one_batch():
+    """d(C_D, C_L) along alpha, the inflow eddy-viscosity ratio and the normal displacements of
+    eight wall nodes, as one batched tangent solve: every direction equals its own
+    single-instance tangent, and the alpha and one wall-node direction match central
+    differences of the FP64 step."""
+    base = mg.naca0012_cmesh(n_target=2500, re_c=1e4, alpha_deg=4.0)
+    steps = 30
+    dirs = [{"dbedge_val": _dbval_alpha(base), "dalpha": 1.0},
+            {"dbedge_val": _dbval_nut_ratio(base, 1.0)}]
+    for x in np.linspace(0.05, 0.9, 8):
+        dirs.append({"dxy": _wall_node_normal(base, float(x))})
+    val, grads = fvlbm.forces_gradient(base, dirs, steps, device=0)
+    assert len(grads) == len(dirs)
+    for k in (0, 1, 5):
+        s = fvlbm.Solver(base, precision=TAN, device=0)
+        if "dxy" in dirs[k]:
+            s.tangent_seed_nodes(dirs[k]["dxy"])
+        else:
+            s.tangent_seed(dirs[k]["dbedge_val"])
+        s.step(steps)
+        _, g1 = s.forces_tangent(dalpha=dirs[k].get("dalpha", 0.0))
+        for key in ("cd", "cl"):
+            assert abs(grads[k][key] - g1[key]) <= 1e-12 * max(abs(g1[key]), 1e-30), (k, key)
+    # alpha against central differences at fixed dt and initial state
+    t = fvlbm.Solver(base, precision=TAN, device=0)
+    dt = t.dt()
+    hr = 1e-5
+    cp = dataclasses.replace(_freeze_init(mg.naca0012_cmesh(n_target=2500, re_c=1e4,
+                                                           alpha_deg=4.0 + math.degrees(hr)), base), dt=dt)
+    cm = dataclasses.replace(_freeze_init(mg.naca0012_cmesh(n_target=2500, re_c=1e4,
+                                                           alpha_deg=4.0 - math.degrees(hr)), base), dt=dt)
+    fp, fm = _gpu_forces(cp, steps), _gpu_forces(cm, steps)
+    fd = (fp["cl"] - fm["cl"]) / (2 * hr)
+    assert abs(grads[0]["cl"] - fd) <= 1e-5 * abs(fd)
+    # a wall node against central differences on moved meshes
+    h = 1e-6
+    fp = _gpu_forces(_moved(base, dirs[5]["dxy"], h, dt), steps)
+    fm = _gpu_forces(_moved(base, dirs[5]["dxy"], -h, dt), steps)
+    fd = (fp["cl"] - fm["cl"]) / (2 * h)
+    assert abs(grads[5]["cl"] - fd) <= 1e-4 * abs(fd) + 1e-9
