@@ -78,7 +78,8 @@ typedef struct oracle {
     double nu, rho0, dt, uref, lref, alpha_deg;
     double *dtc;                 /* local time stepping: dt of each cell (NULL: dt everywhere) */
     int variant;                 /* reading variants (bit mask): 1 limiter on the gradient of f,
-                                    2 non-orthogonal correction of the SST diffusion */
+                                    2 non-orthogonal correction of the SST diffusion, 4 SST
+                                    re-solved before every stage */
     int sst;
     int scheme;                  /* 0: IMEX Runge-Kutta (Part II); 1: explicit Euler (Part I) */
     double *f;                   /* [nc * Q], cell-major */
@@ -757,12 +758,33 @@ static int imex_step(oracle *o)
 {
     int nc = o->nc;
     size_t nq = (size_t)nc * Q;
+    /* Variant 4 (the other reading of Step 5, "repeat Steps 1-4" per stage): before every stage
+     * the SST update is solved again from (k, omega, nu_t) of t^n with the macros of the latest
+     * stage value (f^n, f^(1), f^(2)), and the stage uses the resulting tau; the last solve
+     * gives k, omega at t^{n+1}. */
+    int per_stage = o->sst && (o->variant & 4);
+    double *k0 = NULL, *w0 = NULL, *nt0 = NULL;
+    if (per_stage) {
+        k0 = (double *)xcalloc(nc, sizeof(double));
+        w0 = (double *)xcalloc(nc, sizeof(double));
+        nt0 = (double *)xcalloc(nc, sizeof(double));
+        memcpy(k0, o->k, nc * sizeof(double));
+        memcpy(w0, o->om, nc * sizeof(double));
+        memcpy(nt0, o->nut, nc * sizeof(double));
+    }
     if (o->sst) sst_update(o); /* Step 1 */
     else
         for (int i = 0; i < nc; i++) o->tau[i] = o->nu / CS2;
     memcpy(o->fn, o->f, nq * sizeof(double));
     double defect = 0.0;
     for (int J = 0; J < 3; J++) {
+        if (per_stage && J > 0) {
+            memcpy(o->k, k0, nc * sizeof(double));
+            memcpy(o->om, w0, nc * sizeof(double));
+            memcpy(o->nut, nt0, nc * sizeof(double));
+            for (int i = 0; i < nc; i++) moments(&o->fst[(size_t)i * Q], &o->rho[i], &o->ux[i], &o->uy[i]);
+            sst_update(o);
+        }
         for (int i = 0; i < nc; i++) {
             double tau = o->tau[i];
             double dt = cell_dt(o, i);
@@ -802,6 +824,11 @@ static int imex_step(oracle *o)
         o->f[q] = s;
     }
     o->moment_defect = defect;
+    if (per_stage) {
+        /* finish_step measures the change of u from t^n */
+        for (int i = 0; i < nc; i++) moments(&o->fn[(size_t)i * Q], &o->rho[i], &o->ux[i], &o->uy[i]);
+        free(k0); free(w0); free(nt0);
+    }
     return finish_step(o);
 }
 

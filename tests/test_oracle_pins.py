@@ -491,3 +491,37 @@ def test_nonorthogonal_variant_linear_k_has_no_net_diffusion():
         rk = (o.fields()["k"] * (1 + 1e-3 * 0.09 * 1e3) - k) / 1e-3   # point-implicit decay removed
         out[var] = np.abs(rk[inner]).max() / scale
     assert out[2] < 1e-3 and out[0] > 1.0, out
+
+
+def test_per_stage_sst_variant_orders():
+    """Variant 4 (the other reading of Step 5: SST solved again before every stage from
+    (k, omega, nu_t) of t^n with the latest stage's macros, each stage with its own tau).
+    Over one step from a developed state the macros change by O(dt), so nu_t (a point function
+    of the strain rate) moves by O(dt), while k and u, which only feel it through a dt-weighted
+    update, move by O(dt^2): halving dt halves the first and quarters the others."""
+    base = mg.bfs_hybrid(n_target=1500)
+    o = Oracle(base)
+    o.step(200)
+    f0, fl = o.get_f(), o.fields()
+    diffs = []
+    for frac in (1.0, 0.5):
+        res = {}
+        for v in (0, 4):
+            c = dataclasses.replace(base, variant=v, k=fl["k"], omega=fl["omega"],
+                                    dt=o.dt * frac, cfl=0.0)
+            x = Oracle(c)
+            x.set_f(f0)
+            x.step(1)
+            res[v] = x.fields()
+        diffs.append({key: np.abs(res[4][key] - res[0][key]).max() for key in ("k", "nut", "u")})
+    ratio = {key: diffs[0][key] / diffs[1][key] for key in diffs[0]}
+    assert 1.8 < ratio["nut"] < 2.2, ratio
+    assert 3.5 < ratio["k"] < 4.5, ratio
+    assert 3.5 < ratio["u"] < 4.5, ratio
+    # in a closed cavity with k = 0 (walls keep it 0) there is no eddy viscosity, and the
+    # variant is the default bit for bit
+    c0 = dataclasses.replace(mg.cavity_quad(16, re=400.0), sst=True)
+    a, b = Oracle(c0), Oracle(dataclasses.replace(c0, variant=4))
+    a.step(5)
+    b.step(5)
+    assert np.array_equal(a.get_f(), b.get_f())
