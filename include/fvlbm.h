@@ -116,7 +116,13 @@ typedef struct {
                                      none); runs the two-pass kernels;
                                   2: non-orthogonal correction of the SST diffusion flux,
                                      grad phi . n = (phi_j - phi_i)/|d| + mean grad phi .
-                                     (n - d/|d|), instead of the two-point difference alone. */
+                                     (n - d/|d|), instead of the two-point difference alone;
+                                  4: the SST solved again before stages 2 and 3 from k, omega,
+                                     nu_t of t^n with the macros of f^(1), f^(2) (Sec. 3.2
+                                     Step 5 read as "repeat Steps 1-4" per stage); stage J
+                                     relaxes with its own tau^(J); the last solve gives
+                                     t^{n+1}.  Runs the two-pass kernels; all instances of a
+                                     batch must agree on this bit. */
 } fvlbm_params;
 
 typedef struct {

@@ -193,6 +193,21 @@ __global__ void __launch_bounds__(kTile) k_stage1(const T *__restrict__ fn, T *_
     store9(fs, np, i, f);
 }
 
+// Macros (rho, u, v) of a stage value, for the SST solve before the next stage (per-stage
+// SST reading).
+template <class T>
+__global__ void __launch_bounds__(kTile) k_stage_macros(const T *__restrict__ fs, T *__restrict__ mac,
+                                                        Geo<T> G) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    T f[kQ], dr, r, u, v;
+    load9(fs, np, i, f);
+    moments(f, T(G.ip[G.tile_inst[blockIdx.x]].rho0), dr, r, u, v);
+    mac[i] = r;
+    mac[np + i] = u;
+    mac[2 * np + i] = v;
+}
+
 // ------------------------------------------------------------------ gradient of f
 // Least-squares cell gradient (Step 2): g_i = sum_m W_m (f_m - f_i), data from face neighbours
 // and, on boundary faces, the boundary value at the face midpoint.
@@ -324,7 +339,7 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
                                               T *__restrict__ mac, double *__restrict__ partial,
                                               const T *__restrict__ area,
                                               T *__restrict__ frel = nullptr,
-                                              bool fn_read = false) {
+                                              bool fn_read = false, T t1_i = T(0)) {
     const T rho0 = T(P.rho0);
     const T dt = dt_i;
     const T itau = T(1) / t_i;          // one division per cell, products below
@@ -349,7 +364,13 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
             for (int a = 0; a < kQ; ++a) f0[a] = FN_FROM_F1 ? fn[a * np + i] : a1[a * ld1 + c1];
             moments(f0, rho0, dr, r, u, v);
             feq_dev(dr, r, u, v, eq);
-            const T s1 = z * inv;  // f^(1) = (f^n + zq f^eq) / (1 + zq)
+            // f^(1) = (f^n + zq1 f^eq) / (1 + zq1), relaxed with tau^(1) (= tau unless the SST
+            // is solved per stage, when stage 2 has its own tau)
+            T s1 = z * inv;
+            if (t1_i > T(0)) {
+                const T z1 = dt / t1_i;
+                s1 = z1 / (T(1) + T(0.25) * z1);
+            }
 #pragma unroll
             for (int a = 0; a < kQ; ++a) dgc1[a] = (eq[a] - f0[a]) * s1;
         }
@@ -432,10 +453,10 @@ __device__ __forceinline__ void stage_update(int i, size_t np, const T *fi, cons
                                              T *__restrict__ fn, T *__restrict__ Bacc,
                                              T *__restrict__ Cacc, const T *__restrict__ tau,
                                              T *__restrict__ mac, double *__restrict__ partial,
-                                             const T *__restrict__ area, T dt_i) {
+                                             const T *__restrict__ area, T dt_i, T t1_i) {
     const T *a1 = STAGE == 1 ? fn : (STAGE == 2 ? Bacc : Cacc);
     stage_algebra<T, STAGE, STATS, NT>(i, np, fi, acc, P, tau[i], dt_i, a1, np, i, Cacc, np, i, fs_out,
-                                       fn, Bacc, Cacc, mac, partial, area);
+                                       fn, Bacc, Cacc, mac, partial, area, nullptr, false, t1_i);
 }
 
 // ------------------------------------------------------------------ flux + stage solve
@@ -446,7 +467,7 @@ __global__ void __launch_bounds__(kTile)
     k_flux_stage(const T *__restrict__ fs, const T *__restrict__ g, T *__restrict__ fs_out,
                  T *__restrict__ fn, T *__restrict__ Bacc, T *__restrict__ Cacc,
                  const T *__restrict__ tau, T *__restrict__ mac, double *__restrict__ partial,
-                 Geo<T> G) {
+                 Geo<T> G, const T *__restrict__ tau1 = nullptr) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -483,7 +504,8 @@ __global__ void __launch_bounds__(kTile)
         }
     }
     stage_update<T, STAGE, STATS, kTile>(i, np, fi, acc, P, fs_out, fn, Bacc, Cacc, tau, mac, partial,
-                                         G.area, cell_dt(G, P, i));
+                                         G.area, cell_dt(G, P, i),
+                                         (STAGE == 1 && tau1 != nullptr) ? tau1[i] : T(0));
 }
 
 // ------------------------------------------------------------------ fused stage kernel
@@ -1396,6 +1418,8 @@ struct fvlbm_handle {
     int scheme = 0;         // 0: IMEX Runge-Kutta; 1: explicit Euler (comparison scheme)
     bool limit_f = false;   // an instance uses the limiter variant (two-pass kernels only)
     bool nonorth = false;   // an instance uses the non-orthogonal SST diffusion correction
+    bool per_stage = false; // SST solved before every stage (reading variant 4; two-pass only)
+    void *tau1 = nullptr, *mac2 = nullptr;  // per-stage SST: tau of stage 1, stage macros
     int *d_err = nullptr;   // device error flag (a staging wait gave up)
     void *gq = nullptr;     // fused path: node positions minus centroid [8 np]
     void *dvec = nullptr;   // fused path: neighbour-centroid offsets d_m [8 np]
@@ -1518,7 +1542,7 @@ void launch(fvlbm_handle *h, int id, const char *name, F &&fn) {
 
 enum KernelId {
     K_SST_GRAD, K_SST_UPDATE, K_STAGE1, K_GRAD, K_FLUX1, K_FLUX2, K_FLUX3, K_REDUCE,
-    K_FUSED1, K_FUSED2, K_FUSED3, K_EULER
+    K_FUSED1, K_FUSED2, K_FUSED3, K_EULER, K_MACROS
 };
 
 // The three fused stages with BLK-cell blocks (halo set S).
@@ -1610,6 +1634,54 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
                                                                          tau, G, fn, nullptr, CG);
             });
         }
+        if (h->per_stage && h->scheme == 0) {
+            // per-stage SST reading (two-pass kernels): the SST is solved again from t^n before
+            // stages 2 and 3 with the macros of f^(1) and f^(2); stage J relaxes with tau^(J)
+            T *t1 = static_cast<T *>(h->tau1), *m2 = static_cast<T *>(h->mac2);
+            auto solve = [&](T *macp, T *tau_out) {
+                launch(h, K_SST_GRAD, "sst_grad", [&] {
+                    k_sst_grad<T, false><<<grid, block, 0, s>>>(macp, kc, wc, sg, f1, G, CG);
+                });
+                launch(h, K_SST_UPDATE, "sst_update", [&] {
+                    if (h->nonorth)
+                        k_sst_update<T, false, true><<<grid, block, 0, s>>>(macp, kc, wc, nc, sg, f1, kn, wn,
+                                                                            nn, tau_out, G, fn, nullptr, CG);
+                    else
+                        k_sst_update<T, false, false><<<grid, block, 0, s>>>(macp, kc, wc, nc, sg, f1, kn, wn,
+                                                                             nn, tau_out, G, fn, nullptr, CG);
+                });
+            };
+            // the solve of the step start already ran above into tau; stage 1 relaxes with it
+            launch(h, K_STAGE1, "stage1", [&] { k_stage1<T><<<grid, block, 0, s>>>(fn, s0, tau, G); });
+            cudaMemcpyAsync(t1, tau, sizeof(T) * static_cast<size_t>(h->np), cudaMemcpyDeviceToDevice, s);
+            launch(h, K_MACROS, "stage_macros", [&] { k_stage_macros<T><<<grid, block, 0, s>>>(s0, m2, G); });
+            solve(m2, tau);
+            launch(h, K_GRAD, "grad_f", [&] { grad_f<T>(h, grid, block, s, s0, g, G); });
+            launch(h, K_FLUX1, "flux_stage1", [&] {
+                k_flux_stage<T, 1, false><<<grid, block, 0, s>>>(s0, g, s1, fn, B, C, tau, mac, nullptr, G, t1);
+            });
+            launch(h, K_MACROS, "stage_macros", [&] { k_stage_macros<T><<<grid, block, 0, s>>>(s1, m2, G); });
+            solve(m2, tau);
+            launch(h, K_GRAD, "grad_f", [&] { grad_f<T>(h, grid, block, s, s1, g, G); });
+            launch(h, K_FLUX2, "flux_stage2", [&] {
+                k_flux_stage<T, 2, false><<<grid, block, 0, s>>>(s1, g, s0, fn, B, C, tau, mac, nullptr, G);
+            });
+            launch(h, K_GRAD, "grad_f", [&] { grad_f<T>(h, grid, block, s, s0, g, G); });
+            if (stats) {
+                launch(h, K_FLUX3, "flux_stage3", [&] {
+                    k_flux_stage<T, 3, true><<<grid, block, 0, s>>>(s0, g, s1, fn, B, C, tau, mac, h->d_partial, G);
+                });
+                launch(h, K_REDUCE, "reduce", [&] {
+                    k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->d_inst_tile0, h->d_inst_sums);
+                });
+            } else {
+                launch(h, K_FLUX3, "flux_stage3", [&] {
+                    k_flux_stage<T, 3, false><<<grid, block, 0, s>>>(s0, g, s1, fn, B, C, tau, mac, nullptr, G);
+                });
+            }
+            h->turb = n;
+            return;
+        }
         h->turb = n;
     }
     if (h->scheme == 1) {  // explicit Euler: gradient, flux + collision into s0, copy back
@@ -1671,6 +1743,7 @@ void enqueue(fvlbm_handle *h, bool stats) {
 }
 
 int launches_per_step(const fvlbm_handle *h) {
+    if (h->sst && h->per_stage && h->scheme == 0) return 2 + 1 + 3 + 2 + 3 + 2 + 2;
     return (h->sst ? 2 : 0) + (h->scheme == 1 ? 2 : (h->config != 2 ? 3 : 7));
 }
 
@@ -1809,6 +1882,10 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
     for (int b = 0; b < 2; ++b)
         for (void **p : {&h->kk[b], &h->ww[b], &h->nut[b]})
             if ((rc = dalloc(h, p, np * ts))) return rc;
+    if (h->sst && h->per_stage) {
+        if ((rc = dalloc(h, &h->tau1, np * ts))) return rc;
+        if ((rc = dalloc(h, &h->mac2, 3 * np * ts))) return rc;
+    }
     if (h->sst) {
         if ((rc = dalloc(h, &h->sgrad, 12 * np * ts))) return rc;
         if ((rc = dalloc(h, &h->f1, np * ts))) return rc;
@@ -1990,9 +2067,11 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     for (int q = 0; q < n; ++q) {
         h->limit_f |= (params[q].variant & 1) != 0;
         h->nonorth |= (params[q].variant & 2) != 0;
+        if (((params[q].variant ^ params[0].variant) & 4) != 0) return FVLBM_ERR_BAD_PARAM;
     }
+    h->per_stage = (params[0].variant & 4) != 0;
     h->fused = params[0].kernel_path == 0 && h->scheme == 0 && prec != FVLBM_FP64_TANGENT &&
-               !h->limit_f;
+               !h->limit_f && !h->per_stage;
     h->ninst = n;
     int cell_off = 0, bface_off = 0;
     std::vector<int> tile_inst, inst_tile0;

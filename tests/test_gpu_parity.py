@@ -445,11 +445,12 @@ VARIANT_CASES = {
 }
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 7])
 @pytest.mark.parametrize("name", sorted(VARIANT_CASES))
 def test_variant_parity_fp64(name, variant):
     """Reading variants (1: limiter on grad f; 2: non-orthogonal SST diffusion correction;
-    3: both) against the oracle's variants, element by element."""
+    4: SST solved per stage; 3 and 7: combinations) against the oracle's variants, element by
+    element."""
     case = dataclasses.replace(VARIANT_CASES[name](), variant=variant)
     s = fvlbm.Solver(case, precision=FP64, device=0)
     o = Oracle(case)
@@ -476,17 +477,33 @@ def test_variant_limiter_uses_two_pass_and_fp32_parity():
     assert _vel_l2(s.fields(), o.fields()) < 1e-4
 
 
+def test_per_stage_variant_batch_rule_and_fp32():
+    """All instances of a batch agree on the per-stage SST bit (else BAD_PARAM); the FP32
+    per-stage path stays within the FP32 bound of the oracle."""
+    a = dataclasses.replace(VARIANT_CASES["bfs_sst"](), variant=4)
+    b = VARIANT_CASES["naca_sst"]()
+    with pytest.raises(fvlbm.FvlbmError) as e:
+        fvlbm.Solver([a, b], precision=FP64, device=0)
+    assert e.value.code == fvlbm.FVLBM_ERR_BAD_PARAM
+    s = fvlbm.Solver(a, precision=FP32, device=0)
+    o = Oracle(a)
+    s.step(40)
+    o.step(40)
+    assert _vel_l2(s.fields(), o.fields()) < 1e-4
+    assert _rel_max(s.fields()["nut"], o.fields()["nut"]) < 1e-3
+
+
 def test_variant_sensitivity_is_bounded():
     """Sensitivity of the wall force to the readings (NACA 0012, SST, 400 steps from the free
     stream): every variant moves C_L and C_D, and by less than the uncertainty the readings
     themselves carry (a few per cent of the transient values)."""
     base = VARIANT_CASES["naca_sst"]()
     res = {}
-    for v in (0, 1, 2, 3):
+    for v in (0, 1, 2, 3, 4):
         s = fvlbm.Solver(dataclasses.replace(base, variant=v), precision=FP64, device=0)
         s.step(400)
         res[v] = s.forces()
-    for v in (1, 2, 3):
+    for v in (1, 2, 3, 4):
         for key in ("cl", "cd"):
             rel = abs(res[v][key] - res[0][key]) / abs(res[0][key])
             assert 0 < rel < 0.1, (v, key, res[v][key], res[0][key])
