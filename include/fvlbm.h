@@ -240,6 +240,28 @@ int fvlbm_get_f_tangent(fvlbm_handle *h, int instance, double *df);
 int fvlbm_tangent_seed_nodes(fvlbm_handle *h, int instance, const double *dxy);
 int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *out, double *dout);
 
+/* ---------------------------------------------------------------------------------------------
+ * Checkpoint / resume and divergence rollback (no counterpart in the paper).
+ *
+ * The state of a handle -- f^n, f^(1) of the coming step, the macros, tau, k / omega / nu_t and
+ * their ping-pong parity, and the step count -- as one opaque host blob in the handle's internal
+ * cell order.  fvlbm_state_bytes gives its size; fvlbm_save_state writes it into buf (bytes at
+ * least that size); fvlbm_load_state restores it into this handle or into any handle created
+ * from the same meshes and parameters (the preprocessing is deterministic).  The blob's header
+ * carries the precision, the sizes and a checksum of the cell order; a blob of another
+ * configuration returns FVLBM_ERR_BAD_PARAM and changes nothing.  Both synchronise.
+ *
+ * fvlbm_set_rollback(h, every): with every > 0, the handle keeps one device copy of its state
+ * (fvlbm_state_bytes of device memory), refreshed at the end of an fvlbm_step call with stats
+ * that finds the state finite, at most once per `every` steps.  When an fvlbm_step with stats
+ * finds a NaN / Inf, it restores that copy before returning FVLBM_ERR_DIVERGED, and
+ * stats->steps is the restored step.  every = 0 frees the copy.
+ * Errors: BAD_PARAM, OOM, CUDA. */
+int fvlbm_state_bytes(fvlbm_handle *h, long long *bytes);
+int fvlbm_save_state(fvlbm_handle *h, void *buf, long long bytes);
+int fvlbm_load_state(fvlbm_handle *h, const void *buf, long long bytes);
+int fvlbm_set_rollback(fvlbm_handle *h, int every);
+
 void fvlbm_destroy(fvlbm_handle *h);
 const char *fvlbm_strerror(int code);
 

@@ -1419,6 +1419,11 @@ struct fvlbm_handle {
     bool limit_f = false;   // an instance uses the limiter variant (two-pass kernels only)
     bool nonorth = false;   // an instance uses the non-orthogonal SST diffusion correction
     bool per_stage = false; // SST solved before every stage (reading variant 4; two-pass only)
+    unsigned long long order_hash = 0;  // checksum of the internal cell order (state blobs)
+    int rollback_every = 0;             // watchdog: device copy of the state every N steps
+    void *rollback = nullptr;           // that copy (state_regions layout)
+    long long rollback_step = -1, rollback_last = -1;
+    int rollback_turb = 0;
     void *tau1 = nullptr, *mac2 = nullptr;  // per-stage SST: tau of stage 1, stage macros
     int *d_err = nullptr;   // device error flag (a staging wait gave up)
     void *gq = nullptr;     // fused path: node positions minus centroid [8 np]
@@ -1504,6 +1509,36 @@ int dalloc(fvlbm_handle *h, void **p, size_t bytes) {
     h->device_bytes += bytes;
     return FVLBM_OK;
 }
+
+// The device arrays that make up the state a step reads (everything else is scratch):
+// f^n, f^(1) of the coming step, the macros, tau and both k / omega / nu_t ping-pong buffers.
+std::vector<std::pair<void *, size_t>> state_regions(const fvlbm_handle *h) {
+    size_t ts = 0;
+    dispatch(h->precision, [&](auto z_) { ts = sizeof(z_); });
+    const size_t np = h->np;
+    std::vector<std::pair<void *, size_t>> st = {
+        {h->fn, kQ * np * ts}, {h->frel, kQ * np * ts}, {h->mac, 3 * np * ts}, {h->tau, np * ts}};
+    for (int b = 0; b < 2; ++b) {
+        st.push_back({h->kk[b], np * ts});
+        st.push_back({h->ww[b], np * ts});
+        st.push_back({h->nut[b], np * ts});
+    }
+    return st;
+}
+
+size_t state_bytes(const fvlbm_handle *h) {
+    size_t t = 0;
+    for (auto &e : state_regions(h)) t += e.second;
+    return t;
+}
+
+struct StateHeader {
+    char magic[8];
+    int version, precision, np, ninst, turb, pad;
+    long long steps;
+    unsigned long long order_hash;
+    unsigned long long payload;
+};
 
 template <class T>
 int upload_as(fvlbm_handle *h, void **dst, const std::vector<double> &src) {
@@ -1946,6 +1981,14 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
     if ((rc = upload_raw(h, &h->d_btype, btype))) return rc;
     if ((rc = upload_raw(h, &h->d_bowner, bowner))) return rc;
     if ((rc = upload_raw(h, &h->d_perm, perm))) return rc;
+    {  // FNV-1a over the internal order of every instance (state blobs check it)
+        unsigned long long hsh = 1469598103934665603ull;
+        for (int q = 0; q < h->ninst; ++q) {
+            hsh = (hsh ^ static_cast<unsigned long long>(P[q]->np)) * 1099511628211ull;
+            for (int v : P[q]->perm) hsh = (hsh ^ static_cast<unsigned long long>(v)) * 1099511628211ull;
+        }
+        h->order_hash = hsh;
+    }
     {
         std::vector<int> map;
         int out_off = 0;
@@ -2296,7 +2339,31 @@ int fvlbm_step(fvlbm_handle *h, int n_steps, fvlbm_stats *stats) {
             stats->mass += sums[4 * q + 2];
             if (sums[4 * q + 3] != 0.0 || !std::isfinite(e)) stats->diverged = 1;
         }
-        if (stats->diverged) return FVLBM_ERR_DIVERGED;
+        if (stats->diverged) {
+            if (h->rollback && h->rollback_step >= 0) {  // back to the last finite state
+                size_t off = 0;
+                for (auto &e : state_regions(h)) {
+                    CK(cudaMemcpyAsync(e.first, static_cast<char *>(h->rollback) + off, e.second,
+                                       cudaMemcpyDeviceToDevice, h->stream));
+                    off += e.second;
+                }
+                CK(cudaStreamSynchronize(h->stream));
+                h->steps = h->rollback_step;
+                h->turb = h->rollback_turb;
+                stats->steps = h->steps;
+            }
+            return FVLBM_ERR_DIVERGED;
+        }
+        if (h->rollback && (h->rollback_last < 0 || h->steps - h->rollback_last >= h->rollback_every)) {
+            size_t off = 0;
+            for (auto &e : state_regions(h)) {
+                CK(cudaMemcpyAsync(static_cast<char *>(h->rollback) + off, e.first, e.second,
+                                   cudaMemcpyDeviceToDevice, h->stream));
+                off += e.second;
+            }
+            h->rollback_step = h->rollback_last = h->steps;
+            h->rollback_turb = h->turb;
+        }
     }
     return FVLBM_OK;
 }
@@ -2605,16 +2672,7 @@ int fvlbm_autotune(fvlbm_handle *h, int trial_steps, int *chosen, double *ms_per
         return FVLBM_OK;
     }
     // snapshot of the state a step reads (the rest is scratch)
-    size_t ts = 0;
-    dispatch(h->precision, [&](auto z_) { ts = sizeof(z_); });
-    const size_t np = h->np;
-    std::vector<std::pair<void *, size_t>> st = {
-        {h->fn, kQ * np * ts}, {h->frel, kQ * np * ts}, {h->mac, 3 * np * ts}, {h->tau, np * ts}};
-    for (int b = 0; b < 2; ++b) {
-        st.push_back({h->kk[b], np * ts});
-        st.push_back({h->ww[b], np * ts});
-        st.push_back({h->nut[b], np * ts});
-    }
+    const std::vector<std::pair<void *, size_t>> st = state_regions(h);
     size_t total = 0;
     for (auto &e : st) total += e.second;
     char *snap = nullptr;
@@ -2676,6 +2734,78 @@ int fvlbm_autotune(fvlbm_handle *h, int trial_steps, int *chosen, double *ms_per
     if (chosen) *chosen = best_c;
     if (err != cudaSuccess) return cuda_fail(err);
     CK(cudaGetLastError());
+    return FVLBM_OK;
+}
+
+int fvlbm_state_bytes(fvlbm_handle *h, long long *bytes) {
+    if (!h || !bytes) return FVLBM_ERR_BAD_PARAM;
+    *bytes = static_cast<long long>(sizeof(StateHeader) + state_bytes(h));
+    return FVLBM_OK;
+}
+
+int fvlbm_save_state(fvlbm_handle *h, void *buf, long long bytes) {
+    if (!h || !buf || bytes < static_cast<long long>(sizeof(StateHeader) + state_bytes(h)))
+        return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    StateHeader hd{};
+    std::memcpy(hd.magic, "FVLBMST", 8);
+    hd.version = 1;
+    hd.precision = h->precision;
+    hd.np = h->np;
+    hd.ninst = h->ninst;
+    hd.turb = h->turb;
+    hd.steps = h->steps;
+    hd.order_hash = h->order_hash;
+    hd.payload = state_bytes(h);
+    std::memcpy(buf, &hd, sizeof(hd));
+    char *dst = static_cast<char *>(buf) + sizeof(hd);
+    for (auto &e : state_regions(h)) {
+        CK(cudaMemcpyAsync(dst, e.first, e.second, cudaMemcpyDeviceToHost, h->stream));
+        dst += e.second;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return FVLBM_OK;
+}
+
+int fvlbm_load_state(fvlbm_handle *h, const void *buf, long long bytes) {
+    if (!h || !buf || bytes < static_cast<long long>(sizeof(StateHeader))) return FVLBM_ERR_BAD_PARAM;
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (std::memcmp(hd.magic, "FVLBMST", 8) != 0 || hd.version != 1 || hd.precision != h->precision ||
+        hd.np != h->np || hd.ninst != h->ninst || hd.order_hash != h->order_hash ||
+        hd.payload != state_bytes(h) || bytes < static_cast<long long>(sizeof(hd) + hd.payload)) {
+        fprintf(stderr, "fvlbm_load_state: the blob does not match this handle\n");
+        return FVLBM_ERR_BAD_PARAM;
+    }
+    CK(cudaSetDevice(h->device));
+    const char *src = static_cast<const char *>(buf) + sizeof(hd);
+    for (auto &e : state_regions(h)) {
+        CK(cudaMemcpyAsync(e.first, src, e.second, cudaMemcpyHostToDevice, h->stream));
+        src += e.second;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    h->steps = hd.steps;
+    h->turb = hd.turb;
+    return FVLBM_OK;
+}
+
+int fvlbm_set_rollback(fvlbm_handle *h, int every) {
+    if (!h || every < 0) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    if (every == 0) {
+        if (h->rollback) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(h->rollback);
+            h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), h->rollback));
+            h->device_bytes -= state_bytes(h);
+            h->rollback = nullptr;
+        }
+    } else if (!h->rollback) {
+        int rc = dalloc(h, &h->rollback, state_bytes(h));
+        if (rc) return rc;
+    }
+    h->rollback_every = every;
+    h->rollback_step = h->rollback_last = -1;
     return FVLBM_OK;
 }
 

@@ -61,7 +61,8 @@ EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "
            "fvlbm_set_f", "fvlbm_get_fields", "fvlbm_info", "fvlbm_footprint",
            "fvlbm_profile_kernels", "fvlbm_autotune", "fvlbm_destroy", "fvlbm_strerror",
            "fvlbm_stats_reduce_static", "fvlbm_tangent_seed", "fvlbm_tangent_seed_nodes",
-           "fvlbm_get_f_tangent", "fvlbm_forces_tangent"]
+           "fvlbm_get_f_tangent", "fvlbm_forces_tangent", "fvlbm_state_bytes", "fvlbm_save_state",
+           "fvlbm_load_state", "fvlbm_set_rollback"]
 
 _lib = None
 
@@ -94,6 +95,10 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_footprint.argtypes = [vp, P(C.c_longlong), P(i)]
     lib.fvlbm_profile_kernels.argtypes = [vp, i, i, vp, vp, vp]
     lib.fvlbm_autotune.argtypes = [vp, i, P(i), vp]
+    lib.fvlbm_state_bytes.argtypes = [vp, P(C.c_longlong)]
+    lib.fvlbm_save_state.argtypes = [vp, vp, C.c_longlong]
+    lib.fvlbm_load_state.argtypes = [vp, vp, C.c_longlong]
+    lib.fvlbm_set_rollback.argtypes = [vp, i]
     lib.fvlbm_tangent_seed.argtypes = [vp, i, vp, vp]
     lib.fvlbm_get_f_tangent.argtypes = [vp, i, vp]
     lib.fvlbm_tangent_seed_nodes.argtypes = [vp, i, vp]
@@ -266,6 +271,25 @@ def fvlbm_forces_tangent(h, instance: int = 0, dalpha: float = 0.0) -> tuple[dic
     return dict(zip(keys, out)), dict(zip(keys, dout))
 
 
+def fvlbm_save_state(h) -> bytes:
+    """The handle's state as an opaque blob (checkpoint)."""
+    n = C.c_longlong()
+    _check(load().fvlbm_state_bytes(h, C.byref(n)), "fvlbm_state_bytes")
+    buf = C.create_string_buffer(n.value)
+    _check(load().fvlbm_save_state(h, buf, n.value), "fvlbm_save_state")
+    return buf.raw
+
+
+def fvlbm_load_state(h, blob: bytes) -> None:
+    """Restore a blob written by fvlbm_save_state (same meshes and parameters)."""
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(load().fvlbm_load_state(h, buf, len(blob)), "fvlbm_load_state")
+
+
+def fvlbm_set_rollback(h, every: int) -> None:
+    _check(load().fvlbm_set_rollback(h, int(every)), "fvlbm_set_rollback")
+
+
 def forces_gradient(case, directions, steps: int, device: int = -1):
     """Derivatives of the wall force of ``case`` after ``steps`` steps along several parameter
     directions at once: one FVLBM_FP64_TANGENT batch with one instance per direction, so that
@@ -369,6 +393,15 @@ class Solver:
 
     def profile_kernels(self, n_steps: int) -> dict:
         return fvlbm_profile_kernels(self.h, n_steps)
+
+    def save_state(self) -> bytes:
+        return fvlbm_save_state(self.h)
+
+    def load_state(self, blob: bytes) -> None:
+        fvlbm_load_state(self.h, blob)
+
+    def set_rollback(self, every: int) -> None:
+        fvlbm_set_rollback(self.h, every)
 
     def tangent_seed(self, dbedge_val=None, df=None, i: int = 0) -> None:
         fvlbm_tangent_seed(self.h, i, dbedge_val, df)

@@ -507,3 +507,51 @@ def test_variant_sensitivity_is_bounded():
         for key in ("cl", "cd"):
             rel = abs(res[v][key] - res[0][key]) / abs(res[0][key])
             assert 0 < rel < 0.1, (v, key, res[v][key], res[0][key])
+
+
+# ----------------------------------------------------------------- checkpoint / rollback
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_save_load_state_resumes_bitwise(prec):
+    """A state blob saved after 10 steps and loaded into a fresh handle built from the same
+    cases continues bit for bit like the original (SST parity, step count and f^(1) included);
+    a blob of another configuration is refused and changes nothing."""
+    cases = [mg.naca0012_cmesh(n_target=3000, alpha_deg=3.0), mg.cavity_quad(20, re=400.0)]
+    a = fvlbm.Solver(cases, precision=prec, device=0)
+    a.step(11)
+    blob = a.save_state()
+    a.step(21)
+    b = fvlbm.Solver(cases, precision=prec, device=0)
+    b.load_state(blob)
+    st = b.step(21, stats=True)
+    assert st["steps"] == 32
+    for i in range(2):
+        np.testing.assert_array_equal(a.get_f(i), b.get_f(i))
+        np.testing.assert_array_equal(a.fields(i)["omega"], b.fields(i)["omega"])
+    other = fvlbm.Solver(mg.cavity_quad(21, re=400.0), precision=prec, device=0)
+    before = other.get_f()
+    with pytest.raises(fvlbm.FvlbmError) as e:
+        other.load_state(blob)
+    assert e.value.code == fvlbm.FVLBM_ERR_BAD_PARAM
+    np.testing.assert_array_equal(other.get_f(), before)
+
+
+def test_rollback_restores_last_finite_state():
+    """With rollback on, a step that produces NaN (planted on the host through set_f) returns
+    DIVERGED and leaves the handle at the last finite checkpoint, from which it continues."""
+    case = mg.bfs_hybrid(n_target=2000)
+    s = fvlbm.Solver(case, precision=FP32, device=0)
+    s.set_rollback(5)
+    assert s.step(10, stats=True)["diverged"] == 0
+    good = s.get_f()
+    om = s.fields()["omega"]
+    bad = good.copy()
+    bad[7, 3] = np.nan
+    s.set_f(bad)
+    st = s.step(4, stats=True)
+    assert st["diverged"] == 1 and st["steps"] == 10
+    np.testing.assert_array_equal(s.get_f(), good)
+    np.testing.assert_array_equal(s.fields()["omega"], om)
+    ref = fvlbm.Solver(case, precision=FP32, device=0)
+    ref.step(13)
+    s.step(3)
+    np.testing.assert_array_equal(s.get_f(), ref.get_f())
