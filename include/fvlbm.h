@@ -122,7 +122,9 @@ typedef struct {
                                      Step 5 read as "repeat Steps 1-4" per stage); stage J
                                      relaxes with its own tau^(J); the last solve gives
                                      t^{n+1}.  Runs the two-pass kernels; all instances of a
-                                     batch must agree on this bit. */
+                                     batch must agree on this bit;
+                                  8: Menter's production limiter P_k <= 10 beta* omega k, which
+                                     the paper's SST (Sec. 2) does not list. */
 } fvlbm_params;
 
 typedef struct {

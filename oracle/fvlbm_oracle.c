@@ -79,7 +79,7 @@ typedef struct oracle {
     double *dtc;                 /* local time stepping: dt of each cell (NULL: dt everywhere) */
     int variant;                 /* reading variants (bit mask): 1 limiter on the gradient of f,
                                     2 non-orthogonal correction of the SST diffusion, 4 SST
-                                    re-solved before every stage */
+                                    re-solved before every stage, 8 production limiter */
     int sst;
     int scheme;                  /* 0: IMEX Runge-Kutta (Part II); 1: explicit Euler (Part I) */
     double *f;                   /* [nc * Q], cell-major */
@@ -718,6 +718,8 @@ static void sst_update(oracle *o)
                      (1.0 - f1) * (B2 / BSTAR - SW2 * KAPPA * KAPPA / sqrt(BSTAR));
         /* production P / rho = nu_t (2 S_ij S_ij - 2/3 (div u)^2) - 2/3 k div u */
         double pk = o->nut[i] * (2.0 * SS[i] - 2.0 / 3.0 * dv[i] * dv[i]) - 2.0 / 3.0 * o->k[i] * dv[i];
+        /* variant 8: Menter's production limiter P_k <= 10 beta* omega k (not in the paper) */
+        if ((o->variant & 8) && pk > 10.0 * BSTAR * o->om[i] * o->k[i]) pk = 10.0 * BSTAR * o->om[i] * o->k[i];
         /* gamma P / nu_t, with the k div u / nu_t part taken as 0 when nu_t = 0 */
         double pw = gam * (2.0 * SS[i] - 2.0 / 3.0 * dv[i] * dv[i]);
         if (o->nut[i] > 0.0) pw -= 2.0 / 3.0 * gam * o->k[i] * dv[i] / o->nut[i];

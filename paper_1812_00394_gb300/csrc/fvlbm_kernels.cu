@@ -23,6 +23,7 @@
 // (FVLBM_FP32_DEV).  Every map of the step is affine in f with weights summing to one, and
 // the convection of a constant vanishes on closed cells, so the offset w_alpha rho0 drops out.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>  // header-only; ranges cost a check unless a profiler is attached
 
 #include <algorithm>
 #include <cmath>
@@ -72,7 +73,8 @@ struct InstParam {
     double dt, nu, rho0, omega_min;
     int sst;      // 1: k-omega SST instance; 0: laminar (SST kernels skip its tiles)
     int local;    // 1: local time stepping (cell steps in Geo::dtc)
-    int variant;  // reading variants: 1 limiter on grad f, 2 SST non-orthogonal correction
+    int variant;  // reading variants: 1 limiter on grad f, 2 SST non-orthogonal correction,
+                  // 4 SST per stage, 8 production limiter
 };
 
 template <class T>
@@ -971,7 +973,11 @@ __device__ __forceinline__ void sst_cell_update(const InstParam &P, T dt, T ui, 
     const T cw1 = T(kB1 / kBstar - kSw1 * kKappa * kKappa / 0.3);
     const T cw2 = T(kB2 / kBstar - kSw2 * kKappa * kKappa / 0.3);
     const T gam = f1 * cw1 + (T(1) - f1) * cw2;
-    const T pk = nti * (T(2) * SS - T(2.0 / 3.0) * dv * dv) - T(2.0 / 3.0) * ki * dv;
+    T pk = nti * (T(2) * SS - T(2.0 / 3.0) * dv * dv) - T(2.0 / 3.0) * ki * dv;
+    if (NONORTH && (P.variant & 8)) {  // Menter's production limiter (reading variant 8)
+        const T cap = T(10.0 * kBstar) * wi * ki;
+        pk = pk > cap ? cap : pk;
+    }
     T pw = gam * (T(2) * SS - T(2.0 / 3.0) * dv * dv);
     if (nti > T(0)) pw -= T(2.0 / 3.0) * gam * ki * dv / nti;
     const T cross = T(2) * (T(1) - f1) * T(kSw2) / wi * (g[4] * g[6] + g[5] * g[7]);
@@ -1084,8 +1090,9 @@ __global__ void __launch_bounds__(kTile)
 }
 
 // The k / omega update and the new relaxation time (and, on the fused path, f^(1)).
-// NONORTH compiles the non-orthogonal diffusion correction (reading variant 2) in; without it
-// the kernel keeps the register count (and occupancy) of the default reading.
+// NONORTH compiles the SST reading variants in (2: non-orthogonal diffusion correction, 8:
+// production limiter); without them the kernel keeps the register count (and occupancy) of
+// the default reading.
 template <class T, bool COMPACT, bool NONORTH>
 __global__ void __launch_bounds__(kTile)
     k_sst_update(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
@@ -1417,7 +1424,7 @@ struct fvlbm_handle {
     int config = 2;         // 0: fused 256, 1: fused 128, 2: two-pass (see fvlbm_autotune)
     int scheme = 0;         // 0: IMEX Runge-Kutta; 1: explicit Euler (comparison scheme)
     bool limit_f = false;   // an instance uses the limiter variant (two-pass kernels only)
-    bool nonorth = false;   // an instance uses the non-orthogonal SST diffusion correction
+    bool nonorth = false;   // an instance uses an SST reading variant (2 or 8)
     bool per_stage = false; // SST solved before every stage (reading variant 4; two-pass only)
     unsigned long long order_hash = 0;  // checksum of the internal cell order (state blobs)
     int rollback_every = 0;             // watchdog: device copy of the state every N steps
@@ -1557,9 +1564,8 @@ int upload_raw(fvlbm_handle *h, V **dst, const std::vector<V> &src) {
     return FVLBM_OK;
 }
 
-// Launch helper: records events around the launch when profiling.
 template <class F>
-void launch(fvlbm_handle *h, int id, const char *name, F &&fn) {
+void launch_timed(fvlbm_handle *h, int id, const char *name, F &&fn) {
     if (h->profiling) {
         if (static_cast<int>(h->timers.size()) <= id) h->timers.resize(id + 1);
         h->timers[id].name = name;
@@ -1574,6 +1580,21 @@ void launch(fvlbm_handle *h, int id, const char *name, F &&fn) {
         fn();
     }
 }
+
+// Launch helper: an NVTX range named after the kernel around every launch (visible to nsys /
+// ncu range filters), and CUDA events around it when profiling.
+template <class F>
+void launch(fvlbm_handle *h, int id, const char *name, F &&fn) {
+    nvtxRangePushA(name);
+    launch_timed(h, id, name, fn);
+    nvtxRangePop();
+}
+
+// NVTX range for the lifetime of a scope (entry points with several returns).
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+};
 
 enum KernelId {
     K_SST_GRAD, K_SST_UPDATE, K_STAGE1, K_GRAD, K_FLUX1, K_FLUX2, K_FLUX3, K_REDUCE,
@@ -2109,7 +2130,7 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     if (h->scheme != 0 && h->scheme != 1) return FVLBM_ERR_BAD_PARAM;
     for (int q = 0; q < n; ++q) {
         h->limit_f |= (params[q].variant & 1) != 0;
-        h->nonorth |= (params[q].variant & 2) != 0;
+        h->nonorth |= (params[q].variant & (2 | 8)) != 0;
         if (((params[q].variant ^ params[0].variant) & 4) != 0) return FVLBM_ERR_BAD_PARAM;
     }
     h->per_stage = (params[0].variant & 4) != 0;
@@ -2282,6 +2303,7 @@ int fvlbm_create_batch(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs,
 
 int fvlbm_step(fvlbm_handle *h, int n_steps, fvlbm_stats *stats) {
     if (!h || n_steps < 0) return FVLBM_ERR_BAD_PARAM;
+    NvtxScope range("fvlbm_step");
     CK(cudaSetDevice(h->device));
     int remaining = n_steps;
     const bool want_stats = stats != nullptr && n_steps > 0;

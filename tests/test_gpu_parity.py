@@ -445,12 +445,12 @@ VARIANT_CASES = {
 }
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 7])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 7, 8, 15])
 @pytest.mark.parametrize("name", sorted(VARIANT_CASES))
 def test_variant_parity_fp64(name, variant):
     """Reading variants (1: limiter on grad f; 2: non-orthogonal SST diffusion correction;
-    4: SST solved per stage; 3 and 7: combinations) against the oracle's variants, element by
-    element."""
+    4: SST solved per stage; 8: production limiter; 3, 7 and 15: combinations) against the
+    oracle's variants, element by element."""
     case = dataclasses.replace(VARIANT_CASES[name](), variant=variant)
     s = fvlbm.Solver(case, precision=FP64, device=0)
     o = Oracle(case)

@@ -525,3 +525,23 @@ def test_per_stage_sst_variant_orders():
     a.step(5)
     b.step(5)
     assert np.array_equal(a.get_f(), b.get_f())
+
+
+def test_production_limiter_variant_homogeneous_shear():
+    """Variant 8 (Menter's production limiter P_k <= 10 beta* omega k; the paper lists none)
+    and the default production term, in closed form: in plane shear u = S y with uniform k and
+    omega, the interior cells see no convection, diffusion or cross diffusion of k, and
+    P_k = nu_t 2 S_ij S_ij = (k / omega) S^2 (nu_t of t^n = k / omega), so one point-implicit
+    step gives k' = (k + dt P) / (1 + dt beta* omega) with P = k S^2 / omega (default) or
+    min(k S^2 / omega, 10 beta* omega k) (variant)."""
+    S, k0, w0, dt, n = 0.03, 1e-4, 0.01, 0.02, 16
+    m = mg.couette_channel(6, n, U=S, H=1.0)
+    g = Oracle(mg.Case(m, nu=1e-3, dt=dt)).geometry()
+    inner = (g["cy"] > 2.5 / n) & (g["cy"] < 1 - 2.5 / n)
+    for var, P in ((0, k0 * S * S / w0), (8, min(k0 * S * S / w0, 10 * 0.09 * w0 * k0))):
+        case = mg.Case(m, nu=1e-3, dt=dt, sst=True, uref=S, u=S * g["cy"],
+                       k=np.full(m.n_cells, k0), omega=np.full(m.n_cells, w0), variant=var)
+        o = Oracle(case)
+        o.step(1)
+        kn = o.fields()["k"][inner]
+        np.testing.assert_allclose(kn, (k0 + dt * P) / (1 + dt * 0.09 * w0), rtol=1e-12)
