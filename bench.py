@@ -297,8 +297,10 @@ def run_ours(args):
     if rank == 0 and not args.no_oracle_check:
         err = _oracle_errors(cases, fvlbm, dev, stream, torch, nsteps=args.check_steps)
 
-    # end to end through the C ABI with pinned host buffers: set_f, one step, read u, v
-    e2e = _e2e(torch, fvlbm, s32, stream, args, world, dist)
+    # end to end through the C ABI with pinned host buffers: upload f, one step, read u, v;
+    # pipelined (async calls) for the headline, synchronous calls for context
+    e2e = _e2e(torch, fvlbm, s32, stream, args, world, dist, pipelined=True)
+    e2e_sync = _e2e(torch, fvlbm, s32, stream, args, world, dist, pipelined=False)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -338,6 +340,7 @@ def run_ours(args):
                         for k, v in prof.items()},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "e2e_sync": e2e_sync,
             "clocks": results["f32"]["clocks"],
             "clocks_fp64": results["f64"]["clocks"],
             "gpu_launches": lps * args.steps,
@@ -412,43 +415,58 @@ def _oracle_errors(cases, fvlbm, dev, stream, torch, nsteps):
     return out
 
 
-def _e2e(torch, fvlbm, solver, stream, args, world, dist):
-    """Same metric through the public API with host buffers: per step, one fvlbm_set_f of the
-    whole state (all instances, FVLBM_ALL_INSTANCES) from pinned host memory, one fvlbm_step,
-    and one fvlbm_get_fields of u and v back to pinned host memory."""
+def _e2e(torch, fvlbm, solver, stream, args, world, dist, pipelined=True):
+    """Same metric through the public API with host buffers: per step, an upload of the whole
+    state (all instances, FVLBM_ALL_INSTANCES) from pinned host memory, one fvlbm_step, and a
+    read of u and v back to pinned host memory.  pipelined=True uses fvlbm_set_f_async /
+    fvlbm_get_fields_async (transfers on the copy engines overlap the steps, two host buffers
+    per direction, one fvlbm_wait at the end); pipelined=False the synchronous calls."""
     import ctypes as C
     total = fvlbm.fvlbm_info(solver.h, -1)[0]
-    host_f = torch.empty((total, 9), dtype=torch.float64, pin_memory=True).numpy()
-    host_f[:] = fvlbm.fvlbm_get_f(solver.h, -1)
-    u = torch.empty(total, dtype=torch.float64, pin_memory=True).numpy()
-    v = torch.empty(total, dtype=torch.float64, pin_memory=True).numpy()
+    host_f = [torch.empty((total, 9), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+    for hf in host_f:
+        hf[:] = fvlbm.fvlbm_get_f(solver.h, -1)
+    u = [torch.empty(total, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+    v = [torch.empty(total, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
     lib = fvlbm.load()
     k = max(3, min(args.steps // 10, 20))
+    vp = C.c_void_p
 
-    def one_step():
-        rc = lib.fvlbm_set_f(solver.h, -1, host_f.ctypes.data_as(C.c_void_p))
+    def check(rc, what):
         if rc:
-            raise fvlbm.FvlbmError(rc, "fvlbm_set_f")
-        solver.step(1)
-        rc = lib.fvlbm_get_fields(solver.h, -1, None, u.ctypes.data_as(C.c_void_p),
-                                  v.ctypes.data_as(C.c_void_p), None, None, None)
-        if rc:
-            raise fvlbm.FvlbmError(rc, "fvlbm_get_fields")
+            raise fvlbm.FvlbmError(rc, what)
+
+    def one_step(j):
+        b = j % 2
+        if pipelined:
+            check(lib.fvlbm_set_f_async(solver.h, -1, host_f[b].ctypes.data_as(vp)), "fvlbm_set_f_async")
+            solver.step(1)
+            check(lib.fvlbm_get_fields_async(solver.h, -1, None, u[b].ctypes.data_as(vp),
+                                             v[b].ctypes.data_as(vp), None, None, None),
+                  "fvlbm_get_fields_async")
+        else:
+            check(lib.fvlbm_set_f(solver.h, -1, host_f[b].ctypes.data_as(vp)), "fvlbm_set_f")
+            solver.step(1)
+            check(lib.fvlbm_get_fields(solver.h, -1, None, u[b].ctypes.data_as(vp),
+                                       v[b].ctypes.data_as(vp), None, None, None), "fvlbm_get_fields")
     with torch.cuda.stream(stream):
-        one_step()
+        one_step(0)
+        check(lib.fvlbm_wait(solver.h), "fvlbm_wait")
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
-        for _ in range(k):
-            one_step()
+        for j in range(k):
+            one_step(j)
+        check(lib.fvlbm_wait(solver.h), "fvlbm_wait")
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
     if world > 1:
         el = max_over_ranks(torch, dist, world, el, device="cuda")
     return {"value": total * world / (el / k) / 1e6, "unit": UNIT,
             "h2d_bytes_per_step": int(total * 9 * 8), "d2h_bytes_per_step": int(total * 2 * 8),
-            "steps": k, "ms_per_step": el / k * 1e3}
+            "steps": k, "ms_per_step": el / k * 1e3,
+            "io": "pipelined (async calls, copy engines)" if pipelined else "synchronous calls"}
 
 
 def run_profile_mode(args):
@@ -478,7 +496,7 @@ def run_profile_mode(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep", choices=["sweep", "delaunay40k", "cavity64"])

@@ -177,6 +177,25 @@ int fvlbm_set_f(fvlbm_handle *h, int instance, const double *f);
 int fvlbm_get_fields(fvlbm_handle *h, int instance, double *rho, double *u, double *v,
                      double *k, double *omega, double *nut);
 
+/* Pipelined variants of fvlbm_set_f and fvlbm_get_fields that do not synchronise, so that host
+ * transfers overlap the steps (no counterpart in the paper).  Each call stages its data in one
+ * of two device slots per direction (alternating), copies on a transfer stream of the handle
+ * (a copy engine, concurrent with kernels when the host buffers are pinned), and orders itself
+ * after the work already issued on the handle's stream:
+ *   fvlbm_set_f_async: host f -> slot (transfer stream), then the handle's stream waits for
+ *     it and scatters it into the state (work issued later sees the new state);
+ *   fvlbm_get_fields_async: the fields as of the work issued so far are gathered into a slot
+ *     on the handle's stream and copied to the host pointers on the other transfer stream.
+ * The host buffers must stay valid and unchanged (set) or unread (get) until fvlbm_wait(h)
+ * returns.  Any number of calls may be issued: a call whose slot is still in use waits for it
+ * on the device, not on the host (a slot that must grow synchronises once).  fvlbm_wait blocks
+ * until the handle's stream and both transfer streams are idle.  Errors: BAD_PARAM, OOM,
+ * CUDA. */
+int fvlbm_set_f_async(fvlbm_handle *h, int instance, const double *f);
+int fvlbm_get_fields_async(fvlbm_handle *h, int instance, double *rho, double *u, double *v,
+                           double *k, double *omega, double *nut);
+int fvlbm_wait(fvlbm_handle *h);
+
 /* Sizes and the time step actually used (instance -1: totals over all instances, dt = 0). */
 int fvlbm_info(fvlbm_handle *h, int instance, int *n_cells, int *n_bedges, double *dt);
 

@@ -1427,6 +1427,14 @@ struct fvlbm_handle {
     bool nonorth = false;   // an instance uses an SST reading variant (2 or 8)
     bool per_stage = false; // SST solved before every stage (reading variant 4; two-pass only)
     unsigned long long order_hash = 0;  // checksum of the internal cell order (state blobs)
+    struct AsyncIO {
+        bool init = false;
+        cudaStream_t s_in = nullptr, s_out = nullptr;
+        double *d_in[2] = {nullptr, nullptr}, *d_out[2] = {nullptr, nullptr};
+        size_t in_cap[2] = {0, 0}, out_cap[2] = {0, 0};
+        cudaEvent_t in_ready[2], in_free[2], out_ready[2], out_free[2];
+        int in_next = 0, out_next = 0;
+    } aio;
     int rollback_every = 0;             // watchdog: device copy of the state every N steps
     void *rollback = nullptr;           // that copy (state_regions layout)
     long long rollback_step = -1, rollback_last = -1;
@@ -2086,6 +2094,20 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
 }
 
 void free_all(fvlbm_handle *h) {
+    auto &A = h->aio;
+    if (A.init) {
+        cudaStreamSynchronize(A.s_in);
+        cudaStreamSynchronize(A.s_out);
+        for (int k = 0; k < 2; ++k) {
+            if (A.d_in[k]) cudaFree(A.d_in[k]);
+            if (A.d_out[k]) cudaFree(A.d_out[k]);
+            for (cudaEvent_t e : {A.in_ready[k], A.in_free[k], A.out_ready[k], A.out_free[k]})
+                cudaEventDestroy(e);
+        }
+        cudaStreamDestroy(A.s_in);
+        cudaStreamDestroy(A.s_out);
+        A.init = false;
+    }
     for (int k = 0; k < 3; ++k)
         if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
     for (void *p : h->allocs) cudaFree(p);
@@ -2236,6 +2258,81 @@ int perm_offset(const fvlbm_handle *h, int instance) {
     int o = 0;
     for (int q = 0; q < instance; ++q) o += h->inst[q].nc;
     return o;
+}
+
+// Cells addressed by an instance argument (FVLBM_ALL_INSTANCES: all of them).
+size_t io_cells(const fvlbm_handle *h, int instance) {
+    return instance == -1 ? static_cast<size_t>(h->total_nc) : static_cast<size_t>(h->inst[instance].nc);
+}
+
+// f (absolute, input cell order, [cells][9]) from a DEVICE buffer into the state, then f^(1)
+// of the coming step; on the handle's stream.
+void scatter_f_dev(fvlbm_handle *h, int instance, const double *src) {
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        if (instance == -1) {
+            const int n = h->total_nc;
+            k_scatter_f_all<T><<<(n + 255) / 256, 256, 0, h->stream>>>(
+                static_cast<T *>(h->fn), static_cast<T *>(h->mac), h->d_all_map, n, h->np, h->d_tile_inst,
+                h->d_ip, src);
+        } else {
+            const InstInfo &I = h->inst[instance];
+            k_scatter_f<T><<<(I.nc + 255) / 256, 256, 0, h->stream>>>(
+                static_cast<T *>(h->fn), static_cast<T *>(h->mac), h->d_perm + perm_offset(h, instance),
+                I.cell_off, I.nc, I.rho0, h->np, src);
+        }
+        relax_all<T>(h);
+    });
+}
+
+// rho, u, v, k, omega, nu_t (input cell order, field-major [6][cells]) into a DEVICE buffer.
+void gather_fields_dev(fvlbm_handle *h, int instance, double *dst) {
+    const int c = h->turb;
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        if (instance == -1) {
+            const int n = h->total_nc;
+            k_gather_fields_all<T><<<(n + 255) / 256, 256, 0, h->stream>>>(
+                static_cast<T *>(h->mac), static_cast<T *>(h->kk[c]), static_cast<T *>(h->ww[c]),
+                static_cast<T *>(h->nut[c]), h->d_all_map, n, h->np, dst);
+        } else {
+            const InstInfo &I = h->inst[instance];
+            k_gather_fields<T><<<(I.nc + 255) / 256, 256, 0, h->stream>>>(
+                static_cast<T *>(h->mac), static_cast<T *>(h->kk[c]), static_cast<T *>(h->ww[c]),
+                static_cast<T *>(h->nut[c]), h->d_perm + perm_offset(h, instance), I.cell_off, I.nc, h->np,
+                dst);
+        }
+    });
+}
+
+// Pipelined host I/O: two staging slots per direction and two transfer streams, so that
+// host-device copies run on the copy engines while the compute stream steps.
+int async_init(fvlbm_handle *h) {
+    auto &A = h->aio;
+    if (A.init) return FVLBM_OK;
+    CK(cudaStreamCreateWithFlags(&A.s_in, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&A.s_out, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k)
+        for (cudaEvent_t *e : {&A.in_ready[k], &A.in_free[k], &A.out_ready[k], &A.out_free[k]}) {
+            CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+            CK(cudaEventRecord(*e, h->stream));
+        }
+    A.init = true;
+    return FVLBM_OK;
+}
+
+int async_slot(fvlbm_handle *h, double **buf, size_t *cap, size_t bytes) {
+    if (*cap >= bytes) return FVLBM_OK;
+    // growing a slot: let everything in flight finish first
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaStreamSynchronize(h->aio.s_in));
+    CK(cudaStreamSynchronize(h->aio.s_out));
+    if (*buf) CK(cudaFree(*buf));
+    *buf = nullptr;
+    *cap = 0;
+    CK(cudaMalloc(reinterpret_cast<void **>(buf), bytes));
+    *cap = bytes;
+    return FVLBM_OK;
 }
 
 // Wall force and coefficients of one instance; dout (may be NULL) receives their derivatives
@@ -2427,35 +2524,11 @@ int fvlbm_get_f(fvlbm_handle *h, int instance, double *f) {
 int fvlbm_set_f(fvlbm_handle *h, int instance, const double *f) {
     if (!h || instance < -1 || instance >= h->ninst || !f) return FVLBM_ERR_BAD_PARAM;
     CK(cudaSetDevice(h->device));
-    if (instance == -1) {
-        const int n = h->total_nc;
-        int rc = io_buffer(h, sizeof(double) * kQ * n);
-        if (rc) return rc;
-        CK(cudaMemcpyAsync(h->d_io, f, sizeof(double) * kQ * n, cudaMemcpyHostToDevice, h->stream));
-        const int nb = (n + 255) / 256;
-        dispatch(h->precision, [&](auto z_) {
-            using T = decltype(z_);
-            k_scatter_f_all<T><<<nb, 256, 0, h->stream>>>(static_cast<T *>(h->fn),
-                                                               static_cast<T *>(h->mac), h->d_all_map, n,
-                                                               h->np, h->d_tile_inst, h->d_ip, h->d_io);
-            relax_all<T>(h);
-        });
-        CK(cudaGetLastError());
-        CK(cudaStreamSynchronize(h->stream));
-        return FVLBM_OK;
-    }
-    const InstInfo &I = h->inst[instance];
-    int rc = io_buffer(h, sizeof(double) * kQ * I.nc);
+    const size_t n = io_cells(h, instance);
+    int rc = io_buffer(h, sizeof(double) * kQ * n);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(h->d_io, f, sizeof(double) * kQ * I.nc, cudaMemcpyHostToDevice, h->stream));
-    const int po = perm_offset(h, instance);
-    const int nb = (I.nc + 255) / 256;
-    dispatch(h->precision, [&](auto z_) {
-        using T = decltype(z_);
-        k_scatter_f<T><<<nb, 256, 0, h->stream>>>(static_cast<T *>(h->fn), static_cast<T *>(h->mac),
-                                                       h->d_perm + po, I.cell_off, I.nc, I.rho0, h->np, h->d_io);
-        relax_all<T>(h);
-    });
+    CK(cudaMemcpyAsync(h->d_io, f, sizeof(double) * kQ * n, cudaMemcpyHostToDevice, h->stream));
+    scatter_f_dev(h, instance, h->d_io);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     return FVLBM_OK;
@@ -2465,46 +2538,72 @@ int fvlbm_get_fields(fvlbm_handle *h, int instance, double *rho, double *u, doub
                      double *omega, double *nut) {
     if (!h || instance < -1 || instance >= h->ninst) return FVLBM_ERR_BAD_PARAM;
     CK(cudaSetDevice(h->device));
-    if (instance == -1) {
-        const size_t n = h->total_nc;
-        int rc = io_buffer(h, sizeof(double) * 6 * n);
-        if (rc) return rc;
-        const int nb = static_cast<int>((n + 255) / 256);
-        const int c = h->turb;
-        dispatch(h->precision, [&](auto z_) {
-            using T = decltype(z_);
-            k_gather_fields_all<T><<<nb, 256, 0, h->stream>>>(
-                static_cast<T *>(h->mac), static_cast<T *>(h->kk[c]), static_cast<T *>(h->ww[c]),
-                static_cast<T *>(h->nut[c]), h->d_all_map, static_cast<int>(n), h->np, h->d_io);
-        });
-        CK(cudaGetLastError());
-        double *dst[6] = {rho, u, v, k, omega, nut};
-        for (int q = 0; q < 6; ++q)
-            if (dst[q])
-                CK(cudaMemcpyAsync(dst[q], h->d_io + q * n, sizeof(double) * n, cudaMemcpyDeviceToHost,
-                                   h->stream));
-        CK(cudaStreamSynchronize(h->stream));
-        return FVLBM_OK;
-    }
-    const InstInfo &I = h->inst[instance];
-    const size_t n = I.nc;
+    const size_t n = io_cells(h, instance);
     int rc = io_buffer(h, sizeof(double) * 6 * n);
     if (rc) return rc;
-    const int po = perm_offset(h, instance);
-    const int nb = (I.nc + 255) / 256;
-    const int c = h->turb;
-    dispatch(h->precision, [&](auto z_) {
-        using T = decltype(z_);
-        k_gather_fields<T><<<nb, 256, 0, h->stream>>>(
-            static_cast<T *>(h->mac), static_cast<T *>(h->kk[c]), static_cast<T *>(h->ww[c]),
-            static_cast<T *>(h->nut[c]), h->d_perm + po, I.cell_off, I.nc, h->np, h->d_io);
-    });
+    gather_fields_dev(h, instance, h->d_io);
     CK(cudaGetLastError());
     double *dst[6] = {rho, u, v, k, omega, nut};
     for (int q = 0; q < 6; ++q)
         if (dst[q])
             CK(cudaMemcpyAsync(dst[q], h->d_io + q * n, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    return FVLBM_OK;
+}
+
+int fvlbm_set_f_async(fvlbm_handle *h, int instance, const double *f) {
+    if (!h || instance < -1 || instance >= h->ninst || !f) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    int rc = async_init(h);
+    if (rc) return rc;
+    auto &A = h->aio;
+    const int slot = A.in_next;
+    A.in_next ^= 1;
+    const size_t bytes = sizeof(double) * kQ * io_cells(h, instance);
+    if ((rc = async_slot(h, &A.d_in[slot], &A.in_cap[slot], bytes))) return rc;
+    CK(cudaStreamWaitEvent(A.s_in, A.in_free[slot], 0));  // the slot's last scatter has run
+    CK(cudaMemcpyAsync(A.d_in[slot], f, bytes, cudaMemcpyHostToDevice, A.s_in));
+    CK(cudaEventRecord(A.in_ready[slot], A.s_in));
+    CK(cudaStreamWaitEvent(h->stream, A.in_ready[slot], 0));
+    scatter_f_dev(h, instance, A.d_in[slot]);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(A.in_free[slot], h->stream));
+    return FVLBM_OK;
+}
+
+int fvlbm_get_fields_async(fvlbm_handle *h, int instance, double *rho, double *u, double *v, double *k,
+                           double *omega, double *nut) {
+    if (!h || instance < -1 || instance >= h->ninst) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    int rc = async_init(h);
+    if (rc) return rc;
+    auto &A = h->aio;
+    const int slot = A.out_next;
+    A.out_next ^= 1;
+    const size_t n = io_cells(h, instance);
+    if ((rc = async_slot(h, &A.d_out[slot], &A.out_cap[slot], sizeof(double) * 6 * n))) return rc;
+    CK(cudaStreamWaitEvent(h->stream, A.out_free[slot], 0));  // the slot's last copy-out is done
+    gather_fields_dev(h, instance, A.d_out[slot]);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(A.out_ready[slot], h->stream));
+    CK(cudaStreamWaitEvent(A.s_out, A.out_ready[slot], 0));
+    double *dst[6] = {rho, u, v, k, omega, nut};
+    for (int q = 0; q < 6; ++q)
+        if (dst[q])
+            CK(cudaMemcpyAsync(dst[q], A.d_out[slot] + q * n, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                               A.s_out));
+    CK(cudaEventRecord(A.out_free[slot], A.s_out));
+    return FVLBM_OK;
+}
+
+int fvlbm_wait(fvlbm_handle *h) {
+    if (!h) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->aio.init) {
+        CK(cudaStreamSynchronize(h->aio.s_in));
+        CK(cudaStreamSynchronize(h->aio.s_out));
+    }
     return FVLBM_OK;
 }
 

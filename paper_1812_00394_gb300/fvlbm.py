@@ -62,7 +62,8 @@ EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "
            "fvlbm_profile_kernels", "fvlbm_autotune", "fvlbm_destroy", "fvlbm_strerror",
            "fvlbm_stats_reduce_static", "fvlbm_tangent_seed", "fvlbm_tangent_seed_nodes",
            "fvlbm_get_f_tangent", "fvlbm_forces_tangent", "fvlbm_state_bytes", "fvlbm_save_state",
-           "fvlbm_load_state", "fvlbm_set_rollback"]
+           "fvlbm_load_state", "fvlbm_set_rollback", "fvlbm_set_f_async", "fvlbm_get_fields_async",
+           "fvlbm_wait"]
 
 _lib = None
 
@@ -95,6 +96,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_footprint.argtypes = [vp, P(C.c_longlong), P(i)]
     lib.fvlbm_profile_kernels.argtypes = [vp, i, i, vp, vp, vp]
     lib.fvlbm_autotune.argtypes = [vp, i, P(i), vp]
+    lib.fvlbm_set_f_async.argtypes = [vp, i, vp]
+    lib.fvlbm_get_fields_async.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
+    lib.fvlbm_wait.argtypes = [vp]
     lib.fvlbm_state_bytes.argtypes = [vp, P(C.c_longlong)]
     lib.fvlbm_save_state.argtypes = [vp, vp, C.c_longlong]
     lib.fvlbm_load_state.argtypes = [vp, vp, C.c_longlong]
