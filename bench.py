@@ -299,7 +299,8 @@ def run_ours(args):
 
     # end to end through the C ABI with pinned host buffers: upload f, one step, read u, v;
     # pipelined (async calls) for the headline, synchronous calls for context
-    e2e = _e2e(torch, fvlbm, s32, stream, args, world, dist, pipelined=True)
+    e2e = _e2e(torch, fvlbm, s32, stream, args, world, dist, pipelined=True, f32_io=True)
+    e2e_f64 = _e2e(torch, fvlbm, s32, stream, args, world, dist, pipelined=True)
     e2e_sync = _e2e(torch, fvlbm, s32, stream, args, world, dist, pipelined=False)
 
     cpu = None
@@ -340,6 +341,7 @@ def run_ours(args):
                         for k, v in prof.items()},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "e2e_f64_io": e2e_f64,
             "e2e_sync": e2e_sync,
             "clocks": results["f32"]["clocks"],
             "clocks_fp64": results["f64"]["clocks"],
@@ -415,22 +417,30 @@ def _oracle_errors(cases, fvlbm, dev, stream, torch, nsteps):
     return out
 
 
-def _e2e(torch, fvlbm, solver, stream, args, world, dist, pipelined=True):
+def _e2e(torch, fvlbm, solver, stream, args, world, dist, pipelined=True, f32_io=False):
     """Same metric through the public API with host buffers: per step, an upload of the whole
     state (all instances, FVLBM_ALL_INSTANCES) from pinned host memory, one fvlbm_step, and a
     read of u and v back to pinned host memory.  pipelined=True uses fvlbm_set_f_async /
     fvlbm_get_fields_async (transfers on the copy engines overlap the steps, two host buffers
-    per direction, one fvlbm_wait at the end); pipelined=False the synchronous calls."""
+    per direction, one fvlbm_wait at the end); pipelined=False the synchronous calls.
+    f32_io=True uploads the state in the FP32 deviation format of the FP32 path
+    (fvlbm_set_fdev_f32_async: f - w rho0 as float, half the bytes of double f)."""
     import ctypes as C
     total = fvlbm.fvlbm_info(solver.h, -1)[0]
-    host_f = [torch.empty((total, 9), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
-    for hf in host_f:
-        hf[:] = fvlbm.fvlbm_get_f(solver.h, -1)
+    lib = fvlbm.load()
+    vp = C.c_void_p
+    if f32_io:
+        host_f = [torch.empty((total, 9), dtype=torch.float32, pin_memory=True).numpy() for _ in range(2)]
+        for hf in host_f:
+            if lib.fvlbm_get_fdev_f32(solver.h, -1, hf.ctypes.data_as(vp)):
+                raise RuntimeError("fvlbm_get_fdev_f32 failed")
+    else:
+        host_f = [torch.empty((total, 9), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+        for hf in host_f:
+            hf[:] = fvlbm.fvlbm_get_f(solver.h, -1)
     u = [torch.empty(total, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
     v = [torch.empty(total, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
-    lib = fvlbm.load()
     k = max(3, min(args.steps // 10, 20))
-    vp = C.c_void_p
 
     def check(rc, what):
         if rc:
@@ -439,7 +449,11 @@ def _e2e(torch, fvlbm, solver, stream, args, world, dist, pipelined=True):
     def one_step(j):
         b = j % 2
         if pipelined:
-            check(lib.fvlbm_set_f_async(solver.h, -1, host_f[b].ctypes.data_as(vp)), "fvlbm_set_f_async")
+            if f32_io:
+                check(lib.fvlbm_set_fdev_f32_async(solver.h, -1, host_f[b].ctypes.data_as(vp)),
+                      "fvlbm_set_fdev_f32_async")
+            else:
+                check(lib.fvlbm_set_f_async(solver.h, -1, host_f[b].ctypes.data_as(vp)), "fvlbm_set_f_async")
             solver.step(1)
             check(lib.fvlbm_get_fields_async(solver.h, -1, None, u[b].ctypes.data_as(vp),
                                              v[b].ctypes.data_as(vp), None, None, None),
@@ -463,10 +477,12 @@ def _e2e(torch, fvlbm, solver, stream, args, world, dist, pipelined=True):
         el = time.perf_counter() - t0
     if world > 1:
         el = max_over_ranks(torch, dist, world, el, device="cuda")
+    io = "pipelined (async calls, copy engines)" if pipelined else "synchronous calls"
+    io += "; state uploaded as FP32 deviations f - w rho0" if f32_io else "; state uploaded as FP64 f"
     return {"value": total * world / (el / k) / 1e6, "unit": UNIT,
-            "h2d_bytes_per_step": int(total * 9 * 8), "d2h_bytes_per_step": int(total * 2 * 8),
-            "steps": k, "ms_per_step": el / k * 1e3,
-            "io": "pipelined (async calls, copy engines)" if pipelined else "synchronous calls"}
+            "h2d_bytes_per_step": int(total * 9 * (4 if f32_io else 8)),
+            "d2h_bytes_per_step": int(total * 2 * 8),
+            "steps": k, "ms_per_step": el / k * 1e3, "io": io}
 
 
 def run_profile_mode(args):

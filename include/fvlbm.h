@@ -196,6 +196,14 @@ int fvlbm_get_fields_async(fvlbm_handle *h, int instance, double *rho, double *u
                            double *k, double *omega, double *nut);
 int fvlbm_wait(fvlbm_handle *h);
 
+/* FP32 deviation I/O: the state as f - w_alpha rho0 in float, cell-major [cells][9] in input
+ * order (instance -1: all instances concatenated).  For FVLBM_FP32_DEV handles this is their
+ * storage format, so values pass unchanged, at half the bytes of the double interface; other
+ * precisions convert.  fvlbm_get_fdev_f32 synchronises; fvlbm_set_fdev_f32_async is pipelined
+ * like fvlbm_set_f_async (same slots, streams and fvlbm_wait). */
+int fvlbm_get_fdev_f32(fvlbm_handle *h, int instance, float *fdev);
+int fvlbm_set_fdev_f32_async(fvlbm_handle *h, int instance, const float *fdev);
+
 /* Sizes and the time step actually used (instance -1: totals over all instances, dt = 0). */
 int fvlbm_info(fvlbm_handle *h, int instance, int *n_cells, int *n_bedges, double *dt);
 

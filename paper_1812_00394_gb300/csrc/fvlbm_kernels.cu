@@ -1319,6 +1319,37 @@ __global__ void k_scatter_f_all(T *__restrict__ f, T *__restrict__ mac, const in
     mac[2 * np + i] = v;
 }
 
+// FP32 deviation I/O: positions j < n of the concatenated input order (map gives the internal
+// cell); values are f - w_alpha rho0 in float, [n][9].
+template <class T>
+__global__ void k_scatter_fdev32(T *__restrict__ f, T *__restrict__ mac, const int *__restrict__ map,
+                                 int n, size_t np, const int *__restrict__ tile_inst,
+                                 const InstParam *__restrict__ ip, const float *__restrict__ in) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int i = map[j];
+    const T rho0 = T(ip[tile_inst[i / kTile]].rho0);
+    T d[kQ];
+    for (int a = 0; a < kQ; ++a) {
+        d[a] = T(double(in[static_cast<size_t>(j) * kQ + a]));
+        f[a * np + i] = d[a];
+    }
+    T dr, r, u, v;
+    moments(d, rho0, dr, r, u, v);
+    mac[i] = r;
+    mac[np + i] = u;
+    mac[2 * np + i] = v;
+}
+
+template <class T>
+__global__ void k_gather_fdev32(const T *__restrict__ f, const int *__restrict__ map, int n, size_t np,
+                                float *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int i = map[j];
+    for (int a = 0; a < kQ; ++a) out[static_cast<size_t>(j) * kQ + a] = float(double(f[a * np + i]));
+}
+
 template <class T>
 __global__ void k_gather_fields_all(const T *__restrict__ mac, const T *__restrict__ kk,
                                     const T *__restrict__ ww, const T *__restrict__ nut,
@@ -2593,6 +2624,55 @@ int fvlbm_get_fields_async(fvlbm_handle *h, int instance, double *rho, double *u
             CK(cudaMemcpyAsync(dst[q], A.d_out[slot] + q * n, sizeof(double) * n, cudaMemcpyDeviceToHost,
                                A.s_out));
     CK(cudaEventRecord(A.out_free[slot], A.s_out));
+    return FVLBM_OK;
+}
+
+int fvlbm_get_fdev_f32(fvlbm_handle *h, int instance, float *fdev) {
+    if (!h || instance < -1 || instance >= h->ninst || !fdev) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    const int n = static_cast<int>(io_cells(h, instance));
+    const int po = instance == -1 ? 0 : perm_offset(h, instance);
+    int rc = io_buffer(h, sizeof(float) * kQ * static_cast<size_t>(n));
+    if (rc) return rc;
+    float *buf = reinterpret_cast<float *>(h->d_io);
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        k_gather_fdev32<T><<<(n + 255) / 256, 256, 0, h->stream>>>(static_cast<const T *>(h->fn),
+                                                                   h->d_all_map + po, n, h->np, buf);
+    });
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(fdev, buf, sizeof(float) * kQ * static_cast<size_t>(n), cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FVLBM_OK;
+}
+
+int fvlbm_set_fdev_f32_async(fvlbm_handle *h, int instance, const float *fdev) {
+    if (!h || instance < -1 || instance >= h->ninst || !fdev) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    int rc = async_init(h);
+    if (rc) return rc;
+    auto &A = h->aio;
+    const int slot = A.in_next;
+    A.in_next ^= 1;
+    const int n = static_cast<int>(io_cells(h, instance));
+    const int po = instance == -1 ? 0 : perm_offset(h, instance);
+    const size_t bytes = sizeof(float) * kQ * static_cast<size_t>(n);
+    if ((rc = async_slot(h, &A.d_in[slot], &A.in_cap[slot], bytes))) return rc;
+    float *buf = reinterpret_cast<float *>(A.d_in[slot]);
+    CK(cudaStreamWaitEvent(A.s_in, A.in_free[slot], 0));
+    CK(cudaMemcpyAsync(buf, fdev, bytes, cudaMemcpyHostToDevice, A.s_in));
+    CK(cudaEventRecord(A.in_ready[slot], A.s_in));
+    CK(cudaStreamWaitEvent(h->stream, A.in_ready[slot], 0));
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        k_scatter_fdev32<T><<<(n + 255) / 256, 256, 0, h->stream>>>(
+            static_cast<T *>(h->fn), static_cast<T *>(h->mac), h->d_all_map + po, n, h->np, h->d_tile_inst,
+            h->d_ip, buf);
+        relax_all<T>(h);
+    });
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(A.in_free[slot], h->stream));
     return FVLBM_OK;
 }
 

@@ -63,7 +63,7 @@ EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "
            "fvlbm_stats_reduce_static", "fvlbm_tangent_seed", "fvlbm_tangent_seed_nodes",
            "fvlbm_get_f_tangent", "fvlbm_forces_tangent", "fvlbm_state_bytes", "fvlbm_save_state",
            "fvlbm_load_state", "fvlbm_set_rollback", "fvlbm_set_f_async", "fvlbm_get_fields_async",
-           "fvlbm_wait"]
+           "fvlbm_wait", "fvlbm_get_fdev_f32", "fvlbm_set_fdev_f32_async"]
 
 _lib = None
 
@@ -99,6 +99,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_set_f_async.argtypes = [vp, i, vp]
     lib.fvlbm_get_fields_async.argtypes = [vp, i, vp, vp, vp, vp, vp, vp]
     lib.fvlbm_wait.argtypes = [vp]
+    lib.fvlbm_get_fdev_f32.argtypes = [vp, i, vp]
+    lib.fvlbm_set_fdev_f32_async.argtypes = [vp, i, vp]
     lib.fvlbm_state_bytes.argtypes = [vp, P(C.c_longlong)]
     lib.fvlbm_save_state.argtypes = [vp, vp, C.c_longlong]
     lib.fvlbm_load_state.argtypes = [vp, vp, C.c_longlong]

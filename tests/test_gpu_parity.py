@@ -589,3 +589,31 @@ def test_async_io_pipeline_matches_synchronous_calls():
     for j in range(5):
         np.testing.assert_array_equal(outs[j][0], want[j][0])
         np.testing.assert_array_equal(outs[j][1], want[j][1])
+
+
+def test_fp32_deviation_io_roundtrip_and_pipeline():
+    """The FP32 deviation format is the FP32 path's storage: get -> async set -> get is the
+    identity bit for bit, and a step from it matches a step from the double interface."""
+    cases = [mg.naca0012_cmesh(n_target=3000, alpha_deg=3.0), mg.cavity_quad(20, re=400.0)]
+    s = fvlbm.Solver(cases, precision=FP32, device=0)
+    s.step(7)
+    lib = fvlbm.load()
+    import ctypes as C
+    vp = C.c_void_p
+    n = fvlbm.fvlbm_info(s.h, -1)[0]
+    d0 = np.empty((n, 9), np.float32)
+    assert lib.fvlbm_get_fdev_f32(s.h, -1, d0.ctypes.data_as(vp)) == 0
+    f_before = fvlbm.fvlbm_get_f(s.h, -1)
+    s.step(3)
+    assert lib.fvlbm_set_fdev_f32_async(s.h, -1, d0.ctypes.data_as(vp)) == 0
+    assert lib.fvlbm_wait(s.h) == 0
+    d1 = np.empty_like(d0)
+    assert lib.fvlbm_get_fdev_f32(s.h, -1, d1.ctypes.data_as(vp)) == 0
+    np.testing.assert_array_equal(d0, d1)
+    np.testing.assert_array_equal(fvlbm.fvlbm_get_f(s.h, -1), f_before)
+    # one instance alone, and the deviation values against the double interface
+    d2 = np.empty((s.cells[1], 9), np.float32)
+    assert lib.fvlbm_get_fdev_f32(s.h, 1, d2.ctypes.data_as(vp)) == 0
+    np.testing.assert_array_equal(d2, d0[s.cells[0]:])
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    np.testing.assert_allclose(d2.astype(np.float64) + w * 1.0, s.get_f(1), rtol=0, atol=1e-15)
