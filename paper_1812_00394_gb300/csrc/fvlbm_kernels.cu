@@ -1206,44 +1206,6 @@ __global__ void k_gather_f(const T *__restrict__ f, const int *__restrict__ perm
     }
 }
 
-template <class T>
-__global__ void k_scatter_f(T *__restrict__ f, T *__restrict__ mac, const int *__restrict__ perm,
-                            int off, int nc, double rho0, size_t np,
-                            const double *__restrict__ in) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nc) return;
-    const int src = perm[k];
-    T d[kQ];
-    for (int a = 0; a < kQ; ++a) {
-        const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-        d[a] = T(in[static_cast<size_t>(src) * kQ + a] - wa * rho0);
-        f[a * np + off + k] = d[a];
-    }
-    T dr, r, u, v;
-    moments(d, T(rho0), dr, r, u, v);
-    mac[off + k] = r;
-    mac[np + off + k] = u;
-    mac[2 * np + off + k] = v;
-}
-
-// fields[c][perm[k]] for c = rho, u, v, k, omega, nu_t
-template <class T>
-__global__ void k_gather_fields(const T *__restrict__ mac, const T *__restrict__ kk,
-                                const T *__restrict__ ww, const T *__restrict__ nut,
-                                const int *__restrict__ perm, int off, int nc, size_t np,
-                                double *__restrict__ out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nc) return;
-    const int dst = perm[k];
-    const size_t n = nc;
-    out[0 * n + dst] = double(mac[off + k]);
-    out[1 * n + dst] = double(mac[np + off + k]);
-    out[2 * n + dst] = double(mac[2 * np + off + k]);
-    out[3 * n + dst] = double(kk[off + k]);
-    out[4 * n + dst] = double(ww[off + k]);
-    out[5 * n + dst] = double(nut[off + k]);
-}
-
 // Per wall face momentum flux and Cp (FP64): out[5][nb_inst] = fx, fy, cp, dfx/dp, dfy/dp (the
 // last two are 0 except for the tangent type).
 template <class T>
@@ -1298,47 +1260,54 @@ __global__ void k_gather_f_all(const T *__restrict__ f, const int *__restrict__ 
     }
 }
 
-template <class T>
-__global__ void k_scatter_f_all(T *__restrict__ f, T *__restrict__ mac, const int *__restrict__ map,
-                                int total, size_t np, const int *__restrict__ tile_inst,
-                                const InstParam *__restrict__ ip, const double *__restrict__ in) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= total) return;
-    const int i = map[j];
-    const double rho0 = ip[tile_inst[i / kTile]].rho0;
-    T d[kQ];
-    for (int a = 0; a < kQ; ++a) {
-        const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-        d[a] = T(in[static_cast<size_t>(j) * kQ + a] - wa * rho0);
-        f[a * np + i] = d[a];
-    }
-    T dr, r, u, v;
-    moments(d, T(rho0), dr, r, u, v);
-    mac[i] = r;
-    mac[np + i] = u;
-    mac[2 * np + i] = v;
-}
-
-// FP32 deviation I/O: positions j < n of the concatenated input order (map gives the internal
-// cell); values are f - w_alpha rho0 in float, [n][9].
-template <class T>
-__global__ void k_scatter_fdev32(T *__restrict__ f, T *__restrict__ mac, const int *__restrict__ map,
-                                 int n, size_t np, const int *__restrict__ tile_inst,
-                                 const InstParam *__restrict__ ip, const float *__restrict__ in) {
+// State input: positions j < n of the concatenated input order (map gives the internal cell).
+// IN = double: absolute f; IN = float: the FP32 deviation f - w_alpha rho0.  Writes f^n, the
+// macros and f^(1) of the coming step (relaxed like k_stage1, for the fused stages).
+template <class T, class IN>
+__global__ void k_scatter_state(T *__restrict__ f, T *__restrict__ mac, T *__restrict__ frel,
+                                const T *__restrict__ tau, const int *__restrict__ map, int n,
+                                Geo<T> G, const IN *__restrict__ in) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int i = map[j];
-    const T rho0 = T(ip[tile_inst[i / kTile]].rho0);
+    const size_t np = G.np;
+    const InstParam P = G.ip[G.tile_inst[i / kTile]];
     T d[kQ];
     for (int a = 0; a < kQ; ++a) {
-        d[a] = T(double(in[static_cast<size_t>(j) * kQ + a]));
+        const double x = double(in[static_cast<size_t>(j) * kQ + a]);
+        if (sizeof(IN) == sizeof(double)) {
+            const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+            d[a] = T(x - wa * P.rho0);
+        } else {
+            d[a] = T(x);
+        }
         f[a * np + i] = d[a];
     }
     T dr, r, u, v;
-    moments(d, rho0, dr, r, u, v);
+    moments(d, T(P.rho0), dr, r, u, v);
     mac[i] = r;
     mac[np + i] = u;
     mac[2 * np + i] = v;
+    relax9(d, T(P.rho0), cell_dt(G, P, i), tau[i]);
+    store9(frel, np, i, d);
+}
+
+// Output fields[q][j] for the fields q (rho, u, v, k, omega, nu_t) selected by mask bit q.
+template <class T>
+__global__ void k_gather_fields_map(const T *__restrict__ mac, const T *__restrict__ kk,
+                                    const T *__restrict__ ww, const T *__restrict__ nut,
+                                    const int *__restrict__ map, int n, size_t np, unsigned mask,
+                                    double *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int i = map[j];
+    const size_t m = n;
+    if (mask & 1u) out[0 * m + j] = double(mac[i]);
+    if (mask & 2u) out[1 * m + j] = double(mac[np + i]);
+    if (mask & 4u) out[2 * m + j] = double(mac[2 * np + i]);
+    if (mask & 8u) out[3 * m + j] = double(kk[i]);
+    if (mask & 16u) out[4 * m + j] = double(ww[i]);
+    if (mask & 32u) out[5 * m + j] = double(nut[i]);
 }
 
 template <class T>
@@ -1348,23 +1317,6 @@ __global__ void k_gather_fdev32(const T *__restrict__ f, const int *__restrict__
     if (j >= n) return;
     const int i = map[j];
     for (int a = 0; a < kQ; ++a) out[static_cast<size_t>(j) * kQ + a] = float(double(f[a * np + i]));
-}
-
-template <class T>
-__global__ void k_gather_fields_all(const T *__restrict__ mac, const T *__restrict__ kk,
-                                    const T *__restrict__ ww, const T *__restrict__ nut,
-                                    const int *__restrict__ map, int total, size_t np,
-                                    double *__restrict__ out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= total) return;
-    const int i = map[j];
-    const size_t n = total;
-    out[0 * n + j] = double(mac[i]);
-    out[1 * n + j] = double(mac[np + i]);
-    out[2 * n + j] = double(mac[2 * np + i]);
-    out[3 * n + j] = double(kk[i]);
-    out[4 * n + j] = double(ww[i]);
-    out[5 * n + j] = double(nut[i]);
 }
 
 // Tangent seed: df/dp of instance cells (off + k) from in[perm[k] * 9 + a]; the macros are
@@ -2296,44 +2248,39 @@ size_t io_cells(const fvlbm_handle *h, int instance) {
     return instance == -1 ? static_cast<size_t>(h->total_nc) : static_cast<size_t>(h->inst[instance].nc);
 }
 
-// f (absolute, input cell order, [cells][9]) from a DEVICE buffer into the state, then f^(1)
-// of the coming step; on the handle's stream.
-void scatter_f_dev(fvlbm_handle *h, int instance, const double *src) {
+// The state from a DEVICE buffer (input cell order, [cells][9]; IN = double: absolute f,
+// float: FP32 deviations) into f^n, the macros and f^(1) of the coming step; handle's stream.
+template <class IN>
+void scatter_state_dev(fvlbm_handle *h, int instance, const IN *src) {
+    const int n = static_cast<int>(io_cells(h, instance));
+    const int po = instance == -1 ? 0 : perm_offset(h, instance);
     dispatch(h->precision, [&](auto z_) {
         using T = decltype(z_);
-        if (instance == -1) {
-            const int n = h->total_nc;
-            k_scatter_f_all<T><<<(n + 255) / 256, 256, 0, h->stream>>>(
-                static_cast<T *>(h->fn), static_cast<T *>(h->mac), h->d_all_map, n, h->np, h->d_tile_inst,
-                h->d_ip, src);
-        } else {
-            const InstInfo &I = h->inst[instance];
-            k_scatter_f<T><<<(I.nc + 255) / 256, 256, 0, h->stream>>>(
-                static_cast<T *>(h->fn), static_cast<T *>(h->mac), h->d_perm + perm_offset(h, instance),
-                I.cell_off, I.nc, I.rho0, h->np, src);
-        }
-        relax_all<T>(h);
+        k_scatter_state<T, IN><<<(n + 255) / 256, 256, 0, h->stream>>>(
+            static_cast<T *>(h->fn), static_cast<T *>(h->mac), static_cast<T *>(h->frel),
+            static_cast<const T *>(h->tau), h->d_all_map + po, n, geo_of<T>(h), src);
     });
 }
 
-// rho, u, v, k, omega, nu_t (input cell order, field-major [6][cells]) into a DEVICE buffer.
-void gather_fields_dev(fvlbm_handle *h, int instance, double *dst) {
+// Selected fields (mask bits: rho, u, v, k, omega, nu_t) into a DEVICE buffer, field-major
+// [6][cells] in input cell order.
+void gather_fields_dev(fvlbm_handle *h, int instance, unsigned mask, double *dst) {
+    const int n = static_cast<int>(io_cells(h, instance));
+    const int po = instance == -1 ? 0 : perm_offset(h, instance);
     const int c = h->turb;
     dispatch(h->precision, [&](auto z_) {
         using T = decltype(z_);
-        if (instance == -1) {
-            const int n = h->total_nc;
-            k_gather_fields_all<T><<<(n + 255) / 256, 256, 0, h->stream>>>(
-                static_cast<T *>(h->mac), static_cast<T *>(h->kk[c]), static_cast<T *>(h->ww[c]),
-                static_cast<T *>(h->nut[c]), h->d_all_map, n, h->np, dst);
-        } else {
-            const InstInfo &I = h->inst[instance];
-            k_gather_fields<T><<<(I.nc + 255) / 256, 256, 0, h->stream>>>(
-                static_cast<T *>(h->mac), static_cast<T *>(h->kk[c]), static_cast<T *>(h->ww[c]),
-                static_cast<T *>(h->nut[c]), h->d_perm + perm_offset(h, instance), I.cell_off, I.nc, h->np,
-                dst);
-        }
+        k_gather_fields_map<T><<<(n + 255) / 256, 256, 0, h->stream>>>(
+            static_cast<T *>(h->mac), static_cast<T *>(h->kk[c]), static_cast<T *>(h->ww[c]),
+            static_cast<T *>(h->nut[c]), h->d_all_map + po, n, h->np, mask, dst);
     });
+}
+
+unsigned field_mask(const double *const *dst) {
+    unsigned m = 0;
+    for (int q = 0; q < 6; ++q)
+        if (dst[q]) m |= 1u << q;
+    return m;
 }
 
 // Pipelined host I/O: two staging slots per direction and two transfer streams, so that
@@ -2559,7 +2506,7 @@ int fvlbm_set_f(fvlbm_handle *h, int instance, const double *f) {
     int rc = io_buffer(h, sizeof(double) * kQ * n);
     if (rc) return rc;
     CK(cudaMemcpyAsync(h->d_io, f, sizeof(double) * kQ * n, cudaMemcpyHostToDevice, h->stream));
-    scatter_f_dev(h, instance, h->d_io);
+    scatter_state_dev(h, instance, static_cast<const double *>(h->d_io));
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
     return FVLBM_OK;
@@ -2572,9 +2519,9 @@ int fvlbm_get_fields(fvlbm_handle *h, int instance, double *rho, double *u, doub
     const size_t n = io_cells(h, instance);
     int rc = io_buffer(h, sizeof(double) * 6 * n);
     if (rc) return rc;
-    gather_fields_dev(h, instance, h->d_io);
-    CK(cudaGetLastError());
     double *dst[6] = {rho, u, v, k, omega, nut};
+    gather_fields_dev(h, instance, field_mask(dst), h->d_io);
+    CK(cudaGetLastError());
     for (int q = 0; q < 6; ++q)
         if (dst[q])
             CK(cudaMemcpyAsync(dst[q], h->d_io + q * n, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
@@ -2596,7 +2543,7 @@ int fvlbm_set_f_async(fvlbm_handle *h, int instance, const double *f) {
     CK(cudaMemcpyAsync(A.d_in[slot], f, bytes, cudaMemcpyHostToDevice, A.s_in));
     CK(cudaEventRecord(A.in_ready[slot], A.s_in));
     CK(cudaStreamWaitEvent(h->stream, A.in_ready[slot], 0));
-    scatter_f_dev(h, instance, A.d_in[slot]);
+    scatter_state_dev(h, instance, static_cast<const double *>(A.d_in[slot]));
     CK(cudaGetLastError());
     CK(cudaEventRecord(A.in_free[slot], h->stream));
     return FVLBM_OK;
@@ -2614,11 +2561,11 @@ int fvlbm_get_fields_async(fvlbm_handle *h, int instance, double *rho, double *u
     const size_t n = io_cells(h, instance);
     if ((rc = async_slot(h, &A.d_out[slot], &A.out_cap[slot], sizeof(double) * 6 * n))) return rc;
     CK(cudaStreamWaitEvent(h->stream, A.out_free[slot], 0));  // the slot's last copy-out is done
-    gather_fields_dev(h, instance, A.d_out[slot]);
+    double *dst[6] = {rho, u, v, k, omega, nut};
+    gather_fields_dev(h, instance, field_mask(dst), A.d_out[slot]);
     CK(cudaGetLastError());
     CK(cudaEventRecord(A.out_ready[slot], h->stream));
     CK(cudaStreamWaitEvent(A.s_out, A.out_ready[slot], 0));
-    double *dst[6] = {rho, u, v, k, omega, nut};
     for (int q = 0; q < 6; ++q)
         if (dst[q])
             CK(cudaMemcpyAsync(dst[q], A.d_out[slot] + q * n, sizeof(double) * n, cudaMemcpyDeviceToHost,
@@ -2655,22 +2602,14 @@ int fvlbm_set_fdev_f32_async(fvlbm_handle *h, int instance, const float *fdev) {
     auto &A = h->aio;
     const int slot = A.in_next;
     A.in_next ^= 1;
-    const int n = static_cast<int>(io_cells(h, instance));
-    const int po = instance == -1 ? 0 : perm_offset(h, instance);
-    const size_t bytes = sizeof(float) * kQ * static_cast<size_t>(n);
+    const size_t bytes = sizeof(float) * kQ * io_cells(h, instance);
     if ((rc = async_slot(h, &A.d_in[slot], &A.in_cap[slot], bytes))) return rc;
     float *buf = reinterpret_cast<float *>(A.d_in[slot]);
     CK(cudaStreamWaitEvent(A.s_in, A.in_free[slot], 0));
     CK(cudaMemcpyAsync(buf, fdev, bytes, cudaMemcpyHostToDevice, A.s_in));
     CK(cudaEventRecord(A.in_ready[slot], A.s_in));
     CK(cudaStreamWaitEvent(h->stream, A.in_ready[slot], 0));
-    dispatch(h->precision, [&](auto z_) {
-        using T = decltype(z_);
-        k_scatter_fdev32<T><<<(n + 255) / 256, 256, 0, h->stream>>>(
-            static_cast<T *>(h->fn), static_cast<T *>(h->mac), h->d_all_map + po, n, h->np, h->d_tile_inst,
-            h->d_ip, buf);
-        relax_all<T>(h);
-    });
+    scatter_state_dev(h, instance, static_cast<const float *>(buf));
     CK(cudaGetLastError());
     CK(cudaEventRecord(A.in_free[slot], h->stream));
     return FVLBM_OK;
