@@ -1,0 +1,132 @@
+"""C_L and C_D of an airfoil case as a differentiable PyTorch function.
+
+``forces(model, p)`` returns the tensor (C_L, C_D) after ``model.steps`` FP64 time steps
+(Steps 1-7 of Sec. 3.2, through the C ABI) of the case with parameters
+
+    p = [alpha (radians), inflow eddy-viscosity ratio nu_t/nu, d_1, ..., d_W]
+
+where d_j is the displacement of wall node ``model.wall_nodes[j]`` along its outward normal.
+alpha sets the far-field velocity (U cos alpha, U sin alpha) and the drag / lift directions;
+the ratio sets the far-field omega_b = k_b / (nu ratio).  The differentiated map keeps the
+initial state and the time step of the base case fixed (they are inputs of the time
+integration, not functions of p).
+
+The backward pass is the library's forward-mode tangent (precision FVLBM_FP64_TANGENT): one
+batched tangent solve with one instance per parameter gives every column of the Jacobian
+J = d(C_L, C_D)/dp at once, and the gradient is grad_output @ J.  For a handful of outputs
+and up to a few hundred parameters this costs one batched solve of twice the FP64 work; the
+derivatives are the same ones a reverse-mode adjoint of the discrete step would give.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import torch
+
+from . import fvlbm
+from .meshgen import BC_FARFIELD, BC_WALL
+
+
+class AirfoilForces:
+    """The parameter-to-(C_L, C_D) map of one airfoil case (see the module docstring)."""
+
+    def __init__(self, base_case, wall_nodes, steps: int, device: int = 0):
+        self.base = dataclasses.replace(base_case, mesh=base_case.mesh.normalized())
+        m = self.base.mesh
+        self.steps = int(steps)
+        self.device = device
+        self.wall_nodes = np.asarray(wall_nodes, np.int64)
+        self.ff = m.bedge_type == BC_FARFIELD
+        bv = m.bedge_val[self.ff]
+        self.U = float(np.hypot(bv[0, 1], bv[0, 2]))
+        self.k_b = bv[:, 3].copy()
+        self.normals = self._wall_normals()
+        probe = fvlbm.Solver(self.base, precision=fvlbm.FVLBM_FP64, device=device, kernel_path=1)
+        self.dt = probe.dt()
+        probe.close()
+        rho, u, v, k, w = self.base.init_arrays()
+        self.init = dict(rho=rho, u=u, v=v, k=k, omega=w)
+
+    def _wall_normals(self) -> np.ndarray:
+        """Outward unit normal (away from the body) at each chosen wall node, from the chord of
+        its two wall neighbours."""
+        m = self.base.mesh
+        wall = m.bedge_nodes[m.bedge_type == BC_WALL]
+        centre = m.xy[np.unique(wall)].mean(0)
+        out = np.zeros((len(self.wall_nodes), 2))
+        for j, nd in enumerate(self.wall_nodes):
+            nb = np.unique(wall[(wall == nd).any(1)])
+            nb = nb[nb != nd]
+            if nb.size != 2:
+                raise ValueError(f"node {nd} is not an interior wall node")
+            t = m.xy[nb[1]] - m.xy[nb[0]]
+            n = np.array([-t[1], t[0]]) / np.linalg.norm(t)
+            if np.dot(n, m.xy[nd] - centre) < 0:
+                n = -n
+            out[j] = n
+        return out
+
+    def n_params(self) -> int:
+        return 2 + len(self.wall_nodes)
+
+    def case_at(self, p: np.ndarray):
+        """The case at parameters p (initial state and dt of the base case)."""
+        alpha, ratio, disp = float(p[0]), float(p[1]), np.asarray(p[2:], np.float64)
+        m = self.base.mesh
+        bval = m.bedge_val.copy()
+        bval[self.ff, 1] = self.U * math.cos(alpha)
+        bval[self.ff, 2] = self.U * math.sin(alpha)
+        bval[self.ff, 4] = self.k_b / (self.base.nu * ratio)
+        xy = m.xy.copy()
+        xy[self.wall_nodes] += disp[:, None] * self.normals
+        mesh = dataclasses.replace(m, xy=xy, bedge_val=bval)
+        return dataclasses.replace(self.base, mesh=mesh, dt=self.dt, alpha_deg=math.degrees(alpha),
+                                   **self.init)
+
+    def value(self, p: np.ndarray) -> np.ndarray:
+        s = fvlbm.Solver(self.case_at(p), precision=fvlbm.FVLBM_FP64, device=self.device,
+                         kernel_path=1)
+        s.step(self.steps)
+        f = s.forces()
+        s.close()
+        return np.array([f["cl"], f["cd"]])
+
+    def jacobian(self, p: np.ndarray) -> np.ndarray:
+        """J[o, q] = d output_o / d p_q (outputs C_L, C_D) from one batched tangent solve."""
+        case = self.case_at(p)
+        m = case.mesh
+        nb = m.n_bedges
+        d_alpha = np.zeros((nb, 5))
+        d_alpha[self.ff, 1] = -m.bedge_val[self.ff, 2]
+        d_alpha[self.ff, 2] = m.bedge_val[self.ff, 1]
+        d_ratio = np.zeros((nb, 5))
+        d_ratio[self.ff, 4] = -m.bedge_val[self.ff, 4] / float(p[1])
+        dirs = [{"dbedge_val": d_alpha, "dalpha": 1.0}, {"dbedge_val": d_ratio}]
+        for j, nd in enumerate(self.wall_nodes):
+            dxy = np.zeros_like(m.xy)
+            dxy[nd] = self.normals[j]
+            dirs.append({"dxy": dxy})
+        _, grads = fvlbm.forces_gradient(case, dirs, self.steps, device=self.device)
+        return np.array([[g["cl"] for g in grads], [g["cd"] for g in grads]])
+
+
+class _ForcesFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, p, model):
+        pn = p.detach().cpu().double().numpy()
+        ctx.model, ctx.pn = model, pn
+        return torch.as_tensor(model.value(pn), dtype=p.dtype)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        J = ctx.model.jacobian(ctx.pn)
+        g = grad_out.detach().cpu().double().numpy() @ J
+        return torch.as_tensor(g, dtype=grad_out.dtype), None
+
+
+def forces(model: AirfoilForces, p: torch.Tensor) -> torch.Tensor:
+    """(C_L, C_D) of ``model`` at parameters ``p`` (1-D tensor of length model.n_params()),
+    differentiable with respect to p."""
+    return _ForcesFunction.apply(p, model)
