@@ -326,7 +326,8 @@ def run_ours(args):
                                     "note": "comparison scheme of Sec. 4.1: stable only for dt < 2 tau"},
             "error": {"fp32_vs_fp64_gpu_velocity_rel_l2": l2_32_64, **err},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
-                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": _ncu_traffic(kname, args.workload, world),
                          "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": kbytes,
                          "avg_launch_ms": per_launch_ms},
@@ -362,6 +363,29 @@ def _workload_desc(name):
                      "C-meshes 50k-200k cells alpha 0-12 deg), CFL 0.5 each",
             "delaunay40k": "laminar lid-driven cavity Re 1000, seeded Delaunay ~40k triangles, dt = 5 tau",
             "cavity64": "laminar lid-driven cavity Re 400, 64x64 quads, CFL 0.5"}[name]
+
+
+def _ncu_traffic(kname, workload, world):
+    """DRAM bytes (read + write) per launch of kernel `kname` from the committed ncu summary of
+    the default sweep, when that summary was taken on the kernel source as it is now (its
+    recorded SHA-256 of csrc/fvlbm_kernels.cu matches); else None."""
+    import hashlib
+    import re
+    if workload != "sweep":
+        return None
+    try:
+        src = os.path.join(ROOT, "paper_1812_00394_gb300", "csrc", "fvlbm_kernels.cu")
+        with open(src, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+        with open(os.path.join(ROOT, "profiles", "k_fused_stage_fp32_sweep.md")) as fh:
+            txt = fh.read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256=([0-9a-f]{64})((?: \w+=\d+)+)", txt)
+    if not m or m.group(1) != sha:
+        return None
+    vals = dict(kv.split("=") for kv in m.group(2).split())
+    return float(vals[kname]) if kname in vals else None
 
 
 def _kernel_bytes(kname, prec, cells, sst_cells):

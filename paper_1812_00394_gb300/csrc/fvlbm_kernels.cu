@@ -75,7 +75,19 @@ struct InstParam {
     int local;    // 1: local time stepping (cell steps in Geo::dtc)
     int variant;  // reading variants: 1 limiter on grad f, 2 SST non-orthogonal correction,
                   // 4 SST per stage, 8 production limiter
+    float dt_f, nu_f, rho0_f, omega_min_f;  // the same values rounded once, for float kernels
 };
+
+// An instance parameter in the kernel's type: float kernels read the pre-rounded copy instead
+// of converting the double (a conversion that runs on the slow FP64 pipe of this GPU).
+template <class T>
+__device__ __forceinline__ T ipv(double d, float) {
+    return T(d);
+}
+template <>
+__device__ __forceinline__ float ipv<float>(double, float f) {
+    return f;
+}
 
 template <class T>
 struct Geo {
@@ -98,7 +110,7 @@ struct Geo {
 // Time step of cell i: its own under local time stepping, else the instance's.
 template <class T>
 __device__ __forceinline__ T cell_dt(const Geo<T> &G, const InstParam &P, int i) {
-    return G.dtc != nullptr ? G.dtc[i] : T(P.dt);
+    return G.dtc != nullptr ? G.dtc[i] : ipv<T>(P.dt, P.dt_f);
 }
 
 // ------------------------------------------------------------------ cell algebra
@@ -191,7 +203,7 @@ __global__ void __launch_bounds__(kTile) k_stage1(const T *__restrict__ fn, T *_
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
     T f[kQ];
     load9(fn, np, i, f);
-    relax9(f, T(P.rho0), cell_dt(G, P, i), tau[i]);
+    relax9(f, ipv<T>(P.rho0, P.rho0_f), cell_dt(G, P, i), tau[i]);
     store9(fs, np, i, f);
 }
 
@@ -204,7 +216,8 @@ __global__ void __launch_bounds__(kTile) k_stage_macros(const T *__restrict__ fs
     const size_t np = G.np;
     T f[kQ], dr, r, u, v;
     load9(fs, np, i, f);
-    moments(f, T(G.ip[G.tile_inst[blockIdx.x]].rho0), dr, r, u, v);
+    const InstParam &P = G.ip[G.tile_inst[blockIdx.x]];
+    moments(f, ipv<T>(P.rho0, P.rho0_f), dr, r, u, v);
     mac[i] = r;
     mac[np + i] = u;
     mac[2 * np + i] = v;
@@ -219,7 +232,7 @@ __global__ void __launch_bounds__(kTile) k_grad(const T *__restrict__ f, T *__re
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
-    const T rho0 = T(P.rho0);
+    const T rho0 = ipv<T>(P.rho0, P.rho0_f);
     T fi[kQ], gx[kQ], gy[kQ], lo[kQ], hi[kQ];
     load9(f, np, i, fi);
 #pragma unroll
@@ -342,7 +355,7 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
                                               const T *__restrict__ area,
                                               T *__restrict__ frel = nullptr,
                                               bool fn_read = false, T t1_i = T(0)) {
-    const T rho0 = T(P.rho0);
+    const T rho0 = ipv<T>(P.rho0, P.rho0_f);
     const T dt = dt_i;
     const T itau = T(1) / t_i;          // one division per cell, products below
     const T dt3 = dt * T(1.0 / 3.0), dt6 = dt * T(1.0 / 6.0);
@@ -473,7 +486,7 @@ __global__ void __launch_bounds__(kTile)
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
-    const T rho0 = T(P.rho0);
+    const T rho0 = ipv<T>(P.rho0, P.rho0_f);
     T fi[kQ], acc[kQ];
     load9(fs, np, i, fi);
 #pragma unroll
@@ -641,7 +654,7 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
     const int i = base + t;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[b * (BLK / kTile)]];
-    const T rho0 = T(P.rho0);
+    const T rho0 = ipv<T>(P.rho0, P.rho0_f);
     const int h0 = H.halo_ptr[b], nh = H.halo_ptr[b + 1] - h0, nr1 = H.r1[b];
     const int E = BLK + nh, NG = BLK + nr1;
     const unsigned *__restrict__ adj_g = H.adj + 4 * static_cast<size_t>(H.adj_ptr[b]);
@@ -912,7 +925,7 @@ __device__ __forceinline__ void sst_cell_update(const InstParam &P, T dt, T ui, 
                                                 T nti, T di, const T *g, const T *lgi, T f1,
                                                 const SstFace<T> *F, T &kn, T &wn, T &ntn,
                                                 T &tnew) {
-    const T nu = T(P.nu);
+    const T nu = ipv<T>(P.nu, P.nu_f);
     const T sk_i = f1 * T(kSk1) + (T(1) - f1) * T(kSk2);
     const T sw_i = f1 * T(kSw1) + (T(1) - f1) * T(kSw2);
     T ck = 0, cw = 0, dk = 0, dw = 0;
@@ -987,7 +1000,7 @@ __device__ __forceinline__ void sst_cell_update(const InstParam &P, T dt, T ui, 
     kn = (ki + dt * rk) / (T(1) + dt * T(kBstar) * wi);
     wn = (wi + dt * rw) / (T(1) + dt * beta * wi);
     kn = kn > T(0) ? kn : T(0);
-    wn = wn > T(P.omega_min) ? wn : T(P.omega_min);
+    wn = wn > ipv<T>(P.omega_min, P.omega_min_f) ? wn : ipv<T>(P.omega_min, P.omega_min_f);
     const T arg2 = fmax(T(2) * sqrt(kn) / (T(kBstar) * wn * di), T(500) * nu / (wn * di * di));
     const T f2 = tanh(arg2 * arg2);
     ntn = T(kA1) * kn / fmax(T(kA1) * wn, Sabs * f2);
@@ -1046,7 +1059,7 @@ __global__ void __launch_bounds__(kTile)
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
     if (!P.sst) return;  // laminar instance: tau stays nu / cs^2
-    const T nu = T(P.nu);
+    const T nu = ipv<T>(P.nu, P.nu_f);
     const T own[4] = {mac[np + i], mac[2 * np + i], kk[i], ww[i]};
     const T di = G.wdist[i];
     bool has[4];
@@ -1105,7 +1118,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 5 : 1)
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
     if (!P.sst) return;  // laminar instance
-    const T nu = T(P.nu);
+    const T nu = ipv<T>(P.nu, P.nu_f);
     const T ui = mac[np + i], vi = mac[2 * np + i], ki = kk[i], wi = ww[i], nti = nut[i];
     const T di = G.wdist[i];
     T g[8], lgi[4];
@@ -1170,7 +1183,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 5 : 1)
     if (frel != nullptr) {  // fused path: stage 1's f^(1) with the new relaxation time
         T f[kQ];
         load9(fn, np, i, f);
-        relax9(f, T(P.rho0), dt_i, tnew);
+        relax9(f, ipv<T>(P.rho0, P.rho0_f), dt_i, tnew);
         store9(frel, np, i, f);
     }
 }
@@ -1182,7 +1195,8 @@ __global__ void k_init_state(T *__restrict__ fn, T *__restrict__ mac, const doub
                              Geo<T> G) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
-    const T rho0 = T(G.ip[G.tile_inst[blockIdx.x]].rho0);
+    const InstParam &P = G.ip[G.tile_inst[blockIdx.x]];
+    const T rho0 = ipv<T>(P.rho0, P.rho0_f);
     const T r = T(r0[i]), u = T(u0[i]), v = T(v0[i]);
     T eq[kQ];
     feq_dev(T(r0[i] - double(rho0)), r, u, v, eq);
@@ -1285,11 +1299,11 @@ __global__ void k_scatter_state(T *__restrict__ f, T *__restrict__ mac, T *__res
         f[a * np + i] = d[a];
     }
     T dr, r, u, v;
-    moments(d, T(P.rho0), dr, r, u, v);
+    moments(d, ipv<T>(P.rho0, P.rho0_f), dr, r, u, v);
     mac[i] = r;
     mac[np + i] = u;
     mac[2 * np + i] = v;
-    relax9(d, T(P.rho0), cell_dt(G, P, i), tau[i]);
+    relax9(d, ipv<T>(P.rho0, P.rho0_f), cell_dt(G, P, i), tau[i]);
     store9(frel, np, i, d);
 }
 
@@ -2191,6 +2205,10 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
         ip[q] = InstParam{p.dt, params[q].nu, params[q].rho0,
                           1e-12 * params[q].uref / params[q].lref, params[q].sst ? 1 : 0,
                           p.dt_cell.empty() ? 0 : 1, params[q].variant};
+        ip[q].dt_f = static_cast<float>(ip[q].dt);
+        ip[q].nu_f = static_cast<float>(ip[q].nu);
+        ip[q].rho0_f = static_cast<float>(ip[q].rho0);
+        ip[q].omega_min_f = static_cast<float>(ip[q].omega_min);
         cell_off += p.np;
         bface_off += p.nb;
         h->inst.push_back(I);
