@@ -67,3 +67,12 @@ def test_bench_entry_points_exist():
     """Every mode main() dispatches to is defined (the ncu profile mode included)."""
     for name in ("run_ours", "run_reference", "run_profile_mode"):
         assert callable(getattr(bench, name)), name
+
+
+def test_ncu_traffic_lookup_follows_the_kernel_source():
+    """roofline.traffic comes from the committed ncu summary only for the default workload and
+    only while the recorded hash matches the kernel source; otherwise it is None."""
+    assert bench._ncu_traffic("fused_stage2", "cavity64", 1) is None
+    assert bench._ncu_traffic("no_such_kernel", "sweep", 1) is None
+    got = bench._ncu_traffic("fused_stage2", "sweep", 1)
+    assert got is None or got > 1e8
