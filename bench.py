@@ -277,6 +277,22 @@ def run_ours(args):
     v32 = np.concatenate([_vel(s32.fields(i)) for i in range(s32.n)])
     v64 = np.concatenate([_vel(s64.fields(i)) for i in range(s64.n)])
     l2_32_64 = float(np.linalg.norm(v32 - v64) / np.linalg.norm(v64))
+    # the same per kind of instance, and the wall-force coefficients of the airfoils
+    err_kind = {}
+    for kind in sorted({c.name.split("_")[0].rstrip("0123456789") for c in cases}):
+        idx = [i for i, c in enumerate(cases) if c.name.split("_")[0].rstrip("0123456789") == kind]
+        a = np.concatenate([_vel(s32.fields(i)) for i in idx])
+        b = np.concatenate([_vel(s64.fields(i)) for i in idx])
+        err_kind[f"fp32_vs_fp64_gpu_velocity_rel_l2[{kind}]"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    cl_cd = []
+    for i, c in enumerate(cases):
+        if c.name.startswith("naca"):
+            f32, f64 = s32.forces(i), s64.forces(i)
+            cl_cd.append(max(abs(f32["cl"] - f64["cl"]) / max(abs(f64["cl"]), 1e-12),
+                             abs(f32["cd"] - f64["cd"]) / max(abs(f64["cd"]), 1e-12)))
+    if cl_cd:
+        err_kind["fp32_vs_fp64_gpu_cl_cd_max_rel"] = float(max(cl_cd))
+    err_kind["fp32_vs_fp64_after_steps"] = args.warmup + args.steps
 
     # per-kernel device times (CUDA events on the handle's stream) for the roofline
     with torch.cuda.stream(stream):
@@ -324,7 +340,7 @@ def run_ours(args):
             "explicit_euler_fp32": {"ms_per_step": ms_euler / args.steps,
                                     "imex_over_euler_cost_per_step": ms32 / ms_euler,
                                     "note": "comparison scheme of Sec. 4.1: stable only for dt < 2 tau"},
-            "error": {"fp32_vs_fp64_gpu_velocity_rel_l2": l2_32_64, **err},
+            "error": {"fp32_vs_fp64_gpu_velocity_rel_l2": l2_32_64, **err_kind, **err},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": _ncu_traffic(kname, args.workload, world),
