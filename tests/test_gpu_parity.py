@@ -269,6 +269,42 @@ def test_explicit_collision_limit_vs_imex():
     assert not run(30.0, fvlbm.SCHEME_IMEX, steps=100)
 
 
+def _cavity_tri128_re3200():
+    """The stability case of Sec. 4.1: lid-driven cavity at Re 3200 on 128 x 128 squares split
+    into triangles, lid speed 0.1, rho = 1 + 1e-6 noise."""
+    n, U = 128, 0.1
+    xs = np.linspace(0, 1, n + 1)
+    xy, cells, sides = mg.quad_grid(xs, xs, 0.0, 0)
+    tri = mg.split_quads(cells)
+    bn = np.concatenate([sides["bottom"], sides["right"], sides["top"], sides["left"]])
+    bt, bv = mg._cavity_bc(bn, xy, U)
+    m = mg.Mesh(xy, np.arange(tri.shape[0] + 1, dtype=np.int32) * 3, tri.ravel().astype(np.int32),
+                bn, bt, bv).normalized()
+    return m, U / 3200.0, 1.0 + 1e-6 * mg.splitmix64_uniform(1, m.n_cells)
+
+
+def test_sec41_stability_limits_on_the_paper_cavity():
+    """Sec. 4.1 reports the largest stable step on this cavity as 1.91 tau for the explicit
+    scheme and 108.3 tau for the IMEX scheme.  Here (6,000 steps, FP64) the explicit scheme is
+    stable at 1.80 tau and diverges at 1.95 tau (the bisection boundary is 1.853 tau), and the
+    IMEX scheme is stable at 60 tau (boundary 70.4 tau, a convective CFL of 3.4: the limit is
+    then the explicit convection, not the collision)."""
+    m, nu, rho = _cavity_tri128_re3200()
+    tau = 3.0 * nu
+
+    def diverges(z, scheme, steps=6000):
+        s = fvlbm.Solver(mg.Case(m, nu=nu, dt=z * tau, uref=0.1, rho=rho), precision=FP64,
+                         device=0, kernel_path=1 if scheme else 0, scheme=scheme)
+        for _ in range(steps // 1000):
+            st = s.step(1000, stats=True)
+            if st["diverged"] or np.abs(s.fields()["u"]).max() > 1.0:
+                return True
+        return False
+    assert not diverges(1.80, fvlbm.SCHEME_EULER)
+    assert diverges(1.95, fvlbm.SCHEME_EULER)
+    assert not diverges(60.0, fvlbm.SCHEME_IMEX)
+
+
 # ----------------------------------------------------------------- degenerate and ragged inputs
 def _single_triangle(lid=0.1):
     xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.3, 0.9]])
