@@ -213,9 +213,18 @@ def rank_seed(rank: int) -> int:
     return 5 + 7919 * rank
 
 
-def aggregate_rate(cells_per_rank: int, world: int, steps: int, ms_max: float) -> float:
+def sum_over_ranks(torch, dist, world: int, value: float, device: str = "cuda") -> float:
+    """The sum over ranks (the cells every rank's own sweep holds); a no-op for one rank."""
+    if world <= 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def aggregate_rate(cells_all_ranks: float, steps: int, ms_max: float) -> float:
     """Whole-job Mcell-steps/s: the cells all ranks advanced over the slowest rank's time."""
-    return cells_per_rank * world * steps / (ms_max * 1e-3) / 1e6
+    return cells_all_ranks * steps / (ms_max * 1e-3) / 1e6
 
 
 def _vel(fields):
@@ -268,9 +277,10 @@ def run_ours(args):
     setup_s = time.perf_counter() - t_setup
 
     ms32 = results["f32"]["ms"]
-    value = aggregate_rate(total_cells, world, args.steps, ms32)
+    cells_job = sum_over_ranks(torch, dist, world, total_cells)  # ranks' sweeps differ in size
+    value = aggregate_rate(cells_job, args.steps, ms32)
     ms64 = results["f64"]["ms"]
-    value64 = aggregate_rate(total_cells, world, args.steps, ms64)
+    value64 = aggregate_rate(cells_job, args.steps, ms64)
 
     # FP32 vs FP64 (both GPU, same number of steps) on every cell of the workload
     s32, s64 = solvers["f32"], solvers["f64"]
@@ -516,11 +526,13 @@ def _e2e(torch, fvlbm, solver, stream, args, world, dist, pipelined=True, f32_io
         check(lib.fvlbm_wait(solver.h), "fvlbm_wait")
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+    total_job = total
     if world > 1:
         el = max_over_ranks(torch, dist, world, el, device="cuda")
+        total_job = sum_over_ranks(torch, dist, world, total)
     io = "pipelined (async calls, copy engines)" if pipelined else "synchronous calls"
     io += "; state uploaded as FP32 deviations f - w rho0" if f32_io else "; state uploaded as FP64 f"
-    return {"value": total * world / (el / k) / 1e6, "unit": UNIT,
+    return {"value": total_job / (el / k) / 1e6, "unit": UNIT,
             "h2d_bytes_per_step": int(total * 9 * (4 if f32_io else 8)),
             "d2h_bytes_per_step": int(total * 2 * 8),
             "steps": k, "ms_per_step": el / k * 1e3, "io": io}

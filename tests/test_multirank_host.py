@@ -32,7 +32,8 @@ def _worker(rank, world, port, out):
         seed = bench.rank_seed(rank)
         seeds = [None] * world
         dist.all_gather_object(seeds, seed)
-        out[rank] = (got, seeds)
+        cells = bench.sum_over_ranks(torch, dist, world, 1000 + 10 * rank, device="cpu")
+        out[rank] = (got, seeds, cells)
     finally:
         dist.destroy_process_group()
 
@@ -46,12 +47,14 @@ def test_two_gloo_ranks_max_time_and_distinct_seeds():
         res = dict(out)
     assert res[0][0] == res[1][0] == 15.0            # max over ranks, seen by every rank
     assert len(set(res[0][1])) == world               # every rank its own sweep
+    assert res[0][2] == res[1][2] == 2010.0           # cells summed over the ranks' own sweeps
 
 
 def test_single_rank_is_identity_and_rate():
     assert bench.max_over_ranks(torch, None, 1, 3.5) == 3.5
-    # 1000 cells, 2 ranks, 10 steps in 2 ms -> 10 Mcell-steps/s
-    assert abs(bench.aggregate_rate(1000, 2, 10, 2.0) - 10.0) < 1e-12
+    # 2000 cells over all ranks, 10 steps in 2 ms -> 10 Mcell-steps/s
+    assert abs(bench.aggregate_rate(2000, 10, 2.0) - 10.0) < 1e-12
+    assert bench.sum_over_ranks(torch, None, 1, 7.0) == 7.0
 
 
 @pytest.mark.parametrize("rank", [0, 1, 3])
