@@ -612,14 +612,19 @@ __device__ __forceinline__ void face_geo_s(const T *q, int ld, int m, int nv, T 
 
 // Shared-memory layout of the fused kernel (element offsets, every row 16-byte aligned):
 //   sf  [9][emax]   f^(J) of block, ring-1 and ring-2 cells
-//   sg  [16][gmax]  gradients (alpha = 1..8) of block and ring-1 cells
+//   sg  [gmax][17]  gradients (alpha = 1..8; x, y) of block and ring-1 cells, cell-major
 //   sD  [8][gmax]   neighbour-centroid offsets d_m of block and ring-1 cells
 //   adj [4 gmax] words, then one 8-byte mbarrier
+
+// Gradients in shared memory are cell-major, 16 values (alpha = 1..8, x and y) in a row of 17
+// words: one base address per cell serves all 16 reads (immediate offsets), and the odd row
+// length keeps consecutive cells in distinct banks.
+constexpr int kGradStride = 17;
 
 template <class T>
 struct FusedSmem {
     static __host__ __device__ size_t elems(int emax, int gmax) {
-        return size_t(kQ) * emax + 16u * gmax + 8u * gmax;
+        return size_t(kQ) * emax + size_t(kGradStride) * gmax + 8u * gmax;
     }
     static __host__ __device__ size_t bytes(int emax, int gmax) {
         return elems(emax, gmax) * sizeof(T) + 4u * gmax * sizeof(unsigned) + 16;
@@ -645,7 +650,7 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
     const int E0 = H.emax, G0 = H.gmax;
     T *sf = reinterpret_cast<T *>(smem_raw);
     T *sg = sf + kQ * E0;
-    T *sD = sg + 16 * G0;
+    T *sD = sg + kGradStride * G0;
     unsigned *sAdj = reinterpret_cast<unsigned *>(sD + 8 * G0);
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(sAdj + 4 * G0);
 
@@ -761,8 +766,8 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
         }
 #pragma unroll
         for (int a = 1; a < kQ; ++a) {
-            sg[(2 * a - 2) * G0 + c] = gx[a];
-            sg[(2 * a - 1) * G0 + c] = gy[a];
+            sg[c * kGradStride + 2 * a - 2] = gx[a];
+            sg[c * kGradStride + 2 * a - 1] = gy[a];
         }
     }
     __syncthreads();
@@ -808,8 +813,8 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
                 const bool own = en >= T(0);           // upwind side, branch free
                 const int src = own ? t : j;
                 const T rx = own ? rox : rnx, ry = own ? roy : rny;
-                const T fv = sf[a * E0 + src] + sg[(2 * a - 2) * G0 + src] * rx +
-                             sg[(2 * a - 1) * G0 + src] * ry;
+                const T *gs = sg + src * kGradStride;
+                const T fv = sf[a * E0 + src] + gs[2 * a - 2] * rx + gs[2 * a - 1] * ry;
                 acc[a] += en * fv;
             }
         }
