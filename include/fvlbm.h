@@ -270,6 +270,33 @@ int fvlbm_tangent_seed_nodes(fvlbm_handle *h, int instance, const double *dxy);
 int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *out, double *dout);
 
 /* ---------------------------------------------------------------------------------------------
+ * Discrete adjoint (reverse mode; no counterpart in the paper, which its conclusion's design use
+ * of the solver motivates like the tangent above).  One call gives the gradient of one scalar
+ * objective with respect to every cell's initial distributions and every boundary value, where
+ * the tangent needs one run per input direction.
+ *
+ *   J = w[0] C_D + w[1] C_L of `instance` after n_steps steps from the handle's current state,
+ *
+ * C_D, C_L as fvlbm_forces.  The step differentiated is the IMEX step of Sec. 3.1-3.2 (Steps 2-7)
+ * with one dt per instance, as the two-pass kernels run it in FP64 (the fused kernels give the
+ * same values up to rounding).  Where the step is not differentiable (the upwind switch on
+ * e.n = 0) the derivative of the branch the value takes is used, as in the tangent.
+ * Outputs (host, each may be NULL):
+ *   J              the objective's value;
+ *   dJ_df          [n_cells * 9] dJ/df of the current state, cell-major like fvlbm_get_f;
+ *   dJ_dbedge_val  [5 * n_bedges] dJ/d(rho_b, u_b, v_b, k_b, omega_b) in boundary-edge input
+ *                  order, the layout of fvlbm_tangent_seed (k_b and omega_b: 0; periodic
+ *                  edges: 0).
+ * Neither the state nor the step count of the handle changes.  The steps are recomputed from
+ * checkpoints: about 3 n_steps forward steps and n_steps adjoint steps, with (2 sqrt(n_steps)
+ * + 24) * 9 doubles per cell of device memory allocated for the call and freed before it returns.
+ * Valid on FVLBM_FP64 handles whose instances are all laminar, with the IMEX scheme, one dt per
+ * instance and no limiter or per-stage variant; else FVLBM_ERR_NOT_SUPPORTED.  Synchronises.
+ * Errors: BAD_PARAM (w NULL, n_steps < 0, bad instance), NOT_SUPPORTED, OOM, CUDA. */
+int fvlbm_adjoint(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
+                  double *dJ_dbedge_val);
+
+/* ---------------------------------------------------------------------------------------------
  * Checkpoint / resume and divergence rollback (no counterpart in the paper).
  *
  * The state of a handle -- f^n, f^(1) of the coming step, the macros, tau, k / omega / nu_t and

@@ -1413,6 +1413,7 @@ struct fvlbm_handle {
     int *d_nbr = nullptr, *d_tile_inst = nullptr, *d_btype = nullptr, *d_bowner = nullptr;
     int *d_perm = nullptr, *d_inst_tile0 = nullptr;
     int *d_all_map = nullptr;   // output position (all instances) -> internal cell
+    int *d_back = nullptr;      // FP64 handles: slot of each face at its neighbour [4 np] (adjoint)
     int total_nc = 0, total_nb = 0;
     // fused path: per-block halo lists and local adjacency, for each fused block size
     struct HaloSet {
@@ -2043,6 +2044,8 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
     if ((rc = upload_as<T>(h, &h->bval, bval))) return rc;
     if ((rc = upload_as<T>(h, &h->bnrm, bnrm))) return rc;
     if ((rc = upload_as<T>(h, &h->blen, blen))) return rc;
+    if (std::is_same<T, double>::value)
+        if ((rc = upload_raw(h, &h->d_back, back))) return rc;
     bool any_local = false;
     for (const Prepared *p : P) any_local |= !p->dt_cell.empty();
     if (any_local) {  // local time stepping: every cell's step (global instances: their dt)
@@ -2338,8 +2341,10 @@ int async_slot(fvlbm_handle *h, double **buf, size_t *cap, size_t bytes) {
 }
 
 // Wall force and coefficients of one instance; dout (may be NULL) receives their derivatives
-// (tangent handles), dalpha the derivative of the free-stream angle in radians.
-int forces_impl(fvlbm_handle *h, int instance, double dalpha, double *out, double *dout, double *cp) {
+// (tangent handles), dalpha the derivative of the free-stream angle in radians; fsrc (may be
+// NULL: the current state) the distributions they are taken from.
+int forces_impl(fvlbm_handle *h, int instance, double dalpha, double *out, double *dout, double *cp,
+                const void *fsrc = nullptr) {
     if (!h || instance < 0 || instance >= h->ninst || !out) return FVLBM_ERR_BAD_PARAM;
     CK(cudaSetDevice(h->device));
     const InstInfo &I = h->inst[instance];
@@ -2351,7 +2356,7 @@ int forces_impl(fvlbm_handle *h, int instance, double dalpha, double *out, doubl
         dispatch(h->precision, [&](auto z_) {
             using T = decltype(z_);
             k_wall_forces<T><<<nb, 256, 0, h->stream>>>(
-                static_cast<T *>(h->fn), h->d_bowner, static_cast<T *>(h->bnrm),
+                static_cast<const T *>(fsrc ? fsrc : h->fn), h->d_bowner, static_cast<T *>(h->bnrm),
                 static_cast<T *>(h->blen), I.bface_off, nbi, I.rho0, I.uref, geo_of<T>(h), h->d_io);
         });
         CK(cudaGetLastError());
@@ -2387,6 +2392,8 @@ int forces_impl(fvlbm_handle *h, int instance, double dalpha, double *out, doubl
 }
 
 }  // namespace
+
+#include "fvlbm_adjoint.cuh"
 
 extern "C" {
 
@@ -2652,6 +2659,11 @@ int fvlbm_wait(fvlbm_handle *h) {
 
 int fvlbm_forces(fvlbm_handle *h, int instance, double *out, double *cp) {
     return forces_impl(h, instance, 0.0, out, nullptr, cp);
+}
+
+int fvlbm_adjoint(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
+                  double *dJ_dbedge_val) {
+    return adjoint_impl(h, instance, n_steps, w, J, dJ_df, dJ_dbedge_val);
 }
 
 int fvlbm_tangent_seed(fvlbm_handle *h, int instance, const double *dbedge_val, const double *df) {

@@ -61,9 +61,9 @@ EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "
            "fvlbm_set_f", "fvlbm_get_fields", "fvlbm_info", "fvlbm_footprint",
            "fvlbm_profile_kernels", "fvlbm_autotune", "fvlbm_destroy", "fvlbm_strerror",
            "fvlbm_stats_reduce_static", "fvlbm_tangent_seed", "fvlbm_tangent_seed_nodes",
-           "fvlbm_get_f_tangent", "fvlbm_forces_tangent", "fvlbm_state_bytes", "fvlbm_save_state",
-           "fvlbm_load_state", "fvlbm_set_rollback", "fvlbm_set_f_async", "fvlbm_get_fields_async",
-           "fvlbm_wait", "fvlbm_get_fdev_f32", "fvlbm_set_fdev_f32_async"]
+           "fvlbm_get_f_tangent", "fvlbm_forces_tangent", "fvlbm_adjoint", "fvlbm_state_bytes",
+           "fvlbm_save_state", "fvlbm_load_state", "fvlbm_set_rollback", "fvlbm_set_f_async",
+           "fvlbm_get_fields_async", "fvlbm_wait", "fvlbm_get_fdev_f32", "fvlbm_set_fdev_f32_async"]
 
 _lib = None
 
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_get_f_tangent.argtypes = [vp, i, vp]
     lib.fvlbm_tangent_seed_nodes.argtypes = [vp, i, vp]
     lib.fvlbm_forces_tangent.argtypes = [vp, i, d, vp, vp]
+    lib.fvlbm_adjoint.argtypes = [vp, i, i, vp, vp, vp, vp]
     lib.fvlbm_destroy.argtypes = [vp]
     lib.fvlbm_destroy.restype = None
     lib.fvlbm_strerror.argtypes = [i]
@@ -277,6 +278,20 @@ def fvlbm_forces_tangent(h, instance: int = 0, dalpha: float = 0.0) -> tuple[dic
     return dict(zip(keys, out)), dict(zip(keys, dout))
 
 
+def fvlbm_adjoint(h, instance: int, n_steps: int, w_cd: float = 0.0, w_cl: float = 0.0):
+    """Reverse-mode gradient of J = w_cd C_D + w_cl C_L after n_steps FP64 steps from the
+    current state: (J, dJ/df [n_cells, 9], dJ/dbedge_val [n_bedges, 5]).  The handle's state is
+    unchanged."""
+    n, nb, _ = fvlbm_info(h, instance)
+    w = np.array([w_cd, w_cl], np.float64)
+    J = C.c_double()
+    df = np.empty((n, Q))
+    db = np.empty((nb, 5))
+    _check(load().fvlbm_adjoint(h, instance, int(n_steps), _p(w), C.byref(J), _p(df), _p(db)),
+           "fvlbm_adjoint")
+    return J.value, df, db
+
+
 def fvlbm_save_state(h) -> bytes:
     """The handle's state as an opaque blob (checkpoint)."""
     n = C.c_longlong()
@@ -420,3 +435,6 @@ class Solver:
 
     def forces_tangent(self, i: int = 0, dalpha: float = 0.0):
         return fvlbm_forces_tangent(self.h, i, dalpha)
+
+    def adjoint(self, n_steps: int, w_cd: float = 0.0, w_cl: float = 0.0, i: int = 0):
+        return fvlbm_adjoint(self.h, i, n_steps, w_cd, w_cl)

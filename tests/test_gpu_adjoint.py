@@ -1,0 +1,141 @@
+"""GPU checks of the discrete adjoint (fvlbm_adjoint) against the forward-mode tangent.
+
+Both differentiate the same FP64 two-pass IMEX step (Sec. 3.1-3.2, Steps 2-7) of a laminar
+instance.  For any seed (g, d) of the initial state and of the boundary values, the tangent gives
+dJ/dp after N steps by one forward run, and the adjoint gives the gradient whose inner product
+with (g, d) is the same number:  <dJ/df^0, g> + <dJ/dbval, d> = dJ/dp.  The two are computed by
+different kernels (the tangent carries dual numbers forward; the adjoint transposes the flux and
+gradient operators by gathers over the back slots of each face and the per-cell maps through
+their local Jacobians), so agreement to rounding checks every transposed piece.  A central
+finite difference of the FP64 step closes the loop on a boundary-value direction.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_1812_00394_gb300 import fvlbm, meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+FP64, TAN = fvlbm.FVLBM_FP64, fvlbm.FVLBM_FP64_TANGENT
+W = (0.7, -1.3)  # J = 0.7 C_D - 1.3 C_L
+
+
+def _cavity():
+    return mg.cavity_quad(16, re=400.0, lid_u=0.1, seed=3)
+
+
+def _naca_laminar():
+    c = mg.naca0012_cmesh(n_target=2500, re_c=2000.0, alpha_deg=5.0)
+    return dataclasses.replace(c, sst=False)
+
+
+def _bfs_laminar():
+    c = mg.bfs_hybrid(n_target=3000)
+    return dataclasses.replace(c, sst=False)
+
+
+CASES = {"cavity": _cavity, "naca": _naca_laminar, "bfs": _bfs_laminar}
+
+
+def _seeds(case, rng):
+    m = case.mesh.normalized()
+    g = 1e-3 * rng.standard_normal((m.n_cells, 9))
+    d = np.zeros((m.n_bedges, 5))
+    d[:, :3] = 1e-2 * rng.standard_normal((m.n_bedges, 3))
+    return g, d
+
+
+def _tangent_dJ(case, warm, n, g, d):
+    t = fvlbm.Solver(case, precision=TAN, device=0)
+    t.step(warm)
+    t.tangent_seed(d, g)
+    t.step(n)
+    val, dv = t.forces_tangent(dalpha=0.0)
+    t.close()
+    return W[0] * val["cd"] + W[1] * val["cl"], W[0] * dv["cd"] + W[1] * dv["cl"]
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("n", [0, 1, 7, 20])
+def test_adjoint_dot_product_against_tangent(name, n):
+    case = CASES[name]()
+    warm = 15
+    rng = np.random.default_rng(100 + n)
+    g, d = _seeds(case, rng)
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    s.step(warm)
+    f_before = s.get_f()
+    J, dJdf, dJdb = s.adjoint(n, W[0], W[1])
+    # the handle's state does not move
+    np.testing.assert_array_equal(s.get_f(), f_before)
+    Jt, dJt = _tangent_dJ(case, warm, n, g, d)
+    adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
+    assert abs(J - Jt) <= 1e-10 * max(abs(Jt), 1e-12)
+    assert abs(adj - dJt) <= 1e-9 * max(abs(dJt), 1e-30), (adj, dJt)
+    # k_b, omega_b do not enter a laminar step
+    assert np.all(dJdb[:, 3:] == 0.0)
+    s.close()
+
+
+def test_adjoint_value_matches_fp64_forces():
+    case = _naca_laminar()
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    s.step(10)
+    J, _, _ = s.adjoint(12, 1.0, 0.0)
+    JL, _, _ = s.adjoint(12, 0.0, 1.0)
+    s.step(12)
+    ref = s.forces()
+    assert abs(J - ref["cd"]) <= 1e-10 * abs(ref["cd"])
+    assert abs(JL - ref["cl"]) <= 1e-10 * abs(ref["cl"])
+    s.close()
+
+
+def test_adjoint_lid_speed_vs_fd():
+    """Cavity, p = lid speed: dJ/dp = <dJ/dbval, d(bval)/dp> against central differences of
+    the FP64 step (independent of both derivative codes)."""
+    U, h, n = 0.1, 1e-5, 25
+    base = _cavity()
+
+    def solver(u):
+        c = mg.cavity_quad(16, re=400.0, lid_u=u, seed=3)
+        # only the lid's boundary value moves: viscosity and the C_D / C_L normalisation stay
+        c = dataclasses.replace(c, rho=base.rho, u=base.u, v=base.v, nu=base.nu, uref=base.uref)
+        return fvlbm.Solver(c, precision=FP64, device=0, kernel_path=1)
+
+    m = base.mesh.normalized()
+    d = np.zeros((m.n_bedges, 5))
+    d[m.bedge_val[:, 1] != 0.0, 1] = 1.0
+    s = solver(U)
+    _, _, dJdb = s.adjoint(n, *W)
+    vals = []
+    for u in (U + h, U - h):
+        x = solver(u)
+        x.step(n)
+        f = x.forces()
+        vals.append(W[0] * f["cd"] + W[1] * f["cl"])
+        x.close()
+    fd = (vals[0] - vals[1]) / (2 * h)
+    adj = float(np.sum(dJdb * d))
+    assert abs(adj - fd) <= 1e-6 * abs(fd), (adj, fd)
+    s.close()
+
+
+def test_adjoint_rejects_unsupported_handles():
+    case = _cavity()
+    for kw in ({"precision": fvlbm.FVLBM_FP32_DEV}, {"precision": TAN}):
+        s = fvlbm.Solver(case, device=0, **kw)
+        with pytest.raises(fvlbm.FvlbmError) as e:
+            s.adjoint(3, 1.0, 0.0)
+        assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
+        s.close()
+    sst = mg.naca0012_cmesh(n_target=2500)
+    s = fvlbm.Solver(sst, precision=FP64, device=0)
+    with pytest.raises(fvlbm.FvlbmError) as e:
+        s.adjoint(3, 1.0, 0.0)
+    assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
+    with pytest.raises(fvlbm.FvlbmError) as e:
+        s.adjoint(-1, 1.0, 0.0)
+    assert e.value.code == fvlbm.FVLBM_ERR_BAD_PARAM
+    s.close()
