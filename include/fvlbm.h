@@ -286,15 +286,22 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
  *   dJ_df          [n_cells * 9] dJ/df of the current state, cell-major like fvlbm_get_f;
  *   dJ_dbedge_val  [5 * n_bedges] dJ/d(rho_b, u_b, v_b, k_b, omega_b) in boundary-edge input
  *                  order, the layout of fvlbm_tangent_seed (k_b and omega_b: 0; periodic
- *                  edges: 0).
+ *                  edges: 0);
+ *   dJ_dxy         [2 * n_nodes] dJ/d(x, y) of every mesh node at fixed dt and fixed initial
+ *                  state, through the preprocessed geometry (areas, face normals and lengths,
+ *                  centroids, face offsets, least-squares weights, the wall normals and lengths
+ *                  of the force): the gradient whose inner product with a node displacement is
+ *                  what fvlbm_tangent_seed_nodes gives for it.  Not for meshes with periodic
+ *                  pairs (FVLBM_ERR_NOT_SUPPORTED).
  * Neither the state nor the step count of the handle changes.  The steps are recomputed from
  * checkpoints: about 3 n_steps forward steps and n_steps adjoint steps, with (2 sqrt(n_steps)
- * + 24) * 9 doubles per cell of device memory allocated for the call and freed before it returns.
+ * + 24) * 9 doubles per cell of device memory (32 more per cell with dJ_dxy) allocated for the
+ * call and freed before it returns; dJ_dxy adds one pass over the cells on the host.
  * Valid on FVLBM_FP64 handles whose instances are all laminar, with the IMEX scheme, one dt per
  * instance and no limiter or per-stage variant; else FVLBM_ERR_NOT_SUPPORTED.  Synchronises.
  * Errors: BAD_PARAM (w NULL, n_steps < 0, bad instance), NOT_SUPPORTED, OOM, CUDA. */
 int fvlbm_adjoint(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
-                  double *dJ_dbedge_val);
+                  double *dJ_dbedge_val, double *dJ_dxy);
 
 /* ---------------------------------------------------------------------------------------------
  * Checkpoint / resume and divergence rollback (no counterpart in the paper).

@@ -245,6 +245,74 @@ __global__ void __launch_bounds__(kTile) k_adj_gradT(const double *__restrict__ 
     for (int a = 0; a < kQ; ++a) lf[a * np + j] = lfj[a];
 }
 
+// ---- adjoints of the geometry arrays read by one flux and gradient evaluation: with la the
+// adjoint of acc and lg that of g at this stage value, accumulate dJ/d(sn, rown, rnbr, lsq) of
+// every face slot of the cell (one thread per cell, its own slots only).
+__global__ void __launch_bounds__(kTile) k_adj_geom(const double *__restrict__ fs, const double *__restrict__ g,
+                                                    const double *__restrict__ la, const double *__restrict__ lg,
+                                                    Geo<double> G, double *__restrict__ a_sn,
+                                                    double *__restrict__ a_lsq, double *__restrict__ a_rown,
+                                                    double *__restrict__ a_rnbr) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    const double rho0 = G.ip[G.tile_inst[blockIdx.x]].rho0;
+    double fi[kQ];
+    load9(fs, np, i, fi);
+    for (int m = 0; m < 4; ++m) {
+        const int nb = G.nbr[m * np + i];
+        if (nb == kNone) continue;
+        const double snx = G.sn[(2 * m) * np + i], sny = G.sn[(2 * m + 1) * np + i];
+        double s_snx = 0, s_sny = 0, s_rox = 0, s_roy = 0, s_rnx = 0, s_rny = 0, s_lx = 0, s_ly = 0;
+        if (nb >= 0) {
+            const double rox = G.rown[(2 * m) * np + i], roy = G.rown[(2 * m + 1) * np + i];
+            const double rnx = G.rnbr[(2 * m) * np + i], rny = G.rnbr[(2 * m + 1) * np + i];
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) {
+                const double en = edot<double>(a, snx, sny);
+                const double l = la[a * np + i];
+                const double fm = fs[a * np + nb];
+                double fv;
+                if (en >= 0.0) {
+                    const double gx = g[(2 * a) * np + i], gy = g[(2 * a + 1) * np + i];
+                    fv = fi[a] + gx * rox + gy * roy;
+                    s_rox += l * en * gx;
+                    s_roy += l * en * gy;
+                } else {
+                    const double gx = g[(2 * a) * np + nb], gy = g[(2 * a + 1) * np + nb];
+                    fv = fm + gx * rnx + gy * rny;
+                    s_rnx += l * en * gx;
+                    s_rny += l * en * gy;
+                }
+                s_snx += l * ex_of(a) * fv;
+                s_sny += l * ey_of(a) * fv;
+                s_lx += lg[(2 * a) * np + i] * (fm - fi[a]);
+                s_ly += lg[(2 * a + 1) * np + i] * (fm - fi[a]);
+            }
+        } else {
+            const int bf = -nb - 1;
+            double dr, r, u, v, fb[kQ];
+            moments(fi, rho0, dr, r, u, v);
+            boundary_values(G.btype[bf], G.bval + bf, 0, G.nbt, snx, sny, fi, dr, r, u, v, rho0, fb);
+#pragma unroll
+            for (int a = 0; a < kQ; ++a) {
+                const double l = la[a * np + i];
+                s_snx += l * ex_of(a) * fb[a];
+                s_sny += l * ey_of(a) * fb[a];
+                s_lx += lg[(2 * a) * np + i] * (fb[a] - fi[a]);
+                s_ly += lg[(2 * a + 1) * np + i] * (fb[a] - fi[a]);
+            }
+        }
+        a_sn[(2 * m) * np + i] += s_snx;
+        a_sn[(2 * m + 1) * np + i] += s_sny;
+        a_lsq[(2 * m) * np + i] += s_lx;
+        a_lsq[(2 * m + 1) * np + i] += s_ly;
+        a_rown[(2 * m) * np + i] += s_rox;
+        a_rown[(2 * m + 1) * np + i] += s_roy;
+        a_rnbr[(2 * m) * np + i] += s_rnx;
+        a_rnbr[(2 * m + 1) * np + i] += s_rny;
+    }
+}
+
 // ---- stage 3: lf3 = L, lc = L, la3 = -dt/3 L
 __global__ void __launch_bounds__(kTile) k_adj_stage3(const double *__restrict__ L, double *__restrict__ lf3,
                                                       double *__restrict__ lc, double *__restrict__ la,
@@ -362,6 +430,7 @@ __global__ void __launch_bounds__(kTile) k_adj_relax(const double *__restrict__ 
 __global__ void __launch_bounds__(kTile) k_adj_seed(const double *__restrict__ fn, const double *__restrict__ bnrm,
                                                     const double *__restrict__ blen, int inst, double cx, double cy,
                                                     double *__restrict__ L, double *__restrict__ lbval,
+                                                    double *__restrict__ a_bnrm, double *__restrict__ a_blen,
                                                     Geo<double> G) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
@@ -387,6 +456,20 @@ __global__ void __launch_bounds__(kTile) k_adj_seed(const double *__restrict__ f
             adj_bvals_T(FVLBM_BC_WALL, bv3, nx, ny, fi, rho0, c, lfi, lb3);
             if (lbval != nullptr)
                 for (int q = 0; q < 3; ++q) lbval[q * G.nbt + bf] += lb3[q];
+            if (a_bnrm != nullptr) {  // F = sum_a e_a (e_a . n) (f_bc + w rho0) dl
+                double dr, r, u, v, fb[kQ], sx = 0, sy = 0, sl = 0;
+                moments(fi, rho0, dr, r, u, v);
+                boundary_values(FVLBM_BC_WALL, G.bval + bf, 0, G.nbt, nx, ny, fi, dr, r, u, v, rho0, fb);
+                for (int a = 0; a < kQ; ++a) {
+                    const double wgt = (ex_of(a) * cx + ey_of(a) * cy) * (fb[a] + w_of<double>(a) * rho0);
+                    sx += wgt * ex_of(a);
+                    sy += wgt * ey_of(a);
+                    sl += wgt * edot<double>(a, nx, ny);
+                }
+                a_bnrm[bf] = sx * blen[bf];
+                a_bnrm[G.nbt + bf] = sy * blen[bf];
+                a_blen[bf] = sl;
+            }
         }
     }
 #pragma unroll
@@ -456,6 +539,8 @@ void adj_forward_step(fvlbm_handle *h, const Geo<double> &G, const double *f_in,
 // is replaced by the adjoint of f^n; boundary-value adjoints are added into lbval.
 struct AdjVars {
     double *L, *lf3, *lc, *la, *lg, *lB, *lf2, *ls1, *lf0, *lbval;
+    double *a_sn = nullptr, *a_lsq = nullptr, *a_rown = nullptr, *a_rnbr = nullptr;  // shape adjoint
+    double *a_bnrm = nullptr, *a_blen = nullptr;
 };
 
 void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const double *f0, const AdjStep &S,
@@ -465,29 +550,37 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const double *f0, 
     const size_t nq = static_cast<size_t>(kQ) * h->np;
     const double *tau = static_cast<const double *>(h->tau);
     const int *back = h->d_back;
+    auto geom = [&](const double *fs, const double *g) {
+        if (A.a_sn)
+            k_adj_geom<<<grid, block, 0, s>>>(fs, g, A.la, A.lg, G, A.a_sn, A.a_lsq, A.a_rown, A.a_rnbr);
+    };
     k_adj_stage3<<<grid, block, 0, s>>>(A.L, A.lf3, A.lc, A.la, G);
     k_adj_fluxT<<<grid, block, 0, s>>>(S.f3, A.la, A.lf3, A.lg, A.lbval, G, back);
+    geom(S.f3, S.g3);
     k_adj_gradT<<<grid, block, 0, s>>>(S.f3, A.lg, A.lf3, A.lbval, G, back);
     k_adj_stage2<<<grid, block, 0, s>>>(S.B, S.f2, S.g2, tau, A.lf3, A.lc, A.lB, A.la, G);
     cudaMemsetAsync(A.lf2, 0, nq * sizeof(double), s);
     k_adj_fluxT<<<grid, block, 0, s>>>(S.f2, A.la, A.lf2, A.lg, A.lbval, G, back);
+    geom(S.f2, S.g2);
     k_adj_gradT<<<grid, block, 0, s>>>(S.f2, A.lg, A.lf2, A.lbval, G, back);
     k_adj_stage1<<<grid, block, 0, s>>>(f0, S.s1, S.g1, tau, A.lf2, A.lB, A.lc, A.lf0, A.la, G);
     cudaMemsetAsync(A.ls1, 0, nq * sizeof(double), s);
     k_adj_fluxT<<<grid, block, 0, s>>>(S.s1, A.la, A.ls1, A.lg, A.lbval, G, back);
+    geom(S.s1, S.g1);
     k_adj_gradT<<<grid, block, 0, s>>>(S.s1, A.lg, A.ls1, A.lbval, G, back);
     k_adj_relax<<<grid, block, 0, s>>>(f0, tau, A.ls1, A.lf0, G);
     std::swap(A.L, A.lf0);
 }
 
 int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
-                 double *dJ_dbedge) {
+                 double *dJ_dbedge, double *dJ_dxy) {
     if (!h || instance < 0 || instance >= h->ninst || n_steps < 0 || !w) return FVLBM_ERR_BAD_PARAM;
     if (h->precision != FVLBM_FP64 || h->sst || h->scheme != 0 || h->dtc != nullptr || h->limit_f ||
         h->per_stage || h->d_back == nullptr)
         return FVLBM_ERR_NOT_SUPPORTED;
-    CK(cudaSetDevice(h->device));
     const InstInfo &I = h->inst[instance];
+    if (dJ_dxy && (!I.mesh || !I.mesh->ppairs.empty())) return FVLBM_ERR_NOT_SUPPORTED;
+    CK(cudaSetDevice(h->device));
     const Geo<double> G = geo_of<double>(h);
     const size_t np = h->np, nq = static_cast<size_t>(kQ) * np;
     const int K = std::max(1, static_cast<int>(std::ceil(std::sqrt(static_cast<double>(n_steps)))));
@@ -503,8 +596,23 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
     AdjVars A{M.get(nq, &err), M.get(nq, &err), M.get(nq, &err), M.get(nq, &err), M.get(2 * nq, &err),
               M.get(nq, &err), M.get(nq, &err), M.get(nq, &err), M.get(nq, &err),
               M.get(3 * static_cast<size_t>(std::max(h->nbt, 1)), &err)};
+    const size_t nbt = std::max(h->nbt, 1);
+    if (dJ_dxy) {
+        A.a_sn = M.get(8 * np, &err);
+        A.a_lsq = M.get(8 * np, &err);
+        A.a_rown = M.get(8 * np, &err);
+        A.a_rnbr = M.get(8 * np, &err);
+        A.a_bnrm = M.get(2 * nbt, &err);
+        A.a_blen = M.get(nbt, &err);
+    }
     if (err != cudaSuccess) return cuda_fail(err);
     cudaStream_t s = h->stream;
+    if (dJ_dxy) {
+        for (double *x : {A.a_sn, A.a_lsq, A.a_rown, A.a_rnbr})
+            CK(cudaMemsetAsync(x, 0, 8 * np * sizeof(double), s));
+        CK(cudaMemsetAsync(A.a_bnrm, 0, 2 * nbt * sizeof(double), s));
+        CK(cudaMemsetAsync(A.a_blen, 0, nbt * sizeof(double), s));
+    }
     // forward sweep: f^N and the checkpoints
     CK(cudaMemcpyAsync(xa, h->fn, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (nck > 0) CK(cudaMemcpyAsync(ck[0], xa, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -526,7 +634,7 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
     CK(cudaMemsetAsync(A.lbval, 0, 3 * static_cast<size_t>(std::max(h->nbt, 1)) * sizeof(double), s));
     k_adj_seed<<<h->ntiles, kTile, 0, s>>>(xa, static_cast<const double *>(h->bnrm),
                                            static_cast<const double *>(h->blen), instance, cx, cy, A.L,
-                                           A.lbval, G);
+                                           A.lbval, A.a_bnrm, A.a_blen, G);
     CK(cudaGetLastError());
     // backward sweep, one checkpoint segment at a time
     for (int c = nck - 1; c >= 0; --c) {
@@ -552,8 +660,59 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
             CK(cudaMemcpyAsync(lb.data() + static_cast<size_t>(c) * I.nb,
                                A.lbval + static_cast<size_t>(c) * h->nbt + I.bface_off, sizeof(double) * I.nb,
                                cudaMemcpyDeviceToHost, s));
+    // shape adjoint: the instance's slices of the geometry adjoints, in input order, then the
+    // reverse of the host preprocessing
+    GeometryAdjoint GA;
+    std::vector<int> perm(std::max(I.nc, 1));
+    std::vector<double> runs;
+    if (dJ_dxy) {
+        const size_t nc = I.nc;
+        CK(cudaMemcpyAsync(perm.data(), h->d_perm + perm_offset(h, instance), sizeof(int) * nc,
+                           cudaMemcpyDeviceToHost, s));
+        runs.resize(4 * 8 * nc + 3 * static_cast<size_t>(std::max(I.nb, 1)));
+        const double *src[4] = {A.a_sn, A.a_lsq, A.a_rown, A.a_rnbr};
+        for (int q = 0; q < 4; ++q)
+            for (int c = 0; c < 8; ++c)
+                CK(cudaMemcpyAsync(runs.data() + (8 * q + c) * nc, src[q] + c * np + I.cell_off, sizeof(double) * nc,
+                                   cudaMemcpyDeviceToHost, s));
+        double *bt = runs.data() + 32 * nc;
+        if (I.nb > 0) {
+            CK(cudaMemcpyAsync(bt, A.a_bnrm + I.bface_off, sizeof(double) * I.nb, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(bt + I.nb, A.a_bnrm + h->nbt + I.bface_off, sizeof(double) * I.nb,
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(bt + 2 * I.nb, A.a_blen + I.bface_off, sizeof(double) * I.nb, cudaMemcpyDeviceToHost,
+                               s));
+        }
+    }
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
+    if (dJ_dxy) {
+        const size_t nc = I.nc;
+        const MeshCopy &mc = *I.mesh;
+        std::vector<double> *dst[4] = {&GA.sn, &GA.lsq, &GA.rown, &GA.rnbr};
+        for (int q = 0; q < 4; ++q) {
+            dst[q]->assign(8 * nc, 0.0);
+            for (size_t k = 0; k < nc; ++k)
+                for (int c = 0; c < 8; ++c)  // component c = 2 l + (x, y) of slot l
+                    (*dst[q])[8 * static_cast<size_t>(perm[k]) + c] = runs[(8 * q + c) * nc + k];
+        }
+        const size_t nbe = mc.btype.size();
+        GA.bnrm.assign(2 * nbe, 0.0);
+        GA.blen.assign(nbe, 0.0);
+        const double *bt = runs.data() + 32 * nc;
+        for (int f = 0; f < I.nb; ++f) {
+            const int e = I.bedge_of[f];
+            GA.bnrm[2 * e] = bt[f];
+            GA.bnrm[2 * e + 1] = bt[I.nb + f];
+            GA.blen[e] = bt[2 * I.nb + f];
+        }
+        const fvlbm_mesh Mm{I.n_nodes, mc.xy.data(), I.nc, mc.cell_ptr.data(), mc.cell_nodes.data()};
+        const fvlbm_bc Bm{static_cast<int>(nbe), mc.bnodes.data(), mc.btype.data(), mc.bval.data(), 0, nullptr,
+                          nullptr};
+        std::string why;
+        const int grc = geometry_adjoint(Mm, Bm, GA, dJ_dxy, &why);
+        if (grc) return grc;
+    }
     if (dJ_dbedge) {
         std::fill(dJ_dbedge, dJ_dbedge + 5 * static_cast<size_t>(I.n_bedges_in), 0.0);
         for (int b = 0; b < I.nb; ++b)

@@ -415,6 +415,183 @@ int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_para
     return FVLBM_OK;
 }
 
+namespace {
+
+// Area and centroid of cell i as prepare_instance_t forms them (relative to node 0).
+template <class S>
+void cell_area_centroid(const fvlbm_mesh &m, int i, const S *xy, S *area, S *cx, S *cy) {
+    const int p0 = m.cell_ptr[i], nv = m.cell_ptr[i + 1] - p0;
+    const int n0 = m.cell_nodes[p0];
+    const S ox = xy[2 * n0], oy = xy[2 * n0 + 1];
+    S a2 = 0, mx = 0, my = 0;
+    for (int l = 0; l < nv; ++l) {
+        const int a = m.cell_nodes[p0 + l], b = m.cell_nodes[p0 + (l + 1) % nv];
+        const S x0 = xy[2 * a] - ox, y0 = xy[2 * a + 1] - oy;
+        const S x1 = xy[2 * b] - ox, y1 = xy[2 * b + 1] - oy;
+        const S c = x0 * y1 - x1 * y0;
+        a2 += c;
+        mx += (x0 + x1) * c;
+        my += (y0 + y1) * c;
+    }
+    *area = S(0.5) * a2;
+    *cx = ox + mx / (S(3.0) * a2);
+    *cy = oy + my / (S(3.0) * a2);
+}
+
+// The geometry of cell i's faces (slot outputs of prepare_instance_t) from its node positions
+// xy and its face neighbours' centroids (nbx, nby; slots with nbr[l] < 0 are boundary faces).
+template <class S>
+struct CellGeo {
+    S sn[8], lsq[8], rown[8], rnbr[8], nrm[8], len[4];
+};
+
+template <class S>
+void cell_geometry(const fvlbm_mesh &m, int i, const S *xy, const int *nbr, const S *nbx, const S *nby,
+                   CellGeo<S> *G) {
+    const int p0 = m.cell_ptr[i], nv = m.cell_ptr[i + 1] - p0;
+    S area, cx, cy;
+    cell_area_centroid(m, i, xy, &area, &cx, &cy);
+    S dx[4], dy[4];
+    S mxx = 0, mxy = 0, myy = 0;
+    for (int l = 0; l < nv; ++l) {
+        const int a = m.cell_nodes[p0 + l], b = m.cell_nodes[p0 + (l + 1) % nv];
+        const S ex = xy[2 * b] - xy[2 * a], ey = xy[2 * b + 1] - xy[2 * a + 1];
+        const S len = sqrt(ex * ex + ey * ey);
+        const S nx = ey / len, ny = -ex / len;
+        const S xm = S(0.5) * (xy[2 * a] + xy[2 * b]), ym = S(0.5) * (xy[2 * a + 1] + xy[2 * b + 1]);
+        if (nbr[l] >= 0) {
+            dx[l] = nbx[l] - cx;
+            dy[l] = nby[l] - cy;
+            G->rnbr[2 * l] = xm - nbx[l];
+            G->rnbr[2 * l + 1] = ym - nby[l];
+        } else {
+            dx[l] = xm - cx;
+            dy[l] = ym - cy;
+            G->rnbr[2 * l] = G->rnbr[2 * l + 1] = S(0.0);
+        }
+        G->sn[2 * l] = nx * len / area;
+        G->sn[2 * l + 1] = ny * len / area;
+        G->rown[2 * l] = xm - cx;
+        G->rown[2 * l + 1] = ym - cy;
+        G->nrm[2 * l] = nx;
+        G->nrm[2 * l + 1] = ny;
+        G->len[l] = len;
+        mxx += dx[l] * dx[l];
+        mxy += dx[l] * dy[l];
+        myy += dy[l] * dy[l];
+    }
+    const S det = mxx * myy - mxy * mxy;
+    for (int l = 0; l < nv; ++l) {
+        G->lsq[2 * l] = (myy * dx[l] - mxy * dy[l]) / det;
+        G->lsq[2 * l + 1] = (mxx * dy[l] - mxy * dx[l]) / det;
+    }
+}
+
+}  // namespace
+
+int geometry_adjoint(const fvlbm_mesh &m, const fvlbm_bc &bc, const GeometryAdjoint &A, double *dxy,
+                     std::string *why) {
+    const int nc = m.n_cells, nn = m.n_nodes;
+    if (bc.n_periodic > 0) {
+        *why = "shape adjoint of periodic meshes";
+        return FVLBM_ERR_NOT_SUPPORTED;
+    }
+    // face neighbours (input ids) and boundary edges of every face slot
+    std::vector<int> nbr(4 * static_cast<size_t>(nc), kNone);
+    std::unordered_map<uint64_t, Side> open;
+    open.reserve(static_cast<size_t>(nc) * 3);
+    for (int i = 0; i < nc; ++i) {
+        const int p0 = m.cell_ptr[i], nv = m.cell_ptr[i + 1] - p0;
+        for (int l = 0; l < nv; ++l) {
+            const uint64_t id = edge_id(m.cell_nodes[p0 + l], m.cell_nodes[p0 + (l + 1) % nv]);
+            auto it = open.find(id);
+            if (it == open.end()) {
+                open.emplace(id, Side{i, l});
+            } else {
+                nbr[4 * static_cast<size_t>(i) + l] = it->second.cell;
+                nbr[4 * static_cast<size_t>(it->second.cell) + it->second.local] = i;
+            }
+        }
+    }
+    for (int b = 0; b < bc.n_bedges; ++b) {
+        auto it = open.find(edge_id(bc.bedge_nodes[2 * b], bc.bedge_nodes[2 * b + 1]));
+        if (it == open.end()) {
+            *why = "boundary edge not on the mesh";
+            return FVLBM_ERR_BAD_BC;
+        }
+        nbr[4 * static_cast<size_t>(it->second.cell) + it->second.local] = -(b + 1);
+    }
+    std::vector<double> cxv(nc), cyv(nc), dc(2 * static_cast<size_t>(nc), 0.0);
+    for (int i = 0; i < nc; ++i) {
+        double ar;
+        cell_area_centroid(m, i, m.xy, &ar, &cxv[i], &cyv[i]);
+    }
+    std::fill(dxy, dxy + 2 * static_cast<size_t>(nn), 0.0);
+    std::vector<Dual> xyd(2 * static_cast<size_t>(nn));
+    for (size_t k = 0; k < xyd.size(); ++k) xyd[k] = Dual(m.xy[k], 0.0);
+    for (int i = 0; i < nc; ++i) {
+        const int p0 = m.cell_ptr[i], nv = m.cell_ptr[i + 1] - p0;
+        const int *nb = nbr.data() + 4 * static_cast<size_t>(i);
+        Dual nbx[4], nby[4];
+        for (int l = 0; l < nv; ++l)
+            if (nb[l] >= 0) {
+                nbx[l] = Dual(cxv[nb[l]]);
+                nby[l] = Dual(cyv[nb[l]]);
+            }
+        // adjoint . d(outputs) for the current seed
+        auto contract = [&](const CellGeo<Dual> &G) {
+            double s = 0.0;
+            for (int l = 0; l < nv; ++l) {
+                const size_t o = (4 * static_cast<size_t>(i) + l) * 2;
+                for (int c = 0; c < 2; ++c) {
+                    s += A.sn[o + c] * G.sn[2 * l + c].d + A.lsq[o + c] * G.lsq[2 * l + c].d +
+                         A.rown[o + c] * G.rown[2 * l + c].d + A.rnbr[o + c] * G.rnbr[2 * l + c].d;
+                }
+                if (nb[l] < 0 && nb[l] != kNone) {
+                    const int b = -nb[l] - 1;
+                    s += A.bnrm[2 * b] * G.nrm[2 * l].d + A.bnrm[2 * b + 1] * G.nrm[2 * l + 1].d +
+                         A.blen[b] * G.len[l].d;
+                }
+            }
+            return s;
+        };
+        CellGeo<Dual> G;
+        for (int l = 0; l < nv; ++l) {  // own node coordinates
+            const int a = m.cell_nodes[p0 + l];
+            for (int c = 0; c < 2; ++c) {
+                xyd[2 * a + c].d = 1.0;
+                cell_geometry<Dual>(m, i, xyd.data(), nb, nbx, nby, &G);
+                xyd[2 * a + c].d = 0.0;
+                dxy[2 * a + c] += contract(G);
+            }
+        }
+        for (int l = 0; l < nv; ++l) {  // neighbour centroids
+            if (nb[l] < 0) continue;
+            for (int c = 0; c < 2; ++c) {
+                (c == 0 ? nbx[l] : nby[l]).d = 1.0;
+                cell_geometry<Dual>(m, i, xyd.data(), nb, nbx, nby, &G);
+                (c == 0 ? nbx[l] : nby[l]).d = 0.0;
+                dc[2 * static_cast<size_t>(nb[l]) + c] += contract(G);
+            }
+        }
+    }
+    // centroid adjoints to the nodes of their cells
+    for (int j = 0; j < nc; ++j) {
+        const int p0 = m.cell_ptr[j], nv = m.cell_ptr[j + 1] - p0;
+        for (int l = 0; l < nv; ++l) {
+            const int a = m.cell_nodes[p0 + l];
+            for (int c = 0; c < 2; ++c) {
+                xyd[2 * a + c].d = 1.0;
+                Dual ar, cx, cy;
+                cell_area_centroid<Dual>(m, j, xyd.data(), &ar, &cx, &cy);
+                xyd[2 * a + c].d = 0.0;
+                dxy[2 * a + c] += dc[2 * static_cast<size_t>(j)] * cx.d + dc[2 * static_cast<size_t>(j) + 1] * cy.d;
+            }
+        }
+    }
+    return FVLBM_OK;
+}
+
 template int prepare_instance_t<double>(const fvlbm_mesh &, const fvlbm_bc &, const fvlbm_params &,
                                         const double *, PreparedT<double> *, std::string *);
 template int prepare_instance_t<Dual>(const fvlbm_mesh &, const fvlbm_bc &, const fvlbm_params &,

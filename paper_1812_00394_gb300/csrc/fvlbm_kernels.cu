@@ -1387,7 +1387,7 @@ struct InstInfo {
     int cell_off, tile_off, bface_off;
     double dt, rho0, uref, lref, alpha_deg, nu;
     std::vector<int> bedge_of;   // boundary face -> input edge (local)
-    std::shared_ptr<MeshCopy> mesh;  // tangent handles only
+    std::shared_ptr<MeshCopy> mesh;  // FP64 and tangent handles (shape derivatives)
 };
 
 struct KernelTimer {
@@ -2187,7 +2187,7 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
         I.nu = params[q].nu;
         I.bedge_of = p.bedge_of;
         I.n_nodes = meshes[q].n_nodes;
-        if (prec == FVLBM_FP64_TANGENT) {
+        if (prec == FVLBM_FP64_TANGENT || prec == FVLBM_FP64) {  // shape derivatives need the mesh
             const fvlbm_mesh &M = meshes[q];
             const fvlbm_bc &B = bcs[q];
             auto mc = std::make_shared<MeshCopy>();
@@ -2662,8 +2662,8 @@ int fvlbm_forces(fvlbm_handle *h, int instance, double *out, double *cp) {
 }
 
 int fvlbm_adjoint(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
-                  double *dJ_dbedge_val) {
-    return adjoint_impl(h, instance, n_steps, w, J, dJ_df, dJ_dbedge_val);
+                  double *dJ_dbedge_val, double *dJ_dxy) {
+    return adjoint_impl(h, instance, n_steps, w, J, dJ_df, dJ_dbedge_val, dJ_dxy);
 }
 
 int fvlbm_tangent_seed(fvlbm_handle *h, int instance, const double *dbedge_val, const double *df) {

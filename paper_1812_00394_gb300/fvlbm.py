@@ -109,7 +109,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_get_f_tangent.argtypes = [vp, i, vp]
     lib.fvlbm_tangent_seed_nodes.argtypes = [vp, i, vp]
     lib.fvlbm_forces_tangent.argtypes = [vp, i, d, vp, vp]
-    lib.fvlbm_adjoint.argtypes = [vp, i, i, vp, vp, vp, vp]
+    lib.fvlbm_adjoint.argtypes = [vp, i, i, vp, vp, vp, vp, vp]
     lib.fvlbm_destroy.argtypes = [vp]
     lib.fvlbm_destroy.restype = None
     lib.fvlbm_strerror.argtypes = [i]
@@ -278,18 +278,21 @@ def fvlbm_forces_tangent(h, instance: int = 0, dalpha: float = 0.0) -> tuple[dic
     return dict(zip(keys, out)), dict(zip(keys, dout))
 
 
-def fvlbm_adjoint(h, instance: int, n_steps: int, w_cd: float = 0.0, w_cl: float = 0.0):
+def fvlbm_adjoint(h, instance: int, n_steps: int, w_cd: float = 0.0, w_cl: float = 0.0,
+                  n_nodes: int | None = None):
     """Reverse-mode gradient of J = w_cd C_D + w_cl C_L after n_steps FP64 steps from the
-    current state: (J, dJ/df [n_cells, 9], dJ/dbedge_val [n_bedges, 5]).  The handle's state is
-    unchanged."""
+    current state: (J, dJ/df [n_cells, 9], dJ/dbedge_val [n_bedges, 5], dJ/dxy [n_nodes, 2] or
+    None).  dJ/dxy is computed when n_nodes (the instance's node count) is given.  The handle's
+    state is unchanged."""
     n, nb, _ = fvlbm_info(h, instance)
     w = np.array([w_cd, w_cl], np.float64)
     J = C.c_double()
     df = np.empty((n, Q))
     db = np.empty((nb, 5))
-    _check(load().fvlbm_adjoint(h, instance, int(n_steps), _p(w), C.byref(J), _p(df), _p(db)),
-           "fvlbm_adjoint")
-    return J.value, df, db
+    dxy = None if n_nodes is None else np.empty((int(n_nodes), 2))
+    _check(load().fvlbm_adjoint(h, instance, int(n_steps), _p(w), C.byref(J), _p(df), _p(db),
+                                _p(dxy)), "fvlbm_adjoint")
+    return J.value, df, db, dxy
 
 
 def fvlbm_save_state(h) -> bytes:
@@ -378,6 +381,7 @@ class Solver:
             self.h = fvlbm_create_batch([p.mesh for p in packs], [p.bc for p in packs],
                                         [p.params for p in packs], device, stream)
         self.n = len(cases)
+        self.n_nodes = [int(c.mesh.n_nodes) for c in cases]
         self.cells = [fvlbm_info(self.h, i)[0] for i in range(self.n)]
 
     def close(self):
@@ -436,5 +440,8 @@ class Solver:
     def forces_tangent(self, i: int = 0, dalpha: float = 0.0):
         return fvlbm_forces_tangent(self.h, i, dalpha)
 
-    def adjoint(self, n_steps: int, w_cd: float = 0.0, w_cl: float = 0.0, i: int = 0):
-        return fvlbm_adjoint(self.h, i, n_steps, w_cd, w_cl)
+    def adjoint(self, n_steps: int, w_cd: float = 0.0, w_cl: float = 0.0, i: int = 0,
+                shape: bool = False):
+        """(J, dJ/df, dJ/dbedge_val, dJ/dxy or None); see fvlbm_adjoint."""
+        nn = self.n_nodes[i] if shape else None
+        return fvlbm_adjoint(self.h, i, n_steps, w_cd, w_cl, nn)

@@ -1,11 +1,13 @@
-"""CPU checks of the tangent path's host side: the dual-number geometry.
+"""CPU checks of the host side of the derivative paths: the dual-number geometry of the tangent
+and the reverse-mode geometry of the adjoint.
 
 The tangent (FVLBM_FP64_TANGENT) differentiates the mesh preprocessing with respect to node
 positions by running it with dual numbers.  A small native program (tests/native) built here
 with g++ from the library's own host sources compares those derivatives with central
 differences of the double-precision preprocessing, for an interior node of a jittered cavity
 and for a wall node of an airfoil C-mesh (where the wall distance and the boundary normals
-move too)."""
+move too).  A second one checks the adjoint's reverse-mode geometry (geometry_adjoint) against
+that forward mode by the dot-product identity <A, J v> = <J^T A, v> for random A and v."""
 import os
 import shutil
 import struct
@@ -76,3 +78,36 @@ def test_dual_number_operations(tmp_path):
     for name in ("mul_add", "div", "sqrt", "tanh", "fmin_fmax", "neg_sub"):
         assert out[name] < 1e-8, (name, out[name])
     assert out["sqrt0"] == 0.0
+
+
+@pytest.fixture(scope="module")
+def adjoint_checker(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    out = str(tmp_path_factory.mktemp("geoadj") / "geometry_adjoint_check")
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-fopenmp", "-I", os.path.join(ROOT, "include"),
+                           "-I", CSRC, os.path.join(HERE, "native", "geometry_adjoint_check.cpp"),
+                           os.path.join(CSRC, "fvlbm_host.cpp"), "-o", out])
+    return out
+
+
+@pytest.mark.parametrize("which", ["cavity_jitter", "naca", "bfs"])
+def test_geometry_adjoint_dot_product(adjoint_checker, tmp_path, which):
+    if which == "cavity_jitter":
+        m = mg.cavity_quad(12, re=400.0, jitter=0.2, seed=7).mesh.normalized()
+    elif which == "naca":
+        m = mg.naca0012_cmesh(n_target=1500, re_c=1e4, alpha_deg=4.0).mesh.normalized()
+    else:
+        m = mg.bfs_hybrid(n_target=1500).mesh.normalized()
+    path = str(tmp_path / "mesh.bin")
+    with open(path, "wb") as fh:
+        fh.write(struct.pack("<i", m.n_nodes)); fh.write(m.xy.astype("<f8").tobytes())
+        fh.write(struct.pack("<i", m.n_cells)); fh.write(m.cell_ptr.astype("<i4").tobytes())
+        fh.write(m.cell_nodes.astype("<i4").tobytes())
+        fh.write(struct.pack("<i", m.n_bedges)); fh.write(m.bedge_nodes.astype("<i4").tobytes())
+        fh.write(m.bedge_type.astype("<i4").tobytes()); fh.write(m.bedge_val.astype("<f8").tobytes())
+        fh.write(struct.pack("<Q", 12345))
+    res = subprocess.run([adjoint_checker, path], capture_output=True, text=True, check=True).stdout
+    out = {ln.split()[0]: float(ln.split()[1]) for ln in res.splitlines()}
+    assert abs(out["forward"]) > 0
+    assert abs(out["forward"] - out["reverse"]) <= 1e-10 * abs(out["forward"]), out

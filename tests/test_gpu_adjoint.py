@@ -67,7 +67,7 @@ def test_adjoint_dot_product_against_tangent(name, n):
     s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
     s.step(warm)
     f_before = s.get_f()
-    J, dJdf, dJdb = s.adjoint(n, W[0], W[1])
+    J, dJdf, dJdb, _ = s.adjoint(n, W[0], W[1])
     # the handle's state does not move
     np.testing.assert_array_equal(s.get_f(), f_before)
     Jt, dJt = _tangent_dJ(case, warm, n, g, d)
@@ -79,12 +79,60 @@ def test_adjoint_dot_product_against_tangent(name, n):
     s.close()
 
 
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("n", [0, 6])
+def test_adjoint_shape_gradient_against_tangent(name, n):
+    """dJ/dxy (reverse through the step and the host preprocessing) against the tangent of a
+    random displacement of every node (forward through both), at fixed dt and initial state."""
+    case = CASES[name]()
+    warm = 10
+    m = case.mesh.normalized()
+    v = 1e-3 * np.random.default_rng(7 + n).standard_normal((m.n_nodes, 2))
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    s.step(warm)
+    J, _, _, dxy = s.adjoint(n, W[0], W[1], shape=True)
+    s.close()
+    t = fvlbm.Solver(case, precision=TAN, device=0)
+    t.step(warm)
+    t.tangent_seed_nodes(v)
+    t.step(n)
+    val, dv = t.forces_tangent(dalpha=0.0)
+    t.close()
+    dJt = W[0] * dv["cd"] + W[1] * dv["cl"]
+    adj = float(np.sum(dxy * v))
+    assert abs(J - (W[0] * val["cd"] + W[1] * val["cl"])) <= 1e-10 * abs(J)
+    assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)
+
+
+def test_adjoint_shape_gradient_of_one_wall_node():
+    """The NACA 0012 use: dJ/d(normal displacement of one wall node) from one adjoint solve
+    equals the tangent's derivative for that displacement."""
+    case = _naca_laminar()
+    m = case.mesh.normalized()
+    wall = np.unique(m.bedge_nodes[m.bedge_type == mg.BC_WALL])
+    node = int(wall[np.argmin(np.abs(m.xy[wall, 0] - 0.3) + 10 * (m.xy[wall, 1] < 0))])
+    v = np.zeros((m.n_nodes, 2))
+    v[node] = (0.0, 1.0)
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    s.step(5)
+    _, _, _, dxy = s.adjoint(20, W[0], W[1], shape=True)
+    s.close()
+    t = fvlbm.Solver(case, precision=TAN, device=0)
+    t.step(5)
+    t.tangent_seed_nodes(v)
+    t.step(20)
+    _, dv = t.forces_tangent(dalpha=0.0)
+    t.close()
+    dJt = W[0] * dv["cd"] + W[1] * dv["cl"]
+    assert abs(dxy[node, 1] - dJt) <= 1e-8 * abs(dJt), (dxy[node, 1], dJt)
+
+
 def test_adjoint_value_matches_fp64_forces():
     case = _naca_laminar()
     s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
     s.step(10)
-    J, _, _ = s.adjoint(12, 1.0, 0.0)
-    JL, _, _ = s.adjoint(12, 0.0, 1.0)
+    J, _, _, _ = s.adjoint(12, 1.0, 0.0)
+    JL, _, _, _ = s.adjoint(12, 0.0, 1.0)
     s.step(12)
     ref = s.forces()
     assert abs(J - ref["cd"]) <= 1e-10 * abs(ref["cd"])
@@ -108,7 +156,7 @@ def test_adjoint_lid_speed_vs_fd():
     d = np.zeros((m.n_bedges, 5))
     d[m.bedge_val[:, 1] != 0.0, 1] = 1.0
     s = solver(U)
-    _, _, dJdb = s.adjoint(n, *W)
+    _, _, dJdb, _ = s.adjoint(n, *W)
     vals = []
     for u in (U + h, U - h):
         x = solver(u)
@@ -139,3 +187,10 @@ def test_adjoint_rejects_unsupported_handles():
         s.adjoint(-1, 1.0, 0.0)
     assert e.value.code == fvlbm.FVLBM_ERR_BAD_PARAM
     s.close()
+    # shape gradients of periodic meshes are not built; the other outputs are
+    per = fvlbm.Solver(mg.Case(mg.periodic_box(8), nu=1e-3, cfl=0.5), precision=FP64, device=0)
+    per.adjoint(2, 1.0, 0.0)
+    with pytest.raises(fvlbm.FvlbmError) as e:
+        per.adjoint(2, 1.0, 0.0, shape=True)
+    assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
+    per.close()
