@@ -293,15 +293,22 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
  *                  of the force): the gradient whose inner product with a node displacement is
  *                  what fvlbm_tangent_seed_nodes gives for it.  Not for meshes with periodic
  *                  pairs (FVLBM_ERR_NOT_SUPPORTED).
- * Neither the state nor the step count of the handle changes.  The steps are recomputed from
- * checkpoints: about 3 n_steps forward steps and n_steps adjoint steps, with (2 sqrt(n_steps)
- * + 24) * 9 doubles per cell of device memory (32 more per cell with dJ_dxy) allocated for the
- * call and freed before it returns; dJ_dxy adds one pass over the cells on the host.
+ * Neither the state nor the step count of the handle changes.  The call runs n_steps forward
+ * steps that keep their stage values (99 doubles per cell and step) and n_steps adjoint steps.
+ * Where the stage values of all steps do not fit the adjoint budget (fvlbm_set_adjoint_budget;
+ * default half the free device memory), the steps are taken in segments of as many steps as
+ * fit: a first sweep keeps f at each segment start and each segment runs again before its
+ * reverse sweep (2 n_steps forward steps).  The device memory is allocated for the call and
+ * freed before it returns (about 60 + 99 K doubles per cell for segments of K steps, 32 more
+ * with dJ_dxy); dJ_dxy adds one pass over the cells on the host.
  * Valid on FVLBM_FP64 handles whose instances are all laminar, with the IMEX scheme, one dt per
  * instance and no limiter or per-stage variant; else FVLBM_ERR_NOT_SUPPORTED.  Synchronises.
  * Errors: BAD_PARAM (w NULL, n_steps < 0, bad instance), NOT_SUPPORTED, OOM, CUDA. */
 int fvlbm_adjoint(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
                   double *dJ_dbedge_val, double *dJ_dxy);
+/* The device memory fvlbm_adjoint may use for stage values, in bytes (0: half the free device
+ * memory at the time of the call, the default).  Errors: BAD_PARAM. */
+int fvlbm_set_adjoint_budget(fvlbm_handle *h, long long bytes);
 
 /* ---------------------------------------------------------------------------------------------
  * Checkpoint / resume and divergence rollback (no counterpart in the paper).

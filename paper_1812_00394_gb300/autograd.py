@@ -11,11 +11,16 @@ the ratio sets the far-field omega_b = k_b / (nu ratio).  The differentiated map
 initial state and the time step of the base case fixed (they are inputs of the time
 integration, not functions of p).
 
-The backward pass is the library's forward-mode tangent (precision FVLBM_FP64_TANGENT): one
-batched tangent solve with one instance per parameter gives every column of the Jacobian
-J = d(C_L, C_D)/dp at once, and the gradient is grad_output @ J.  For a handful of outputs
-and up to a few hundred parameters this costs one batched solve of twice the FP64 work; the
-derivatives are the same ones a reverse-mode adjoint of the discrete step would give.
+Two backward passes compute the same derivatives of the discrete step:
+  - "tangent" (any case): the library's forward mode (precision FVLBM_FP64_TANGENT); one batched
+    tangent solve with one instance per parameter gives every column of the Jacobian
+    J = d(C_L, C_D)/dp at once, and the gradient is grad_output @ J.  Its cost grows with the
+    number of parameters.
+  - "adjoint" (laminar cases): the library's reverse mode (fvlbm_adjoint); one adjoint solve of
+    J_w = grad_output . (C_L, C_D) gives dJ_w/d(boundary values) and dJ_w/d(node positions), and
+    the gradient is their projection on the parameters plus the explicit dependence of the drag
+    and lift directions on alpha.  Its cost does not grow with the number of wall nodes.
+The default ("auto") takes the adjoint for laminar cases and the tangent otherwise.
 """
 from __future__ import annotations
 
@@ -32,7 +37,12 @@ from .meshgen import BC_FARFIELD, BC_WALL
 class AirfoilForces:
     """The parameter-to-(C_L, C_D) map of one airfoil case (see the module docstring)."""
 
-    def __init__(self, base_case, wall_nodes, steps: int, device: int = 0):
+    def __init__(self, base_case, wall_nodes, steps: int, device: int = 0, mode: str = "auto"):
+        if mode not in ("auto", "tangent", "adjoint"):
+            raise ValueError(f"unknown backward mode {mode!r}")
+        if mode == "adjoint" and base_case.sst:
+            raise ValueError("the adjoint backward needs a laminar case")
+        self.mode = ("tangent" if base_case.sst else "adjoint") if mode == "auto" else mode
         self.base = dataclasses.replace(base_case, mesh=base_case.mesh.normalized())
         m = self.base.mesh
         self.steps = int(steps)
@@ -93,9 +103,8 @@ class AirfoilForces:
         s.close()
         return np.array([f["cl"], f["cd"]])
 
-    def jacobian(self, p: np.ndarray) -> np.ndarray:
-        """J[o, q] = d output_o / d p_q (outputs C_L, C_D) from one batched tangent solve."""
-        case = self.case_at(p)
+    def _bval_directions(self, case, p: np.ndarray):
+        """d(boundary values)/d alpha and d(boundary values)/d ratio at p."""
         m = case.mesh
         nb = m.n_bedges
         d_alpha = np.zeros((nb, 5))
@@ -103,6 +112,29 @@ class AirfoilForces:
         d_alpha[self.ff, 2] = m.bedge_val[self.ff, 1]
         d_ratio = np.zeros((nb, 5))
         d_ratio[self.ff, 4] = -m.bedge_val[self.ff, 4] / float(p[1])
+        return d_alpha, d_ratio
+
+    def vjp(self, p: np.ndarray, g: np.ndarray, out: np.ndarray) -> np.ndarray:
+        """g @ d(C_L, C_D)/dp from one adjoint solve (laminar cases); out = (C_L, C_D) at p."""
+        case = self.case_at(p)
+        d_alpha, d_ratio = self._bval_directions(case, p)
+        s = fvlbm.Solver(case, precision=fvlbm.FVLBM_FP64, device=self.device, kernel_path=1)
+        # J_w = g0 C_L + g1 C_D
+        _, _, dbv, dxy = s.adjoint(self.steps, w_cd=float(g[1]), w_cl=float(g[0]), shape=True)
+        s.close()
+        # dC_D/dalpha = C_L and dC_L/dalpha = -C_D through the drag and lift directions
+        proj = float(g[1]) * out[0] - float(g[0]) * out[1]
+        grad = np.empty(self.n_params())
+        grad[0] = float(np.sum(dbv * d_alpha)) + proj
+        grad[1] = float(np.sum(dbv * d_ratio))
+        grad[2:] = np.einsum("jc,jc->j", dxy[self.wall_nodes], self.normals)
+        return grad
+
+    def jacobian(self, p: np.ndarray) -> np.ndarray:
+        """J[o, q] = d output_o / d p_q (outputs C_L, C_D) from one batched tangent solve."""
+        case = self.case_at(p)
+        m = case.mesh
+        d_alpha, d_ratio = self._bval_directions(case, p)
         dirs = [{"dbedge_val": d_alpha, "dalpha": 1.0}, {"dbedge_val": d_ratio}]
         for j, nd in enumerate(self.wall_nodes):
             dxy = np.zeros_like(m.xy)
@@ -116,13 +148,17 @@ class _ForcesFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, p, model):
         pn = p.detach().cpu().double().numpy()
-        ctx.model, ctx.pn = model, pn
-        return torch.as_tensor(model.value(pn), dtype=p.dtype)
+        out = model.value(pn)
+        ctx.model, ctx.pn, ctx.out = model, pn, out
+        return torch.as_tensor(out, dtype=p.dtype)
 
     @staticmethod
     def backward(ctx, grad_out):
-        J = ctx.model.jacobian(ctx.pn)
-        g = grad_out.detach().cpu().double().numpy() @ J
+        gn = grad_out.detach().cpu().double().numpy()
+        if ctx.model.mode == "adjoint":
+            g = ctx.model.vjp(ctx.pn, gn, ctx.out)
+        else:
+            g = gn @ ctx.model.jacobian(ctx.pn)
         return torch.as_tensor(g, dtype=grad_out.dtype), None
 
 

@@ -9,93 +9,98 @@
 // with A(f) = sum over faces of (e . n dl / A) times the upwind linear face value built from
 // the least-squares gradient, boundary faces taking the boundary values of Part I.  The adjoint
 // runs these in reverse: the linear flux and gradient operators are transposed by gathering
-// over each cell's faces (the neighbour's view of a shared face comes from its back slot), and
-// the per-cell nonlinear maps (R, S1, S2, the boundary values) are transposed through their
-// local Jacobians, evaluated column by column with the dual-number type of the tangent path.
-// States are recomputed from checkpoints (every K-th state kept, K ~ sqrt(n_steps); one
-// segment of K states rebuilt at a time), so the storage is about 2 sqrt(n_steps) states.
+// over each cell's faces (the neighbour's view of a shared face comes from its back slot); the
+// per-cell maps R, S1, S2 and the boundary values are transposed in closed form (they are affine
+// but for f^eq, whose transposed Jacobian is written out below).
+// The stage values of whole segments of steps stay in device memory (see adjoint_impl for the
+// plan): with room for all steps the forward steps run once, else twice.
 
 namespace fvlbm {
 
-// ---- per-cell maps, written out exactly as the forward kernels evaluate them
-template <class T>
-__device__ __forceinline__ void adj_relax(const T *f0, T rho0, T dt, T tau, T *s1) {
-#pragma unroll
-    for (int a = 0; a < kQ; ++a) s1[a] = f0[a];
-    relax9(s1, rho0, dt, tau);
-}
-
-// Stage-1 algebra of the two-pass path (stage_algebra, J = 1, f^n given).
-template <class T>
-__device__ __forceinline__ void adj_stage1(const T *f0, const T *acc, T rho0, T dt, T tau, T *f2, T *B,
-                                           T *C) {
-    const T itau = T(1) / tau;
-    const T dt6 = dt * T(1.0 / 6.0);
-    T eq[kQ], X[kQ], dgc1[kQ], dr, r, u, v;
-    const T z = dt * itau;
-    const T zq = z * T(0.25);
-    const T inv = T(1) / (T(1) + zq);
-    moments(f0, rho0, dr, r, u, v);
-    feq_dev(dr, r, u, v, eq);
-    const T s1 = z * inv;
-#pragma unroll
-    for (int a = 0; a < kQ; ++a) dgc1[a] = (eq[a] - f0[a]) * s1;
-#pragma unroll
-    for (int a = 0; a < kQ; ++a) X[a] = f0[a] - T(0.5) * dt * acc[a];
-    moments(X, rho0, dr, r, u, v);
-    feq_dev(dr, r, u, v, eq);
-    const T s2 = z * inv;
+// ---- per-cell maps.  Each is affine in its inputs except through the equilibrium of a stage
+// value X, f^eq(X) = feq_dev(moments(X)), so its adjoint needs only the transposed Jacobian of
+// that map, formed in closed form:
+//   f^eq_a = w_a [drho + rho P_a],  P_a = 3 e_a.u + 4.5 (e_a.u)^2 - 1.5 u.u,  u = j / rho,
+//   dP_a/du = (3 + 9 e_a.u) e_a - 3 u,  du/dj = 1/rho,  du/drho = -u/rho,
+// and lam_b += l_drho + e_b . l_j for the moments drho = sum d, j = sum e d.
+// For f^eq_a = w_a [d + r P_a(u, v)] with d and r moving together (d r = d d): the adjoints
+// l_d = sum_a mu_a w_a (1 + P_a) and l_(u, v) = sum_a mu_a w_a r dP_a/d(u, v).
+__device__ __forceinline__ void feq_uv_vjp(double r, double u, double v, const double *mu, double &l_d,
+                                           double &l_u, double &l_v) {
+    const double uu = 1.5 * (u * u + v * v);
+    l_d = l_u = l_v = 0.0;
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
-        f2[a] = (X[a] + zq * eq[a]) * inv;
-        const T dgc2 = (eq[a] - X[a]) * s2;
-        B[a] = X[a] + T(1.0 / 3.0) * (dgc1[a] + dgc2);
-        C[a] = dt6 * acc[a];
+        const double eu = edot<double>(a, u, v);
+        const double wm = w_of<double>(a) * mu[a];
+        l_d += wm * (1.0 + 3.0 * eu + 4.5 * eu * eu - uu);
+        const double c = wm * r * (3.0 + 9.0 * eu);
+        l_u += c * ex_of(a) - 3.0 * wm * r * u;
+        l_v += c * ey_of(a) - 3.0 * wm * r * v;
     }
 }
 
-// Stage-2 solve from X = B - dt/2 acc (stage_algebra, J = 2).
-template <class T>
-__device__ __forceinline__ void adj_stage2(const T *X, T rho0, T dt, T tau, T *f3) {
-    const T itau = T(1) / tau;
-    const T dt3 = dt * T(1.0 / 3.0);
-    T eq[kQ], dr, r, u, v;
-    moments(X, rho0, dr, r, u, v);
-    feq_dev(dr, r, u, v, eq);
-    const T zt = dt3 * itau;
-    const T inv = T(1) / (T(1) + zt);
+// lam += adjoint of the moments (drho, rho, u, v) of X given l_d (drho and rho together) and
+// l_(u, v), with u = j / rho.
+__device__ __forceinline__ void moments_vjp(double r, double u, double v, double l_d, double l_u, double l_v,
+                                            double *lam) {
+    const double ir = 1.0 / r;
+    const double l_jx = l_u * ir, l_jy = l_v * ir;
+    l_d -= (l_u * u + l_v * v) * ir;
 #pragma unroll
-    for (int a = 0; a < kQ; ++a) f3[a] = (X[a] + zt * eq[a]) * inv;
+    for (int a = 0; a < kQ; ++a) lam[a] += l_d + edot<double>(a, l_jx, l_jy);
 }
 
-// Boundary values of one face as a function of the owner's f and of (rho_b, u_b, v_b).
-template <class T>
-__device__ __forceinline__ void adj_bvals(int type, const T *bv3, T snx, T sny, const T *fP, T rho0,
-                                          T *fb) {
-    T dr, r, u, v;
-    moments(fP, rho0, dr, r, u, v);
-    const T bvl[5] = {bv3[0], bv3[1], bv3[2], T(0), T(0)};
-    boundary_values(type, bvl, 0, 1, snx, sny, fP, dr, r, u, v, rho0, fb);
+// lam += (d f^eq(moments(X)) / d X)^T mu
+__device__ __forceinline__ void feq_vjp(const double *X, double rho0, const double *mu, double *lam) {
+    double dr, r, u, v, l_d, l_u, l_v;
+    moments(X, rho0, dr, r, u, v);
+    feq_uv_vjp(r, u, v, mu, l_d, l_u, l_v);
+    moments_vjp(r, u, v, l_d, l_u, l_v, lam);
 }
 
-// lf += (d fb / d fP)^T c and lb3 += (d fb / d(rho_b, u_b, v_b))^T c for one boundary face.
+// lf += (d fb / d fP)^T c and lb3 += (d fb / d(rho_b, u_b, v_b))^T c for one boundary face whose
+// values fb = boundary_values(type, ...) are formed from the owner's fP:
+//   wall, inlet:  fb = fP + f^eq(drho_P, rho_P, u_b, v_b) - f^eq(moments(fP))
+//   outlet:       fb = fP + f^eq(rho_b - rho0, rho_b, u_P, v_P) - f^eq(moments(fP))
+//   far field:    fb_a = f^eq(rho_b - rho0, rho_b, u_b, v_b)_a where e_a . n < 0, else fP_a
 __device__ __forceinline__ void adj_bvals_T(int type, const double *bv3, double snx, double sny,
                                             const double *fP, double rho0, const double *c,
                                             double *lf, double *lb3) {
-    for (int k = 0; k < kQ + 3; ++k) {
-        Dual fd[kQ], bd[3], fb[kQ];
+    double dr, r, u, v, l_d, l_u, l_v;
+    moments(fP, rho0, dr, r, u, v);
+    const double rb = bv3[0], ub = bv3[1], vb = bv3[2];
+    if (type == FVLBM_BC_WALL || type == FVLBM_BC_INLET || type == FVLBM_BC_OUTLET) {
+        double mneg[kQ];
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) fd[a] = Dual(fP[a], k == a ? 1.0 : 0.0);
+        for (int a = 0; a < kQ; ++a) {
+            lf[a] += c[a];
+            mneg[a] = -c[a];
+        }
+        feq_vjp(fP, rho0, mneg, lf);
+        if (type == FVLBM_BC_OUTLET) {  // f^eq at rho_b and the owner's velocity
+            feq_uv_vjp(rb, u, v, c, l_d, l_u, l_v);
+            moments_vjp(r, u, v, 0.0, l_u, l_v, lf);
+            lb3[0] += l_d;
+        } else {  // f^eq at the owner's density and the boundary velocity
+            feq_uv_vjp(r, ub, vb, c, l_d, l_u, l_v);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) bd[q] = Dual(bv3[q], k == kQ + q ? 1.0 : 0.0);
-        adj_bvals<Dual>(type, bd, Dual(snx), Dual(sny), fd, Dual(rho0), fb);
-        double s = 0;
+            for (int a = 0; a < kQ; ++a) lf[a] += l_d;
+            lb3[1] += l_u;
+            lb3[2] += l_v;
+        }
+    } else {
+        double cin[kQ];
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) s += fb[a].d * c[a];
-        if (k < kQ)
-            lf[k] += s;
-        else if (lb3 != nullptr)
-            lb3[k - kQ] += s;
+        for (int a = 0; a < kQ; ++a) {
+            const bool in = edot<double>(a, snx, sny) < 0.0;
+            cin[a] = in ? c[a] : 0.0;
+            if (!in) lf[a] += c[a];
+        }
+        feq_uv_vjp(rb, ub, vb, cin, l_d, l_u, l_v);
+        lb3[0] += l_d;
+        lb3[1] += l_u;
+        lb3[2] += l_v;
     }
 }
 
@@ -139,57 +144,43 @@ __device__ __forceinline__ void adj_bv3(const Geo<double> &G, int b, double *bv3
     for (int q = 0; q < 3; ++q) bv3[q] = G.bval[q * G.nbt + b];
 }
 
-// ---- transposed flux: la (adjoint of acc) -> lf += (d acc / d f)^T la, lg = (d acc / d g)^T la
-__global__ void __launch_bounds__(kTile) k_adj_fluxT(const double *__restrict__ fs, const double *__restrict__ la,
-                                                     double *__restrict__ lf, double *__restrict__ lg,
-                                                     double *__restrict__ lbval, Geo<double> G,
+// ---- transposed flux over interior faces: la (adjoint of acc) -> lf += (d acc / d f)^T la,
+// lg = (d acc / d g)^T la (boundary faces: k_adj_bndT)
+__global__ void __launch_bounds__(kTile) k_adj_fluxT(const double *__restrict__ la, double *__restrict__ lf,
+                                                     double *__restrict__ lg, Geo<double> G,
                                                      const int *__restrict__ back) {
     const int j = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
-    const double rho0 = G.ip[G.tile_inst[blockIdx.x]].rho0;
-    double lfj[kQ], lgx[kQ], lgy[kQ], laj[kQ], fj[kQ];
+    double lfj[kQ], lgx[kQ], lgy[kQ], laj[kQ];
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
         lfj[a] = lf[a * np + j];
         lgx[a] = lgy[a] = 0.0;
         laj[a] = la[a * np + j];
-        fj[a] = fs[a * np + j];
     }
     for (int m = 0; m < 4; ++m) {
         const int nb = G.nbr[m * np + j];
-        if (nb == kNone) continue;
+        if (nb < 0) continue;  // no face, or a boundary face
         const double snx = G.sn[(2 * m) * np + j], sny = G.sn[(2 * m + 1) * np + j];
-        if (nb >= 0) {
-            const double rox = G.rown[(2 * m) * np + j], roy = G.rown[(2 * m + 1) * np + j];
-            const int b = back[m * np + j];
-            const double six = G.sn[(2 * b) * np + nb], siy = G.sn[(2 * b + 1) * np + nb];
-            const double rix = G.rnbr[(2 * b) * np + nb], riy = G.rnbr[(2 * b + 1) * np + nb];
+        const double rox = G.rown[(2 * m) * np + j], roy = G.rown[(2 * m + 1) * np + j];
+        const int b = back[m * np + j];
+        const double six = G.sn[(2 * b) * np + nb], siy = G.sn[(2 * b + 1) * np + nb];
+        const double rix = G.rnbr[(2 * b) * np + nb], riy = G.rnbr[(2 * b + 1) * np + nb];
 #pragma unroll
-            for (int a = 1; a < kQ; ++a) {
-                const double en = edot<double>(a, snx, sny);
-                if (en >= 0.0) {  // this cell's own flux took its own reconstruction
-                    lfj[a] += en * laj[a];
-                    lgx[a] += en * rox * laj[a];
-                    lgy[a] += en * roy * laj[a];
-                }
-                const double eni = edot<double>(a, six, siy);
-                if (!(eni >= 0.0)) {  // the neighbour's flux through this face took this cell's
-                    const double lai = la[a * np + nb];
-                    lfj[a] += eni * lai;
-                    lgx[a] += eni * rix * lai;
-                    lgy[a] += eni * riy * lai;
-                }
+        for (int a = 1; a < kQ; ++a) {
+            const double en = edot<double>(a, snx, sny);
+            if (en >= 0.0) {  // this cell's own flux took its own reconstruction
+                lfj[a] += en * laj[a];
+                lgx[a] += en * rox * laj[a];
+                lgy[a] += en * roy * laj[a];
             }
-        } else {
-            const int bf = -nb - 1;
-            double c[kQ], bv3[3];
-#pragma unroll
-            for (int a = 0; a < kQ; ++a) c[a] = edot<double>(a, snx, sny) * laj[a];
-            adj_bv3(G, bf, bv3);
-            double lb3[3] = {0, 0, 0};
-            adj_bvals_T(G.btype[bf], bv3, snx, sny, fj, rho0, c, lfj, lb3);
-            if (lbval != nullptr)
-                for (int q = 0; q < 3; ++q) lbval[q * G.nbt + bf] += lb3[q];
+            const double eni = edot<double>(a, six, siy);
+            if (!(eni >= 0.0)) {  // the neighbour's flux through this face took this cell's
+                const double lai = la[a * np + nb];
+                lfj[a] += eni * lai;
+                lgx[a] += eni * rix * lai;
+                lgy[a] += eni * riy * lai;
+            }
         }
     }
 #pragma unroll
@@ -200,46 +191,73 @@ __global__ void __launch_bounds__(kTile) k_adj_fluxT(const double *__restrict__ 
     }
 }
 
-// ---- transposed gradient: lf += (d g / d f)^T lg
-__global__ void __launch_bounds__(kTile) k_adj_gradT(const double *__restrict__ fs, const double *__restrict__ lg,
-                                                     double *__restrict__ lf, double *__restrict__ lbval,
+// ---- transposed gradient, linear part: lf += (d g / d f)^T lg with the boundary values held
+// fixed (g_j = sum_m W_m (f_m - f_j)); their dependence on f_j is added by k_adj_bndT
+__global__ void __launch_bounds__(kTile) k_adj_gradT(const double *__restrict__ lg, double *__restrict__ lf,
                                                      Geo<double> G, const int *__restrict__ back) {
     const int j = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
-    const double rho0 = G.ip[G.tile_inst[blockIdx.x]].rho0;
-    double lfj[kQ], lgx[kQ], lgy[kQ], fj[kQ];
+    double lfj[kQ], lgx[kQ], lgy[kQ];
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
         lfj[a] = lf[a * np + j];
         lgx[a] = lg[(2 * a) * np + j];
         lgy[a] = lg[(2 * a + 1) * np + j];
-        fj[a] = fs[a * np + j];
     }
     for (int m = 0; m < 4; ++m) {
         const int nb = G.nbr[m * np + j];
         if (nb == kNone) continue;
         const double wx = G.lsq[(2 * m) * np + j], wy = G.lsq[(2 * m + 1) * np + j];
-        double c[kQ];
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) {
-            c[a] = wx * lgx[a] + wy * lgy[a];
-            lfj[a] -= c[a];  // g_j = sum_m W_m (f_m - f_j)
-        }
+        for (int a = 0; a < kQ; ++a) lfj[a] -= wx * lgx[a] + wy * lgy[a];
         if (nb >= 0) {
             const int b = back[m * np + j];
             const double wix = G.lsq[(2 * b) * np + nb], wiy = G.lsq[(2 * b + 1) * np + nb];
 #pragma unroll
             for (int a = 0; a < kQ; ++a)
                 lfj[a] += wix * lg[(2 * a) * np + nb] + wiy * lg[(2 * a + 1) * np + nb];
-        } else {
-            const int bf = -nb - 1;
-            double bv3[3], lb3[3] = {0, 0, 0};
-            adj_bv3(G, bf, bv3);
-            adj_bvals_T(G.btype[bf], bv3, G.sn[(2 * m) * np + j], G.sn[(2 * m + 1) * np + j], fj, rho0, c,
-                        lfj, lb3);
-            if (lbval != nullptr)
-                for (int q = 0; q < 3; ++q) lbval[q * G.nbt + bf] += lb3[q];
         }
+    }
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) lf[a * np + j] = lfj[a];
+}
+
+// ---- boundary faces: the face value f_bc(f_j, bval) enters the flux (weight e.n) and the
+// gradient (weight W_m); one transposed local Jacobian per face serves both:
+//   c = (e.n) la_j + W_m^T lg_j,  lf_j += (d f_bc / d f_j)^T c,  lbval += (d f_bc / d bval)^T c
+__global__ void __launch_bounds__(kTile) k_adj_bndT(const double *__restrict__ fs, const double *__restrict__ la,
+                                                    const double *__restrict__ lg, double *__restrict__ lf,
+                                                    double *__restrict__ lbval, Geo<double> G) {
+    const int j = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    int nbnd = 0;
+    for (int m = 0; m < 4; ++m) {
+        const int nb = G.nbr[m * np + j];
+        nbnd += (nb < 0 && nb != kNone) ? 1 : 0;
+    }
+    if (nbnd == 0) return;
+    const double rho0 = G.ip[G.tile_inst[blockIdx.x]].rho0;
+    double lfj[kQ], fj[kQ];
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+        lfj[a] = lf[a * np + j];
+        fj[a] = fs[a * np + j];
+    }
+    for (int m = 0; m < 4; ++m) {
+        const int nb = G.nbr[m * np + j];
+        if (nb >= 0 || nb == kNone) continue;
+        const int bf = -nb - 1;
+        const double snx = G.sn[(2 * m) * np + j], sny = G.sn[(2 * m + 1) * np + j];
+        const double wx = G.lsq[(2 * m) * np + j], wy = G.lsq[(2 * m + 1) * np + j];
+        double c[kQ], bv3[3], lb3[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < kQ; ++a)
+            c[a] = edot<double>(a, snx, sny) * la[a * np + j] + wx * lg[(2 * a) * np + j] +
+                   wy * lg[(2 * a + 1) * np + j];
+        adj_bv3(G, bf, bv3);
+        adj_bvals_T(G.btype[bf], bv3, snx, sny, fj, rho0, c, lfj, lb3);
+        if (lbval != nullptr)
+            for (int q = 0; q < 3; ++q) lbval[q * G.nbt + bf] += lb3[q];
     }
 #pragma unroll
     for (int a = 0; a < kQ; ++a) lf[a * np + j] = lfj[a];
@@ -329,7 +347,8 @@ __global__ void __launch_bounds__(kTile) k_adj_stage3(const double *__restrict__
     }
 }
 
-// ---- stage 2: from lf3, lc -> lB, la2 (X = B - dt/2 a2, f3 = S2(X), C' = C + dt/6 a2)
+// ---- stage 2: from lf3, lc -> lB, la2.  Forward: X = B - dt/2 a2, f3 = (X + zt f^eq(X)) / (1 + zt)
+// with zt = (dt/3)/tau (Eq. (fnewstage), J = 3), C' = C + dt/6 a2.
 __global__ void __launch_bounds__(kTile) k_adj_stage2(const double *__restrict__ Bv, const double *__restrict__ f2,
                                                       const double *__restrict__ g2, const double *__restrict__ tau,
                                                       const double *__restrict__ lf3, const double *__restrict__ lc,
@@ -339,24 +358,18 @@ __global__ void __launch_bounds__(kTile) k_adj_stage2(const double *__restrict__
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
     const double dt = P.dt;
-    double acc[kQ], X[kQ], l3[kQ];
+    double acc[kQ], X[kQ], mu[kQ], lX[kQ];
     adj_flux_acc(i, f2, g2, G, P.rho0, acc);
+    const double zt = dt * (1.0 / 3.0) * (1.0 / tau[i]);
+    const double inv = 1.0 / (1.0 + zt);
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
         X[a] = Bv[a * np + i] - 0.5 * dt * acc[a];
-        l3[a] = lf3[a * np + i];
+        const double l3 = lf3[a * np + i];
+        lX[a] = inv * l3;
+        mu[a] = zt * inv * l3;
     }
-    double lX[kQ];
-    for (int k = 0; k < kQ; ++k) {
-        Dual xd[kQ], f3[kQ];
-#pragma unroll
-        for (int a = 0; a < kQ; ++a) xd[a] = Dual(X[a], k == a ? 1.0 : 0.0);
-        adj_stage2<Dual>(xd, Dual(P.rho0), Dual(dt), Dual(tau[i]), f3);
-        double s = 0;
-#pragma unroll
-        for (int a = 0; a < kQ; ++a) s += f3[a].d * l3[a];
-        lX[k] = s;
-    }
+    feq_vjp(X, P.rho0, mu, lX);
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
         lB[a * np + i] = lX[a];
@@ -364,7 +377,9 @@ __global__ void __launch_bounds__(kTile) k_adj_stage2(const double *__restrict__
     }
 }
 
-// ---- stage 1: from lf2, lB, lc -> lf0 (=), la1 ((f2, B, C) = S1(f0, a1))
+// ---- stage 1: from lf2, lB, lc -> lf0 (=), la1.  Forward (z = dt/tau, zq = z/4, s = z/(1 + zq)):
+//   X = f0 - dt/2 a1,  f2 = (X + zq f^eq(X)) / (1 + zq),
+//   B = X + (s/3) [(f^eq(f0) - f0) + (f^eq(X) - X)],  C = dt/6 a1.
 __global__ void __launch_bounds__(kTile) k_adj_stage1(const double *__restrict__ f0, const double *__restrict__ s1,
                                                       const double *__restrict__ g1, const double *__restrict__ tau,
                                                       const double *__restrict__ lf2, const double *__restrict__ lB,
@@ -373,56 +388,57 @@ __global__ void __launch_bounds__(kTile) k_adj_stage1(const double *__restrict__
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
-    double acc[kQ], x0[kQ], l2[kQ], lb[kQ], lcc[kQ];
+    const double dt = P.dt;
+    double acc[kQ], x0[kQ], X[kQ], lX[kQ], mu[kQ], lb[kQ];
     adj_flux_acc(i, s1, g1, G, P.rho0, acc);
+    const double z = dt * (1.0 / tau[i]);
+    const double zq = z * 0.25;
+    const double inv = 1.0 / (1.0 + zq);
+    const double s3 = z * inv * (1.0 / 3.0);
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
         x0[a] = f0[a * np + i];
-        l2[a] = lf2[a * np + i];
+        X[a] = x0[a] - 0.5 * dt * acc[a];
+        const double l2 = lf2[a * np + i];
         lb[a] = lB[a * np + i];
-        lcc[a] = lc[a * np + i];
+        lX[a] = inv * l2 + (1.0 - s3) * lb[a];
+        mu[a] = zq * inv * l2 + s3 * lb[a];
     }
-    for (int k = 0; k < 2 * kQ; ++k) {
-        Dual fd[kQ], ad[kQ], f2[kQ], B[kQ], C[kQ];
+    feq_vjp(X, P.rho0, mu, lX);
+    double l0[kQ];
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) {
-            fd[a] = Dual(x0[a], k == a ? 1.0 : 0.0);
-            ad[a] = Dual(acc[a], k == kQ + a ? 1.0 : 0.0);
-        }
-        adj_stage1<Dual>(fd, ad, Dual(P.rho0), Dual(P.dt), Dual(tau[i]), f2, B, C);
-        double s = 0;
+    for (int a = 0; a < kQ; ++a) {
+        l0[a] = lX[a] - s3 * lb[a];
+        mu[a] = s3 * lb[a];
+    }
+    feq_vjp(x0, P.rho0, mu, l0);
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) s += f2[a].d * l2[a] + B[a].d * lb[a] + C[a].d * lcc[a];
-        if (k < kQ)
-            lf0[k * np + i] = s;
-        else
-            la[(k - kQ) * np + i] = s;
+    for (int a = 0; a < kQ; ++a) {
+        lf0[a * np + i] = l0[a];
+        la[a * np + i] = -0.5 * dt * lX[a] + dt * (1.0 / 6.0) * lc[a * np + i];
     }
 }
 
-// ---- relaxation of stage 1: lf0 += (d s1 / d f0)^T ls1
+// ---- relaxation of stage 1: lf0 += (d s1 / d f0)^T ls1, s1 = (f0 + zq f^eq(f0)) / (1 + zq)
 __global__ void __launch_bounds__(kTile) k_adj_relax(const double *__restrict__ f0, const double *__restrict__ tau,
                                                      const double *__restrict__ ls1, double *__restrict__ lf0,
                                                      Geo<double> G) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
-    double x0[kQ], l1[kQ];
+    const double zq = P.dt / tau[i] * 0.25;
+    const double inv = 1.0 / (1.0 + zq);
+    double x0[kQ], l0[kQ], mu[kQ];
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
         x0[a] = f0[a * np + i];
-        l1[a] = ls1[a * np + i];
+        const double l1 = ls1[a * np + i];
+        l0[a] = lf0[a * np + i] + inv * l1;
+        mu[a] = zq * inv * l1;
     }
-    for (int k = 0; k < kQ; ++k) {
-        Dual fd[kQ], s1[kQ];
+    feq_vjp(x0, P.rho0, mu, l0);
 #pragma unroll
-        for (int a = 0; a < kQ; ++a) fd[a] = Dual(x0[a], k == a ? 1.0 : 0.0);
-        adj_relax<Dual>(fd, Dual(P.rho0), Dual(P.dt), Dual(tau[i]), s1);
-        double s = 0;
-#pragma unroll
-        for (int a = 0; a < kQ; ++a) s += s1[a].d * l1[a];
-        lf0[k * np + i] += s;
-    }
+    for (int a = 0; a < kQ; ++a) lf0[a * np + i] = l0[a];
 }
 
 // ---- objective J = (cx Fx + cy Fy) / (q l) over the wall faces of one instance: its
@@ -489,24 +505,24 @@ __global__ void k_adj_gather(const double *__restrict__ L, const int *__restrict
 
 namespace {
 
-// Device buffers of one adjoint call, freed when it returns.
+// Device buffers of one adjoint call: one allocation, carved in 256-byte aligned pieces, freed
+// when the call returns.  The carving runs twice: once to measure, once on the allocation.
 struct AdjScratch {
-    std::vector<void *> p;
-    size_t bytes = 0;
+    char *base = nullptr;
+    size_t off = 0;
     ~AdjScratch() {
-        for (void *x : p) cudaFree(x);
+        if (base) cudaFree(base);
     }
-    double *get(size_t n, cudaError_t *err) {
-        void *x = nullptr;
-        const size_t b = std::max<size_t>(n, 2) * sizeof(double);
-        const cudaError_t e = cudaMalloc(&x, b);
-        if (e != cudaSuccess) {
-            if (*err == cudaSuccess) *err = e;
-            return nullptr;
-        }
-        p.push_back(x);
-        bytes += b;
-        return static_cast<double *>(x);
+    double *get(size_t n) {
+        const size_t b = (std::max<size_t>(n, 2) * sizeof(double) + 255) / 256 * 256;
+        double *p = base ? reinterpret_cast<double *>(base + off) : nullptr;
+        off += b;
+        return p;
+    }
+    cudaError_t allocate() {
+        const size_t total = off;
+        off = 0;
+        return cudaMalloc(reinterpret_cast<void **>(&base), total);
     }
 };
 
@@ -554,20 +570,21 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const double *f0, 
         if (A.a_sn)
             k_adj_geom<<<grid, block, 0, s>>>(fs, g, A.la, A.lg, G, A.a_sn, A.a_lsq, A.a_rown, A.a_rnbr);
     };
+    // transpose of one flux + gradient evaluation at stage value fs (gradient g): la -> lf
+    auto evalT = [&](const double *fs, const double *g, double *lf) {
+        k_adj_fluxT<<<grid, block, 0, s>>>(A.la, lf, A.lg, G, back);
+        geom(fs, g);
+        k_adj_gradT<<<grid, block, 0, s>>>(A.lg, lf, G, back);
+        k_adj_bndT<<<grid, block, 0, s>>>(fs, A.la, A.lg, lf, A.lbval, G);
+    };
     k_adj_stage3<<<grid, block, 0, s>>>(A.L, A.lf3, A.lc, A.la, G);
-    k_adj_fluxT<<<grid, block, 0, s>>>(S.f3, A.la, A.lf3, A.lg, A.lbval, G, back);
-    geom(S.f3, S.g3);
-    k_adj_gradT<<<grid, block, 0, s>>>(S.f3, A.lg, A.lf3, A.lbval, G, back);
+    evalT(S.f3, S.g3, A.lf3);
     k_adj_stage2<<<grid, block, 0, s>>>(S.B, S.f2, S.g2, tau, A.lf3, A.lc, A.lB, A.la, G);
     cudaMemsetAsync(A.lf2, 0, nq * sizeof(double), s);
-    k_adj_fluxT<<<grid, block, 0, s>>>(S.f2, A.la, A.lf2, A.lg, A.lbval, G, back);
-    geom(S.f2, S.g2);
-    k_adj_gradT<<<grid, block, 0, s>>>(S.f2, A.lg, A.lf2, A.lbval, G, back);
+    evalT(S.f2, S.g2, A.lf2);
     k_adj_stage1<<<grid, block, 0, s>>>(f0, S.s1, S.g1, tau, A.lf2, A.lB, A.lc, A.lf0, A.la, G);
     cudaMemsetAsync(A.ls1, 0, nq * sizeof(double), s);
-    k_adj_fluxT<<<grid, block, 0, s>>>(S.s1, A.la, A.ls1, A.lg, A.lbval, G, back);
-    geom(S.s1, S.g1);
-    k_adj_gradT<<<grid, block, 0, s>>>(S.s1, A.lg, A.ls1, A.lbval, G, back);
+    evalT(S.s1, S.g1, A.ls1);
     k_adj_relax<<<grid, block, 0, s>>>(f0, tau, A.ls1, A.lf0, G);
     std::swap(A.L, A.lf0);
 }
@@ -583,29 +600,68 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
     CK(cudaSetDevice(h->device));
     const Geo<double> G = geo_of<double>(h);
     const size_t np = h->np, nq = static_cast<size_t>(kQ) * np;
-    const int K = std::max(1, static_cast<int>(std::ceil(std::sqrt(static_cast<double>(n_steps)))));
-    const int nck = (n_steps + K - 1) / K;  // f^n kept at n = 0, K, 2K, ...
-    cudaError_t err = cudaSuccess;
-    AdjScratch M;
-    std::vector<double *> ck(std::max(nck, 1)), seg(K);
-    for (auto &x : ck) x = M.get(nq, &err);
-    for (auto &x : seg) x = M.get(nq, &err);
-    double *xa = M.get(nq, &err), *xb = M.get(nq, &err);
-    AdjStep S{M.get(nq, &err), M.get(2 * nq, &err), M.get(nq, &err), M.get(2 * nq, &err), M.get(nq, &err),
-              M.get(nq, &err), M.get(nq, &err), M.get(2 * nq, &err), M.get(3 * np, &err)};
-    AdjVars A{M.get(nq, &err), M.get(nq, &err), M.get(nq, &err), M.get(nq, &err), M.get(2 * nq, &err),
-              M.get(nq, &err), M.get(nq, &err), M.get(nq, &err), M.get(nq, &err),
-              M.get(3 * static_cast<size_t>(std::max(h->nbt, 1)), &err)};
-    const size_t nbt = std::max(h->nbt, 1);
-    if (dJ_dxy) {
-        A.a_sn = M.get(8 * np, &err);
-        A.a_lsq = M.get(8 * np, &err);
-        A.a_rown = M.get(8 * np, &err);
-        A.a_rnbr = M.get(8 * np, &err);
-        A.a_bnrm = M.get(2 * nbt, &err);
-        A.a_blen = M.get(nbt, &err);
+    // Memory plan.  The stage values one adjoint step reads take 99 doubles per cell (f^n, f^(1),
+    // f^(2), B, f^(3) and the three gradients).  Segments of K consecutive steps keep theirs
+    // whole, K as large as the budget allows (the handle's adjoint budget, else half the free
+    // device memory).  With one segment every step runs once; with several, a first sweep keeps
+    // f^n at each segment start and each segment then runs a second time before its reverse
+    // sweep.
+    const size_t per_step = 99 * np * sizeof(double);
+    size_t budget = h->adj_budget;
+    if (budget == 0) {
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        budget = fr / 2;
     }
-    if (err != cudaSuccess) return cuda_fail(err);
+    const int K = static_cast<int>(
+        std::max<size_t>(1, std::min<size_t>(budget / per_step, static_cast<size_t>(std::max(n_steps, 1)))));
+    const int nseg = (n_steps + K - 1) / K;
+    AdjScratch M;
+    double *xa, *xb, *Cs, *macs;
+    std::vector<double *> ck(nseg > 1 ? nseg : 0), f0s(K);
+    std::vector<AdjStep> slot(K);
+    AdjVars A{};
+    const size_t nbt = std::max(h->nbt, 1);
+    auto carve = [&] {
+        xa = M.get(nq);
+        xb = M.get(nq);
+        Cs = M.get(nq);
+        macs = M.get(3 * np);
+        for (auto &x : ck) x = M.get(nq);
+        for (int k = 0; k < K; ++k) {
+            f0s[k] = M.get(nq);
+            slot[k].s1 = M.get(nq);
+            slot[k].g1 = M.get(2 * nq);
+            slot[k].f2 = M.get(nq);
+            slot[k].g2 = M.get(2 * nq);
+            slot[k].B = M.get(nq);
+            slot[k].C = Cs;
+            slot[k].f3 = M.get(nq);
+            slot[k].g3 = M.get(2 * nq);
+            slot[k].mac = macs;
+        }
+        A.L = M.get(nq);
+        A.lf3 = M.get(nq);
+        A.lc = M.get(nq);
+        A.la = M.get(nq);
+        A.lg = M.get(2 * nq);
+        A.lB = M.get(nq);
+        A.lf2 = M.get(nq);
+        A.ls1 = M.get(nq);
+        A.lf0 = M.get(nq);
+        A.lbval = M.get(3 * nbt);
+        if (dJ_dxy) {
+            A.a_sn = M.get(8 * np);
+            A.a_lsq = M.get(8 * np);
+            A.a_rown = M.get(8 * np);
+            A.a_rnbr = M.get(8 * np);
+            A.a_bnrm = M.get(2 * nbt);
+            A.a_blen = M.get(nbt);
+        }
+    };
+    carve();
+    CK(M.allocate());
+    carve();
     cudaStream_t s = h->stream;
     if (dJ_dxy) {
         for (double *x : {A.a_sn, A.a_lsq, A.a_rown, A.a_rnbr})
@@ -613,38 +669,51 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         CK(cudaMemsetAsync(A.a_bnrm, 0, 2 * nbt * sizeof(double), s));
         CK(cudaMemsetAsync(A.a_blen, 0, nbt * sizeof(double), s));
     }
-    // forward sweep: f^N and the checkpoints
-    CK(cudaMemcpyAsync(xa, h->fn, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (nck > 0) CK(cudaMemcpyAsync(ck[0], xa, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    for (int n = 0; n < n_steps; ++n) {
-        adj_forward_step(h, G, xa, xb, S);
-        std::swap(xa, xb);
-        if ((n + 1) % K == 0 && (n + 1) / K < nck)
-            CK(cudaMemcpyAsync(ck[(n + 1) / K], xa, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    // steps k0 .. k1-1 from `start` with their stage values kept; f^{k1} into xb
+    auto fill = [&](int k0, int k1, const double *start) -> int {
+        CK(cudaMemcpyAsync(f0s[0], start, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        for (int n = k0; n < k1; ++n)
+            adj_forward_step(h, G, f0s[n - k0], n + 1 < k1 ? f0s[n + 1 - k0] : xb, slot[n - k0]);
+        CK(cudaGetLastError());
+        return FVLBM_OK;
+    };
+    const double *fN = xb;
+    if (nseg > 1) {  // first sweep: f^N and the segment starts
+        CK(cudaMemcpyAsync(xa, h->fn, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        for (int n = 0; n < n_steps; ++n) {
+            if (n % K == 0) CK(cudaMemcpyAsync(ck[n / K], xa, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            adj_forward_step(h, G, xa, xb, slot[0]);
+            std::swap(xa, xb);
+        }
+        fN = xa;
+        CK(cudaGetLastError());
+    } else if (n_steps > 0) {
+        int rc = fill(0, n_steps, static_cast<const double *>(h->fn));
+        if (rc) return rc;
+    } else {
+        fN = static_cast<const double *>(h->fn);
     }
-    CK(cudaGetLastError());
     // J at f^N and its direct derivatives
     double out[4];
-    int rc = forces_impl(h, instance, 0.0, out, nullptr, nullptr, xa);
+    int rc = forces_impl(h, instance, 0.0, out, nullptr, nullptr, fN);
     if (rc) return rc;
     if (J) *J = w[0] * out[2] + w[1] * out[3];
     const double q = 0.5 * I.rho0 * I.uref * I.uref * I.lref;
     const double al = I.alpha_deg * M_PI / 180.0, ca = std::cos(al), sa = std::sin(al);
     const double cx = (w[0] * ca - w[1] * sa) / q, cy = (w[0] * sa + w[1] * ca) / q;
     CK(cudaMemsetAsync(A.lbval, 0, 3 * static_cast<size_t>(std::max(h->nbt, 1)) * sizeof(double), s));
-    k_adj_seed<<<h->ntiles, kTile, 0, s>>>(xa, static_cast<const double *>(h->bnrm),
+    k_adj_seed<<<h->ntiles, kTile, 0, s>>>(fN, static_cast<const double *>(h->bnrm),
                                            static_cast<const double *>(h->blen), instance, cx, cy, A.L,
                                            A.lbval, A.a_bnrm, A.a_blen, G);
     CK(cudaGetLastError());
-    // backward sweep, one checkpoint segment at a time
-    for (int c = nck - 1; c >= 0; --c) {
+    // reverse sweep, one segment at a time
+    for (int c = nseg - 1; c >= 0; --c) {
         const int k0 = c * K, k1 = std::min(n_steps, k0 + K);
-        CK(cudaMemcpyAsync(seg[0], ck[c], nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        for (int n = k0; n + 1 < k1; ++n) adj_forward_step(h, G, seg[n - k0], seg[n - k0 + 1], S);
-        for (int n = k1 - 1; n >= k0; --n) {
-            adj_forward_step(h, G, seg[n - k0], xb, S);
-            adj_backward_step(h, G, seg[n - k0], S, A);
+        if (nseg > 1) {
+            int rc = fill(k0, k1, ck[c]);
+            if (rc) return rc;
         }
+        for (int n = k1 - 1; n >= k0; --n) adj_backward_step(h, G, f0s[n - k0], slot[n - k0], A);
         CK(cudaGetLastError());
     }
     if (dJ_df && I.nc > 0) {

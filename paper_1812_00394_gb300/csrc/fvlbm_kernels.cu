@@ -1414,6 +1414,7 @@ struct fvlbm_handle {
     int *d_perm = nullptr, *d_inst_tile0 = nullptr;
     int *d_all_map = nullptr;   // output position (all instances) -> internal cell
     int *d_back = nullptr;      // FP64 handles: slot of each face at its neighbour [4 np] (adjoint)
+    size_t adj_budget = 0;      // device bytes the adjoint may keep stage values in (0: half the free)
     int total_nc = 0, total_nb = 0;
     // fused path: per-block halo lists and local adjacency, for each fused block size
     struct HaloSet {
@@ -2664,6 +2665,12 @@ int fvlbm_forces(fvlbm_handle *h, int instance, double *out, double *cp) {
 int fvlbm_adjoint(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
                   double *dJ_dbedge_val, double *dJ_dxy) {
     return adjoint_impl(h, instance, n_steps, w, J, dJ_df, dJ_dbedge_val, dJ_dxy);
+}
+
+int fvlbm_set_adjoint_budget(fvlbm_handle *h, long long bytes) {
+    if (!h || bytes < 0) return FVLBM_ERR_BAD_PARAM;
+    h->adj_budget = static_cast<size_t>(bytes);
+    return FVLBM_OK;
 }
 
 int fvlbm_tangent_seed(fvlbm_handle *h, int instance, const double *dbedge_val, const double *df) {

@@ -61,8 +61,9 @@ EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "
            "fvlbm_set_f", "fvlbm_get_fields", "fvlbm_info", "fvlbm_footprint",
            "fvlbm_profile_kernels", "fvlbm_autotune", "fvlbm_destroy", "fvlbm_strerror",
            "fvlbm_stats_reduce_static", "fvlbm_tangent_seed", "fvlbm_tangent_seed_nodes",
-           "fvlbm_get_f_tangent", "fvlbm_forces_tangent", "fvlbm_adjoint", "fvlbm_state_bytes",
-           "fvlbm_save_state", "fvlbm_load_state", "fvlbm_set_rollback", "fvlbm_set_f_async",
+           "fvlbm_get_f_tangent", "fvlbm_forces_tangent", "fvlbm_adjoint",
+           "fvlbm_set_adjoint_budget", "fvlbm_state_bytes", "fvlbm_save_state",
+           "fvlbm_load_state", "fvlbm_set_rollback", "fvlbm_set_f_async",
            "fvlbm_get_fields_async", "fvlbm_wait", "fvlbm_get_fdev_f32", "fvlbm_set_fdev_f32_async"]
 
 _lib = None
@@ -110,6 +111,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_tangent_seed_nodes.argtypes = [vp, i, vp]
     lib.fvlbm_forces_tangent.argtypes = [vp, i, d, vp, vp]
     lib.fvlbm_adjoint.argtypes = [vp, i, i, vp, vp, vp, vp, vp]
+    lib.fvlbm_set_adjoint_budget.argtypes = [vp, C.c_longlong]
     lib.fvlbm_destroy.argtypes = [vp]
     lib.fvlbm_destroy.restype = None
     lib.fvlbm_strerror.argtypes = [i]
@@ -439,6 +441,9 @@ class Solver:
 
     def forces_tangent(self, i: int = 0, dalpha: float = 0.0):
         return fvlbm_forces_tangent(self.h, i, dalpha)
+
+    def set_adjoint_budget(self, nbytes: int) -> None:
+        _check(load().fvlbm_set_adjoint_budget(self.h, int(nbytes)), "fvlbm_set_adjoint_budget")
 
     def adjoint(self, n_steps: int, w_cd: float = 0.0, w_cl: float = 0.0, i: int = 0,
                 shape: bool = False):

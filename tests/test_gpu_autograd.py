@@ -1,7 +1,7 @@
 """GPU check of the autograd wrapper: gradients of (C_L, C_D) with respect to the free-stream
 angle, the inflow eddy-viscosity ratio and wall-node normal displacements, taken by
-torch.autograd through the tangent-mode backward, against central differences of the
-forward map."""
+torch.autograd through the tangent-mode backward (SST case) and through the adjoint backward
+(laminar case), against central differences of the forward map and against each other."""
 import math
 
 import numpy as np
@@ -36,3 +36,40 @@ def test_autograd_gradients_match_central_differences():
         assert abs(g[q] - fd) <= tol * abs(fd) + 1e-9, (q, g[q], fd)
     # the forward value is the FP64 step of the base case at p0
     np.testing.assert_allclose(out.detach().numpy(), model.value(p0), rtol=0, atol=0)
+
+
+def _laminar_model(mode):
+    import dataclasses
+    base = dataclasses.replace(mg.naca0012_cmesh(n_target=2500, re_c=2000.0, alpha_deg=3.0),
+                               sst=False)
+    m = base.mesh.normalized()
+    wall = np.unique(m.bedge_nodes[m.bedge_type == mg.BC_WALL])
+    upper = wall[m.xy[wall, 1] > 0]
+    lower = wall[m.xy[wall, 1] < 0]
+    picks = [int(upper[np.argmin(np.abs(m.xy[upper, 0] - 0.3))]),
+             int(lower[np.argmin(np.abs(m.xy[lower, 0] - 0.6))])]
+    return fa.AirfoilForces(base, picks, steps=25, device=0, mode=mode)
+
+
+def test_autograd_adjoint_backward_matches_tangent_and_fd():
+    p0 = np.array([math.radians(3.0), 1.0, 0.0, 0.0])
+    grads = {}
+    for mode in ("adjoint", "tangent"):
+        model = _laminar_model(mode)
+        assert model.mode == mode
+        p = torch.tensor(p0, requires_grad=True)
+        out = fa.forces(model, p)
+        (0.8 * out[0] - 2.0 * out[1]).backward()
+        grads[mode] = p.grad.numpy().copy()
+    ga, gt = grads["adjoint"], grads["tangent"]
+    assert ga[1] == 0.0 and abs(gt[1]) <= 1e-14   # omega_b does not enter a laminar step
+    for q in (0, 2, 3):
+        assert abs(ga[q] - gt[q]) <= 1e-8 * abs(gt[q]), (q, ga[q], gt[q])
+    model = _laminar_model("auto")
+    assert model.mode == "adjoint"
+    for q, h in ((0, 1e-5), (2, 1e-6)):
+        e = np.zeros_like(p0)
+        e[q] = h
+        vp, vm = model.value(p0 + e), model.value(p0 - e)
+        fd = ((0.8 * vp[0] - 2.0 * vp[1]) - (0.8 * vm[0] - 2.0 * vm[1])) / (2 * h)
+        assert abs(ga[q] - fd) <= 1e-5 * abs(fd), (q, ga[q], fd)
