@@ -562,6 +562,46 @@ def run_profile_mode(args):
     return 0
 
 
+def run_adjoint_mode(args):
+    """Cost of the discrete adjoint (fvlbm_adjoint, FP64, laminar) against the FP64 primal step it
+    differentiates, on a laminar NACA 0012 C-mesh (Re_c = 2000, alpha = 4 degrees) or a 256 x 256
+    lid-driven cavity.  Per-step costs are marginal: (time at 3S steps - time at S steps) / 2S, so
+    allocation and set-up drop out.  Not a bench line of the step; prints one JSON object."""
+    import dataclasses
+    import torch
+    from paper_1812_00394_gb300 import fvlbm, meshgen as mg
+    torch.cuda.set_device(0)
+    if args.adjoint_case == "naca_laminar":
+        case = dataclasses.replace(mg.naca0012_cmesh(n_target=args.adjoint_cells, re_c=2000.0,
+                                                     alpha_deg=4.0), sst=False)
+    else:
+        case = mg.cavity_quad(256, re=1000.0)
+    s = fvlbm.Solver(case, precision=fvlbm.FVLBM_FP64, device=0, kernel_path=1)
+    s.step(args.warmup)
+    s.adjoint(2, 1.0, 0.0)
+    n1 = max(1, args.steps)
+    t = {}
+    for n in (n1, 3 * n1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(n)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        s.adjoint(n, 1.0, 0.0)
+        t2 = time.perf_counter()
+        s.adjoint(n, 1.0, 0.0, shape=True)
+        t3 = time.perf_counter()
+        t[n] = (t1 - t0, t2 - t1, t3 - t2)
+    d = 2 * n1
+    fwd, adj, shp = ((t[3 * n1][q] - t[n1][q]) / d * 1e3 for q in range(3))
+    print(json.dumps({"mode": "adjoint", "case": args.adjoint_case, "cells": case.mesh.n_cells,
+                      "steps": [n1, 3 * n1], "fwd_fp64_ms_per_step": fwd,
+                      "adjoint_ms_per_step": adj, "adjoint_with_shape_ms_per_step": shp,
+                      "adjoint_over_fwd": adj / fwd, "shape_setup_s": t[n1][2] - n1 * shp / 1e3}))
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -578,6 +618,10 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--kernel-path", type=int, default=0, choices=[0, 1],
                     help="profile mode: 0 fused stage kernels, 1 two-pass kernels")
+    ap.add_argument("--adjoint-mode", action="store_true",
+                    help="time the FP64 laminar adjoint against its primal step (not a bench line)")
+    ap.add_argument("--adjoint-case", default="naca_laminar", choices=["naca_laminar", "cavity256"])
+    ap.add_argument("--adjoint-cells", type=int, default=200000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -585,6 +629,8 @@ def main():
         return run_reference(args)
     if args.profile_mode:
         return run_profile_mode(args)
+    if args.adjoint_mode:
+        return run_adjoint_mode(args)
     return run_ours(args)
 
 

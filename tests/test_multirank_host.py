@@ -68,7 +68,7 @@ def test_rank_workloads_differ_but_are_seeded(rank):
 
 def test_bench_entry_points_exist():
     """Every mode main() dispatches to is defined (the ncu profile mode included)."""
-    for name in ("run_ours", "run_reference", "run_profile_mode"):
+    for name in ("run_ours", "run_reference", "run_profile_mode", "run_adjoint_mode"):
         assert callable(getattr(bench, name)), name
 
 
