@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(kTile) k_adj_stage2(const double *__restrict__
                                                       const double *__restrict__ g2, const double *__restrict__ tau,
                                                       const double *__restrict__ lf3, const double *__restrict__ lc,
                                                       double *__restrict__ lB, double *__restrict__ la,
-                                                      Geo<double> G) {
+                                                      double *__restrict__ ltau, Geo<double> G) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -368,6 +368,14 @@ __global__ void __launch_bounds__(kTile) k_adj_stage2(const double *__restrict__
         const double l3 = lf3[a * np + i];
         lX[a] = inv * l3;
         mu[a] = zt * inv * l3;
+    }
+    if (ltau != nullptr) {  // d f3 / d zt = (f^eq(X) - X) / (1 + zt)^2, d zt / d tau = -zt / tau
+        double eq[kQ], dr, r, u, v, l_z = 0.0;
+        moments(X, P.rho0, dr, r, u, v);
+        feq_dev(dr, r, u, v, eq);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) l_z += lf3[a * np + i] * (eq[a] - X[a]);
+        ltau[i] = -l_z * inv * inv * zt / tau[i];
     }
     feq_vjp(X, P.rho0, mu, lX);
 #pragma unroll
@@ -384,7 +392,8 @@ __global__ void __launch_bounds__(kTile) k_adj_stage1(const double *__restrict__
                                                       const double *__restrict__ g1, const double *__restrict__ tau,
                                                       const double *__restrict__ lf2, const double *__restrict__ lB,
                                                       const double *__restrict__ lc, double *__restrict__ lf0,
-                                                      double *__restrict__ la, Geo<double> G) {
+                                                      double *__restrict__ la, double *__restrict__ ltau,
+                                                      Geo<double> G) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -404,6 +413,20 @@ __global__ void __launch_bounds__(kTile) k_adj_stage1(const double *__restrict__
         lX[a] = inv * l2 + (1.0 - s3) * lb[a];
         mu[a] = zq * inv * l2 + s3 * lb[a];
     }
+    if (ltau != nullptr) {
+        // z = dt/tau: d f2 / d z = (f^eq(X) - X) inv^2 / 4; B carries (s/3)(f^eq(f0) - f0 +
+        // f^eq(X) - X) with s = z inv, ds/dz = inv^2
+        double e1[kQ], e2[kQ], dr, r, u, v, l_z = 0.0;
+        moments(X, P.rho0, dr, r, u, v);
+        feq_dev(dr, r, u, v, e2);
+        moments(x0, P.rho0, dr, r, u, v);
+        feq_dev(dr, r, u, v, e1);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a)
+            l_z += lf2[a * np + i] * (e2[a] - X[a]) * 0.25 +
+                   lb[a] * (1.0 / 3.0) * (e1[a] - x0[a] + e2[a] - X[a]);
+        ltau[i] += -l_z * inv * inv * z / tau[i];
+    }
     feq_vjp(X, P.rho0, mu, lX);
     double l0[kQ];
 #pragma unroll
@@ -422,7 +445,7 @@ __global__ void __launch_bounds__(kTile) k_adj_stage1(const double *__restrict__
 // ---- relaxation of stage 1: lf0 += (d s1 / d f0)^T ls1, s1 = (f0 + zq f^eq(f0)) / (1 + zq)
 __global__ void __launch_bounds__(kTile) k_adj_relax(const double *__restrict__ f0, const double *__restrict__ tau,
                                                      const double *__restrict__ ls1, double *__restrict__ lf0,
-                                                     Geo<double> G) {
+                                                     double *__restrict__ ltau, Geo<double> G) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -435,6 +458,14 @@ __global__ void __launch_bounds__(kTile) k_adj_relax(const double *__restrict__ 
         const double l1 = ls1[a * np + i];
         l0[a] = lf0[a * np + i] + inv * l1;
         mu[a] = zq * inv * l1;
+    }
+    if (ltau != nullptr) {  // d s1 / d zq = (f^eq(f0) - f0) / (1 + zq)^2, zq = dt / (4 tau)
+        double eq[kQ], dr, r, u, v, l_z = 0.0;
+        moments(x0, P.rho0, dr, r, u, v);
+        feq_dev(dr, r, u, v, eq);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) l_z += ls1[a * np + i] * (eq[a] - x0[a]);
+        ltau[i] += -l_z * inv * inv * zq / tau[i];
     }
     feq_vjp(x0, P.rho0, mu, l0);
 #pragma unroll
@@ -503,6 +534,8 @@ __global__ void k_adj_gather(const double *__restrict__ L, const int *__restrict
 
 }  // namespace fvlbm
 
+#include "fvlbm_adjoint_sst.cuh"
+
 namespace {
 
 // Device buffers of one adjoint call: one allocation, carved in 256-byte aligned pieces, freed
@@ -526,20 +559,37 @@ struct AdjScratch {
     }
 };
 
-// Stage values of one step that its adjoint reads.
-struct AdjStep {
-    double *s1, *g1, *f2, *g2, *B, *C, *f3, *g3, *mac;
+// The state a step starts from: f and, for SST handles, the macros (rho, u, v) of f, k, omega
+// and nu_t (laminar handles: NULL).
+struct AdjState {
+    double *f = nullptr, *mac = nullptr, *k = nullptr, *w = nullptr, *nt = nullptr;
 };
 
-// One two-pass FP64 step f_in -> f_out (the launches of the laminar two-pass path, with the
-// stage values kept in S).
-void adj_forward_step(fvlbm_handle *h, const Geo<double> &G, const double *f_in, double *f_out,
+// Stage values of one step that its adjoint reads (SST: also the SST gradients [12 np], f1 and
+// the step's tau; laminar: tau is the handle's).
+struct AdjStep {
+    double *s1, *g1, *f2, *g2, *B, *C, *f3, *g3, *mac;
+    double *sg = nullptr, *f1 = nullptr, *tau = nullptr;
+};
+
+// One two-pass FP64 step from state `in` to state `out` (the launches of the two-pass path:
+// the SST solve first on SST handles), with the stage values kept in S.
+void adj_forward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in, const AdjState &out,
                       const AdjStep &S) {
     const dim3 grid(h->ntiles), block(kTile);
     cudaStream_t s = h->stream;
     const double *tau = static_cast<const double *>(h->tau);
-    double *fin = const_cast<double *>(f_in);
-    k_stage1<double><<<grid, block, 0, s>>>(f_in, S.s1, tau, G);
+    double *mac_out = S.mac;
+    if (h->sst) {
+        const CompactGeo<double> CG{nullptr, nullptr};
+        k_sst_grad<double, false><<<grid, block, 0, s>>>(in.mac, in.k, in.w, S.sg, S.f1, G, CG);
+        k_sst_update<double, false, false><<<grid, block, 0, s>>>(in.mac, in.k, in.w, in.nt, S.sg, S.f1, out.k,
+                                                                  out.w, out.nt, S.tau, G, nullptr, nullptr, CG);
+        tau = S.tau;
+        mac_out = out.mac;
+    }
+    double *fin = in.f;
+    k_stage1<double><<<grid, block, 0, s>>>(in.f, S.s1, tau, G);
     k_grad<double, false><<<grid, block, 0, s>>>(S.s1, S.g1, G);
     k_flux_stage<double, 1, false><<<grid, block, 0, s>>>(S.s1, S.g1, S.f2, fin, S.B, S.C, tau, S.mac,
                                                           nullptr, G);
@@ -547,25 +597,31 @@ void adj_forward_step(fvlbm_handle *h, const Geo<double> &G, const double *f_in,
     k_flux_stage<double, 2, false><<<grid, block, 0, s>>>(S.f2, S.g2, S.f3, fin, S.B, S.C, tau, S.mac,
                                                           nullptr, G);
     k_grad<double, false><<<grid, block, 0, s>>>(S.f3, S.g3, G);
-    k_flux_stage<double, 3, false><<<grid, block, 0, s>>>(S.f3, S.g3, nullptr, f_out, S.B, S.C, tau,
-                                                          S.mac, nullptr, G);
+    k_flux_stage<double, 3, false><<<grid, block, 0, s>>>(S.f3, S.g3, nullptr, out.f, S.B, S.C, tau,
+                                                          mac_out, nullptr, G);
 }
 
-// Adjoint of the step whose stage values S were just recomputed from f0: L (adjoint of f^{n+1})
-// is replaced by the adjoint of f^n; boundary-value adjoints are added into lbval.
+// Adjoint variables.  L is the adjoint of f^{n+1} on entry to a step's reverse and of f^n on
+// exit; lk, lw, lnt those of k, omega, nu_t (SST); lbval [5][nbt] accumulates the boundary
+// values' adjoints.
 struct AdjVars {
     double *L, *lf3, *lc, *la, *lg, *lB, *lf2, *ls1, *lf0, *lbval;
     double *a_sn = nullptr, *a_lsq = nullptr, *a_rown = nullptr, *a_rnbr = nullptr;  // shape adjoint
     double *a_bnrm = nullptr, *a_blen = nullptr;
+    double *lk = nullptr, *lw = nullptr, *lnt = nullptr, *ltau = nullptr;  // SST
+    double *own = nullptr, *fbu = nullptr, *fbg = nullptr;
 };
 
-void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const double *f0, const AdjStep &S,
+// Reverse of the step that went from state `in` (stage values S): L <- adjoint of f^n, and on
+// SST handles (lk, lw, lnt) <- adjoints of (k, omega, nu_t)^n.
+void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in, const AdjStep &S,
                        AdjVars &A) {
     const dim3 grid(h->ntiles), block(kTile);
     cudaStream_t s = h->stream;
     const size_t nq = static_cast<size_t>(kQ) * h->np;
-    const double *tau = static_cast<const double *>(h->tau);
+    const double *tau = h->sst ? S.tau : static_cast<const double *>(h->tau);
     const int *back = h->d_back;
+    const double *f0 = in.f;
     auto geom = [&](const double *fs, const double *g) {
         if (A.a_sn)
             k_adj_geom<<<grid, block, 0, s>>>(fs, g, A.la, A.lg, G, A.a_sn, A.a_lsq, A.a_rown, A.a_rnbr);
@@ -579,34 +635,42 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const double *f0, 
     };
     k_adj_stage3<<<grid, block, 0, s>>>(A.L, A.lf3, A.lc, A.la, G);
     evalT(S.f3, S.g3, A.lf3);
-    k_adj_stage2<<<grid, block, 0, s>>>(S.B, S.f2, S.g2, tau, A.lf3, A.lc, A.lB, A.la, G);
+    k_adj_stage2<<<grid, block, 0, s>>>(S.B, S.f2, S.g2, tau, A.lf3, A.lc, A.lB, A.la, A.ltau, G);
     cudaMemsetAsync(A.lf2, 0, nq * sizeof(double), s);
     evalT(S.f2, S.g2, A.lf2);
-    k_adj_stage1<<<grid, block, 0, s>>>(f0, S.s1, S.g1, tau, A.lf2, A.lB, A.lc, A.lf0, A.la, G);
+    k_adj_stage1<<<grid, block, 0, s>>>(f0, S.s1, S.g1, tau, A.lf2, A.lB, A.lc, A.lf0, A.la, A.ltau, G);
     cudaMemsetAsync(A.ls1, 0, nq * sizeof(double), s);
     evalT(S.s1, S.g1, A.ls1);
-    k_adj_relax<<<grid, block, 0, s>>>(f0, tau, A.ls1, A.lf0, G);
+    k_adj_relax<<<grid, block, 0, s>>>(f0, tau, A.ls1, A.lf0, A.ltau, G);
+    if (h->sst) {
+        k_adj_sst_update<<<grid, block, 0, s>>>(in.mac, in.k, in.w, in.nt, S.sg, S.f1, A.lk, A.lw, A.lnt, A.ltau,
+                                                A.own, A.fbu, A.lbval, G);
+        k_adj_sst_grad<<<grid, block, 0, s>>>(in.mac, in.k, in.w, S.sg, S.f1, A.fbu, A.own, A.fbg, A.lbval, G,
+                                              back);
+        k_adj_sst_finish<<<grid, block, 0, s>>>(f0, A.own, A.fbu, A.fbg, A.lf0, A.lk, A.lw, A.lnt, G, back);
+    }
     std::swap(A.L, A.lf0);
 }
 
 int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
                  double *dJ_dbedge, double *dJ_dxy) {
     if (!h || instance < 0 || instance >= h->ninst || n_steps < 0 || !w) return FVLBM_ERR_BAD_PARAM;
-    if (h->precision != FVLBM_FP64 || h->sst || h->scheme != 0 || h->dtc != nullptr || h->limit_f ||
-        h->per_stage || h->d_back == nullptr)
+    if (h->precision != FVLBM_FP64 || h->scheme != 0 || h->dtc != nullptr || h->limit_f || h->per_stage ||
+        h->nonorth || h->d_back == nullptr)
         return FVLBM_ERR_NOT_SUPPORTED;
     const InstInfo &I = h->inst[instance];
-    if (dJ_dxy && (!I.mesh || !I.mesh->ppairs.empty())) return FVLBM_ERR_NOT_SUPPORTED;
+    if (dJ_dxy && (h->sst || !I.mesh || !I.mesh->ppairs.empty())) return FVLBM_ERR_NOT_SUPPORTED;
     CK(cudaSetDevice(h->device));
     const Geo<double> G = geo_of<double>(h);
+    const bool sst = h->sst;
     const size_t np = h->np, nq = static_cast<size_t>(kQ) * np;
     // Memory plan.  The stage values one adjoint step reads take 99 doubles per cell (f^n, f^(1),
-    // f^(2), B, f^(3) and the three gradients).  Segments of K consecutive steps keep theirs
-    // whole, K as large as the budget allows (the handle's adjoint budget, else half the free
-    // device memory).  With one segment every step runs once; with several, a first sweep keeps
-    // f^n at each segment start and each segment then runs a second time before its reverse
-    // sweep.
-    const size_t per_step = 99 * np * sizeof(double);
+    // f^(2), B, f^(3) and the three gradients; SST adds 20: the macros, k, omega, nu_t, the SST
+    // gradients, f1 and tau).  Segments of K consecutive steps keep theirs whole, K as large as
+    // the budget allows (the handle's adjoint budget, else half the free device memory).  With
+    // one segment every step runs once; with several, a first sweep keeps the state at each
+    // segment start and each segment then runs a second time before its reverse sweep.
+    const size_t per_step = (sst ? 119 : 99) * np * sizeof(double);
     size_t budget = h->adj_budget;
     if (budget == 0) {
         size_t fr = 0, tot = 0;
@@ -617,19 +681,29 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         std::max<size_t>(1, std::min<size_t>(budget / per_step, static_cast<size_t>(std::max(n_steps, 1)))));
     const int nseg = (n_steps + K - 1) / K;
     AdjScratch M;
-    double *xa, *xb, *Cs, *macs;
-    std::vector<double *> ck(nseg > 1 ? nseg : 0), f0s(K);
+    double *Cs, *macs;
+    AdjState xa, xb;
+    std::vector<AdjState> ck(nseg > 1 ? nseg : 0), st(K);
     std::vector<AdjStep> slot(K);
     AdjVars A{};
     const size_t nbt = std::max(h->nbt, 1);
+    auto state = [&](AdjState &x) {
+        x.f = M.get(nq);
+        if (sst) {
+            x.mac = M.get(3 * np);
+            x.k = M.get(np);
+            x.w = M.get(np);
+            x.nt = M.get(np);
+        }
+    };
     auto carve = [&] {
-        xa = M.get(nq);
-        xb = M.get(nq);
+        state(xa);
+        state(xb);
         Cs = M.get(nq);
         macs = M.get(3 * np);
-        for (auto &x : ck) x = M.get(nq);
+        for (auto &x : ck) state(x);
         for (int k = 0; k < K; ++k) {
-            f0s[k] = M.get(nq);
+            state(st[k]);
             slot[k].s1 = M.get(nq);
             slot[k].g1 = M.get(2 * nq);
             slot[k].f2 = M.get(nq);
@@ -639,6 +713,11 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
             slot[k].f3 = M.get(nq);
             slot[k].g3 = M.get(2 * nq);
             slot[k].mac = macs;
+            if (sst) {
+                slot[k].sg = M.get(12 * np);
+                slot[k].f1 = M.get(np);
+                slot[k].tau = M.get(np);
+            }
         }
         A.L = M.get(nq);
         A.lf3 = M.get(nq);
@@ -649,7 +728,16 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         A.lf2 = M.get(nq);
         A.ls1 = M.get(nq);
         A.lf0 = M.get(nq);
-        A.lbval = M.get(3 * nbt);
+        A.lbval = M.get(5 * nbt);
+        if (sst) {
+            A.lk = M.get(np);
+            A.lw = M.get(np);
+            A.lnt = M.get(np);
+            A.ltau = M.get(np);
+            A.own = M.get(kSstOwn * np);
+            A.fbu = M.get(4 * kSstFU * np);
+            A.fbg = M.get(4 * kSstFG * np);
+        }
         if (dJ_dxy) {
             A.a_sn = M.get(8 * np);
             A.a_lsq = M.get(8 * np);
@@ -669,29 +757,57 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         CK(cudaMemsetAsync(A.a_bnrm, 0, 2 * nbt * sizeof(double), s));
         CK(cudaMemsetAsync(A.a_blen, 0, nbt * sizeof(double), s));
     }
-    // steps k0 .. k1-1 from `start` with their stage values kept; f^{k1} into xb
-    auto fill = [&](int k0, int k1, const double *start) -> int {
-        CK(cudaMemcpyAsync(f0s[0], start, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (sst) {  // J does not depend on k, omega, nu_t of the last state
+        for (double *x : {A.lk, A.lw, A.lnt}) CK(cudaMemsetAsync(x, 0, np * sizeof(double), s));
+        // laminar instances of the batch keep the handle's tau (the SST kernels skip them)
+        for (int k = 0; k < K; ++k)
+            CK(cudaMemcpyAsync(slot[k].tau, h->tau, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    auto copy_state = [&](const AdjState &dst, const AdjState &src) -> int {
+        CK(cudaMemcpyAsync(dst.f, src.f, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (sst) {
+            CK(cudaMemcpyAsync(dst.mac, src.mac, 3 * np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            for (int q = 0; q < 3; ++q) {
+                double *d = q == 0 ? dst.k : (q == 1 ? dst.w : dst.nt);
+                const double *c = q == 0 ? src.k : (q == 1 ? src.w : src.nt);
+                CK(cudaMemcpyAsync(d, c, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            }
+        }
+        return FVLBM_OK;
+    };
+    AdjState h0;  // the handle's current state
+    h0.f = static_cast<double *>(h->fn);
+    if (sst) {
+        h0.mac = static_cast<double *>(h->mac);
+        h0.k = static_cast<double *>(h->kk[h->turb]);
+        h0.w = static_cast<double *>(h->ww[h->turb]);
+        h0.nt = static_cast<double *>(h->nut[h->turb]);
+    }
+    // steps k0 .. k1-1 from `start` with their stage values kept; the state after them into xb
+    auto fill = [&](int k0, int k1, const AdjState &start) -> int {
+        int rc = copy_state(st[0], start);
+        if (rc) return rc;
         for (int n = k0; n < k1; ++n)
-            adj_forward_step(h, G, f0s[n - k0], n + 1 < k1 ? f0s[n + 1 - k0] : xb, slot[n - k0]);
+            adj_forward_step(h, G, st[n - k0], n + 1 < k1 ? st[n + 1 - k0] : xb, slot[n - k0]);
         CK(cudaGetLastError());
         return FVLBM_OK;
     };
-    const double *fN = xb;
-    if (nseg > 1) {  // first sweep: f^N and the segment starts
-        CK(cudaMemcpyAsync(xa, h->fn, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const double *fN = xb.f;
+    if (nseg > 1) {  // first sweep: the last state and the segment starts
+        int rc = copy_state(xa, h0);
+        if (rc) return rc;
         for (int n = 0; n < n_steps; ++n) {
-            if (n % K == 0) CK(cudaMemcpyAsync(ck[n / K], xa, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            if (n % K == 0 && (rc = copy_state(ck[n / K], xa))) return rc;
             adj_forward_step(h, G, xa, xb, slot[0]);
             std::swap(xa, xb);
         }
-        fN = xa;
+        fN = xa.f;
         CK(cudaGetLastError());
     } else if (n_steps > 0) {
-        int rc = fill(0, n_steps, static_cast<const double *>(h->fn));
+        int rc = fill(0, n_steps, h0);
         if (rc) return rc;
     } else {
-        fN = static_cast<const double *>(h->fn);
+        fN = h0.f;
     }
     // J at f^N and its direct derivatives
     double out[4];
@@ -701,7 +817,7 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
     const double q = 0.5 * I.rho0 * I.uref * I.uref * I.lref;
     const double al = I.alpha_deg * M_PI / 180.0, ca = std::cos(al), sa = std::sin(al);
     const double cx = (w[0] * ca - w[1] * sa) / q, cy = (w[0] * sa + w[1] * ca) / q;
-    CK(cudaMemsetAsync(A.lbval, 0, 3 * static_cast<size_t>(std::max(h->nbt, 1)) * sizeof(double), s));
+    CK(cudaMemsetAsync(A.lbval, 0, 5 * nbt * sizeof(double), s));
     k_adj_seed<<<h->ntiles, kTile, 0, s>>>(fN, static_cast<const double *>(h->bnrm),
                                            static_cast<const double *>(h->blen), instance, cx, cy, A.L,
                                            A.lbval, A.a_bnrm, A.a_blen, G);
@@ -710,22 +826,23 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
     for (int c = nseg - 1; c >= 0; --c) {
         const int k0 = c * K, k1 = std::min(n_steps, k0 + K);
         if (nseg > 1) {
-            int rc = fill(k0, k1, ck[c]);
-            if (rc) return rc;
+            int rc2 = fill(k0, k1, ck[c]);
+            if (rc2) return rc2;
         }
-        for (int n = k1 - 1; n >= k0; --n) adj_backward_step(h, G, f0s[n - k0], slot[n - k0], A);
+        for (int n = k1 - 1; n >= k0; --n) adj_backward_step(h, G, st[n - k0], slot[n - k0], A);
         CK(cudaGetLastError());
     }
+    double *xscr = xb.f;
     if (dJ_df && I.nc > 0) {
         k_adj_gather<<<(I.nc + 255) / 256, 256, 0, s>>>(A.L, h->d_perm + perm_offset(h, instance), I.cell_off,
-                                                         I.nc, np, xb);
+                                                         I.nc, np, xscr);
         CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(dJ_df, xb, sizeof(double) * kQ * static_cast<size_t>(I.nc), cudaMemcpyDeviceToHost,
+        CK(cudaMemcpyAsync(dJ_df, xscr, sizeof(double) * kQ * static_cast<size_t>(I.nc), cudaMemcpyDeviceToHost,
                            s));
     }
-    std::vector<double> lb(3 * static_cast<size_t>(std::max(I.nb, 1)));
+    std::vector<double> lb(5 * static_cast<size_t>(std::max(I.nb, 1)));
     if (dJ_dbedge && I.nb > 0)
-        for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < 5; ++c)
             CK(cudaMemcpyAsync(lb.data() + static_cast<size_t>(c) * I.nb,
                                A.lbval + static_cast<size_t>(c) * h->nbt + I.bface_off, sizeof(double) * I.nb,
                                cudaMemcpyDeviceToHost, s));
@@ -785,7 +902,7 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
     if (dJ_dbedge) {
         std::fill(dJ_dbedge, dJ_dbedge + 5 * static_cast<size_t>(I.n_bedges_in), 0.0);
         for (int b = 0; b < I.nb; ++b)
-            for (int c = 0; c < 3; ++c)
+            for (int c = 0; c < 5; ++c)
                 dJ_dbedge[5 * static_cast<size_t>(I.bedge_of[b]) + c] = lb[static_cast<size_t>(c) * I.nb + b];
     }
     return FVLBM_OK;

@@ -200,13 +200,18 @@ def test_adjoint_rejects_unsupported_handles():
         s.close()
     sst = mg.naca0012_cmesh(n_target=2500)
     s = fvlbm.Solver(sst, precision=FP64, device=0)
-    with pytest.raises(fvlbm.FvlbmError) as e:
-        s.adjoint(3, 1.0, 0.0)
+    with pytest.raises(fvlbm.FvlbmError) as e:   # the SST solve's geometry is not transposed
+        s.adjoint(3, 1.0, 0.0, shape=True)
     assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
     with pytest.raises(fvlbm.FvlbmError) as e:
         s.adjoint(-1, 1.0, 0.0)
     assert e.value.code == fvlbm.FVLBM_ERR_BAD_PARAM
     s.close()
+    var = fvlbm.Solver(dataclasses.replace(sst, variant=2), precision=FP64, device=0)
+    with pytest.raises(fvlbm.FvlbmError) as e:
+        var.adjoint(3, 1.0, 0.0)
+    assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
+    var.close()
     # shape gradients of periodic meshes are not built; the other outputs are
     per = fvlbm.Solver(mg.Case(mg.periodic_box(8), nu=1e-3, cfl=0.5), precision=FP64, device=0)
     per.adjoint(2, 1.0, 0.0)
@@ -214,3 +219,81 @@ def test_adjoint_rejects_unsupported_handles():
         per.adjoint(2, 1.0, 0.0, shape=True)
     assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
     per.close()
+
+
+# ------------------------------------------------------------------ k-omega SST
+def _naca_sst(alpha_deg=4.0):
+    return mg.naca0012_cmesh(n_target=2500, alpha_deg=alpha_deg)
+
+
+def _bfs_sst():
+    return mg.bfs_hybrid(n_target=3000)
+
+
+SST_CASES = {"naca": _naca_sst, "bfs": _bfs_sst}
+
+
+def _sst_seeds(case, rng):
+    """Random seeds of f^0 and of all five boundary values (k_b, omega_b relative to their
+    values)."""
+    m = case.mesh.normalized()
+    g = 1e-4 * rng.standard_normal((m.n_cells, 9))
+    d = np.zeros((m.n_bedges, 5))
+    d[:, :3] = 1e-3 * rng.standard_normal((m.n_bedges, 3))
+    d[:, 3:] = 1e-3 * m.bedge_val[:, 3:] * rng.standard_normal((m.n_bedges, 2))
+    return g, d
+
+
+@pytest.mark.parametrize("name", sorted(SST_CASES))
+@pytest.mark.parametrize("n", [0, 1, 4, 15])
+def test_adjoint_sst_dot_product_against_tangent(name, n):
+    """SST cases: <dJ/df^0, g> + <dJ/dbval, d> from one adjoint solve equals the tangent's
+    dJ/dp for the same seeds (the SST solve, its tau, the macros it reads and all five boundary
+    values transposed).  On the backward-facing step the inlet (k_b, omega_b) and the outlet
+    reach the walls within a few steps."""
+    case = SST_CASES[name]()
+    warm = 8
+    g, d = _sst_seeds(case, np.random.default_rng(200 + n))
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    s.step(warm)
+    J, dJdf, dJdb, _ = s.adjoint(n, *W)
+    s.close()
+    Jt, dJt = _tangent_dJ(case, warm, n, g, d)
+    adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
+    assert abs(J - Jt) <= 1e-10 * abs(Jt)
+    assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)
+
+
+def test_adjoint_sst_inflow_turbulence_and_alpha():
+    """Parameter derivatives from one adjoint solve each, against the tangent: the inflow
+    eddy-viscosity ratio of the backward-facing step through omega_b = k_b / (nu ratio) on the
+    inlet, and alpha of the NACA case through (u_b, v_b) plus the drag / lift projection."""
+    bfs = _bfs_sst()
+    m = bfs.mesh.normalized()
+    inlet = m.bedge_type == mg.BC_INLET
+    d_ratio = np.zeros((m.n_bedges, 5))
+    d_ratio[inlet, 4] = -m.bedge_val[inlet, 4]          # ratio = 1
+    naca = _naca_sst()
+    mn = naca.mesh.normalized()
+    ff = mn.bedge_type == mg.BC_FARFIELD
+    d_alpha = np.zeros((mn.n_bedges, 5))
+    d_alpha[ff, 1] = -mn.bedge_val[ff, 2]
+    d_alpha[ff, 2] = mn.bedge_val[ff, 1]
+    n = 20
+    for case, d, dalpha in ((bfs, d_ratio, 0.0), (naca, d_alpha, 1.0)):
+        s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+        s.step(10)
+        _, _, dJdb, _ = s.adjoint(n, *W)
+        s.close()
+        t = fvlbm.Solver(case, precision=TAN, device=0)
+        t.step(10)
+        t.tangent_seed(d)
+        t.step(n)
+        val, dv = t.forces_tangent(dalpha=dalpha)
+        t.close()
+        dJt = W[0] * dv["cd"] + W[1] * dv["cl"]
+        adj = float(np.sum(dJdb * d))
+        if dalpha:
+            adj += W[0] * val["cl"] - W[1] * val["cd"]
+        assert abs(dJt) > 1e-12, (dalpha, dJt)
+        assert abs(adj - dJt) <= 1e-8 * abs(dJt), (dalpha, adj, dJt)
