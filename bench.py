@@ -563,15 +563,17 @@ def run_profile_mode(args):
 
 
 def run_adjoint_mode(args):
-    """Cost of the discrete adjoint (fvlbm_adjoint, FP64, laminar) against the FP64 primal step it
-    differentiates, on a laminar NACA 0012 C-mesh (Re_c = 2000, alpha = 4 degrees) or a 256 x 256
-    lid-driven cavity.  Per-step costs are marginal: (time at 3S steps - time at S steps) / 2S, so
+    """Cost of the discrete adjoint (fvlbm_adjoint, FP64) against the FP64 primal step it
+    differentiates, on the NACA 0012 C-mesh (k-omega SST, Re_c = 6e6, alpha = 4 degrees, or
+    laminar at Re_c = 2000) or a 256 x 256 lid-driven cavity.  Per-step costs are marginal: (time at 3S steps - time at S steps) / 2S, so
     allocation and set-up drop out.  Not a bench line of the step; prints one JSON object."""
     import dataclasses
     import torch
     from paper_1812_00394_gb300 import fvlbm, meshgen as mg
     torch.cuda.set_device(0)
-    if args.adjoint_case == "naca_laminar":
+    if args.adjoint_case == "naca_sst":
+        case = mg.naca0012_cmesh(n_target=args.adjoint_cells, alpha_deg=4.0)
+    elif args.adjoint_case == "naca_laminar":
         case = dataclasses.replace(mg.naca0012_cmesh(n_target=args.adjoint_cells, re_c=2000.0,
                                                      alpha_deg=4.0), sst=False)
     else:
@@ -589,15 +591,19 @@ def run_adjoint_mode(args):
         t1 = time.perf_counter()
         s.adjoint(n, 1.0, 0.0)
         t2 = time.perf_counter()
-        s.adjoint(n, 1.0, 0.0, shape=True)
+        if not case.sst:   # shape gradients: laminar only
+            s.adjoint(n, 1.0, 0.0, shape=True)
         t3 = time.perf_counter()
         t[n] = (t1 - t0, t2 - t1, t3 - t2)
     d = 2 * n1
     fwd, adj, shp = ((t[3 * n1][q] - t[n1][q]) / d * 1e3 for q in range(3))
+    if case.sst:
+        shp = None
     print(json.dumps({"mode": "adjoint", "case": args.adjoint_case, "cells": case.mesh.n_cells,
                       "steps": [n1, 3 * n1], "fwd_fp64_ms_per_step": fwd,
                       "adjoint_ms_per_step": adj, "adjoint_with_shape_ms_per_step": shp,
-                      "adjoint_over_fwd": adj / fwd, "shape_setup_s": t[n1][2] - n1 * shp / 1e3}))
+                      "adjoint_over_fwd": adj / fwd,
+                      "shape_setup_s": None if shp is None else t[n1][2] - n1 * shp / 1e3}))
     s.close()
     return 0
 
@@ -620,7 +626,8 @@ def main():
                     help="profile mode: 0 fused stage kernels, 1 two-pass kernels")
     ap.add_argument("--adjoint-mode", action="store_true",
                     help="time the FP64 laminar adjoint against its primal step (not a bench line)")
-    ap.add_argument("--adjoint-case", default="naca_laminar", choices=["naca_laminar", "cavity256"])
+    ap.add_argument("--adjoint-case", default="naca_laminar",
+                    choices=["naca_laminar", "naca_sst", "cavity256"])
     ap.add_argument("--adjoint-cells", type=int, default=200000)
     args = ap.parse_args()
     if args.warmup < 3:

@@ -277,32 +277,37 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
  *
  *   J = w[0] C_D + w[1] C_L of `instance` after n_steps steps from the handle's current state,
  *
- * C_D, C_L as fvlbm_forces.  The step differentiated is the IMEX step of Sec. 3.1-3.2 (Steps 2-7)
- * with one dt per instance, as the two-pass kernels run it in FP64 (the fused kernels give the
- * same values up to rounding).  Where the step is not differentiable (the upwind switch on
- * e.n = 0) the derivative of the branch the value takes is used, as in the tangent.
+ * C_D, C_L as fvlbm_forces.  The step differentiated is the IMEX step of Sec. 3.1-3.2 (Steps 1-7:
+ * the k-omega SST solve on SST instances, then the stages) with one dt per instance, as the
+ * two-pass kernels run it in FP64 (the fused kernels give the same values up to rounding).
+ * Where the step is not differentiable (the upwind switch on e.n = 0, the SST's limiter, clip
+ * and blending branches) the derivative of the branch the value takes is used, as in the
+ * tangent.
  * Outputs (host, each may be NULL):
  *   J              the objective's value;
  *   dJ_df          [n_cells * 9] dJ/df of the current state, cell-major like fvlbm_get_f;
  *   dJ_dbedge_val  [5 * n_bedges] dJ/d(rho_b, u_b, v_b, k_b, omega_b) in boundary-edge input
- *                  order, the layout of fvlbm_tangent_seed (k_b and omega_b: 0; periodic
- *                  edges: 0);
+ *                  order, the layout of fvlbm_tangent_seed (k_b, omega_b: 0 on laminar
+ *                  instances; periodic edges: 0);
  *   dJ_dxy         [2 * n_nodes] dJ/d(x, y) of every mesh node at fixed dt and fixed initial
  *                  state, through the preprocessed geometry (areas, face normals and lengths,
  *                  centroids, face offsets, least-squares weights, the wall normals and lengths
  *                  of the force): the gradient whose inner product with a node displacement is
- *                  what fvlbm_tangent_seed_nodes gives for it.  Not for meshes with periodic
- *                  pairs (FVLBM_ERR_NOT_SUPPORTED).
+ *                  what fvlbm_tangent_seed_nodes gives for it.  Laminar handles without periodic
+ *                  pairs only (else FVLBM_ERR_NOT_SUPPORTED).
+ * The initial k, omega and nu_t of SST instances are held fixed (their adjoints are not output).
  * Neither the state nor the step count of the handle changes.  The call runs n_steps forward
- * steps that keep their stage values (99 doubles per cell and step) and n_steps adjoint steps.
+ * steps that keep their stage values (99 doubles per cell and step, 119 with SST) and n_steps
+ * adjoint steps.
  * Where the stage values of all steps do not fit the adjoint budget (fvlbm_set_adjoint_budget;
  * default half the free device memory), the steps are taken in segments of as many steps as
- * fit: a first sweep keeps f at each segment start and each segment runs again before its
+ * fit: a first sweep keeps the state at each segment start and each segment runs again before its
  * reverse sweep (2 n_steps forward steps).  The device memory is allocated for the call and
- * freed before it returns (about 60 + 99 K doubles per cell for segments of K steps, 32 more
- * with dJ_dxy); dJ_dxy adds one pass over the cells on the host.
- * Valid on FVLBM_FP64 handles whose instances are all laminar, with the IMEX scheme, one dt per
- * instance and no limiter or per-stage variant; else FVLBM_ERR_NOT_SUPPORTED.  Synchronises.
+ * freed before it returns (about 60 + 99 K doubles per cell for segments of K steps, 119 K with
+ * SST, 32 more with dJ_dxy); dJ_dxy adds one pass over the cells on the host.
+ * Valid on FVLBM_FP64 handles with the IMEX scheme, one dt per instance and the default reading
+ * (variant 0: no limiter, non-orthogonal correction, per-stage solve or production limiter);
+ * else FVLBM_ERR_NOT_SUPPORTED.  Synchronises.
  * Errors: BAD_PARAM (w NULL, n_steps < 0, bad instance), NOT_SUPPORTED, OOM, CUDA. */
 int fvlbm_adjoint(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
                   double *dJ_dbedge_val, double *dJ_dxy);

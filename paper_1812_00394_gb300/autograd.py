@@ -16,11 +16,14 @@ Two backward passes compute the same derivatives of the discrete step:
     tangent solve with one instance per parameter gives every column of the Jacobian
     J = d(C_L, C_D)/dp at once, and the gradient is grad_output @ J.  Its cost grows with the
     number of parameters.
-  - "adjoint" (laminar cases): the library's reverse mode (fvlbm_adjoint); one adjoint solve of
-    J_w = grad_output . (C_L, C_D) gives dJ_w/d(boundary values) and dJ_w/d(node positions), and
-    the gradient is their projection on the parameters plus the explicit dependence of the drag
-    and lift directions on alpha.  Its cost does not grow with the number of wall nodes.
-The default ("auto") takes the adjoint for laminar cases and the tangent otherwise.
+  - "adjoint": the library's reverse mode (fvlbm_adjoint); one adjoint solve of
+    J_w = grad_output . (C_L, C_D) gives dJ_w/d(boundary values) and, on laminar cases,
+    dJ_w/d(node positions); the gradient is their projection on the parameters plus the
+    explicit dependence of the drag and lift directions on alpha.  Its cost does not grow with
+    the number of parameters.  Wall-node parameters need a laminar case (the SST solve's
+    geometry is not transposed).
+The default ("auto") takes the adjoint for laminar cases and for SST cases without wall-node
+parameters, and the tangent otherwise.
 """
 from __future__ import annotations
 
@@ -40,9 +43,12 @@ class AirfoilForces:
     def __init__(self, base_case, wall_nodes, steps: int, device: int = 0, mode: str = "auto"):
         if mode not in ("auto", "tangent", "adjoint"):
             raise ValueError(f"unknown backward mode {mode!r}")
-        if mode == "adjoint" and base_case.sst:
-            raise ValueError("the adjoint backward needs a laminar case")
-        self.mode = ("tangent" if base_case.sst else "adjoint") if mode == "auto" else mode
+        shape = len(wall_nodes) > 0
+        if mode == "adjoint" and base_case.sst and shape:
+            raise ValueError("wall-node parameters in the adjoint backward need a laminar case")
+        if mode == "auto":
+            mode = "tangent" if (base_case.sst and shape) else "adjoint"
+        self.mode = mode
         self.base = dataclasses.replace(base_case, mesh=base_case.mesh.normalized())
         m = self.base.mesh
         self.steps = int(steps)
@@ -115,19 +121,21 @@ class AirfoilForces:
         return d_alpha, d_ratio
 
     def vjp(self, p: np.ndarray, g: np.ndarray, out: np.ndarray) -> np.ndarray:
-        """g @ d(C_L, C_D)/dp from one adjoint solve (laminar cases); out = (C_L, C_D) at p."""
+        """g @ d(C_L, C_D)/dp from one adjoint solve; out = (C_L, C_D) at p."""
         case = self.case_at(p)
         d_alpha, d_ratio = self._bval_directions(case, p)
         s = fvlbm.Solver(case, precision=fvlbm.FVLBM_FP64, device=self.device, kernel_path=1)
         # J_w = g0 C_L + g1 C_D
-        _, _, dbv, dxy = s.adjoint(self.steps, w_cd=float(g[1]), w_cl=float(g[0]), shape=True)
+        shape = len(self.wall_nodes) > 0
+        _, _, dbv, dxy = s.adjoint(self.steps, w_cd=float(g[1]), w_cl=float(g[0]), shape=shape)
         s.close()
         # dC_D/dalpha = C_L and dC_L/dalpha = -C_D through the drag and lift directions
         proj = float(g[1]) * out[0] - float(g[0]) * out[1]
         grad = np.empty(self.n_params())
         grad[0] = float(np.sum(dbv * d_alpha)) + proj
         grad[1] = float(np.sum(dbv * d_ratio))
-        grad[2:] = np.einsum("jc,jc->j", dxy[self.wall_nodes], self.normals)
+        if shape:
+            grad[2:] = np.einsum("jc,jc->j", dxy[self.wall_nodes], self.normals)
         return grad
 
     def jacobian(self, p: np.ndarray) -> np.ndarray:

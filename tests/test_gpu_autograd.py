@@ -73,3 +73,20 @@ def test_autograd_adjoint_backward_matches_tangent_and_fd():
         vp, vm = model.value(p0 + e), model.value(p0 - e)
         fd = ((0.8 * vp[0] - 2.0 * vp[1]) - (0.8 * vm[0] - 2.0 * vm[1])) / (2 * h)
         assert abs(ga[q] - fd) <= 1e-5 * abs(fd), (q, ga[q], fd)
+
+
+def test_autograd_sst_adjoint_backward_matches_tangent():
+    """SST NACA 0012 with (alpha, inflow ratio) only: the default backward is the adjoint, and
+    it equals the tangent backward."""
+    base = mg.naca0012_cmesh(n_target=2500, re_c=1e4, alpha_deg=4.0)
+    p0 = np.array([math.radians(4.0), 1.0])
+    grads = {}
+    for mode in ("auto", "tangent"):
+        model = fa.AirfoilForces(base, [], steps=30, device=0, mode=mode)
+        assert model.mode == ("adjoint" if mode == "auto" else "tangent")
+        p = torch.tensor(p0, requires_grad=True)
+        out = fa.forces(model, p)
+        (out[0] + 0.5 * out[1]).backward()
+        grads[mode] = p.grad.numpy().copy()
+    for q in range(2):
+        assert abs(grads["auto"][q] - grads["tangent"][q]) <= 1e-8 * abs(grads["tangent"][q]) + 1e-14, q
