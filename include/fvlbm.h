@@ -293,8 +293,9 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
  *                  state, through the preprocessed geometry (areas, face normals and lengths,
  *                  centroids, face offsets, least-squares weights, the wall normals and lengths
  *                  of the force): the gradient whose inner product with a node displacement is
- *                  what fvlbm_tangent_seed_nodes gives for it.  Laminar handles without periodic
- *                  pairs only (else FVLBM_ERR_NOT_SUPPORTED).
+ *                  what fvlbm_tangent_seed_nodes gives for it; on SST instances also through
+ *                  1/|d| and the wall distance d.  Not for meshes with periodic pairs
+ *                  (FVLBM_ERR_NOT_SUPPORTED).
  * The initial k, omega and nu_t of SST instances are held fixed (their adjoints are not output).
  * Neither the state nor the step count of the handle changes.  The call runs n_steps forward
  * steps that keep their stage values (99 doubles per cell and step, 119 with SST) and n_steps
@@ -304,7 +305,8 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
  * fit: a first sweep keeps the state at each segment start and each segment runs again before its
  * reverse sweep (2 n_steps forward steps).  The device memory is allocated for the call and
  * freed before it returns (about 60 + 99 K doubles per cell for segments of K steps, 119 K with
- * SST, 32 more with dJ_dxy); dJ_dxy adds one pass over the cells on the host.
+ * SST, 32 more with dJ_dxy); dJ_dxy adds one pass over the cells on the host (SST: and a
+ * nearest-wall search per cell).
  * Valid on FVLBM_FP64 handles with the IMEX scheme, one dt per instance and the default reading
  * (variant 0: no limiter, non-orthogonal correction, per-stage solve or production limiter);
  * else FVLBM_ERR_NOT_SUPPORTED.  Synchronises.

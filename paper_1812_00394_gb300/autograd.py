@@ -17,13 +17,11 @@ Two backward passes compute the same derivatives of the discrete step:
     J = d(C_L, C_D)/dp at once, and the gradient is grad_output @ J.  Its cost grows with the
     number of parameters.
   - "adjoint": the library's reverse mode (fvlbm_adjoint); one adjoint solve of
-    J_w = grad_output . (C_L, C_D) gives dJ_w/d(boundary values) and, on laminar cases,
-    dJ_w/d(node positions); the gradient is their projection on the parameters plus the
-    explicit dependence of the drag and lift directions on alpha.  Its cost does not grow with
-    the number of parameters.  Wall-node parameters need a laminar case (the SST solve's
-    geometry is not transposed).
-The default ("auto") takes the adjoint for laminar cases and for SST cases without wall-node
-parameters, and the tangent otherwise.
+    J_w = grad_output . (C_L, C_D) gives dJ_w/d(boundary values) and dJ_w/d(node positions);
+    the gradient is their projection on the parameters plus the explicit dependence of the drag
+    and lift directions on alpha.  Its cost does not grow with the number of parameters.  It
+    needs the default reading (variant 0).
+The default ("auto") takes the adjoint for the default reading and the tangent otherwise.
 """
 from __future__ import annotations
 
@@ -43,11 +41,11 @@ class AirfoilForces:
     def __init__(self, base_case, wall_nodes, steps: int, device: int = 0, mode: str = "auto"):
         if mode not in ("auto", "tangent", "adjoint"):
             raise ValueError(f"unknown backward mode {mode!r}")
-        shape = len(wall_nodes) > 0
-        if mode == "adjoint" and base_case.sst and shape:
-            raise ValueError("wall-node parameters in the adjoint backward need a laminar case")
+        reading = int(getattr(base_case, "variant", 0))
+        if mode == "adjoint" and reading:
+            raise ValueError("the adjoint backward needs the default reading (variant 0)")
         if mode == "auto":
-            mode = "tangent" if (base_case.sst and shape) else "adjoint"
+            mode = "tangent" if reading else "adjoint"
         self.mode = mode
         self.base = dataclasses.replace(base_case, mesh=base_case.mesh.normalized())
         m = self.base.mesh

@@ -608,6 +608,7 @@ struct AdjVars {
     double *L, *lf3, *lc, *la, *lg, *lB, *lf2, *ls1, *lf0, *lbval;
     double *a_sn = nullptr, *a_lsq = nullptr, *a_rown = nullptr, *a_rnbr = nullptr;  // shape adjoint
     double *a_bnrm = nullptr, *a_blen = nullptr;
+    double *a_dinv = nullptr, *a_wd = nullptr;  // shape adjoint, SST only
     double *lk = nullptr, *lw = nullptr, *lnt = nullptr, *ltau = nullptr;  // SST
     double *own = nullptr, *fbu = nullptr, *fbg = nullptr;
 };
@@ -643,10 +644,11 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in
     evalT(S.s1, S.g1, A.ls1);
     k_adj_relax<<<grid, block, 0, s>>>(f0, tau, A.ls1, A.lf0, A.ltau, G);
     if (h->sst) {
+        const AdjGeo AG{A.a_sn, A.a_rown, A.a_rnbr, A.a_lsq, A.a_dinv, A.a_wd};
         k_adj_sst_update<<<grid, block, 0, s>>>(in.mac, in.k, in.w, in.nt, S.sg, S.f1, A.lk, A.lw, A.lnt, A.ltau,
-                                                A.own, A.fbu, A.lbval, G);
+                                                A.own, A.fbu, A.lbval, G, AG);
         k_adj_sst_grad<<<grid, block, 0, s>>>(in.mac, in.k, in.w, S.sg, S.f1, A.fbu, A.own, A.fbg, A.lbval, G,
-                                              back);
+                                              back, AG);
         k_adj_sst_finish<<<grid, block, 0, s>>>(f0, A.own, A.fbu, A.fbg, A.lf0, A.lk, A.lw, A.lnt, G, back);
     }
     std::swap(A.L, A.lf0);
@@ -659,7 +661,7 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         h->nonorth || h->d_back == nullptr)
         return FVLBM_ERR_NOT_SUPPORTED;
     const InstInfo &I = h->inst[instance];
-    if (dJ_dxy && (h->sst || !I.mesh || !I.mesh->ppairs.empty())) return FVLBM_ERR_NOT_SUPPORTED;
+    if (dJ_dxy && (!I.mesh || !I.mesh->ppairs.empty())) return FVLBM_ERR_NOT_SUPPORTED;
     CK(cudaSetDevice(h->device));
     const Geo<double> G = geo_of<double>(h);
     const bool sst = h->sst;
@@ -745,6 +747,10 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
             A.a_rnbr = M.get(8 * np);
             A.a_bnrm = M.get(2 * nbt);
             A.a_blen = M.get(nbt);
+            if (sst) {
+                A.a_dinv = M.get(4 * np);
+                A.a_wd = M.get(np);
+            }
         }
     };
     carve();
@@ -756,6 +762,10 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
             CK(cudaMemsetAsync(x, 0, 8 * np * sizeof(double), s));
         CK(cudaMemsetAsync(A.a_bnrm, 0, 2 * nbt * sizeof(double), s));
         CK(cudaMemsetAsync(A.a_blen, 0, nbt * sizeof(double), s));
+        if (sst) {
+            CK(cudaMemsetAsync(A.a_dinv, 0, 4 * np * sizeof(double), s));
+            CK(cudaMemsetAsync(A.a_wd, 0, np * sizeof(double), s));
+        }
     }
     if (sst) {  // J does not depend on k, omega, nu_t of the last state
         for (double *x : {A.lk, A.lw, A.lnt}) CK(cudaMemsetAsync(x, 0, np * sizeof(double), s));
@@ -855,13 +865,20 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         const size_t nc = I.nc;
         CK(cudaMemcpyAsync(perm.data(), h->d_perm + perm_offset(h, instance), sizeof(int) * nc,
                            cudaMemcpyDeviceToHost, s));
-        runs.resize(4 * 8 * nc + 3 * static_cast<size_t>(std::max(I.nb, 1)));
+        runs.resize(4 * 8 * nc + 5 * nc + 3 * static_cast<size_t>(std::max(I.nb, 1)));
         const double *src[4] = {A.a_sn, A.a_lsq, A.a_rown, A.a_rnbr};
         for (int q = 0; q < 4; ++q)
             for (int c = 0; c < 8; ++c)
                 CK(cudaMemcpyAsync(runs.data() + (8 * q + c) * nc, src[q] + c * np + I.cell_off, sizeof(double) * nc,
                                    cudaMemcpyDeviceToHost, s));
-        double *bt = runs.data() + 32 * nc;
+        if (sst) {  // 1 / |d| [4 runs] and the wall distance
+            for (int c = 0; c < 4; ++c)
+                CK(cudaMemcpyAsync(runs.data() + (32 + c) * nc, A.a_dinv + c * np + I.cell_off, sizeof(double) * nc,
+                                   cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(runs.data() + 36 * nc, A.a_wd + I.cell_off, sizeof(double) * nc,
+                               cudaMemcpyDeviceToHost, s));
+        }
+        double *bt = runs.data() + 37 * nc;
         if (I.nb > 0) {
             CK(cudaMemcpyAsync(bt, A.a_bnrm + I.bface_off, sizeof(double) * I.nb, cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(bt + I.nb, A.a_bnrm + h->nbt + I.bface_off, sizeof(double) * I.nb,
@@ -882,10 +899,18 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
                 for (int c = 0; c < 8; ++c)  // component c = 2 l + (x, y) of slot l
                     (*dst[q])[8 * static_cast<size_t>(perm[k]) + c] = runs[(8 * q + c) * nc + k];
         }
+        if (sst) {
+            GA.dinv.assign(4 * nc, 0.0);
+            GA.wdist.assign(nc, 0.0);
+            for (size_t k = 0; k < nc; ++k) {
+                for (int l = 0; l < 4; ++l) GA.dinv[4 * static_cast<size_t>(perm[k]) + l] = runs[(32 + l) * nc + k];
+                GA.wdist[perm[k]] = runs[36 * nc + k];
+            }
+        }
         const size_t nbe = mc.btype.size();
         GA.bnrm.assign(2 * nbe, 0.0);
         GA.blen.assign(nbe, 0.0);
-        const double *bt = runs.data() + 32 * nc;
+        const double *bt = runs.data() + 37 * nc;
         for (int f = 0; f < I.nb; ++f) {
             const int e = I.bedge_of[f];
             GA.bnrm[2 * e] = bt[f];

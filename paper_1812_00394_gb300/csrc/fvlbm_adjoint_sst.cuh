@@ -32,6 +32,12 @@ __device__ __forceinline__ void sst_bvals_T(const Geo<double> &G, int b, const d
     }
 }
 
+// Adjoints of the geometry arrays the SST kernels read (all NULL: no shape gradient): n dl / A,
+// face offsets r_own and r_nbr, least-squares weights, 1 / |d| and the wall distance.
+struct AdjGeo {
+    double *sn, *rown, *rnbr, *lsq, *dinv, *wd;
+};
+
 // Per-face buffer layout: value c of face slot m of cell i at buf[(c * 4 + m) * np + i].
 // Update buffer (10 values): adjoints of the neighbour's u, v, k, omega, limited gradients (4),
 // f1, nu_t.  Gradient buffer (4 values): adjoints of the neighbour's u, v, k, omega.
@@ -46,7 +52,7 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
     const double *__restrict__ nut, const double *__restrict__ grads, const double *__restrict__ f1a,
     const double *__restrict__ lk1, const double *__restrict__ lw1, const double *__restrict__ lnt1,
     const double *__restrict__ ltau, double *__restrict__ own, double *__restrict__ fbuf,
-    double *__restrict__ lbval, Geo<double> G) {
+    double *__restrict__ lbval, Geo<double> G, AdjGeo AG) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -151,11 +157,14 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
         l_wn += l_Dn * kA1;
     }
     const double l_arg2 = l_f2 * (1.0 - f2 * f2) * 2.0 * arg2;
+    double l_di = 0.0;
     if (X2 > X1) {
         l_wn -= l_arg2 * X2 / wn;
+        l_di -= l_arg2 * 2.0 * X2 / di;
     } else {
         if (kn > 0.0) l_kn += l_arg2 / (kBstar * wn * di * sqrt(kn));
         l_wn -= l_arg2 * X1 / wn;
+        l_di -= l_arg2 * X1 / di;
     }
     const double l_kn0 = kn0 > 0.0 ? l_kn : 0.0;
     const double l_wn0 = wn0 > P.omega_min ? l_wn : 0.0;
@@ -224,6 +233,16 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
             const double l_kup = l_ck * un, l_wup = l_cw * un;
             const double l_gkf = l_dk * dkn * dla, l_gwf = l_dw * dwn * dla;
             const double l_dkn = l_dk * gkf * dla, l_dwn = l_dw * gwf * dla;
+            if (AG.sn != nullptr) {  // geometry: n dl / A (through u.n and dl/A), r_nbr, 1/|d|
+                const double l_dla = l_dk * gkf * dkn + l_dw * gwf * dwn;
+                AG.sn[(2 * m) * np + i] += l_un * 0.5 * (ui + f.u) + l_dla * f.snx / dla;
+                AG.sn[(2 * m + 1) * np + i] += l_un * 0.5 * (vi + f.v) + l_dla * f.sny / dla;
+                if (!up) {
+                    AG.rnbr[(2 * m) * np + i] += l_kup * f.lg[0] + l_wup * f.lg[2];
+                    AG.rnbr[(2 * m + 1) * np + i] += l_kup * f.lg[1] + l_wup * f.lg[3];
+                }
+                AG.dinv[m * np + i] += l_dkn * (f.k - ki) + l_dwn * (f.w - wi);
+            }
             lf[2] += l_dkn * f.dinv;
             l_ki -= l_dkn * f.dinv;
             lf[3] += l_dwn * f.dinv;
@@ -263,6 +282,13 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
             }
             lf[0] += l_un * f.snx;
             lf[1] += l_un * f.sny;
+            if (AG.sn != nullptr) {
+                const double l_dla = l_dk * (nu + sk_i * nti) * dkn + l_dw * (nu + sw_i * nti) * dwn;
+                AG.sn[(2 * m) * np + i] += l_un * f.u + l_dla * f.snx / dla;
+                AG.sn[(2 * m + 1) * np + i] += l_un * f.v + l_dla * f.sny / dla;
+                AG.dinv[m * np + i] += l_dk * (nu + sk_i * nti) * dla * (f.k - ki) +
+                                       l_dw * (nu + sw_i * nti) * dla * (f.w - wi);
+            }
             l_sk += l_dk * nti * dkn * dla;
             l_sw += l_dw * nti * dwn * dla;
             l_nti += (l_dk * sk_i * dkn + l_dw * sw_i * dwn) * dla;
@@ -272,6 +298,8 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
             lf[3] += l_dwn * f.dinv;
             l_wi -= l_dwn * f.dinv;
             double lown[4] = {0, 0, 0, 0};
+            if (G.btype[-G.nbr[m * np + i] - 1] == FVLBM_BC_WALL)  // omega_b = 60 nu / (beta1 d^2)
+                l_di -= lf[3] * 2.0 * f.w / di;
             sst_bvals_T(G, -G.nbr[m * np + i] - 1, lf, lown, lbval);
             l_ui += lown[0];
             l_vi += lown[1];
@@ -279,6 +307,10 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
             l_wi += lown[3];
 #pragma unroll
             for (int c = 0; c < kSstFU; ++c) lf[c] = 0.0;  // nothing goes to a neighbour
+        }
+        if (AG.sn != nullptr) {
+            AG.rown[(2 * m) * np + i] += l_kin * lgi[0] + l_win * lgi[2];
+            AG.rown[(2 * m + 1) * np + i] += l_kin * lgi[1] + l_win * lgi[3];
         }
         l_ki += l_kin;
         l_lgi[0] += l_kin * f.rox;
@@ -290,6 +322,7 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
         for (int c = 0; c < kSstFU; ++c) fbuf[(c * 4 + m) * np + i] = lf[c];
     }
     l_f1 += l_sk * (kSk1 - kSk2) + l_sw * (kSw1 - kSw2);
+    if (AG.sn != nullptr) AG.wd[i] += l_di;
     own[0 * np + i] = l_ui;
     own[1 * np + i] = l_vi;
     own[2 * np + i] = l_ki;
@@ -309,7 +342,7 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_grad(
     const double *__restrict__ mac, const double *__restrict__ kk, const double *__restrict__ ww,
     const double *__restrict__ grads, const double *__restrict__ f1a, const double *__restrict__ fbu,
     double *__restrict__ own, double *__restrict__ fbg, double *__restrict__ lbval, Geo<double> G,
-    const int *__restrict__ back) {
+    const int *__restrict__ back, AdjGeo AG) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -413,6 +446,7 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_grad(
     l_own[3] -= l_a * a / wi;
     l_own[3] -= l_bb * bb / wi;
     l_own[2] += l_c * 4.0 * kSw2 / (cd * di * di);
+    double l_di = -(l_a * a + 2.0 * l_bb * bb + 2.0 * l_c * c) / di;
     const double l_cd = -l_c * c / cd;
     if (cd0 > 1e-20) {
         l_own[3] -= l_cd * cd0 / wi;
@@ -434,6 +468,10 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_grad(
         const double l_N = l_pk / dkf, l_d = -l_pk * pk / dkf;
         l_g[4] += l_d * rx;
         l_g[5] += l_d * ry;
+        if (AG.sn != nullptr) {
+            AG.rown[(2 * mk) * np + i] += l_d * g[4];
+            AG.rown[(2 * mk + 1) * np + i] += l_d * g[5];
+        }
         const int e = khi_side ? ikhi : iklo;  // the extreme: -1 is k_i itself (k_i - k_i)
         if (e >= 0) {
             l_q[e][2] += l_N;
@@ -446,6 +484,10 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_grad(
         const double l_N = l_pw / dwf, l_d = -l_pw * pw / dwf;
         l_g[6] += l_d * rx;
         l_g[7] += l_d * ry;
+        if (AG.sn != nullptr) {
+            AG.rown[(2 * mw) * np + i] += l_d * g[6];
+            AG.rown[(2 * mw + 1) * np + i] += l_d * g[7];
+        }
         const int e = whi_side ? iwhi : iwlo;
         if (e >= 0) {
             l_q[e][3] += l_N;
@@ -455,11 +497,18 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_grad(
     // g = sum_m W_m (q_m - own)
     for (int m = 0; m < 4; ++m) {
         if (!has[m]) continue;
+        double lwx = 0.0, lwy = 0.0;
 #pragma unroll
         for (int c4 = 0; c4 < 4; ++c4) {
             const double l = W[2 * m] * l_g[2 * c4] + W[2 * m + 1] * l_g[2 * c4 + 1];
             l_q[m][c4] += l;
             l_own[c4] -= l;
+            lwx += l_g[2 * c4] * (q[m][c4] - ow[c4]);
+            lwy += l_g[2 * c4 + 1] * (q[m][c4] - ow[c4]);
+        }
+        if (AG.sn != nullptr) {
+            AG.lsq[(2 * m) * np + i] += lwx;
+            AG.lsq[(2 * m + 1) * np + i] += lwy;
         }
     }
     for (int m = 0; m < 4; ++m) {
@@ -469,6 +518,7 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_grad(
 #pragma unroll
                 for (int c4 = 0; c4 < 4; ++c4) out[c4] = l_q[m][c4];
             } else {
+                if (G.btype[-nbs[m] - 1] == FVLBM_BC_WALL) l_di -= l_q[m][3] * 2.0 * q[m][3] / di;
                 sst_bvals_T(G, -nbs[m] - 1, l_q[m], l_own, lbval);
             }
         }
@@ -477,6 +527,7 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_grad(
     }
 #pragma unroll
     for (int c4 = 0; c4 < 4; ++c4) own[c4 * np + i] += l_own[c4];
+    if (AG.sn != nullptr) AG.wd[i] += l_di;
 }
 
 // ---- totals: lam(u, v, k, omega, nu_t) of every cell = own + neighbours' face entries; the

@@ -442,7 +442,7 @@ void cell_area_centroid(const fvlbm_mesh &m, int i, const S *xy, S *area, S *cx,
 // xy and its face neighbours' centroids (nbx, nby; slots with nbr[l] < 0 are boundary faces).
 template <class S>
 struct CellGeo {
-    S sn[8], lsq[8], rown[8], rnbr[8], nrm[8], len[4];
+    S sn[8], lsq[8], rown[8], rnbr[8], nrm[8], len[4], dinv[4];
 };
 
 template <class S>
@@ -476,6 +476,7 @@ void cell_geometry(const fvlbm_mesh &m, int i, const S *xy, const int *nbr, cons
         G->nrm[2 * l] = nx;
         G->nrm[2 * l + 1] = ny;
         G->len[l] = len;
+        G->dinv[l] = S(1.0) / sqrt(dx[l] * dx[l] + dy[l] * dy[l]);
         mxx += dx[l] * dx[l];
         mxy += dx[l] * dy[l];
         myy += dy[l] * dy[l];
@@ -547,6 +548,7 @@ int geometry_adjoint(const fvlbm_mesh &m, const fvlbm_bc &bc, const GeometryAdjo
                     s += A.sn[o + c] * G.sn[2 * l + c].d + A.lsq[o + c] * G.lsq[2 * l + c].d +
                          A.rown[o + c] * G.rown[2 * l + c].d + A.rnbr[o + c] * G.rnbr[2 * l + c].d;
                 }
+                if (!A.dinv.empty()) s += A.dinv[4 * static_cast<size_t>(i) + l] * G.dinv[l].d;
                 if (nb[l] < 0 && nb[l] != kNone) {
                     const int b = -nb[l] - 1;
                     s += A.bnrm[2 * b] * G.nrm[2 * l].d + A.bnrm[2 * b + 1] * G.nrm[2 * l + 1].d +
@@ -572,6 +574,39 @@ int geometry_adjoint(const fvlbm_mesh &m, const fvlbm_bc &bc, const GeometryAdjo
                 cell_geometry<Dual>(m, i, xyd.data(), nb, nbx, nby, &G);
                 (c == 0 ? nbx[l] : nby[l]).d = 0.0;
                 dc[2 * static_cast<size_t>(nb[l]) + c] += contract(G);
+            }
+        }
+    }
+    // wall distance: the nearest wall face (first of equals, in input order, as the forward
+    // search keeps it) and the point-segment distance's local Jacobian
+    if (!A.wdist.empty()) {
+        std::vector<int> walls;
+        for (int b = 0; b < bc.n_bedges; ++b)
+            if (bc.bedge_type[b] == FVLBM_BC_WALL) walls.push_back(b);
+        for (int i = 0; i < nc && !walls.empty(); ++i) {
+            const double lw = A.wdist[i];
+            if (lw == 0.0) continue;
+            double best = 1e300;
+            int bw = -1;
+            for (int b : walls) {
+                const int a0 = bc.bedge_nodes[2 * b], a1 = bc.bedge_nodes[2 * b + 1];
+                const double d = point_segment(cxv[i], cyv[i], m.xy[2 * a0], m.xy[2 * a0 + 1], m.xy[2 * a1],
+                                               m.xy[2 * a1 + 1]);
+                if (d < best) {
+                    best = d;
+                    bw = b;
+                }
+            }
+            const int a0 = bc.bedge_nodes[2 * bw], a1 = bc.bedge_nodes[2 * bw + 1];
+            for (int k = 0; k < 6; ++k) {
+                Dual in[6] = {Dual(cxv[i]), Dual(cyv[i]), Dual(m.xy[2 * a0]), Dual(m.xy[2 * a0 + 1]),
+                              Dual(m.xy[2 * a1]), Dual(m.xy[2 * a1 + 1])};
+                in[k].d = 1.0;
+                const double g = lw * point_segment(in[0], in[1], in[2], in[3], in[4], in[5]).d;
+                if (k < 2)
+                    dc[2 * static_cast<size_t>(i) + k] += g;
+                else
+                    dxy[2 * (k < 4 ? a0 : a1) + (k & 1)] += g;
             }
         }
     }

@@ -80,18 +80,20 @@ inline int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm
     return prepare_instance_t<double>(m, bc, p, m.xy, out, why);
 }
 
-// Adjoints of the geometry arrays a laminar step reads, in input order: for face l of input cell
-// i (joining its nodes l and l + 1), entry (4 i + l) * 2 + c of sn, lsq, rown, rnbr (c = x, y);
-// for input boundary edge b, bnrm[2 b + c] and blen[b] (periodic edges: unused).
+// Adjoints of the geometry arrays a step reads, in input order: for face l of input cell i
+// (joining its nodes l and l + 1), entry (4 i + l) * 2 + c of sn, lsq, rown, rnbr (c = x, y) and
+// entry 4 i + l of dinv; wdist[i]; for input boundary edge b, bnrm[2 b + c] and blen[b]
+// (periodic edges: unused).  dinv and wdist may be empty (laminar steps do not read them).
 struct GeometryAdjoint {
-    std::vector<double> sn, lsq, rown, rnbr, bnrm, blen;
+    std::vector<double> sn, lsq, rown, rnbr, bnrm, blen, dinv, wdist;
 };
 
 // Reverse mode of the preprocessing above with respect to the node positions: dxy[2 n_nodes] =
 // sum over the arrays of adjoint x d(array)/d(x, y), for the areas, centroids, face normals,
-// lengths and midpoints, face offsets and least-squares weights as prepare_instance_t forms them
-// (each cell's local Jacobian by dual numbers, the neighbour centroids' adjoints carried to their
-// cells' nodes).  Meshes with periodic pairs: FVLBM_ERR_NOT_SUPPORTED.
+// lengths and midpoints, face offsets, least-squares weights, 1 / |d| and the wall distance as
+// prepare_instance_t forms them (each cell's local Jacobian by dual numbers, the neighbour
+// centroids' adjoints carried to their cells' nodes; the wall distance through its nearest wall
+// face).  Meshes with periodic pairs: FVLBM_ERR_NOT_SUPPORTED.
 int geometry_adjoint(const fvlbm_mesh &m, const fvlbm_bc &bc, const GeometryAdjoint &A, double *dxy,
                      std::string *why);
 

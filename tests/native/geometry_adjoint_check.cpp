@@ -1,5 +1,7 @@
 // Host-side check of the reverse-mode geometry (geometry_adjoint) used by the shape gradient of
-// the adjoint: for random adjoints A of the geometry arrays and a random node displacement v,
+// the adjoint: for random adjoints A of the geometry arrays (face normals and lengths, offsets,
+// least-squares weights, 1 / |d|, wall distance, wall normals and lengths) and a random node
+// displacement v,
 //   <A, d(geometry)/d(xy) v>  from prepare_instance_t<Dual> (forward mode, one direction)
 // must equal
 //   <geometry_adjoint(A), v>  (reverse mode).
@@ -57,6 +59,10 @@ int main(int argc, char **argv) {
         v->resize(8 * static_cast<size_t>(nc));
         for (double &x : *v) x = uniform(s);
     }
+    A.dinv.resize(4 * static_cast<size_t>(nc));
+    for (double &x : A.dinv) x = uniform(s);
+    A.wdist.resize(nc);
+    for (double &x : A.wdist) x = uniform(s);
     A.bnrm.resize(2 * static_cast<size_t>(nbe));
     A.blen.resize(nbe);
     for (double &x : A.bnrm) x = uniform(s);
@@ -73,6 +79,8 @@ int main(int argc, char **argv) {
     double fwd = 0.0;
     for (int k = 0; k < D.nc; ++k) {
         const size_t i = D.perm[k];
+        fwd += A.wdist[i] * D.wdist[k].d;
+        for (int l = 0; l < D.nface[k]; ++l) fwd += A.dinv[4 * i + l] * D.dinv[l * np + k].d;
         for (int l = 0; l < D.nface[k]; ++l)
             for (int c = 0; c < 2; ++c) {
                 const size_t o = (4 * i + l) * 2 + c, q = (2 * l + c) * np + k;

@@ -200,9 +200,6 @@ def test_adjoint_rejects_unsupported_handles():
         s.close()
     sst = mg.naca0012_cmesh(n_target=2500)
     s = fvlbm.Solver(sst, precision=FP64, device=0)
-    with pytest.raises(fvlbm.FvlbmError) as e:   # the SST solve's geometry is not transposed
-        s.adjoint(3, 1.0, 0.0, shape=True)
-    assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
     with pytest.raises(fvlbm.FvlbmError) as e:
         s.adjoint(-1, 1.0, 0.0)
     assert e.value.code == fvlbm.FVLBM_ERR_BAD_PARAM
@@ -297,3 +294,28 @@ def test_adjoint_sst_inflow_turbulence_and_alpha():
             adj += W[0] * val["cl"] - W[1] * val["cd"]
         assert abs(dJt) > 1e-12, (dalpha, dJt)
         assert abs(adj - dJt) <= 1e-8 * abs(dJt), (dalpha, adj, dJt)
+
+
+@pytest.mark.parametrize("name", sorted(SST_CASES))
+@pytest.mark.parametrize("n", [1, 6])
+def test_adjoint_sst_shape_gradient_against_tangent(name, n):
+    """SST cases: dJ/dxy through the LBM stages and the SST solve (face geometry, least-squares
+    weights, 1/|d| and the wall distance of f1, f2 and the wall omega) against the tangent of a
+    random displacement of every node."""
+    case = SST_CASES[name]()
+    warm = 8
+    m = case.mesh.normalized()
+    v = 1e-3 * np.random.default_rng(300 + n).standard_normal((m.n_nodes, 2))
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    s.step(warm)
+    _, _, _, dxy = s.adjoint(n, W[0], W[1], shape=True)
+    s.close()
+    t = fvlbm.Solver(case, precision=TAN, device=0)
+    t.step(warm)
+    t.tangent_seed_nodes(v)
+    t.step(n)
+    _, dv = t.forces_tangent(dalpha=0.0)
+    t.close()
+    dJt = W[0] * dv["cd"] + W[1] * dv["cl"]
+    adj = float(np.sum(dxy * v))
+    assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)

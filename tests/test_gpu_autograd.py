@@ -13,13 +13,14 @@ from paper_1812_00394_gb300 import autograd as fa, meshgen as mg
 pytestmark = pytest.mark.gpu
 
 
-def test_autograd_gradients_match_central_differences():
+@pytest.mark.parametrize("mode", ["tangent", "adjoint"])
+def test_autograd_gradients_match_central_differences(mode):
     base = mg.naca0012_cmesh(n_target=2500, re_c=1e4, alpha_deg=4.0)
     m = base.mesh.normalized()
     wall = np.unique(m.bedge_nodes[m.bedge_type == mg.BC_WALL])
     upper = wall[m.xy[wall, 1] > 0]
     picks = [int(upper[np.argmin(np.abs(m.xy[upper, 0] - x))]) for x in (0.1, 0.4, 0.8)]
-    model = fa.AirfoilForces(base, picks, steps=30, device=0)
+    model = fa.AirfoilForces(base, picks, steps=30, device=0, mode=mode)
     p0 = np.array([math.radians(4.0), 1.0, 0.0, 0.0, 0.0])
     p = torch.tensor(p0, requires_grad=True)
     out = fa.forces(model, p)
@@ -76,17 +77,21 @@ def test_autograd_adjoint_backward_matches_tangent_and_fd():
 
 
 def test_autograd_sst_adjoint_backward_matches_tangent():
-    """SST NACA 0012 with (alpha, inflow ratio) only: the default backward is the adjoint, and
-    it equals the tangent backward."""
+    """SST NACA 0012 with alpha, the inflow ratio and two wall nodes: the default backward is the
+    adjoint, and it equals the tangent backward."""
     base = mg.naca0012_cmesh(n_target=2500, re_c=1e4, alpha_deg=4.0)
-    p0 = np.array([math.radians(4.0), 1.0])
+    m = base.mesh.normalized()
+    wall = np.unique(m.bedge_nodes[m.bedge_type == mg.BC_WALL])
+    upper = wall[m.xy[wall, 1] > 0]
+    picks = [int(upper[np.argmin(np.abs(m.xy[upper, 0] - x))]) for x in (0.2, 0.6)]
+    p0 = np.array([math.radians(4.0), 1.0, 0.0, 0.0])
     grads = {}
     for mode in ("auto", "tangent"):
-        model = fa.AirfoilForces(base, [], steps=30, device=0, mode=mode)
+        model = fa.AirfoilForces(base, picks, steps=30, device=0, mode=mode)
         assert model.mode == ("adjoint" if mode == "auto" else "tangent")
         p = torch.tensor(p0, requires_grad=True)
         out = fa.forces(model, p)
         (out[0] + 0.5 * out[1]).backward()
         grads[mode] = p.grad.numpy().copy()
-    for q in range(2):
+    for q in range(4):
         assert abs(grads["auto"][q] - grads["tangent"][q]) <= 1e-8 * abs(grads["tangent"][q]) + 1e-14, q
