@@ -583,20 +583,25 @@ int geometry_adjoint(const fvlbm_mesh &m, const fvlbm_bc &bc, const GeometryAdjo
         std::vector<int> walls;
         for (int b = 0; b < bc.n_bedges; ++b)
             if (bc.bedge_type[b] == FVLBM_BC_WALL) walls.push_back(b);
-        for (int i = 0; i < nc && !walls.empty(); ++i) {
-            const double lw = A.wdist[i];
-            if (lw == 0.0) continue;
+        std::vector<int> nearest(walls.empty() ? 0 : nc, -1);
+#pragma omp parallel for schedule(static)
+        for (int i = 0; i < static_cast<int>(nearest.size()); ++i) {
+            if (A.wdist[i] == 0.0) continue;
             double best = 1e300;
-            int bw = -1;
             for (int b : walls) {
                 const int a0 = bc.bedge_nodes[2 * b], a1 = bc.bedge_nodes[2 * b + 1];
                 const double d = point_segment(cxv[i], cyv[i], m.xy[2 * a0], m.xy[2 * a0 + 1], m.xy[2 * a1],
                                                m.xy[2 * a1 + 1]);
                 if (d < best) {
                     best = d;
-                    bw = b;
+                    nearest[i] = b;
                 }
             }
+        }
+        for (int i = 0; i < static_cast<int>(nearest.size()); ++i) {
+            const double lw = A.wdist[i];
+            if (lw == 0.0 || nearest[i] < 0) continue;
+            const int bw = nearest[i];
             const int a0 = bc.bedge_nodes[2 * bw], a1 = bc.bedge_nodes[2 * bw + 1];
             for (int k = 0; k < 6; ++k) {
                 Dual in[6] = {Dual(cxv[i]), Dual(cyv[i]), Dual(m.xy[2 * a0]), Dual(m.xy[2 * a0 + 1]),
