@@ -301,12 +301,14 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
  * steps that keep their stage values (99 doubles per cell and step, 119 with SST) and n_steps
  * adjoint steps.
  * Where the stage values of all steps do not fit the adjoint budget (fvlbm_set_adjoint_budget;
- * default half the free device memory), the steps are taken in segments of as many steps as
- * fit: a first sweep keeps the state at each segment start and each segment runs again before its
- * reverse sweep (2 n_steps forward steps).  The device memory is allocated for the call and
- * freed before it returns (about 60 + 99 K doubles per cell for segments of K steps, 119 K with
- * SST, 32 more with dJ_dxy); dJ_dxy adds one pass over the cells on the host (SST: and a
- * nearest-wall search per cell).
+ * default half the free device memory), the run is cut into units of K steps whose stage values
+ * fit in half the budget; the other half holds c state snapshots (9 doubles per cell, 15 with
+ * SST), and the units are reversed on the binomial (revolve) schedule: with r the least number
+ * with C(c + r, c) >= the number of units, no unit runs forward more than r + 1 times (2 when
+ * there is a snapshot for every unit start).  The device memory is allocated for the call and
+ * freed before it returns (about 60 doubles per cell plus the stage values and snapshots, 32
+ * more with dJ_dxy); dJ_dxy adds one pass over the cells on the host (SST: and a nearest-wall
+ * search per cell).
  * Valid on FVLBM_FP64 handles with the IMEX scheme, one dt per instance and the default reading
  * (variant 0: no limiter, non-orthogonal correction, per-stage solve or production limiter);
  * else FVLBM_ERR_NOT_SUPPORTED.  Synchronises.

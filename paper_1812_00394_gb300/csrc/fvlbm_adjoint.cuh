@@ -15,6 +15,8 @@
 // The stage values of whole segments of steps stay in device memory (see adjoint_impl for the
 // plan): with room for all steps the forward steps run once, else twice.
 
+#include <functional>
+
 namespace fvlbm {
 
 // ---- per-cell maps.  Each is affine in its inputs except through the equilibrium of a stage
@@ -668,24 +670,34 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
     const size_t np = h->np, nq = static_cast<size_t>(kQ) * np;
     // Memory plan.  The stage values one adjoint step reads take 99 doubles per cell (f^n, f^(1),
     // f^(2), B, f^(3) and the three gradients; SST adds 20: the macros, k, omega, nu_t, the SST
-    // gradients, f1 and tau).  Segments of K consecutive steps keep theirs whole, K as large as
-    // the budget allows (the handle's adjoint budget, else half the free device memory).  With
-    // one segment every step runs once; with several, a first sweep keeps the state at each
-    // segment start and each segment then runs a second time before its reverse sweep.
+    // gradients, f1 and tau); a state snapshot takes 9 (SST: 15).  Within the budget (the
+    // handle's adjoint budget, else half the free device memory) all steps keep their stage
+    // values when they fit, and every step runs forward once.  Otherwise the run is cut into
+    // units of K steps whose stage values fit in half the budget, the other half holds c state
+    // snapshots, and the units are reversed on a binomial (revolve) schedule: with c snapshots
+    // and r forward passes per unit at most, C(c + r, c) units can be reversed, and r is the
+    // least such number.  With a snapshot for every unit start that is r = 1: each unit runs
+    // forward twice (once to reach the next snapshot, once keeping its stage values).
     const size_t per_step = (sst ? 119 : 99) * np * sizeof(double);
+    const size_t per_snap = (sst ? 15 : 9) * np * sizeof(double);
     size_t budget = h->adj_budget;
     if (budget == 0) {
         size_t fr = 0, tot = 0;
         CK(cudaMemGetInfo(&fr, &tot));
         budget = fr / 2;
     }
-    const int K = static_cast<int>(
-        std::max<size_t>(1, std::min<size_t>(budget / per_step, static_cast<size_t>(std::max(n_steps, 1)))));
-    const int nseg = (n_steps + K - 1) / K;
+    int K = std::max(n_steps, 1), nsnap = 0;
+    if (static_cast<size_t>(n_steps) * per_step > budget) {
+        K = static_cast<int>(std::max<size_t>(1, budget / 2 / per_step));
+        const int units = (n_steps + K - 1) / K;
+        const size_t left = budget > K * per_step ? budget - K * per_step : 0;
+        nsnap = static_cast<int>(std::min<size_t>(units - 1, std::max<size_t>(1, left / per_snap)));
+    }
+    const int units = n_steps > 0 ? (n_steps + K - 1) / K : 0;
     AdjScratch M;
     double *Cs, *macs;
     AdjState xa, xb;
-    std::vector<AdjState> ck(nseg > 1 ? nseg : 0), st(K);
+    std::vector<AdjState> snap(nsnap), st(K);
     std::vector<AdjStep> slot(K);
     AdjVars A{};
     const size_t nbt = std::max(h->nbt, 1);
@@ -703,7 +715,7 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         state(xb);
         Cs = M.get(nq);
         macs = M.get(3 * np);
-        for (auto &x : ck) state(x);
+        for (auto &x : snap) state(x);
         for (int k = 0; k < K; ++k) {
             state(st[k]);
             slot[k].s1 = M.get(nq);
@@ -802,45 +814,79 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         CK(cudaGetLastError());
         return FVLBM_OK;
     };
-    const double *fN = xb.f;
-    if (nseg > 1) {  // first sweep: the last state and the segment starts
-        int rc = copy_state(xa, h0);
+    // units u0 .. u1-1 forward from `start` without keeping stage values; the state into `dst`
+    auto advance = [&](int u0, int u1, const AdjState &start, const AdjState &dst) -> int {
+        const int k0 = u0 * K, k1 = std::min(n_steps, u1 * K);
+        if (k1 <= k0) return copy_state(dst, start);
+        int rc = copy_state(xa, start);
         if (rc) return rc;
-        for (int n = 0; n < n_steps; ++n) {
-            if (n % K == 0 && (rc = copy_state(ck[n / K], xa))) return rc;
-            adj_forward_step(h, G, xa, xb, slot[0]);
+        for (int n = k0; n < k1; ++n) {
+            adj_forward_step(h, G, xa, n + 1 < k1 ? xb : dst, slot[0]);
             std::swap(xa, xb);
         }
-        fN = xa.f;
         CK(cudaGetLastError());
-    } else if (n_steps > 0) {
-        int rc = fill(0, n_steps, h0);
+        return FVLBM_OK;
+    };
+    // J at f^N and its derivatives with respect to f^N: taken when the last unit has been filled
+    // (its end state is f^N), before the first reverse step
+    bool seeded = false;
+    auto seed = [&](const double *fN) -> int {
+        double out[4];
+        int rc = forces_impl(h, instance, 0.0, out, nullptr, nullptr, fN);
         if (rc) return rc;
-    } else {
-        fN = h0.f;
-    }
-    // J at f^N and its direct derivatives
-    double out[4];
-    int rc = forces_impl(h, instance, 0.0, out, nullptr, nullptr, fN);
-    if (rc) return rc;
-    if (J) *J = w[0] * out[2] + w[1] * out[3];
-    const double q = 0.5 * I.rho0 * I.uref * I.uref * I.lref;
-    const double al = I.alpha_deg * M_PI / 180.0, ca = std::cos(al), sa = std::sin(al);
-    const double cx = (w[0] * ca - w[1] * sa) / q, cy = (w[0] * sa + w[1] * ca) / q;
-    CK(cudaMemsetAsync(A.lbval, 0, 5 * nbt * sizeof(double), s));
-    k_adj_seed<<<h->ntiles, kTile, 0, s>>>(fN, static_cast<const double *>(h->bnrm),
-                                           static_cast<const double *>(h->blen), instance, cx, cy, A.L,
-                                           A.lbval, A.a_bnrm, A.a_blen, G);
-    CK(cudaGetLastError());
-    // reverse sweep, one segment at a time
-    for (int c = nseg - 1; c >= 0; --c) {
-        const int k0 = c * K, k1 = std::min(n_steps, k0 + K);
-        if (nseg > 1) {
-            int rc2 = fill(k0, k1, ck[c]);
-            if (rc2) return rc2;
-        }
+        if (J) *J = w[0] * out[2] + w[1] * out[3];
+        const double q = 0.5 * I.rho0 * I.uref * I.uref * I.lref;
+        const double al = I.alpha_deg * M_PI / 180.0, ca = std::cos(al), sa = std::sin(al);
+        const double cx = (w[0] * ca - w[1] * sa) / q, cy = (w[0] * sa + w[1] * ca) / q;
+        CK(cudaMemsetAsync(A.lbval, 0, 5 * nbt * sizeof(double), s));
+        k_adj_seed<<<h->ntiles, kTile, 0, s>>>(fN, static_cast<const double *>(h->bnrm),
+                                               static_cast<const double *>(h->blen), instance, cx, cy, A.L,
+                                               A.lbval, A.a_bnrm, A.a_blen, G);
+        CK(cudaGetLastError());
+        seeded = true;
+        return FVLBM_OK;
+    };
+    // reverse one unit whose start state is `start`
+    auto reverse_unit = [&](int u, const AdjState &start) -> int {
+        const int k0 = u * K, k1 = std::min(n_steps, k0 + K);
+        int rc = fill(k0, k1, start);
+        if (rc) return rc;
+        if (!seeded && (rc = seed(xb.f))) return rc;
         for (int n = k1 - 1; n >= k0; --n) adj_backward_step(h, G, st[n - k0], slot[n - k0], A);
         CK(cudaGetLastError());
+        return FVLBM_OK;
+    };
+    // binomial coefficient C(c + r, c), saturated
+    auto beta = [](int c, int r) {
+        double b = 1.0;
+        for (int i = 1; i <= c; ++i) b = b * (r + i) / i;
+        return b > 2e9 ? 2000000000 : static_cast<int>(b + 0.5);
+    };
+    // reverse units u0 .. u0+n-1, the state at u0 in `start`, snapshots free from index `free`
+    std::function<int(int, int, const AdjState &, int)> revolve = [&](int u0, int n, const AdjState &start,
+                                                                       int free) -> int {
+        if (n <= 0) return FVLBM_OK;
+        if (n == 1) return reverse_unit(u0, start);
+        const int c = nsnap - free;
+        // every frame with n >= 2 has a free snapshot: the plan gives at least one when there are
+        // two units or more, and a frame with c free snapshots hands its tail (c - 1 free) at
+        // most C(c - 1 + r, c - 1) units, which is 1 when c = 1
+        if (c <= 0) return FVLBM_ERR_BAD_PARAM;
+        int r = 1;
+        while (beta(c, r) < n) ++r;
+        const int tail = std::min(n - 1, beta(c - 1, r));
+        const int head = n - tail;
+        int rc = advance(u0, u0 + head, start, snap[free]);
+        if (rc) return rc;
+        if ((rc = revolve(u0 + head, tail, snap[free], free + 1))) return rc;
+        return revolve(u0, head, start, free);
+    };
+    if (n_steps == 0) {
+        int rc = seed(h0.f);
+        if (rc) return rc;
+    } else {
+        int rc = revolve(0, units, h0, 0);
+        if (rc) return rc;
     }
     double *xscr = xb.f;
     if (dJ_df && I.nc > 0) {

@@ -127,18 +127,22 @@ def test_adjoint_shape_gradient_of_one_wall_node():
     assert abs(dxy[node, 1] - dJt) <= 1e-8 * abs(dJt), (dxy[node, 1], dJt)
 
 
-@pytest.mark.parametrize("steps_per_segment", [1, 3, 7])
-def test_adjoint_segments_match_one_segment(steps_per_segment):
-    """A budget that holds only a few steps' stage values (checkpointed segments, each run a
-    second time) gives the same gradient as keeping every step: the steps recomputed from a
-    segment start repeat the first sweep's arithmetic exactly."""
-    case = _naca_laminar()
+@pytest.mark.parametrize("sst", [False, True])
+@pytest.mark.parametrize("steps_of_budget,snaps_of_budget", [(1.0, 0), (2.0, 3), (6.0, 0)])
+def test_adjoint_checkpoint_schedules_match_one_segment(sst, steps_of_budget, snaps_of_budget):
+    """Budgets that hold the stage values of only one or three steps: the run is cut into units
+    reversed on the binomial (revolve) schedule with 1 snapshot (quadratic recomputation), with
+    14 snapshots for 16 unit starts (two passes for some units), or with a snapshot at every unit
+    start.  The gradient is bit-identical to keeping every step: recomputed steps repeat the
+    first pass's arithmetic exactly."""
+    case = _naca_sst() if sst else _naca_laminar()
     s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
     s.step(5)
     ref = s.adjoint(17, *W, shape=True)
-    n = s.cells[0]
-    np_pad = -(-n // 256) * 256
-    s.set_adjoint_budget(99 * 8 * np_pad * steps_per_segment)
+    np_pad = -(-s.cells[0] // 256) * 256
+    per_step = (119 if sst else 99) * 8 * np_pad
+    per_snap = (15 if sst else 9) * 8 * np_pad
+    s.set_adjoint_budget(int(steps_of_budget * per_step + snaps_of_budget * per_snap))
     got = s.adjoint(17, *W, shape=True)
     s.set_adjoint_budget(0)
     assert got[0] == ref[0]
