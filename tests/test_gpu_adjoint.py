@@ -5,15 +5,19 @@ instance.  For any seed (g, d) of the initial state and of the boundary values, 
 dJ/dp after N steps by one forward run, and the adjoint gives the gradient whose inner product
 with (g, d) is the same number:  <dJ/df^0, g> + <dJ/dbval, d> = dJ/dp.  The two are computed by
 different kernels (the tangent carries dual numbers forward; the adjoint transposes the flux and
-gradient operators by gathers over the back slots of each face and the per-cell maps through
-their local Jacobians), so agreement to rounding checks every transposed piece.  A central
-finite difference of the FP64 step closes the loop on a boundary-value direction.
+gradient operators by gathers over the back slots of each face and the per-cell maps in closed
+form), so agreement to rounding checks every transposed piece.  Central finite differences
+close the loop: of the FP64 GPU step on a boundary-value direction, and of the FP64 CPU oracle
+(no GPU code on that side) for the angle of attack, the inflow eddy-viscosity ratio and a
+wall-node displacement.
 """
 import dataclasses
+import math
 
 import numpy as np
 import pytest
 
+from oracle.oracle import Oracle
 from paper_1812_00394_gb300 import fvlbm, meshgen as mg
 
 pytestmark = pytest.mark.gpu
@@ -323,3 +327,102 @@ def test_adjoint_sst_shape_gradient_against_tangent(name, n):
     dJt = W[0] * dv["cd"] + W[1] * dv["cl"]
     adj = float(np.sum(dxy * v))
     assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)
+
+
+# ------------------------------------------------------------------ against the CPU oracle
+def _freeze(case, base):
+    return dataclasses.replace(case, rho=base.rho, u=base.u, v=base.v, k=base.k, omega=base.omega)
+
+
+def _oracle_J(case, steps, dt=None):
+    o = Oracle(case, dt=dt)
+    o.step(steps)
+    f = o.forces()
+    return W[0] * f["cd"] + W[1] * f["cl"]
+
+
+def test_adjoint_alpha_vs_oracle_fd():
+    """SST NACA 0012: dJ/d alpha (radians) from one adjoint solve, through the far-field
+    velocity and the drag / lift projection, against central differences of the FP64 CPU
+    oracle at alpha +- 1e-5 rad from the same initial state."""
+    a0, steps, hr = 3.0, 30, 1e-5
+    base = mg.naca0012_cmesh(n_target=1500, alpha_deg=a0)
+    m = base.mesh.normalized()
+    ff = m.bedge_type == mg.BC_FARFIELD
+    d_alpha = np.zeros((m.n_bedges, 5))
+    d_alpha[ff, 1] = -m.bedge_val[ff, 2]
+    d_alpha[ff, 2] = m.bedge_val[ff, 1]
+    s = fvlbm.Solver(base, precision=FP64, device=0, kernel_path=1)
+    _, _, dJdb, _ = s.adjoint(steps, *W)
+    s.step(steps)
+    f = s.forces()
+    s.close()
+    adj = float(np.sum(dJdb * d_alpha)) + W[0] * f["cl"] - W[1] * f["cd"]
+    hd = math.degrees(hr)
+    Jp = _oracle_J(_freeze(mg.naca0012_cmesh(n_target=1500, alpha_deg=a0 + hd), base), steps)
+    Jm = _oracle_J(_freeze(mg.naca0012_cmesh(n_target=1500, alpha_deg=a0 - hd), base), steps)
+    fd = (Jp - Jm) / (2 * hr)
+    assert abs(adj - fd) <= 1e-5 * abs(fd), (adj, fd)
+
+
+def test_adjoint_inflow_ratio_vs_fd():
+    """SST backward-facing step: dJ/d(inflow nu_t / nu ratio) through the inlet omega_b from one
+    adjoint solve over 1000 steps (long enough for the inflow turbulence to reach the walls
+    downstream: over a few tens of steps the derivative is at the rounding level of J, 1e-11 of
+    it), against central differences at ratio 10 +- 0.01:
+    - of the FP64 GPU step, to 1e-5 (measured 7e-7);
+    - of the FP64 CPU oracle (no GPU code on that side), to 3e-4: measured 8e-5, the rounding
+      noise of the oracle's J over 1000 steps (its differences at h = 1e-3 and 1e-4 move by
+      6e-4 and 1e-2 while the GPU step's stay within 2e-5 and 5e-4)."""
+    r0, steps, h = 10.0, 1000, 1e-2
+    base = mg.bfs_hybrid(n_target=1500, nut_ratio=r0)
+    m = base.mesh.normalized()
+    inlet = m.bedge_type == mg.BC_INLET
+    d_ratio = np.zeros((m.n_bedges, 5))
+    d_ratio[inlet, 4] = -m.bedge_val[inlet, 4] / r0
+    s = fvlbm.Solver(base, precision=FP64, device=0, kernel_path=1)
+    _, _, dJdb, _ = s.adjoint(steps, *W)
+    s.close()
+    adj = float(np.sum(dJdb * d_ratio))
+    cases = [_freeze(mg.bfs_hybrid(n_target=1500, nut_ratio=r0 + e), base) for e in (h, -h)]
+    gpu = []
+    for c in cases:
+        g = fvlbm.Solver(c, precision=FP64, device=0, kernel_path=1)
+        g.step(steps)
+        f = g.forces()
+        g.close()
+        gpu.append(W[0] * f["cd"] + W[1] * f["cl"])
+    fd_gpu = (gpu[0] - gpu[1]) / (2 * h)
+    fd_oracle = (_oracle_J(cases[0], steps) - _oracle_J(cases[1], steps)) / (2 * h)
+    assert abs(adj - fd_gpu) <= 1e-5 * abs(fd_gpu), (adj, fd_gpu)
+    assert abs(adj - fd_oracle) <= 3e-4 * abs(fd_oracle), (adj, fd_oracle)
+
+
+def test_adjoint_wall_node_vs_oracle_fd():
+    """SST NACA 0012 at Re_c = 1e4: dJ/d(normal displacement of one wall node) from the adjoint's
+    shape gradient, at fixed dt, against central differences of the FP64 CPU oracle on moved
+    meshes."""
+    steps, h = 30, 1e-6
+    base = mg.naca0012_cmesh(n_target=1500, re_c=1e4, alpha_deg=4.0)
+    m = base.mesh.normalized()
+    wall = m.bedge_nodes[m.bedge_type == mg.BC_WALL]
+    nodes = np.unique(wall)
+    upper = nodes[m.xy[nodes, 1] > 0]
+    j = int(upper[np.argmin(np.abs(m.xy[upper, 0] - 0.3))])
+    nb = np.unique(wall[(wall == j).any(1)])
+    nb = nb[nb != j]
+    t = m.xy[nb[1]] - m.xy[nb[0]]
+    n = np.array([-t[1], t[0]]) / np.linalg.norm(t)
+    n = n if n[1] > 0 else -n
+    s = fvlbm.Solver(base, precision=FP64, device=0, kernel_path=1)
+    dt = s.dt()
+    _, _, _, dxy = s.adjoint(steps, *W, shape=True)
+    s.close()
+    adj = float(dxy[j] @ n)
+
+    def moved(eps):
+        xy = m.xy.copy()
+        xy[j] += eps * n
+        return dataclasses.replace(base, mesh=dataclasses.replace(m, xy=xy), dt=dt)
+    fd = (_oracle_J(moved(h), steps, dt) - _oracle_J(moved(-h), steps, dt)) / (2 * h)
+    assert abs(adj - fd) <= 1e-5 * abs(fd), (adj, fd)
