@@ -278,8 +278,8 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
  *   J = w[0] C_D + w[1] C_L of `instance` after n_steps steps from the handle's current state,
  *
  * C_D, C_L as fvlbm_forces.  The step differentiated is the IMEX step of Sec. 3.1-3.2 (Steps 1-7:
- * the k-omega SST solve on SST instances, then the stages) with one dt per instance, as the
- * two-pass kernels run it in FP64 (the fused kernels give the same values up to rounding).
+ * the k-omega SST solve on SST instances, then the stages), with one dt per instance or local
+ * time steps, as the two-pass kernels run it in FP64 (the fused kernels give the same values up to rounding).
  * Where the step is not differentiable (the upwind switch on e.n = 0, the SST's limiter, clip
  * and blending branches) the derivative of the branch the value takes is used, as in the
  * tangent.
@@ -309,9 +309,9 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
  * freed before it returns (about 60 doubles per cell plus the stage values and snapshots, 32
  * more with dJ_dxy); dJ_dxy adds one pass over the cells on the host (SST: and a nearest-wall
  * search per cell).
- * Valid on FVLBM_FP64 handles with the IMEX scheme, one dt per instance and the default reading
- * (variant 0: no limiter, non-orthogonal correction, per-stage solve or production limiter);
- * else FVLBM_ERR_NOT_SUPPORTED.  Synchronises.
+ * Valid on FVLBM_FP64 handles with the IMEX scheme and the default reading (variant 0: no
+ * limiter, non-orthogonal correction, per-stage solve or production limiter); else
+ * FVLBM_ERR_NOT_SUPPORTED.  Synchronises.
  * Errors: BAD_PARAM (w NULL, n_steps < 0, bad instance), NOT_SUPPORTED, OOM, CUDA. */
 int fvlbm_adjoint(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
                   double *dJ_dbedge_val, double *dJ_dxy);

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kTile) k_adj_stage3(const double *__restrict__
                                                       Geo<double> G) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
-    const double dt = G.ip[G.tile_inst[blockIdx.x]].dt;
+    const double dt = cell_dt(G, G.ip[G.tile_inst[blockIdx.x]], i);
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
         const double l = L[a * np + i];
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kTile) k_adj_stage2(const double *__restrict__
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
-    const double dt = P.dt;
+    const double dt = cell_dt(G, P, i);
     double acc[kQ], X[kQ], mu[kQ], lX[kQ];
     adj_flux_acc(i, f2, g2, G, P.rho0, acc);
     const double zt = dt * (1.0 / 3.0) * (1.0 / tau[i]);
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kTile) k_adj_stage1(const double *__restrict__
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
-    const double dt = P.dt;
+    const double dt = cell_dt(G, P, i);
     double acc[kQ], x0[kQ], X[kQ], lX[kQ], mu[kQ], lb[kQ];
     adj_flux_acc(i, s1, g1, G, P.rho0, acc);
     const double z = dt * (1.0 / tau[i]);
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(kTile) k_adj_relax(const double *__restrict__ 
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
-    const double zq = P.dt / tau[i] * 0.25;
+    const double zq = cell_dt(G, P, i) / tau[i] * 0.25;
     const double inv = 1.0 / (1.0 + zq);
     double x0[kQ], l0[kQ], mu[kQ];
 #pragma unroll
@@ -659,7 +659,7 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in
 int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
                  double *dJ_dbedge, double *dJ_dxy) {
     if (!h || instance < 0 || instance >= h->ninst || n_steps < 0 || !w) return FVLBM_ERR_BAD_PARAM;
-    if (h->precision != FVLBM_FP64 || h->scheme != 0 || h->dtc != nullptr || h->limit_f || h->per_stage ||
+    if (h->precision != FVLBM_FP64 || h->scheme != 0 || h->limit_f || h->per_stage ||
         h->nonorth || h->d_back == nullptr)
         return FVLBM_ERR_NOT_SUPPORTED;
     const InstInfo &I = h->inst[instance];

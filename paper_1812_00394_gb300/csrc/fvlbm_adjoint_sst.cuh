@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
     if (!P.sst) return;
-    const double nu = P.nu, dt = P.dt;
+    const double nu = P.nu, dt = cell_dt(G, P, i);
     const double ui = mac[np + i], vi = mac[2 * np + i], ki = kk[i], wi = ww[i], nti = nut[i];
     const double di = G.wdist[i], f1 = f1a[i];
     double g[8], lgi[4];

@@ -426,3 +426,21 @@ def test_adjoint_wall_node_vs_oracle_fd():
         return dataclasses.replace(base, mesh=dataclasses.replace(m, xy=xy), dt=dt)
     fd = (_oracle_J(moved(h), steps, dt) - _oracle_J(moved(-h), steps, dt)) / (2 * h)
     assert abs(adj - fd) <= 1e-5 * abs(fd), (adj, fd)
+
+
+@pytest.mark.parametrize("sst", [False, True])
+def test_adjoint_local_time_steps_against_tangent(sst):
+    """Local time stepping (every cell its own dt_i): the adjoint of the step with per-cell
+    steps in the stages, the implicit collision and the SST update, against the tangent."""
+    base = _naca_sst() if sst else _naca_laminar()
+    case = dataclasses.replace(base, local_dt=True, cfl=0.2)
+    warm, n = 5, 8
+    g, d = _sst_seeds(case, np.random.default_rng(400 + int(sst)))
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    s.step(warm)
+    J, dJdf, dJdb, _ = s.adjoint(n, *W)
+    s.close()
+    Jt, dJt = _tangent_dJ(case, warm, n, g, d)
+    adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
+    assert abs(J - Jt) <= 1e-10 * abs(Jt)
+    assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)
