@@ -444,3 +444,45 @@ def test_adjoint_local_time_steps_against_tangent(sst):
     adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
     assert abs(J - Jt) <= 1e-10 * abs(Jt)
     assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)
+
+
+def test_adjoint_periodic_channel_against_tangent():
+    """A jittered triangular Couette channel, periodic in x: the transposed flux and gradient
+    gather across the glued faces through their back slots (the shifted neighbour offsets)."""
+    m = mg.couette_channel(12, 8, kind="tri", jitter=0.2, seed=4)
+    case = mg.Case(m, nu=0.01, cfl=0.5, uref=0.1)
+    warm, n = 10, 12
+    rng = np.random.default_rng(55)
+    g = 1e-3 * rng.standard_normal((m.n_cells, 9))
+    d = np.zeros((m.n_bedges, 5))
+    d[:, :3] = 1e-2 * rng.standard_normal((m.n_bedges, 3))
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    s.step(warm)
+    J, dJdf, dJdb, _ = s.adjoint(n, *W)
+    s.close()
+    Jt, dJt = _tangent_dJ(case, warm, n, g, d)
+    adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
+    assert abs(J - Jt) <= 1e-10 * abs(Jt)
+    assert abs(adj - dJt) <= 1e-9 * abs(dJt), (adj, dJt)
+    # glued edges carry no boundary value
+    glued = m.periodic_pairs.ravel()
+    assert np.all(dJdb[glued] == 0.0)
+
+
+def test_adjoint_instance_of_a_batch_equals_single_handle():
+    """In a batch (laminar cavity, SST airfoil, laminar airfoil) the adjoint of one instance
+    equals that of a handle holding the instance alone: instances do not couple, and the other
+    instances' adjoints stay zero."""
+    cases = [_cavity(), _naca_sst(), _naca_laminar()]
+    b = fvlbm.Solver(cases, precision=FP64, device=0, kernel_path=1)
+    b.step(6)
+    for i, c in enumerate(cases):
+        one = fvlbm.Solver(c, precision=FP64, device=0, kernel_path=1)
+        one.step(6)
+        got = b.adjoint(9, *W, i=i, shape=True)
+        ref = one.adjoint(9, *W, shape=True)
+        one.close()
+        assert abs(got[0] - ref[0]) <= 1e-12 * abs(ref[0])
+        for x, y in zip(got[1:], ref[1:]):
+            np.testing.assert_allclose(x, y, rtol=1e-10, atol=1e-12 * np.abs(y).max())
+    b.close()
