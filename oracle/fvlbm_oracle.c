@@ -28,10 +28,43 @@
  * by tests against closed forms and invariants.  The turbulent cases as a whole (inlet,
  * outlet and far-field readings together with SST transport) have no closed form: parity
  * unpinned beyond those invariants.
+ *
+ * Built with ORACLE_COMPLEX_STEP, the same source is the oracle's own tangent (complex-step
+ * method, see `real` below); its real parts equal the double build's values exactly, and its
+ * derivatives are pinned against central differences of the double build on a laminar case.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* The state arithmetic (f, the macros, k, omega, nu_t, tau, the boundary values and every
+ * quantity formed from them) is done in the type `real`: double, or -- when this file is
+ * compiled with ORACLE_COMPLEX_STEP -- double complex, for the complex-step derivative of the
+ * step (Squire and Trapp 1998): with the inputs seeded as x + i h d, every analytic operation
+ * carries f(x) + i h f'(x) d + O(h^2), so Im(J)/h is the directional derivative of J to
+ * rounding, with no difference taken.  Branches (upwind choice, limiters, clips, min / max)
+ * act on real parts, so the derivative is that of the branch the value takes; sqrt uses its
+ * first-order rule with derivative 0 at 0, the convention of the GPU tangent.  The geometry
+ * stays double.  In the double build every expression is the one the plain oracle evaluates. */
+#ifdef ORACLE_COMPLEX_STEP
+#include <complex.h>
+typedef double complex real;
+#define RE(x) creal(x)
+static real rsqrt(real x)
+{
+    double v = creal(x), s = v > 0.0 ? sqrt(v) : 0.0;
+    return s > 0.0 ? s + I * (cimag(x) / (2.0 * s)) : 0.0;
+}
+#define rtanh(x) ctanh(x)
+#else
+typedef double real;
+#define RE(x) (x)
+#define rsqrt(x) sqrt(x)
+#define rtanh(x) tanh(x)
+#endif
+/* min / max of two reals by value, keeping the first argument on ties */
+static real rmin(real a, real b) { return RE(b) < RE(a) ? b : a; }
+static real rmax(real a, real b) { return RE(b) > RE(a) ? b : a; }
 
 #define Q 9
 #ifndef M_PI
@@ -73,7 +106,7 @@ typedef struct oracle {
     oface *face;                 /* [nc * 4] */
     double *area, *cx, *cy, *wdist;
     int *btype, *bcell;
-    double *bval;                /* [nb * 5]: rho_b, u_b, v_b, k_b, omega_b */
+    real *bval;                  /* [nb * 5]: rho_b, u_b, v_b, k_b, omega_b */
     double *bxm, *bym, *bnx, *bny, *blen;
     double nu, rho0, dt, uref, lref, alpha_deg;
     double *dtc;                 /* local time stepping: dt of each cell (NULL: dt everywhere) */
@@ -82,13 +115,13 @@ typedef struct oracle {
                                     re-solved before every stage, 8 production limiter */
     int sst;
     int scheme;                  /* 0: IMEX Runge-Kutta (Part II); 1: explicit Euler (Part I) */
-    double *f;                   /* [nc * Q], cell-major */
-    double *rho, *ux, *uy, *k, *om, *nut, *tau;
+    real *f;                     /* [nc * Q], cell-major */
+    real *rho, *ux, *uy, *k, *om, *nut, *tau;
     double residual, moment_defect;
     long steps;
     /* work arrays */
-    double *fn, *fst, *ga[3], *gc[3], *gradf, *fbc, *feqs, *X;
-    double *gu, *gv, *gk, *gw, *rk, *rw, *f1, *Sabs;
+    real *fn, *fst, *ga[3], *gc[3], *gradf, *fbc, *feqs, *X;
+    real *gu, *gv, *gk, *gw, *rk, *rw, *f1, *Sabs;
 } oracle;
 
 /* Time step of cell i: its own under local time stepping, else the global one. */
@@ -97,19 +130,22 @@ static double cell_dt(const struct oracle *o, int i) { return o->dtc ? o->dtc[i]
 /* ------------------------------------------------------------------ equilibrium */
 /* f^eq_alpha(rho, u) = w_alpha rho [1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u.u]: the second-order
  * D2Q9 equilibrium with c = 1 (Part I; Sec. 3.1 names the lattice). */
-void oracle_feq(double rho, double u, double v, double *feq)
+static void feq_r(real rho, real u, real v, real *feq)
 {
-    double uu = u * u + v * v;
+    real uu = u * u + v * v;
     for (int a = 0; a < Q; a++) {
-        double eu = EX[a] * u + EY[a] * v;
+        real eu = EX[a] * u + EY[a] * v;
         feq[a] = WQ[a] * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
     }
 }
+#ifndef ORACLE_COMPLEX_STEP
+void oracle_feq(double rho, double u, double v, double *feq) { feq_r(rho, u, v, feq); }
+#endif
 
 /* rho = sum_alpha f_alpha, rho u = sum_alpha e_alpha f_alpha (collision invariants). */
-static void moments(const double *f, double *rho, double *u, double *v)
+static void moments(const real *f, real *rho, real *u, real *v)
 {
-    double r = 0, mx = 0, my = 0;
+    real r = 0, mx = 0, my = 0;
     for (int a = 0; a < Q; a++) {
         r += f[a];
         mx += EX[a] * f[a];
@@ -186,14 +222,14 @@ oracle *oracle_create(int n_nodes, const double *xy, int n_cells, const int *cel
     o->wdist = (double *)xcalloc(nc, sizeof(double));
     o->btype = (int *)xcalloc(nb, sizeof(int));
     o->bcell = (int *)xcalloc(nb, sizeof(int));
-    o->bval = (double *)xcalloc((size_t)nb * 5, sizeof(double));
+    o->bval = (real *)xcalloc((size_t)nb * 5, sizeof(real));
     o->bxm = (double *)xcalloc(nb, sizeof(double));
     o->bym = (double *)xcalloc(nb, sizeof(double));
     o->bnx = (double *)xcalloc(nb, sizeof(double));
     o->bny = (double *)xcalloc(nb, sizeof(double));
     o->blen = (double *)xcalloc(nb, sizeof(double));
     memcpy(o->btype, bedge_type, sizeof(int) * (size_t)nb);
-    memcpy(o->bval, bedge_val, sizeof(double) * 5 * (size_t)nb);
+    for (size_t q = 0; q < 5 * (size_t)nb; q++) o->bval[q] = bedge_val[q];
 
     /* cell area and centroid (polygon formulas, taken relative to the first node) */
     for (int i = 0; i < nc; i++) {
@@ -303,38 +339,38 @@ oracle *oracle_create(int n_nodes, const double *xy, int n_cells, const int *cel
 
     /* state and work arrays */
     size_t nq = (size_t)nc * Q;
-    o->f = (double *)xcalloc(nq, sizeof(double));
-    o->fn = (double *)xcalloc(nq, sizeof(double));
-    o->fst = (double *)xcalloc(nq, sizeof(double));
-    o->feqs = (double *)xcalloc(nq, sizeof(double));
-    o->X = (double *)xcalloc(nq, sizeof(double));
+    o->f = (real *)xcalloc(nq, sizeof(real));
+    o->fn = (real *)xcalloc(nq, sizeof(real));
+    o->fst = (real *)xcalloc(nq, sizeof(real));
+    o->feqs = (real *)xcalloc(nq, sizeof(real));
+    o->X = (real *)xcalloc(nq, sizeof(real));
     for (int J = 0; J < 3; J++) {
-        o->ga[J] = (double *)xcalloc(nq, sizeof(double));
-        o->gc[J] = (double *)xcalloc(nq, sizeof(double));
+        o->ga[J] = (real *)xcalloc(nq, sizeof(real));
+        o->gc[J] = (real *)xcalloc(nq, sizeof(real));
     }
-    o->gradf = (double *)xcalloc(nq * 2, sizeof(double));
-    o->fbc = (double *)xcalloc((size_t)nb * Q, sizeof(double));
-    o->rho = (double *)xcalloc(nc, sizeof(double));
-    o->ux = (double *)xcalloc(nc, sizeof(double));
-    o->uy = (double *)xcalloc(nc, sizeof(double));
-    o->k = (double *)xcalloc(nc, sizeof(double));
-    o->om = (double *)xcalloc(nc, sizeof(double));
-    o->nut = (double *)xcalloc(nc, sizeof(double));
-    o->tau = (double *)xcalloc(nc, sizeof(double));
-    o->gu = (double *)xcalloc((size_t)nc * 2, sizeof(double));
-    o->gv = (double *)xcalloc((size_t)nc * 2, sizeof(double));
-    o->gk = (double *)xcalloc((size_t)nc * 2, sizeof(double));
-    o->gw = (double *)xcalloc((size_t)nc * 2, sizeof(double));
-    o->rk = (double *)xcalloc(nc, sizeof(double));
-    o->rw = (double *)xcalloc(nc, sizeof(double));
-    o->f1 = (double *)xcalloc(nc, sizeof(double));
-    o->Sabs = (double *)xcalloc(nc, sizeof(double));
+    o->gradf = (real *)xcalloc(nq * 2, sizeof(real));
+    o->fbc = (real *)xcalloc((size_t)nb * Q, sizeof(real));
+    o->rho = (real *)xcalloc(nc, sizeof(real));
+    o->ux = (real *)xcalloc(nc, sizeof(real));
+    o->uy = (real *)xcalloc(nc, sizeof(real));
+    o->k = (real *)xcalloc(nc, sizeof(real));
+    o->om = (real *)xcalloc(nc, sizeof(real));
+    o->nut = (real *)xcalloc(nc, sizeof(real));
+    o->tau = (real *)xcalloc(nc, sizeof(real));
+    o->gu = (real *)xcalloc((size_t)nc * 2, sizeof(real));
+    o->gv = (real *)xcalloc((size_t)nc * 2, sizeof(real));
+    o->gk = (real *)xcalloc((size_t)nc * 2, sizeof(real));
+    o->gw = (real *)xcalloc((size_t)nc * 2, sizeof(real));
+    o->rk = (real *)xcalloc(nc, sizeof(real));
+    o->rw = (real *)xcalloc(nc, sizeof(real));
+    o->f1 = (real *)xcalloc(nc, sizeof(real));
+    o->Sabs = (real *)xcalloc(nc, sizeof(real));
 
     /* Step 0: f = f^eq(rho, u); k, omega initial; nu_t^0 = k / omega; tau from Eq. turbtau */
     for (int i = 0; i < nc; i++) {
         double r = rho_init ? rho_init[i] : o->rho0;
         double u = u_init ? u_init[i] : 0.0, v = v_init ? v_init[i] : 0.0;
-        oracle_feq(r, u, v, &o->f[(size_t)i * Q]);
+        feq_r(r, u, v, &o->f[(size_t)i * Q]);
         moments(&o->f[(size_t)i * Q], &o->rho[i], &o->ux[i], &o->uy[i]);
         o->k[i] = k_init ? k_init[i] : 0.0;
         o->om[i] = w_init ? w_init[i] : 1.0;
@@ -390,14 +426,16 @@ void oracle_destroy(oracle *o)
  * neighbour centroids (periodic ones shifted) with their cell values and, on boundary faces,
  * the face midpoint with the boundary value.  g = M^{-1} sum_m d_m (phi_m - phi_i),
  * M = sum_m d_m d_m^T.  phi is strided (value of cell i at phi[i*stride]). */
-static void lsq_gradient(const oracle *o, int i, const double *phi, int stride,
-                         const double *phib, int bstride, double *gx, double *gy)
+static void lsq_gradient(const oracle *o, int i, const real *phi, int stride,
+                         const real *phib, int bstride, real *gx, real *gy)
 {
-    double mxx = 0, mxy = 0, myy = 0, bx = 0, by = 0;
-    double pi = phi[(size_t)i * stride];
+    double mxx = 0, mxy = 0, myy = 0;
+    real bx = 0, by = 0;
+    real pi = phi[(size_t)i * stride];
     for (int l = 0; l < o->nface[i]; l++) {
         const oface *F = &o->face[4 * i + l];
-        double dx, dy, dp;
+        double dx, dy;
+        real dp;
         if (F->nbr >= 0) {
             dx = o->cx[F->nbr] + F->sx - o->cx[i];
             dy = o->cy[F->nbr] + F->sy - o->cy[i];
@@ -423,26 +461,26 @@ static void lsq_gradient(const oracle *o, int i, const double *phi, int stride,
  *   wall / inlet:  f^eq(rho_P, u_b) + [f_P - f^eq(rho_P, u_P)]   (non-equilibrium extrapolation)
  *   outlet:        f^eq(rho_b, u_P) + [f_P - f^eq(rho_P, u_P)]
  *   far field:     f^eq(rho_b, u_b) where e.n < 0 (incoming), f_P where e.n >= 0 (outgoing) */
-static void boundary_f(const oracle *o, const double *f, double *fbc)
+static void boundary_f(const oracle *o, const real *f, real *fbc)
 {
     for (int b = 0; b < o->nb; b++) {
         int t = o->btype[b];
         if (t == BC_PERIODIC) continue;
         int P = o->bcell[b];
-        const double *fp = &f[(size_t)P * Q];
-        const double *bv = &o->bval[5 * (size_t)b];
-        double *out = &fbc[(size_t)b * Q];
-        double rP, uP, vP, eqP[Q], eqB[Q];
+        const real *fp = &f[(size_t)P * Q];
+        const real *bv = &o->bval[5 * (size_t)b];
+        real *out = &fbc[(size_t)b * Q];
+        real rP, uP, vP, eqP[Q], eqB[Q];
         moments(fp, &rP, &uP, &vP);
-        oracle_feq(rP, uP, vP, eqP);
+        feq_r(rP, uP, vP, eqP);
         if (t == BC_WALL || t == BC_INLET) {
-            oracle_feq(rP, bv[1], bv[2], eqB);
+            feq_r(rP, bv[1], bv[2], eqB);
             for (int a = 0; a < Q; a++) out[a] = eqB[a] + (fp[a] - eqP[a]);
         } else if (t == BC_OUTLET) {
-            oracle_feq(bv[0], uP, vP, eqB);
+            feq_r(bv[0], uP, vP, eqB);
             for (int a = 0; a < Q; a++) out[a] = eqB[a] + (fp[a] - eqP[a]);
         } else { /* BC_FARFIELD */
-            oracle_feq(bv[0], bv[1], bv[2], eqB);
+            feq_r(bv[0], bv[1], bv[2], eqB);
             for (int a = 0; a < Q; a++) {
                 double en = EX[a] * o->bnx[b] + EY[a] * o->bny[b];
                 out[a] = en < 0.0 ? eqB[a] : fp[a];
@@ -457,27 +495,27 @@ static void boundary_f(const oracle *o, const double *f, double *fbc)
  * reconstructed increment g . (x_f - x_i) to face m, phi_m = [(D1^2 + e2) D2 + 2 D2^2 D1] /
  * [D1^2 + 2 D2^2 + D1 D2 + e2] / D2 (1 where D2 = 0), and phi = min_m phi_m.  e2 = (K h)^3
  * with h = sqrt(A_i) and K = 1 keeps smooth regions unlimited. */
-static double vk_limiter(const oracle *o, int i, const double *phi, int stride,
-                         const double *phib, int bstride, double gx, double gy)
+static real vk_limiter(const oracle *o, int i, const real *phi, int stride,
+                       const real *phib, int bstride, real gx, real gy)
 {
-    double pi = phi[(size_t)i * stride], lo = pi, hi = pi;
+    real pi = phi[(size_t)i * stride], lo = pi, hi = pi;
     for (int l = 0; l < o->nface[i]; l++) {
         const oface *F = &o->face[4 * i + l];
-        double q = F->nbr >= 0 ? phi[(size_t)F->nbr * stride] : phib[(size_t)F->bedge * bstride];
-        if (q < lo) lo = q;
-        if (q > hi) hi = q;
+        real q = F->nbr >= 0 ? phi[(size_t)F->nbr * stride] : phib[(size_t)F->bedge * bstride];
+        if (RE(q) < RE(lo)) lo = q;
+        if (RE(q) > RE(hi)) hi = q;
     }
     double h = sqrt(o->area[i]);
     double e2 = h * h * h;
-    double psi = 1.0;
+    real psi = 1.0;
     for (int l = 0; l < o->nface[i]; l++) {
         const oface *F = &o->face[4 * i + l];
-        double d2 = gx * (F->xm - o->cx[i]) + gy * (F->ym - o->cy[i]);
-        if (d2 == 0.0) continue;
-        double d1 = d2 > 0.0 ? hi - pi : lo - pi;
-        double r = ((d1 * d1 + e2) * d2 + 2.0 * d2 * d2 * d1) /
-                   (d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + e2) / d2;
-        if (r < psi) psi = r;
+        real d2 = gx * (F->xm - o->cx[i]) + gy * (F->ym - o->cy[i]);
+        if (RE(d2) == 0.0) continue;
+        real d1 = RE(d2) > 0.0 ? hi - pi : lo - pi;
+        real r = ((d1 * d1 + e2) * d2 + 2.0 * d2 * d2 * d1) /
+                 (d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + e2) / d2;
+        if (RE(r) < RE(psi)) psi = r;
     }
     return psi;
 }
@@ -487,16 +525,16 @@ static double vk_limiter(const oracle *o, int i, const double *phi, int stride,
  * Interior face values: upwind by the sign of e_alpha . n (n out of this cell), linear
  * reconstruction f + grad f . (x_face - x_cell) from the upwind cell (Part I reading).
  * Boundary faces use boundary_f(). */
-static void convection(oracle *o, const double *f, double *ga)
+static void convection(oracle *o, const real *f, real *ga)
 {
     int nc = o->nc;
     boundary_f(o, f, o->fbc);
     for (int i = 0; i < nc; i++)
         for (int a = 0; a < Q; a++) {
-            double gx, gy;
+            real gx, gy;
             lsq_gradient(o, i, f + a, Q, o->fbc + a, Q, &gx, &gy);
             if (o->variant & 1) {
-                double phi = vk_limiter(o, i, f + a, Q, o->fbc + a, Q, gx, gy);
+                real phi = vk_limiter(o, i, f + a, Q, o->fbc + a, Q, gx, gy);
                 gx *= phi;
                 gy *= phi;
             }
@@ -505,19 +543,19 @@ static void convection(oracle *o, const double *f, double *ga)
         }
     for (int i = 0; i < nc; i++) {
         for (int a = 0; a < Q; a++) {
-            double sum = 0.0;
+            real sum = 0.0;
             for (int l = 0; l < o->nface[i]; l++) {
                 const oface *F = &o->face[4 * i + l];
                 double en = EX[a] * F->nx + EY[a] * F->ny;
-                double fv;
+                real fv;
                 if (F->nbr < 0) {
                     fv = o->fbc[(size_t)F->bedge * Q + a];
                 } else if (en >= 0.0) {
-                    const double *g = &o->gradf[((size_t)i * Q + a) * 2];
+                    const real *g = &o->gradf[((size_t)i * Q + a) * 2];
                     fv = f[(size_t)i * Q + a] + g[0] * (F->xm - o->cx[i]) + g[1] * (F->ym - o->cy[i]);
                 } else {
                     int j = F->nbr;
-                    const double *g = &o->gradf[((size_t)j * Q + a) * 2];
+                    const real *g = &o->gradf[((size_t)j * Q + a) * 2];
                     fv = f[(size_t)j * Q + a] + g[0] * (F->xm - (o->cx[j] + F->sx)) +
                          g[1] * (F->ym - (o->cy[j] + F->sy));
                 }
@@ -534,32 +572,33 @@ static void convection(oracle *o, const double *f, double *ga)
  * arg1 = min(max(sqrt(k)/(0.09 omega d), 500 nu/(omega d^2)), 4 sigma_w2 k/(CD_kw d^2));
  * f1 = tanh(arg1^4); arg2 = max(2 sqrt(k)/(0.09 omega d), 500 nu/(omega d^2)); f2 = tanh(arg2^2);
  * nu_t = a1 k / max(a1 omega, S f2). */
-static double sst_cdkw(double w, double gkx, double gky, double gwx, double gwy)
+static real sst_cdkw(real w, real gkx, real gky, real gwx, real gwy)
 {
-    double c = 2.0 * SW2 / w * (gkx * gwx + gky * gwy);
-    return c > 1e-20 ? c : 1e-20;
+    real c = 2.0 * SW2 / w * (gkx * gwx + gky * gwy);
+    return RE(c) > 1e-20 ? c : 1e-20;
 }
 
-static double sst_f1(double k, double w, double d, double nu, double cdkw)
+static real sst_f1(real k, real w, double d, double nu, real cdkw)
 {
-    double a = sqrt(k) / (BSTAR * w * d);
-    double b = 500.0 * nu / (w * d * d);
-    double c = 4.0 * SW2 * k / (cdkw * d * d);
-    double arg1 = fmin(fmax(a, b), c);
-    return tanh(arg1 * arg1 * arg1 * arg1);
+    real a = rsqrt(k) / (BSTAR * w * d);
+    real b = 500.0 * nu / (w * d * d);
+    real c = 4.0 * SW2 * k / (cdkw * d * d);
+    real arg1 = rmin(rmax(a, b), c);
+    return rtanh(arg1 * arg1 * arg1 * arg1);
 }
 
-static double sst_f2(double k, double w, double d, double nu)
+static real sst_f2(real k, real w, double d, double nu)
 {
-    double arg2 = fmax(2.0 * sqrt(k) / (BSTAR * w * d), 500.0 * nu / (w * d * d));
-    return tanh(arg2 * arg2);
+    real arg2 = rmax(2.0 * rsqrt(k) / (BSTAR * w * d), 500.0 * nu / (w * d * d));
+    return rtanh(arg2 * arg2);
 }
 
-static double sst_nut(double k, double w, double S, double f2)
+static real sst_nut(real k, real w, real S, real f2)
 {
-    return A1 * k / fmax(A1 * w, S * f2);
+    return A1 * k / rmax(A1 * w, S * f2);
 }
 
+#ifndef ORACLE_COMPLEX_STEP
 /* out = {f1, f2, CD_kw, nu_t} at one point (for tests). */
 void oracle_sst_point(double k, double w, double d, double gkx, double gky, double gwx,
                       double gwy, double S, double nu, double *out)
@@ -571,15 +610,16 @@ void oracle_sst_point(double k, double w, double d, double gkx, double gky, doub
     out[2] = cd;
     out[3] = sst_nut(k, w, S, f2);
 }
+#endif
 
 /* Boundary values of u, v, k, omega for the SST gradients and face fluxes (Menter 1994
  * boundary conditions, Sec. 3.2; readings): wall k = 0, omega = 60 nu / (beta1 d^2) with d
  * the wall cell's wall distance; inlet / far field k_b, omega_b given; outlet zero gradient.
  * Velocity: wall / inlet / far field u_b; outlet the cell velocity. */
-static void sst_boundary(const oracle *o, int b, double *ub, double *vb, double *kb, double *wb)
+static void sst_boundary(const oracle *o, int b, real *ub, real *vb, real *kb, real *wb)
 {
     int P = o->bcell[b];
-    const double *bv = &o->bval[5 * (size_t)b];
+    const real *bv = &o->bval[5 * (size_t)b];
     switch (o->btype[b]) {
     case BC_WALL:
         *ub = bv[1]; *vb = bv[2]; *kb = 0.0;
@@ -598,24 +638,24 @@ static void sst_boundary(const oracle *o, int b, double *ub, double *vb, double 
  * scheme of Sec. 3.2 on unstructured cells): the largest psi in [0, 1] such that every face
  * value phi_i + psi grad phi . (x_f - x_i) stays within the min / max of phi_i, its face
  * neighbours and its boundary values. */
-static double bj_limiter(const oracle *o, int i, const double *phi, const double *phib,
-                         int bstride, const double *g)
+static real bj_limiter(const oracle *o, int i, const real *phi, const real *phib,
+                       int bstride, const real *g)
 {
-    double lo = phi[i], hi = phi[i];
+    real lo = phi[i], hi = phi[i];
     for (int l = 0; l < o->nface[i]; l++) {
         const oface *F = &o->face[4 * i + l];
-        double q = F->nbr >= 0 ? phi[F->nbr] : phib[(size_t)F->bedge * bstride];
-        if (q < lo) lo = q;
-        if (q > hi) hi = q;
+        real q = F->nbr >= 0 ? phi[F->nbr] : phib[(size_t)F->bedge * bstride];
+        if (RE(q) < RE(lo)) lo = q;
+        if (RE(q) > RE(hi)) hi = q;
     }
-    double psi = 1.0;
+    real psi = 1.0;
     for (int l = 0; l < o->nface[i]; l++) {
         const oface *F = &o->face[4 * i + l];
-        double d = g[0] * (F->xm - o->cx[i]) + g[1] * (F->ym - o->cy[i]);
-        double r = 1.0;
-        if (d > 0.0) r = (hi - phi[i]) / d;
-        else if (d < 0.0) r = (lo - phi[i]) / d;
-        if (r < psi) psi = r;
+        real d = g[0] * (F->xm - o->cx[i]) + g[1] * (F->ym - o->cy[i]);
+        real r = 1.0;
+        if (RE(d) > 0.0) r = (hi - phi[i]) / d;
+        else if (RE(d) < 0.0) r = (lo - phi[i]) / d;
+        if (RE(r) < RE(psi)) psi = r;
     }
     return psi;
 }
@@ -628,7 +668,7 @@ static double bj_limiter(const oracle *o, int i, const double *phi, const double
 static void sst_update(oracle *o)
 {
     int nc = o->nc, nb = o->nb;
-    double *ubc = (double *)xcalloc((size_t)nb * 4, sizeof(double));
+    real *ubc = (real *)xcalloc((size_t)nb * 4, sizeof(real));
     for (int b = 0; b < nb; b++)
         if (o->btype[b] != BC_PERIODIC)
             sst_boundary(o, b, &ubc[4 * b], &ubc[4 * b + 1], &ubc[4 * b + 2], &ubc[4 * b + 3]);
@@ -639,53 +679,54 @@ static void sst_update(oracle *o)
         lsq_gradient(o, i, o->om, 1, ubc + 3, 4, &o->gw[2 * i], &o->gw[2 * i + 1]);
     }
     /* limited gradients for the upwind face values of k and omega */
-    double *lk = (double *)xcalloc((size_t)nc * 2, sizeof(double));
-    double *lw = (double *)xcalloc((size_t)nc * 2, sizeof(double));
+    real *lk = (real *)xcalloc((size_t)nc * 2, sizeof(real));
+    real *lw = (real *)xcalloc((size_t)nc * 2, sizeof(real));
     for (int i = 0; i < nc; i++) {
-        double pk = bj_limiter(o, i, o->k, ubc + 2, 4, &o->gk[2 * i]);
-        double pw = bj_limiter(o, i, o->om, ubc + 3, 4, &o->gw[2 * i]);
+        real pk = bj_limiter(o, i, o->k, ubc + 2, 4, &o->gk[2 * i]);
+        real pw = bj_limiter(o, i, o->om, ubc + 3, 4, &o->gw[2 * i]);
         lk[2 * i] = pk * o->gk[2 * i];
         lk[2 * i + 1] = pk * o->gk[2 * i + 1];
         lw[2 * i] = pw * o->gw[2 * i];
         lw[2 * i + 1] = pw * o->gw[2 * i + 1];
     }
-    double *sk = (double *)xcalloc(nc, sizeof(double));
-    double *sw = (double *)xcalloc(nc, sizeof(double));
-    double *SS = (double *)xcalloc(nc, sizeof(double));
-    double *dv = (double *)xcalloc(nc, sizeof(double));
+    real *sk = (real *)xcalloc(nc, sizeof(real));
+    real *sw = (real *)xcalloc(nc, sizeof(real));
+    real *SS = (real *)xcalloc(nc, sizeof(real));
+    real *dv = (real *)xcalloc(nc, sizeof(real));
     for (int i = 0; i < nc; i++) {
-        double s11 = o->gu[2 * i], s22 = o->gv[2 * i + 1];
-        double s12 = 0.5 * (o->gu[2 * i + 1] + o->gv[2 * i]);
+        real s11 = o->gu[2 * i], s22 = o->gv[2 * i + 1];
+        real s12 = 0.5 * (o->gu[2 * i + 1] + o->gv[2 * i]);
         SS[i] = s11 * s11 + s22 * s22 + 2.0 * s12 * s12; /* S_ij S_ij */
         dv[i] = s11 + s22;
-        o->Sabs[i] = sqrt(2.0 * SS[i]);
-        double cd = sst_cdkw(o->om[i], o->gk[2 * i], o->gk[2 * i + 1], o->gw[2 * i], o->gw[2 * i + 1]);
+        o->Sabs[i] = rsqrt(2.0 * SS[i]);
+        real cd = sst_cdkw(o->om[i], o->gk[2 * i], o->gk[2 * i + 1], o->gw[2 * i], o->gw[2 * i + 1]);
         o->f1[i] = sst_f1(o->k[i], o->om[i], o->wdist[i], o->nu, cd);
         sk[i] = o->f1[i] * SK1 + (1.0 - o->f1[i]) * SK2;
         sw[i] = o->f1[i] * SW1 + (1.0 - o->f1[i]) * SW2;
     }
     for (int i = 0; i < nc; i++) {
-        double ck = 0, cw = 0, dk = 0, dw = 0;
+        real ck = 0, cw = 0, dk = 0, dw = 0;
         for (int l = 0; l < o->nface[i]; l++) {
             const oface *F = &o->face[4 * i + l];
-            double uf, vf, kup, wup, rx = F->xm - o->cx[i], ry = F->ym - o->cy[i];
-            double kin = o->k[i] + lk[2 * i] * rx + lk[2 * i + 1] * ry;
-            double win = o->om[i] + lw[2 * i] * rx + lw[2 * i + 1] * ry;
+            double rx = F->xm - o->cx[i], ry = F->ym - o->cy[i];
+            real uf, vf, kup, wup;
+            real kin = o->k[i] + lk[2 * i] * rx + lk[2 * i + 1] * ry;
+            real win = o->om[i] + lw[2 * i] * rx + lw[2 * i + 1] * ry;
             if (F->nbr >= 0) {
                 int j = F->nbr;
                 double xj = o->cx[j] + F->sx, yj = o->cy[j] + F->sy;
                 uf = 0.5 * (o->ux[i] + o->ux[j]);
                 vf = 0.5 * (o->uy[i] + o->uy[j]);
-                double un = uf * F->nx + vf * F->ny;
+                real un = uf * F->nx + vf * F->ny;
                 double sx = F->xm - xj, sy = F->ym - yj;
-                kup = un >= 0.0 ? kin : o->k[j] + lk[2 * j] * sx + lk[2 * j + 1] * sy;
-                wup = un >= 0.0 ? win : o->om[j] + lw[2 * j] * sx + lw[2 * j + 1] * sy;
+                kup = RE(un) >= 0.0 ? kin : o->k[j] + lk[2 * j] * sx + lk[2 * j + 1] * sy;
+                wup = RE(un) >= 0.0 ? win : o->om[j] + lw[2 * j] * sx + lw[2 * j + 1] * sy;
                 double dist = sqrt((xj - o->cx[i]) * (xj - o->cx[i]) + (yj - o->cy[i]) * (yj - o->cy[i]));
-                double gkf = 0.5 * ((o->nu + sk[i] * o->nut[i]) + (o->nu + sk[j] * o->nut[j]));
-                double gwf = 0.5 * ((o->nu + sw[i] * o->nut[i]) + (o->nu + sw[j] * o->nut[j]));
+                real gkf = 0.5 * ((o->nu + sk[i] * o->nut[i]) + (o->nu + sk[j] * o->nut[j]));
+                real gwf = 0.5 * ((o->nu + sw[i] * o->nut[i]) + (o->nu + sw[j] * o->nut[j]));
                 ck += un * kup * F->len;
                 cw += un * wup * F->len;
-                double ck_n = (o->k[j] - o->k[i]) / dist, cw_n = (o->om[j] - o->om[i]) / dist;
+                real ck_n = (o->k[j] - o->k[i]) / dist, cw_n = (o->om[j] - o->om[i]) / dist;
                 if (o->variant & 2) {
                     /* non-orthogonal correction (variant 2): grad phi . n = (phi_j - phi_i)/|d|
                      * + mean grad phi . (n - d/|d|) */
@@ -696,14 +737,14 @@ static void sst_update(oracle *o)
                 dk += gkf * ck_n * F->len;
                 dw += gwf * cw_n * F->len;
             } else {
-                const double *ub = &ubc[4 * F->bedge];
-                double un = ub[0] * F->nx + ub[1] * F->ny;
-                kup = un >= 0.0 ? kin : ub[2];
-                wup = un >= 0.0 ? win : ub[3];
+                const real *ub = &ubc[4 * F->bedge];
+                real un = ub[0] * F->nx + ub[1] * F->ny;
+                kup = RE(un) >= 0.0 ? kin : ub[2];
+                wup = RE(un) >= 0.0 ? win : ub[3];
                 double dist = sqrt(rx * rx + ry * ry);
                 ck += un * kup * F->len;
                 cw += un * wup * F->len;
-                double ck_n = (ub[2] - o->k[i]) / dist, cw_n = (ub[3] - o->om[i]) / dist;
+                real ck_n = (ub[2] - o->k[i]) / dist, cw_n = (ub[3] - o->om[i]) / dist;
                 if (o->variant & 2) {
                     double tx = F->nx - rx / dist, ty = F->ny - ry / dist;
                     ck_n += o->gk[2 * i] * tx + o->gk[2 * i + 1] * ty;
@@ -713,33 +754,33 @@ static void sst_update(oracle *o)
                 dw += (o->nu + sw[i] * o->nut[i]) * cw_n * F->len;
             }
         }
-        double f1 = o->f1[i];
-        double gam = f1 * (B1 / BSTAR - SW1 * KAPPA * KAPPA / sqrt(BSTAR)) +
-                     (1.0 - f1) * (B2 / BSTAR - SW2 * KAPPA * KAPPA / sqrt(BSTAR));
+        real f1 = o->f1[i];
+        real gam = f1 * (B1 / BSTAR - SW1 * KAPPA * KAPPA / sqrt(BSTAR)) +
+                   (1.0 - f1) * (B2 / BSTAR - SW2 * KAPPA * KAPPA / sqrt(BSTAR));
         /* production P / rho = nu_t (2 S_ij S_ij - 2/3 (div u)^2) - 2/3 k div u */
-        double pk = o->nut[i] * (2.0 * SS[i] - 2.0 / 3.0 * dv[i] * dv[i]) - 2.0 / 3.0 * o->k[i] * dv[i];
+        real pk = o->nut[i] * (2.0 * SS[i] - 2.0 / 3.0 * dv[i] * dv[i]) - 2.0 / 3.0 * o->k[i] * dv[i];
         /* variant 8: Menter's production limiter P_k <= 10 beta* omega k (not in the paper) */
-        if ((o->variant & 8) && pk > 10.0 * BSTAR * o->om[i] * o->k[i]) pk = 10.0 * BSTAR * o->om[i] * o->k[i];
+        if ((o->variant & 8) && RE(pk) > RE(10.0 * BSTAR * o->om[i] * o->k[i])) pk = 10.0 * BSTAR * o->om[i] * o->k[i];
         /* gamma P / nu_t, with the k div u / nu_t part taken as 0 when nu_t = 0 */
-        double pw = gam * (2.0 * SS[i] - 2.0 / 3.0 * dv[i] * dv[i]);
-        if (o->nut[i] > 0.0) pw -= 2.0 / 3.0 * gam * o->k[i] * dv[i] / o->nut[i];
-        double cross = 2.0 * (1.0 - f1) * SW2 / o->om[i] *
+        real pw = gam * (2.0 * SS[i] - 2.0 / 3.0 * dv[i] * dv[i]);
+        if (RE(o->nut[i]) > 0.0) pw -= 2.0 / 3.0 * gam * o->k[i] * dv[i] / o->nut[i];
+        real cross = 2.0 * (1.0 - f1) * SW2 / o->om[i] *
                        (o->gk[2 * i] * o->gw[2 * i] + o->gk[2 * i + 1] * o->gw[2 * i + 1]);
         o->rk[i] = (-ck + dk) / o->area[i] + pk;
         o->rw[i] = (-cw + dw) / o->area[i] + pw + cross;
     }
     double wmin = 1e-12 * o->uref / o->lref;
     for (int i = 0; i < nc; i++) {
-        double f1 = o->f1[i];
-        double beta = f1 * B1 + (1.0 - f1) * B2;
+        real f1 = o->f1[i];
+        real beta = f1 * B1 + (1.0 - f1) * B2;
         double dt = cell_dt(o, i);
-        double kn = (o->k[i] + dt * o->rk[i]) / (1.0 + dt * BSTAR * o->om[i]);
-        double wn = (o->om[i] + dt * o->rw[i]) / (1.0 + dt * beta * o->om[i]);
-        o->k[i] = kn > 0.0 ? kn : 0.0;
-        o->om[i] = wn > wmin ? wn : wmin;
+        real kn = (o->k[i] + dt * o->rk[i]) / (1.0 + dt * BSTAR * o->om[i]);
+        real wn = (o->om[i] + dt * o->rw[i]) / (1.0 + dt * beta * o->om[i]);
+        o->k[i] = RE(kn) > 0.0 ? kn : 0.0;
+        o->om[i] = RE(wn) > wmin ? wn : wmin;
     }
     for (int i = 0; i < nc; i++) {
-        double f2 = sst_f2(o->k[i], o->om[i], o->wdist[i], o->nu);
+        real f2 = sst_f2(o->k[i], o->om[i], o->wdist[i], o->nu);
         o->nut[i] = sst_nut(o->k[i], o->om[i], o->Sabs[i], f2);
         o->tau[i] = (o->nu + o->nut[i]) / CS2;
     }
@@ -765,45 +806,45 @@ static int imex_step(oracle *o)
      * stage value (f^n, f^(1), f^(2)), and the stage uses the resulting tau; the last solve
      * gives k, omega at t^{n+1}. */
     int per_stage = o->sst && (o->variant & 4);
-    double *k0 = NULL, *w0 = NULL, *nt0 = NULL;
+    real *k0 = NULL, *w0 = NULL, *nt0 = NULL;
     if (per_stage) {
-        k0 = (double *)xcalloc(nc, sizeof(double));
-        w0 = (double *)xcalloc(nc, sizeof(double));
-        nt0 = (double *)xcalloc(nc, sizeof(double));
-        memcpy(k0, o->k, nc * sizeof(double));
-        memcpy(w0, o->om, nc * sizeof(double));
-        memcpy(nt0, o->nut, nc * sizeof(double));
+        k0 = (real *)xcalloc(nc, sizeof(real));
+        w0 = (real *)xcalloc(nc, sizeof(real));
+        nt0 = (real *)xcalloc(nc, sizeof(real));
+        memcpy(k0, o->k, nc * sizeof(real));
+        memcpy(w0, o->om, nc * sizeof(real));
+        memcpy(nt0, o->nut, nc * sizeof(real));
     }
     if (o->sst) sst_update(o); /* Step 1 */
     else
         for (int i = 0; i < nc; i++) o->tau[i] = o->nu / CS2;
-    memcpy(o->fn, o->f, nq * sizeof(double));
+    memcpy(o->fn, o->f, nq * sizeof(real));
     double defect = 0.0;
     for (int J = 0; J < 3; J++) {
         if (per_stage && J > 0) {
-            memcpy(o->k, k0, nc * sizeof(double));
-            memcpy(o->om, w0, nc * sizeof(double));
-            memcpy(o->nut, nt0, nc * sizeof(double));
+            memcpy(o->k, k0, nc * sizeof(real));
+            memcpy(o->om, w0, nc * sizeof(real));
+            memcpy(o->nut, nt0, nc * sizeof(real));
             for (int i = 0; i < nc; i++) moments(&o->fst[(size_t)i * Q], &o->rho[i], &o->ux[i], &o->uy[i]);
             sst_update(o);
         }
         for (int i = 0; i < nc; i++) {
-            double tau = o->tau[i];
+            real tau = o->tau[i];
             double dt = cell_dt(o, i);
-            double *X = &o->X[(size_t)i * Q];
-            const double *fn = &o->fn[(size_t)i * Q];
+            real *X = &o->X[(size_t)i * Q];
+            const real *fn = &o->fn[(size_t)i * Q];
             for (int a = 0; a < Q; a++) {
-                double s = fn[a];
+                real s = fn[a];
                 for (int k = 0; k < J; k++) s += dt * MT[J][k] * o->ga[k][(size_t)i * Q + a];
                 X[a] = s;
             }
-            double r, u, v, eq[Q];
+            real r, u, v, eq[Q];
             moments(X, &r, &u, &v);
-            oracle_feq(r, u, v, eq);
-            double zJ = dt / tau * MI[J][J];
-            double *fs = &o->fst[(size_t)i * Q];
+            feq_r(r, u, v, eq);
+            real zJ = dt / tau * MI[J][J];
+            real *fs = &o->fst[(size_t)i * Q];
             for (int a = 0; a < Q; a++) {
-                double num = fn[a];
+                real num = fn[a];
                 for (int k = 0; k < J; k++)
                     num += dt * (MT[J][k] * o->ga[k][(size_t)i * Q + a] +
                                  MI[J][k] * o->gc[k][(size_t)i * Q + a]);
@@ -812,16 +853,16 @@ static int imex_step(oracle *o)
                 o->gc[J][(size_t)i * Q + a] = -(fs[a] - eq[a]) / tau;
             }
             /* moment elimination check: sum f^(J) psi must equal the moments of X */
-            double r2, u2, v2;
+            real r2, u2, v2;
             moments(fs, &r2, &u2, &v2);
-            double dd = fabs(r2 - r) + fabs(r2 * u2 - r * u) + fabs(r2 * v2 - r * v);
+            double dd = fabs(RE(r2 - r)) + fabs(RE(r2 * u2 - r * u)) + fabs(RE(r2 * v2 - r * v));
             if (dd > defect) defect = dd;
         }
         convection(o, o->fst, o->ga[J]); /* Step 2 for the next stage / the final update */
     }
     for (size_t q = 0; q < nq; q++) {
         double dt = cell_dt(o, (int)(q / Q));
-        double s = o->fn[q];
+        real s = o->fn[q];
         for (int J = 0; J < 3; J++) s += dt * (NT[J] * o->ga[J][q] + NI[J] * o->gc[J][q]);
         o->f[q] = s;
     }
@@ -841,14 +882,14 @@ static int finish_step(oracle *o)
     double num = 0.0, den = 0.0;
     int bad = 0;
     for (int i = 0; i < nc; i++) {
-        double r, u, v;
+        real r, u, v;
         moments(&o->f[(size_t)i * Q], &r, &u, &v);
-        num += (u - o->ux[i]) * (u - o->ux[i]) + (v - o->uy[i]) * (v - o->uy[i]);
-        den += u * u + v * v;
+        num += RE((u - o->ux[i]) * (u - o->ux[i]) + (v - o->uy[i]) * (v - o->uy[i]));
+        den += RE(u * u + v * v);
         o->rho[i] = r;
         o->ux[i] = u;
         o->uy[i] = v;
-        if (!(r == r) || !(u == u) || !(v == v)) bad = 1;
+        if (!(RE(r) == RE(r)) || !(RE(u) == RE(u)) || !(RE(v) == RE(v))) bad = 1;
     }
     o->residual = den > 0.0 ? sqrt(num) / sqrt(den) : sqrt(num);
     o->steps++;
@@ -867,12 +908,12 @@ static int euler_step(oracle *o)
     convection(o, o->f, o->ga[0]);
     for (int i = 0; i < nc; i++) {
         double dt = cell_dt(o, i);
-        double *f = &o->f[(size_t)i * Q];
-        double r, u, v, eq[Q];
+        real *f = &o->f[(size_t)i * Q];
+        real r, u, v, eq[Q];
         moments(f, &r, &u, &v);
-        oracle_feq(r, u, v, eq);
+        feq_r(r, u, v, eq);
         for (int a = 0; a < Q; a++) {
-            double gc = -(f[a] - eq[a]) / o->tau[i];
+            real gc = -(f[a] - eq[a]) / o->tau[i];
             f[a] = f[a] + dt * (o->ga[0][(size_t)i * Q + a] + gc);
         }
     }
@@ -898,11 +939,14 @@ void oracle_dt_cells(const oracle *o, double *out)
 double oracle_residual(const oracle *o) { return o->residual; }
 double oracle_moment_defect(const oracle *o) { return o->moment_defect; }
 
-void oracle_get_f(const oracle *o, double *f) { memcpy(f, o->f, sizeof(double) * (size_t)o->nc * Q); }
+void oracle_get_f(const oracle *o, double *f)
+{
+    for (size_t q = 0; q < (size_t)o->nc * Q; q++) f[q] = RE(o->f[q]);
+}
 
 void oracle_set_f(oracle *o, const double *f)
 {
-    memcpy(o->f, f, sizeof(double) * (size_t)o->nc * Q);
+    for (size_t q = 0; q < (size_t)o->nc * Q; q++) o->f[q] = f[q];
     for (int i = 0; i < o->nc; i++) moments(&o->f[(size_t)i * Q], &o->rho[i], &o->ux[i], &o->uy[i]);
 }
 
@@ -910,12 +954,12 @@ void oracle_get_fields(const oracle *o, double *rho, double *u, double *v, doubl
                        double *w, double *nut)
 {
     for (int i = 0; i < o->nc; i++) {
-        if (rho) rho[i] = o->rho[i];
-        if (u) u[i] = o->ux[i];
-        if (v) v[i] = o->uy[i];
-        if (k) k[i] = o->k[i];
-        if (w) w[i] = o->om[i];
-        if (nut) nut[i] = o->nut[i];
+        if (rho) rho[i] = RE(o->rho[i]);
+        if (u) u[i] = RE(o->ux[i]);
+        if (v) v[i] = RE(o->uy[i]);
+        if (k) k[i] = RE(o->k[i]);
+        if (w) w[i] = RE(o->om[i]);
+        if (nut) nut[i] = RE(o->nut[i]);
     }
 }
 
@@ -934,13 +978,14 @@ double oracle_mass(const oracle *o)
 {
     double m = 0.0;
     for (int i = 0; i < o->nc; i++) {
-        double r = 0.0;
+        real r = 0.0;
         for (int a = 0; a < Q; a++) r += o->f[(size_t)i * Q + a];
-        m += r * o->area[i];
+        m += RE(r) * o->area[i];
     }
     return m;
 }
 
+#ifndef ORACLE_COMPLEX_STEP
 /* Gradient of a per-cell field phi with boundary values phib (one per boundary edge). */
 /* The limiter value of the f reconstruction (variant 1) for a scalar field phi with boundary
  * values phib [n_bedges], at its least-squares gradient, per cell (test access). */
@@ -960,37 +1005,38 @@ void oracle_gradient(oracle *o, const double *phi, const double *phib, double *g
 
 /* Gamma^a of a given f [nc * Q] with the mesh's boundary conditions. */
 void oracle_convection(oracle *o, const double *f, double *ga) { convection(o, f, ga); }
+#endif
 
 /* Force on the walls (reading): F = sum_{wall faces} sum_alpha e_alpha (e_alpha . n) f_{alpha,bc}
  * Delta l, n out of the fluid cell -- the momentum flux of the face values of Eq. (advection).
  * out = {Fx, Fy, C_D, C_L} with C_D, C_L along / normal to the free-stream angle and
  * normalised by 0.5 rho0 U^2 L; cp[b] = (cs^2 rho_P - cs^2 rho0) / (0.5 rho0 U^2) on wall
  * edges, 0 elsewhere; fxe / fye (optional) receive the force on each wall edge. */
-void oracle_forces(oracle *o, double *out, double *cp, double *fxe, double *fye)
+static void forces_r(oracle *o, real *out, double *cp, double *fxe, double *fye)
 {
     boundary_f(o, o->f, o->fbc);
-    double fx = 0.0, fy = 0.0;
+    real fx = 0.0, fy = 0.0;
     double q = 0.5 * o->rho0 * o->uref * o->uref;
     for (int b = 0; b < o->nb; b++) {
         if (cp) cp[b] = 0.0;
         if (fxe) fxe[b] = 0.0;
         if (fye) fye[b] = 0.0;
         if (o->btype[b] != BC_WALL) continue;
-        double ex = 0.0, ey = 0.0;
+        real ex = 0.0, ey = 0.0;
         for (int a = 0; a < Q; a++) {
             double en = EX[a] * o->bnx[b] + EY[a] * o->bny[b];
-            double m = en * o->fbc[(size_t)b * Q + a] * o->blen[b];
+            real m = en * o->fbc[(size_t)b * Q + a] * o->blen[b];
             ex += EX[a] * m;
             ey += EY[a] * m;
         }
         fx += ex;
         fy += ey;
-        if (fxe) fxe[b] = ex;
-        if (fye) fye[b] = ey;
+        if (fxe) fxe[b] = RE(ex);
+        if (fye) fye[b] = RE(ey);
         if (cp) {
-            double r = 0.0;
+            real r = 0.0;
             for (int a = 0; a < Q; a++) r += o->f[(size_t)o->bcell[b] * Q + a];
-            cp[b] = (CS2 * r - CS2 * o->rho0) / q;
+            cp[b] = RE((CS2 * r - CS2 * o->rho0) / q);
         }
     }
     double al = o->alpha_deg * M_PI / 180.0;
@@ -999,3 +1045,36 @@ void oracle_forces(oracle *o, double *out, double *cp, double *fxe, double *fye)
     out[2] = (fx * cos(al) + fy * sin(al)) / (q * o->lref);
     out[3] = (-fx * sin(al) + fy * cos(al)) / (q * o->lref);
 }
+
+void oracle_forces(oracle *o, double *out, double *cp, double *fxe, double *fye)
+{
+    real r[4];
+    forces_r(o, r, cp, fxe, fye);
+    for (int c = 0; c < 4; c++) out[c] = RE(r[c]);
+}
+
+#ifdef ORACLE_COMPLEX_STEP
+/* Complex-step seeding: the boundary values [5 * n_bedges] and f [n_cells * 9] (either may be
+ * NULL) take imaginary parts h * d; the macros follow f. */
+void oracle_cs_seed(oracle *o, const double *dbval, const double *df, double h)
+{
+    if (dbval)
+        for (size_t q = 0; q < 5 * (size_t)o->nb; q++) o->bval[q] += I * (h * dbval[q]);
+    if (df) {
+        for (size_t q = 0; q < (size_t)o->nc * Q; q++) o->f[q] += I * (h * df[q]);
+        for (int i = 0; i < o->nc; i++) moments(&o->f[(size_t)i * Q], &o->rho[i], &o->ux[i], &o->uy[i]);
+    }
+}
+
+/* Fx, Fy, C_D, C_L (real parts) and their derivatives along the seeded direction (imaginary
+ * parts / h). */
+void oracle_cs_forces(oracle *o, double h, double *val, double *der)
+{
+    real r[4];
+    forces_r(o, r, NULL, NULL, NULL);
+    for (int c = 0; c < 4; c++) {
+        val[c] = creal(r[c]);
+        der[c] = cimag(r[c]) / h;
+    }
+}
+#endif

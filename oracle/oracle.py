@@ -18,24 +18,64 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "fvlbm_oracle.c")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboracle.so")
+LIB_CS = os.path.join(BUILD, "liboracle_cs.so")   # complex-step build (the oracle's tangent)
 _lock = threading.Lock()
 _lib = None
+_lib_cs = None
 
 Q = 9
 _D = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
 _I = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, complex_step: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, so that every product is rounded as
-    written)."""
+    written); with ``complex_step`` the same source in complex arithmetic (the oracle's own
+    tangent by the complex-step method)."""
     os.makedirs(BUILD, exist_ok=True)
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + f".tmp{os.getpid()}"
+    lib = LIB_CS if complex_step else LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(SRC):
+        tmp = lib + f".tmp{os.getpid()}"
+        flags = ["-DORACLE_COMPLEX_STEP"] if complex_step else []
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, SRC, "-lm"])
-        os.replace(tmp, LIB)
-    return LIB
+                               *flags, "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, lib)
+    return lib
+
+
+def _common(lib):
+    vp = C.c_void_p
+    opt_d = C.c_void_p  # nullable double*
+    lib.oracle_create.restype = vp
+    lib.oracle_create.argtypes = [C.c_int, _D, C.c_int, _I, _I, C.c_int, _I, _I, _D, C.c_int,
+                                  _I, _D, opt_d, opt_d, opt_d, opt_d, opt_d, _D]
+    lib.oracle_destroy.argtypes = [vp]
+    lib.oracle_step.argtypes = [vp, C.c_int]
+    lib.oracle_step.restype = C.c_int
+    for name in ("oracle_dt", "oracle_residual", "oracle_moment_defect", "oracle_mass"):
+        getattr(lib, name).argtypes = [vp]
+        getattr(lib, name).restype = C.c_double
+    lib.oracle_dt_cells.argtypes = [vp, _D]
+    lib.oracle_n_cells.argtypes = [vp]
+    lib.oracle_n_cells.restype = C.c_int
+    lib.oracle_get_f.argtypes = [vp, _D]
+    lib.oracle_set_f.argtypes = [vp, _D]
+    lib.oracle_get_fields.argtypes = [vp, _D, _D, _D, _D, _D, _D]
+    lib.oracle_geometry.argtypes = [vp, _D, _D, _D, _D]
+    lib.oracle_forces.argtypes = [vp, _D, opt_d, opt_d, opt_d]
+
+
+def _load_cs():
+    global _lib_cs
+    with _lock:
+        if _lib_cs is not None:
+            return _lib_cs
+        lib = C.CDLL(build(complex_step=True))
+        _common(lib)
+        lib.oracle_cs_seed.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double]
+        lib.oracle_cs_forces.argtypes = [C.c_void_p, C.c_double, _D, _D]
+        _lib_cs = lib
+        return lib
 
 
 def _load():
@@ -44,28 +84,11 @@ def _load():
         if _lib is not None:
             return _lib
         lib = C.CDLL(build())
+        _common(lib)
         vp = C.c_void_p
-        opt_d = C.c_void_p  # nullable double*
-        lib.oracle_create.restype = vp
-        lib.oracle_create.argtypes = [C.c_int, _D, C.c_int, _I, _I, C.c_int, _I, _I, _D, C.c_int,
-                                      _I, _D, opt_d, opt_d, opt_d, opt_d, opt_d, _D]
-        lib.oracle_destroy.argtypes = [vp]
-        lib.oracle_step.argtypes = [vp, C.c_int]
-        lib.oracle_step.restype = C.c_int
-        for name in ("oracle_dt", "oracle_residual", "oracle_moment_defect", "oracle_mass"):
-            getattr(lib, name).argtypes = [vp]
-            getattr(lib, name).restype = C.c_double
-        lib.oracle_dt_cells.argtypes = [vp, _D]
         lib.oracle_limiter.argtypes = [vp, _D, _D, _D]
-        lib.oracle_n_cells.argtypes = [vp]
-        lib.oracle_n_cells.restype = C.c_int
-        lib.oracle_get_f.argtypes = [vp, _D]
-        lib.oracle_set_f.argtypes = [vp, _D]
-        lib.oracle_get_fields.argtypes = [vp, _D, _D, _D, _D, _D, _D]
-        lib.oracle_geometry.argtypes = [vp, _D, _D, _D, _D]
         lib.oracle_gradient.argtypes = [vp, _D, _D, _D]
         lib.oracle_convection.argtypes = [vp, _D, _D]
-        lib.oracle_forces.argtypes = [vp, _D, opt_d, opt_d, opt_d]
         lib.oracle_feq.argtypes = [C.c_double, C.c_double, C.c_double, _D]
         lib.oracle_sst_point.argtypes = [C.c_double] * 9 + [_D]
         _lib = lib
@@ -93,8 +116,8 @@ class Oracle:
     f is cell-major [n_cells, 9]."""
 
     def __init__(self, case, dt: float | None = None, sst: bool | None = None,
-                 scheme: int = 0):
-        lib = _load()
+                 scheme: int = 0, complex_step: bool = False):
+        lib = _load_cs() if complex_step else _load()
         m = case.mesh.normalized()
         rho, u, v, k, w = case.init_arrays()
         self._keep = (m, rho, u, v, k, w)
@@ -180,6 +203,20 @@ class Oracle:
         ga = np.zeros(self.n_cells * Q)
         self.lib.oracle_convection(self._h, np.ascontiguousarray(f, np.float64).ravel(), ga)
         return ga.reshape(self.n_cells, Q)
+
+    def cs_seed(self, dbedge_val=None, df=None, h: float = 1e-30) -> None:
+        """Complex-step build only: seed d(boundary values) [n_bedges, 5] and / or df [n_cells, 9]
+        as imaginary parts h * d."""
+        bv = None if dbedge_val is None else np.ascontiguousarray(dbedge_val, np.float64)
+        f = None if df is None else np.ascontiguousarray(df, np.float64)
+        self.lib.oracle_cs_seed(self._h, _ptr(bv), _ptr(f), float(h))
+
+    def cs_forces(self, h: float = 1e-30):
+        """Complex-step build only: (forces, d forces / dp along the seeded direction)."""
+        val, der = np.zeros(4), np.zeros(4)
+        self.lib.oracle_cs_forces(self._h, float(h), val, der)
+        keys = ("fx", "fy", "cd", "cl")
+        return dict(zip(keys, val)), dict(zip(keys, der))
 
     def forces(self, per_edge: bool = False):
         """Total wall force and C_D, C_L; with ``per_edge`` also Cp and the force per edge."""

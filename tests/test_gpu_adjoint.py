@@ -486,3 +486,37 @@ def test_adjoint_instance_of_a_batch_equals_single_handle():
         for x, y in zip(got[1:], ref[1:]):
             np.testing.assert_allclose(x, y, rtol=1e-10, atol=1e-12 * np.abs(y).max())
     b.close()
+
+
+# ------------------------------------------------------------------ against the oracle's tangent
+@pytest.mark.parametrize("name", ["cavity", "bfs_sst", "naca_sst"])
+def test_adjoint_against_oracle_complex_step_tangent(name):
+    """The oracle's own tangent: its source compiled in complex arithmetic (complex-step method,
+    no GPU code, no differences taken) along a random seed of f^0 and of the boundary values,
+    against the adjoint's inner product with the same seed, on tiny meshes.  The initial
+    k / omega fields are uniform, so the SST limiters start at exact ties; both sides take the
+    branch of the first argument there (finite differences, which average the two one-sided
+    derivatives, cannot be used at this point)."""
+    case = {"cavity": lambda: mg.cavity_quad(12, re=400.0, jitter=0.2, seed=7),
+            "bfs_sst": lambda: mg.bfs_hybrid(n_target=800),
+            "naca_sst": lambda: mg.naca0012_cmesh(n_target=800, alpha_deg=3.0)}[name]()
+    m = case.mesh.normalized()
+    rng = np.random.default_rng(3)
+    n = 10
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    f0 = s.get_f()
+    g = 1e-3 * rng.standard_normal(f0.shape)
+    d = np.zeros((m.n_bedges, 5))
+    d[:, :3] = 1e-2 * rng.standard_normal((m.n_bedges, 3))
+    d[:, 3:] = 1e-3 * m.bedge_val[:, 3:] * rng.standard_normal((m.n_bedges, 2))
+    J, dJdf, dJdb, _ = s.adjoint(n, *W)
+    s.close()
+    o = Oracle(case, complex_step=True)
+    o.cs_seed(d, g)
+    o.step(n)
+    val, der = o.cs_forces()
+    Jo = W[0] * val["cd"] + W[1] * val["cl"]
+    dJo = W[0] * der["cd"] + W[1] * der["cl"]
+    adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
+    assert abs(J - Jo) <= 1e-10 * abs(Jo)
+    assert abs(adj - dJo) <= 1e-8 * abs(dJo), (adj, dJo)

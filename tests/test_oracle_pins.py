@@ -545,3 +545,50 @@ def test_production_limiter_variant_homogeneous_shear():
         o.step(1)
         kn = o.fields()["k"][inner]
         np.testing.assert_allclose(kn, (k0 + dt * P) / (1 + dt * 0.09 * w0), rtol=1e-12)
+
+
+# ------------------------------------------------------------------ the oracle's own tangent
+@pytest.mark.parametrize("sst", [False, True])
+def test_complex_step_build_real_parts_equal_the_oracle(sst):
+    """The complex-step build (the same source in complex arithmetic) carries in its real parts
+    exactly the double oracle's values, seeded or not (the seed is O(h^2) = 1e-60 in the real
+    parts)."""
+    case = mg.naca0012_cmesh(n_target=600, alpha_deg=3.0) if sst else \
+        mg.cavity_quad(10, re=400.0, jitter=0.2, seed=7)
+    m = case.mesh.normalized()
+    ref = Oracle(case)
+    ref.step(6)
+    cs = Oracle(case, complex_step=True)
+    rng = np.random.default_rng(1)
+    cs.cs_seed(rng.standard_normal((m.n_bedges, 5)), rng.standard_normal((m.n_cells, 9)))
+    cs.step(6)
+    np.testing.assert_array_equal(cs.get_f(), ref.get_f())
+    val, _ = cs.cs_forces()
+    assert val == {k: ref.forces()[k] for k in ("fx", "fy", "cd", "cl")}
+
+
+def test_complex_step_tangent_against_central_differences():
+    """Laminar cavity, random seed of f^0 and of the boundary values: the complex-step
+    derivative of the wall force after 10 steps against central differences of the double
+    oracle (the laminar step has no branch that the perturbation crosses)."""
+    case = mg.cavity_quad(12, re=400.0, jitter=0.2, seed=7)
+    m = case.mesh.normalized()
+    rng = np.random.default_rng(3)
+    f0 = Oracle(case).get_f()
+    g = 1e-3 * rng.standard_normal(f0.shape)
+    d = np.zeros((m.n_bedges, 5))
+    d[:, :3] = 1e-2 * rng.standard_normal((m.n_bedges, 3))
+    cs = Oracle(case, complex_step=True)
+    cs.cs_seed(d, g)
+    cs.step(10)
+    _, der = cs.cs_forces()
+    h, out = 1e-6, []
+    for sgn in (1.0, -1.0):
+        c = dataclasses.replace(case, mesh=dataclasses.replace(m, bedge_val=m.bedge_val + sgn * h * d))
+        o = Oracle(c)
+        o.set_f(f0 + sgn * h * g)
+        o.step(10)
+        out.append(o.forces())
+    for key in ("fx", "fy"):
+        fd = (out[0][key] - out[1][key]) / (2 * h)
+        assert abs(der[key] - fd) <= 1e-6 * abs(fd), (key, der[key], fd)
