@@ -1,19 +1,20 @@
-// fvlbm_adjoint.cuh -- discrete adjoint (reverse mode) of the laminar FP64 time step, included
-// into fvlbm_kernels.cu after the handle and its helpers.
+// fvlbm_adjoint.cuh -- discrete adjoint (reverse mode) of the FP64 time step, included into
+// fvlbm_kernels.cu after the handle and its helpers.
 //
 // The map differentiated is the two-pass IMEX step exactly as the library runs it (Sec. 3.2,
-// Steps 2-7 without Step 1): f^(1) = R(f^n) (Eq. (fnewstage), J = 1), three gradient + flux
+// Steps 1-7): on SST instances the k-omega SST solve first (its reverse is in
+// fvlbm_adjoint_sst.cuh), then f^(1) = R(f^n) (Eq. (fnewstage), J = 1), three gradient + flux
 // evaluations (Step 2, Eq. (advection)) and the stage algebra of the two accumulators.  Per step
 //   s1 = R(f0);  a1 = A(s1);  (f2, B, C) = S1(f0, a1);  a2 = A(f2);  f3 = S2(B - dt/2 a2);
 //   C' = C + dt/6 a2;  a3 = A(f3);  f^{n+1} = f3 + C' - dt/3 a3,
 // with A(f) = sum over faces of (e . n dl / A) times the upwind linear face value built from
-// the least-squares gradient, boundary faces taking the boundary values of Part I.  The adjoint
-// runs these in reverse: the linear flux and gradient operators are transposed by gathering
-// over each cell's faces (the neighbour's view of a shared face comes from its back slot); the
-// per-cell maps R, S1, S2 and the boundary values are transposed in closed form (they are affine
-// but for f^eq, whose transposed Jacobian is written out below).
-// The stage values of whole segments of steps stay in device memory (see adjoint_impl for the
-// plan): with room for all steps the forward steps run once, else twice.
+// the least-squares gradient, boundary faces taking the boundary values of Part I, and R, S1,
+// S2 relaxing with the step's tau.  The adjoint runs these in reverse: the linear flux and
+// gradient operators are transposed by gathering over each cell's faces (the neighbour's view
+// of a shared face comes from its back slot); the per-cell maps R, S1, S2 and the boundary
+// values are transposed in closed form (they are affine but for f^eq, whose transposed Jacobian
+// is written out below).  Stage values stay in device memory for whole runs of steps, and
+// longer runs are reversed on a binomial checkpoint schedule (see adjoint_impl).
 
 #include <functional>
 
