@@ -20,8 +20,8 @@ Two backward passes compute the same derivatives of the discrete step:
     J_w = grad_output . (C_L, C_D) gives dJ_w/d(boundary values) and dJ_w/d(node positions);
     the gradient is their projection on the parameters plus the explicit dependence of the drag
     and lift directions on alpha.  Its cost does not grow with the number of parameters.  It
-    needs the default reading (variant 0).
-The default ("auto") takes the adjoint for the default reading and the tangent otherwise.
+    covers reading variants 0, 2 and 8.
+The default ("auto") takes the adjoint unless the case uses reading variant 1 or 4.
 """
 from __future__ import annotations
 
@@ -41,9 +41,9 @@ class AirfoilForces:
     def __init__(self, base_case, wall_nodes, steps: int, device: int = 0, mode: str = "auto"):
         if mode not in ("auto", "tangent", "adjoint"):
             raise ValueError(f"unknown backward mode {mode!r}")
-        reading = int(getattr(base_case, "variant", 0))
+        reading = int(getattr(base_case, "variant", 0)) & 5   # variants the adjoint lacks
         if mode == "adjoint" and reading:
-            raise ValueError("the adjoint backward needs the default reading (variant 0)")
+            raise ValueError("the adjoint backward does not cover reading variants 1 and 4")
         if mode == "auto":
             mode = "tangent" if reading else "adjoint"
         self.mode = mode

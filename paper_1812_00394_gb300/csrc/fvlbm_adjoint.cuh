@@ -586,8 +586,12 @@ void adj_forward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in,
     if (h->sst) {
         const CompactGeo<double> CG{nullptr, nullptr};
         k_sst_grad<double, false><<<grid, block, 0, s>>>(in.mac, in.k, in.w, S.sg, S.f1, G, CG);
-        k_sst_update<double, false, false><<<grid, block, 0, s>>>(in.mac, in.k, in.w, in.nt, S.sg, S.f1, out.k,
-                                                                  out.w, out.nt, S.tau, G, nullptr, nullptr, CG);
+        if (h->nonorth)  // reading variants 2 / 8 compiled in
+            k_sst_update<double, false, true><<<grid, block, 0, s>>>(in.mac, in.k, in.w, in.nt, S.sg, S.f1, out.k,
+                                                                     out.w, out.nt, S.tau, G, nullptr, nullptr, CG);
+        else
+            k_sst_update<double, false, false><<<grid, block, 0, s>>>(in.mac, in.k, in.w, in.nt, S.sg, S.f1, out.k,
+                                                                      out.w, out.nt, S.tau, G, nullptr, nullptr, CG);
         tau = S.tau;
         mac_out = out.mac;
     }
@@ -660,8 +664,7 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in
 int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
                  double *dJ_dbedge, double *dJ_dxy) {
     if (!h || instance < 0 || instance >= h->ninst || n_steps < 0 || !w) return FVLBM_ERR_BAD_PARAM;
-    if (h->precision != FVLBM_FP64 || h->scheme != 0 || h->limit_f || h->per_stage ||
-        h->nonorth || h->d_back == nullptr)
+    if (h->precision != FVLBM_FP64 || h->scheme != 0 || h->limit_f || h->per_stage || h->d_back == nullptr)
         return FVLBM_ERR_NOT_SUPPORTED;
     const InstInfo &I = h->inst[instance];
     if (dJ_dxy && (!I.mesh || !I.mesh->ppairs.empty())) return FVLBM_ERR_NOT_SUPPORTED;

@@ -38,10 +38,80 @@ struct AdjGeo {
     double *sn, *rown, *rnbr, *lsq, *dinv, *wd;
 };
 
+// Reverse of the non-orthogonal correction of face m: l_dkn, l_dwn (adjoints of the face's
+// normal derivatives) to the own gradients l_g, the neighbour's gradients (lf[10..13]) and the
+// face geometry.
+__device__ __forceinline__ void sst_face_correction_T(const SstFace<double> &f, const double *g, double dla,
+                                                      double l_dkn, double l_dwn, double *l_g, double *lf,
+                                                      const AdjGeo &AG, int m, size_t np, int i) {
+    double ax, ay, l_tx, l_ty;
+    if (!f.bnd) {
+        ax = f.rox - f.rnx;
+        ay = f.roy - f.rny;
+        const double tx = f.snx / dla - ax * f.dinv, ty = f.sny / dla - ay * f.dinv;
+        l_g[4] += 0.5 * l_dkn * tx;
+        l_g[5] += 0.5 * l_dkn * ty;
+        l_g[6] += 0.5 * l_dwn * tx;
+        l_g[7] += 0.5 * l_dwn * ty;
+        lf[10] += 0.5 * l_dkn * tx;
+        lf[11] += 0.5 * l_dkn * ty;
+        lf[12] += 0.5 * l_dwn * tx;
+        lf[13] += 0.5 * l_dwn * ty;
+        l_tx = 0.5 * (l_dkn * (g[4] + f.gn[0]) + l_dwn * (g[6] + f.gn[2]));
+        l_ty = 0.5 * (l_dkn * (g[5] + f.gn[1]) + l_dwn * (g[7] + f.gn[3]));
+    } else {
+        ax = f.rox;
+        ay = f.roy;
+        const double tx = f.snx / dla - ax * f.dinv, ty = f.sny / dla - ay * f.dinv;
+        l_g[4] += l_dkn * tx;
+        l_g[5] += l_dkn * ty;
+        l_g[6] += l_dwn * tx;
+        l_g[7] += l_dwn * ty;
+        l_tx = l_dkn * g[4] + l_dwn * g[6];
+        l_ty = l_dkn * g[5] + l_dwn * g[7];
+    }
+    if (AG.sn != nullptr) {  // t = n dl/A / |n dl/A| - a / |d|
+        const double d3 = dla * dla * dla;
+        AG.sn[(2 * m) * np + i] += l_tx * (1.0 / dla - f.snx * f.snx / d3) - l_ty * f.snx * f.sny / d3;
+        AG.sn[(2 * m + 1) * np + i] += -l_tx * f.snx * f.sny / d3 + l_ty * (1.0 / dla - f.sny * f.sny / d3);
+        AG.rown[(2 * m) * np + i] -= l_tx * f.dinv;
+        AG.rown[(2 * m + 1) * np + i] -= l_ty * f.dinv;
+        if (!f.bnd) {
+            AG.rnbr[(2 * m) * np + i] += l_tx * f.dinv;
+            AG.rnbr[(2 * m + 1) * np + i] += l_ty * f.dinv;
+        }
+        AG.dinv[m * np + i] -= l_tx * ax + l_ty * ay;
+    }
+}
+
 // Per-face buffer layout: value c of face slot m of cell i at buf[(c * 4 + m) * np + i].
-// Update buffer (10 values): adjoints of the neighbour's u, v, k, omega, limited gradients (4),
-// f1, nu_t.  Gradient buffer (4 values): adjoints of the neighbour's u, v, k, omega.
-constexpr int kSstFU = 10, kSstFG = 4;
+// Update buffer (14 values): adjoints of the neighbour's u, v, k, omega, limited gradients (4),
+// f1, nu_t and (non-orthogonal correction, reading variant 2) its k / omega gradients (4).
+// Gradient buffer (4 values): adjoints of the neighbour's u, v, k, omega.
+constexpr int kSstFU = 14, kSstFG = 4;
+
+// Normal derivatives of k and omega on one face as sst_cell_update forms them: the two-point
+// difference and, under reading variant 2, the non-orthogonal correction with the mean (interior)
+// or own (boundary) gradient along n - d/|d|.
+__device__ __forceinline__ void sst_face_normal_gradients(const SstFace<double> &f, const double *g, double ki,
+                                                          double wi, double dla, bool nonorth, double &dkn,
+                                                          double &dwn) {
+    dkn = (f.k - ki) * f.dinv;
+    dwn = (f.w - wi) * f.dinv;
+    if (!nonorth) return;
+    if (!f.bnd) {
+        const double tx = f.snx / dla - (f.rox - f.rnx) * f.dinv;
+        const double ty = f.sny / dla - (f.roy - f.rny) * f.dinv;
+        dkn += 0.5 * ((g[4] + f.gn[0]) * tx + (g[5] + f.gn[1]) * ty);
+        dwn += 0.5 * ((g[6] + f.gn[2]) * tx + (g[7] + f.gn[3]) * ty);
+    } else {
+        const double tx = f.snx / dla - f.rox * f.dinv, ty = f.sny / dla - f.roy * f.dinv;
+        dkn += g[4] * tx + g[5] * ty;
+        dwn += g[6] * tx + g[7] * ty;
+    }
+}
+
+
 // Own adjoints after the update: u, v, k, omega, nu_t, g[8], lg[4], f1 (18 values, [18][np]).
 constexpr int kSstOwn = 18;
 
@@ -60,6 +130,7 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
     const double nu = P.nu, dt = cell_dt(G, P, i);
     const double ui = mac[np + i], vi = mac[2 * np + i], ki = kk[i], wi = ww[i], nti = nut[i];
     const double di = G.wdist[i], f1 = f1a[i];
+    const bool nonorth = (P.variant & 2) != 0;
     double g[8], lgi[4];
 #pragma unroll
     for (int c = 0; c < 8; ++c) g[c] = grads[c * np + i];
@@ -90,6 +161,8 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
             f.rny = G.rnbr[(2 * m + 1) * np + i];
 #pragma unroll
             for (int c = 0; c < 4; ++c) f.lg[c] = grads[(8 + c) * np + nb];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) f.gn[c] = grads[(4 + c) * np + nb];
             f.f1 = f1a[nb];
             f.nut = nut[nb];
         } else {
@@ -98,6 +171,8 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
         const double kin = ki + lgi[0] * f.rox + lgi[1] * f.roy;
         const double win = wi + lgi[2] * f.rox + lgi[3] * f.roy;
         const double dla = sqrt(f.snx * f.snx + f.sny * f.sny);
+        double dkn, dwn;
+        sst_face_normal_gradients(f, g, ki, wi, dla, nonorth, dkn, dwn);
         if (!f.bnd) {
             const double un = 0.5 * (ui + f.u) * f.snx + 0.5 * (vi + f.v) * f.sny;
             const double kup = un >= 0.0 ? kin : f.k + f.lg[0] * f.rnx + f.lg[1] * f.rny;
@@ -106,14 +181,14 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
             const double swj = f.f1 * kSw1 + (1.0 - f.f1) * kSw2;
             ck += un * kup;
             cw += un * wup;
-            dk += 0.5 * ((nu + sk_i * nti) + (nu + skj * f.nut)) * ((f.k - ki) * f.dinv) * dla;
-            dw += 0.5 * ((nu + sw_i * nti) + (nu + swj * f.nut)) * ((f.w - wi) * f.dinv) * dla;
+            dk += 0.5 * ((nu + sk_i * nti) + (nu + skj * f.nut)) * dkn * dla;
+            dw += 0.5 * ((nu + sw_i * nti) + (nu + swj * f.nut)) * dwn * dla;
         } else {
             const double un = f.u * f.snx + f.v * f.sny;
             ck += un * (un >= 0.0 ? kin : f.k);
             cw += un * (un >= 0.0 ? win : f.w);
-            dk += (nu + sk_i * nti) * ((f.k - ki) * f.dinv) * dla;
-            dw += (nu + sw_i * nti) * ((f.w - wi) * f.dinv) * dla;
+            dk += (nu + sk_i * nti) * dkn * dla;
+            dw += (nu + sw_i * nti) * dwn * dla;
         }
     }
     const double s11 = g[0], s22 = g[3], s12 = 0.5 * (g[1] + g[2]);
@@ -124,7 +199,10 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
     const double cw2 = kB2 / kBstar - kSw2 * kKappa * kKappa / 0.3;
     const double gam = f1 * cw1 + (1.0 - f1) * cw2;
     const double Q = 2.0 * SS - (2.0 / 3.0) * dv * dv;
-    const double pk = nti * Q - (2.0 / 3.0) * ki * dv;
+    const double pk0 = nti * Q - (2.0 / 3.0) * ki * dv;
+    const double cap = 10.0 * kBstar * wi * ki;  // production limiter (reading variant 8)
+    const bool capped = (P.variant & 8) && pk0 > cap;
+    const double pk = capped ? cap : pk0;
     double pw = gam * Q;
     if (nti > 0.0) pw -= (2.0 / 3.0) * gam * ki * dv / nti;
     const double G46 = g[4] * g[6] + g[5] * g[7];
@@ -197,10 +275,15 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
         l_dv -= l_pw * (2.0 / 3.0) * gam * ki / nti;
         l_nti += l_pw * t / nti;
     }
-    l_nti += l_pk * Q;
-    l_Q += l_pk * nti;
-    l_dv -= l_pk * (2.0 / 3.0) * ki;
-    l_ki -= l_pk * (2.0 / 3.0) * dv;
+    const double l_pk0 = capped ? 0.0 : l_pk;
+    if (capped) {
+        l_wi += l_pk * 10.0 * kBstar * ki;
+        l_ki += l_pk * 10.0 * kBstar * wi;
+    }
+    l_nti += l_pk0 * Q;
+    l_Q += l_pk0 * nti;
+    l_dv -= l_pk0 * (2.0 / 3.0) * ki;
+    l_ki -= l_pk0 * (2.0 / 3.0) * dv;
     l_f1 += l_gam * (cw1 - cw2);
     double l_SS = 2.0 * l_Q;
     l_dv -= l_Q * (4.0 / 3.0) * dv;
@@ -218,7 +301,9 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
         const double win = wi + lgi[2] * f.rox + lgi[3] * f.roy;
         const double dla = sqrt(f.snx * f.snx + f.sny * f.sny);
         double l_kin = 0, l_win = 0;
-        double lf[kSstFU] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // u, v, k, w, lg0..3, f1, nut
+        double lf[kSstFU] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // u v k w, lg0..3, f1, nut, gn0..3
+        double dkn, dwn;
+        sst_face_normal_gradients(f, g, ki, wi, dla, nonorth, dkn, dwn);
         if (!f.bnd) {
             const double un = 0.5 * (ui + f.u) * f.snx + 0.5 * (vi + f.v) * f.sny;
             const bool up = un >= 0.0;
@@ -228,11 +313,11 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
             const double swj = f.f1 * kSw1 + (1.0 - f.f1) * kSw2;
             const double gkf = 0.5 * ((nu + sk_i * nti) + (nu + skj * f.nut));
             const double gwf = 0.5 * ((nu + sw_i * nti) + (nu + swj * f.nut));
-            const double dkn = (f.k - ki) * f.dinv, dwn = (f.w - wi) * f.dinv;
             const double l_un = l_ck * kup + l_cw * wup;
             const double l_kup = l_ck * un, l_wup = l_cw * un;
             const double l_gkf = l_dk * dkn * dla, l_gwf = l_dw * dwn * dla;
             const double l_dkn = l_dk * gkf * dla, l_dwn = l_dw * gwf * dla;
+            if (nonorth) sst_face_correction_T(f, g, dla, l_dkn, l_dwn, l_g, lf, AG, m, np, i);
             if (AG.sn != nullptr) {  // geometry: n dl / A (through u.n and dl/A), r_nbr, 1/|d|
                 const double l_dla = l_dk * gkf * dkn + l_dw * gwf * dwn;
                 AG.sn[(2 * m) * np + i] += l_un * 0.5 * (ui + f.u) + l_dla * f.snx / dla;
@@ -271,7 +356,6 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
             const double un = f.u * f.snx + f.v * f.sny;
             const bool up = un >= 0.0;
             const double kup = up ? kin : f.k, wup = up ? win : f.w;
-            const double dkn = (f.k - ki) * f.dinv, dwn = (f.w - wi) * f.dinv;
             const double l_un = l_ck * kup + l_cw * wup;
             if (up) {
                 l_kin += l_ck * un;
@@ -293,6 +377,7 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_update(
             l_sw += l_dw * nti * dwn * dla;
             l_nti += (l_dk * sk_i * dkn + l_dw * sw_i * dwn) * dla;
             const double l_dkn = l_dk * (nu + sk_i * nti) * dla, l_dwn = l_dw * (nu + sw_i * nti) * dla;
+            if (nonorth) sst_face_correction_T(f, g, dla, l_dkn, l_dwn, l_g, lf, AG, m, np, i);
             lf[2] += l_dkn * f.dinv;
             l_ki -= l_dkn * f.dinv;
             lf[3] += l_dwn * f.dinv;
@@ -381,6 +466,8 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_grad(
 #pragma unroll
             for (int c = 0; c < 4; ++c) l_lg[c] += fbu[((4 + c) * 4 + b) * np + nb];
             l_f1 += fbu[(8 * 4 + b) * np + nb];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) l_g[4 + c] += fbu[((10 + c) * 4 + b) * np + nb];
         } else {
             sst_bvals(G, -nb - 1, nu, ow[0], ow[1], ow[2], ow[3], di, q[m][0], q[m][1], q[m][2], q[m][3]);
         }

@@ -212,7 +212,7 @@ def test_adjoint_rejects_unsupported_handles():
         s.adjoint(-1, 1.0, 0.0)
     assert e.value.code == fvlbm.FVLBM_ERR_BAD_PARAM
     s.close()
-    var = fvlbm.Solver(dataclasses.replace(sst, variant=2), precision=FP64, device=0)
+    var = fvlbm.Solver(dataclasses.replace(sst, variant=4), precision=FP64, device=0)
     with pytest.raises(fvlbm.FvlbmError) as e:
         var.adjoint(3, 1.0, 0.0)
     assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
@@ -520,3 +520,31 @@ def test_adjoint_against_oracle_complex_step_tangent(name):
     adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
     assert abs(J - Jo) <= 1e-10 * abs(Jo)
     assert abs(adj - dJo) <= 1e-8 * abs(dJo), (adj, dJo)
+
+
+@pytest.mark.parametrize("variant", [2, 8, 10])
+def test_adjoint_sst_reading_variants_against_tangent(variant):
+    """SST reading variants 2 (non-orthogonal correction of the diffusion, with the neighbours'
+    gradients) and 8 (production limiter): the dot-product identity of the adjoint against the
+    tangent, for seeds of f^0 and the boundary values and for a random node displacement."""
+    case = dataclasses.replace(_bfs_sst(), variant=variant)
+    warm, n = 8, 6
+    g, d = _sst_seeds(case, np.random.default_rng(500 + variant))
+    m = case.mesh.normalized()
+    v = 1e-3 * np.random.default_rng(600 + variant).standard_normal((m.n_nodes, 2))
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    s.step(warm)
+    J, dJdf, dJdb, dxy = s.adjoint(n, *W, shape=True)
+    s.close()
+    Jt, dJt = _tangent_dJ(case, warm, n, g, d)
+    adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
+    assert abs(J - Jt) <= 1e-10 * abs(Jt)
+    assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)
+    t = fvlbm.Solver(case, precision=TAN, device=0)
+    t.step(warm)
+    t.tangent_seed_nodes(v)
+    t.step(n)
+    _, dv = t.forces_tangent(dalpha=0.0)
+    t.close()
+    dJv = W[0] * dv["cd"] + W[1] * dv["cl"]
+    assert abs(float(np.sum(dxy * v)) - dJv) <= 1e-8 * abs(dJv), (float(np.sum(dxy * v)), dJv)
