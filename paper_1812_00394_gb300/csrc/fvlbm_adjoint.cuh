@@ -197,7 +197,8 @@ __global__ void __launch_bounds__(kTile) k_adj_fluxT(const double *__restrict__ 
 // ---- transposed gradient, linear part: lf += (d g / d f)^T lg with the boundary values held
 // fixed (g_j = sum_m W_m (f_m - f_j)); their dependence on f_j is added by k_adj_bndT
 __global__ void __launch_bounds__(kTile) k_adj_gradT(const double *__restrict__ lg, double *__restrict__ lf,
-                                                     Geo<double> G, const int *__restrict__ back) {
+                                                     Geo<double> G, const int *__restrict__ back,
+                                                     const double *__restrict__ lnb) {
     const int j = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     double lfj[kQ], lgx[kQ], lgy[kQ];
@@ -219,10 +220,112 @@ __global__ void __launch_bounds__(kTile) k_adj_gradT(const double *__restrict__ 
 #pragma unroll
             for (int a = 0; a < kQ; ++a)
                 lfj[a] += wix * lg[(2 * a) * np + nb] + wiy * lg[(2 * a + 1) * np + nb];
+            if (lnb != nullptr)  // the neighbour's limiter took this cell's value as its extreme
+                for (int a = 1; a < kQ; ++a) lfj[a] += lnb[(a * 4 + b) * np + nb];
         }
     }
 #pragma unroll
     for (int a = 0; a < kQ; ++a) lf[a * np + j] = lfj[a];
+}
+
+// ---- limiter on grad f (reading variant 1): the stage used g = phi g_raw with the
+// Venkatakrishnan factor phi = min over faces of r(d1, d2) (d2 = g_raw . r_m, d1 = the distance
+// from f_i to the max / min over the cell, its neighbours and its boundary values; e2 = A^(3/2)).
+// In: lg, the adjoint of the limited gradient.  Out: lg <- the adjoint of g_raw; lf_i gets the
+// adjoint of f_i through d1; the extreme's share goes to the per-face buffers, lnb[(a * 4 + m)
+// * np + i] for a neighbour (gathered by k_adj_gradT) and lbf for a boundary value (added by
+// k_adj_bndT).  Branches (extremes, the minimum over faces) follow the values, ties keeping the
+// first argument, as the forward's fmin / fmax.
+__global__ void __launch_bounds__(kTile) k_adj_limT(const double *__restrict__ fs, double *__restrict__ lg,
+                                                    double *__restrict__ lf, double *__restrict__ lnb,
+                                                    double *__restrict__ lbf, Geo<double> G) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
+    for (int c = 0; c < 4 * kQ; ++c) {
+        lnb[c * np + i] = 0.0;
+        lbf[c * np + i] = 0.0;
+    }
+    if (!(P.variant & 1)) return;
+    const double rho0 = P.rho0;
+    double fi[kQ], fbv[4][kQ];
+    load9(fs, np, i, fi);
+    bool has[4];
+    int nbs[4];
+    for (int m = 0; m < 4; ++m) {
+        nbs[m] = G.nbr[m * np + i];
+        has[m] = nbs[m] != kNone;
+        if (has[m] && nbs[m] < 0) {
+            const int b = -nbs[m] - 1;
+            double dr, r, u, v;
+            moments(fi, rho0, dr, r, u, v);
+            boundary_values(G.btype[b], G.bval + b, 0, G.nbt, G.sn[(2 * m) * np + i], G.sn[(2 * m + 1) * np + i],
+                            fi, dr, r, u, v, rho0, fbv[m]);
+        }
+    }
+    const double ar = G.area[i];
+    const double e2 = ar * sqrt(ar);
+    double lfi[kQ];
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) lfi[a] = lf[a * np + i];
+    for (int a = 1; a < kQ; ++a) {
+        // raw gradient and the extremes (index -1: the cell itself)
+        double gx = 0.0, gy = 0.0, lo = fi[a], hi = fi[a];
+        int ilo = -1, ihi = -1;
+        for (int m = 0; m < 4; ++m) {
+            if (!has[m]) continue;
+            const double fm = nbs[m] >= 0 ? fs[a * np + nbs[m]] : fbv[m][a];
+            const double d = fm - fi[a];
+            gx += G.lsq[(2 * m) * np + i] * d;
+            gy += G.lsq[(2 * m + 1) * np + i] * d;
+            if (fm < lo) { lo = fm; ilo = m; }
+            if (fm > hi) { hi = fm; ihi = m; }
+        }
+        double phi = 1.0, rsel_d1 = 0.0, rsel_d2 = 0.0;
+        int msel = -1;
+        bool upper = false;
+        for (int m = 0; m < 4; ++m) {
+            if (!has[m]) continue;
+            const double d2 = gx * G.rown[(2 * m) * np + i] + gy * G.rown[(2 * m + 1) * np + i];
+            if (d2 == 0.0) continue;
+            const double d1 = d2 > 0.0 ? hi - fi[a] : lo - fi[a];
+            const double r = ((d1 * d1 + e2) * d2 + 2.0 * d2 * d2 * d1) /
+                             (d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + e2) / d2;
+            if (r < phi) {
+                phi = r;
+                msel = m;
+                rsel_d1 = d1;
+                rsel_d2 = d2;
+                upper = d2 > 0.0;
+            }
+        }
+        const double lgx = lg[(2 * a) * np + i], lgy = lg[(2 * a + 1) * np + i];
+        const double l_phi = lgx * gx + lgy * gy;
+        double lrx = phi * lgx, lry = phi * lgy;
+        if (msel >= 0) {
+            const double d1 = rsel_d1, d2 = rsel_d2;
+            const double N = (d1 * d1 + e2) * d2 + 2.0 * d2 * d2 * d1;
+            const double D = d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + e2;
+            const double dr_d1 = ((2.0 * d1 * d2 + 2.0 * d2 * d2) * D - N * (2.0 * d1 + d2)) / (D * D * d2);
+            const double dr_d2 = ((d1 * d1 + e2 + 4.0 * d2 * d1) * D * d2 - N * ((4.0 * d2 + d1) * d2 + D)) /
+                                 (D * D * d2 * d2);
+            const double l_d1 = l_phi * dr_d1, l_d2 = l_phi * dr_d2;
+            lrx += l_d2 * G.rown[(2 * msel) * np + i];
+            lry += l_d2 * G.rown[(2 * msel + 1) * np + i];
+            const int e = upper ? ihi : ilo;  // d1 = f_ext - f_i; the cell itself gives 0
+            if (e >= 0) {
+                lfi[a] -= l_d1;
+                if (nbs[e] >= 0)
+                    lnb[(a * 4 + e) * np + i] += l_d1;
+                else
+                    lbf[(a * 4 + e) * np + i] += l_d1;
+            }
+        }
+        lg[(2 * a) * np + i] = lrx;
+        lg[(2 * a + 1) * np + i] = lry;
+    }
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) lf[a * np + i] = lfi[a];
 }
 
 // ---- boundary faces: the face value f_bc(f_j, bval) enters the flux (weight e.n) and the
@@ -230,7 +333,8 @@ __global__ void __launch_bounds__(kTile) k_adj_gradT(const double *__restrict__ 
 //   c = (e.n) la_j + W_m^T lg_j,  lf_j += (d f_bc / d f_j)^T c,  lbval += (d f_bc / d bval)^T c
 __global__ void __launch_bounds__(kTile) k_adj_bndT(const double *__restrict__ fs, const double *__restrict__ la,
                                                     const double *__restrict__ lg, double *__restrict__ lf,
-                                                    double *__restrict__ lbval, Geo<double> G) {
+                                                    double *__restrict__ lbval, Geo<double> G,
+                                                    const double *__restrict__ lbf) {
     const int j = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     int nbnd = 0;
@@ -256,7 +360,7 @@ __global__ void __launch_bounds__(kTile) k_adj_bndT(const double *__restrict__ f
 #pragma unroll
         for (int a = 0; a < kQ; ++a)
             c[a] = edot<double>(a, snx, sny) * la[a * np + j] + wx * lg[(2 * a) * np + j] +
-                   wy * lg[(2 * a + 1) * np + j];
+                   wy * lg[(2 * a + 1) * np + j] + (lbf != nullptr ? lbf[(a * 4 + m) * np + j] : 0.0);
         adj_bv3(G, bf, bv3);
         adj_bvals_T(G.btype[bf], bv3, snx, sny, fj, rho0, c, lfj, lb3);
         if (lbval != nullptr)
@@ -597,13 +701,13 @@ void adj_forward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in,
     }
     double *fin = in.f;
     k_stage1<double><<<grid, block, 0, s>>>(in.f, S.s1, tau, G);
-    k_grad<double, false><<<grid, block, 0, s>>>(S.s1, S.g1, G);
+    grad_f<double>(h, grid, block, s, S.s1, S.g1, G);
     k_flux_stage<double, 1, false><<<grid, block, 0, s>>>(S.s1, S.g1, S.f2, fin, S.B, S.C, tau, S.mac,
                                                           nullptr, G);
-    k_grad<double, false><<<grid, block, 0, s>>>(S.f2, S.g2, G);
+    grad_f<double>(h, grid, block, s, S.f2, S.g2, G);
     k_flux_stage<double, 2, false><<<grid, block, 0, s>>>(S.f2, S.g2, S.f3, fin, S.B, S.C, tau, S.mac,
                                                           nullptr, G);
-    k_grad<double, false><<<grid, block, 0, s>>>(S.f3, S.g3, G);
+    grad_f<double>(h, grid, block, s, S.f3, S.g3, G);
     k_flux_stage<double, 3, false><<<grid, block, 0, s>>>(S.f3, S.g3, nullptr, out.f, S.B, S.C, tau,
                                                           mac_out, nullptr, G);
 }
@@ -618,6 +722,7 @@ struct AdjVars {
     double *a_dinv = nullptr, *a_wd = nullptr;  // shape adjoint, SST only
     double *lk = nullptr, *lw = nullptr, *lnt = nullptr, *ltau = nullptr;  // SST
     double *own = nullptr, *fbu = nullptr, *fbg = nullptr;
+    double *lnb = nullptr, *lbf = nullptr;  // limiter on grad f (reading variant 1)
 };
 
 // Reverse of the step that went from state `in` (stage values S): L <- adjoint of f^n, and on
@@ -637,9 +742,10 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in
     // transpose of one flux + gradient evaluation at stage value fs (gradient g): la -> lf
     auto evalT = [&](const double *fs, const double *g, double *lf) {
         k_adj_fluxT<<<grid, block, 0, s>>>(A.la, lf, A.lg, G, back);
+        if (A.lnb) k_adj_limT<<<grid, block, 0, s>>>(fs, A.lg, lf, A.lnb, A.lbf, G);
         geom(fs, g);
-        k_adj_gradT<<<grid, block, 0, s>>>(A.lg, lf, G, back);
-        k_adj_bndT<<<grid, block, 0, s>>>(fs, A.la, A.lg, lf, A.lbval, G);
+        k_adj_gradT<<<grid, block, 0, s>>>(A.lg, lf, G, back, A.lnb);
+        k_adj_bndT<<<grid, block, 0, s>>>(fs, A.la, A.lg, lf, A.lbval, G, A.lbf);
     };
     k_adj_stage3<<<grid, block, 0, s>>>(A.L, A.lf3, A.lc, A.la, G);
     evalT(S.f3, S.g3, A.lf3);
@@ -664,10 +770,11 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in
 int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
                  double *dJ_dbedge, double *dJ_dxy) {
     if (!h || instance < 0 || instance >= h->ninst || n_steps < 0 || !w) return FVLBM_ERR_BAD_PARAM;
-    if (h->precision != FVLBM_FP64 || h->scheme != 0 || h->limit_f || h->per_stage || h->d_back == nullptr)
+    if (h->precision != FVLBM_FP64 || h->scheme != 0 || h->per_stage || h->d_back == nullptr)
         return FVLBM_ERR_NOT_SUPPORTED;
     const InstInfo &I = h->inst[instance];
-    if (dJ_dxy && (!I.mesh || !I.mesh->ppairs.empty())) return FVLBM_ERR_NOT_SUPPORTED;
+    // shape gradients: the limiter's dependence on the cell area is not transposed
+    if (dJ_dxy && (!I.mesh || !I.mesh->ppairs.empty() || h->limit_f)) return FVLBM_ERR_NOT_SUPPORTED;
     CK(cudaSetDevice(h->device));
     const Geo<double> G = geo_of<double>(h);
     const bool sst = h->sst;
@@ -755,6 +862,10 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
             A.own = M.get(kSstOwn * np);
             A.fbu = M.get(4 * kSstFU * np);
             A.fbg = M.get(4 * kSstFG * np);
+        }
+        if (h->limit_f) {
+            A.lnb = M.get(4 * kQ * np);
+            A.lbf = M.get(4 * kQ * np);
         }
         if (dJ_dxy) {
             A.a_sn = M.get(8 * np);

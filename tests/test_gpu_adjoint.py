@@ -548,3 +548,26 @@ def test_adjoint_sst_reading_variants_against_tangent(variant):
     t.close()
     dJv = W[0] * dv["cd"] + W[1] * dv["cl"]
     assert abs(float(np.sum(dxy * v)) - dJv) <= 1e-8 * abs(dJv), (float(np.sum(dxy * v)), dJv)
+
+
+@pytest.mark.parametrize("name,variant", [("naca_laminar", 1), ("bfs_sst", 1), ("bfs_sst", 11)])
+def test_adjoint_gradient_limiter_against_tangent(name, variant):
+    """Reading variant 1 (Venkatakrishnan limiter on grad f): the limiter's transpose (through
+    the selected face's factor, the raw gradient and the extreme among the cell, its neighbours
+    and its boundary values) against the tangent, for seeds of f^0 and of the boundary values;
+    with variants 2 and 8 on top on the SST step.  Shape gradients are not offered with it."""
+    base = _naca_laminar() if name == "naca_laminar" else _bfs_sst()
+    case = dataclasses.replace(base, variant=variant)
+    warm, n = 8, 6
+    g, d = _sst_seeds(case, np.random.default_rng(700 + variant))
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    s.step(warm)
+    J, dJdf, dJdb, _ = s.adjoint(n, *W)
+    with pytest.raises(fvlbm.FvlbmError) as e:
+        s.adjoint(n, *W, shape=True)
+    assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
+    s.close()
+    Jt, dJt = _tangent_dJ(case, warm, n, g, d)
+    adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
+    assert abs(J - Jt) <= 1e-10 * abs(Jt)
+    assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)
