@@ -20,7 +20,7 @@ Two backward passes compute the same derivatives of the discrete step:
     J_w = grad_output . (C_L, C_D) gives dJ_w/d(boundary values) and dJ_w/d(node positions);
     the gradient is their projection on the parameters plus the explicit dependence of the drag
     and lift directions on alpha.  Its cost does not grow with the number of parameters.  It
-    covers reading variants 1, 2 and 8 (with variant 1, no wall-node parameters).
+    covers every reading variant (with variant 1, no wall-node parameters).
 The default ("auto") takes the adjoint where it covers the case, and the tangent otherwise.
 """
 from __future__ import annotations
@@ -42,8 +42,8 @@ class AirfoilForces:
         if mode not in ("auto", "tangent", "adjoint"):
             raise ValueError(f"unknown backward mode {mode!r}")
         variant = int(getattr(base_case, "variant", 0))
-        # the adjoint lacks variant 4, and shape gradients under variant 1
-        reading = (variant & 4) or ((variant & 1) and len(wall_nodes) > 0)
+        # the adjoint lacks shape gradients under variant 1
+        reading = (variant & 1) and len(wall_nodes) > 0
         if mode == "adjoint" and reading:
             raise ValueError("the adjoint backward does not cover this reading variant")
         if mode == "auto":

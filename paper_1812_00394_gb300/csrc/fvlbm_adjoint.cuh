@@ -492,15 +492,18 @@ __global__ void __launch_bounds__(kTile) k_adj_stage2(const double *__restrict__
     }
 }
 
-// ---- stage 1: from lf2, lB, lc -> lf0 (=), la1.  Forward (z = dt/tau, zq = z/4, s = z/(1 + zq)):
+// ---- stage 1: from lf2, lB, lc -> lf0 (=), la1.  Forward (z = dt/tau, zq = z/4, s = z/(1 + zq);
+// s1 = s, or from tau1 under the per-stage SST reading):
 //   X = f0 - dt/2 a1,  f2 = (X + zq f^eq(X)) / (1 + zq),
-//   B = X + (s/3) [(f^eq(f0) - f0) + (f^eq(X) - X)],  C = dt/6 a1.
+//   B = X + (s1/3) (f^eq(f0) - f0) + (s/3) (f^eq(X) - X),  C = dt/6 a1.
+// ltau (and ltau1 when tau1 is given) receive the adjoints of the relaxation times (added).
 __global__ void __launch_bounds__(kTile) k_adj_stage1(const double *__restrict__ f0, const double *__restrict__ s1,
                                                       const double *__restrict__ g1, const double *__restrict__ tau,
                                                       const double *__restrict__ lf2, const double *__restrict__ lB,
                                                       const double *__restrict__ lc, double *__restrict__ lf0,
                                                       double *__restrict__ la, double *__restrict__ ltau,
-                                                      Geo<double> G) {
+                                                      Geo<double> G, const double *__restrict__ tau1,
+                                                      double *__restrict__ ltau1) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -510,7 +513,10 @@ __global__ void __launch_bounds__(kTile) k_adj_stage1(const double *__restrict__
     const double z = dt * (1.0 / tau[i]);
     const double zq = z * 0.25;
     const double inv = 1.0 / (1.0 + zq);
-    const double s3 = z * inv * (1.0 / 3.0);
+    const double s3 = z * inv * (1.0 / 3.0);  // the stage-2 collision term's share of B
+    const double z1 = tau1 != nullptr ? dt / tau1[i] : z;
+    const double inv1 = tau1 != nullptr ? 1.0 / (1.0 + 0.25 * z1) : inv;
+    const double s31 = tau1 != nullptr ? z1 * inv1 * (1.0 / 3.0) : s3;  // the stage-1 term's
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
         x0[a] = f0[a * np + i];
@@ -521,25 +527,32 @@ __global__ void __launch_bounds__(kTile) k_adj_stage1(const double *__restrict__
         mu[a] = zq * inv * l2 + s3 * lb[a];
     }
     if (ltau != nullptr) {
-        // z = dt/tau: d f2 / d z = (f^eq(X) - X) inv^2 / 4; B carries (s/3)(f^eq(f0) - f0 +
-        // f^eq(X) - X) with s = z inv, ds/dz = inv^2
-        double e1[kQ], e2[kQ], dr, r, u, v, l_z = 0.0;
+        // z = dt/tau: d f2 / d z = (f^eq(X) - X) inv^2 / 4; B carries (s/3)(f^eq(X) - X) and
+        // (s1/3)(f^eq(f0) - f0) with s = z inv, ds/dz = inv^2 (s1 likewise in z1)
+        double e1[kQ], e2[kQ], dr, r, u, v, l_z = 0.0, l_z1 = 0.0;
         moments(X, P.rho0, dr, r, u, v);
         feq_dev(dr, r, u, v, e2);
         moments(x0, P.rho0, dr, r, u, v);
         feq_dev(dr, r, u, v, e1);
 #pragma unroll
-        for (int a = 0; a < kQ; ++a)
-            l_z += lf2[a * np + i] * (e2[a] - X[a]) * 0.25 +
-                   lb[a] * (1.0 / 3.0) * (e1[a] - x0[a] + e2[a] - X[a]);
-        ltau[i] += -l_z * inv * inv * z / tau[i];
+        for (int a = 0; a < kQ; ++a) {
+            l_z += lf2[a * np + i] * (e2[a] - X[a]) * 0.25 + lb[a] * (1.0 / 3.0) * (e2[a] - X[a]);
+            l_z1 += lb[a] * (1.0 / 3.0) * (e1[a] - x0[a]);
+        }
+        const double lt = -l_z * inv * inv * z / tau[i];
+        if (tau1 != nullptr) {
+            ltau[i] += lt;
+            ltau1[i] += -l_z1 * inv1 * inv1 * z1 / tau1[i];
+        } else {
+            ltau[i] += lt - l_z1 * inv * inv * z / tau[i];
+        }
     }
     feq_vjp(X, P.rho0, mu, lX);
     double l0[kQ];
 #pragma unroll
     for (int a = 0; a < kQ; ++a) {
-        l0[a] = lX[a] - s3 * lb[a];
-        mu[a] = s3 * lb[a];
+        l0[a] = lX[a] - s31 * lb[a];
+        mu[a] = s31 * lb[a];
     }
     feq_vjp(x0, P.rho0, mu, l0);
 #pragma unroll
@@ -677,6 +690,11 @@ struct AdjState {
 struct AdjStep {
     double *s1, *g1, *f2, *g2, *B, *C, *f3, *g3, *mac;
     double *sg = nullptr, *f1 = nullptr, *tau = nullptr;
+    // per-stage SST reading: the solves before stages 1 and 2 (their gradients, f1, tau) and the
+    // macros of f^(1), f^(2) they read; the solve before stage 3 uses sg, f1, tau above
+    double *sgA = nullptr, *f1A = nullptr, *tauA = nullptr, *sgB = nullptr, *f1B = nullptr, *tauB = nullptr;
+    double *mac1 = nullptr, *mac2 = nullptr;
+    double *kS = nullptr, *wS = nullptr, *ntS = nullptr;  // discarded k, omega, nu_t of those solves
 };
 
 // One two-pass FP64 step from state `in` to state `out` (the launches of the two-pass path:
@@ -687,6 +705,38 @@ void adj_forward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in,
     cudaStream_t s = h->stream;
     const double *tau = static_cast<const double *>(h->tau);
     double *mac_out = S.mac;
+    auto solve = [&](const double *mac, double *sg, double *f1, double *ko, double *wo, double *nto,
+                     double *tau_out) {
+        const CompactGeo<double> CG{nullptr, nullptr};
+        k_sst_grad<double, false><<<grid, block, 0, s>>>(mac, in.k, in.w, sg, f1, G, CG);
+        if (h->nonorth)
+            k_sst_update<double, false, true><<<grid, block, 0, s>>>(mac, in.k, in.w, in.nt, sg, f1, ko, wo, nto,
+                                                                     tau_out, G, nullptr, nullptr, CG);
+        else
+            k_sst_update<double, false, false><<<grid, block, 0, s>>>(mac, in.k, in.w, in.nt, sg, f1, ko, wo, nto,
+                                                                      tau_out, G, nullptr, nullptr, CG);
+    };
+    if (h->per_stage) {
+        // the SST solved from t^n before every stage with the macros of f^n, f^(1), f^(2); stage 1
+        // relaxes with the first tau, its algebra takes the second for f^(2); the last solve
+        // gives the state of t^{n+1} and the tau of stages 2 and 3
+        solve(in.mac, S.sgA, S.f1A, S.kS, S.wS, S.ntS, S.tauA);
+        k_stage1<double><<<grid, block, 0, s>>>(in.f, S.s1, S.tauA, G);
+        k_stage_macros<double><<<grid, block, 0, s>>>(S.s1, S.mac1, G);
+        solve(S.mac1, S.sgB, S.f1B, S.kS, S.wS, S.ntS, S.tauB);
+        grad_f<double>(h, grid, block, s, S.s1, S.g1, G);
+        k_flux_stage<double, 1, false><<<grid, block, 0, s>>>(S.s1, S.g1, S.f2, in.f, S.B, S.C, S.tauB, S.mac,
+                                                              nullptr, G, S.tauA);
+        k_stage_macros<double><<<grid, block, 0, s>>>(S.f2, S.mac2, G);
+        solve(S.mac2, S.sg, S.f1, out.k, out.w, out.nt, S.tau);
+        grad_f<double>(h, grid, block, s, S.f2, S.g2, G);
+        k_flux_stage<double, 2, false><<<grid, block, 0, s>>>(S.f2, S.g2, S.f3, in.f, S.B, S.C, S.tau, S.mac,
+                                                              nullptr, G);
+        grad_f<double>(h, grid, block, s, S.f3, S.g3, G);
+        k_flux_stage<double, 3, false><<<grid, block, 0, s>>>(S.f3, S.g3, nullptr, out.f, S.B, S.C, S.tau,
+                                                              out.mac, nullptr, G);
+        return;
+    }
     if (h->sst) {
         const CompactGeo<double> CG{nullptr, nullptr};
         k_sst_grad<double, false><<<grid, block, 0, s>>>(in.mac, in.k, in.w, S.sg, S.f1, G, CG);
@@ -722,6 +772,9 @@ struct AdjVars {
     double *a_dinv = nullptr, *a_wd = nullptr;  // shape adjoint, SST only
     double *lk = nullptr, *lw = nullptr, *lnt = nullptr, *ltau = nullptr;  // SST
     double *own = nullptr, *fbu = nullptr, *fbg = nullptr;
+    // per-stage SST reading: the state adjoints of t^n as the three solves add them up, the
+    // adjoints of the first two relaxation times, and zeros for the discarded solve outputs
+    double *lkN = nullptr, *lwN = nullptr, *lntN = nullptr, *ltauA = nullptr, *ltauB = nullptr, *zero = nullptr;
     double *lnb = nullptr, *lbf = nullptr;  // limiter on grad f (reading variant 1)
 };
 
@@ -750,9 +803,42 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in
     k_adj_stage3<<<grid, block, 0, s>>>(A.L, A.lf3, A.lc, A.la, G);
     evalT(S.f3, S.g3, A.lf3);
     k_adj_stage2<<<grid, block, 0, s>>>(S.B, S.f2, S.g2, tau, A.lf3, A.lc, A.lB, A.la, A.ltau, G);
+    if (h->per_stage) {
+        const size_t nb1 = static_cast<size_t>(h->np) * sizeof(double);
+        const AdjGeo AG{A.a_sn, A.a_rown, A.a_rnbr, A.a_lsq, A.a_dinv, A.a_wd};
+        // reverse of one SST solve from t^n with macros of fs: outputs' adjoints (lk, lw, lnt,
+        // ltau) -> lf (through the macros) and the t^n state adjoints (lkN.. written or added)
+        auto solveT = [&](const double *mac, const double *sg, const double *f1, const double *lk,
+                          const double *lw, const double *lnt, const double *ltau, const double *fs, double *lf,
+                          bool add) {
+            k_adj_sst_update<<<grid, block, 0, s>>>(mac, in.k, in.w, in.nt, sg, f1, lk, lw, lnt, ltau, A.own, A.fbu,
+                                                    A.lbval, G, AG);
+            k_adj_sst_grad<<<grid, block, 0, s>>>(mac, in.k, in.w, sg, f1, A.fbu, A.own, A.fbg, A.lbval, G, back,
+                                                  AG);
+            k_adj_sst_finish<<<grid, block, 0, s>>>(fs, A.own, A.fbu, A.fbg, lf, A.lkN, A.lwN, A.lntN, G, back, add);
+        };
+        cudaMemsetAsync(A.lf2, 0, nq * sizeof(double), s);
+        solveT(S.mac2, S.sg, S.f1, A.lk, A.lw, A.lnt, A.ltau, S.f2, A.lf2, false);
+        evalT(S.f2, S.g2, A.lf2);
+        cudaMemsetAsync(A.ltauA, 0, nb1, s);
+        cudaMemsetAsync(A.ltauB, 0, nb1, s);
+        k_adj_stage1<<<grid, block, 0, s>>>(f0, S.s1, S.g1, S.tauB, A.lf2, A.lB, A.lc, A.lf0, A.la, A.ltauB, G,
+                                            S.tauA, A.ltauA);
+        cudaMemsetAsync(A.ls1, 0, nq * sizeof(double), s);
+        solveT(S.mac1, S.sgB, S.f1B, A.zero, A.zero, A.zero, A.ltauB, S.s1, A.ls1, true);
+        evalT(S.s1, S.g1, A.ls1);
+        k_adj_relax<<<grid, block, 0, s>>>(f0, S.tauA, A.ls1, A.lf0, A.ltauA, G);
+        solveT(in.mac, S.sgA, S.f1A, A.zero, A.zero, A.zero, A.ltauA, f0, A.lf0, true);
+        std::swap(A.L, A.lf0);
+        std::swap(A.lk, A.lkN);
+        std::swap(A.lw, A.lwN);
+        std::swap(A.lnt, A.lntN);
+        return;
+    }
     cudaMemsetAsync(A.lf2, 0, nq * sizeof(double), s);
     evalT(S.f2, S.g2, A.lf2);
-    k_adj_stage1<<<grid, block, 0, s>>>(f0, S.s1, S.g1, tau, A.lf2, A.lB, A.lc, A.lf0, A.la, A.ltau, G);
+    k_adj_stage1<<<grid, block, 0, s>>>(f0, S.s1, S.g1, tau, A.lf2, A.lB, A.lc, A.lf0, A.la, A.ltau, G, nullptr,
+                                        nullptr);
     cudaMemsetAsync(A.ls1, 0, nq * sizeof(double), s);
     evalT(S.s1, S.g1, A.ls1);
     k_adj_relax<<<grid, block, 0, s>>>(f0, tau, A.ls1, A.lf0, A.ltau, G);
@@ -762,7 +848,7 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in
                                                 A.own, A.fbu, A.lbval, G, AG);
         k_adj_sst_grad<<<grid, block, 0, s>>>(in.mac, in.k, in.w, S.sg, S.f1, A.fbu, A.own, A.fbg, A.lbval, G,
                                               back, AG);
-        k_adj_sst_finish<<<grid, block, 0, s>>>(f0, A.own, A.fbu, A.fbg, A.lf0, A.lk, A.lw, A.lnt, G, back);
+        k_adj_sst_finish<<<grid, block, 0, s>>>(f0, A.own, A.fbu, A.fbg, A.lf0, A.lk, A.lw, A.lnt, G, back, false);
     }
     std::swap(A.L, A.lf0);
 }
@@ -770,7 +856,7 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in
 int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
                  double *dJ_dbedge, double *dJ_dxy) {
     if (!h || instance < 0 || instance >= h->ninst || n_steps < 0 || !w) return FVLBM_ERR_BAD_PARAM;
-    if (h->precision != FVLBM_FP64 || h->scheme != 0 || h->per_stage || h->d_back == nullptr)
+    if (h->precision != FVLBM_FP64 || h->scheme != 0 || h->d_back == nullptr)
         return FVLBM_ERR_NOT_SUPPORTED;
     const InstInfo &I = h->inst[instance];
     // shape gradients: the limiter's dependence on the cell area is not transposed
@@ -789,7 +875,8 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
     // and r forward passes per unit at most, C(c + r, c) units can be reversed, and r is the
     // least such number.  With a snapshot for every unit start that is r = 1: each unit runs
     // forward twice (once to reach the next snapshot, once keeping its stage values).
-    const size_t per_step = (sst ? 119 : 99) * np * sizeof(double);
+    const bool ps = h->per_stage;
+    const size_t per_step = (ps ? 153 : (sst ? 119 : 99)) * np * sizeof(double);
     const size_t per_snap = (sst ? 15 : 9) * np * sizeof(double);
     size_t budget = h->adj_budget;
     if (budget == 0) {
@@ -806,7 +893,7 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
     }
     const int units = n_steps > 0 ? (n_steps + K - 1) / K : 0;
     AdjScratch M;
-    double *Cs, *macs;
+    double *Cs, *macs, *kS = nullptr, *wS = nullptr, *ntS = nullptr;
     AdjState xa, xb;
     std::vector<AdjState> snap(nsnap), st(K);
     std::vector<AdjStep> slot(K);
@@ -826,6 +913,11 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         state(xb);
         Cs = M.get(nq);
         macs = M.get(3 * np);
+        if (ps) {
+            kS = M.get(np);
+            wS = M.get(np);
+            ntS = M.get(np);
+        }
         for (auto &x : snap) state(x);
         for (int k = 0; k < K; ++k) {
             state(st[k]);
@@ -842,6 +934,19 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
                 slot[k].sg = M.get(12 * np);
                 slot[k].f1 = M.get(np);
                 slot[k].tau = M.get(np);
+            }
+            if (ps) {
+                slot[k].sgA = M.get(12 * np);
+                slot[k].f1A = M.get(np);
+                slot[k].tauA = M.get(np);
+                slot[k].sgB = M.get(12 * np);
+                slot[k].f1B = M.get(np);
+                slot[k].tauB = M.get(np);
+                slot[k].mac1 = M.get(3 * np);
+                slot[k].mac2 = M.get(3 * np);
+                slot[k].kS = kS;
+                slot[k].wS = wS;
+                slot[k].ntS = ntS;
             }
         }
         A.L = M.get(nq);
@@ -862,6 +967,14 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
             A.own = M.get(kSstOwn * np);
             A.fbu = M.get(4 * kSstFU * np);
             A.fbg = M.get(4 * kSstFG * np);
+        }
+        if (ps) {
+            A.lkN = M.get(np);
+            A.lwN = M.get(np);
+            A.lntN = M.get(np);
+            A.ltauA = M.get(np);
+            A.ltauB = M.get(np);
+            A.zero = M.get(np);
         }
         if (h->limit_f) {
             A.lnb = M.get(4 * kQ * np);
@@ -898,7 +1011,9 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         for (double *x : {A.lk, A.lw, A.lnt}) CK(cudaMemsetAsync(x, 0, np * sizeof(double), s));
         // laminar instances of the batch keep the handle's tau (the SST kernels skip them)
         for (int k = 0; k < K; ++k)
-            CK(cudaMemcpyAsync(slot[k].tau, h->tau, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            for (double *t : {slot[k].tau, slot[k].tauA, slot[k].tauB})
+                if (t) CK(cudaMemcpyAsync(t, h->tau, np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (ps) CK(cudaMemsetAsync(A.zero, 0, np * sizeof(double), s));
     }
     auto copy_state = [&](const AdjState &dst, const AdjState &src) -> int {
         CK(cudaMemcpyAsync(dst.f, src.f, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_grad(
 __global__ void __launch_bounds__(kTile) k_adj_sst_finish(
     const double *__restrict__ fn, const double *__restrict__ own, const double *__restrict__ fbu,
     const double *__restrict__ fbg, double *__restrict__ lf, double *__restrict__ lk,
-    double *__restrict__ lw, double *__restrict__ lnt, Geo<double> G, const int *__restrict__ back) {
+    double *__restrict__ lw, double *__restrict__ lnt, Geo<double> G, const int *__restrict__ back, bool add) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -639,9 +639,15 @@ __global__ void __launch_bounds__(kTile) k_adj_sst_finish(
         for (int c = 0; c < 4; ++c) l[c] += fbu[(c * 4 + b) * np + nb] + fbg[(c * 4 + b) * np + nb];
         l[4] += fbu[(9 * 4 + b) * np + nb];
     }
-    lk[i] = l[2];
-    lw[i] = l[3];
-    lnt[i] = l[4];
+    if (add) {  // several solves read the same state (per-stage reading)
+        lk[i] += l[2];
+        lw[i] += l[3];
+        lnt[i] += l[4];
+    } else {
+        lk[i] = l[2];
+        lw[i] = l[3];
+        lnt[i] = l[4];
+    }
     double f[kQ], dr, r, u, v, lfi[kQ];
     load9(fn, np, i, f);
     moments(f, P.rho0, dr, r, u, v);

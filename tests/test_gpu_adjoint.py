@@ -212,11 +212,16 @@ def test_adjoint_rejects_unsupported_handles():
         s.adjoint(-1, 1.0, 0.0)
     assert e.value.code == fvlbm.FVLBM_ERR_BAD_PARAM
     s.close()
-    var = fvlbm.Solver(dataclasses.replace(sst, variant=4), precision=FP64, device=0)
-    with pytest.raises(fvlbm.FvlbmError) as e:
-        var.adjoint(3, 1.0, 0.0)
+    var = fvlbm.Solver(dataclasses.replace(sst, variant=1), precision=FP64, device=0)
+    with pytest.raises(fvlbm.FvlbmError) as e:   # the limiter's area dependence
+        var.adjoint(3, 1.0, 0.0, shape=True)
     assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
     var.close()
+    eul = fvlbm.Solver(sst, precision=FP64, device=0, scheme=1)   # the explicit comparison scheme
+    with pytest.raises(fvlbm.FvlbmError) as e:
+        eul.adjoint(3, 1.0, 0.0)
+    assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
+    eul.close()
     # shape gradients of periodic meshes are not built; the other outputs are
     per = fvlbm.Solver(mg.Case(mg.periodic_box(8), nu=1e-3, cfl=0.5), precision=FP64, device=0)
     per.adjoint(2, 1.0, 0.0)
@@ -571,3 +576,33 @@ def test_adjoint_gradient_limiter_against_tangent(name, variant):
     adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
     assert abs(J - Jt) <= 1e-10 * abs(Jt)
     assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)
+
+
+@pytest.mark.parametrize("name,variant", [("bfs_sst", 4), ("naca_sst", 4), ("bfs_sst", 14)])
+def test_adjoint_per_stage_sst_against_tangent(name, variant):
+    """Reading variant 4 (the SST solved from t^n before every stage, with the macros of f^n,
+    f^(1), f^(2)): three SST transposes per step, each feeding the adjoint of its stage value
+    and the shared t^n state; against the tangent for state, boundary and node seeds (with
+    variants 2 and 8 on top)."""
+    base = _bfs_sst() if name == "bfs_sst" else _naca_sst()
+    case = dataclasses.replace(base, variant=variant)
+    warm, n = 8, 6
+    g, d = _sst_seeds(case, np.random.default_rng(800 + variant))
+    m = case.mesh.normalized()
+    v = 1e-3 * np.random.default_rng(900 + variant).standard_normal((m.n_nodes, 2))
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    s.step(warm)
+    J, dJdf, dJdb, dxy = s.adjoint(n, *W, shape=True)
+    s.close()
+    Jt, dJt = _tangent_dJ(case, warm, n, g, d)
+    adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
+    assert abs(J - Jt) <= 1e-10 * abs(Jt)
+    assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)
+    t = fvlbm.Solver(case, precision=TAN, device=0)
+    t.step(warm)
+    t.tangent_seed_nodes(v)
+    t.step(n)
+    _, dv = t.forces_tangent(dalpha=0.0)
+    t.close()
+    dJv = W[0] * dv["cd"] + W[1] * dv["cl"]
+    assert abs(float(np.sum(dxy * v)) - dJv) <= 1e-8 * abs(dJv), (float(np.sum(dxy * v)), dJv)
