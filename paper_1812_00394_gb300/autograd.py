@@ -20,8 +20,8 @@ Two backward passes compute the same derivatives of the discrete step:
     J_w = grad_output . (C_L, C_D) gives dJ_w/d(boundary values) and dJ_w/d(node positions);
     the gradient is their projection on the parameters plus the explicit dependence of the drag
     and lift directions on alpha.  Its cost does not grow with the number of parameters.  It
-    covers every reading variant (with variant 1, no wall-node parameters).
-The default ("auto") takes the adjoint where it covers the case, and the tangent otherwise.
+    covers every reading variant.
+The default ("auto") takes the adjoint.
 """
 from __future__ import annotations
 
@@ -41,14 +41,7 @@ class AirfoilForces:
     def __init__(self, base_case, wall_nodes, steps: int, device: int = 0, mode: str = "auto"):
         if mode not in ("auto", "tangent", "adjoint"):
             raise ValueError(f"unknown backward mode {mode!r}")
-        variant = int(getattr(base_case, "variant", 0))
-        # the adjoint lacks shape gradients under variant 1
-        reading = (variant & 1) and len(wall_nodes) > 0
-        if mode == "adjoint" and reading:
-            raise ValueError("the adjoint backward does not cover this reading variant")
-        if mode == "auto":
-            mode = "tangent" if reading else "adjoint"
-        self.mode = mode
+        self.mode = "adjoint" if mode == "auto" else mode
         self.base = dataclasses.replace(base_case, mesh=base_case.mesh.normalized())
         m = self.base.mesh
         self.steps = int(steps)

@@ -238,7 +238,8 @@ __global__ void __launch_bounds__(kTile) k_adj_gradT(const double *__restrict__ 
 // first argument, as the forward's fmin / fmax.
 __global__ void __launch_bounds__(kTile) k_adj_limT(const double *__restrict__ fs, double *__restrict__ lg,
                                                     double *__restrict__ lf, double *__restrict__ lnb,
-                                                    double *__restrict__ lbf, Geo<double> G) {
+                                                    double *__restrict__ lbf, Geo<double> G,
+                                                    double *__restrict__ a_rown, double *__restrict__ a_area) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kTile) k_adj_limT(const double *__restrict__ f
     }
     const double ar = G.area[i];
     const double e2 = ar * sqrt(ar);
-    double lfi[kQ];
+    double lfi[kQ], l_e2 = 0.0;
 #pragma unroll
     for (int a = 0; a < kQ; ++a) lfi[a] = lf[a * np + i];
     for (int a = 1; a < kQ; ++a) {
@@ -312,6 +313,11 @@ __global__ void __launch_bounds__(kTile) k_adj_limT(const double *__restrict__ f
             const double l_d1 = l_phi * dr_d1, l_d2 = l_phi * dr_d2;
             lrx += l_d2 * G.rown[(2 * msel) * np + i];
             lry += l_d2 * G.rown[(2 * msel + 1) * np + i];
+            if (a_rown != nullptr) {  // shape: d2 = g_raw . r_m, e2 = A^(3/2)
+                a_rown[(2 * msel) * np + i] += l_d2 * gx;
+                a_rown[(2 * msel + 1) * np + i] += l_d2 * gy;
+                l_e2 += l_phi * (d2 * D - N) / (D * D * d2);
+            }
             const int e = upper ? ihi : ilo;  // d1 = f_ext - f_i; the cell itself gives 0
             if (e >= 0) {
                 lfi[a] -= l_d1;
@@ -326,6 +332,7 @@ __global__ void __launch_bounds__(kTile) k_adj_limT(const double *__restrict__ f
     }
 #pragma unroll
     for (int a = 0; a < kQ; ++a) lf[a * np + i] = lfi[a];
+    if (a_area != nullptr) a_area[i] += l_e2 * 1.5 * sqrt(ar);
 }
 
 // ---- boundary faces: the face value f_bc(f_j, bval) enters the flux (weight e.n) and the
@@ -770,6 +777,7 @@ struct AdjVars {
     double *a_sn = nullptr, *a_lsq = nullptr, *a_rown = nullptr, *a_rnbr = nullptr;  // shape adjoint
     double *a_bnrm = nullptr, *a_blen = nullptr;
     double *a_dinv = nullptr, *a_wd = nullptr;  // shape adjoint, SST only
+    double *a_area = nullptr;                     // shape adjoint, limiter on grad f only
     double *lk = nullptr, *lw = nullptr, *lnt = nullptr, *ltau = nullptr;  // SST
     double *own = nullptr, *fbu = nullptr, *fbg = nullptr;
     // per-stage SST reading: the state adjoints of t^n as the three solves add them up, the
@@ -795,7 +803,7 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in
     // transpose of one flux + gradient evaluation at stage value fs (gradient g): la -> lf
     auto evalT = [&](const double *fs, const double *g, double *lf) {
         k_adj_fluxT<<<grid, block, 0, s>>>(A.la, lf, A.lg, G, back);
-        if (A.lnb) k_adj_limT<<<grid, block, 0, s>>>(fs, A.lg, lf, A.lnb, A.lbf, G);
+        if (A.lnb) k_adj_limT<<<grid, block, 0, s>>>(fs, A.lg, lf, A.lnb, A.lbf, G, A.a_rown, A.a_area);
         geom(fs, g);
         k_adj_gradT<<<grid, block, 0, s>>>(A.lg, lf, G, back, A.lnb);
         k_adj_bndT<<<grid, block, 0, s>>>(fs, A.la, A.lg, lf, A.lbval, G, A.lbf);
@@ -859,8 +867,7 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
     if (h->precision != FVLBM_FP64 || h->scheme != 0 || h->d_back == nullptr)
         return FVLBM_ERR_NOT_SUPPORTED;
     const InstInfo &I = h->inst[instance];
-    // shape gradients: the limiter's dependence on the cell area is not transposed
-    if (dJ_dxy && (!I.mesh || !I.mesh->ppairs.empty() || h->limit_f)) return FVLBM_ERR_NOT_SUPPORTED;
+    if (dJ_dxy && (!I.mesh || !I.mesh->ppairs.empty())) return FVLBM_ERR_NOT_SUPPORTED;
     CK(cudaSetDevice(h->device));
     const Geo<double> G = geo_of<double>(h);
     const bool sst = h->sst;
@@ -991,6 +998,7 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
                 A.a_dinv = M.get(4 * np);
                 A.a_wd = M.get(np);
             }
+            if (h->limit_f) A.a_area = M.get(np);
         }
     };
     carve();
@@ -1006,6 +1014,7 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
             CK(cudaMemsetAsync(A.a_dinv, 0, 4 * np * sizeof(double), s));
             CK(cudaMemsetAsync(A.a_wd, 0, np * sizeof(double), s));
         }
+        if (A.a_area) CK(cudaMemsetAsync(A.a_area, 0, np * sizeof(double), s));
     }
     if (sst) {  // J does not depend on k, omega, nu_t of the last state
         for (double *x : {A.lk, A.lw, A.lnt}) CK(cudaMemsetAsync(x, 0, np * sizeof(double), s));
@@ -1141,7 +1150,7 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         const size_t nc = I.nc;
         CK(cudaMemcpyAsync(perm.data(), h->d_perm + perm_offset(h, instance), sizeof(int) * nc,
                            cudaMemcpyDeviceToHost, s));
-        runs.resize(4 * 8 * nc + 5 * nc + 3 * static_cast<size_t>(std::max(I.nb, 1)));
+        runs.resize(4 * 8 * nc + 6 * nc + 3 * static_cast<size_t>(std::max(I.nb, 1)));
         const double *src[4] = {A.a_sn, A.a_lsq, A.a_rown, A.a_rnbr};
         for (int q = 0; q < 4; ++q)
             for (int c = 0; c < 8; ++c)
@@ -1154,7 +1163,10 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
             CK(cudaMemcpyAsync(runs.data() + 36 * nc, A.a_wd + I.cell_off, sizeof(double) * nc,
                                cudaMemcpyDeviceToHost, s));
         }
-        double *bt = runs.data() + 37 * nc;
+        if (A.a_area)  // the limiter's cell areas
+            CK(cudaMemcpyAsync(runs.data() + 37 * nc, A.a_area + I.cell_off, sizeof(double) * nc,
+                               cudaMemcpyDeviceToHost, s));
+        double *bt = runs.data() + 38 * nc;
         if (I.nb > 0) {
             CK(cudaMemcpyAsync(bt, A.a_bnrm + I.bface_off, sizeof(double) * I.nb, cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(bt + I.nb, A.a_bnrm + h->nbt + I.bface_off, sizeof(double) * I.nb,
@@ -1183,10 +1195,14 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
                 GA.wdist[perm[k]] = runs[36 * nc + k];
             }
         }
+        if (A.a_area) {
+            GA.area.assign(nc, 0.0);
+            for (size_t k = 0; k < nc; ++k) GA.area[perm[k]] = runs[37 * nc + k];
+        }
         const size_t nbe = mc.btype.size();
         GA.bnrm.assign(2 * nbe, 0.0);
         GA.blen.assign(nbe, 0.0);
-        const double *bt = runs.data() + 37 * nc;
+        const double *bt = runs.data() + 38 * nc;
         for (int f = 0; f < I.nb; ++f) {
             const int e = I.bedge_of[f];
             GA.bnrm[2 * e] = bt[f];

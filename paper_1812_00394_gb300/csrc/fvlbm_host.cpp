@@ -442,7 +442,7 @@ void cell_area_centroid(const fvlbm_mesh &m, int i, const S *xy, S *area, S *cx,
 // xy and its face neighbours' centroids (nbx, nby; slots with nbr[l] < 0 are boundary faces).
 template <class S>
 struct CellGeo {
-    S sn[8], lsq[8], rown[8], rnbr[8], nrm[8], len[4], dinv[4];
+    S sn[8], lsq[8], rown[8], rnbr[8], nrm[8], len[4], dinv[4], area;
 };
 
 template <class S>
@@ -451,6 +451,7 @@ void cell_geometry(const fvlbm_mesh &m, int i, const S *xy, const int *nbr, cons
     const int p0 = m.cell_ptr[i], nv = m.cell_ptr[i + 1] - p0;
     S area, cx, cy;
     cell_area_centroid(m, i, xy, &area, &cx, &cy);
+    G->area = area;
     S dx[4], dy[4];
     S mxx = 0, mxy = 0, myy = 0;
     for (int l = 0; l < nv; ++l) {
@@ -541,7 +542,7 @@ int geometry_adjoint(const fvlbm_mesh &m, const fvlbm_bc &bc, const GeometryAdjo
             }
         // adjoint . d(outputs) for the current seed
         auto contract = [&](const CellGeo<Dual> &G) {
-            double s = 0.0;
+            double s = A.area.empty() ? 0.0 : A.area[i] * G.area.d;
             for (int l = 0; l < nv; ++l) {
                 const size_t o = (4 * static_cast<size_t>(i) + l) * 2;
                 for (int c = 0; c < 2; ++c) {

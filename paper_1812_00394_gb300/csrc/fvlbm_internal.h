@@ -82,10 +82,11 @@ inline int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm
 
 // Adjoints of the geometry arrays a step reads, in input order: for face l of input cell i
 // (joining its nodes l and l + 1), entry (4 i + l) * 2 + c of sn, lsq, rown, rnbr (c = x, y) and
-// entry 4 i + l of dinv; wdist[i]; for input boundary edge b, bnrm[2 b + c] and blen[b]
-// (periodic edges: unused).  dinv and wdist may be empty (laminar steps do not read them).
+// entry 4 i + l of dinv; wdist[i] and area[i]; for input boundary edge b, bnrm[2 b + c] and
+// blen[b] (periodic edges: unused).  dinv, wdist and area may be empty (only the SST and the
+// limiter on grad f read them).
 struct GeometryAdjoint {
-    std::vector<double> sn, lsq, rown, rnbr, bnrm, blen, dinv, wdist;
+    std::vector<double> sn, lsq, rown, rnbr, bnrm, blen, dinv, wdist, area;
 };
 
 // Reverse mode of the preprocessing above with respect to the node positions: dxy[2 n_nodes] =

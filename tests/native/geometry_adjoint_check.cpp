@@ -1,6 +1,6 @@
 // Host-side check of the reverse-mode geometry (geometry_adjoint) used by the shape gradient of
 // the adjoint: for random adjoints A of the geometry arrays (face normals and lengths, offsets,
-// least-squares weights, 1 / |d|, wall distance, wall normals and lengths) and a random node
+// least-squares weights, 1 / |d|, wall distance, cell area, wall normals and lengths) and a random node
 // displacement v,
 //   <A, d(geometry)/d(xy) v>  from prepare_instance_t<Dual> (forward mode, one direction)
 // must equal
@@ -63,6 +63,8 @@ int main(int argc, char **argv) {
     for (double &x : A.dinv) x = uniform(s);
     A.wdist.resize(nc);
     for (double &x : A.wdist) x = uniform(s);
+    A.area.resize(nc);
+    for (double &x : A.area) x = uniform(s);
     A.bnrm.resize(2 * static_cast<size_t>(nbe));
     A.blen.resize(nbe);
     for (double &x : A.bnrm) x = uniform(s);
@@ -79,7 +81,7 @@ int main(int argc, char **argv) {
     double fwd = 0.0;
     for (int k = 0; k < D.nc; ++k) {
         const size_t i = D.perm[k];
-        fwd += A.wdist[i] * D.wdist[k].d;
+        fwd += A.wdist[i] * D.wdist[k].d + A.area[i] * D.area[k].d;
         for (int l = 0; l < D.nface[k]; ++l) fwd += A.dinv[4 * i + l] * D.dinv[l * np + k].d;
         for (int l = 0; l < D.nface[k]; ++l)
             for (int c = 0; c < 2; ++c) {

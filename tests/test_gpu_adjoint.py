@@ -212,11 +212,6 @@ def test_adjoint_rejects_unsupported_handles():
         s.adjoint(-1, 1.0, 0.0)
     assert e.value.code == fvlbm.FVLBM_ERR_BAD_PARAM
     s.close()
-    var = fvlbm.Solver(dataclasses.replace(sst, variant=1), precision=FP64, device=0)
-    with pytest.raises(fvlbm.FvlbmError) as e:   # the limiter's area dependence
-        var.adjoint(3, 1.0, 0.0, shape=True)
-    assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
-    var.close()
     eul = fvlbm.Solver(sst, precision=FP64, device=0, scheme=1)   # the explicit comparison scheme
     with pytest.raises(fvlbm.FvlbmError) as e:
         eul.adjoint(3, 1.0, 0.0)
@@ -560,22 +555,30 @@ def test_adjoint_gradient_limiter_against_tangent(name, variant):
     """Reading variant 1 (Venkatakrishnan limiter on grad f): the limiter's transpose (through
     the selected face's factor, the raw gradient and the extreme among the cell, its neighbours
     and its boundary values) against the tangent, for seeds of f^0 and of the boundary values;
-    with variants 2 and 8 on top on the SST step.  Shape gradients are not offered with it."""
+    with variants 2 and 8 on top on the SST step; and the shape gradient (the limiter reads the
+    face offsets and the cell area) against the tangent of a random node displacement."""
     base = _naca_laminar() if name == "naca_laminar" else _bfs_sst()
     case = dataclasses.replace(base, variant=variant)
     warm, n = 8, 6
     g, d = _sst_seeds(case, np.random.default_rng(700 + variant))
+    m = case.mesh.normalized()
+    v = 1e-3 * np.random.default_rng(750 + variant).standard_normal((m.n_nodes, 2))
     s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
     s.step(warm)
-    J, dJdf, dJdb, _ = s.adjoint(n, *W)
-    with pytest.raises(fvlbm.FvlbmError) as e:
-        s.adjoint(n, *W, shape=True)
-    assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
+    J, dJdf, dJdb, dxy = s.adjoint(n, *W, shape=True)
     s.close()
     Jt, dJt = _tangent_dJ(case, warm, n, g, d)
     adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
     assert abs(J - Jt) <= 1e-10 * abs(Jt)
     assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)
+    t = fvlbm.Solver(case, precision=TAN, device=0)
+    t.step(warm)
+    t.tangent_seed_nodes(v)
+    t.step(n)
+    _, dv = t.forces_tangent(dalpha=0.0)
+    t.close()
+    dJv = W[0] * dv["cd"] + W[1] * dv["cl"]
+    assert abs(float(np.sum(dxy * v)) - dJv) <= 1e-8 * abs(dJv), (float(np.sum(dxy * v)), dJv)
 
 
 @pytest.mark.parametrize("name,variant", [("bfs_sst", 4), ("naca_sst", 4), ("bfs_sst", 14)])
