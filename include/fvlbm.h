@@ -309,8 +309,8 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
  * freed before it returns (about 60 doubles per cell plus the stage values and snapshots, 32
  * more with dJ_dxy); dJ_dxy adds one pass over the cells on the host (SST: and a nearest-wall
  * search per cell).
- * Valid on FVLBM_FP64 handles with the IMEX scheme, with every reading variant; the explicit
- * Euler scheme returns FVLBM_ERR_NOT_SUPPORTED.  Synchronises.
+ * Valid on FVLBM_FP64 handles, with either scheme (IMEX or the explicit Euler comparison
+ * scheme) and every reading variant; else FVLBM_ERR_NOT_SUPPORTED.  Synchronises.
  * Errors: BAD_PARAM (w NULL, n_steps < 0, bad instance), NOT_SUPPORTED, OOM, CUDA. */
 int fvlbm_adjoint(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
                   double *dJ_dbedge_val, double *dJ_dxy);

@@ -599,6 +599,39 @@ __global__ void __launch_bounds__(kTile) k_adj_relax(const double *__restrict__ 
     for (int a = 0; a < kQ; ++a) lf0[a * np + i] = l0[a];
 }
 
+// ---- explicit Euler comparison scheme: f^{n+1} = f + dt (-acc(f) + (f^eq(f) - f) / tau).
+// From L (adjoint of f^{n+1}): lf0 = L + (dt/tau) (J_feq^T L - L) (=), la = -dt L, and the
+// relaxation time's adjoint -dt/tau^2 sum L (f^eq - f) (=).
+__global__ void __launch_bounds__(kTile) k_adj_euler(const double *__restrict__ f0, const double *__restrict__ tau,
+                                                     const double *__restrict__ L, double *__restrict__ lf0,
+                                                     double *__restrict__ la, double *__restrict__ ltau,
+                                                     Geo<double> G) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const size_t np = G.np;
+    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
+    const double dt = cell_dt(G, P, i), c = dt / tau[i];
+    double x0[kQ], l0[kQ], mu[kQ];
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+        x0[a] = f0[a * np + i];
+        const double l = L[a * np + i];
+        l0[a] = (1.0 - c) * l;
+        mu[a] = c * l;
+        la[a * np + i] = -dt * l;
+    }
+    if (ltau != nullptr) {
+        double eq[kQ], dr, r, u, v, s = 0.0;
+        moments(x0, P.rho0, dr, r, u, v);
+        feq_dev(dr, r, u, v, eq);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) s += L[a * np + i] * (eq[a] - x0[a]);
+        ltau[i] = -s * c / tau[i];
+    }
+    feq_vjp(x0, P.rho0, mu, l0);
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) lf0[a * np + i] = l0[a];
+}
+
 // ---- objective J = (cx Fx + cy Fy) / (q l) over the wall faces of one instance: its
 // derivative with respect to f (into L, which is zeroed first) and to the boundary values
 __global__ void __launch_bounds__(kTile) k_adj_seed(const double *__restrict__ fn, const double *__restrict__ bnrm,
@@ -723,6 +756,14 @@ void adj_forward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in,
             k_sst_update<double, false, false><<<grid, block, 0, s>>>(mac, in.k, in.w, in.nt, sg, f1, ko, wo, nto,
                                                                       tau_out, G, nullptr, nullptr, CG);
     };
+    if (h->scheme == 1) {  // explicit Euler: the SST solve, then one flux + collision update
+        if (h->sst) solve(in.mac, S.sg, S.f1, out.k, out.w, out.nt, S.tau);
+        grad_f<double>(h, grid, block, s, in.f, S.g1, G);
+        k_flux_stage<double, 4, false><<<grid, block, 0, s>>>(in.f, S.g1, out.f, in.f, S.B, S.C,
+                                                              h->sst ? S.tau : tau, h->sst ? out.mac : S.mac,
+                                                              nullptr, G);
+        return;
+    }
     if (h->per_stage) {
         // the SST solved from t^n before every stage with the macros of f^n, f^(1), f^(2); stage 1
         // relaxes with the first tau, its algebra takes the second for f^(2); the last solve
@@ -808,6 +849,21 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in
         k_adj_gradT<<<grid, block, 0, s>>>(A.lg, lf, G, back, A.lnb);
         k_adj_bndT<<<grid, block, 0, s>>>(fs, A.la, A.lg, lf, A.lbval, G, A.lbf);
     };
+    if (h->scheme == 1) {
+        k_adj_euler<<<grid, block, 0, s>>>(f0, tau, A.L, A.lf0, A.la, A.ltau, G);
+        evalT(f0, S.g1, A.lf0);
+        if (h->sst) {
+            const AdjGeo AG{A.a_sn, A.a_rown, A.a_rnbr, A.a_lsq, A.a_dinv, A.a_wd};
+            k_adj_sst_update<<<grid, block, 0, s>>>(in.mac, in.k, in.w, in.nt, S.sg, S.f1, A.lk, A.lw, A.lnt,
+                                                    A.ltau, A.own, A.fbu, A.lbval, G, AG);
+            k_adj_sst_grad<<<grid, block, 0, s>>>(in.mac, in.k, in.w, S.sg, S.f1, A.fbu, A.own, A.fbg, A.lbval, G,
+                                                  back, AG);
+            k_adj_sst_finish<<<grid, block, 0, s>>>(f0, A.own, A.fbu, A.fbg, A.lf0, A.lk, A.lw, A.lnt, G, back,
+                                                    false);
+        }
+        std::swap(A.L, A.lf0);
+        return;
+    }
     k_adj_stage3<<<grid, block, 0, s>>>(A.L, A.lf3, A.lc, A.la, G);
     evalT(S.f3, S.g3, A.lf3);
     k_adj_stage2<<<grid, block, 0, s>>>(S.B, S.f2, S.g2, tau, A.lf3, A.lc, A.lB, A.la, A.ltau, G);
@@ -864,7 +920,7 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in
 int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
                  double *dJ_dbedge, double *dJ_dxy) {
     if (!h || instance < 0 || instance >= h->ninst || n_steps < 0 || !w) return FVLBM_ERR_BAD_PARAM;
-    if (h->precision != FVLBM_FP64 || h->scheme != 0 || h->d_back == nullptr)
+    if (h->precision != FVLBM_FP64 || h->d_back == nullptr)
         return FVLBM_ERR_NOT_SUPPORTED;
     const InstInfo &I = h->inst[instance];
     if (dJ_dxy && (!I.mesh || !I.mesh->ppairs.empty())) return FVLBM_ERR_NOT_SUPPORTED;

@@ -212,11 +212,7 @@ def test_adjoint_rejects_unsupported_handles():
         s.adjoint(-1, 1.0, 0.0)
     assert e.value.code == fvlbm.FVLBM_ERR_BAD_PARAM
     s.close()
-    eul = fvlbm.Solver(sst, precision=FP64, device=0, scheme=1)   # the explicit comparison scheme
-    with pytest.raises(fvlbm.FvlbmError) as e:
-        eul.adjoint(3, 1.0, 0.0)
-    assert e.value.code == fvlbm.FVLBM_ERR_NOT_SUPPORTED
-    eul.close()
+
     # shape gradients of periodic meshes are not built; the other outputs are
     per = fvlbm.Solver(mg.Case(mg.periodic_box(8), nu=1e-3, cfl=0.5), precision=FP64, device=0)
     per.adjoint(2, 1.0, 0.0)
@@ -602,6 +598,43 @@ def test_adjoint_per_stage_sst_against_tangent(name, variant):
     assert abs(J - Jt) <= 1e-10 * abs(Jt)
     assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)
     t = fvlbm.Solver(case, precision=TAN, device=0)
+    t.step(warm)
+    t.tangent_seed_nodes(v)
+    t.step(n)
+    _, dv = t.forces_tangent(dalpha=0.0)
+    t.close()
+    dJv = W[0] * dv["cd"] + W[1] * dv["cl"]
+    assert abs(float(np.sum(dxy * v)) - dJv) <= 1e-8 * abs(dJv), (float(np.sum(dxy * v)), dJv)
+
+
+@pytest.mark.parametrize("name", ["cavity", "bfs_sst"])
+def test_adjoint_explicit_euler_scheme_against_tangent(name):
+    """The explicit Euler comparison scheme (f^{n+1} = f + dt (Gamma^a + Gamma^c), Part I),
+    laminar and with the SST solve: the adjoint against the tangent for state, boundary and node
+    seeds.  Steps within its collision limit dt < 2 tau."""
+    if name == "cavity":
+        case = mg.cavity_quad(16, re=10.0, lid_u=0.1, seed=3)
+    else:
+        case = dataclasses.replace(_bfs_sst(), dt=1e-5, cfl=0.0)
+    warm, n = 5, 6
+    g, d = _sst_seeds(case, np.random.default_rng(950))
+    m = case.mesh.normalized()
+    v = 1e-3 * np.random.default_rng(951).standard_normal((m.n_nodes, 2))
+    s = fvlbm.Solver(case, precision=FP64, device=0, scheme=1)
+    s.step(warm)
+    J, dJdf, dJdb, dxy = s.adjoint(n, *W, shape=True)
+    s.close()
+    t = fvlbm.Solver(case, precision=TAN, device=0, scheme=1)
+    t.step(warm)
+    t.tangent_seed(d, g)
+    t.step(n)
+    val, dv = t.forces_tangent(dalpha=0.0)
+    t.close()
+    Jt, dJt = W[0] * val["cd"] + W[1] * val["cl"], W[0] * dv["cd"] + W[1] * dv["cl"]
+    adj = float(np.sum(dJdf * g) + np.sum(dJdb * d))
+    assert abs(J - Jt) <= 1e-10 * abs(Jt)
+    assert abs(adj - dJt) <= 1e-8 * abs(dJt), (adj, dJt)
+    t = fvlbm.Solver(case, precision=TAN, device=0, scheme=1)
     t.step(warm)
     t.tangent_seed_nodes(v)
     t.step(n)
