@@ -167,3 +167,63 @@ def forces(model: AirfoilForces, p: torch.Tensor) -> torch.Tensor:
     """(C_L, C_D) of ``model`` at parameters ``p`` (1-D tensor of length model.n_params()),
     differentiable with respect to p."""
     return _ForcesFunction.apply(p, model)
+
+
+class StepForces:
+    """(C_D, C_L) of one case after ``steps`` FP64 steps as a function of the full inputs: the
+    initial distributions f0 [n_cells, 9] (cell-major, as ``Solver.get_f``), the boundary values
+    [n_bedges, 5] and the node positions [n_nodes, 2].  The time step is the base case's, held
+    fixed.  Its backward pass is one adjoint solve (``fvlbm_adjoint``) whatever the number of
+    inputs: the vector-Jacobian product with respect to all three at once."""
+
+    def __init__(self, base_case, steps: int, device: int = 0):
+        self.base = dataclasses.replace(base_case, mesh=base_case.mesh.normalized())
+        self.steps = int(steps)
+        self.device = device
+        probe = fvlbm.Solver(self.base, precision=fvlbm.FVLBM_FP64, device=device, kernel_path=1)
+        self.dt = probe.dt()
+        self.f0 = probe.get_f()
+        probe.close()
+
+    def inputs(self):
+        """The base case's (f0, boundary values, node positions) as float64 tensors."""
+        m = self.base.mesh
+        return (torch.tensor(self.f0), torch.tensor(m.bedge_val.copy()), torch.tensor(m.xy.copy()))
+
+    def solver(self, f0, bval, xy):
+        mesh = dataclasses.replace(self.base.mesh, xy=np.ascontiguousarray(xy, np.float64),
+                                   bedge_val=np.ascontiguousarray(bval, np.float64))
+        case = dataclasses.replace(self.base, mesh=mesh, dt=self.dt)
+        s = fvlbm.Solver(case, precision=fvlbm.FVLBM_FP64, device=self.device, kernel_path=1)
+        s.set_f(np.ascontiguousarray(f0, np.float64))
+        return s
+
+
+class _StepForcesFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, f0, bval, xy, model):
+        arrs = [t.detach().cpu().double().numpy() for t in (f0, bval, xy)]
+        s = model.solver(*arrs)
+        s.step(model.steps)
+        f = s.forces()
+        s.close()
+        ctx.model, ctx.arrs = model, arrs
+        return torch.tensor([f["cd"], f["cl"]], dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, g):
+        gn = g.detach().cpu().double().numpy()
+        s = ctx.model.solver(*ctx.arrs)
+        _, df, db, dxy = s.adjoint(ctx.model.steps, w_cd=float(gn[0]), w_cl=float(gn[1]),
+                                   shape=ctx.needs_input_grad[2])
+        s.close()
+        as_t = lambda a: None if a is None else torch.as_tensor(a, dtype=torch.float64)  # noqa: E731
+        return (as_t(df) if ctx.needs_input_grad[0] else None,
+                as_t(db) if ctx.needs_input_grad[1] else None,
+                as_t(dxy) if ctx.needs_input_grad[2] else None, None)
+
+
+def step_forces(model: StepForces, f0: torch.Tensor, bval: torch.Tensor, xy: torch.Tensor) -> torch.Tensor:
+    """(C_D, C_L) of ``model`` from (f0, boundary values, node positions), differentiable with
+    respect to each of them."""
+    return _StepForcesFunction.apply(f0, bval, xy, model)

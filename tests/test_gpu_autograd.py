@@ -95,3 +95,38 @@ def test_autograd_sst_adjoint_backward_matches_tangent():
         grads[mode] = p.grad.numpy().copy()
     for q in range(4):
         assert abs(grads["auto"][q] - grads["tangent"][q]) <= 1e-8 * abs(grads["tangent"][q]) + 1e-14, q
+
+
+def test_step_forces_gradients_match_central_differences():
+    """The full-input autograd function: a loss of (C_D, C_L) after 20 FP64 steps of a laminar
+    airfoil, differentiated by one adjoint solve with respect to f0, the boundary values and the
+    node positions, against central differences along a direction of each input."""
+    import dataclasses
+    base = dataclasses.replace(mg.naca0012_cmesh(n_target=1500, re_c=2000.0, alpha_deg=4.0), sst=False)
+    model = fa.StepForces(base, steps=20, device=0)
+    f0, bv, xy = (t.requires_grad_(True) for t in model.inputs())
+    out = fa.step_forces(model, f0, bv, xy)
+    (1.5 * out[0] - out[1]).backward()
+    rng = np.random.default_rng(17)
+    # node direction: a dilation about the centroid of the nodes.  It keeps every face normal,
+    # so no upwind choice on an e.n = 0 face (the quads of the boundary layer) changes sides
+    # within the differences, where the derivative is one-sided
+    xy0 = xy.detach().numpy()
+    dirs = [1e-3 * rng.standard_normal(tuple(f0.shape)), np.zeros(tuple(bv.shape)),
+            1e-3 * (xy0 - xy0.mean(0))]
+    dirs[1][:, :3] = 1e-2 * rng.standard_normal((bv.shape[0], 3))
+    base_in = [t.detach().numpy() for t in (f0, bv, xy)]
+    for q, grad in enumerate((f0.grad, bv.grad, xy.grad)):
+        h = (1e-5, 1e-5, 1e-4)[q]
+        vals = []
+        for sgn in (1.0, -1.0):
+            args = [a.copy() for a in base_in]
+            args[q] = args[q] + sgn * h * dirs[q]
+            s = model.solver(*args)
+            s.step(model.steps)
+            f = s.forces()
+            s.close()
+            vals.append(1.5 * f["cd"] - f["cl"])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        adj = float(np.sum(grad.numpy() * dirs[q]))
+        assert abs(adj - fd) <= 1e-5 * abs(fd), (q, adj, fd)
