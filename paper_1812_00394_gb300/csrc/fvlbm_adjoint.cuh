@@ -13,8 +13,10 @@
 // gradient operators are transposed by gathering over each cell's faces (the neighbour's view
 // of a shared face comes from its back slot); the per-cell maps R, S1, S2 and the boundary
 // values are transposed in closed form (they are affine but for f^eq, whose transposed Jacobian
-// is written out below).  Stage values stay in device memory for whole runs of steps, and
-// longer runs are reversed on a binomial checkpoint schedule (see adjoint_impl).
+// is written out below).  The explicit Euler comparison scheme and the per-stage SST reading
+// have their own forward recompute and reverse (adj_forward_step, adj_backward_step).  Stage
+// values stay in device memory for whole runs of steps, and longer runs are reversed on a
+// binomial checkpoint schedule (see adjoint_impl).
 
 #include <functional>
 
@@ -737,8 +739,9 @@ struct AdjStep {
     double *kS = nullptr, *wS = nullptr, *ntS = nullptr;  // discarded k, omega, nu_t of those solves
 };
 
-// One two-pass FP64 step from state `in` to state `out` (the launches of the two-pass path:
-// the SST solve first on SST handles), with the stage values kept in S.
+// One two-pass FP64 step from state `in` to state `out` (the launches of the handle's two-pass
+// path for its scheme and readings: the SST solve first on SST handles, three of them under the
+// per-stage reading), with the stage values kept in S.
 void adj_forward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in, const AdjState &out,
                       const AdjStep &S) {
     const dim3 grid(h->ntiles), block(kTile);
@@ -930,7 +933,8 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
     const size_t np = h->np, nq = static_cast<size_t>(kQ) * np;
     // Memory plan.  The stage values one adjoint step reads take 99 doubles per cell (f^n, f^(1),
     // f^(2), B, f^(3) and the three gradients; SST adds 20: the macros, k, omega, nu_t, the SST
-    // gradients, f1 and tau); a state snapshot takes 9 (SST: 15).  Within the budget (the
+    // gradients, f1 and tau; the per-stage reading 34 more for its two extra solves and the
+    // macros they read); a state snapshot takes 9 (SST: 15).  Within the budget (the
     // handle's adjoint budget, else half the free device memory) all steps keep their stage
     // values when they fit, and every step runs forward once.  Otherwise the run is cut into
     // units of K steps whose stage values fit in half the budget, the other half holds c state
