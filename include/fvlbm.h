@@ -298,8 +298,8 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
  *                  (FVLBM_ERR_NOT_SUPPORTED).
  * The initial k, omega and nu_t of SST instances are held fixed (their adjoints are not output).
  * Neither the state nor the step count of the handle changes.  The call runs n_steps forward
- * steps that keep their stage values (99 doubles per cell and step, 119 with SST) and n_steps
- * adjoint steps.
+ * steps that keep their stage values (99 doubles per cell and step, 119 with SST, 153 under the
+ * per-stage SST reading) and n_steps adjoint steps.
  * Where the stage values of all steps do not fit the adjoint budget (fvlbm_set_adjoint_budget;
  * default half the free device memory), the run is cut into units of K steps whose stage values
  * fit in half the budget; the other half holds c state snapshots (9 doubles per cell, 15 with
