@@ -18,8 +18,6 @@
 // values stay in device memory for whole runs of steps, and longer runs are reversed on a
 // binomial checkpoint schedule (see adjoint_impl).
 
-#include <functional>
-
 namespace fvlbm {
 
 // ---- per-cell maps.  Each is affine in its inputs except through the equilibrium of a stage
@@ -1155,37 +1153,18 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         CK(cudaGetLastError());
         return FVLBM_OK;
     };
-    // binomial coefficient C(c + r, c), saturated
-    auto beta = [](int c, int r) {
-        double b = 1.0;
-        for (int i = 1; i <= c; ++i) b = b * (r + i) / i;
-        return b > 2e9 ? 2000000000 : static_cast<int>(b + 0.5);
-    };
-    // reverse units u0 .. u0+n-1, the state at u0 in `start`, snapshots free from index `free`
-    std::function<int(int, int, const AdjState &, int)> revolve = [&](int u0, int n, const AdjState &start,
-                                                                       int free) -> int {
-        if (n <= 0) return FVLBM_OK;
-        if (n == 1) return reverse_unit(u0, start);
-        const int c = nsnap - free;
-        // every frame with n >= 2 has a free snapshot: the plan gives at least one when there are
-        // two units or more, and a frame with c free snapshots hands its tail (c - 1 free) at
-        // most C(c - 1 + r, c - 1) units, which is 1 when c = 1
-        if (c <= 0) return FVLBM_ERR_BAD_PARAM;
-        int r = 1;
-        while (beta(c, r) < n) ++r;
-        const int tail = std::min(n - 1, beta(c - 1, r));
-        const int head = n - tail;
-        int rc = advance(u0, u0 + head, start, snap[free]);
-        if (rc) return rc;
-        if ((rc = revolve(u0 + head, tail, snap[free], free + 1))) return rc;
-        return revolve(u0, head, start, free);
-    };
     if (n_steps == 0) {
         int rc = seed(h0.f);
         if (rc) return rc;
-    } else {
-        int rc = revolve(0, units, h0, 0);
-        if (rc) return rc;
+    } else {  // the units on the binomial schedule (host logic, revolve_schedule)
+        std::vector<RevolveAction> plan;
+        if (!revolve_schedule(units, nsnap, &plan)) return FVLBM_ERR_BAD_PARAM;
+        for (const RevolveAction &act : plan) {
+            const AdjState &from = act.from < 0 ? h0 : snap[act.from];
+            int rc = act.kind == RevolveAction::kAdvance ? advance(act.u0, act.u1, from, snap[act.to])
+                                                         : reverse_unit(act.u0, from);
+            if (rc) return rc;
+        }
     }
     double *xscr = xb.f;
     if (dJ_df && I.nc > 0) {

@@ -633,6 +633,42 @@ int geometry_adjoint(const fvlbm_mesh &m, const fvlbm_bc &bc, const GeometryAdjo
     return FVLBM_OK;
 }
 
+namespace {
+
+// C(c + r, c), saturated at 2e9
+int binom_cr(int c, int r)
+{
+    double b = 1.0;
+    for (int i = 1; i <= c; ++i) b = b * (r + i) / i;
+    return b > 2e9 ? 2000000000 : static_cast<int>(b + 0.5);
+}
+
+// units u0 .. u0+n-1, the state at u0 in snapshot `from`, snapshots free from index `free`
+bool revolve_rec(int u0, int n, int from, int free, int snaps, std::vector<RevolveAction> *out)
+{
+    if (n <= 0) return true;
+    if (n == 1) {
+        out->push_back({RevolveAction::kReverse, u0, u0 + 1, from, -1});
+        return true;
+    }
+    const int c = snaps - free;
+    if (c <= 0) return false;
+    int r = 1;
+    while (binom_cr(c, r) < n) ++r;
+    const int tail = std::min(n - 1, binom_cr(c - 1, r));
+    const int head = n - tail;
+    out->push_back({RevolveAction::kAdvance, u0, u0 + head, from, free});
+    return revolve_rec(u0 + head, tail, free, free + 1, snaps, out) && revolve_rec(u0, head, from, free, snaps, out);
+}
+
+}  // namespace
+
+bool revolve_schedule(int units, int snaps, std::vector<RevolveAction> *out)
+{
+    out->clear();
+    return revolve_rec(0, units, -1, 0, snaps, out);
+}
+
 template int prepare_instance_t<double>(const fvlbm_mesh &, const fvlbm_bc &, const fvlbm_params &,
                                         const double *, PreparedT<double> *, std::string *);
 template int prepare_instance_t<Dual>(const fvlbm_mesh &, const fvlbm_bc &, const fvlbm_params &,

@@ -98,4 +98,20 @@ struct GeometryAdjoint {
 int geometry_adjoint(const fvlbm_mesh &m, const fvlbm_bc &bc, const GeometryAdjoint &A, double *dxy,
                      std::string *why);
 
+// Binomial checkpoint schedule (revolve) for reversing `units` units of forward work with
+// `snaps` state snapshots.  Snapshot -1 is the initial state, always available.  Actions, in
+// order:
+//   kAdvance: run units [u0, u1) from snapshot `from` (holding the state at u0) and store the
+//             state at u1 in snapshot `to`;
+//   kReverse: run unit u0 from snapshot `from` keeping its stage values, then reverse it.
+// Units are reversed last to first.  With c free snapshots and n units the least r with
+// C(c + r, c) >= n is taken: the head of the range is advanced to a snapshot, the tail
+// (C(c - 1 + r, c - 1) units at most) reversed with c - 1 snapshots, then the head with c.
+// Returns false if the units cannot be reversed (no snapshot for a range of two units or more).
+struct RevolveAction {
+    enum Kind { kAdvance, kReverse } kind;
+    int u0, u1, from, to;
+};
+bool revolve_schedule(int units, int snaps, std::vector<RevolveAction> *out);
+
 }  // namespace fvlbm

@@ -7,7 +7,8 @@ with g++ from the library's own host sources compares those derivatives with cen
 differences of the double-precision preprocessing, for an interior node of a jittered cavity
 and for a wall node of an airfoil C-mesh (where the wall distance and the boundary normals
 move too).  A second one checks the adjoint's reverse-mode geometry (geometry_adjoint) against
-that forward mode by the dot-product identity <A, J v> = <J^T A, v> for random A and v."""
+that forward mode by the dot-product identity <A, J v> = <J^T A, v> for random A and v, and a
+third the adjoint's binomial checkpoint schedule (revolve_schedule)."""
 import os
 import shutil
 import struct
@@ -111,3 +112,23 @@ def test_geometry_adjoint_dot_product(adjoint_checker, tmp_path, which):
     out = {ln.split()[0]: float(ln.split()[1]) for ln in res.splitlines()}
     assert abs(out["forward"]) > 0
     assert abs(out["forward"] - out["reverse"]) <= 1e-10 * abs(out["forward"]), out
+
+
+def test_revolve_schedule(tmp_path):
+    """The adjoint's binomial checkpoint schedule (host code): every unit reversed once, last to
+    first, from a snapshot holding its start; snapshot indices within the count; forward work
+    within (r + 1) units; refused without snapshots for two units or more.  Pass counts of a few
+    cases pin the schedule (17 units with a snapshot each: 2 x 17 - 1)."""
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    exe = str(tmp_path / "revolve_check")
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-fopenmp", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
+                           os.path.join(HERE, "native", "revolve_check.cpp"),
+                           os.path.join(CSRC, "fvlbm_host.cpp"), "-o", exe])
+    res = subprocess.run([exe], capture_output=True, text=True)
+    assert res.returncode == 0, res.stdout
+    passes = {(int(a), int(b)): int(c) for _, a, b, c in
+              (ln.split() for ln in res.stdout.splitlines() if ln.startswith("passes"))}
+    assert passes[(17, 16)] == 33
+    assert passes[(100, 3)] == 595
+    assert passes[(1000, 5)] == 7368
