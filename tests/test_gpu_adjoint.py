@@ -642,3 +642,20 @@ def test_adjoint_explicit_euler_scheme_against_tangent(name):
     t.close()
     dJv = W[0] * dv["cd"] + W[1] * dv["cl"]
     assert abs(float(np.sum(dxy * v)) - dJv) <= 1e-8 * abs(dJv), (float(np.sum(dxy * v)), dJv)
+
+
+@pytest.mark.parametrize("sst", [False, True])
+def test_adjoint_of_a_fused_path_handle(sst):
+    """A handle that steps with the fused kernels (the default) gives the same gradient as one
+    that steps with the two-pass kernels: the adjoint recomputes with the two-pass step from the
+    handle's state, and the two paths' states agree to rounding."""
+    case = _naca_sst() if sst else _naca_laminar()
+    out = []
+    for path in (0, 1):
+        s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=path)
+        s.step(8)
+        out.append(s.adjoint(10, *W, shape=True))
+        s.close()
+    assert abs(out[0][0] - out[1][0]) <= 1e-12 * abs(out[1][0])
+    for a, b in zip(out[0][1:], out[1][1:]):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max()
