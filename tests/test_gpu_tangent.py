@@ -329,3 +329,37 @@ def test_forces_gradient_many_directions_in_one_batch():
     fm = _gpu_forces(_moved(base, dirs[5]["dxy"], -h, dt), steps)
     fd = (fp["cl"] - fm["cl"]) / (2 * h)
     assert abs(grads[5]["cl"] - fd) <= 1e-4 * abs(fd) + 1e-9
+
+
+@pytest.mark.parametrize("name", ["cavity", "bfs_sst", "naca_sst"])
+def test_tangent_against_oracle_complex_step(name):
+    """The tangent (dual numbers on the GPU) against the oracle's own tangent (its source in
+    complex arithmetic on the CPU) along one random seed of f^0 and of the boundary values, on
+    tiny meshes: d(C_D, C_L)/dp after 10 steps to 1e-8 and the values to 1e-10, both relative to
+    the larger of the two coefficients."""
+    case = {"cavity": lambda: mg.cavity_quad(12, re=400.0, jitter=0.2, seed=7),
+            "bfs_sst": lambda: mg.bfs_hybrid(n_target=800),
+            "naca_sst": lambda: mg.naca0012_cmesh(n_target=800, alpha_deg=3.0)}[name]()
+    m = case.mesh.normalized()
+    rng = np.random.default_rng(5)
+    t = fvlbm.Solver(case, precision=TAN, device=0)
+    f0 = t.get_f()
+    g = 1e-3 * rng.standard_normal(f0.shape)
+    d = np.zeros((m.n_bedges, 5))
+    d[:, :3] = 1e-2 * rng.standard_normal((m.n_bedges, 3))
+    d[:, 3:] = 1e-3 * m.bedge_val[:, 3:] * rng.standard_normal((m.n_bedges, 2))
+    t.tangent_seed(d, g)
+    t.step(10)
+    val, dv = t.forces_tangent(dalpha=0.0)
+    t.close()
+    o = Oracle(case, complex_step=True)
+    o.cs_seed(d, g)
+    o.step(10)
+    ov, od = o.cs_forces()
+    # relative to the larger coefficient: the cavity's C_L is a 1e-7 remainder of cancelling
+    # wall forces, so its own size is no scale for rounding
+    sv = max(abs(ov["cd"]), abs(ov["cl"]))
+    sd = max(abs(od["cd"]), abs(od["cl"]))
+    for key in ("cd", "cl"):
+        assert abs(val[key] - ov[key]) <= 1e-10 * sv, key
+        assert abs(dv[key] - od[key]) <= 1e-8 * sd, (key, dv[key], od[key])
