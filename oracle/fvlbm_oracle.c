@@ -31,7 +31,8 @@
  *
  * Built with ORACLE_COMPLEX_STEP, the same source is the oracle's own tangent (complex-step
  * method, see `real` below); its real parts equal the double build's values exactly, and its
- * derivatives are pinned against central differences of the double build on a laminar case.
+ * derivatives are pinned against central differences of the double build (laminar cavity; SST
+ * step and airfoil from a developed state).
  */
 #include <math.h>
 #include <stdlib.h>
