@@ -22,6 +22,10 @@ Two backward passes compute the same derivatives of the discrete step:
     and lift directions on alpha.  Its cost does not grow with the number of parameters.  It
     covers every reading variant.
 The default ("auto") takes the adjoint.
+
+``step_forces(model, f0, bval, xy)`` (with a ``StepForces`` model) is the full-input form:
+(C_D, C_L) as a function of the initial distributions, every boundary value and every node
+position, with a one-adjoint backward pass.
 """
 from __future__ import annotations
 
