@@ -272,14 +272,15 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
 /* ---------------------------------------------------------------------------------------------
  * Discrete adjoint (reverse mode; no counterpart in the paper, which its conclusion's design use
  * of the solver motivates like the tangent above).  One call gives the gradient of one scalar
- * objective with respect to every cell's initial distributions and every boundary value, where
- * the tangent needs one run per input direction.
+ * objective with respect to every cell's initial distributions, every boundary value and every
+ * node position, where the tangent needs one run per input direction.
  *
  *   J = w[0] C_D + w[1] C_L of `instance` after n_steps steps from the handle's current state,
  *
- * C_D, C_L as fvlbm_forces.  The step differentiated is the IMEX step of Sec. 3.1-3.2 (Steps 1-7:
- * the k-omega SST solve on SST instances, then the stages), with one dt per instance or local
- * time steps, as the two-pass kernels run it in FP64 (the fused kernels give the same values up to rounding).
+ * C_D, C_L as fvlbm_forces.  The step differentiated is the handle's step (Sec. 3.1-3.2, Steps
+ * 1-7: the k-omega SST solve on SST instances, then the IMEX stages, or the explicit Euler
+ * update), with one dt per instance or local time steps, as the two-pass kernels run it in FP64
+ * (the fused kernels give the same values up to rounding).
  * Where the step is not differentiable (the upwind switch on e.n = 0, the SST's limiter, clip
  * and blending branches) the derivative of the branch the value takes is used, as in the
  * tangent.
@@ -294,8 +295,8 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
  *                  centroids, face offsets, least-squares weights, the wall normals and lengths
  *                  of the force): the gradient whose inner product with a node displacement is
  *                  what fvlbm_tangent_seed_nodes gives for it; on SST instances also through
- *                  1/|d| and the wall distance d.  Not for meshes with periodic pairs
- *                  (FVLBM_ERR_NOT_SUPPORTED).
+ *                  1/|d| and the wall distance d, and with the limiter on grad f through the
+ *                  cell areas.  Not for meshes with periodic pairs (FVLBM_ERR_NOT_SUPPORTED).
  * The initial k, omega and nu_t of SST instances are held fixed (their adjoints are not output).
  * Neither the state nor the step count of the handle changes.  The call runs n_steps forward
  * steps that keep their stage values (99 doubles per cell and step, 119 with SST, 153 under the
