@@ -108,3 +108,16 @@ def test_rejects_polygon_with_five_nodes():
     m = mg.Mesh(xy, np.array([0, 5], np.int32), cells, bn, np.zeros(5, np.int32),
                 np.tile([1.0, 0, 0, 0, 0], (5, 1)))
     assert _create(mg.Case(m, nu=1e-3, dt=1e-3)) == -1
+
+
+def test_derivative_entry_points_reject_a_null_handle():
+    """The adjoint and tangent entry points check their handle before any device work."""
+    lib = fvlbm.load()
+    w = np.array([1.0, 0.0])
+    out = np.zeros(4)
+    assert lib.fvlbm_adjoint(None, 0, 1, w.ctypes.data_as(C.c_void_p), None, None, None, None) \
+        == fvlbm.FVLBM_ERR_BAD_PARAM
+    assert lib.fvlbm_set_adjoint_budget(None, 0) == fvlbm.FVLBM_ERR_BAD_PARAM
+    assert lib.fvlbm_forces_tangent(None, 0, 0.0, out.ctypes.data_as(C.c_void_p),
+                                    out.ctypes.data_as(C.c_void_p)) == fvlbm.FVLBM_ERR_BAD_PARAM
+    assert lib.fvlbm_tangent_seed(None, 0, None, None) == fvlbm.FVLBM_ERR_BAD_PARAM
