@@ -153,6 +153,35 @@ int fvlbm_create_batch(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs,
                        const fvlbm_params *params, int device, void *stream,
                        fvlbm_handle **out);
 
+/* Validate one (mesh, bc, params) triple on the host alone: no GPU, no CUDA call, nothing
+ * allocated on a device.  It runs the host preprocessing of fvlbm_create, then checks the
+ * result.
+ *
+ * What the preprocessing validates:
+ *   - the mesh and boundary records;
+ *   - periodic pairs: edge b must be edge a moved by the shift, to 1e-8 of its length;
+ *   - the geometry and the least-squares stencils;
+ *   - the renumbering and the time step.
+ *
+ * What the checks on its result cover.  fvlbm_create runs the same checks on every instance.
+ *   - Every index the kernels gather through is in range: neighbours, back slots, boundary
+ *     faces and their owners.
+ *   - The face links are mutual.
+ *   - The padding cells are inert.
+ *   - Every geometry array agrees with the node positions and, across each face, with the
+ *     neighbour's: n dl, face midpoints, centroid offsets, 1/|d|.
+ *   - The least-squares weights satisfy sum_m W_m d_m^T = I.
+ *
+ * Arguments:
+ *   - dt (may be NULL) receives the instance's time step: the given dt, or the CFL step.
+ *   - why (may be NULL) receives a NUL-terminated message, at most why_len bytes: empty on
+ *     success.
+ *
+ * Returns FVLBM_OK, or the code fvlbm_create would return for the same input: BAD_MESH,
+ * BAD_BC or BAD_PARAM. */
+int fvlbm_check_mesh(const fvlbm_mesh *mesh, const fvlbm_bc *bc, const fvlbm_params *params,
+                     double *dt, char *why, int why_len);
+
 /* Advance n_steps time steps (Steps 1-7 of Sec. 3.2 each), asynchronously on the handle's
  * stream.  The steps are replayed from a captured CUDA graph.  When `stats` is non-NULL the
  * call synchronises and fills it (FP64 residual of the last step, mass, NaN watchdog) and

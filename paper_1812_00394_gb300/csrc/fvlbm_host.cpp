@@ -176,6 +176,16 @@ int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_para
         const double sx = bc.periodic_shift[2 * q], sy = bc.periodic_shift[2 * q + 1];
         FaceGeo<S> &A = face[4 * static_cast<size_t>(bside[ea].cell) + bside[ea].local];
         FaceGeo<S> &B = face[4 * static_cast<size_t>(bside[eb].cell) + bside[eb].local];
+        // edge b must be edge a moved by the shift (traversed the other way by its cell): same
+        // length, opposite normals, midpoints one shift apart
+        const double la = value_of(A.len), lb = value_of(B.len);
+        const double ex = value_of(B.xm) - sx - value_of(A.xm), ey = value_of(B.ym) - sy - value_of(A.ym);
+        const double nx = value_of(A.nx) + value_of(B.nx), ny = value_of(A.ny) + value_of(B.ny);
+        if (!(std::fabs(la - lb) <= 1e-8 * (la + lb) && std::hypot(ex, ey) <= 1e-8 * (la + lb) &&
+              std::hypot(nx, ny) <= 1e-8)) {
+            *why = "periodic pair " + std::to_string(q) + ": edge b is not edge a moved by the shift";
+            return FVLBM_ERR_BAD_BC;
+        }
         A.nbr = bside[eb].cell;
         A.back = bside[eb].local;
         A.sx = -sx;
@@ -412,7 +422,7 @@ int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_para
         if (p.k_init) P.k_i[k] = p.k_init[i];
         if (p.omega_init) P.w_i[k] = p.omega_init[i];
     }
-    return FVLBM_OK;
+    return check_prepared(P, why);
 }
 
 namespace {
@@ -669,9 +679,193 @@ bool revolve_schedule(int units, int snaps, std::vector<RevolveAction> *out)
     return revolve_rec(0, units, -1, 0, snaps, out);
 }
 
+template <class S>
+int check_prepared(const PreparedT<S> &P, std::string *why) {
+    auto fail = [why](int code, const std::string &msg) {
+        *why = "preprocessing check: " + msg;
+        return code;
+    };
+    auto at = [](int k, int m) { return "cell " + std::to_string(k) + " face " + std::to_string(m); };
+    const int nc = P.nc, nb = P.nb;
+    const size_t np = static_cast<size_t>(P.np), unb = static_cast<size_t>(nb);
+    if (nc <= 0 || P.np < nc || P.np % kBlock != 0 || P.np - nc >= kBlock || nb < 0)
+        return fail(FVLBM_ERR_BAD_MESH, "cell or face counts");
+    const size_t n4 = 4 * np, n8 = 8 * np;
+    if (P.perm.size() != static_cast<size_t>(nc) || P.nbr.size() != n4 || P.back.size() != n4 ||
+        P.nface.size() != np || P.gq.size() != n8 || P.sn.size() != n8 || P.lsq.size() != n8 ||
+        P.dvec.size() != n8 || P.rown.size() != n8 || P.rnbr.size() != n8 || P.dinv.size() != n4 ||
+        P.area.size() != np || P.wdist.size() != np || P.bowner.size() != unb ||
+        P.btype.size() != unb || P.bval.size() != 5 * unb || P.bnrm.size() != 2 * unb ||
+        P.blen.size() != unb || P.bedge_of.size() != unb ||
+        !(P.dt_cell.empty() || P.dt_cell.size() == np) || P.rho_i.size() != np ||
+        P.u_i.size() != np || P.v_i.size() != np || P.k_i.size() != np || P.w_i.size() != np)
+        return fail(FVLBM_ERR_BAD_MESH, "array sizes");
+    std::vector<char> seen(nc, 0);
+    for (int k = 0; k < nc; ++k) {
+        const int i = P.perm[k];
+        if (i < 0 || i >= nc || seen[i]) return fail(FVLBM_ERR_BAD_MESH, "cell order is not a permutation");
+        seen[i] = 1;
+    }
+    for (int f = 0; f < nb; ++f) {
+        if (P.bedge_of[f] < 0 || P.bedge_of[f] >= P.n_bedges_in || (f > 0 && P.bedge_of[f] <= P.bedge_of[f - 1]))
+            return fail(FVLBM_ERR_BAD_BC, "boundary face " + std::to_string(f) + ": input edge index");
+        if (P.btype[f] < FVLBM_BC_WALL || P.btype[f] >= FVLBM_BC_PERIODIC)
+            return fail(FVLBM_ERR_BAD_BC, "boundary face " + std::to_string(f) + ": type");
+    }
+    // Connectivity: every index a kernel gathers through is in range, interior links are mutual
+    // (the neighbour's slot `back` points back here), every boundary face is one cell face of its
+    // owner, slots past a cell's faces and the padding cells are empty.
+    std::vector<long long> bslot(unb, -1);
+    for (size_t k = 0; k < np; ++k) {
+        const int nf = P.nface[k];
+        const double A = value_of(P.area[k]);
+        if (k >= static_cast<size_t>(nc)) {
+            if (nf != 0 || A != 0.0) return fail(FVLBM_ERR_BAD_MESH, "padding cell " + std::to_string(k) + " is not inert");
+        } else if (nf != 3 && nf != 4) {
+            return fail(FVLBM_ERR_BAD_MESH, "cell " + std::to_string(k) + ": face count");
+        } else if (!(A > 0.0 && std::isfinite(A))) {
+            return fail(FVLBM_ERR_BAD_MESH, "cell " + std::to_string(k) + ": area");
+        }
+        for (int m = 0; m < 4; ++m) {
+            const size_t s = static_cast<size_t>(m) * np + k;
+            const int v = P.nbr[s], b = P.back[s];
+            if (m >= nf) {
+                if (v != kNone || b != -1) return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": slot past the faces is not empty");
+                continue;
+            }
+            if (v >= 0) {
+                if (v >= nc || b < 0 || b >= P.nface[v] || P.nbr[static_cast<size_t>(b) * np + v] != static_cast<int>(k) ||
+                    P.back[static_cast<size_t>(b) * np + v] != m)
+                    return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": neighbour link is not mutual");
+            } else if (v == kNone) {
+                return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": open face");
+            } else {
+                const int f = -(v + 1);
+                if (f >= nb || b != -1 || P.bowner[f] != static_cast<int>(k) || bslot[f] >= 0)
+                    return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": boundary face link");
+                bslot[f] = static_cast<long long>(s);
+            }
+        }
+    }
+    for (int f = 0; f < nb; ++f)
+        if (bslot[f] < 0) return fail(FVLBM_ERR_BAD_MESH, "boundary face " + std::to_string(f) + " is no cell face");
+    // Geometry: the arrays agree with the node positions (gq) and with each other across every
+    // face.  Tolerances are relative (1e-6) and far above rounding on cells down to 1e-6 of the
+    // domain; a wrong slot, sign or operand misses them by O(1).
+    constexpr double tol = 1e-6;
+    auto V = [np](const std::vector<S> &a, int c, size_t k) { return value_of(a[static_cast<size_t>(c) * np + k]); };
+    for (int k = 0; k < nc; ++k) {
+        const int nf = P.nface[k];
+        const double A = value_of(P.area[k]);
+        double gx[4], gy[4], h = 0.0;
+        for (int m = 0; m < nf; ++m) {
+            gx[m] = V(P.gq, 2 * m, k);
+            gy[m] = V(P.gq, 2 * m + 1, k);
+            if (!(std::isfinite(gx[m]) && std::isfinite(gy[m]))) return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": node position");
+            h = std::max(h, std::hypot(gx[m], gy[m]));
+        }
+        double a2 = 0.0, mx = 0.0, my = 0.0;  // shoelace area and first moment about the centroid
+        for (int m = 0; m < nf; ++m) {
+            const int m1 = (m + 1) % nf;
+            const double c = gx[m] * gy[m1] - gx[m1] * gy[m];
+            a2 += c;
+            mx += (gx[m] + gx[m1]) * c;
+            my += (gy[m] + gy[m1]) * c;
+        }
+        if (!(std::fabs(0.5 * a2 - A) <= tol * A))
+            return fail(FVLBM_ERR_BAD_MESH, "cell " + std::to_string(k) + ": area disagrees with the nodes");
+        if (!(std::hypot(mx, my) <= tol * h * 3.0 * a2))
+            return fail(FVLBM_ERR_BAD_MESH, "cell " + std::to_string(k) + ": nodes are not relative to the centroid");
+        double E[2][2] = {{0.0, 0.0}, {0.0, 0.0}}, T[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+        for (int m = 0; m < nf; ++m) {
+            const int m1 = (m + 1) % nf;
+            const double tx = gx[m1] - gx[m], ty = gy[m1] - gy[m], L = std::hypot(tx, ty);
+            const double nlx = V(P.sn, 2 * m, k) * A, nly = V(P.sn, 2 * m + 1, k) * A;
+            if (!(std::hypot(nlx - ty, nly + tx) <= tol * L))
+                return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": n dl is not the outward normal of the edge");
+            const double rx = V(P.rown, 2 * m, k), ry = V(P.rown, 2 * m + 1, k);
+            if (!(std::hypot(rx - 0.5 * (gx[m] + gx[m1]), ry - 0.5 * (gy[m] + gy[m1])) <= tol * h))
+                return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": face midpoint");
+            const double dx = V(P.dvec, 2 * m, k), dy = V(P.dvec, 2 * m + 1, k), d = std::hypot(dx, dy);
+            const double qx = V(P.rnbr, 2 * m, k), qy = V(P.rnbr, 2 * m + 1, k);
+            const double di = value_of(P.dinv[static_cast<size_t>(m) * np + k]);
+            if (!(d > 0.0 && std::isfinite(d) && std::fabs(di * d - 1.0) <= 1e-12))
+                return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": centroid offset or 1/|d|");
+            const int v = P.nbr[static_cast<size_t>(m) * np + k];
+            if (v < 0) {  // boundary face: d is the offset to the face midpoint
+                if (dx != rx || dy != ry || qx != 0.0 || qy != 0.0)
+                    return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": boundary face offsets");
+                const int f = -(v + 1);
+                const double bl = value_of(P.blen[f]), bx = value_of(P.bnrm[2 * f]), by = value_of(P.bnrm[2 * f + 1]);
+                if (!(std::fabs(std::hypot(bx, by) - 1.0) <= 1e-12 && std::hypot(bx * bl - nlx, by * bl - nly) <= tol * L))
+                    return fail(FVLBM_ERR_BAD_MESH, "boundary face " + std::to_string(f) + ": normal or length");
+            } else {  // interior (or periodic) face, seen again from the neighbour's slot b
+                const int b = P.back[static_cast<size_t>(m) * np + k];
+                const double Av = value_of(P.area[v]);
+                const double vx = V(P.dvec, 2 * b, v), vy = V(P.dvec, 2 * b + 1, v);
+                const double ox = V(P.rown, 2 * b, v), oy = V(P.rown, 2 * b + 1, v);
+                const double wx = V(P.sn, 2 * b, v) * Av, wy = V(P.sn, 2 * b + 1, v) * Av;
+                if (!(std::hypot(dx + vx, dy + vy) <= tol * d))
+                    return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": d is not the reverse of the neighbour's");
+                if (!(std::hypot(qx - ox, qy - oy) <= tol * (std::hypot(qx, qy) + std::hypot(ox, oy))) ||
+                    !(std::hypot(dx - (rx - qx), dy - (ry - qy)) <= tol * (std::hypot(rx, ry) + std::hypot(qx, qy))))
+                    return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": neighbour-side face offset");
+                if (!(std::hypot(nlx + wx, nly + wy) <= tol * L))
+                    return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": n dl is not the reverse of the neighbour's");
+            }
+            const double w[2] = {V(P.lsq, 2 * m, k), V(P.lsq, 2 * m + 1, k)}, dd[2] = {dx, dy};
+            for (int a = 0; a < 2; ++a)
+                for (int c = 0; c < 2; ++c) {
+                    E[a][c] += w[a] * dd[c];
+                    T[a][c] += std::fabs(w[a] * dd[c]);
+                }
+        }
+        // least-squares weights W_m = M^{-1} d_m reproduce linear fields: sum_m W_m d_m^T = I
+        for (int a = 0; a < 2; ++a)
+            for (int c = 0; c < 2; ++c)
+                if (!(std::fabs(E[a][c] - (a == c ? 1.0 : 0.0)) <= tol * std::max(T[a][c], 1.0)))
+                    return fail(FVLBM_ERR_BAD_MESH, "cell " + std::to_string(k) + ": least-squares weights");
+        const double wd = value_of(P.wdist[k]);
+        if (!(wd >= 0.0 && wd <= 1e30)) return fail(FVLBM_ERR_BAD_MESH, "cell " + std::to_string(k) + ": wall distance");
+    }
+    if (!(P.dt > 0.0 && std::isfinite(P.dt))) return fail(FVLBM_ERR_BAD_PARAM, "time step");
+    for (double t : P.dt_cell)
+        if (!(t > 0.0 && std::isfinite(t))) return fail(FVLBM_ERR_BAD_PARAM, "local time step");
+    return FVLBM_OK;
+}
+
 template int prepare_instance_t<double>(const fvlbm_mesh &, const fvlbm_bc &, const fvlbm_params &,
                                         const double *, PreparedT<double> *, std::string *);
 template int prepare_instance_t<Dual>(const fvlbm_mesh &, const fvlbm_bc &, const fvlbm_params &,
                                       const Dual *, PreparedT<Dual> *, std::string *);
+template int check_prepared<double>(const PreparedT<double> &, std::string *);
+template int check_prepared<Dual>(const PreparedT<Dual> &, std::string *);
 
 }  // namespace fvlbm
+
+extern "C" int fvlbm_check_mesh(const fvlbm_mesh *mesh, const fvlbm_bc *bc, const fvlbm_params *params,
+                                double *dt, char *why, int why_len) {
+    std::string msg;
+    int rc = FVLBM_OK;
+    if (!mesh || !bc || !params) {
+        rc = FVLBM_ERR_BAD_PARAM;
+        msg = "NULL argument";
+    } else if (params->precision != FVLBM_FP64 && params->precision != FVLBM_FP32_DEV &&
+               params->precision != FVLBM_FP64_TANGENT) {
+        rc = FVLBM_ERR_BAD_PARAM;
+        msg = "unknown precision";
+    } else if (params->scheme != 0 && params->scheme != 1) {
+        rc = FVLBM_ERR_BAD_PARAM;
+        msg = "unknown scheme";
+    } else {
+        fvlbm::Prepared P;
+        rc = fvlbm::prepare_instance(*mesh, *bc, *params, &P, &msg);
+        if (rc == FVLBM_OK && dt) *dt = P.dt;
+    }
+    if (why && why_len > 0) {
+        const size_t n = std::min(msg.size(), static_cast<size_t>(why_len - 1));
+        std::memcpy(why, msg.data(), n);
+        why[n] = '\0';
+    }
+    return rc;
+}

@@ -75,6 +75,16 @@ extern template int prepare_instance_t<Dual>(const fvlbm_mesh &, const fvlbm_bc 
                                              const fvlbm_params &, const Dual *, PreparedT<Dual> *,
                                              std::string *);
 
+// Consistency checks on a prepared instance, run at the end of prepare_instance_t: every index
+// the kernels gather through is in range (neighbours, back slots, boundary faces, owners), the
+// face links are mutual, padding cells are inert, and the geometry arrays agree with the node
+// positions and with each other across every face (n dl, midpoints, centroid offsets, 1 / |d|,
+// sum_m W_m d_m^T = I).  Returns FVLBM_OK or an error code with a message in *why.
+template <class S>
+int check_prepared(const PreparedT<S> &P, std::string *why);
+extern template int check_prepared<double>(const PreparedT<double> &, std::string *);
+extern template int check_prepared<Dual>(const PreparedT<Dual> &, std::string *);
+
 inline int prepare_instance(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_params &p,
                             Prepared *out, std::string *why) {
     return prepare_instance_t<double>(m, bc, p, m.xy, out, why);

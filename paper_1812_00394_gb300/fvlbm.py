@@ -15,7 +15,11 @@ import numpy as np
 from . import build as _build
 
 FVLBM_OK = 0
+FVLBM_ERR_BAD_MESH = -1
+FVLBM_ERR_BAD_BC = -2
 FVLBM_ERR_BAD_PARAM = -3
+FVLBM_ERR_OOM = -4
+FVLBM_ERR_CUDA = -5
 FVLBM_ERR_DIVERGED = -6
 FVLBM_ERR_NOT_SUPPORTED = -7
 FVLBM_FP64 = 0
@@ -64,7 +68,8 @@ EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "
            "fvlbm_get_f_tangent", "fvlbm_forces_tangent", "fvlbm_adjoint",
            "fvlbm_set_adjoint_budget", "fvlbm_state_bytes", "fvlbm_save_state",
            "fvlbm_load_state", "fvlbm_set_rollback", "fvlbm_set_f_async",
-           "fvlbm_get_fields_async", "fvlbm_wait", "fvlbm_get_fdev_f32", "fvlbm_set_fdev_f32_async"]
+           "fvlbm_get_fields_async", "fvlbm_wait", "fvlbm_get_fdev_f32", "fvlbm_set_fdev_f32_async",
+           "fvlbm_check_mesh"]
 
 _lib = None
 
@@ -117,6 +122,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_strerror.argtypes = [i]
     lib.fvlbm_strerror.restype = C.c_char_p
     lib.fvlbm_stats_reduce_static.argtypes = [vp] * 6 + [i, vp, vp]
+    lib.fvlbm_check_mesh.argtypes = [P(fvlbm_mesh), P(fvlbm_bc), P(fvlbm_params), P(d), C.c_char_p, i]
     for name in EXPORTS:
         if name not in ("fvlbm_destroy", "fvlbm_strerror"):
             getattr(lib, name).restype = i
@@ -148,6 +154,14 @@ def fvlbm_create(mesh: fvlbm_mesh, bc: fvlbm_bc, params: fvlbm_params, device: i
     _check(load().fvlbm_create(C.byref(mesh), C.byref(bc), C.byref(params), device,
                                C.c_void_p(stream) if stream else None, C.byref(h)), "fvlbm_create")
     return h
+
+
+def fvlbm_check_mesh(mesh: fvlbm_mesh, bc: fvlbm_bc, params: fvlbm_params) -> tuple[int, float, str]:
+    """(return code, time step, message) of the host-only validation; no GPU is touched."""
+    dt = C.c_double(0.0)
+    why = C.create_string_buffer(512)
+    rc = load().fvlbm_check_mesh(C.byref(mesh), C.byref(bc), C.byref(params), C.byref(dt), why, 512)
+    return rc, dt.value, why.value.decode()
 
 
 def fvlbm_create_batch(meshes, bcs, params, device: int = -1, stream: int | None = None):
@@ -367,6 +381,13 @@ class _Pack:
                                    _p(v), _p(k), _p(w), kernel_path, scheme,
                                    int(bool(getattr(case, "local_dt", False))),
                                    int(getattr(case, "variant", 0)))
+
+
+def check_case(case, precision: int = FVLBM_FP64, kernel_path: int = 0,
+               scheme: int = 0) -> tuple[int, float, str]:
+    """``fvlbm_check_mesh`` on a ``meshgen.Case``: (return code, time step, message)."""
+    pk = _Pack(case, precision, kernel_path, scheme)
+    return fvlbm_check_mesh(pk.mesh, pk.bc, pk.params)
 
 
 class Solver:
