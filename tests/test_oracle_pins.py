@@ -265,6 +265,38 @@ def test_sst_point_limits():
     assert abs(pos["cdkw"] - 2 * 0.856 / 10.0 * 2.0) < 1e-15
 
 
+def test_sst_point_values_with_each_branch_active():
+    """Blending functions and eddy viscosity of Sec. 2 at points built so that each branch of
+    arg1 = min(max(a, b), c) is the active one in turn, with round numbers:
+      - a = sqrt(k) / (beta* omega d) = 0.9 / 1.8 = 0.5, the turbulent length-scale ratio;
+      - b = 500 nu / (omega d^2) = 0.5, the viscous ratio;
+      - c = 4 sigma_w2 k / (CD d^2) = 0.25 with CD = 2 sigma_w2 grad k . grad omega / omega.
+    So f1 = tanh(arg1^4) and f2 = tanh(arg2^2), with arg2 = max(2a, b), are tanh of 1/16,
+    1/256, 1/4 or 1.  nu_t = a1 k / max(a1 omega, S f2) is k / omega unless the strain term is
+    larger.  A wrong constant (0.09, 500, 0.856, 0.31), power or factor 2 moves a value by far
+    more than the rounding of these few operations."""
+    nu, rel = 1e-5, 1e-13
+
+    def close(x, y):
+        return abs(x - y) <= rel * abs(y)
+
+    # a active: k = 0.81, omega = 10, d = 2 -> a = 0.5, b = 1.25e-4, c = inf (CD at its floor)
+    A = sst_point(0.81, 10.0, 2.0, (0, 0), (0, 0), 0.0, nu)
+    assert close(A["f1"], math.tanh(0.5 ** 4)) and close(A["f2"], math.tanh(1.0))
+    assert close(A["nut"], 0.081) and A["cdkw"] == 1e-20
+    # b active: nu = 1e-4, omega = 10, d = 0.1 -> b = 0.5; k = 8.1e-5 -> a = 0.1, arg2 = 0.5
+    B = sst_point(8.1e-5, 10.0, 0.1, (0, 0), (0, 0), 0.0, 1e-4)
+    assert close(B["f1"], math.tanh(0.5 ** 4)) and close(B["f2"], math.tanh(0.25))
+    # c active: the point of A with grad k = (1.8, 0), grad omega = (9, 0):
+    # CD = 2 (0.856) (16.2) / 10 = 2.77344 and c = 4 (0.856) (0.81) / (2.77344 * 4) = 0.25
+    C = sst_point(0.81, 10.0, 2.0, (1.8, 0.0), (9.0, 0.0), 0.0, nu)
+    assert close(C["cdkw"], 2.77344)
+    assert close(C["f1"], math.tanh(0.25 ** 4)) and close(C["f2"], math.tanh(1.0))
+    # strain-limited eddy viscosity: S f2 = 10 tanh(1) > a1 omega = 3.1
+    D = sst_point(0.81, 10.0, 2.0, (0, 0), (0, 0), 10.0, nu)
+    assert close(D["nut"], 0.31 * 0.81 / (10.0 * math.tanh(1.0)))
+
+
 def test_sst_homogeneous_decay():
     """Homogeneous, unstrained turbulence far from walls: d omega/dt = -beta2 omega^2 and
     dk/dt = -beta* omega k, with closed forms omega = w0/(1 + beta2 w0 t) and
