@@ -148,11 +148,25 @@ def _p(a):
 
 
 # ------------------------------------------------------------------ C-named wrappers
+def _create_failed(rc: int, what: str, triples) -> None:
+    """Raise FvlbmError for a failed create; for an input error the message names the first
+    instance that fvlbm_check_mesh refuses and its reason."""
+    if rc in (FVLBM_ERR_BAD_MESH, FVLBM_ERR_BAD_BC, FVLBM_ERR_BAD_PARAM):
+        for i, (m, b, p) in enumerate(triples):
+            rc_i, _, why = fvlbm_check_mesh(m, b, p)
+            if rc_i < 0:
+                what = f"{what}: instance {i}: {why}"
+                break
+    raise FvlbmError(rc, what)
+
+
 def fvlbm_create(mesh: fvlbm_mesh, bc: fvlbm_bc, params: fvlbm_params, device: int = -1,
                  stream: int | None = None) -> C.c_void_p:
     h = C.c_void_p()
-    _check(load().fvlbm_create(C.byref(mesh), C.byref(bc), C.byref(params), device,
-                               C.c_void_p(stream) if stream else None, C.byref(h)), "fvlbm_create")
+    rc = load().fvlbm_create(C.byref(mesh), C.byref(bc), C.byref(params), device,
+                             C.c_void_p(stream) if stream else None, C.byref(h))
+    if rc < 0:
+        _create_failed(rc, "fvlbm_create", [(mesh, bc, params)])
     return h
 
 
@@ -170,8 +184,10 @@ def fvlbm_create_batch(meshes, bcs, params, device: int = -1, stream: int | None
     B = (fvlbm_bc * n)(*bcs)
     Pm = (fvlbm_params * n)(*params)
     h = C.c_void_p()
-    _check(load().fvlbm_create_batch(n, M, B, Pm, device, C.c_void_p(stream) if stream else None,
-                                     C.byref(h)), "fvlbm_create_batch")
+    rc = load().fvlbm_create_batch(n, M, B, Pm, device, C.c_void_p(stream) if stream else None,
+                                   C.byref(h))
+    if rc < 0:
+        _create_failed(rc, "fvlbm_create_batch", list(zip(meshes, bcs, params)))
     return h
 
 

@@ -170,3 +170,21 @@ def test_error_codes_match_create():
     # fvlbm_create checks the scheme after it has selected the device; the host check alone
     pack = fvlbm._Pack(mg.Case(m, nu=1e-3, dt=1e-3), fvlbm.FVLBM_FP64, scheme=3)
     assert fvlbm.fvlbm_check_mesh(pack.mesh, pack.bc, pack.params)[0] == fvlbm.FVLBM_ERR_BAD_PARAM
+
+
+def test_create_error_names_the_instance_and_reason():
+    """A refused create raises FvlbmError with the code, the failing instance and the reason that
+    the host validation gives (no device work happens before the refusal)."""
+    m = mg.cavity_quad(4).mesh
+    cw = m.cell_nodes.copy().reshape(-1, 4)
+    cw[5] = cw[5][::-1]
+    bad = mg.Case(mg.Mesh(m.xy, m.cell_ptr, cw.ravel(), m.bedge_nodes, m.bedge_type, m.bedge_val),
+                  nu=1e-3, dt=1e-3)
+    with pytest.raises(fvlbm.FvlbmError) as e:
+        fvlbm.Solver(bad, precision=fvlbm.FVLBM_FP64, device=0)
+    assert e.value.code == fvlbm.FVLBM_ERR_BAD_MESH
+    assert "instance 0" in str(e.value) and "non-positive area" in str(e.value)
+    good = mg.Case(m, nu=1e-3, dt=1e-3)
+    with pytest.raises(fvlbm.FvlbmError) as e:
+        fvlbm.Solver([good, bad], precision=fvlbm.FVLBM_FP64, device=0)
+    assert e.value.code == fvlbm.FVLBM_ERR_BAD_MESH and "instance 1" in str(e.value)
