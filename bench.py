@@ -156,8 +156,21 @@ def run_reference(args):
     picks = _sample_indices(cases)
     from oracle.oracle import Oracle
     oracles = [Oracle(cases[i]) for i in picks]
+    # the first warm-up step times each sampled instance; the largest are dropped until the
+    # remaining steps fit the time budget (one instance stays)
+    cost = []
+    for o in oracles:
+        t0 = time.perf_counter()
+        o.step(1)
+        cost.append(time.perf_counter() - t0)
+    keep = list(range(len(picks)))
+    rest = args.steps + max(args.warmup - 1, 0)
+    while len(keep) > 1 and rest * sum(cost[j] for j in keep) > args.ref_budget:
+        keep.remove(max(keep, key=lambda j: cost[j]))
+    picks = [picks[j] for j in keep]
+    oracles = [oracles[j] for j in keep]
     cells = sum(cases[i].mesh.n_cells for i in picks)
-    for _ in range(args.warmup):
+    for _ in range(args.warmup - 1):
         for o in oracles:
             o.step(1)
     t0 = time.perf_counter()
@@ -614,6 +627,9 @@ def main():
     ap.add_argument("--workload", default="sweep", choices=["sweep", "delaunay40k", "cavity64"])
     ap.add_argument("--check-steps", type=int, default=5)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="seconds the reference arm's steps may take; it samples fewer instances "
+                         "to stay within it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--profile-mode", action="store_true",
