@@ -23,11 +23,15 @@
  * Where Part I (not available) or the text is silent, the reading taken is stated beside the
  * code; each is listed with its reason in the design notes of this repository.
  *
- * Parity status: f^eq, the IMEX tableau, the moment elimination, the gradient, the flux,
- * the wall boundary, mass conservation, Couette flow and the SST point functions are pinned
- * by tests against closed forms and invariants.  The turbulent cases as a whole (inlet,
- * outlet and far-field readings together with SST transport) have no closed form: parity
- * unpinned beyond those invariants.
+ * Parity status.
+ *   - Pinned by tests against closed forms and invariants: f^eq, the IMEX tableau, the moment
+ *     elimination, the gradient, the flux, the wall boundary, mass conservation, Couette flow
+ *     and the SST point functions.
+ *   - Pinned on tiny meshes against an independent NumPy restatement of the same equations:
+ *     one whole step, laminar and turbulent, with every boundary kind.
+ *   - Unpinned: the turbulent cases as a whole (the inlet, outlet and far-field readings
+ *     together with SST transport) have no closed form, so the readings themselves stay
+ *     unpinned beyond those checks.
  *
  * Built with ORACLE_COMPLEX_STEP, the same source is the oracle's own tangent (complex-step
  * method, see `real` below); its real parts equal the double build's values exactly, and its

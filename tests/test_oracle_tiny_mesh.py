@@ -14,6 +14,13 @@ The meshes:
     one of them periodic;
   - a jittered periodic 3 x 3 box of triangles.
 
+A second comparison restates the SST update of Step 1 as well (Sec. 2 with readings 7-10, the
+constants from tests/golden/sst_constants.json).  It takes two turbulent steps on a jittered
+3 x 3 mesh with all four boundary kinds:
+  - limited upwind convection and central diffusion of k and omega, by faces;
+  - the blending functions, production, cross diffusion and point-implicit destruction;
+  - the eddy viscosity and tau = (nu + nu_t) / cs^2, which then drives the IMEX stages.
+
 Initial states are equilibria of random density and velocity plus a random non-equilibrium
 part, so every term of the step is active.  The restatement shares no code with the oracle; a
 dropped term, a wrong sign, index or shift in either one shows up far above the 1e-13 rounding
@@ -123,7 +130,7 @@ class Restated:
                 d = self.c[N] + F["s"] - self.c[P]
                 rows[P].append((d, f[N] - f[P]))
                 rows[N].append((-d, f[P] - f[N]))
-        g = np.zeros((nc, 9, 2))
+        g = np.zeros((nc, f.shape[1], 2))
         for i in range(nc):
             D = np.array([r[0] for r in rows[i]])
             R = np.array([r[1] for r in rows[i]])
@@ -152,7 +159,8 @@ class Restated:
     def imex_step(self, f, tab):
         mt, mi = np.array(tab["m_tilde"]), np.array(tab["m"])
         nt, ni = np.array(tab["n_tilde"]), np.array(tab["n"])
-        dt, tau = self.dt, self.tau
+        dt = self.dt
+        tau = np.reshape(self.tau, (-1, 1)) if np.ndim(self.tau) else self.tau
         ga, gc = [], []
         for J in range(3):
             expl = f + dt * sum(mt[J, k] * ga[k] for k in range(J))
@@ -164,22 +172,135 @@ class Restated:
             ga.append(self.convection(fJ))
         return f + dt * sum(nt[J] * ga[J] + ni[J] * gc[J] for J in range(3))
 
+    # ---------------------------------------------------------------- SST (Step 1)
+    def sst_setup(self, m: mg.Mesh, sst: dict, uref: float, lref: float):
+        """Constants, omega floor and the wall distance (centroid to nearest wall edge)."""
+        self.K = sst
+        self.wmin = 1e-12 * uref / lref
+        m = m.normalized()
+        segs = [m.xy[m.bedge_nodes[e]] for e in range(m.n_bedges) if m.bedge_type[e] == mg.BC_WALL]
+        self.wd = np.full(len(self.area), 1e30)
+        for i, c in enumerate(self.c):
+            for a, b in segs:
+                t = np.clip(np.dot(c - a, b - a) / np.dot(b - a, b - a), 0.0, 1.0)
+                self.wd[i] = min(self.wd[i], float(np.hypot(*(a + t * (b - a) - c))))
+
+    def _cell_faces(self):
+        """Per cell: (midpoint offset from the centroid, neighbour or -1, face index)."""
+        out = [[] for _ in self.area]
+        for q, F in enumerate(self.faces):
+            out[F["P"]].append((F["x"] - self.c[F["P"]], F["N"], q))
+            if F["N"] >= 0:
+                out[F["N"]].append((F["x"] - F["s"] - self.c[F["N"]], F["P"], q))
+        return out
+
+    def _f1_f2(self, k, w, d, cd):
+        K, nu = self.K, self.nu
+        a = np.sqrt(k) / (K["beta_star"] * w * d)
+        b = 500.0 * nu / (w * d * d)
+        arg1 = np.minimum(np.maximum(a, b), 4.0 * K["sigma_w2"] * k / (cd * d * d))
+        arg2 = np.maximum(2.0 * a, b)
+        return np.tanh(arg1 ** 4), np.tanh(arg2 ** 2)
+
+    def sst_update(self, f, k, w, nut):
+        """One step of k, omega from the macros of f (t^n); returns k, omega, nu_t, tau."""
+        K, nu, dt = self.K, self.nu, self.dt
+        _, u = macros(f)
+        phi = np.column_stack([u, k, w])                  # u, v, k, omega per cell
+        pb = []
+        for F in self.faces:                               # boundary values (reading 7)
+            if F["N"] >= 0:
+                pb.append(None)
+                continue
+            P, v = F["P"], F["val"]
+            if F["kind"] == mg.BC_WALL:
+                pb.append(np.array([v[1], v[2], 0.0, 60.0 * nu / (K["beta1"] * self.wd[P] ** 2)]))
+            elif F["kind"] == mg.BC_OUTLET:
+                pb.append(phi[P].copy())
+            else:
+                pb.append(np.array([v[1], v[2], v[3], v[4]]))
+        g = self.gradients(phi, pb)                        # [nc, 4, 2]
+        cf = self._cell_faces()
+        lim = np.ones((len(k), 2))                         # Barth-Jespersen for k, omega
+        for i, faces in enumerate(cf):
+            for c in (2, 3):
+                vals = [phi[i, c]] + [phi[N, c] if N >= 0 else pb[q][c] for _, N, q in faces]
+                lo, hi = min(vals), max(vals)
+                for r, _, _ in faces:
+                    d = g[i, c] @ r
+                    ratio = (hi - phi[i, c]) / d if d > 0 else ((lo - phi[i, c]) / d if d < 0 else 1.0)
+                    lim[i, c - 2] = min(lim[i, c - 2], ratio)
+        gl = g[:, 2:4, :] * lim[:, :, None]                # limited gradients of k, omega
+        s11, s22 = g[:, 0, 0], g[:, 1, 1]
+        s12 = 0.5 * (g[:, 0, 1] + g[:, 1, 0])
+        SS = s11 ** 2 + s22 ** 2 + 2.0 * s12 ** 2
+        div = s11 + s22
+        gkgw = (g[:, 2, :] * g[:, 3, :]).sum(1)
+        cd = np.maximum(2.0 * K["sigma_w2"] / w * gkgw, 1e-20)
+        f1, _ = self._f1_f2(k, w, self.wd, cd)
+        sk = f1 * K["sigma_k1"] + (1 - f1) * K["sigma_k2"]
+        sw = f1 * K["sigma_w1"] + (1 - f1) * K["sigma_w2"]
+        conv = np.zeros((len(k), 2))                       # sum of un phi_up dl, per cell
+        diff = np.zeros((len(k), 2))                       # sum of Gamma dphi/dn dl, per cell
+        for q, F in enumerate(self.faces):
+            P, N = F["P"], F["N"]
+            rP = F["x"] - self.c[P]
+            fromP = phi[P, 2:4] + gl[P] @ rP
+            if N < 0:
+                b = pb[q]
+                un = b[:2] @ F["n"]
+                up = fromP if un >= 0 else b[2:4]
+                dist = np.hypot(*rP)
+                gam = nu + np.array([sk[P], sw[P]]) * nut[P]
+                conv[P] += un * up * F["l"]
+                diff[P] += gam * (b[2:4] - phi[P, 2:4]) / dist * F["l"]
+                continue
+            xN = self.c[N] + F["s"]
+            un = 0.5 * (u[P] + u[N]) @ F["n"]
+            fromN = phi[N, 2:4] + gl[N] @ (F["x"] - xN)
+            up = fromP if un >= 0 else fromN
+            dist = np.hypot(*(xN - self.c[P]))
+            gam = nu + 0.5 * (np.array([sk[P], sw[P]]) * nut[P] + np.array([sk[N], sw[N]]) * nut[N])
+            flux = un * up * F["l"]
+            dflux = gam * (phi[N, 2:4] - phi[P, 2:4]) / dist * F["l"]
+            conv[P] += flux
+            conv[N] -= flux
+            diff[P] += dflux
+            diff[N] -= dflux
+        kap2 = K["kappa"] ** 2 / np.sqrt(K["beta_star"])
+        gamma = f1 * (K["beta1"] / K["beta_star"] - K["sigma_w1"] * kap2) + \
+            (1 - f1) * (K["beta2"] / K["beta_star"] - K["sigma_w2"] * kap2)
+        shear = 2.0 * SS - 2.0 / 3.0 * div ** 2
+        pk = nut * shear - 2.0 / 3.0 * k * div
+        pw = gamma * shear - np.where(nut > 0, 2.0 / 3.0 * gamma * k * div / np.where(nut > 0, nut, 1.0), 0.0)
+        cross = 2.0 * (1 - f1) * K["sigma_w2"] / w * gkgw
+        rk = (-conv[:, 0] + diff[:, 0]) / self.area + pk
+        rw = (-conv[:, 1] + diff[:, 1]) / self.area + pw + cross
+        beta = f1 * K["beta1"] + (1 - f1) * K["beta2"]
+        k1 = np.maximum((k + dt * rk) / (1 + dt * K["beta_star"] * w), 0.0)
+        w1 = (w + dt * rw) / (1 + dt * beta * w)
+        w1 = np.where(w1 > self.wmin, w1, self.wmin)
+        _, f2 = self._f1_f2(k1, w1, self.wd, np.full(len(k), 1e-20))
+        nut1 = K["a1"] * k1 / np.maximum(K["a1"] * w1, np.sqrt(2.0 * SS) * f2)
+        return k1, w1, nut1, (nu + nut1) / CS2
+
     def euler_step(self, f):
         return f + self.dt * (self.convection(f) + (equilibrium(*macros(f)) - f) / self.tau)
 
 
-def _four_boundary_mesh(seed):
-    xs = np.array([0.0, 0.5, 1.0])
+def _four_boundary_mesh(seed, n=2):
+    """n x n jittered quads on the unit square: a wall below sliding at u = 0.05, a far field
+    above, an inlet on the left and an outlet on the right."""
+    xs = np.linspace(0.0, 1.0, n + 1)
     xy, cells, sides = mg.quad_grid(xs, xs, 0.25, seed)
     bn = np.concatenate([sides["bottom"], sides["top"], sides["left"], sides["right"]])
-    kind = np.array([mg.BC_WALL] * 2 + [mg.BC_FARFIELD] * 2 + [mg.BC_INLET] * 2 + [mg.BC_OUTLET] * 2,
-                    np.int32)
-    bv = np.zeros((8, 5))
-    bv[0:2] = [1.0, 0.05, 0.0, 0.0, 1.0]      # wall sliding at u = 0.05
-    bv[2:4] = [1.02, 0.08, 0.01, 0.0, 1.0]    # far field
-    bv[4:6] = [1.0, 0.1, -0.02, 0.0, 1.0]     # inlet velocity
-    bv[6:8] = [0.98, 0.0, 0.0, 0.0, 1.0]      # outlet density
-    return mg.Mesh(xy, np.arange(5, dtype=np.int32) * 4, cells.ravel(), bn, kind, bv)
+    kind = np.repeat(np.array([mg.BC_WALL, mg.BC_FARFIELD, mg.BC_INLET, mg.BC_OUTLET], np.int32), n)
+    bv = np.zeros((4 * n, 5))
+    bv[0:n] = [1.0, 0.05, 0.0, 0.0, 1.0]          # wall velocity
+    bv[n:2 * n] = [1.02, 0.08, 0.01, 0.0, 1.0]    # far field
+    bv[2 * n:3 * n] = [1.0, 0.1, -0.02, 0.0, 1.0]  # inlet velocity
+    bv[3 * n:] = [0.98, 0.0, 0.0, 0.0, 1.0]       # outlet density
+    return mg.Mesh(xy, np.arange(n * n + 1, dtype=np.int32) * 4, cells.ravel(), bn, kind, bv)
 
 
 MESHES = {
@@ -230,3 +351,61 @@ def test_restatement_sees_a_planted_term():
     tab["m"][2][2] = 0.25
     want = Restated(m, 0.01, 0.04).imex_step(f0, tab)
     assert np.abs(o.get_f() - want).max() > 1e-6
+
+
+def _sst_run(sst_constants):
+    """Two SST steps of the oracle and of the restatement (with the given constants) from the
+    same seeded state; returns both (f, k, omega, nu_t) and the oracle's wall distance."""
+    m = _four_boundary_mesh(11, n=3).normalized()
+    nc = m.n_cells
+    rng = np.random.default_rng(29)
+    k0 = 1e-3 * (1.0 + rng.uniform(0, 1, nc))
+    w0 = 0.5 + rng.uniform(0, 1, nc)
+    m.bedge_val[:, 3] = np.where(m.bedge_type == mg.BC_WALL, 0.0, 1.2e-3)   # k_b
+    m.bedge_val[:, 4] = np.where(m.bedge_type == mg.BC_WALL, 1.0, 0.8)      # omega_b
+    nu, dt = 1e-3, 0.04
+    o = Oracle(mg.Case(m, nu=nu, dt=dt, sst=True, k=k0, omega=w0, uref=0.1, lref=1.0))
+    f0 = _state(nc, 7)
+    o.set_f(f0)
+    with open(os.path.join(GOLD, "imex_tableau.json")) as fh:
+        tab = json.load(fh)
+    r = Restated(m, nu, dt)
+    r.sst_setup(m, sst_constants, 0.1, 1.0)
+    f, k, w, nut = f0, k0, w0, k0 / w0           # Step 0: nu_t = k / omega
+    steps = []
+    for _ in range(2):
+        k, w, nut, r.tau = r.sst_update(f, k, w, nut)
+        f = r.imex_step(f, tab)
+        o.step(1)
+        got = o.fields()
+        steps.append(((o.get_f(), got["k"], got["omega"], got["nut"]), (f, k, w, nut)))
+    return steps, (k0, w0), (r.wd, o.geometry()["wdist"])
+
+
+def _sst_constants():
+    with open(os.path.join(GOLD, "sst_constants.json")) as fh:
+        return json.load(fh)
+
+
+def test_two_sst_steps_match_numpy_restatement():
+    steps, (k0, w0), (wd, wd_oracle) = _sst_run(_sst_constants())
+    assert np.allclose(wd, wd_oracle, rtol=1e-14, atol=0)
+    for got, want in steps:
+        assert np.abs(got[0] - want[0]).max() <= 1e-13 * np.abs(want[0]).max()
+        for name, g, v in zip(("k", "omega", "nut"), got[1:], want[1:]):
+            assert np.abs(g - v).max() <= 1e-12 * np.abs(v).max(), name
+    k, _, nut = steps[-1][1][1:]                   # the restatement after two steps
+    assert np.abs(k - k0).max() > 1e-2 * k0.max() and np.abs(nut - k0 / w0).max() > 1e-2 * nut.max()
+
+
+@pytest.mark.parametrize("name,value", [("sigma_w2", 0.85), ("sigma_k1", 0.86), ("beta1", 0.0755),
+                                        ("kappa", 0.405)])
+def test_sst_restatement_sees_a_changed_constant(name, value):
+    """The SST comparison is sharp: a constant of Sec. 2 moved by about 1 % in the restatement
+    moves k, omega or nu_t far above the tolerance."""
+    K = _sst_constants()
+    K[name] = value
+    steps, _, _ = _sst_run(K)
+    got, want = steps[-1]
+    worst = max(np.abs(g - v).max() / np.abs(v).max() for g, v in zip(got[1:], want[1:]))
+    assert worst > 1e-8, (name, worst)
