@@ -57,9 +57,10 @@ def macros(f):
 class Restated:
     """Face-based finite-volume data of a mesh and the laminar FVLBM step on it."""
 
-    def __init__(self, m: mg.Mesh, nu: float, dt: float):
+    def __init__(self, m: mg.Mesh, nu: float, dt: float, variant: int = 0):
         m = m.normalized()
         self.nu, self.dt, self.tau = nu, dt, nu / CS2
+        self.variant = variant
         nc = m.n_cells
         polys = [m.cell_nodes[m.cell_ptr[i]:m.cell_ptr[i + 1]] for i in range(nc)]
         self.area = np.zeros(nc)
@@ -142,6 +143,8 @@ class Restated:
         (Eq. (advection), reading 5); each interior face adds to its two cells."""
         fb = [self.boundary_value(F, f) if F["N"] < 0 else None for F in self.faces]
         g = self.gradients(f, fb)
+        if self.variant & 1:
+            g = g * self.venkatakrishnan(f, fb, g)[:, :, None]
         ga = np.zeros_like(f)
         for F, vb in zip(self.faces, fb):
             P, N = F["P"], F["N"]
@@ -156,18 +159,40 @@ class Restated:
             ga[N] += flux / self.area[N]
         return ga
 
-    def imex_step(self, f, tab):
+    def venkatakrishnan(self, f, fb, g):
+        """Variant 1: limiter of each f_alpha's reconstruction per cell.  D1 is the distance to
+        the max (min) over the cell, its face neighbours and its boundary values, D2 the
+        increment to a face, eps^2 = A^(3/2); phi = min over faces of
+        [(D1^2 + eps^2) D2 + 2 D2^2 D1] / [D1^2 + 2 D2^2 + D1 D2 + eps^2] / D2."""
+        psi = np.ones_like(f)
+        for i, faces in enumerate(self._cell_faces()):
+            vals = np.array([f[i]] + [f[N] if N >= 0 else fb[q] for _, N, q in faces])
+            hi, lo = vals.max(0), vals.min(0)
+            e2 = self.area[i] ** 1.5
+            for r, _, _ in faces:
+                d2 = g[i] @ r
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    d1 = np.where(d2 > 0, hi - f[i], lo - f[i])
+                    phi = ((d1 ** 2 + e2) * d2 + 2 * d2 ** 2 * d1) / (d1 ** 2 + 2 * d2 ** 2 + d1 * d2 + e2) / d2
+                psi[i] = np.where(d2 != 0, np.minimum(psi[i], phi), psi[i])
+        return psi
+
+    def imex_step(self, f, tab, stage_tau=None):
         mt, mi = np.array(tab["m_tilde"]), np.array(tab["m"])
         nt, ni = np.array(tab["n_tilde"]), np.array(tab["n"])
         dt = self.dt
         tau = np.reshape(self.tau, (-1, 1)) if np.ndim(self.tau) else self.tau
         ga, gc = [], []
+        latest = f
         for J in range(3):
+            if stage_tau is not None:           # variant 4: SST re-solved before each stage
+                tau = np.reshape(stage_tau(J, latest), (-1, 1))
             expl = f + dt * sum(mt[J, k] * ga[k] for k in range(J))
             eq = equilibrium(*macros(expl))     # collision invariants: moments of expl
             rhs = expl + dt * sum(mi[J, k] * gc[k] for k in range(J))
             z = dt * mi[J, J] / tau
             fJ = (rhs + z * eq) / (1.0 + z)
+            latest = fJ
             gc.append((eq - fJ) / tau)
             ga.append(self.convection(fJ))
         return f + dt * sum(nt[J] * ga[J] + ni[J] * gc[J] for J in range(3))
@@ -252,8 +277,11 @@ class Restated:
                 up = fromP if un >= 0 else b[2:4]
                 dist = np.hypot(*rP)
                 gam = nu + np.array([sk[P], sw[P]]) * nut[P]
+                dn = (b[2:4] - phi[P, 2:4]) / dist
+                if self.variant & 2:            # + grad phi . (n - r / |r|)
+                    dn = dn + g[P, 2:4] @ (F["n"] - rP / dist)
                 conv[P] += un * up * F["l"]
-                diff[P] += gam * (b[2:4] - phi[P, 2:4]) / dist * F["l"]
+                diff[P] += gam * dn * F["l"]
                 continue
             xN = self.c[N] + F["s"]
             un = 0.5 * (u[P] + u[N]) @ F["n"]
@@ -262,7 +290,10 @@ class Restated:
             dist = np.hypot(*(xN - self.c[P]))
             gam = nu + 0.5 * (np.array([sk[P], sw[P]]) * nut[P] + np.array([sk[N], sw[N]]) * nut[N])
             flux = un * up * F["l"]
-            dflux = gam * (phi[N, 2:4] - phi[P, 2:4]) / dist * F["l"]
+            dn = (phi[N, 2:4] - phi[P, 2:4]) / dist
+            if self.variant & 2:                # + mean grad phi . (n - d / |d|)
+                dn = dn + 0.5 * (g[P, 2:4] + g[N, 2:4]) @ (F["n"] - (xN - self.c[P]) / dist)
+            dflux = gam * dn * F["l"]
             conv[P] += flux
             conv[N] -= flux
             diff[P] += dflux
@@ -272,6 +303,8 @@ class Restated:
             (1 - f1) * (K["beta2"] / K["beta_star"] - K["sigma_w2"] * kap2)
         shear = 2.0 * SS - 2.0 / 3.0 * div ** 2
         pk = nut * shear - 2.0 / 3.0 * k * div
+        if self.variant & 8:                    # P_k <= 10 beta* omega k
+            pk = np.minimum(pk, 10.0 * K["beta_star"] * w * k)
         pw = gamma * shear - np.where(nut > 0, 2.0 / 3.0 * gamma * k * div / np.where(nut > 0, nut, 1.0), 0.0)
         cross = 2.0 * (1 - f1) * K["sigma_w2"] / w * gkgw
         rk = (-conv[:, 0] + diff[:, 0]) / self.area + pk
@@ -380,29 +413,42 @@ def test_restatement_sees_a_planted_term():
     assert np.abs(o.get_f() - want).max() > 1e-6
 
 
-def _sst_run(sst_constants):
-    """Two SST steps of the oracle and of the restatement (with the given constants) from the
-    same seeded state; returns both (f, k, omega, nu_t) and the oracle's wall distance."""
+def _sst_run(sst_constants, variant=0, w_scale=1.0):
+    """Two SST steps of the oracle and of the restatement (with the given constants and reading
+    variant) from the same seeded state; returns both (f, k, omega, nu_t) per step, the initial
+    k and omega, and the two wall distances."""
     m = _four_boundary_mesh(11, n=3).normalized()
     nc = m.n_cells
     rng = np.random.default_rng(29)
     k0 = 1e-3 * (1.0 + rng.uniform(0, 1, nc))
-    w0 = 0.5 + rng.uniform(0, 1, nc)
+    w0 = w_scale * (0.5 + rng.uniform(0, 1, nc))
     m.bedge_val[:, 3] = np.where(m.bedge_type == mg.BC_WALL, 0.0, 1.2e-3)   # k_b
     m.bedge_val[:, 4] = np.where(m.bedge_type == mg.BC_WALL, 1.0, 0.8)      # omega_b
     nu, dt = 1e-3, 0.04
-    o = Oracle(mg.Case(m, nu=nu, dt=dt, sst=True, k=k0, omega=w0, uref=0.1, lref=1.0))
+    o = Oracle(mg.Case(m, nu=nu, dt=dt, sst=True, k=k0, omega=w0, uref=0.1, lref=1.0,
+                       variant=variant))
     f0 = _state(nc, 7)
     o.set_f(f0)
     with open(os.path.join(GOLD, "imex_tableau.json")) as fh:
         tab = json.load(fh)
-    r = Restated(m, nu, dt)
+    r = Restated(m, nu, dt, variant)
     r.sst_setup(m, sst_constants, 0.1, 1.0)
     f, k, w, nut = f0, k0, w0, k0 / w0           # Step 0: nu_t = k / omega
     steps = []
     for _ in range(2):
-        k, w, nut, r.tau = r.sst_update(f, k, w, nut)
-        f = r.imex_step(f, tab)
+        if variant & 4:
+            # each stage re-solves the update from k, omega, nu_t of t^n with the macros of the
+            # latest stage value (f^n, f^(1), f^(2)); the last solve gives t^{n+1}
+            start, solved = (k, w, nut), {}
+
+            def stage_tau(J, latest, start=start, solved=solved):
+                solved["out"] = r.sst_update(latest, *start)
+                return solved["out"][3]
+            f = r.imex_step(f, tab, stage_tau)
+            k, w, nut, _ = solved["out"]
+        else:
+            k, w, nut, r.tau = r.sst_update(f, k, w, nut)
+            f = r.imex_step(f, tab)
         o.step(1)
         got = o.fields()
         steps.append(((o.get_f(), got["k"], got["omega"], got["nut"]), (f, k, w, nut)))
@@ -436,3 +482,24 @@ def test_sst_restatement_sees_a_changed_constant(name, value):
     got, want = steps[-1]
     worst = max(np.abs(g - v).max() / np.abs(v).max() for g, v in zip(got[1:], want[1:]))
     assert worst > 1e-8, (name, worst)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 4, 8, 1 | 2 | 8])
+def test_reading_variants_match_numpy_restatement(variant):
+    """The reading variants, restated term by term:
+      - 1: Venkatakrishnan limiter on grad f;
+      - 2: non-orthogonal diffusion correction of k and omega;
+      - 4: SST re-solved before every stage;
+      - 8: Menter's production limiter.
+    omega starts near 0.1-0.15 so that nu_t = k / omega is large and the production limiter
+    acts.  Each variant must change the result (so it is exercised), and the oracle and the
+    restatement must agree to the rounding level."""
+    K = _sst_constants()
+    steps, _, _ = _sst_run(K, variant=variant, w_scale=0.1)
+    base, _, _ = _sst_run(K, variant=0, w_scale=0.1)
+    for got, want in steps:
+        assert np.abs(got[0] - want[0]).max() <= 1e-13 * np.abs(want[0]).max()
+        for name, g, v in zip(("k", "omega", "nut"), got[1:], want[1:]):
+            assert np.abs(g - v).max() <= 1e-12 * np.abs(v).max(), name
+    moved = max(np.abs(a - b).max() / np.abs(b).max() for a, b in zip(steps[-1][1], base[-1][1]))
+    assert moved > 1e-6, moved
