@@ -13,6 +13,9 @@ that ``fvlbm_create`` runs on every prepared instance).
     of a uniform quad grid is cfl h / 2: the diagonal velocities leave through two faces.
   - A periodic pair whose edges are not translates by the shift is rejected.
   - The error code of a bad input equals the one ``fvlbm_create`` returns for it.
+  - What the preprocessing hands the kernels matches the oracle's own, independent geometry:
+    areas, wall distances, the CFL step and least-squares gradients (a second native program,
+    tests/native/prepared_geometry_dump.cpp).
 """
 import ctypes as C
 import dataclasses
@@ -188,3 +191,60 @@ def test_create_error_names_the_instance_and_reason():
     with pytest.raises(fvlbm.FvlbmError) as e:
         fvlbm.Solver([good, bad], precision=fvlbm.FVLBM_FP64, device=0)
     assert e.value.code == fvlbm.FVLBM_ERR_BAD_MESH and "instance 1" in str(e.value)
+
+
+@pytest.fixture(scope="module")
+def dumper(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    out = str(tmp_path_factory.mktemp("prepdump") / "prepared_geometry_dump")
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-fopenmp", "-I", os.path.join(ROOT, "include"),
+                           "-I", CSRC, os.path.join(HERE, "native", "prepared_geometry_dump.cpp"),
+                           os.path.join(CSRC, "fvlbm_host.cpp"), "-o", out])
+    return out
+
+
+@pytest.mark.parametrize("name", ["cavity_delaunay", "bfs_hybrid", "naca0012_sst", "periodic_box_tri"])
+def test_host_geometry_matches_the_oracle(dumper, tmp_path, name):
+    """What the library's host preprocessing hands the kernels, against the oracle's own,
+    independent geometry (both FP64, no GPU):
+      - cell areas;
+      - wall distances;
+      - the CFL time step;
+      - the least-squares gradient of a random field with random boundary values, formed from
+        the library's stored weights as the kernels form it."""
+    from oracle.oracle import Oracle
+    case = dataclasses.replace(_cases()[name], dt=0.0, cfl=0.5)
+    m = case.mesh.normalized()
+    rng = np.random.default_rng(8)
+    phi = rng.standard_normal(m.n_cells)
+    phib = rng.standard_normal(m.n_bedges)
+    path = str(tmp_path / "mesh.bin")
+    _run_write(path, m, phi, phib)
+    out = str(tmp_path / "dump.bin")
+    subprocess.run([dumper, path, out], check=True)
+    d = np.fromfile(out, dtype="<f8")
+    dt, cells = d[0], d[1:].reshape(m.n_cells, 4)
+    o = Oracle(dataclasses.replace(case, mesh=m))
+    geo = o.geometry()
+    np.testing.assert_allclose(cells[:, 0], geo["area"], rtol=1e-13, atol=0)
+    walls = geo["wdist"] < 1e29
+    np.testing.assert_allclose(cells[walls, 1], geo["wdist"][walls], rtol=1e-13, atol=0)
+    assert np.all(cells[~walls, 1] >= 1e29)
+    assert abs(dt - o.dt) <= 1e-14 * o.dt
+    g = o.gradient(phi, phib)
+    scale = np.abs(g).max()
+    assert np.abs(cells[:, 2:] - g).max() <= 1e-12 * scale, np.abs(cells[:, 2:] - g).max() / scale
+
+
+def _run_write(path, m, phi=None, phib=None):
+    with open(path, "wb") as fh:
+        fh.write(struct.pack("<i", m.n_nodes)); fh.write(m.xy.astype("<f8").tobytes())
+        fh.write(struct.pack("<i", m.n_cells)); fh.write(m.cell_ptr.astype("<i4").tobytes())
+        fh.write(m.cell_nodes.astype("<i4").tobytes())
+        fh.write(struct.pack("<i", m.n_bedges)); fh.write(m.bedge_nodes.astype("<i4").tobytes())
+        fh.write(m.bedge_type.astype("<i4").tobytes()); fh.write(m.bedge_val.astype("<f8").tobytes())
+        fh.write(struct.pack("<i", m.periodic_pairs.shape[0]))
+        fh.write(m.periodic_pairs.astype("<i4").tobytes()); fh.write(m.periodic_shift.astype("<f8").tobytes())
+        if phi is not None:
+            fh.write(np.asarray(phi, "<f8").tobytes()); fh.write(np.asarray(phib, "<f8").tobytes())
