@@ -3,8 +3,9 @@
 // gradient of a given cell field with given boundary-edge values.  The gradient is formed as
 // the kernels form it: sum over face slots of W_m (phi_neighbour - phi_i), with the boundary
 // face value for a boundary slot.  Input: the binary mesh file of prepared_check.cpp followed
-// by phi [n_cells] and phi_b [n_bedges].  Output: a binary file of doubles,
-// dt, then per input cell (area, wall distance, gx, gy).
+// by phi [n_cells] and phi_b [n_bedges].  A third argument "local" asks for local time
+// stepping.  Output: a binary file of doubles, dt, then per input cell (area, wall distance,
+// gx, gy, the cell's own time step).
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -42,6 +43,7 @@ int main(int argc, char **argv) {
     p.nu = 1e-3;
     p.rho0 = 1.0;
     p.cfl = 0.5;
+    p.local_dt = argc > 3 && std::string(argv[3]) == "local";
     Prepared P;
     std::string why;
     if (prepare_instance(M, B, p, &P, &why)) {
@@ -49,7 +51,7 @@ int main(int argc, char **argv) {
         return 3;
     }
     const size_t np = P.np;
-    std::vector<double> out(1 + 4 * static_cast<size_t>(nc));
+    std::vector<double> out(1 + 5 * static_cast<size_t>(nc));
     out[0] = P.dt;
     for (int k = 0; k < P.nc; ++k) {
         const int i = P.perm[k];
@@ -60,10 +62,12 @@ int main(int argc, char **argv) {
             gx += P.lsq[(2 * m) * np + k] * (q - phi[i]);
             gy += P.lsq[(2 * m + 1) * np + k] * (q - phi[i]);
         }
-        out[1 + 4 * static_cast<size_t>(i)] = P.area[k];
-        out[2 + 4 * static_cast<size_t>(i)] = P.wdist[k];
-        out[3 + 4 * static_cast<size_t>(i)] = gx;
-        out[4 + 4 * static_cast<size_t>(i)] = gy;
+        double *row = &out[1 + 5 * static_cast<size_t>(i)];
+        row[0] = P.area[k];
+        row[1] = P.wdist[k];
+        row[2] = gx;
+        row[3] = gy;
+        row[4] = P.dt_cell.empty() ? P.dt : P.dt_cell[k];
     }
     FILE *o = fopen(argv[2], "wb");
     if (!o) return 2;

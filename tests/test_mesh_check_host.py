@@ -224,7 +224,7 @@ def test_host_geometry_matches_the_oracle(dumper, tmp_path, name):
     out = str(tmp_path / "dump.bin")
     subprocess.run([dumper, path, out], check=True)
     d = np.fromfile(out, dtype="<f8")
-    dt, cells = d[0], d[1:].reshape(m.n_cells, 4)
+    dt, cells = d[0], d[1:].reshape(m.n_cells, 5)
     o = Oracle(dataclasses.replace(case, mesh=m))
     geo = o.geometry()
     np.testing.assert_allclose(cells[:, 0], geo["area"], rtol=1e-13, atol=0)
@@ -234,7 +234,7 @@ def test_host_geometry_matches_the_oracle(dumper, tmp_path, name):
     assert abs(dt - o.dt) <= 1e-14 * o.dt
     g = o.gradient(phi, phib)
     scale = np.abs(g).max()
-    assert np.abs(cells[:, 2:] - g).max() <= 1e-12 * scale, np.abs(cells[:, 2:] - g).max() / scale
+    assert np.abs(cells[:, 2:4] - g).max() <= 1e-12 * scale, np.abs(cells[:, 2:4] - g).max() / scale
 
 
 def _run_write(path, m, phi=None, phib=None):
@@ -248,3 +248,22 @@ def _run_write(path, m, phi=None, phib=None):
         fh.write(m.periodic_pairs.astype("<i4").tobytes()); fh.write(m.periodic_shift.astype("<f8").tobytes())
         if phi is not None:
             fh.write(np.asarray(phi, "<f8").tobytes()); fh.write(np.asarray(phib, "<f8").tobytes())
+
+
+@pytest.mark.parametrize("name", ["bfs_hybrid", "naca0012_laminar"])
+def test_host_local_time_steps_match_the_oracle(dumper, tmp_path, name):
+    """Local time stepping: every cell's dt_i = cfl / max_alpha sum_m max(e_alpha . n_m, 0)
+    dl_m / A_i from the library's preprocessing equals the oracle's, and the global dt is the
+    smallest of them."""
+    from oracle.oracle import Oracle
+    case = dataclasses.replace(_cases()[name], dt=0.0, cfl=0.5, local_dt=True)
+    m = case.mesh.normalized()
+    path = str(tmp_path / "mesh.bin")
+    _run_write(path, m, np.zeros(m.n_cells), np.zeros(m.n_bedges))
+    out = str(tmp_path / "dump.bin")
+    subprocess.run([dumper, path, out, "local"], check=True)
+    d = np.fromfile(out, dtype="<f8")
+    dt, dti = d[0], d[1:].reshape(m.n_cells, 5)[:, 4]
+    want = Oracle(dataclasses.replace(case, mesh=m)).dt_cells()
+    np.testing.assert_allclose(dti, want, rtol=1e-14, atol=0)
+    assert dt == dti.min() and dti.max() > 10 * dti.min()
