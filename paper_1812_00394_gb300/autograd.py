@@ -56,9 +56,10 @@ class AirfoilForces:
         self.U = float(np.hypot(bv[0, 1], bv[0, 2]))
         self.k_b = bv[:, 3].copy()
         self.normals = self._wall_normals()
-        probe = fvlbm.Solver(self.base, precision=fvlbm.FVLBM_FP64, device=device, kernel_path=1)
-        self.dt = probe.dt()
-        probe.close()
+        # the base case's time step from the host preprocessing (no device work)
+        rc, self.dt, why = fvlbm.check_case(self.base, precision=fvlbm.FVLBM_FP64, kernel_path=1)
+        if rc < 0:
+            raise fvlbm.FvlbmError(rc, f"AirfoilForces: {why}")
         rho, u, v, k, w = self.base.init_arrays()
         self.init = dict(rho=rho, u=u, v=v, k=k, omega=w)
 
