@@ -1,0 +1,39 @@
+"""CPU check of bench.py's reference arm: it runs the oracle with no GPU and prints one JSON
+line with the keys that the measurement contract asks for.  It also stays within its time
+budget by sampling fewer instances."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(*args):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", *args],
+                         capture_output=True, text=True, check=True, cwd=ROOT, timeout=600).stdout
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out
+    return json.loads(lines[0])
+
+
+def test_reference_arm_json_line():
+    d = _run("--workload", "cavity64", "--steps", "3", "--warmup", "3")
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 3 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["config"]["workload"] == "cavity64"
+
+
+def test_reference_arm_sampling_follows_the_budget():
+    """On the batched sweep the sample is one instance of each kind (three); a tiny budget keeps
+    only the cheapest one."""
+    wide = _run("--workload", "sweep", "--steps", "1", "--warmup", "3", "--ref-budget", "1e9")
+    assert "3 instances" in wide["cpu_baseline"]["sample"]
+    tight = _run("--workload", "sweep", "--steps", "1", "--warmup", "3", "--ref-budget", "1e-9")
+    assert "1 instances" in tight["cpu_baseline"]["sample"]
+    assert tight["config"]["sample_cells"] < wide["config"]["sample_cells"]
