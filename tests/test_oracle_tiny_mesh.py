@@ -102,7 +102,7 @@ class Restated:
                 j = sides[frozenset(map(int, m.bedge_nodes[eb]))][0][0]
                 self.faces.append(dict(P=i, N=j, s=-shift, n=n, l=length, x=mid))
             else:
-                self.faces.append(dict(P=i, N=-1, n=n, l=length, x=mid,
+                self.faces.append(dict(P=i, N=-1, n=n, l=length, x=mid, e=e,
                                        kind=int(m.bedge_type[e]), val=m.bedge_val[e]))
 
     def boundary_value(self, F, f):
@@ -131,7 +131,7 @@ class Restated:
                 d = self.c[N] + F["s"] - self.c[P]
                 rows[P].append((d, f[N] - f[P]))
                 rows[N].append((-d, f[P] - f[N]))
-        g = np.zeros((nc, f.shape[1], 2))
+        g = np.zeros((nc, f.shape[1], 2), dtype=f.dtype)
         for i in range(nc):
             D = np.array([r[0] for r in rows[i]])
             R = np.array([r[1] for r in rows[i]])
@@ -398,6 +398,57 @@ def test_local_time_steps_match_numpy_restatement(scheme):
         tab = json.load(fh)
     want = r.imex_step(f0, tab) if scheme == 0 else r.euler_step(f0)
     assert np.abs(o.get_f() - want).max() <= 1e-13 * np.abs(want).max()
+
+
+def restated_forces(r, f, rho0, U, L, alpha_deg):
+    """Reading 12 on the restatement: the wall force, the momentum flux sum over wall faces of
+    sum_alpha e_alpha (e_alpha . n) f_{alpha,bc} dl with n out of the fluid; C_D and C_L are
+    its components along and across the free stream at alpha, over 1/2 rho0 U^2 L."""
+    force = 0.0
+    for F in r.faces:
+        if F["N"] < 0 and F["kind"] == mg.BC_WALL:
+            force = force + E.T @ ((E @ F["n"]) * r.boundary_value(F, f)) * F["l"]
+    a = np.radians(alpha_deg)
+    q = 0.5 * rho0 * U * U * L
+    return {"fx": force[0], "fy": force[1], "cd": (force[0] * np.cos(a) + force[1] * np.sin(a)) / q,
+            "cl": (-force[0] * np.sin(a) + force[1] * np.cos(a)) / q}
+
+
+@pytest.mark.parametrize("seeded", ["f0", "boundary_values"])
+def test_complex_step_tangent_matches_the_restatement(seeded):
+    """The oracle's complex-step build (its own tangent) against the same method applied to the
+    restatement: seed f0, or the boundary values of every edge, with imaginary parts
+    h d (h = 1e-30), take two IMEX steps, and compare d(F_x, F_y, C_D, C_L) = Im / h."""
+    m = MESHES["four_boundary_kinds"]().normalized()
+    U, L, alpha, h = 0.1, 0.7, 10.0, 1e-30
+    case = mg.Case(m, nu=0.01, dt=0.04, uref=U, lref=L, alpha_deg=alpha)
+    f0 = _state(m.n_cells, 3)
+    rng = np.random.default_rng(41)
+    df = rng.standard_normal(f0.shape) * 1e-3 if seeded == "f0" else None
+    dbv = None
+    if seeded == "boundary_values":
+        dbv = np.zeros((m.n_bedges, 5))
+        dbv[:, :3] = rng.standard_normal((m.n_bedges, 3)) * 1e-2
+    o = Oracle(case, complex_step=True)
+    o.set_f(f0)
+    o.cs_seed(dbedge_val=dbv, df=df, h=h)
+    o.step(2)
+    _, der = o.cs_forces(h)
+    r = Restated(m, 0.01, 0.04)
+    f = f0.astype(complex) + (1j * h * df if df is not None else 0.0)
+    if dbv is not None:
+        for F in r.faces:
+            if F["N"] < 0:
+                F["val"] = F["val"] + 1j * h * dbv[F["e"]]
+    with open(os.path.join(GOLD, "imex_tableau.json")) as fh:
+        tab = json.load(fh)
+    for _ in range(2):
+        f = r.imex_step(f, tab)
+    want = {k: float(np.imag(v)) / h for k, v in restated_forces(r, f, case.rho0, U, L, alpha).items()}
+    scale = max(abs(v) for v in want.values())
+    assert scale > 0
+    for key, v in want.items():
+        assert abs(der[key] - v) <= 1e-10 * scale, (key, der[key], v)
 
 
 def test_wall_force_matches_numpy_restatement():
