@@ -329,7 +329,8 @@ class Restated:
 
     def euler_step(self, f):
         dt = np.reshape(self.dt, (-1, 1)) if np.ndim(self.dt) else self.dt
-        return f + dt * (self.convection(f) + (equilibrium(*macros(f)) - f) / self.tau)
+        tau = np.reshape(self.tau, (-1, 1)) if np.ndim(self.tau) else self.tau
+        return f + dt * (self.convection(f) + (equilibrium(*macros(f)) - f) / tau)
 
 
 def _four_boundary_mesh(seed, n=2):
@@ -494,7 +495,7 @@ def test_restatement_sees_a_planted_term():
     assert np.abs(o.get_f() - want).max() > 1e-6
 
 
-def _sst_run(sst_constants, variant=0, w_scale=1.0):
+def _sst_run(sst_constants, variant=0, w_scale=1.0, scheme=0):
     """Two SST steps of the oracle and of the restatement (with the given constants and reading
     variant) from the same seeded state; returns both (f, k, omega, nu_t) per step, the initial
     k and omega, and the two wall distances."""
@@ -507,7 +508,7 @@ def _sst_run(sst_constants, variant=0, w_scale=1.0):
     m.bedge_val[:, 4] = np.where(m.bedge_type == mg.BC_WALL, 1.0, 0.8)      # omega_b
     nu, dt = 1e-3, 0.04
     o = Oracle(mg.Case(m, nu=nu, dt=dt, sst=True, k=k0, omega=w0, uref=0.1, lref=1.0,
-                       variant=variant))
+                       variant=variant), scheme=scheme)
     f0 = _state(nc, 7)
     o.set_f(f0)
     with open(os.path.join(GOLD, "imex_tableau.json")) as fh:
@@ -529,7 +530,7 @@ def _sst_run(sst_constants, variant=0, w_scale=1.0):
             k, w, nut, _ = solved["out"]
         else:
             k, w, nut, r.tau = r.sst_update(f, k, w, nut)
-            f = r.imex_step(f, tab)
+            f = r.imex_step(f, tab) if scheme == 0 else r.euler_step(f)
         o.step(1)
         got = o.fields()
         steps.append(((o.get_f(), got["k"], got["omega"], got["nut"]), (f, k, w, nut)))
@@ -541,8 +542,9 @@ def _sst_constants():
         return json.load(fh)
 
 
-def test_two_sst_steps_match_numpy_restatement():
-    steps, (k0, w0), (wd, wd_oracle) = _sst_run(_sst_constants())
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_two_sst_steps_match_numpy_restatement(scheme):
+    steps, (k0, w0), (wd, wd_oracle) = _sst_run(_sst_constants(), scheme=scheme)
     assert np.allclose(wd, wd_oracle, rtol=1e-14, atol=0)
     for got, want in steps:
         assert np.abs(got[0] - want[0]).max() <= 1e-13 * np.abs(want[0]).max()
