@@ -159,7 +159,7 @@ int fvlbm_create_batch(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs,
  *
  * What the preprocessing validates:
  *   - the mesh and boundary records;
- *   - periodic pairs: edge b must be edge a moved by the shift, to 1e-8 of its length;
+ *   - periodic pairs: edge b must be edge a moved by the shift, to 1e-4 of its length;
  *   - the geometry and the least-squares stencils;
  *   - the renumbering and the time step.
  *

@@ -181,8 +181,10 @@ int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_para
         const double la = value_of(A.len), lb = value_of(B.len);
         const double ex = value_of(B.xm) - sx - value_of(A.xm), ey = value_of(B.ym) - sy - value_of(A.ym);
         const double nx = value_of(A.nx) + value_of(B.nx), ny = value_of(A.ny) + value_of(B.ny);
-        if (!(std::fabs(la - lb) <= 1e-8 * (la + lb) && std::hypot(ex, ey) <= 1e-8 * (la + lb) &&
-              std::hypot(nx, ny) <= 1e-8)) {
+        // (to 1e-4 of the length: enough for meshes read from files with 6-8 digits, while a
+        // wrong partner or shift misses by O(1))
+        if (!(std::fabs(la - lb) <= 1e-4 * (la + lb) && std::hypot(ex, ey) <= 1e-4 * (la + lb) &&
+              std::hypot(nx, ny) <= 1e-4)) {
             *why = "periodic pair " + std::to_string(q) + ": edge b is not edge a moved by the shift";
             return FVLBM_ERR_BAD_BC;
         }
@@ -753,6 +755,9 @@ int check_prepared(const PreparedT<S> &P, std::string *why) {
     // face.  Tolerances are relative (1e-6) and far above rounding on cells down to 1e-6 of the
     // domain; a wrong slot, sign or operand misses them by O(1).
     constexpr double tol = 1e-6;
+    // Across a periodic pair the two edges agree only to the gluing tolerance (1e-4), so the
+    // checks that compare a face with the neighbour's own copy of it use a looser one.
+    constexpr double tol_link = 1e-3;
     auto V = [np](const std::vector<S> &a, int c, size_t k) { return value_of(a[static_cast<size_t>(c) * np + k]); };
     for (int k = 0; k < nc; ++k) {
         const int nf = P.nface[k];
@@ -781,7 +786,8 @@ int check_prepared(const PreparedT<S> &P, std::string *why) {
             const int m1 = (m + 1) % nf;
             const double tx = gx[m1] - gx[m], ty = gy[m1] - gy[m], L = std::hypot(tx, ty);
             const double nlx = V(P.sn, 2 * m, k) * A, nly = V(P.sn, 2 * m + 1, k) * A;
-            if (!(std::hypot(nlx - ty, nly + tx) <= tol * L))
+            const int v = P.nbr[static_cast<size_t>(m) * np + k];
+            if (!(std::hypot(nlx - ty, nly + tx) <= (v >= 0 ? tol_link : tol) * L))
                 return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": n dl is not the outward normal of the edge");
             const double rx = V(P.rown, 2 * m, k), ry = V(P.rown, 2 * m + 1, k);
             if (!(std::hypot(rx - 0.5 * (gx[m] + gx[m1]), ry - 0.5 * (gy[m] + gy[m1])) <= tol * h))
@@ -791,7 +797,6 @@ int check_prepared(const PreparedT<S> &P, std::string *why) {
             const double di = value_of(P.dinv[static_cast<size_t>(m) * np + k]);
             if (!(d > 0.0 && std::isfinite(d) && std::fabs(di * d - 1.0) <= 1e-12))
                 return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": centroid offset or 1/|d|");
-            const int v = P.nbr[static_cast<size_t>(m) * np + k];
             if (v < 0) {  // boundary face: d is the offset to the face midpoint
                 if (dx != rx || dy != ry || qx != 0.0 || qy != 0.0)
                     return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": boundary face offsets");
@@ -807,8 +812,8 @@ int check_prepared(const PreparedT<S> &P, std::string *why) {
                 const double wx = V(P.sn, 2 * b, v) * Av, wy = V(P.sn, 2 * b + 1, v) * Av;
                 if (!(std::hypot(dx + vx, dy + vy) <= tol * d))
                     return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": d is not the reverse of the neighbour's");
-                if (!(std::hypot(qx - ox, qy - oy) <= tol * (std::hypot(qx, qy) + std::hypot(ox, oy))) ||
-                    !(std::hypot(dx - (rx - qx), dy - (ry - qy)) <= tol * (std::hypot(rx, ry) + std::hypot(qx, qy))))
+                if (!(std::hypot(dx - (rx - qx), dy - (ry - qy)) <= tol * (std::hypot(rx, ry) + std::hypot(qx, qy))) ||
+                    !(std::hypot(qx - ox, qy - oy) <= tol_link * (std::hypot(qx, qy) + std::hypot(ox, oy) + L)))
                     return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": neighbour-side face offset");
                 if (!(std::hypot(nlx + wx, nly + wy) <= tol * L))
                     return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": n dl is not the reverse of the neighbour's");

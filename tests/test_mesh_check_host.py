@@ -267,3 +267,16 @@ def test_host_local_time_steps_match_the_oracle(dumper, tmp_path, name):
     want = Oracle(dataclasses.replace(case, mesh=m)).dt_cells()
     np.testing.assert_allclose(dti, want, rtol=1e-14, atol=0)
     assert dt == dti.min() and dti.max() > 10 * dti.min()
+
+
+def test_periodic_mesh_read_with_six_digits_is_accepted():
+    """A periodic mesh whose node coordinates were written with 6 decimals (as a mesh file
+    might hold them) still glues: the edges agree to about 1e-5 of their length, within the
+    1e-4 tolerance.  A shift that is wrong by a tenth of an edge is still refused."""
+    m = mg.periodic_box(16, kind="tri", jitter=0.2, seed=9)
+    rounded = dataclasses.replace(m, xy=np.round(m.xy, 6))
+    assert fvlbm.check_case(mg.Case(rounded, nu=1e-3, cfl=0.5))[0] == 0
+    bad = m.periodic_shift.copy()
+    bad[:, 0] += 0.1 / 16
+    rc, _, why = fvlbm.check_case(mg.Case(dataclasses.replace(rounded, periodic_shift=bad), nu=1e-3, cfl=0.5))
+    assert rc == fvlbm.FVLBM_ERR_BAD_BC, (rc, why)
