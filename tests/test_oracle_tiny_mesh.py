@@ -10,6 +10,8 @@ both schemes) is compared with an independent NumPy restatement of the same equa
 The meshes:
   - a 2 x 2 jittered quad mesh with all four boundary kinds: a moving wall, an inlet, an outlet
     and a far field;
+  - the same boundary kinds on a 3 x 3 grid with alternate cells split into triangles (mixed
+    triangles and quads);
   - a doubly periodic 2 x 2 quad box, where each cell meets its x-neighbour through two faces,
     one of them periodic;
   - a jittered periodic 3 x 3 box of triangles.
@@ -348,8 +350,18 @@ def _four_boundary_mesh(seed, n=2):
     return mg.Mesh(xy, np.arange(n * n + 1, dtype=np.int32) * 4, cells.ravel(), bn, kind, bv)
 
 
+def _hybrid_mesh(seed):
+    """3 x 3 jittered grid on the unit square, alternate cells split into two triangles (a
+    mixed triangle / quad mesh), with the four boundary kinds of _four_boundary_mesh."""
+    m = _four_boundary_mesh(seed, n=3)
+    cells4 = m.cell_nodes.reshape(-1, 4)
+    ptr, nodes = mg._hybrid_cells(cells4, np.arange(9) % 2 == 0)
+    return mg.Mesh(m.xy, ptr, nodes, m.bedge_nodes, m.bedge_type, m.bedge_val)
+
+
 MESHES = {
     "four_boundary_kinds": lambda: _four_boundary_mesh(11),
+    "hybrid_3x3": lambda: _hybrid_mesh(13),
     "periodic_quads_2x2": lambda: mg.periodic_box(2, kind="quad"),
     "periodic_triangles_3x3": lambda: mg.periodic_box(3, kind="tri", jitter=0.2, seed=5),
 }
