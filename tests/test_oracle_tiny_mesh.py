@@ -498,11 +498,11 @@ def test_restatement_sees_a_planted_term():
     assert np.abs(o.get_f() - want).max() > 1e-6
 
 
-def _sst_run(sst_constants, variant=0, w_scale=1.0, scheme=0):
+def _sst_run(sst_constants, variant=0, w_scale=1.0, scheme=0, mesh="quads"):
     """Two SST steps of the oracle and of the restatement (with the given constants and reading
     variant) from the same seeded state; returns both (f, k, omega, nu_t) per step, the initial
     k and omega, and the two wall distances."""
-    m = _four_boundary_mesh(11, n=3).normalized()
+    m = (_four_boundary_mesh(11, n=3) if mesh == "quads" else _hybrid_mesh(13)).normalized()
     nc = m.n_cells
     rng = np.random.default_rng(29)
     k0 = 1e-3 * (1.0 + rng.uniform(0, 1, nc))
@@ -545,9 +545,9 @@ def _sst_constants():
         return json.load(fh)
 
 
-@pytest.mark.parametrize("scheme", [0, 1])
-def test_two_sst_steps_match_numpy_restatement(scheme):
-    steps, (k0, w0), (wd, wd_oracle) = _sst_run(_sst_constants(), scheme=scheme)
+@pytest.mark.parametrize("scheme,mesh", [(0, "quads"), (1, "quads"), (0, "hybrid")])
+def test_two_sst_steps_match_numpy_restatement(scheme, mesh):
+    steps, (k0, w0), (wd, wd_oracle) = _sst_run(_sst_constants(), scheme=scheme, mesh=mesh)
     assert np.allclose(wd, wd_oracle, rtol=1e-14, atol=0)
     for got, want in steps:
         assert np.abs(got[0] - want[0]).max() <= 1e-13 * np.abs(want[0]).max()
