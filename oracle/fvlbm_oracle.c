@@ -42,6 +42,21 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Threads of the per-cell loops (1 unless oracle_set_threads asks for more, and only in a
+ * build with OpenMP).  Every loop so marked writes per-cell results from per-cell arithmetic
+ * in the same order as the serial loop, so the results are bitwise the same for any thread
+ * count; sums over cells (residual, mass) stay serial. */
+static int g_threads = 1;
+void oracle_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+#ifdef _OPENMP
+#define OMP_FOR _Pragma("omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)")
+#define OMP_FOR_MAX_DEFECT \
+    _Pragma("omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1) reduction(max : defect)")
+#else
+#define OMP_FOR
+#define OMP_FOR_MAX_DEFECT
+#endif
+
 /* The state arithmetic (f, the macros, k, omega, nu_t, tau, the boundary values and every
  * quantity formed from them) is done in the type `real`: double, or -- when this file is
  * compiled with ORACLE_COMPLEX_STEP -- double complex, for the complex-step derivative of the
@@ -468,6 +483,7 @@ static void lsq_gradient(const oracle *o, int i, const real *phi, int stride,
  *   far field:     f^eq(rho_b, u_b) where e.n < 0 (incoming), f_P where e.n >= 0 (outgoing) */
 static void boundary_f(const oracle *o, const real *f, real *fbc)
 {
+    OMP_FOR
     for (int b = 0; b < o->nb; b++) {
         int t = o->btype[b];
         if (t == BC_PERIODIC) continue;
@@ -534,6 +550,7 @@ static void convection(oracle *o, const real *f, real *ga)
 {
     int nc = o->nc;
     boundary_f(o, f, o->fbc);
+    OMP_FOR
     for (int i = 0; i < nc; i++)
         for (int a = 0; a < Q; a++) {
             real gx, gy;
@@ -546,6 +563,7 @@ static void convection(oracle *o, const real *f, real *ga)
             o->gradf[((size_t)i * Q + a) * 2] = gx;
             o->gradf[((size_t)i * Q + a) * 2 + 1] = gy;
         }
+    OMP_FOR
     for (int i = 0; i < nc; i++) {
         for (int a = 0; a < Q; a++) {
             real sum = 0.0;
@@ -677,6 +695,7 @@ static void sst_update(oracle *o)
     for (int b = 0; b < nb; b++)
         if (o->btype[b] != BC_PERIODIC)
             sst_boundary(o, b, &ubc[4 * b], &ubc[4 * b + 1], &ubc[4 * b + 2], &ubc[4 * b + 3]);
+    OMP_FOR
     for (int i = 0; i < nc; i++) {
         lsq_gradient(o, i, o->ux, 1, ubc + 0, 4, &o->gu[2 * i], &o->gu[2 * i + 1]);
         lsq_gradient(o, i, o->uy, 1, ubc + 1, 4, &o->gv[2 * i], &o->gv[2 * i + 1]);
@@ -686,6 +705,7 @@ static void sst_update(oracle *o)
     /* limited gradients for the upwind face values of k and omega */
     real *lk = (real *)xcalloc((size_t)nc * 2, sizeof(real));
     real *lw = (real *)xcalloc((size_t)nc * 2, sizeof(real));
+    OMP_FOR
     for (int i = 0; i < nc; i++) {
         real pk = bj_limiter(o, i, o->k, ubc + 2, 4, &o->gk[2 * i]);
         real pw = bj_limiter(o, i, o->om, ubc + 3, 4, &o->gw[2 * i]);
@@ -698,6 +718,7 @@ static void sst_update(oracle *o)
     real *sw = (real *)xcalloc(nc, sizeof(real));
     real *SS = (real *)xcalloc(nc, sizeof(real));
     real *dv = (real *)xcalloc(nc, sizeof(real));
+    OMP_FOR
     for (int i = 0; i < nc; i++) {
         real s11 = o->gu[2 * i], s22 = o->gv[2 * i + 1];
         real s12 = 0.5 * (o->gu[2 * i + 1] + o->gv[2 * i]);
@@ -709,6 +730,7 @@ static void sst_update(oracle *o)
         sk[i] = o->f1[i] * SK1 + (1.0 - o->f1[i]) * SK2;
         sw[i] = o->f1[i] * SW1 + (1.0 - o->f1[i]) * SW2;
     }
+    OMP_FOR
     for (int i = 0; i < nc; i++) {
         real ck = 0, cw = 0, dk = 0, dw = 0;
         for (int l = 0; l < o->nface[i]; l++) {
@@ -775,6 +797,7 @@ static void sst_update(oracle *o)
         o->rw[i] = (-cw + dw) / o->area[i] + pw + cross;
     }
     double wmin = 1e-12 * o->uref / o->lref;
+    OMP_FOR
     for (int i = 0; i < nc; i++) {
         real f1 = o->f1[i];
         real beta = f1 * B1 + (1.0 - f1) * B2;
@@ -784,6 +807,7 @@ static void sst_update(oracle *o)
         o->k[i] = RE(kn) > 0.0 ? kn : 0.0;
         o->om[i] = RE(wn) > wmin ? wn : wmin;
     }
+    OMP_FOR
     for (int i = 0; i < nc; i++) {
         real f2 = sst_f2(o->k[i], o->om[i], o->wdist[i], o->nu);
         o->nut[i] = sst_nut(o->k[i], o->om[i], o->Sabs[i], f2);
@@ -833,6 +857,7 @@ static int imex_step(oracle *o)
             for (int i = 0; i < nc; i++) moments(&o->fst[(size_t)i * Q], &o->rho[i], &o->ux[i], &o->uy[i]);
             sst_update(o);
         }
+        OMP_FOR_MAX_DEFECT
         for (int i = 0; i < nc; i++) {
             real tau = o->tau[i];
             double dt = cell_dt(o, i);
@@ -865,6 +890,7 @@ static int imex_step(oracle *o)
         }
         convection(o, o->fst, o->ga[J]); /* Step 2 for the next stage / the final update */
     }
+    OMP_FOR
     for (size_t q = 0; q < nq; q++) {
         double dt = cell_dt(o, (int)(q / Q));
         real s = o->fn[q];
@@ -911,6 +937,7 @@ static int euler_step(oracle *o)
     else
         for (int i = 0; i < nc; i++) o->tau[i] = o->nu / CS2;
     convection(o, o->f, o->ga[0]);
+    OMP_FOR
     for (int i = 0; i < nc; i++) {
         double dt = cell_dt(o, i);
         real *f = &o->f[(size_t)i * Q];
@@ -1000,6 +1027,28 @@ void oracle_limiter(oracle *o, const double *phi, const double *phib, double *ps
         double gx, gy;
         lsq_gradient(o, i, phi, 1, phib, 1, &gx, &gy);
         psi[i] = vk_limiter(o, i, phi, 1, phib, 1, gx, gy);
+    }
+}
+
+/* The Barth-Jespersen limiter value of the SST reconstruction (bj_limiter) for a scalar
+ * field phi with boundary values phib [n_bedges], at its least-squares gradient, per cell
+ * (test access). */
+void oracle_bj_limiter(oracle *o, const double *phi, const double *phib, double *psi)
+{
+    for (int i = 0; i < o->nc; i++) {
+        double g[2];
+        lsq_gradient(o, i, phi, 1, phib, 1, &g[0], &g[1]);
+        psi[i] = bj_limiter(o, i, phi, phib, 1, g);
+    }
+}
+
+/* The SST boundary values (sst_boundary) of every non-periodic boundary edge at the current
+ * state: out [4 n_bedges] = u_b, v_b, k_b, omega_b (test access). */
+void oracle_sst_bvals(oracle *o, double *out)
+{
+    for (int b = 0; b < o->nb; b++) {
+        if (o->btype[b] == BC_PERIODIC) continue;
+        sst_boundary(o, b, &out[4 * b], &out[4 * b + 1], &out[4 * b + 2], &out[4 * b + 3]);
     }
 }
 

@@ -30,13 +30,15 @@ _I = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
 
 def build(force: bool = False, complex_step: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, so that every product is rounded as
-    written); with ``complex_step`` the same source in complex arithmetic (the oracle's own
-    tangent by the complex-step method)."""
+    written; OpenMP for its optional multi-threaded per-cell loops); with ``complex_step`` the
+    same source in complex arithmetic (the oracle's own tangent by the complex-step method)."""
     os.makedirs(BUILD, exist_ok=True)
     lib = LIB_CS if complex_step else LIB
     if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(SRC):
         tmp = lib + f".tmp{os.getpid()}"
-        flags = ["-DORACLE_COMPLEX_STEP"] if complex_step else []
+        # the double build runs its per-cell loops on oracle_set_threads() threads (1 unless
+        # asked; results are bitwise the same for any count)
+        flags = ["-DORACLE_COMPLEX_STEP"] if complex_step else ["-fopenmp"]
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
                                *flags, "-o", tmp, SRC, "-lm"])
         os.replace(tmp, lib)
@@ -88,11 +90,19 @@ def _load():
         vp = C.c_void_p
         lib.oracle_limiter.argtypes = [vp, _D, _D, _D]
         lib.oracle_gradient.argtypes = [vp, _D, _D, _D]
+        lib.oracle_bj_limiter.argtypes = [vp, _D, _D, _D]
+        lib.oracle_set_threads.argtypes = [C.c_int]
+        lib.oracle_sst_bvals.argtypes = [vp, _D]
         lib.oracle_convection.argtypes = [vp, _D, _D]
         lib.oracle_feq.argtypes = [C.c_double, C.c_double, C.c_double, _D]
         lib.oracle_sst_point.argtypes = [C.c_double] * 9 + [_D]
         _lib = lib
         return lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's per-cell loops (default 1).  The results do not depend on it."""
+    _load().oracle_set_threads(int(n))
 
 
 def feq(rho: float, u: float, v: float) -> np.ndarray:
@@ -198,6 +208,21 @@ class Oracle:
         self.lib.oracle_limiter(self._h, np.ascontiguousarray(phi, np.float64),
                                 np.ascontiguousarray(phib, np.float64), psi)
         return psi
+
+    def bj_limiter(self, phi: np.ndarray, phib: np.ndarray) -> np.ndarray:
+        """Barth-Jespersen limiter value per cell of the SST reconstruction of a scalar field
+        with boundary values phib [n_bedges], at its least-squares gradient."""
+        psi = np.zeros(self.n_cells)
+        self.lib.oracle_bj_limiter(self._h, np.ascontiguousarray(phi, np.float64),
+                                   np.ascontiguousarray(phib, np.float64), psi)
+        return psi
+
+    def sst_bvals(self) -> np.ndarray:
+        """[n_bedges, 4] boundary values (u, v, k, omega) the SST update uses at the current
+        state (zeros on periodic edges)."""
+        out = np.zeros(4 * self.n_bedges)
+        self.lib.oracle_sst_bvals(self._h, out)
+        return out.reshape(self.n_bedges, 4)
 
     def convection(self, f: np.ndarray) -> np.ndarray:
         ga = np.zeros(self.n_cells * Q)
