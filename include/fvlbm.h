@@ -43,6 +43,8 @@ extern "C" {
 #define FVLBM_ERR_CUDA (-5)        /* a CUDA runtime call failed */
 #define FVLBM_ERR_DIVERGED (-6)    /* NaN or Inf in the state (watchdog) */
 #define FVLBM_ERR_NOT_SUPPORTED (-7)
+#define FVLBM_ERR_TIMEOUT (-8)     /* a bounded wait inside a kernel gave up; the steps since the
+                                      last stats step are not valid (restore a saved state) */
 
 /* boundary-edge types */
 #define FVLBM_BC_WALL 0       /* no-slip wall moving at (u_b, v_b) */
@@ -95,7 +97,16 @@ typedef struct {
     const double *k_init;      /* [n_cells] or NULL (0) */
     const double *omega_init;  /* [n_cells] or NULL (1) */
     int kernel_path;           /* 0: fused stage kernels with shared-memory halo staging
-                                  (default); 1: two-pass kernels (gradient array in HBM) */
+                                  (default); 1: two-pass kernels (gradient array in HBM);
+                                  2: fused stage kernels in the face-value form (each cell
+                                  publishes its upwind face values once per face); 3: the
+                                  face-value form as a persistent kernel that stages the next
+                                  work item while it computes the current one.  The autotuner
+                                  may still pick any fused form.
+                                  A handle with a periodic pair whose edges are translates only
+                                  to the gluing tolerance (not to 1e-12 of the edge length)
+                                  runs the two-pass kernels: they give both sides of the glued
+                                  face side A's normal and length, as the oracle does. */
     int scheme;                /* 0: three-stage IMEX Runge-Kutta of Sec. 3.1 (default);
                                   1: explicit Euler f^{n+1} = f^n + dt (Gamma^a + Gamma^c), the
                                   original scheme that Sec. 3.1 and Sec. 4.1 compare against
@@ -185,8 +196,18 @@ int fvlbm_check_mesh(const fvlbm_mesh *mesh, const fvlbm_bc *bc, const fvlbm_par
 /* Advance n_steps time steps (Steps 1-7 of Sec. 3.2 each), asynchronously on the handle's
  * stream.  The steps are replayed from a captured CUDA graph.  When `stats` is non-NULL the
  * call synchronises and fills it (FP64 residual of the last step, mass, NaN watchdog) and
- * returns FVLBM_ERR_DIVERGED if the state is not finite. */
+ * returns FVLBM_ERR_DIVERGED if the state is not finite.  It also reads the device flag that
+ * the fused stage kernels set when a staging wait gave up: FVLBM_ERR_TIMEOUT then (the flag is
+ * cleared, so the next step starts clean; the state of the failed steps is not valid). */
 int fvlbm_step(fvlbm_handle *h, int n_steps, fvlbm_stats *stats);
+
+/* Diagnostic for the error path above (not in the paper): the number of polls the first
+ * staging wait of the fused stage kernels (kernel_path 0, 256- and 128-cell blocks) makes
+ * before giving up; default 2^26, 0 gives up after the first poll.  Only that wait changes:
+ * before a block returns it still waits, with the full bound, for its own copies in flight,
+ * so that no copy lands in shared memory after the block has left.  The face-value kernels
+ * do not wait on a barrier.  Drops the captured step graphs.  Errors: BAD_PARAM. */
+int fvlbm_set_wait_limit(fvlbm_handle *h, long long polls);
 
 /* Force on the wall faces of `instance`: F = sum over wall faces of sum_alpha e_alpha
  * (e_alpha . n) f_{alpha,bc} Delta l (momentum flux of the Eq. (advection) face values, FP64).
@@ -248,9 +269,10 @@ int fvlbm_profile_kernels(fvlbm_handle *h, int n_steps, int max_kernels, char *n
 
 /* Kernel autotuner (not in the paper).  Times trial_steps steps of each kernel configuration the
  * handle supports -- 0: fused stages with 256-cell blocks, 1: fused stages with 128-cell blocks,
- * 2: two-pass kernels -- on a snapshot of the current state, restores the state exactly, and
+ * 2: two-pass kernels, 3: fused stages in the face-value form, 4: the face-value form as a
+ * persistent kernel -- on a snapshot of the current state, restores the state exactly, and
  * keeps the fastest for all later steps.  *chosen (may be NULL) receives the configuration and
- * ms_per_step[3] (may be NULL) the measured milliseconds per step, -1 for configurations not
+ * ms_per_step[5] (may be NULL) the measured milliseconds per step, -1 for configurations not
  * available (a block's halo too large for shared memory, kernel_path 1, or the explicit
  * scheme).  Allocates a temporary snapshot of the state (about 28 words per cell) and
  * synchronises the stream.  Errors: BAD_PARAM, OOM, CUDA. */
@@ -344,6 +366,30 @@ int fvlbm_forces_tangent(fvlbm_handle *h, int instance, double dalpha, double *o
  * Errors: BAD_PARAM (w NULL, n_steps < 0, bad instance), NOT_SUPPORTED, OOM, CUDA. */
 int fvlbm_adjoint(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
                   double *dJ_dbedge_val, double *dJ_dxy);
+/* Parameter-level gradient of J = w[0] C_D + w[1] C_L (Sec. 4.3's force coefficients) after
+ * n_steps FP64 steps from the handle's current state, with respect to the three parameter
+ * kinds of the airfoil study: one fvlbm_adjoint solve, then the chain rule through
+ *   alpha  the free-stream angle in radians.  It turns the velocity (u_b, v_b) of every
+ *          FVLBM_BC_FARFIELD edge, d(u_b, v_b)/d alpha = (-v_b, u_b), and the drag and lift
+ *          axes of fvlbm_forces, dC_D/d alpha = C_L, dC_L/d alpha = -C_D;
+ *   ratio  the inflow eddy-viscosity ratio r = nu_t / nu, entering as omega_b = k_b / (nu r)
+ *          on every FVLBM_BC_FARFIELD and FVLBM_BC_INLET edge with k_b > 0 (Sec. 3.2's Menter
+ *          inflow values; r is read off each edge as k_b / (nu omega_b));
+ *   s_j    the displacement of mesh node wall_nodes[j] along the direction
+ *          wall_normals[2 j], wall_normals[2 j + 1] (the caller's choice, e.g. the outward unit
+ *          normal of the wall there), through the mesh geometry as in fvlbm_adjoint's dJ_dxy.
+ * The initial state and dt stay fixed, as in fvlbm_adjoint.
+ * Inputs: w [2] (host); n_wall >= 0; wall_nodes [n_wall] node ids of the input mesh;
+ * wall_normals [2 n_wall] (host).  Outputs (host, NULL to skip): J; cdcl [2] = C_D, C_L after
+ * the n_steps steps; dJ_dalpha; dJ_dratio (0 on laminar instances); dJ_dwall [n_wall] (needed
+ * when n_wall > 0).  Same device memory, schedule and synchronisation as fvlbm_adjoint; the
+ * handle's state is unchanged.
+ * Errors: BAD_PARAM (NULL w, bad instance, n_wall < 0, a NULL wall array with n_wall > 0, a
+ * node id out of range); NOT_SUPPORTED (not FVLBM_FP64; n_wall > 0 on a mesh with periodic
+ * pairs); OOM; CUDA. */
+int fvlbm_adjoint_params(fvlbm_handle *h, int instance, int n_steps, const double *w, int n_wall,
+                         const int *wall_nodes, const double *wall_normals, double *J, double *cdcl,
+                         double *dJ_dalpha, double *dJ_dratio, double *dJ_dwall);
 /* The device memory fvlbm_adjoint may use for stage values, in bytes (0: half the free device
  * memory at the time of the call, the default).  Errors: BAD_PARAM. */
 int fvlbm_set_adjoint_budget(fvlbm_handle *h, long long bytes);
@@ -392,7 +438,11 @@ const char *fvlbm_strerror(int code);
  * asynchronous; read `out` after synchronising that stream.
  *
  * The first call on a device looks up the device address of the scratch array
- * (cudaGetSymbolAddress); make that first call before any stream capture.  Every call shares
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  Later calls look
+ * it up again unless `stream` is being captured, so a call after cudaDeviceReset (which
+ * unloads the module, and with it the array) finds the array's new address; a call under
+ * capture uses the address of the last lookup, so do not capture the first call after a
+ * reset.  Every call shares
  * the one scratch array, so calls that overlap on the GPU (several streams or host threads)
  * race; serialise them.  Each call overwrites all the scratch it reads, so no clearing is
  * needed between calls.

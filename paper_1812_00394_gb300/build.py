@@ -18,7 +18,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfvlbm.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 SOURCES = ["fvlbm_host.cpp", "fvlbm_kernels.cu", "fvlbm_noalloc.cu"]
-HEADERS = ["fvlbm_internal.h", "fvlbm_dual.h", "fvlbm_adjoint.cuh", "fvlbm_adjoint_sst.cuh"]
+HEADERS = ["fvlbm_internal.h", "fvlbm_dual.h", "fvlbm_adjoint.cuh", "fvlbm_adjoint_sst.cuh",
+           "fvlbm_fused_fv.cuh"]
 
 
 def _nvcc() -> str:

@@ -919,7 +919,7 @@ void adj_backward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in
 }
 
 int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, double *J, double *dJ_df,
-                 double *dJ_dbedge, double *dJ_dxy) {
+                 double *dJ_dbedge, double *dJ_dxy, double *cdcl = nullptr) {
     if (!h || instance < 0 || instance >= h->ninst || n_steps < 0 || !w) return FVLBM_ERR_BAD_PARAM;
     if (h->precision != FVLBM_FP64 || h->d_back == nullptr)
         return FVLBM_ERR_NOT_SUPPORTED;
@@ -1132,6 +1132,10 @@ int adjoint_impl(fvlbm_handle *h, int instance, int n_steps, const double *w, do
         int rc = forces_impl(h, instance, 0.0, out, nullptr, nullptr, fN);
         if (rc) return rc;
         if (J) *J = w[0] * out[2] + w[1] * out[3];
+        if (cdcl) {
+            cdcl[0] = out[2];
+            cdcl[1] = out[3];
+        }
         const double q = 0.5 * I.rho0 * I.uref * I.uref * I.lref;
         const double al = I.alpha_deg * M_PI / 180.0, ca = std::cos(al), sa = std::sin(al);
         const double cx = (w[0] * ca - w[1] * sa) / q, cy = (w[0] * sa + w[1] * ca) / q;

@@ -167,6 +167,7 @@ int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_para
         face[4 * static_cast<size_t>(it->second.cell) + it->second.local].nbr = -(b + 1);
     }
     std::vector<char> glued(nbe, 0);
+    double gap = 0.0;  // largest mismatch of a glued pair (side B's own edge against side A's)
     for (int q = 0; q < bc.n_periodic; ++q) {
         const int ea = bc.periodic_pairs[2 * q], eb = bc.periodic_pairs[2 * q + 1];
         if (ea < 0 || eb < 0 || ea >= nbe || eb >= nbe || glued[ea] || glued[eb]) {
@@ -188,6 +189,8 @@ int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_para
             *why = "periodic pair " + std::to_string(q) + ": edge b is not edge a moved by the shift";
             return FVLBM_ERR_BAD_BC;
         }
+        gap = std::max(gap, std::max(std::fabs(la - lb), std::hypot(ex, ey)) / (0.5 * (la + lb)));
+        gap = std::max(gap, std::hypot(nx, ny));
         A.nbr = bside[eb].cell;
         A.back = bside[eb].local;
         A.sx = -sx;
@@ -273,6 +276,7 @@ int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_para
     PreparedT<S> &P = *out;
     P = PreparedT<S>();
     P.nc = nc;
+    P.periodic_gap = gap;
     P.np = (nc + kBlock - 1) / kBlock * kBlock;
     P.n_bedges_in = nbe;
     const size_t np = P.np;
@@ -307,6 +311,7 @@ int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_para
 
     P.nbr.assign(4 * np, kNone);
     P.back.assign(4 * np, -1);
+    P.glued.assign(4 * np, 0);
     P.nface.assign(np, 0);
     P.gq.assign(8 * np, S(0.0));
     P.sn.assign(8 * np, S(0.0));
@@ -335,6 +340,7 @@ int prepare_instance_t(const fvlbm_mesh &m, const fvlbm_bc &bc, const fvlbm_para
                 const S xj = cx[F.nbr] + F.sx, yj = cy[F.nbr] + F.sy;
                 P.nbr[l * np + k] = inv[F.nbr];
                 P.back[l * np + k] = F.back;
+                P.glued[l * np + k] = (F.sx != 0.0 || F.sy != 0.0) ? 1 : 0;
                 dx[l] = xj - cx[i];
                 dy[l] = yj - cy[i];
                 P.rnbr[(2 * l) * np + k] = F.xm - xj;
@@ -693,7 +699,7 @@ int check_prepared(const PreparedT<S> &P, std::string *why) {
     if (nc <= 0 || P.np < nc || P.np % kBlock != 0 || P.np - nc >= kBlock || nb < 0)
         return fail(FVLBM_ERR_BAD_MESH, "cell or face counts");
     const size_t n4 = 4 * np, n8 = 8 * np;
-    if (P.perm.size() != static_cast<size_t>(nc) || P.nbr.size() != n4 || P.back.size() != n4 ||
+    if (P.perm.size() != static_cast<size_t>(nc) || P.nbr.size() != n4 || P.back.size() != n4 || P.glued.size() != n4 ||
         P.nface.size() != np || P.gq.size() != n8 || P.sn.size() != n8 || P.lsq.size() != n8 ||
         P.dvec.size() != n8 || P.rown.size() != n8 || P.rnbr.size() != n8 || P.dinv.size() != n4 ||
         P.area.size() != np || P.wdist.size() != np || P.bowner.size() != unb ||
@@ -755,8 +761,9 @@ int check_prepared(const PreparedT<S> &P, std::string *why) {
     // face.  Tolerances are relative (1e-6) and far above rounding on cells down to 1e-6 of the
     // domain; a wrong slot, sign or operand misses them by O(1).
     constexpr double tol = 1e-6;
-    // Across a periodic pair the two edges agree only to the gluing tolerance (1e-4), so the
-    // checks that compare a face with the neighbour's own copy of it use a looser one.
+    // Across a periodic pair the two edges agree only to the gluing tolerance (1e-4), so on
+    // glued faces (only there) the checks that compare a face with the neighbour's own copy
+    // of it use a looser one.
     constexpr double tol_link = 1e-3;
     auto V = [np](const std::vector<S> &a, int c, size_t k) { return value_of(a[static_cast<size_t>(c) * np + k]); };
     for (int k = 0; k < nc; ++k) {
@@ -787,7 +794,8 @@ int check_prepared(const PreparedT<S> &P, std::string *why) {
             const double tx = gx[m1] - gx[m], ty = gy[m1] - gy[m], L = std::hypot(tx, ty);
             const double nlx = V(P.sn, 2 * m, k) * A, nly = V(P.sn, 2 * m + 1, k) * A;
             const int v = P.nbr[static_cast<size_t>(m) * np + k];
-            if (!(std::hypot(nlx - ty, nly + tx) <= (v >= 0 ? tol_link : tol) * L))
+            const bool per = P.glued[static_cast<size_t>(m) * np + k] != 0;
+            if (!(std::hypot(nlx - ty, nly + tx) <= (per ? tol_link : tol) * L))
                 return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": n dl is not the outward normal of the edge");
             const double rx = V(P.rown, 2 * m, k), ry = V(P.rown, 2 * m + 1, k);
             if (!(std::hypot(rx - 0.5 * (gx[m] + gx[m1]), ry - 0.5 * (gy[m] + gy[m1])) <= tol * h))
@@ -813,7 +821,7 @@ int check_prepared(const PreparedT<S> &P, std::string *why) {
                 if (!(std::hypot(dx + vx, dy + vy) <= tol * d))
                     return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": d is not the reverse of the neighbour's");
                 if (!(std::hypot(dx - (rx - qx), dy - (ry - qy)) <= tol * (std::hypot(rx, ry) + std::hypot(qx, qy))) ||
-                    !(std::hypot(qx - ox, qy - oy) <= tol_link * (std::hypot(qx, qy) + std::hypot(ox, oy) + L)))
+                    !(std::hypot(qx - ox, qy - oy) <= (per ? tol_link : tol) * (std::hypot(qx, qy) + std::hypot(ox, oy) + L)))
                     return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": neighbour-side face offset");
                 if (!(std::hypot(nlx + wx, nly + wy) <= tol * L))
                     return fail(FVLBM_ERR_BAD_MESH, at(k, m) + ": n dl is not the reverse of the neighbour's");

@@ -46,6 +46,7 @@ struct PreparedT {
     std::vector<S> rown;   // [8 np]  face midpoint - own centroid
     std::vector<S> rnbr;   // [8 np]  face midpoint - (neighbour centroid + periodic shift)
     std::vector<S> dinv;   // [4 np]  1 / |d_m| (SST central diffusion distance)
+    std::vector<unsigned char> glued;  // [4 np] 1 where face m joins a periodic partner
     std::vector<S> area;   // [np]    0 for padding cells
     std::vector<S> wdist;  // [np]    distance to the nearest wall face (1e30 if none)
     // boundary faces, ordered by input boundary-edge index (periodic edges dropped)
@@ -56,6 +57,8 @@ struct PreparedT {
     std::vector<S> blen;   // [nb]
     std::vector<int> bedge_of;  // [nb] input boundary-edge index of each boundary face
     double dt = 0.0;            // the instance's step (local stepping: the smallest dt_i)
+    double periodic_gap = 0.0;  // largest mismatch of a glued periodic pair, relative to the
+                                // edge length (0 without periodic pairs; ~1e-16 for exact ones)
     std::vector<double> dt_cell;  // [np] local time stepping: dt_i of each cell; empty otherwise
     std::vector<double> rho_i, u_i, v_i, k_i, w_i;  // initial fields, internal order [np]
 };

@@ -354,7 +354,8 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
                                               T *__restrict__ mac, double *__restrict__ partial,
                                               const T *__restrict__ area,
                                               T *__restrict__ frel = nullptr,
-                                              bool fn_read = false, T t1_i = T(0)) {
+                                              bool fn_read = false, T t1_i = T(0),
+                                              T *macv = nullptr) {
     const T rho0 = ipv<T>(P.rho0, P.rho0_f);
     const T dt = dt_i;
     const T itau = T(1) / t_i;          // one division per cell, products below
@@ -454,6 +455,11 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
         mac[0 * np + i] = r;
         mac[1 * np + i] = u;
         mac[2 * np + i] = v;
+        if (macv) {  // the new macros, for a caller that forms the statistics itself
+            macv[0] = r;
+            macv[1] = u;
+            macv[2] = v;
+        }
         if (frel != nullptr && !P.sst) {  // laminar: tau is constant, relax for the next step
             relax9(fnew, rho0, dt, t_i);
             store9(frel, np, i, fnew);
@@ -542,6 +548,7 @@ struct Halo {
     const unsigned *__restrict__ adj;   // per block [4][kBlock + r1] adjacency words
     int *__restrict__ err;              // set to 1 if a staging wait gave up
     int emax, gmax;                     // smem row strides: max ext cells, max gradient cells
+    long long wait_first;               // polls of the first staging wait (fvlbm_set_wait_limit)
 };
 
 // Compact geometry of the fused kernels: per cell the node positions relative to the centroid
@@ -572,6 +579,17 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// non-blocking test of the phase (returns at once)
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
@@ -703,8 +721,10 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
     cp_async_wait_all();
     {
         long long it = 0;
-        bool done = mbar_try_wait(bar, 0);
-        while (!done && ++it < kWaitLimit) done = mbar_try_wait(bar, 0);
+        // (a limit of 0 polls once without blocking: try_wait itself may suspend the thread for
+        // a while, test_wait returns at once)
+        bool done = H.wait_first > 0 ? mbar_try_wait(bar, 0) : mbar_test_wait(bar, 0);
+        while (!done && ++it < H.wait_first) done = mbar_try_wait(bar, 0);
         // the block leaves together if any thread gave up: flag it, wait once more (bounded)
         if (__syncthreads_or(!done)) {
             if (t == 0) atomicExch(H.err, 1);
@@ -834,6 +854,8 @@ __global__ void k_reduce_instances(const double *__restrict__ partial,
         for (int k = 0; k < 4; ++k) s[k] += partial[4 * t + k];
     block_sum<4>(s, out + 4 * inst);
 }
+
+#include "fvlbm_fused_fv.cuh"
 
 // ------------------------------------------------------------------ SST (Step 1)
 // ---- per-cell SST arithmetic, shared by the two-pass and the fused kernels
@@ -1075,14 +1097,29 @@ __global__ void __launch_bounds__(kTile)
         nbs[m] = G.nbr[m * np + i];
         has[m] = nbs[m] != kNone;
     }
-    if (COMPACT) {
-        T SN[8], RN[8], DI[4];
-        compact_face_geo(CG, np, i, has, R, SN, RN, DI, W);
+    // The least-squares weights are read as precomputed (formed in FP64 on the host): on
+    // the 1000:1 wall cells of y+ ~ 1 meshes M = sum d d^T has a condition number near 1e7, and
+    // inverting it in FP32 on chip would leave the weights with almost no correct digits.
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        W[2 * m] = G.lsq[(2 * m) * np + i];
+        W[2 * m + 1] = G.lsq[(2 * m + 1) * np + i];
+    }
+    if (COMPACT) {  // face offsets from the node positions
+        T q8[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) q8[k] = CG.gq[k * np + i];
+        const bool tri = !has[3];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const T x1 = m == 3 ? q8[0] : (m == 2 && tri ? q8[0] : q8[2 * m + 2]);
+            const T y1 = m == 3 ? q8[1] : (m == 2 && tri ? q8[1] : q8[2 * m + 3]);
+            R[2 * m] = T(0.5) * (q8[2 * m] + x1);
+            R[2 * m + 1] = T(0.5) * (q8[2 * m + 1] + y1);
+        }
     } else {
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            W[2 * m] = G.lsq[(2 * m) * np + i];
-            W[2 * m + 1] = G.lsq[(2 * m + 1) * np + i];
             R[2 * m] = G.rown[(2 * m) * np + i];
             R[2 * m + 1] = G.rown[(2 * m + 1) * np + i];
         }
@@ -1425,9 +1462,19 @@ struct fvlbm_handle {
         int *d_inst_blk0 = nullptr;
         unsigned *d_adj = nullptr;
     } hs[2];                // [0]: 256-cell blocks, [1]: 128-cell blocks
-    bool fused = false;     // fused kernels available (IMEX scheme, kernel_path 0)
-    int config = 2;         // 0: fused 256, 1: fused 128, 2: two-pass (see fvlbm_autotune)
+    struct FvSet {          // work items of the face-value fused kernels (configs 3 and 4)
+        bool ok = false;
+        int nitem = 0, n_split = 0;
+        int grid_p = 0;     // CTAs of the persistent form (SMs x resident CTAs, <= nitem)
+        int4 *d_hdr = nullptr;
+        int *d_r1 = nullptr, *d_halo = nullptr, *d_inst_item0 = nullptr;
+        uint4 *d_adj = nullptr;
+    } fv;
+    bool fused = false;     // fused kernels available (IMEX scheme, kernel_path 0 or 2)
+    int config = 2;         // 0: fused 256, 1: fused 128, 2: two-pass, 3: face-value fused,
+                            // 4: face-value fused, persistent (see fvlbm_autotune)
     int scheme = 0;         // 0: IMEX Runge-Kutta; 1: explicit Euler (comparison scheme)
+    int kernel_path = 0;    // as requested at create (fvlbm_params.kernel_path)
     bool limit_f = false;   // an instance uses the limiter variant (two-pass kernels only)
     bool nonorth = false;   // an instance uses an SST reading variant (2 or 8)
     bool per_stage = false; // SST solved before every stage (reading variant 4; two-pass only)
@@ -1446,6 +1493,7 @@ struct fvlbm_handle {
     int rollback_turb = 0;
     void *tau1 = nullptr, *mac2 = nullptr;  // per-stage SST: tau of stage 1, stage macros
     int *d_err = nullptr;   // device error flag (a staging wait gave up)
+    long long wait_first = kWaitLimit;  // polls of the fused kernels' first staging wait
     void *gq = nullptr;     // fused path: node positions minus centroid [8 np]
     void *dvec = nullptr;   // fused path: neighbour-centroid offsets d_m [8 np]
     InstParam *d_ip = nullptr;
@@ -1623,7 +1671,8 @@ void enqueue_fused(fvlbm_handle *h, bool stats, const fvlbm_handle::HaloSet &S) 
     T *B = static_cast<T *>(h->bacc), *C = static_cast<T *>(h->cacc);
     T *tau = static_cast<T *>(h->tau), *mac = static_cast<T *>(h->mac);
     T *fr = static_cast<T *>(h->frel);
-    const Halo H{S.d_halo_ptr, S.d_halo, S.d_r1, S.d_adj_ptr, S.d_adj, h->d_err, S.emax, S.gmax};
+    const Halo H{S.d_halo_ptr, S.d_halo, S.d_r1, S.d_adj_ptr, S.d_adj, h->d_err, S.emax, S.gmax,
+                 h->wait_first};
     const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
     const dim3 fg(S.nblk), fb(BLK);
     const size_t sm = S.smem;
@@ -1644,6 +1693,73 @@ void enqueue_fused(fvlbm_handle *h, bool stats, const fvlbm_handle::HaloSet &S) 
     } else {
         launch(h, K_FUSED3, "fused_stage3", [&] {
             k_fused_stage<T, 3, false, BLK><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, H, fr, CG);
+        });
+    }
+}
+
+// The three stages in the face-value form (config 3).
+template <class T>
+void enqueue_fused_fv(fvlbm_handle *h, bool stats) {
+    Geo<T> G = geo_of<T>(h);
+    cudaStream_t s = h->stream;
+    T *fn = static_cast<T *>(h->fn), *s0 = static_cast<T *>(h->s0), *s1 = static_cast<T *>(h->s1);
+    T *B = static_cast<T *>(h->bacc), *C = static_cast<T *>(h->cacc);
+    T *tau = static_cast<T *>(h->tau), *mac = static_cast<T *>(h->mac);
+    const FvItems W{h->fv.d_hdr, h->fv.d_r1, h->fv.d_halo, h->fv.d_adj, h->d_err, h->wait_first};
+    const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
+    const dim3 fg(h->fv.nitem), fb(kFvThreads);
+    const size_t sm = FvSmem<T>::bytes;
+    // stage 1 stages f^n and relaxes it on chip; no f^(1) array is kept between steps
+    launch(h, K_FUSED1, "fused_stage1", [&] {
+        k_fused_fv<T, 1, false><<<fg, fb, sm, s>>>(fn, s1, fn, B, C, tau, mac, nullptr, G, W, nullptr, CG);
+    });
+    launch(h, K_FUSED2, "fused_stage2", [&] {
+        k_fused_fv<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, W, nullptr, CG);
+    });
+    if (stats) {
+        launch(h, K_FUSED3, "fused_stage3", [&] {
+            k_fused_fv<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, W, nullptr,
+                                                      CG);
+        });
+        launch(h, K_REDUCE, "reduce", [&] {
+            k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->fv.d_inst_item0, h->d_inst_sums);
+        });
+    } else {
+        launch(h, K_FUSED3, "fused_stage3", [&] {
+            k_fused_fv<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, W, nullptr, CG);
+        });
+    }
+}
+
+// The three stages in the persistent face-value form (config 4).
+template <class T>
+void enqueue_fused_fvp(fvlbm_handle *h, bool stats) {
+    Geo<T> G = geo_of<T>(h);
+    cudaStream_t s = h->stream;
+    T *fn = static_cast<T *>(h->fn), *s0 = static_cast<T *>(h->s0), *s1 = static_cast<T *>(h->s1);
+    T *B = static_cast<T *>(h->bacc), *C = static_cast<T *>(h->cacc);
+    T *tau = static_cast<T *>(h->tau), *mac = static_cast<T *>(h->mac);
+    const FvItems W{h->fv.d_hdr, h->fv.d_r1, h->fv.d_halo, h->fv.d_adj, h->d_err, h->wait_first};
+    const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
+    const int ni = h->fv.nitem;
+    const dim3 fg(h->fv.grid_p), fb(kFvThreads);
+    const size_t sm = FvpSmem<T>::bytes;
+    launch(h, K_FUSED1, "fused_stage1", [&] {
+        k_fused_fvp<T, 1, false><<<fg, fb, sm, s>>>(fn, s1, fn, B, C, tau, mac, nullptr, G, W, CG, ni);
+    });
+    launch(h, K_FUSED2, "fused_stage2", [&] {
+        k_fused_fvp<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, W, CG, ni);
+    });
+    if (stats) {
+        launch(h, K_FUSED3, "fused_stage3", [&] {
+            k_fused_fvp<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, W, CG, ni);
+        });
+        launch(h, K_REDUCE, "reduce", [&] {
+            k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->fv.d_inst_item0, h->d_inst_sums);
+        });
+    } else {
+        launch(h, K_FUSED3, "fused_stage3", [&] {
+            k_fused_fvp<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, W, CG, ni);
         });
     }
 }
@@ -1680,7 +1796,9 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
                     k_sst_grad<T, true><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG);
                 });
                 launch(h, K_SST_UPDATE, "sst_update", [&] {
-                    T *fr = static_cast<T *>(h->frel);
+                    // the face-value stages relax f^n themselves; the other fused form reads
+                    // stage 1's f^(1), relaxed here with the new tau
+                    T *fr = h->config >= 3 ? nullptr : static_cast<T *>(h->frel);
                     if (h->nonorth)
                         k_sst_update<T, true, true><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn,
                                                                            tau, G, fn, fr, CG);
@@ -1771,6 +1889,14 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         return;
     }
     if constexpr (kHasFused<T>) {
+        if (h->config == 3) {
+            enqueue_fused_fv<T>(h, stats);
+            return;
+        }
+        if (h->config == 4) {
+            enqueue_fused_fvp<T>(h, stats);
+            return;
+        }
         if (h->config == 0) {
             enqueue_fused<T, 256>(h, stats, h->hs[0]);
             return;
@@ -1928,6 +2054,158 @@ int build_halos(fvlbm_handle *h, fvlbm_handle::HaloSet &S, int blk, const std::v
     return FVLBM_OK;
 }
 
+// Work items of the face-value kernel: every 256-cell block whose ring-1 + ring-2 halo and
+// ring-1 count fit its shared memory (kFvEcap, kFvGcap) is one item; a block that does not fit
+// is split into halves, and a half that does not fit into quarters.  Per item: the ring lists,
+// the adjacency words (cell-major) of item and ring-1 cells, and per face which member of each
+// direction pair leaves the cell through it -- decided once per face from the FP64 normal of
+// one side (e_alpha . n >= 0, the upwind rule of Eq. (advection)) and complemented on the
+// other side, so that both sides always agree.  The set is left unusable (ok = false) if a
+// quarter block still does not fit.
+template <class T>
+int build_fv_items(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<int> &back,
+                   const std::vector<double> &sn, const std::vector<int> &inst_tile0) {
+    const size_t np = h->np;
+    // outgoing bits of every (cell, face slot)
+    std::vector<unsigned char> pbits(4 * np, 0);
+    for (size_t g = 0; g < np; ++g)
+        for (int m = 0; m < 4; ++m) {
+            const int v = nbr[m * np + g];
+            if (v < 0) continue;
+            const int b = back[m * np + g];
+            const bool owner = static_cast<size_t>(v) > g || (static_cast<size_t>(v) == g && b > m);
+            const size_t cg = owner ? g : static_cast<size_t>(v);
+            const int mg = owner ? m : b;
+            const double nx = sn[(2 * mg) * np + cg], ny = sn[(2 * mg + 1) * np + cg];
+            unsigned bits = 0;
+            for (int p = 0; p < 4; ++p) {
+                const double en = p == 0 ? nx : (p == 1 ? ny : (p == 2 ? nx + ny : ny - nx));
+                if (en >= 0.0) bits |= 1u << p;
+            }
+            pbits[m * np + g] = static_cast<unsigned char>(owner ? bits : (~bits & 15u));
+        }
+    std::vector<int4> hdr;
+    std::vector<int> r1n, halo, item_inst;
+    std::vector<uint4> adj;
+    std::vector<int> local(np, -1), ring1, ring2;
+    int n_split = 0;
+    bool fits_all = true;
+    // try one item of cnt cells at base; returns false if it does not fit
+    auto try_item = [&](int base, int cnt, bool commit) -> bool {
+        for (int c = 0; c < cnt; ++c) local[base + c] = c;
+        ring1.clear();
+        ring2.clear();
+        int next = cnt;
+        for (int c = 0; c < cnt; ++c)
+            for (int m = 0; m < 4; ++m) {
+                const int v = nbr[m * np + base + c];
+                if (v >= 0 && local[v] < 0) { local[v] = next++; ring1.push_back(v); }
+            }
+        for (int g : ring1)
+            for (int m = 0; m < 4; ++m) {
+                const int v = nbr[m * np + g];
+                if (v >= 0 && local[v] < 0) { local[v] = next++; ring2.push_back(v); }
+            }
+        const int E = next, NG = cnt + static_cast<int>(ring1.size());
+        const bool fit = E <= kFvEcap && NG <= kFvGcap && static_cast<int>(ring1.size()) <= kFvR1cap;
+        if (fit && commit) {
+            hdr.push_back(make_int4(base, cnt, static_cast<int>(halo.size()), static_cast<int>(adj.size())));
+            r1n.push_back(static_cast<int>(ring1.size()));
+            halo.insert(halo.end(), ring1.begin(), ring1.end());
+            halo.insert(halo.end(), ring2.begin(), ring2.end());
+            for (int c = 0; c < NG; ++c) {
+                const int g = c < cnt ? base + c : ring1[c - cnt];
+                unsigned w[4];
+                for (int m = 0; m < 4; ++m) {
+                    const int v = nbr[m * np + g];
+                    if (v == kNone)
+                        w[m] = kFvNone;
+                    else if (v < 0)
+                        w[m] = kFvBnd | static_cast<unsigned>(-v - 1);
+                    else
+                        w[m] = static_cast<unsigned>(local[v]) | (static_cast<unsigned>(back[m * np + g]) << 16) |
+                               (static_cast<unsigned>(pbits[m * np + g]) << 18);
+                }
+                adj.push_back(make_uint4(w[0], w[1], w[2], w[3]));
+            }
+        }
+        for (int c = 0; c < cnt; ++c) local[base + c] = -1;
+        for (int g : ring1) local[g] = -1;
+        for (int g : ring2) local[g] = -1;
+        return fit;
+    };
+    std::vector<int> tile_inst_of(np / kTile);
+    for (size_t q = 0; q + 1 < inst_tile0.size(); ++q)
+        for (int tt = inst_tile0[q]; tt < inst_tile0[q + 1]; ++tt) tile_inst_of[tt] = static_cast<int>(q);
+    constexpr int IT = kFvThreads, HALF = IT / 2, QUART = IT / 4;
+    const int nblk = static_cast<int>(np / IT);
+    for (int b = 0; b < nblk && fits_all; ++b) {
+        const int base = b * IT;
+        int inst = tile_inst_of[base / kTile];
+        if (try_item(base, IT, true)) {
+            item_inst.push_back(inst);
+            continue;
+        }
+        ++n_split;
+        for (int half = 0; half < 2 && fits_all; ++half) {
+            const int hb = base + HALF * half;
+            if (try_item(hb, HALF, true)) {
+                item_inst.push_back(inst);
+                continue;
+            }
+            for (int qq = 0; qq < 2 && fits_all; ++qq) {
+                if (try_item(hb + QUART * qq, QUART, true))
+                    item_inst.push_back(inst);
+                else
+                    fits_all = false;
+            }
+        }
+    }
+    if (!fits_all || hdr.empty() || adj.size() >= (1u << 31)) return FVLBM_OK;  // not usable
+    const int nitem = static_cast<int>(hdr.size());
+    hdr.push_back(make_int4(static_cast<int>(np), 0, static_cast<int>(halo.size()), static_cast<int>(adj.size())));
+    std::vector<int> inst_item0(h->ninst + 1, nitem);
+    for (int k = nitem - 1; k >= 0; --k) inst_item0[item_inst[k]] = k;
+    for (int q = h->ninst - 1; q >= 0; --q)  // instances without items (none in practice)
+        if (inst_item0[q] > inst_item0[q + 1]) inst_item0[q] = inst_item0[q + 1];
+    if (halo.empty()) halo.push_back(0);
+    int rc;
+    if ((rc = upload_raw(h, &h->fv.d_hdr, hdr))) return rc;
+    if ((rc = upload_raw(h, &h->fv.d_r1, r1n))) return rc;
+    if ((rc = upload_raw(h, &h->fv.d_halo, halo))) return rc;
+    if ((rc = upload_raw(h, &h->fv.d_adj, adj))) return rc;
+    if ((rc = upload_raw(h, &h->fv.d_inst_item0, inst_item0))) return rc;
+    CK(cudaFuncSetAttribute(k_fused_fv<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            static_cast<int>(FvSmem<T>::bytes)));
+    CK(cudaFuncSetAttribute(k_fused_fv<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            static_cast<int>(FvSmem<T>::bytes)));
+    CK(cudaFuncSetAttribute(k_fused_fv<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            static_cast<int>(FvSmem<T>::bytes)));
+    CK(cudaFuncSetAttribute(k_fused_fv<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            static_cast<int>(FvSmem<T>::bytes)));
+    const int pb = static_cast<int>(FvpSmem<T>::bytes);
+    CK(cudaFuncSetAttribute(k_fused_fvp<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb));
+    CK(cudaFuncSetAttribute(k_fused_fvp<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb));
+    CK(cudaFuncSetAttribute(k_fused_fvp<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb));
+    CK(cudaFuncSetAttribute(k_fused_fvp<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb));
+    {  // persistent grid: every SM times the CTAs of the tightest stage kernel that fit on it
+        int dev = 0, sms = 0, per = 1 << 30, occ = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_fvp<T, 1, false>, kFvThreads, pb));
+        per = std::min(per, occ);
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_fvp<T, 2, false>, kFvThreads, pb));
+        per = std::min(per, occ);
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_fvp<T, 3, true>, kFvThreads, pb));
+        per = std::min(per, occ);
+        h->fv.grid_p = std::max(1, std::min(static_cast<int>(hdr.size()) - 1, sms * std::max(per, 1)));
+    }
+    h->fv.nitem = nitem;
+    h->fv.n_split = n_split;
+    h->fv.ok = true;
+    return FVLBM_OK;
+}
+
 // f^(1) of the coming step from the current f^n and tau, for every cell (after create and
 // set_f); the fused stage-1 kernel reads it.
 template <class T>
@@ -2067,7 +2345,10 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
         if (h->fused) {
             if ((rc = build_halos<T>(h, h->hs[0], 256, nbr, back, nface, inst_tile0))) return rc;
             if ((rc = build_halos<T>(h, h->hs[1], 128, nbr, back, nface, inst_tile0))) return rc;
+            if ((rc = build_fv_items<T>(h, nbr, back, sn, inst_tile0))) return rc;
             h->config = h->hs[0].ok ? 0 : (h->hs[1].ok ? 1 : 2);
+            if (h->fv.ok && (h->kernel_path == 2 || h->config == 2)) h->config = 3;
+            if (h->fv.ok && h->kernel_path == 3) h->config = 4;
             if (h->config == 2) h->fused = false;
         }
     }
@@ -2163,8 +2444,16 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
         if (((params[q].variant ^ params[0].variant) & 4) != 0) return FVLBM_ERR_BAD_PARAM;
     }
     h->per_stage = (params[0].variant & 4) != 0;
-    h->fused = params[0].kernel_path == 0 && h->scheme == 0 && prec != FVLBM_FP64_TANGENT &&
-               !h->limit_f && !h->per_stage;
+    // The fused and compact-geometry kernels derive n dl of a face from the cell's own nodes.
+    // Across a periodic pair whose edges agree only to a file's precision, side B's own edge
+    // is not side A's reversed, which every other path uses for both sides (one face, one
+    // flux): such handles keep the precomputed geometry of the two-pass kernels.
+    bool periodic_inexact = false;
+    for (int q = 0; q < n; ++q) periodic_inexact |= !(P[q]->periodic_gap <= 1e-12);
+    h->kernel_path = params[0].kernel_path;
+    if (h->kernel_path < 0 || h->kernel_path > 3) return FVLBM_ERR_BAD_PARAM;
+    h->fused = h->kernel_path != 1 && h->scheme == 0 && prec != FVLBM_FP64_TANGENT &&
+               !h->limit_f && !h->per_stage && !periodic_inexact;
     h->ninst = n;
     int cell_off = 0, bface_off = 0;
     std::vector<int> tile_inst, inst_tile0;
@@ -2455,7 +2744,9 @@ int fvlbm_step(fvlbm_handle *h, int n_steps, fvlbm_stats *stats) {
         CK(cudaStreamSynchronize(h->stream));
         if (err) {
             fprintf(stderr, "fvlbm_step: a fused-kernel staging wait gave up\n");
-            return FVLBM_ERR_CUDA;
+            CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));  // the next step starts clean
+            CK(cudaStreamSynchronize(h->stream));
+            return FVLBM_ERR_TIMEOUT;
         }
         stats->steps = h->steps;
         stats->residual = 0;
@@ -2667,6 +2958,67 @@ int fvlbm_adjoint(fvlbm_handle *h, int instance, int n_steps, const double *w, d
     return adjoint_impl(h, instance, n_steps, w, J, dJ_df, dJ_dbedge_val, dJ_dxy);
 }
 
+// Parameter gradient of J = w[0] C_D + w[1] C_L (see the header): one adjoint solve, then
+// the chain rule through the parameter map on the host.
+//   alpha: far-field velocity (u_b, v_b) rotated by alpha, d(u_b, v_b)/d alpha = (-v_b, u_b),
+//          and the drag / lift axes, dC_D/d alpha = C_L, dC_L/d alpha = -C_D;
+//   ratio: omega_b = k_b / (nu ratio) on far-field and inlet edges with k_b > 0,
+//          d omega_b / d ratio = -omega_b / ratio = -omega_b^2 nu / k_b;
+//   wall node j displaced along n_j: dJ/d s_j = dJ/d(x, y)_node . n_j.
+int fvlbm_adjoint_params(fvlbm_handle *h, int instance, int n_steps, const double *w, int n_wall,
+                         const int *wall_nodes, const double *wall_normals, double *J, double *cdcl,
+                         double *dJ_dalpha, double *dJ_dratio, double *dJ_dwall) {
+    if (!h || instance < 0 || instance >= h->ninst || !w || n_wall < 0 ||
+        (n_wall > 0 && (!wall_nodes || !wall_normals || !dJ_dwall)))
+        return FVLBM_ERR_BAD_PARAM;
+    if (h->precision != FVLBM_FP64) return FVLBM_ERR_NOT_SUPPORTED;
+    const InstInfo &I = h->inst[instance];
+    if (!I.mesh) return FVLBM_ERR_NOT_SUPPORTED;
+    const MeshCopy &mc = *I.mesh;
+    for (int j = 0; j < n_wall; ++j)
+        if (wall_nodes[j] < 0 || wall_nodes[j] >= I.n_nodes) return FVLBM_ERR_BAD_PARAM;
+    const int nbe = I.n_bedges_in;
+    std::vector<double> dbv(5 * static_cast<size_t>(std::max(nbe, 1)), 0.0);
+    std::vector<double> dxy;
+    if (n_wall > 0) dxy.assign(2 * static_cast<size_t>(I.n_nodes), 0.0);
+    double Jv = 0.0, cc[2] = {0.0, 0.0};
+    const int rc = adjoint_impl(h, instance, n_steps, w, &Jv, nullptr, dbv.data(),
+                                n_wall > 0 ? dxy.data() : nullptr, cc);
+    if (rc) return rc;
+    double da = w[0] * cc[1] - w[1] * cc[0], dr = 0.0;
+    for (int b = 0; b < nbe; ++b) {
+        const int t = mc.btype[b];
+        const double *v = &mc.bval[5 * static_cast<size_t>(b)];
+        const double *g = &dbv[5 * static_cast<size_t>(b)];
+        if (t == FVLBM_BC_FARFIELD) da += g[1] * (-v[2]) + g[2] * v[1];
+        if ((t == FVLBM_BC_FARFIELD || t == FVLBM_BC_INLET) && v[3] > 0.0)
+            dr += g[4] * (-v[4] * v[4] * I.nu / v[3]);
+    }
+    for (int j = 0; j < n_wall; ++j) {
+        const size_t nd = static_cast<size_t>(wall_nodes[j]);
+        dJ_dwall[j] = dxy[2 * nd] * wall_normals[2 * j] + dxy[2 * nd + 1] * wall_normals[2 * j + 1];
+    }
+    if (J) *J = Jv;
+    if (cdcl) {
+        cdcl[0] = cc[0];
+        cdcl[1] = cc[1];
+    }
+    if (dJ_dalpha) *dJ_dalpha = da;
+    if (dJ_dratio) *dJ_dratio = dr;
+    return FVLBM_OK;
+}
+
+int fvlbm_set_wait_limit(fvlbm_handle *h, long long polls) {
+    if (!h || polls < 0) return FVLBM_ERR_BAD_PARAM;
+    h->wait_first = polls;
+    for (int k = 0; k < 3; ++k)  // captured graphs bake the kernel arguments
+        if (h->graph[k]) {
+            cudaGraphExecDestroy(h->graph[k]);
+            h->graph[k] = nullptr;
+        }
+    return FVLBM_OK;
+}
+
 int fvlbm_set_adjoint_budget(fvlbm_handle *h, long long bytes) {
     if (!h || bytes < 0) return FVLBM_ERR_BAD_PARAM;
     h->adj_budget = static_cast<size_t>(bytes);
@@ -2849,8 +3201,8 @@ int fvlbm_autotune(fvlbm_handle *h, int trial_steps, int *chosen, double *ms_per
     if (!h || trial_steps <= 0) return FVLBM_ERR_BAD_PARAM;
     CK(cudaSetDevice(h->device));
     if (ms_per_step)
-        for (int c = 0; c < 3; ++c) ms_per_step[c] = -1.0;
-    if (h->scheme != 0 || (!h->hs[0].ok && !h->hs[1].ok)) {  // nothing to choose
+        for (int c = 0; c < 5; ++c) ms_per_step[c] = -1.0;
+    if (h->scheme != 0 || (!h->hs[0].ok && !h->hs[1].ok && !h->fv.ok)) {  // nothing to choose
         if (chosen) *chosen = h->config;
         return FVLBM_OK;
     }
@@ -2879,8 +3231,9 @@ int fvlbm_autotune(fvlbm_handle *h, int trial_steps, int *chosen, double *ms_per
     double best = 1e300;
     int best_c = h->config;
     cudaError_t err = cudaSuccess;
-    for (int c = 0; c < 3 && err == cudaSuccess; ++c) {
+    for (int c = 0; c < 5 && err == cudaSuccess; ++c) {
         if (c < 2 && !h->hs[c].ok) continue;
+        if (c >= 3 && !h->fv.ok) continue;
         h->config = c;
         for (int k = 0; k < 2; ++k) enqueue(h, false);  // warm-up
         cudaEventRecord(e0, h->stream);
@@ -3010,6 +3363,7 @@ const char *fvlbm_strerror(int code) {
     case FVLBM_ERR_CUDA: return "CUDA runtime error";
     case FVLBM_ERR_DIVERGED: return "state diverged (NaN or Inf)";
     case FVLBM_ERR_NOT_SUPPORTED: return "not supported";
+    case FVLBM_ERR_TIMEOUT: return "a bounded wait inside a kernel gave up";
     default: return "unknown error";
     }
 }

@@ -22,6 +22,7 @@ FVLBM_ERR_OOM = -4
 FVLBM_ERR_CUDA = -5
 FVLBM_ERR_DIVERGED = -6
 FVLBM_ERR_NOT_SUPPORTED = -7
+FVLBM_ERR_TIMEOUT = -8
 FVLBM_FP64 = 0
 FVLBM_FP32_DEV = 1
 FVLBM_FP64_TANGENT = 2
@@ -69,7 +70,7 @@ EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "
            "fvlbm_set_adjoint_budget", "fvlbm_state_bytes", "fvlbm_save_state",
            "fvlbm_load_state", "fvlbm_set_rollback", "fvlbm_set_f_async",
            "fvlbm_get_fields_async", "fvlbm_wait", "fvlbm_get_fdev_f32", "fvlbm_set_fdev_f32_async",
-           "fvlbm_check_mesh"]
+           "fvlbm_check_mesh", "fvlbm_adjoint_params", "fvlbm_set_wait_limit"]
 
 _lib = None
 
@@ -117,6 +118,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_forces_tangent.argtypes = [vp, i, d, vp, vp]
     lib.fvlbm_adjoint.argtypes = [vp, i, i, vp, vp, vp, vp, vp]
     lib.fvlbm_set_adjoint_budget.argtypes = [vp, C.c_longlong]
+    lib.fvlbm_adjoint_params.argtypes = [vp, i, i, vp, i, vp, vp, vp, vp, vp, vp, vp]
+    lib.fvlbm_set_wait_limit.argtypes = [vp, C.c_longlong]
     lib.fvlbm_destroy.argtypes = [vp]
     lib.fvlbm_destroy.restype = None
     lib.fvlbm_strerror.argtypes = [i]
@@ -273,10 +276,10 @@ def fvlbm_autotune(h, trial_steps: int = 5):
     """Time the available kernel configurations on a snapshot and keep the fastest.
     Returns (chosen, {name: ms_per_step})."""
     chosen = C.c_int()
-    ms = np.zeros(3)
+    ms = np.zeros(5)
     _check(load().fvlbm_autotune(h, int(trial_steps), C.byref(chosen), _p(ms)), "fvlbm_autotune")
-    names = ("fused256", "fused128", "twopass")
-    return names[chosen.value], {names[k]: float(ms[k]) for k in range(3) if ms[k] >= 0}
+    names = ("fused256", "fused128", "twopass", "facevalue", "facevalue_persistent")
+    return names[chosen.value], {names[k]: float(ms[k]) for k in range(5) if ms[k] >= 0}
 
 
 def fvlbm_tangent_seed(h, instance: int, dbedge_val: np.ndarray | None = None,
@@ -327,6 +330,28 @@ def fvlbm_adjoint(h, instance: int, n_steps: int, w_cd: float = 0.0, w_cl: float
     return J.value, df, db, dxy
 
 
+def fvlbm_adjoint_params(h, instance: int, n_steps: int, w_cd: float, w_cl: float,
+                         wall_nodes=None, wall_normals=None) -> dict:
+    """Gradient of J = w_cd C_D + w_cl C_L after n_steps FP64 steps with respect to the
+    free-stream angle (radians), the inflow eddy-viscosity ratio and the displacement of each
+    node ``wall_nodes[j]`` along ``wall_normals[j]`` (see fvlbm_adjoint_params in the header).
+    Returns {"J", "cd", "cl", "dalpha", "dratio", "dwall"}."""
+    nodes = np.zeros(0, np.int32) if wall_nodes is None else np.ascontiguousarray(wall_nodes, np.int32)
+    nw = int(nodes.shape[0])
+    normals = (np.zeros((0, 2)) if wall_normals is None
+               else np.ascontiguousarray(wall_normals, np.float64).reshape(nw, 2))
+    w = np.array([w_cd, w_cl], np.float64)
+    J, da, dr = C.c_double(), C.c_double(), C.c_double()
+    cdcl = np.zeros(2)
+    dwall = np.zeros(nw)
+    _check(load().fvlbm_adjoint_params(h, instance, int(n_steps), _p(w), nw,
+                                       _p(nodes) if nw else None, _p(normals) if nw else None,
+                                       C.byref(J), _p(cdcl), C.byref(da), C.byref(dr),
+                                       _p(dwall) if nw else None), "fvlbm_adjoint_params")
+    return {"J": J.value, "cd": float(cdcl[0]), "cl": float(cdcl[1]), "dalpha": da.value,
+            "dratio": dr.value, "dwall": dwall}
+
+
 def fvlbm_save_state(h) -> bytes:
     """The handle's state as an opaque blob (checkpoint)."""
     n = C.c_longlong()
@@ -340,6 +365,11 @@ def fvlbm_load_state(h, blob: bytes) -> None:
     """Restore a blob written by fvlbm_save_state (same meshes and parameters)."""
     buf = C.create_string_buffer(blob, len(blob))
     _check(load().fvlbm_load_state(h, buf, len(blob)), "fvlbm_load_state")
+
+
+def fvlbm_set_wait_limit(h, polls: int) -> None:
+    """Diagnostic: polls of the fused kernels' first staging wait (see the header)."""
+    _check(load().fvlbm_set_wait_limit(h, int(polls)), "fvlbm_set_wait_limit")
 
 
 def fvlbm_set_rollback(h, every: int) -> None:
@@ -487,3 +517,8 @@ class Solver:
         """(J, dJ/df, dJ/dbedge_val, dJ/dxy or None); see fvlbm_adjoint."""
         nn = self.n_nodes[i] if shape else None
         return fvlbm_adjoint(self.h, i, n_steps, w_cd, w_cl, nn)
+
+    def adjoint_params(self, n_steps: int, w_cd: float = 0.0, w_cl: float = 0.0, i: int = 0,
+                       wall_nodes=None, wall_normals=None) -> dict:
+        """See fvlbm_adjoint_params."""
+        return fvlbm_adjoint_params(self.h, i, n_steps, w_cd, w_cl, wall_nodes, wall_normals)

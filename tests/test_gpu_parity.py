@@ -41,7 +41,7 @@ CASES_FP64 = {
 }
 
 
-@pytest.mark.parametrize("path", [0, 1], ids=["fused", "twopass"])
+@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
 @pytest.mark.parametrize("name", sorted(CASES_FP64))
 def test_fp64_step_parity(name, path):
     case = CASES_FP64[name]()
@@ -68,7 +68,7 @@ def test_fp64_delaunay_full_size_z5_and_z50():
         assert _rel_max(s.get_f(), o.get_f()) < 1e-10, z
 
 
-@pytest.mark.parametrize("path", [0, 1], ids=["fused", "twopass"])
+@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
 @pytest.mark.parametrize("maker", [lambda: mg.bfs_hybrid(n_target=3000),
                                    lambda: mg.naca0012_cmesh(n_target=4000, alpha_deg=5.0)])
 def test_fp64_sst_parity(maker, path):
@@ -154,7 +154,7 @@ def test_set_f_get_f_roundtrip_and_watchdog():
     assert st["diverged"] == 1
 
 
-@pytest.mark.parametrize("path", [0, 1], ids=["fused", "twopass"])
+@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
 def test_fp32_dev_cavity_parity(path):
     case = mg.cavity_quad(64, re=400.0)
     s = fvlbm.Solver(case, precision=FP32, device=0, kernel_path=path)
@@ -174,7 +174,7 @@ def test_fp32_dev_delaunay_full_size():
     assert _vel_l2(s.fields(), o.fields()) < 1e-4
 
 
-@pytest.mark.parametrize("path", [0, 1], ids=["fused", "twopass"])
+@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
 @pytest.mark.parametrize("maker", [lambda: mg.bfs_hybrid(n_target=3000),
                                    lambda: mg.naca0012_cmesh(n_target=4000, alpha_deg=7.0)])
 def test_fp32_dev_sst_parity(maker, path):
@@ -189,34 +189,91 @@ def test_fp32_dev_sst_parity(maker, path):
     assert _rel_l2(fg["omega"], fo["omega"]) < 1e-3
 
 
-def test_fp32_dev_forces_within_half_percent():
+@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
+def test_fp32_dev_forces_within_half_percent(path):
+    """C_D and C_L each within 0.5 % of itself (the benchmark spec's bound on the force
+    coefficients), at alpha = 7 degrees where both are far from zero."""
     case = mg.naca0012_cmesh(n_target=4000, alpha_deg=7.0)
-    s = fvlbm.Solver(case, precision=FP32, device=0)
+    s = fvlbm.Solver(case, precision=FP32, device=0, kernel_path=path)
     o = Oracle(case)
     s.step(10)
     o.step(10)
     fg, fo = s.forces(), o.forces()
-    scale = math.hypot(fo["cd"], fo["cl"])
-    assert abs(fg["cd"] - fo["cd"]) <= 5e-3 * scale
-    assert abs(fg["cl"] - fo["cl"]) <= 5e-3 * scale
+    assert abs(fo["cd"]) > 1e-3 and abs(fo["cl"]) > 1e-3
+    assert abs(fg["cd"] - fo["cd"]) <= 5e-3 * abs(fo["cd"])
+    assert abs(fg["cl"] - fo["cl"]) <= 5e-3 * abs(fo["cl"])
 
 
-def test_fused_matches_twopass_fp64():
-    """The fused shared-memory kernels and the two-pass kernels compute the same step (FP64, up
-    to the rounding of the neighbour reconstruction offsets)."""
+@pytest.mark.parametrize("path", [0, 2, 3], ids=["fused", "facevalue", "persistent"])
+def test_fused_matches_twopass_fp64(path):
+    """The fused shared-memory kernels (either form) and the two-pass kernels compute the same
+    step (FP64, up to the rounding of the reconstruction offsets and the summation order)."""
     case = mg.naca0012_cmesh(n_target=6000, alpha_deg=4.0)
-    a = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=0)
+    a = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=path)
     b = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
     a.step(5)
     b.step(5)
     assert _rel_max(a.get_f(), b.get_f()) < 1e-12
 
 
-def test_full_sweep_fp32_sampled_against_oracle():
+def test_periodic_box_read_with_six_digits():
+    """A periodic mesh whose nodes were written with 6 decimals glues only to ~1e-5 of an edge.
+    Every path must give both sides of a glued face one normal and length (side A's), as the
+    oracle does: the fused request runs the two-pass kernels for such a handle, FP64 matches
+    the oracle to 1e-10 and conserves mass to round-off on the closed (periodic) domain."""
+    m = mg.periodic_box(16, kind="tri", jitter=0.2, seed=9)
+    rounded = dataclasses.replace(m, xy=np.round(m.xy, 6))
+    n = rounded.n_cells
+    rng = np.random.default_rng(3)
+    case = mg.Case(rounded, nu=2e-3, cfl=0.5, rho=1.0 + 1e-3 * rng.uniform(-1, 1, n),
+                   u=0.05 * rng.uniform(-1, 1, n), v=0.05 * rng.uniform(-1, 1, n))
+    fused = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=0)
+    face = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=3)
+    twop = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    o = Oracle(case)
+    m0 = fused.step(1, stats=True)["mass"]
+    for s in (face, twop):
+        s.step(1)
+    for s in (fused, face, twop):
+        s.step(18)
+    m1 = fused.step(1, stats=True)["mass"]
+    for s in (face, twop):
+        s.step(1)
+    o.step(20)
+    assert _rel_max(fused.get_f(), twop.get_f()) < 1e-12
+    assert _rel_max(face.get_f(), twop.get_f()) < 1e-12
+    assert _rel_max(fused.get_f(), o.get_f()) < 1e-10
+    assert abs(m1 - m0) <= 1e-13 * m0
+
+
+@pytest.mark.parametrize("maker", [lambda: mg.naca0012_cmesh(n_target=60000, alpha_deg=8.0, seed=3001),
+                                   lambda: mg.bfs_hybrid(n_target=80000, seed=2000)],
+                         ids=["naca60k", "bfs80k"])
+@pytest.mark.parametrize("path", [2, 3], ids=["facevalue", "persistent"])
+def test_fp32_long_run_within_target_of_fp64(maker, path):
+    """Over 1,010 steps (the length the benchmark's default run reaches) the FP32 deviation path
+    of the face-value kernels stays within the benchmark spec's bounds of the FP64 path: velocity
+    relative L2 <= 1e-4 and C_D, C_L each within 0.5 %.  The FP64 GPU path is the reference
+    here because it matches the oracle to 1e-10 per step (the parity tests above); running
+    the CPU oracle itself for 1,010 steps of these meshes would take minutes."""
+    case = maker()
+    a = fvlbm.Solver(case, precision=FP32, device=0, kernel_path=path)
+    b = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
+    a.step(1010)
+    b.step(1010)
+    assert _vel_l2(a.fields(), b.fields()) <= 1e-4
+    fa, fb = a.forces(), b.forces()
+    for key in ("cd", "cl"):
+        if abs(fb[key]) > 1e-3:
+            assert abs(fa[key] - fb[key]) <= 5e-3 * abs(fb[key]), key
+
+
+@pytest.mark.parametrize("path", [0, 2, 3], ids=["fused", "facevalue", "persistent"])
+def test_full_sweep_fp32_sampled_against_oracle(path):
     """The benchmark's workload and launch configuration (48 instances in one FP32 handle, fused
     kernels, graph replay): after 2 steps, sampled instances match the FP64 oracle."""
     cases = mg.batched_sweep()
-    s = fvlbm.Solver(cases, precision=FP32, device=0)
+    s = fvlbm.Solver(cases, precision=FP32, device=0, kernel_path=path)
     s.step(2)
     for i in (0, 17, 32, 36, 47):
         o = Oracle(cases[i])
@@ -316,7 +373,7 @@ def _single_triangle(lid=0.1):
     return mg.Case(m, nu=0.01, cfl=0.4)
 
 
-@pytest.mark.parametrize("path", [0, 1], ids=["fused", "twopass"])
+@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
 def test_single_cell_mesh(path):
     """One triangle with three wall faces (one moving): a block of 255 padding cells and one
     real cell."""
@@ -351,7 +408,7 @@ def test_autotune_restores_state_and_keeps_parity(prec):
     before = [s.get_f(i) for i in range(2)]
     om = s.fields(0)["omega"]
     chosen, times = s.autotune(3)
-    assert chosen in ("fused256", "fused128", "twopass")
+    assert chosen in ("fused256", "fused128", "twopass", "facevalue", "facevalue_persistent")
     assert set(times) >= {"twopass"} and all(t > 0 for t in times.values())
     for i in range(2):
         assert np.array_equal(s.get_f(i), before[i])
@@ -407,7 +464,7 @@ LOCAL_CASES = {
 }
 
 
-@pytest.mark.parametrize("path", [0, 1], ids=["fused", "twopass"])
+@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
 @pytest.mark.parametrize("name", sorted(LOCAL_CASES))
 def test_local_dt_parity_fp64(name, path):
     """Local time stepping: every cell's own dt in the stages, the implicit collision and the
@@ -653,3 +710,25 @@ def test_fp32_deviation_io_roundtrip_and_pipeline():
     np.testing.assert_array_equal(d2, d0[s.cells[0]:])
     w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
     np.testing.assert_allclose(d2.astype(np.float64) + w * 1.0, s.get_f(1), rtol=0, atol=1e-15)
+
+
+def test_staging_wait_give_up_is_reported_and_cleared():
+    """The bounded staging wait of the fused kernel (kernel_path 0) reports FVLBM_ERR_TIMEOUT
+    through the device flag that a stats step reads; the flag is cleared, and with the normal
+    bound back and the saved state restored the next steps are clean and match the oracle.  No
+    fault is involved: only the first wait is shortened (to one poll); every block still waits,
+    with the full bound, for its own copies before it returns."""
+    case = mg.naca0012_cmesh(n_target=6000, alpha_deg=4.0)
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=0)
+    blob = s.save_state()
+    fvlbm.fvlbm_set_wait_limit(s.h, 0)
+    with pytest.raises(fvlbm.FvlbmError) as ei:
+        s.step(2, stats=True)
+    assert ei.value.code == fvlbm.FVLBM_ERR_TIMEOUT
+    fvlbm.fvlbm_set_wait_limit(s.h, 1 << 26)
+    s.load_state(blob)
+    st = s.step(3, stats=True)
+    assert st["diverged"] == 0
+    o = Oracle(case)
+    o.step(3)
+    assert _rel_max(s.get_f(), o.get_f()) < 1e-10
