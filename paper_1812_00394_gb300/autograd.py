@@ -16,11 +16,11 @@ Two backward passes compute the same derivatives of the discrete step:
     tangent solve with one instance per parameter gives every column of the Jacobian
     J = d(C_L, C_D)/dp at once, and the gradient is grad_output @ J.  Its cost grows with the
     number of parameters.
-  - "adjoint": the library's reverse mode (fvlbm_adjoint); one adjoint solve of
-    J_w = grad_output . (C_L, C_D) gives dJ_w/d(boundary values) and dJ_w/d(node positions);
-    the gradient is their projection on the parameters plus the explicit dependence of the drag
-    and lift directions on alpha.  Its cost does not grow with the number of parameters.  It
-    covers every reading variant.
+  - "adjoint": the library's reverse mode at the parameter level (fvlbm_adjoint_params): one
+    adjoint solve of J_w = grad_output . (C_L, C_D), and the library's own chain rule to the
+    angle, the ratio and the wall displacements (including the explicit dependence of the drag
+    and lift directions on alpha).  This module only packs arrays.  Its cost does not grow
+    with the number of parameters.  It covers every reading variant.
 The default ("auto") takes the adjoint.
 
 ``step_forces(model, f0, bval, xy)`` (with a ``StepForces`` model) is the full-input form:
@@ -119,22 +119,16 @@ class AirfoilForces:
         return d_alpha, d_ratio
 
     def vjp(self, p: np.ndarray, g: np.ndarray, out: np.ndarray) -> np.ndarray:
-        """g @ d(C_L, C_D)/dp from one adjoint solve; out = (C_L, C_D) at p."""
-        case = self.case_at(p)
-        d_alpha, d_ratio = self._bval_directions(case, p)
-        s = fvlbm.Solver(case, precision=fvlbm.FVLBM_FP64, device=self.device, kernel_path=1)
-        # J_w = g0 C_L + g1 C_D
-        shape = len(self.wall_nodes) > 0
-        _, _, dbv, dxy = s.adjoint(self.steps, w_cd=float(g[1]), w_cl=float(g[0]), shape=shape)
+        """g @ d(C_L, C_D)/dp (g ordered like the outputs C_L, C_D) from the library's
+        parameter-level adjoint, fvlbm_adjoint_params: one adjoint solve of
+        J = g_CD C_D + g_CL C_L and its chain rule to (alpha, ratio, wall displacements), all
+        behind the C ABI."""
+        s = fvlbm.Solver(self.case_at(p), precision=fvlbm.FVLBM_FP64, device=self.device,
+                         kernel_path=1)
+        r = s.adjoint_params(self.steps, w_cd=float(g[1]), w_cl=float(g[0]),
+                             wall_nodes=self.wall_nodes, wall_normals=self.normals)
         s.close()
-        # dC_D/dalpha = C_L and dC_L/dalpha = -C_D through the drag and lift directions
-        proj = float(g[1]) * out[0] - float(g[0]) * out[1]
-        grad = np.empty(self.n_params())
-        grad[0] = float(np.sum(dbv * d_alpha)) + proj
-        grad[1] = float(np.sum(dbv * d_ratio))
-        if shape:
-            grad[2:] = np.einsum("jc,jc->j", dxy[self.wall_nodes], self.normals)
-        return grad
+        return np.concatenate([[r["dalpha"], r["dratio"]], r["dwall"]])
 
     def jacobian(self, p: np.ndarray) -> np.ndarray:
         """J[o, q] = d output_o / d p_q (outputs C_L, C_D) from one batched tangent solve."""
@@ -156,7 +150,7 @@ class _ForcesFunction(torch.autograd.Function):
         pn = p.detach().cpu().double().numpy()
         out = model.value(pn)
         ctx.model, ctx.pn, ctx.out = model, pn, out
-        return torch.as_tensor(out, dtype=p.dtype)
+        return torch.as_tensor(out, dtype=p.dtype, device=p.device)
 
     @staticmethod
     def backward(ctx, grad_out):
@@ -165,7 +159,7 @@ class _ForcesFunction(torch.autograd.Function):
             g = ctx.model.vjp(ctx.pn, gn, ctx.out)
         else:
             g = gn @ ctx.model.jacobian(ctx.pn)
-        return torch.as_tensor(g, dtype=grad_out.dtype), None
+        return torch.as_tensor(g, dtype=grad_out.dtype, device=grad_out.device), None
 
 
 def forces(model: AirfoilForces, p: torch.Tensor) -> torch.Tensor:
@@ -213,7 +207,8 @@ class _StepForcesFunction(torch.autograd.Function):
         f = s.forces()
         s.close()
         ctx.model, ctx.arrs = model, arrs
-        return torch.tensor([f["cd"], f["cl"]], dtype=torch.float64)
+        ctx.devs = [t.device for t in (f0, bval, xy)]
+        return torch.tensor([f["cd"], f["cl"]], dtype=torch.float64, device=f0.device)
 
     @staticmethod
     def backward(ctx, g):
@@ -222,10 +217,10 @@ class _StepForcesFunction(torch.autograd.Function):
         _, df, db, dxy = s.adjoint(ctx.model.steps, w_cd=float(gn[0]), w_cl=float(gn[1]),
                                    shape=ctx.needs_input_grad[2])
         s.close()
-        as_t = lambda a: None if a is None else torch.as_tensor(a, dtype=torch.float64)  # noqa: E731
-        return (as_t(df) if ctx.needs_input_grad[0] else None,
-                as_t(db) if ctx.needs_input_grad[1] else None,
-                as_t(dxy) if ctx.needs_input_grad[2] else None, None)
+        as_t = lambda a, d: None if a is None else torch.as_tensor(a, dtype=torch.float64, device=d)  # noqa: E731
+        return (as_t(df, ctx.devs[0]) if ctx.needs_input_grad[0] else None,
+                as_t(db, ctx.devs[1]) if ctx.needs_input_grad[1] else None,
+                as_t(dxy, ctx.devs[2]) if ctx.needs_input_grad[2] else None, None)
 
 
 def step_forces(model: StepForces, f0: torch.Tensor, bval: torch.Tensor, xy: torch.Tensor) -> torch.Tensor:

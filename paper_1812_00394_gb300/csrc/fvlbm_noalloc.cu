@@ -31,10 +31,16 @@ std::mutex g_mu;
 double *g_partials_addr[kMaxDevices] = {nullptr};
 
 // Device address of g_partials on the current device (the host-side symbol is only a
-// stand-in and must never be passed to a kernel).  Looked up once per device.
-cudaError_t partials_address(int device, double **out) {
+// stand-in and must never be passed to a kernel).  The first call on a device looks it up.
+// Later calls look it up again whenever `stream` is not being captured, so that a context
+// that was reset (cudaDeviceReset) and loaded the module anew is never handed a stale
+// address; while a capture is under way the address cached by the last lookup is used, since
+// a lookup might load the module and that is not allowed during a capture.
+cudaError_t partials_address(int device, cudaStream_t stream, double **out) {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_partials_addr[device]) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusActive;
+    if (!g_partials_addr[device] || cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
         if (e != cudaSuccess) return e;
@@ -114,9 +120,9 @@ extern "C" int fvlbm_stats_reduce_static(const double *u_old, const double *v_ol
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= kMaxDevices)
         return FVLBM_ERR_CUDA;
-    double *partials = nullptr;
-    if (partials_address(device, &partials) != cudaSuccess) return FVLBM_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *partials = nullptr;
+    if (partials_address(device, s, &partials) != cudaSuccess) return FVLBM_ERR_CUDA;
     const int nblocks = (n + kThreads - 1) / kThreads;
     if (nblocks > 0)
         k_stats_partials<<<nblocks, kThreads, 0, s>>>(u_old, v_old, u_new, v_new, rho, area, n,
