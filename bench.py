@@ -10,8 +10,9 @@ update).  The metric is Mcell-steps/s of the FP32 deviation-storage path; the pl
 is timed on the same workload beside it, and both are compared with the FP64 CPU oracle.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-For N > 1 run under torch.distributed.run: every rank advances its own copy of the sweep
-(seeded by rank; weak scaling, no data exchange) and the slowest rank's time is reported.
+For N > 1 run under torch.distributed.run: the one sweep is split across the ranks, its
+instances balanced by cell count (strong scaling; instances never exchange data inside a
+step), and the slowest rank's time is reported.
 """
 from __future__ import annotations
 
@@ -106,15 +107,23 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- workload
-def make_workload(name: str, rank: int = 0):
+def make_workload(name: str):
     from paper_1812_00394_gb300 import meshgen as mg
     if name == "sweep":
-        return mg.batched_sweep(seed=rank_seed(rank))
+        return mg.batched_sweep(seed=5)
     if name == "delaunay40k":
-        return [mg.cavity_delaunay(re=1000.0, z=5.0, seed=2 + rank)]
+        return [mg.cavity_delaunay(re=1000.0, z=5.0, seed=2)]
     if name == "cavity64":
-        return [mg.cavity_quad(64, re=400.0, seed=1 + rank)]
+        return [mg.cavity_quad(64, re=400.0, seed=1)]
     raise ValueError(name)
+
+
+def host_cores() -> int:
+    """Cores this process may run on (the machine's host cores available to the oracle)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # not Linux
+        return os.cpu_count() or 1
 
 
 def _sample_indices(cases):
@@ -129,10 +138,13 @@ def _sample_indices(cases):
 
 
 # ----------------------------------------------------------------------------- reference arm
-def cpu_oracle_rate(cases, budget_s: float, max_steps: int = 50):
+def cpu_oracle_rate(cases, budget_s: float, max_steps: int = 50, threads: int = 1):
     """Time the FP64 oracle, as it stands, on a bounded sample: each sampled instance is
-    stepped until about budget_s / n_samples seconds are spent.  Returns (Mcell-steps/s, desc)."""
+    stepped until about budget_s / n_samples seconds are spent, with its per-cell loops on
+    `threads` threads.  Returns (Mcell-steps/s, desc)."""
+    from oracle import oracle as orc
     from oracle.oracle import Oracle
+    orc.set_threads(threads)
     picks = _sample_indices(cases)
     cell_steps, secs, desc = 0, 0.0, []
     for i in picks:
@@ -154,7 +166,10 @@ def run_reference(args):
         return 0
     cases = make_workload(args.workload)
     picks = _sample_indices(cases)
+    from oracle import oracle as orc
     from oracle.oracle import Oracle
+    cores = host_cores()
+    orc.set_threads(cores)          # the oracle's per-cell loops on every host core
     oracles = [Oracle(cases[i]) for i in picks]
     # the first warm-up step times each sampled instance; the largest are dropped until the
     # remaining steps fit the time budget (one instance stays)
@@ -180,15 +195,16 @@ def run_reference(args):
     el = time.perf_counter() - t0
     value = cells * args.steps / el / 1e6
     sample = (f"each step = one FP64 oracle time step of {len(picks)} instances of the sweep "
-              f"({', '.join(cases[i].name for i in picks)}; {cells} cells), single thread")
+              f"({', '.join(cases[i].name for i in picks)}; {cells} cells), per-cell loops on "
+              f"{cores} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "sample_cells": cells, "precision": "fp64-cpu"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "host_nproc": cores,
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
     return 0
@@ -212,8 +228,8 @@ def _time_steps(torch, solver, stream, steps, dist, world):
 
 
 def max_over_ranks(torch, dist, world: int, value: float, device: str = "cuda") -> float:
-    """The slowest rank's time (all ranks get it); a no-op for one rank.  This is the only
-    collective of the multi-GPU run: instances are sharded by rank and never exchange data."""
+    """The slowest rank's time (all ranks get it); a no-op for one rank.  Inside a step the
+    ranks exchange nothing: the sweep's instances are sharded by rank."""
     if world <= 1:
         return float(value)
     t = torch.tensor([float(value)], device=device, dtype=torch.float64)
@@ -221,18 +237,22 @@ def max_over_ranks(torch, dist, world: int, value: float, device: str = "cuda") 
     return float(t.item())
 
 
-def rank_seed(rank: int) -> int:
-    """Seed of rank r's own copy of the sweep (weak scaling: every rank a full, distinct sweep)."""
-    return 5 + 7919 * rank
-
-
-def sum_over_ranks(torch, dist, world: int, value: float, device: str = "cuda") -> float:
-    """The sum over ranks (the cells every rank's own sweep holds); a no-op for one rank."""
+def sum_over_ranks(torch, dist, world: int, value, device: str = "cuda"):
+    """The sum over ranks of a number or an array (per-rank parts of a sweep-wide total); a
+    no-op for one rank."""
     if world <= 1:
-        return float(value)
-    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+        return value
+    scalar = np.ndim(value) == 0
+    t = torch.tensor(np.atleast_1d(np.asarray(value, np.float64)), device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    out = t.cpu().numpy()
+    return float(out[0]) if scalar else out
+
+
+def shard_of(cases, world: int, rank: int):
+    """This rank's share of the sweep (cell-balanced, see paper_1812_00394_gb300.shard)."""
+    from paper_1812_00394_gb300.shard import assign_instances
+    return [cases[i] for i in assign_instances([c.mesh.n_cells for c in cases], world)[rank]]
 
 
 def aggregate_rate(cells_all_ranks: float, steps: int, ms_max: float) -> float:
@@ -262,9 +282,11 @@ def run_ours(args):
     stream = torch.cuda.Stream()
 
     t_setup = time.perf_counter()
-    cases = make_workload(args.workload, rank)
+    sweep = make_workload(args.workload)          # the same sweep on every rank
+    cases = shard_of(sweep, world, rank)          # this rank's instances
     total_cells = sum(c.mesh.n_cells for c in cases)
     sst_cells = sum(c.mesh.n_cells for c in cases if c.sst)
+    cells_job = sum(c.mesh.n_cells for c in sweep)
     fvlbm.load()
 
     results = {}
@@ -290,32 +312,39 @@ def run_ours(args):
     setup_s = time.perf_counter() - t_setup
 
     ms32 = results["f32"]["ms"]
-    cells_job = sum_over_ranks(torch, dist, world, total_cells)  # ranks' sweeps differ in size
     value = aggregate_rate(cells_job, args.steps, ms32)
     ms64 = results["f64"]["ms"]
     value64 = aggregate_rate(cells_job, args.steps, ms64)
 
-    # FP32 vs FP64 (both GPU, same number of steps) on every cell of the workload
+    # FP32 against FP64 (both GPU) after the same warmup + timed steps, on every cell of the
+    # sweep: per kind of instance (sums of squares over all ranks) and C_D, C_L of every airfoil
     s32, s64 = solvers["f32"], solvers["f64"]
-    v32 = np.concatenate([_vel(s32.fields(i)) for i in range(s32.n)])
-    v64 = np.concatenate([_vel(s64.fields(i)) for i in range(s64.n)])
-    l2_32_64 = float(np.linalg.norm(v32 - v64) / np.linalg.norm(v64))
-    # the same per kind of instance, and the wall-force coefficients of the airfoils
-    err_kind = {}
-    for kind in sorted({c.name.split("_")[0].rstrip("0123456789") for c in cases}):
-        idx = [i for i, c in enumerate(cases) if c.name.split("_")[0].rstrip("0123456789") == kind]
-        a = np.concatenate([_vel(s32.fields(i)) for i in idx])
-        b = np.concatenate([_vel(s64.fields(i)) for i in idx])
-        err_kind[f"fp32_vs_fp64_gpu_velocity_rel_l2[{kind}]"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
-    cl_cd = []
+    kinds = ("cavity", "bfs", "naca")
+    sq = np.zeros(2 * len(kinds))
+    force_err = np.zeros(2)
     for i, c in enumerate(cases):
+        k = kinds.index(c.name.split("_")[0].rstrip("0123456789"))
+        a, b = _vel(s32.fields(i)), _vel(s64.fields(i))
+        sq[2 * k] += float(np.sum((a - b) ** 2))
+        sq[2 * k + 1] += float(np.sum(b ** 2))
         if c.name.startswith("naca"):
             f32, f64 = s32.forces(i), s64.forces(i)
-            cl_cd.append(max(abs(f32["cl"] - f64["cl"]) / max(abs(f64["cl"]), 1e-12),
-                             abs(f32["cd"] - f64["cd"]) / max(abs(f64["cd"]), 1e-12)))
-    if cl_cd:
-        err_kind["fp32_vs_fp64_gpu_cl_cd_max_rel"] = float(max(cl_cd))
+            force_err[0] = max(force_err[0], abs(f32["cd"] - f64["cd"]) / abs(f64["cd"]))
+            force_err[1] = max(force_err[1], abs(f32["cl"] - f64["cl"]) / max(abs(f64["cl"]), 1e-3))
+    sq = sum_over_ranks(torch, dist, world, sq)
+    force_err = [max_over_ranks(torch, dist, world, float(x)) for x in force_err]
+    err_kind = {}
+    for k, kind in enumerate(kinds):
+        if sq[2 * k + 1] > 0:
+            err_kind[f"fp32_vs_fp64_gpu_velocity_rel_l2[{kind}]"] = float(np.sqrt(sq[2 * k] / sq[2 * k + 1]))
+    l2_32_64 = float(np.sqrt(sq[0::2].sum() / sq[1::2].sum()))
+    err_kind["fp32_vs_fp64_gpu_cd_max_rel"] = float(force_err[0])
+    err_kind["fp32_vs_fp64_gpu_cl_max_rel"] = float(force_err[1])
     err_kind["fp32_vs_fp64_after_steps"] = args.warmup + args.steps
+    err_kind["fp32_within_target"] = bool(
+        all(v <= 1e-4 for kk, v in err_kind.items() if kk.startswith("fp32_vs_fp64_gpu_velocity"))
+        and force_err[0] <= 5e-3 and force_err[1] <= 5e-3)
+    err_kind["target"] = "velocity rel L2 <= 1e-4 per kind of instance; C_D, C_L each <= 0.5 %"
 
     # per-kernel device times (CUDA events on the handle's stream) for the roofline
     with torch.cuda.stream(stream):
@@ -324,12 +353,14 @@ def run_ours(args):
     per_launch_ms = kstat["ms"] / kstat["launches"]
     hbm, peak_kind = _peaks()
     lam_cells = total_cells - sst_cells
-    kbytes = _kernel_bytes(kname, "f32", total_cells, sst_cells)
+    face_value = results["f32"]["autotune"][0] == "facevalue"
+    kbytes = _kernel_bytes(kname, "f32", total_cells, sst_cells, face_value)
     achieved = kbytes / (per_launch_ms * 1e-3) / 1e9
     step_bytes = lam_cells * STEP_BYTES[("f32", False)] + sst_cells * STEP_BYTES[("f32", True)]
     step_gbs = step_bytes / (ms32 / args.steps * 1e-3) / 1e9
     lps = s32.footprint()[1]
     dev_bytes = s32.footprint()[0]
+    traffic, traffic_src = _ncu_traffic(kname, args.workload, world, face_value)
 
     # errors against the FP64 CPU oracle on sampled instances (fresh short runs)
     err = {}
@@ -338,26 +369,31 @@ def run_ours(args):
 
     # end to end through the C ABI with pinned host buffers: upload f, one step, read u, v;
     # pipelined (async calls) for the headline, synchronous calls for context
-    e2e = _e2e(torch, fvlbm, s32, stream, args, world, dist, pipelined=True, f32_io=True)
-    e2e_f64 = _e2e(torch, fvlbm, s32, stream, args, world, dist, pipelined=True)
-    e2e_sync = _e2e(torch, fvlbm, s32, stream, args, world, dist, pipelined=False)
+    e2e = _e2e(torch, fvlbm, s32, stream, args, world, dist, cells_job, pipelined=True, f32_io=True)
+    e2e_f64 = _e2e(torch, fvlbm, s32, stream, args, world, dist, cells_job, pipelined=True)
+    e2e_sync = _e2e(torch, fvlbm, s32, stream, args, world, dist, cells_job, pipelined=False)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, sample = cpu_oracle_rate(cases, args.cpu_budget)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": sample + " (FP64 CPU oracle, single thread, this host)"}
+        cores = host_cores()
+        rate1, sample1 = cpu_oracle_rate(cases, args.cpu_budget / 2, threads=1)
+        rate_n, sample_n = cpu_oracle_rate(cases, args.cpu_budget / 2, threads=cores)
+        cpu = {"value": rate_n, "unit": UNIT, "cores": cores, "host_nproc": cores, "kind": "oracle",
+               "sample": sample_n + f" (FP64 CPU oracle, per-cell loops on {cores} threads, this host)",
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": sample1 + " (FP64 CPU oracle, one thread, this host)"}}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": _workload_desc(args.workload), "instances": len(cases),
-                       "cells_per_gpu": total_cells, "sst_cells_per_gpu": sst_cells,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": _workload_desc(args.workload), "instances": len(sweep),
+                       "cells": cells_job, "cells_rank0": total_cells, "sst_cells_rank0": sst_cells,
                        "precision": "fp32 f-w*rho0 deviation storage, fp32 arithmetic, fp64 reductions",
                        "l2": f"inputs larger than L2 (device working set {dev_bytes / 1e6:.0f} MB > 129 MB); no flush",
-                       "parallelism": f"{world} process(es), one per GPU, each its own sweep"},
+                       "parallelism": f"{world} process(es), one per GPU; the sweep's instances split "
+                                      f"across them by cell count"},
             "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / args.steps,
                            "speedup_fp32_over_fp64": value / value64},
             "explicit_euler_fp32": {"ms_per_step": ms_euler / args.steps,
@@ -365,9 +401,8 @@ def run_ours(args):
                                     "note": "comparison scheme of Sec. 4.1: stable only for dt < 2 tau"},
             "error": {"fp32_vs_fp64_gpu_velocity_rel_l2": l2_32_64, **err_kind, **err},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm,
-                         "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": _ncu_traffic(kname, args.workload, world),
-                         "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                         "traffic_source": traffic_src, "peak_kind": peak_kind,
                          "algorithmic_bytes_per_launch": kbytes,
                          "avg_launch_ms": per_launch_ms},
             "step_roofline": {"bytes_per_cell_step": step_bytes / total_cells,
@@ -404,35 +439,52 @@ def _workload_desc(name):
             "cavity64": "laminar lid-driven cavity Re 400, 64x64 quads, CFL 0.5"}[name]
 
 
-def _ncu_traffic(kname, workload, world):
-    """DRAM bytes (read + write) per launch of kernel `kname` from the committed ncu summary of
-    the default sweep, when that summary was taken on the kernel source as it is now (its
-    recorded SHA-256 of csrc/fvlbm_kernels.cu matches); else None."""
+PROFILE_SUMMARY = {False: "k_fused_stage_fp32_sweep.md", True: "k_fused_fv_fp32_sweep.md"}
+
+
+def kernel_source_sha256() -> str:
+    """SHA-256 over the sources of the stage kernels (fvlbm_kernels.cu, fvlbm_fused_fv.cuh)."""
     import hashlib
+    h = hashlib.sha256()
+    for name in ("fvlbm_kernels.cu", "fvlbm_fused_fv.cuh"):
+        with open(os.path.join(ROOT, "paper_1812_00394_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _ncu_traffic(kname, workload, world, face_value=False):
+    """(DRAM bytes read + written per launch of kernel `kname`, where the figure comes from).
+    The figure is read from the committed ncu summary of the default sweep under profiles/,
+    and only while the kernel sources hash to the value that summary records (the capture was
+    taken on these sources); otherwise (None, reason)."""
     import re
     if workload != "sweep":
-        return None
+        return None, "no ncu capture for this workload"
+    fname = PROFILE_SUMMARY[bool(face_value)]
     try:
-        src = os.path.join(ROOT, "paper_1812_00394_gb300", "csrc", "fvlbm_kernels.cu")
-        with open(src, "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()
-        with open(os.path.join(ROOT, "profiles", "k_fused_stage_fp32_sweep.md")) as fh:
+        sha = kernel_source_sha256()
+        with open(os.path.join(ROOT, "profiles", fname)) as fh:
             txt = fh.read()
     except OSError:
-        return None
+        return None, f"profiles/{fname} not found"
     m = re.search(r"kernel_source_sha256=([0-9a-f]{64})((?: \w+=\d+)+)", txt)
     if not m or m.group(1) != sha:
-        return None
+        return None, f"profiles/{fname} was captured on other kernel sources"
     vals = dict(kv.split("=") for kv in m.group(2).split())
-    return float(vals[kname]) if kname in vals else None
+    if kname not in vals:
+        return None, f"profiles/{fname} has no figure for {kname}"
+    return float(vals[kname]), f"ncu capture committed in profiles/{fname} (kernel sources sha256 {sha[:16]}...)"
 
 
-def _kernel_bytes(kname, prec, cells, sst_cells):
+def _kernel_bytes(kname, prec, cells, sst_cells, face_value=False):
     """Algorithmic bytes of one launch of each kernel: its per-cell state reads and writes
     counted once (neighbour values assumed reused from cache), neighbour indices 4 B each
-    (3.5 per cell), geometry not counted (recomputable)."""
+    (3.5 per cell), geometry not counted (recomputable).  With the face-value stages the SST
+    update writes no f^(1) (stage 1 relaxes f^n itself)."""
     w = 4 if prec == "f32" else 8
     idx = 14.0
+    if face_value and kname == "sst_update":
+        return sst_cells * ((3 + 3 + 12 + 1 + 4) * w + idx)
     words = {
         "stage1": 9 + 1 + 9,                       # f^n, tau -> f^(1)
         "grad_f": 9 + 18,                          # f^(J) -> gradient
@@ -480,7 +532,7 @@ def _oracle_errors(cases, fvlbm, dev, stream, torch, nsteps):
     return out
 
 
-def _e2e(torch, fvlbm, solver, stream, args, world, dist, pipelined=True, f32_io=False):
+def _e2e(torch, fvlbm, solver, stream, args, world, dist, cells_job, pipelined=True, f32_io=False):
     """Same metric through the public API with host buffers: per step, an upload of the whole
     state (all instances, FVLBM_ALL_INSTANCES) from pinned host memory, one fvlbm_step, and a
     read of u and v back to pinned host memory.  pipelined=True uses fvlbm_set_f_async /
@@ -503,7 +555,7 @@ def _e2e(torch, fvlbm, solver, stream, args, world, dist, pipelined=True, f32_io
             hf[:] = fvlbm.fvlbm_get_f(solver.h, -1)
     u = [torch.empty(total, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
     v = [torch.empty(total, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
-    k = max(3, min(args.steps // 10, 20))
+    k = args.steps  # the same step count as the device-timed region
 
     def check(rc, what):
         if rc:
@@ -539,10 +591,9 @@ def _e2e(torch, fvlbm, solver, stream, args, world, dist, pipelined=True, f32_io
         check(lib.fvlbm_wait(solver.h), "fvlbm_wait")
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-    total_job = total
+    total_job = cells_job
     if world > 1:
         el = max_over_ranks(torch, dist, world, el, device="cuda")
-        total_job = sum_over_ranks(torch, dist, world, total)
     io = "pipelined (async calls, copy engines)" if pipelined else "synchronous calls"
     io += "; state uploaded as FP32 deviations f - w rho0" if f32_io else "; state uploaded as FP64 f"
     return {"value": total_job / (el / k) / 1e6, "unit": UNIT,
@@ -635,8 +686,9 @@ def main():
     ap.add_argument("--profile-mode", action="store_true",
                     help="only build the workload and run warmup + steps (for ncu)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--kernel-path", type=int, default=0, choices=[0, 1],
-                    help="profile mode: 0 fused stage kernels, 1 two-pass kernels")
+    ap.add_argument("--kernel-path", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="profile mode: 0 fused stage kernels, 1 two-pass kernels, 2 fused "
+                         "stage kernels in the face-value form, 3 the same as a persistent kernel")
     ap.add_argument("--adjoint-mode", action="store_true",
                     help="time the FP64 laminar adjoint against its primal step (not a bench line)")
     ap.add_argument("--adjoint-case", default="naca_laminar",

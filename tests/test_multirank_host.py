@@ -1,8 +1,9 @@
 """Host logic of the multi-GPU benchmark path on CPU: two gloo ranks.
 
-Each rank advances its own seeded copy of the sweep (weak scaling, no data exchange); the only
-collective is the max over ranks of the timed region.  Here the ranks use the gloo backend and
-the oracle-free host pieces of bench.py.
+The one sweep is split across the ranks by cell count (strong scaling; the instances exchange
+nothing inside a step); the collectives are the max over ranks of the timed region and the
+sums of per-rank parts of sweep-wide totals.  Here the ranks use the gloo backend and the
+oracle-free host pieces of bench.py.
 """
 import os
 import socket
@@ -29,16 +30,19 @@ def _worker(rank, world, port, out):
         # a rank-dependent "elapsed time": the reported value must be the slowest rank's
         ms = 10.0 + 5.0 * rank
         got = bench.max_over_ranks(torch, dist, world, ms, device="cpu")
-        seed = bench.rank_seed(rank)
-        seeds = [None] * world
-        dist.all_gather_object(seeds, seed)
+        from paper_1812_00394_gb300 import meshgen as mg
+        sweep = mg.batched_sweep(seed=5, scale=0.02, n_cavity=4, n_bfs=1, n_naca=1)
+        mine = [c.name for c in bench.shard_of(sweep, world, rank)]
+        names = [None] * world
+        dist.all_gather_object(names, mine)
         cells = bench.sum_over_ranks(torch, dist, world, 1000 + 10 * rank, device="cpu")
-        out[rank] = (got, seeds, cells)
+        parts = bench.sum_over_ranks(torch, dist, world, [1.0 * rank, 2.0], device="cpu")
+        out[rank] = (got, names, cells, list(parts), [c.name for c in sweep])
     finally:
         dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_max_time_and_distinct_seeds():
+def test_two_gloo_ranks_max_time_and_sweep_split():
     world = 2
     port = _free_port()
     with mp.get_context("spawn").Manager() as mgr:  # no fork of a process that may run threads
@@ -46,8 +50,12 @@ def test_two_gloo_ranks_max_time_and_distinct_seeds():
         mp.start_processes(_worker, args=(world, port, out), nprocs=world, start_method="spawn")
         res = dict(out)
     assert res[0][0] == res[1][0] == 15.0            # max over ranks, seen by every rank
-    assert len(set(res[0][1])) == world               # every rank its own sweep
-    assert res[0][2] == res[1][2] == 2010.0           # cells summed over the ranks' own sweeps
+    shares = res[0][1]
+    assert shares == res[1][1]                        # every rank computes the same split
+    assert sorted(shares[0] + shares[1]) == sorted(res[0][4])  # a partition of the one sweep
+    assert not set(shares[0]) & set(shares[1])
+    assert res[0][2] == res[1][2] == 2010.0           # sums of per-rank parts
+    assert res[0][3] == res[1][3] == [1.0, 4.0]
 
 
 def test_single_rank_is_identity_and_rate():
@@ -57,13 +65,20 @@ def test_single_rank_is_identity_and_rate():
     assert bench.sum_over_ranks(torch, None, 1, 7.0) == 7.0
 
 
-@pytest.mark.parametrize("rank", [0, 1, 3])
-def test_rank_workloads_differ_but_are_seeded(rank):
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_sweep_shares_partition_and_balance(world):
+    """The full benchmark sweep (48 instances) split over 1-8 ranks: a partition, no rank more
+    than the largest instance above the mean."""
     from paper_1812_00394_gb300 import meshgen as mg
-    a = mg.batched_sweep(seed=bench.rank_seed(rank), scale=0.02, n_cavity=2, n_bfs=0, n_naca=0)
-    b = mg.batched_sweep(seed=bench.rank_seed(rank), scale=0.02, n_cavity=2, n_bfs=0, n_naca=0)
-    assert [c.mesh.n_cells for c in a] == [c.mesh.n_cells for c in b]
-    assert all((x.mesh.xy == y.mesh.xy).all() for x, y in zip(a, b))
+    sweep = mg.batched_sweep(seed=5, scale=0.05)
+    shares = [bench.shard_of(sweep, world, r) for r in range(world)]
+    names = sorted(c.name for sh in shares for c in sh)
+    assert names == sorted(c.name for c in sweep)
+    loads = [sum(c.mesh.n_cells for c in sh) for sh in shares]
+    cells = [c.mesh.n_cells for c in sweep]
+    assert max(loads) <= sum(cells) / world + max(cells)
+    if world == 1:
+        assert [c.name for c in shares[0]] == [c.name for c in sweep]
 
 
 def test_bench_entry_points_exist():
@@ -75,7 +90,8 @@ def test_bench_entry_points_exist():
 def test_ncu_traffic_lookup_follows_the_kernel_source():
     """roofline.traffic comes from the committed ncu summary only for the default workload and
     only while the recorded hash matches the kernel source; otherwise it is None."""
-    assert bench._ncu_traffic("fused_stage2", "cavity64", 1) is None
-    assert bench._ncu_traffic("no_such_kernel", "sweep", 1) is None
-    got = bench._ncu_traffic("fused_stage2", "sweep", 1)
-    assert got is None or got > 1e8
+    assert bench._ncu_traffic("fused_stage2", "cavity64", 1)[0] is None
+    assert bench._ncu_traffic("no_such_kernel", "sweep", 1)[0] is None
+    for fv in (False, True):
+        got, src = bench._ncu_traffic("fused_stage2", "sweep", 1, fv)
+        assert (got is None) or (got > 1e8 and "profiles/" in src), src
