@@ -686,9 +686,9 @@ def main():
     ap.add_argument("--profile-mode", action="store_true",
                     help="only build the workload and run warmup + steps (for ncu)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--kernel-path", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--kernel-path", type=int, default=0, choices=[0, 1, 2],
                     help="profile mode: 0 fused stage kernels, 1 two-pass kernels, 2 fused "
-                         "stage kernels in the face-value form, 3 the same as a persistent kernel")
+                         "stage kernels in the face-value form")
     ap.add_argument("--adjoint-mode", action="store_true",
                     help="time the FP64 laminar adjoint against its primal step (not a bench line)")
     ap.add_argument("--adjoint-case", default="naca_laminar",

@@ -99,10 +99,8 @@ typedef struct {
     int kernel_path;           /* 0: fused stage kernels with shared-memory halo staging
                                   (default); 1: two-pass kernels (gradient array in HBM);
                                   2: fused stage kernels in the face-value form (each cell
-                                  publishes its upwind face values once per face); 3: the
-                                  face-value form as a persistent kernel that stages the next
-                                  work item while it computes the current one.  The autotuner
-                                  may still pick any fused form.
+                                  publishes its upwind face values once per face; the
+                                  autotuner may still pick any fused form).
                                   A handle with a periodic pair whose edges are translates only
                                   to the gluing tolerance (not to 1e-12 of the edge length)
                                   runs the two-pass kernels: they give both sides of the glued
@@ -202,11 +200,12 @@ int fvlbm_check_mesh(const fvlbm_mesh *mesh, const fvlbm_bc *bc, const fvlbm_par
 int fvlbm_step(fvlbm_handle *h, int n_steps, fvlbm_stats *stats);
 
 /* Diagnostic for the error path above (not in the paper): the number of polls the first
- * staging wait of the fused stage kernels (kernel_path 0, 256- and 128-cell blocks) makes
- * before giving up; default 2^26, 0 gives up after the first poll.  Only that wait changes:
- * before a block returns it still waits, with the full bound, for its own copies in flight,
- * so that no copy lands in shared memory after the block has left.  The face-value kernels
- * do not wait on a barrier.  Drops the captured step graphs.  Errors: BAD_PARAM. */
+ * staging wait of the fused stage kernels (both fused forms: kernel_path 0 with 256- and
+ * 128-cell blocks, and the face-value form of kernel_path 2) makes before giving up; default
+ * 2^26, 0 gives up after the first poll.  Only that wait changes: before a block returns it
+ * still waits, with the full bound, for its own copies in flight, so that no copy lands in
+ * shared memory after the block has left.  Drops the captured step graphs.
+ * Errors: BAD_PARAM. */
 int fvlbm_set_wait_limit(fvlbm_handle *h, long long polls);
 
 /* Force on the wall faces of `instance`: F = sum over wall faces of sum_alpha e_alpha
@@ -226,6 +225,43 @@ int fvlbm_get_f(fvlbm_handle *h, int instance, double *f);
 int fvlbm_set_f(fvlbm_handle *h, int instance, const double *f);
 int fvlbm_get_fields(fvlbm_handle *h, int instance, double *rho, double *u, double *v,
                      double *k, double *omega, double *nut);
+
+/* ---------------------------------------------------------------------------------------------
+ * Partitioned meshes (no counterpart in the paper, whose Sec. 4 only states that its code runs
+ * in parallel).  One mesh is split into parts, each part a handle (one GPU per part) over its
+ * own cells plus the cells within a fixed number of face rings of them (ghosts), with the
+ * faces cut by the split as outlet edges.  After every step each part overwrites its ghosts
+ * with the state their owners computed; a step of Sec. 3.2 reaches 8 rings (2 for the SST
+ * update, 2 per IMEX stage), so with 8 ghost rings the owned cells step exactly as in the
+ * whole mesh.  The time step (fvlbm_params.dt) and the wall distance are those of the whole
+ * mesh.  These calls move the per-cell state of a list of cells and set the wall distance.
+ *
+ * fvlbm_get_cells / fvlbm_set_cells: n cells of `instance`, ids in the instance's input cell
+ * order (0 <= cells[j] < n_cells, else BAD_PARAM and nothing changes).  f [n * 9] cell-major
+ * like fvlbm_get_f; k, omega, nut [n] (current values).  get: any output may be NULL.  set: f
+ * may be NULL (f unchanged), and k, omega, nut are all given or all NULL; setting f also
+ * recomputes the cells' macros (as fvlbm_set_f).  Both synchronise.  Errors: BAD_PARAM, OOM,
+ * CUDA.
+ *
+ * fvlbm_set_wall_distance: d [n_cells] (> 0, input cell order) replaces the distance to the
+ * nearest wall that create computed from the instance's own wall edges (it enters the SST
+ * blending functions and the wall value of omega).  Synchronises.  Errors: BAD_PARAM, CUDA.
+ *
+ * fvlbm_cell_geometry (host only, no CUDA call): area [n_cells] and the wall distance
+ * [n_cells] (1e30 without wall edges) of a (mesh, bc, params) triple as create computes them,
+ * in input cell order; either may be NULL.  Errors: those of fvlbm_check_mesh.
+ *
+ * fvlbm_forces_edges: the wall force of fvlbm_forces per boundary edge, fxy [2 * n_bedges] =
+ * (Fx, Fy) in boundary-edge input order, 0 on edges that are not walls; a partitioned mesh
+ * sums the edges of the cells it owns.  Synchronises.  Errors: BAD_PARAM, CUDA. */
+int fvlbm_get_cells(fvlbm_handle *h, int instance, int n, const int *cells, double *f, double *k,
+                    double *omega, double *nut);
+int fvlbm_set_cells(fvlbm_handle *h, int instance, int n, const int *cells, const double *f,
+                    const double *k, const double *omega, const double *nut);
+int fvlbm_set_wall_distance(fvlbm_handle *h, int instance, const double *d);
+int fvlbm_cell_geometry(const fvlbm_mesh *mesh, const fvlbm_bc *bc, const fvlbm_params *params,
+                        double *area, double *wdist);
+int fvlbm_forces_edges(fvlbm_handle *h, int instance, double *fxy);
 
 /* Pipelined variants of fvlbm_set_f and fvlbm_get_fields that do not synchronise, so that host
  * transfers overlap the steps (no counterpart in the paper).  Each call stages its data in one
@@ -269,10 +305,10 @@ int fvlbm_profile_kernels(fvlbm_handle *h, int n_steps, int max_kernels, char *n
 
 /* Kernel autotuner (not in the paper).  Times trial_steps steps of each kernel configuration the
  * handle supports -- 0: fused stages with 256-cell blocks, 1: fused stages with 128-cell blocks,
- * 2: two-pass kernels, 3: fused stages in the face-value form, 4: the face-value form as a
- * persistent kernel -- on a snapshot of the current state, restores the state exactly, and
- * keeps the fastest for all later steps.  *chosen (may be NULL) receives the configuration and
- * ms_per_step[5] (may be NULL) the measured milliseconds per step, -1 for configurations not
+ * 2: two-pass kernels, 3: fused stages in the face-value form -- on a snapshot of the current
+ * state, restores the state exactly, and keeps the fastest for all later steps.  *chosen (may
+ * be NULL) receives the configuration and ms_per_step[4] (may be NULL) the measured
+ * milliseconds per step, -1 for configurations not
  * available (a block's halo too large for shared memory, kernel_path 1, or the explicit
  * scheme).  Allocates a temporary snapshot of the state (about 28 words per cell) and
  * synchronises the stream.  Errors: BAD_PARAM, OOM, CUDA. */

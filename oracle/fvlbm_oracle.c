@@ -982,6 +982,24 @@ void oracle_set_f(oracle *o, const double *f)
     for (int i = 0; i < o->nc; i++) moments(&o->f[(size_t)i * Q], &o->rho[i], &o->ux[i], &o->uy[i]);
 }
 
+/* k, omega, nu_t of every cell (state access for a mesh split into parts that exchange
+ * ghost cells; no arithmetic). */
+void oracle_set_turb(oracle *o, const double *k, const double *w, const double *nut)
+{
+    for (int i = 0; i < o->nc; i++) {
+        o->k[i] = k[i];
+        o->om[i] = w[i];
+        o->nut[i] = nut[i];
+    }
+}
+
+/* The wall distance of every cell, replacing the one computed from this mesh's own wall edges
+ * (a part of a split mesh takes the whole mesh's). */
+void oracle_set_wdist(oracle *o, const double *d)
+{
+    for (int i = 0; i < o->nc; i++) o->wdist[i] = d[i];
+}
+
 void oracle_get_fields(const oracle *o, double *rho, double *u, double *v, double *k,
                        double *w, double *nut)
 {

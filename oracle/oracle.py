@@ -63,6 +63,8 @@ def _common(lib):
     lib.oracle_get_f.argtypes = [vp, _D]
     lib.oracle_set_f.argtypes = [vp, _D]
     lib.oracle_get_fields.argtypes = [vp, _D, _D, _D, _D, _D, _D]
+    lib.oracle_set_turb.argtypes = [vp, _D, _D, _D]
+    lib.oracle_set_wdist.argtypes = [vp, _D]
     lib.oracle_geometry.argtypes = [vp, _D, _D, _D, _D]
     lib.oracle_forces.argtypes = [vp, _D, opt_d, opt_d, opt_d]
 
@@ -182,6 +184,12 @@ class Oracle:
 
     def set_f(self, f: np.ndarray) -> None:
         self.lib.oracle_set_f(self._h, np.ascontiguousarray(f, np.float64).ravel())
+
+    def set_turb(self, k: np.ndarray, omega: np.ndarray, nut: np.ndarray) -> None:
+        self.lib.oracle_set_turb(self._h, *(np.ascontiguousarray(a, np.float64) for a in (k, omega, nut)))
+
+    def set_wdist(self, d: np.ndarray) -> None:
+        self.lib.oracle_set_wdist(self._h, np.ascontiguousarray(d, np.float64))
 
     def fields(self) -> dict:
         n = self.n_cells

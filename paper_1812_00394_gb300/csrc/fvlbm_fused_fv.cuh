@@ -24,29 +24,30 @@
 // Work items: a block of 256 consecutive cells, or -- where its halo would not fit the
 // shared-memory budget -- a half or a quarter of one (an instance's cells are padded to a
 // multiple of 256, so no item straddles two instances).  One CTA of 256 threads per item.
-// Staging uses cp.async only (no mbarrier wait, so nothing can spin), all issued at the start
-// and waited for once: f^(J) of the item, ring-1 and ring-2 cells in pair-ordered rows, the
-// geometry and adjacency of item and ring-1 cells, and the item's accumulator rows and tau, so
-// that no phase after the wait touches global memory except for its stores.
-// Stage 1 stages f^n with tau and relaxes every staged cell to f^(1) on chip, so no f^(1)
-// array passes through HBM between steps (and f^n is never recovered from a rounded f^(1)).
+//
+// Layouts for the stages of this form.  f^n stays structure-of-arrays (shared with the rest of
+// the library).  The stage values f^(2), f^(3) that stages 1 and 2 write and stages 2 and 3
+// read are cell-major: alpha = 1..8 in pair order (1,3)(2,4)(5,7)(6,8) in one 32-byte row per
+// cell (its two halves swapped where bit 2 of the cell index is set), then f_0 of every cell,
+// so that an item's own rows are one contiguous bulk copy and a halo cell's eight moving
+// directions are one 32-byte sector.  The geometry the kernel reads
+// (node offsets q[8] and least-squares weights W[8]) is likewise one 64-byte row per cell.
+//
+// Staging, all issued before any wait: the item's own rows (its stage values, its accumulator
+// rows and tau) by bulk copies on one mbarrier; the halo rows, the adjacency and the ring-1
+// geometry by cp.async; the item cell's own geometry straight into registers.  Stage 1 takes
+// its own f^n rows from the accumulator copy (the algebra reads them there too) and relaxes
+// every staged cell to f^(1) on chip (Eq. (fnewstage), J = 1), so no f^(1) array passes
+// through HBM and f^n is never recovered from a rounded f^(1).
 //
 // FP32 arithmetic runs on packed pairs (fma.rn.f32x2): the two members of a pair share every
 // geometric factor, so the gradient and face-value updates are one packed FMA per pair.
 
-// Shared-memory capacity of the face-value kernel (cells): ring-1 + ring-2 + item cells and
+// Shared-memory capacity of the face-value kernel (cells): ring-1 + ring-2 + item cells,
 // item + ring-1 cells.  256-cell blocks whose halo exceeds it are split.
-// Cells per work item (and threads per CTA): 256, or 128 with proportionally smaller halos.
-#ifndef FVLBM_FV_ITEM
-#define FVLBM_FV_ITEM 256
-#endif
-constexpr int kFvThreads = FVLBM_FV_ITEM;
-constexpr int kFvEcap = FVLBM_FV_ITEM == 256 ? 448 : 256;
-constexpr int kFvGcap = FVLBM_FV_ITEM == 256 ? 352 : 192;
-// CTAs per SM the FP32 kernel is compiled for (registers per thread: 128 at 2 CTAs of 256)
-#ifndef FVLBM_FV_MIN_BLOCKS
-#define FVLBM_FV_MIN_BLOCKS (512 / FVLBM_FV_ITEM)
-#endif
+constexpr int kFvThreads = 256;
+constexpr int kFvEcap = 448;
+constexpr int kFvGcap = 352;
 
 // Adjacency word of the face-value kernel (cell-major: 4 words per cell):
 //   0xFFFFFFFF: no face; bit 31 set: boundary face (low 31 bits: global boundary face index);
@@ -67,6 +68,10 @@ struct FvItems {
 // Pair p: first members alpha = 1, 2, 5, 6 and their opposites 3, 4, 7, 8.
 __host__ __device__ constexpr int fv_first(int p) { return p == 0 ? 1 : (p == 1 ? 2 : (p == 2 ? 5 : 6)); }
 __host__ __device__ constexpr int fv_second(int p) { return p == 0 ? 3 : (p == 1 ? 4 : (p == 2 ? 7 : 8)); }
+// Position of alpha (1..8) in a pair-ordered row of 8: (1,3)(2,4)(5,7)(6,8).
+__host__ __device__ constexpr int fv_pos(int a) {
+    return a == 1 ? 0 : (a == 3 ? 1 : (a == 2 ? 2 : (a == 4 ? 3 : (a == 5 ? 4 : (a == 7 ? 5 : (a == 6 ? 6 : 7))))));
+}
 
 // e_first(p) . (x, y)
 template <class T>
@@ -94,20 +99,18 @@ struct FvPair<double> {
     static __device__ __forceinline__ V bcast(double a) { return make_double2(a, a); }
 };
 
-// Shared-memory layout (elements of T):
-//   sf  [kFvEcap][8]   f^(J), alpha = 1..8 in pair order (1,3)(2,4)(5,7)(6,8); the two 4-value
-//                      halves of row j are swapped when bit 2 of j is set (bank spread)
-//   sf0 [kFvEcap]      f^(J)_0 of item, ring-1 and ring-2 cells
-//   st  [2][kFvEcap]   tau of the staged cells (stage 1: every staged cell, to relax f^n to
-//                      f^(1) in place with Eq. (fnewstage), J = 1; stages 2, 3: item cells),
-//                      and in stage 1 the cells' time steps under local time stepping
+// Shared-memory layout (bytes):
+//   sf  [kFvEcap][8]   staged f (moving directions, pair order, halves swapped on bit 2 of
+//                      the row), one row per item / ring cell
+//   sf0 [kFvEcap]      staged f_0
+//   st  [2][kFvEcap]   stage 1: tau and the time step of every staged halo cell
 //   sv  [kFvGcap][16]  outgoing face values, 4 per face slot; 16-byte chunk m of row c sits at
 //                      chunk m ^ ((c >> 1) & 3).  Before the face values are written, the
-//                      rows of ring-1 cells hold their geometry in the same swizzled chunks:
-//                      node offsets q[0..3], q[4..7], least-squares weights W[0..3], W[4..7]
+//                      rows of ring-1 cells hold their geometry in the same swizzled chunks
+//                      (q[0..3], q[4..7], W[0..3], W[4..7])
 //   sa  [kFvGcap]      adjacency words (uint4)
-//   sacc [18][256]     the item's accumulator rows for the stage algebra, SoA (stage 1: f^n;
-//                      stage 2: B and C; stage 3: C), by bulk copy
+//   sacc [19][256]     the item's rows for the stage algebra, structure of arrays: stage 1
+//                      f^n; stage 2 B and C; stage 3 C; then tau
 //   one mbarrier for the bulk copies
 template <class T>
 struct FvSmem {
@@ -117,39 +120,65 @@ struct FvSmem {
     static constexpr size_t sv = st + 2 * size_t(kFvEcap) * sizeof(T);
     static constexpr size_t sa = sv + size_t(kFvGcap) * 16 * sizeof(T);
     static constexpr size_t sacc = sa + size_t(kFvGcap) * 16;
-    static constexpr size_t bar = sacc + size_t(18) * kFvThreads * sizeof(T);
+    static constexpr size_t bar = sacc + size_t(2 * kQ + 1) * kFvThreads * sizeof(T);
     static constexpr size_t bytes = bar + 16;
 };
 
-// Position of alpha (1..8) within a pair-ordered row of 8: (1,3)(2,4)(5,7)(6,8).
-__host__ __device__ constexpr int fv_pos(int a) {
-    return a == 1 ? 0 : (a == 3 ? 1 : (a == 2 ? 2 : (a == 4 ? 3 : (a == 5 ? 4 : (a == 7 ? 5 : (a == 6 ? 6 : 7))))));
-}
 // element offset of face slot m in row c of sv
 __device__ __forceinline__ int fv_sv_off(int c, int m) { return c * 16 + 4 * (m ^ ((c >> 1) & 3)); }
 
-// Load the 8 moving directions of row j as 4 pairs.
+// Rows of 8 (staged in shared memory, and the cell-major stage values in global memory) keep
+// their two 4-value halves swapped when bit 2 of the row index is set: consecutive rows then
+// spread over all banks, and since items start at multiples of 64 cells the item rows keep
+// the same bit in both places (one bulk copy moves them unchanged).
+__host__ __device__ __forceinline__ int fv_half(int j, int h) { return h ^ ((j >> 2) & 1); }
+
+// Load the 8 moving directions of staged row j as 4 pairs.
 template <class T>
 __device__ __forceinline__ void fv_load_row(const T *sf, int j, typename FvPair<T>::V *o) {
     using PV = FvPair<T>;
-    const int sw = (j & 4) ? 4 : 0;
-    const T *row = sf + j * 8;
+    const T *lo_p = sf + j * 8 + 4 * fv_half(j, 0);
+    const T *hi_p = sf + j * 8 + 4 * fv_half(j, 1);
     if constexpr (sizeof(T) == 4) {
-        const float4 lo = *reinterpret_cast<const float4 *>(row + sw);
-        const float4 hi = *reinterpret_cast<const float4 *>(row + (sw ^ 4));
+        const float4 lo = *reinterpret_cast<const float4 *>(lo_p);
+        const float4 hi = *reinterpret_cast<const float4 *>(hi_p);
         o[0] = PV::make(lo.x, lo.y);
         o[1] = PV::make(lo.z, lo.w);
         o[2] = PV::make(hi.x, hi.y);
         o[3] = PV::make(hi.z, hi.w);
     } else {
-        const double2 a = *reinterpret_cast<const double2 *>(row + sw);
-        const double2 b = *reinterpret_cast<const double2 *>(row + sw + 2);
-        const double2 c = *reinterpret_cast<const double2 *>(row + (sw ^ 4));
-        const double2 d = *reinterpret_cast<const double2 *>(row + (sw ^ 4) + 2);
-        o[0] = a;
-        o[1] = b;
-        o[2] = c;
-        o[3] = d;
+        o[0] = *reinterpret_cast<const double2 *>(lo_p);
+        o[1] = *reinterpret_cast<const double2 *>(lo_p + 2);
+        o[2] = *reinterpret_cast<const double2 *>(hi_p);
+        o[3] = *reinterpret_cast<const double2 *>(hi_p + 2);
+    }
+}
+// element offset of pair p in row j
+__device__ __forceinline__ int fv_pair_off(int j, int p) { return j * 8 + 4 * fv_half(j, p >> 1) + 2 * (p & 1); }
+// element offset of alpha (1..8) in row j
+__device__ __forceinline__ int fv_alpha_off(int j, int a) {
+    const int pos = fv_pos(a);
+    return j * 8 + 4 * fv_half(j, pos >> 2) + (pos & 3);
+}
+
+// 16-byte vector load of geometry (rows of 16 values, 16-byte aligned) into v[0..7], w[0..7]
+template <class T>
+__device__ __forceinline__ void fv_load_geo_row(const T *__restrict__ g, T *q, T *w) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 *g4 = reinterpret_cast<const float4 *>(g);
+        const float4 a = g4[0], b = g4[1], c = g4[2], d = g4[3];
+        q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w;
+        q[4] = b.x; q[5] = b.y; q[6] = b.z; q[7] = b.w;
+        w[0] = c.x; w[1] = c.y; w[2] = c.z; w[3] = c.w;
+        w[4] = d.x; w[5] = d.y; w[6] = d.z; w[7] = d.w;
+    } else {
+        const double2 *g2 = reinterpret_cast<const double2 *>(g);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double2 x = g2[k], y = g2[4 + k];
+            q[2 * k] = x.x; q[2 * k + 1] = x.y;
+            w[2 * k] = y.x; w[2 * k + 1] = y.y;
+        }
     }
 }
 
@@ -181,8 +210,8 @@ __device__ __forceinline__ void fv_store_vals(T *sv, int c, int m, const T *v) {
 // pairs.
 template <class T>
 __device__ __forceinline__ void fv_boundary_pairs(int type, const T *__restrict__ bval, int nbt, T nx, T ny,
-                                               const typename FvPair<T>::V *fc, T f0, T rho0,
-                                               typename FvPair<T>::V *out) {
+                                                  const typename FvPair<T>::V *fc, T f0, T rho0,
+                                                  typename FvPair<T>::V *out) {
     using PV = FvPair<T>;
     T fcs[kQ], fb[kQ], dr, r, u, v;
     fcs[0] = f0;
@@ -198,29 +227,27 @@ __device__ __forceinline__ void fv_boundary_pairs(int type, const T *__restrict_
 }
 
 // Stage 1: f^(1) = [f^n + (dt/tau)/4 f^eq(f^n)] / (1 + (dt/tau)/4) (Eq. (fnewstage), J = 1)
-// of staged cell e, in place.
+// of a cell given as f[9] (alpha order), written to staged row e.
 template <class T>
-__device__ __forceinline__ void fv_relax_row(T *sf, T *sf0, int e, T rho0, T dt, T tau_e) {
-    using V = typename FvPair<T>::V;
-    V fr[4];
-    fv_load_row(sf, e, fr);
-    T f[kQ];
-    f[0] = sf0[e];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        f[fv_first(p)] = fr[p].x;
-        f[fv_second(p)] = fr[p].y;
-    }
+__device__ __forceinline__ void fv_relax_to_row(T *f, T *sf, T *sf0, int e, T rho0, T dt, T tau_e) {
     relax9(f, rho0, dt, tau_e);
     sf0[e] = f[0];
-    const int sw = (e & 4) ? 4 : 0;
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(sf + e * 8 + 4 * fv_half(e, 0)) = make_float4(f[1], f[3], f[2], f[4]);
+        *reinterpret_cast<float4 *>(sf + e * 8 + 4 * fv_half(e, 1)) = make_float4(f[5], f[7], f[6], f[8]);
+    } else {
 #pragma unroll
-    for (int a = 1; a < kQ; ++a) sf[e * 8 + (fv_pos(a) ^ sw)] = f[a];
+        for (int a = 1; a < kQ; ++a) sf[fv_alpha_off(e, a)] = f[a];
+    }
 }
 
-// Gradient (Step 2) and outgoing face values of item / ring-1 cell c.  q: node positions
-// relative to the centroid; lw: least-squares weights W_m = M^{-1} d_m (x, y per face slot);
-// w: adjacency.
+// End node of face m of a cell (m compile-time): node m + 1, wrapping to node 0 after the last
+// face; selects between static indices keep q in registers.
+#define FV_END_X(m) ((m) == 3 ? q[0] : ((m) == 2 && tri ? q[0] : q[2 * (m) + 2]))
+#define FV_END_Y(m) ((m) == 3 ? q[1] : ((m) == 2 && tri ? q[1] : q[2 * (m) + 3]))
+
+// Gradient (Step 2) and outgoing face values of item cell c.  q: node positions relative to
+// the centroid; lw: least-squares weights W_m = M^{-1} d_m (x, y per face slot); w: adjacency.
 template <class T>
 __device__ __forceinline__ void fv_cell(int c, const T *q, const T *lw, const uint4 &w4,
                                         const T *__restrict__ sf, T f0, T *__restrict__ sv,
@@ -231,10 +258,6 @@ __device__ __forceinline__ void fv_cell(int c, const T *q, const T *lw, const ui
     V fc[4];
     fv_load_row(sf, c, fc);
     const bool tri = w[3] == kFvNone;
-    // end node of face m (m compile-time): node m + 1, wrapping to node 0 after the last face;
-    // selects between static indices keep q in registers
-    auto end_x = [&](int m) { return m == 3 ? q[0] : (m == 2 && tri ? q[0] : q[2 * m + 2]); };
-    auto end_y = [&](int m) { return m == 3 ? q[1] : (m == 2 && tri ? q[1] : q[2 * m + 3]); };
     V gx[4], gy[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) gx[p] = gy[p] = PV::bcast(T(0));
@@ -247,7 +270,7 @@ __device__ __forceinline__ void fv_cell(int c, const T *q, const T *lw, const ui
         if (w[m] & kFvBnd) {
             // boundary face: its value at the face midpoint is one more data point
             const int bf = static_cast<int>(w[m] & ~kFvBnd);
-            const T nx = end_y(m) - q[2 * m + 1], ny = -(end_x(m) - q[2 * m]);  // outward (unscaled)
+            const T nx = FV_END_Y(m) - q[2 * m + 1], ny = -(FV_END_X(m) - q[2 * m]);  // outward
             fv_boundary_pairs<T>(G.btype[bf], G.bval + bf, G.nbt, nx, ny, fc, f0, rho0, fm);
         } else {
             fv_load_row(sf, static_cast<int>(w[m] & 0xFFFFu), fm);
@@ -263,8 +286,8 @@ __device__ __forceinline__ void fv_cell(int c, const T *q, const T *lw, const ui
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         if (w[m] == kFvNone || (w[m] & kFvBnd)) continue;
-        const V rx = PV::bcast(T(0.5) * (q[2 * m] + end_x(m)));
-        const V ry = PV::bcast(T(0.5) * (q[2 * m + 1] + end_y(m)));
+        const V rx = PV::bcast(T(0.5) * (q[2 * m] + FV_END_X(m)));
+        const V ry = PV::bcast(T(0.5) * (q[2 * m + 1] + FV_END_Y(m)));
         T out[4];
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
@@ -272,6 +295,48 @@ __device__ __forceinline__ void fv_cell(int c, const T *q, const T *lw, const ui
             out[p] = ((w[m] >> (18 + p)) & 1u) ? val.x : val.y;
         }
         fv_store_vals(sv, c, m, out);
+    }
+}
+
+// The same for one direction pair p of ring-1 cell c (four threads share a ring-1 cell, one
+// pair each, and write one value per face slot each).
+template <class T>
+__device__ __forceinline__ void fv_cell_pair(int c, int p, const T *q, const T *lw, const uint4 &w4,
+                                             const T *__restrict__ sf, const T *__restrict__ sf0,
+                                             T *__restrict__ sv, const Geo<T> &G, T rho0) {
+    using PV = FvPair<T>;
+    using V = typename PV::V;
+    const unsigned w[4] = {w4.x, w4.y, w4.z, w4.w};
+    const V fc = *reinterpret_cast<const V *>(sf + fv_pair_off(c, p));
+    const bool tri = w[3] == kFvNone;
+    V gx = PV::bcast(T(0)), gy = PV::bcast(T(0));
+    const V mone = PV::bcast(T(-1));
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (w[m] == kFvNone) continue;
+        const V wx = PV::bcast(lw[2 * m]), wy = PV::bcast(lw[2 * m + 1]);
+        V fm;
+        if (w[m] & kFvBnd) {
+            const int bf = static_cast<int>(w[m] & ~kFvBnd);
+            const T nx = FV_END_Y(m) - q[2 * m + 1], ny = -(FV_END_X(m) - q[2 * m]);
+            V fall[4], fb[4];
+            fv_load_row(sf, c, fall);
+            fv_boundary_pairs<T>(G.btype[bf], G.bval + bf, G.nbt, nx, ny, fall, sf0[c], rho0, fb);
+            fm = p == 0 ? fb[0] : (p == 1 ? fb[1] : (p == 2 ? fb[2] : fb[3]));
+        } else {
+            fm = *reinterpret_cast<const V *>(sf + fv_pair_off(static_cast<int>(w[m] & 0xFFFFu), p));
+        }
+        const V df = PV::fma(fc, mone, fm);
+        gx = PV::fma(wx, df, gx);
+        gy = PV::fma(wy, df, gy);
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        if (w[m] == kFvNone || (w[m] & kFvBnd)) continue;
+        const V rx = PV::bcast(T(0.5) * (q[2 * m] + FV_END_X(m)));
+        const V ry = PV::bcast(T(0.5) * (q[2 * m + 1] + FV_END_Y(m)));
+        const V val = PV::fma(gy, ry, PV::fma(gx, rx, fc));
+        sv[fv_sv_off(c, m) + p] = ((w[m] >> (18 + p)) & 1u) ? val.x : val.y;
     }
 }
 
@@ -285,12 +350,10 @@ __device__ __forceinline__ void fv_flux(int t, const T *q, const uint4 &wt, cons
     using V = typename PV::V;
     const unsigned w[4] = {wt.x, wt.y, wt.z, wt.w};
     const bool tri = w[3] == kFvNone;
-    auto end_x = [&](int m) { return m == 3 ? q[0] : (m == 2 && tri ? q[0] : q[2 * m + 2]); };
-    auto end_y = [&](int m) { return m == 3 ? q[1] : (m == 2 && tri ? q[1] : q[2 * m + 3]); };
     T a2x = T(0);  // twice the area (shoelace on centroid-relative nodes)
 #pragma unroll
     for (int m = 0; m < 4; ++m)
-        if (m < 3 || !tri) a2x += q[2 * m] * end_y(m) - end_x(m) * q[2 * m + 1];
+        if (m < 3 || !tri) a2x += q[2 * m] * FV_END_Y(m) - FV_END_X(m) * q[2 * m + 1];
     const T inv_a = a2x > T(0) ? T(2) / a2x : T(0);  // padding cells have no faces
     V ac[4];
 #pragma unroll
@@ -301,7 +364,7 @@ __device__ __forceinline__ void fv_flux(int t, const T *q, const uint4 &wt, cons
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         if (w[m] == kFvNone) continue;
-        const T x1 = end_x(m), y1 = end_y(m);
+        const T x1 = FV_END_X(m), y1 = FV_END_Y(m);
         const T snx = (y1 - q[2 * m + 1]) * inv_a;   // n dl / A
         const T sny = -(x1 - q[2 * m]) * inv_a;
         if (w[m] & kFvBnd) {
@@ -334,14 +397,19 @@ __device__ __forceinline__ void fv_flux(int t, const T *q, const uint4 &wt, cons
     }
 }
 
+#undef FV_END_X
+#undef FV_END_Y
+
 // One IMEX stage (see fvlbm_kernels.cu's stage_algebra for what STAGE computes) in the
-// face-value form, one CTA of 256 threads per work item.
+// face-value form, one CTA of 256 threads per work item.  fin: stage 1 f^n (structure of
+// arrays), stages 2, 3 f^(2), f^(3) (cell-major rows); fs_out: stages 1, 2 write f^(2),
+// f^(3) cell-major; fn: stage 3 writes f^{n+1}; geo: the cell-major geometry rows.
 template <class T, int STAGE, bool STATS>
-__global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? FVLBM_FV_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 2 : 1)
     k_fused_fv(const T *__restrict__ fin, T *__restrict__ fs_out, T *__restrict__ fn,
                T *__restrict__ Bacc, T *__restrict__ Cacc, const T *__restrict__ tau,
                T *__restrict__ mac, double *__restrict__ partial, Geo<T> G, FvItems W,
-               T *__restrict__ frel, CompactGeo<T> CG) {
+               const T *__restrict__ geo) {
     using PV = FvPair<T>;
     using V = typename PV::V;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -366,60 +434,70 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? FVLBM_FV_MIN_BLOC
     const T rho0 = ipv<T>(Pp->rho0, Pp->rho0_f);
     const bool mine = t < cnt;
     const int i = base + t;
+    const T *fa0 = fin + 8 * np;  // stages 2, 3: f_0 of every cell after the cell-major rows
 
-    // 1. staging, issued before any wait: the item's accumulator rows (and tau) by bulk copies
-    //    on one mbarrier; f^(J) of item, ring-1 and ring-2 cells, the adjacency and the ring-1
-    //    geometry by cp.async; the item cell's own geometry straight into registers
+    // 1. staging, issued before any wait
     if (t == 0) mbar_init(bar);
     __syncthreads();
     if (t == 0) {
         const unsigned row = static_cast<unsigned>(cnt * sizeof(T));
-        const int nrows = STAGE == 2 ? 2 * kQ : kQ;
-        mbar_expect_tx(bar, row * (nrows + (STAGE == 1 ? 0 : 1)));
+        // accumulator rows (stage 1: f^n, stage 2: B and C, stage 3: C), tau, and in stages
+        // 2, 3 the item's f rows and f_0
         const T *a1g = STAGE == 1 ? fin : (STAGE == 2 ? Bacc : Cacc);
+        unsigned bytes = row * (STAGE == 2 ? 2 * kQ + 1 : kQ + 1);
+        if (STAGE != 1) bytes += 9 * row;
+        mbar_expect_tx(bar, bytes);
         for (int a = 0; a < kQ; ++a) bulk_g2s(sacc + a * kFvThreads, a1g + a * np + base, row, bar);
         if (STAGE == 2)
             for (int a = 0; a < kQ; ++a) bulk_g2s(sacc + (kQ + a) * kFvThreads, Cacc + a * np + base, row, bar);
-        if (STAGE != 1) bulk_g2s(stau, tau + base, row, bar);
+        bulk_g2s(sacc + 2 * kQ * kFvThreads, tau + base, row, bar);
+        if (STAGE != 1) {
+            bulk_g2s(sf, fin + 8 * static_cast<size_t>(base), 8 * row, bar);
+            bulk_g2s(sf0, fa0 + base, row, bar);
+        }
     }
-    for (int e = t; e < E; e += kFvThreads) {
-        const int gid = e < cnt ? base + e : W.halo[h0 + e - cnt];
-        const int sw = (e & 4) ? 4 : 0;
+    constexpr int per = 16 / sizeof(T);  // elements per 16-byte chunk
+    for (int e = cnt + t; e < E; e += kFvThreads) {  // halo cells (item rows come in bulk)
+        const int gid = W.halo[h0 + e - cnt];
+        if (STAGE == 1) {  // f^n is structure of arrays: one element per direction
 #pragma unroll
-        for (int a = 1; a < kQ; ++a)
-            cp_async<sizeof(T)>(sf + e * 8 + (fv_pos(a) ^ sw), fin + a * np + gid);
-        cp_async<sizeof(T)>(sf0 + e, fin + gid);
-        if (STAGE == 1) {
+            for (int a = 1; a < kQ; ++a) cp_async<sizeof(T)>(sf + fv_alpha_off(e, a), fin + a * np + gid);
+            cp_async<sizeof(T)>(sf0 + e, fin + gid);
             cp_async<sizeof(T)>(stau + e, tau + gid);
             if (G.dtc != nullptr) cp_async<sizeof(T)>(sdt + e, G.dtc + gid);
-        }
-        if (e < NG) {
-            cp_async<16>(sa + e, adj_g + e);
-            if (e >= cnt) {  // ring-1 geometry into its face-value row (swizzled 16-byte chunks)
-                const int cs = (e >> 1) & 3;
+        } else {  // one cell-major row: half h sits at half fv_half(gid, h) there, fv_half(e, h) here
+            const T *src = fin + 8 * static_cast<size_t>(gid);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    cp_async<sizeof(T)>(sv + e * 16 + 4 * ((k >> 2) ^ cs) + (k & 3), CG.gq + k * np + gid);
-                    cp_async<sizeof(T)>(sv + e * 16 + 4 * ((2 + (k >> 2)) ^ cs) + (k & 3), G.lsq + k * np + gid);
-                }
-            }
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int k = 0; k < 4 / per; ++k)
+                    cp_async<16>(sf + e * 8 + 4 * fv_half(e, h) + k * per, src + 4 * fv_half(gid, h) + k * per);
+            cp_async<sizeof(T)>(sf0 + e, fa0 + gid);
+        }
+        if (e < NG) {  // ring-1 geometry into its face-value row (swizzled 16-byte chunks)
+            const T *g = geo + 16 * static_cast<size_t>(gid);
+            const int cs = (e >> 1) & 3;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int h = 0; h < 4 / per; ++h)
+                    cp_async<16>(sv + e * 16 + 4 * (k ^ cs) + h * per, g + 4 * k + h * per);
         }
     }
+    for (int e = t; e < NG; e += kFvThreads) cp_async<16>(sa + e, adj_g + e);
     T q[8], lw[8];
-    if (mine) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            q[k] = CG.gq[k * np + i];
-            lw[k] = G.lsq[k * np + i];
-        }
-    }
+    if (mine) fv_load_geo_row(geo + 16 * static_cast<size_t>(i), q, lw);  // the item cell's geometry row
     cp_async_wait_all();
-    // stage 1: each thread relaxes the cells it staged itself (its own copies have landed), so
-    // the relaxation needs no barrier of its own
+    // stage 1: each thread relaxes the halo cells it staged (its own copies have landed)
+    const T dtg = ipv<T>(Pp->dt, Pp->dt_f);
     if (STAGE == 1) {
-        const T dtg = ipv<T>(Pp->dt, Pp->dt_f);
-        for (int e = t; e < E; e += kFvThreads)
-            fv_relax_row(sf, sf0, e, rho0, G.dtc != nullptr ? sdt[e] : dtg, stau[e]);
+        for (int e = cnt + t; e < E; e += kFvThreads) {
+            T f[kQ];
+            f[0] = sf0[e];
+#pragma unroll
+            for (int a = 1; a < kQ; ++a) f[a] = sf[fv_alpha_off(e, a)];
+            fv_relax_to_row(f, sf, sf0, e, rho0, G.dtc != nullptr ? sdt[e] : dtg, stau[e]);
+        }
     }
     {
         long long it = 0;
@@ -436,24 +514,45 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? FVLBM_FV_MIN_BLOC
             return;
         }
     }
-
-    // 2. gradients and outgoing face values of item and ring-1 cells
-    if (mine) fv_cell<T>(t, q, lw, sa[t], sf, sf0[t], sv, G, rho0);
-    for (int c = (mine ? t + kFvThreads : t); c < NG; c += kFvThreads) {
-        if (c < cnt) continue;  // only when cnt < 256: item cells are all handled above
-        T qr[8], lr[8];
-        fv_load_vals(sv, c, 0, qr);       // geometry chunks staged in the face-value row
+    // stage 1: the item cells' f^(1) from their f^n rows (in the accumulator copy)
+    if (STAGE == 1 && mine) {
+        T f[kQ];
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) f[a] = sacc[a * kFvThreads + t];
+        fv_relax_to_row(f, sf, sf0, t, rho0, G.dtc != nullptr ? G.dtc[i] : dtg, sacc[2 * kQ * kFvThreads + t]);
+    }
+    // ring-1 geometry for the pair-split work below, read before any face value is written
+    const int ru = 4 * nr1;  // ring-1 work units: (cell, pair)
+    T qr[8], lr[8];
+    uint4 wr = make_uint4(kFvNone, kFvNone, kFvNone, kFvNone);
+    if (t < ru) {
+        const int c = cnt + (t >> 2);
+        fv_load_vals(sv, c, 0, qr);
         fv_load_vals(sv, c, 1, qr + 4);
         fv_load_vals(sv, c, 2, lr);
         fv_load_vals(sv, c, 3, lr + 4);
-        fv_cell<T>(c, qr, lr, sa[c], sf, sf0[c], sv, G, rho0);
+        wr = sa[c];
+    }
+    __syncthreads();
+
+    // 2. gradients and outgoing face values: item cells (thread t takes cell t), then ring-1
+    //    cells with one direction pair per thread
+    if (mine) fv_cell<T>(t, q, lw, sa[t], sf, sf0[t], sv, G, rho0);
+    if (t < ru) fv_cell_pair<T>(cnt + (t >> 2), t & 3, qr, lr, wr, sf, sf0, sv, G, rho0);
+    for (int u = t + kFvThreads; u < ru; u += kFvThreads) {  // items with more than 64 ring-1 cells
+        // the face-value rows of these cells may already hold values: read their geometry
+        // from the global rows
+        const int c = cnt + (u >> 2);
+        T q2[8], l2[8];
+        fv_load_geo_row(geo + 16 * static_cast<size_t>(W.halo[h0 + (u >> 2)]), q2, l2);
+        fv_cell_pair<T>(c, u & 3, q2, l2, sa[c], sf, sf0, sv, G, rho0);
     }
     __syncthreads();
 
     // 3. flux of item cell t (Eq. (advection)) from the published face values
-    T fi[kQ], acc[kQ];
     double st[4] = {0.0, 0.0, 0.0, 0.0};
     if (mine) {
+        T fi[kQ], acc[kQ];
         const uint4 wt = sa[t];
         V fr[4];
         fv_load_row(sf, t, fr);
@@ -473,10 +572,10 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? FVLBM_FV_MIN_BLOC
             uo = mac[1 * np + i];
             vo0 = mac[2 * np + i];
         }
-        stage_algebra<T, STAGE, false, kFvThreads, false>(i, np, fi, acc, P, stau[t], cell_dt(G, P, i), sacc,
-                                                          kFvThreads, t, sacc + kQ * kFvThreads, kFvThreads, t,
-                                                          fs_out, fn, Bacc, Cacc, mac, nullptr, G.area, frel,
-                                                          false, T(0), macv);
+        const T tau_i = sacc[2 * kQ * kFvThreads + t];
+        stage_algebra<T, STAGE, false, kFvThreads, false, true>(
+            i, np, fi, acc, P, tau_i, cell_dt(G, P, i), sacc, kFvThreads, t, sacc + kQ * kFvThreads, kFvThreads,
+            t, fs_out, fn, Bacc, Cacc, mac, nullptr, G.area, nullptr, false, T(0), macv);
         if (STATS) {
             const double un = double(macv[1]), vn = double(macv[2]), r = double(macv[0]);
             const bool bad = !(isfinite(un) && isfinite(vn) && isfinite(r));
@@ -487,266 +586,4 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? FVLBM_FV_MIN_BLOC
         }
     }
     if (STATS) block_sum<4, kFvThreads>(st, partial + 4 * blockIdx.x);
-}
-
-// ------------------------------------------------------------------ persistent form
-// The same stage in a persistent kernel: a grid of (SMs x resident CTAs) walks the work items
-// round-robin (CTA b takes items b, b + grid, b + 2 grid, ...: at any time the grid works on a
-// window of consecutive items, whose halos are each other's cells and stay in L2).  While a
-// CTA computes item k, the copies of item k+1 are in flight:
-//   - f^(J) of its item, ring-1 and ring-2 cells, its adjacency, the ring-1 geometry (and in
-//     stage 1 tau and dt of every staged cell) go into the second of two staging buffers by
-//     cp.async, issued when item k starts;
-//   - its accumulator rows and tau (bulk copies on one mbarrier) and its cells' own geometry
-//     (cp.async into their face-value rows) are issued when item k has finished with them.
-// Only the face-value rows and the accumulator rows are single-buffered.
-
-constexpr int kFvR1cap = 96;   // ring-1 cells of one item (the host splits items beyond it)
-
-template <class T>
-struct FvpSmem {
-    // one staging buffer
-    static constexpr size_t sf = 0;
-    static constexpr size_t sf0 = sf + size_t(kFvEcap) * 8 * sizeof(T);
-    static constexpr size_t st = sf0 + ((size_t(kFvEcap) * sizeof(T) + 15) / 16) * 16;
-    static constexpr size_t sa = st + 2 * size_t(kFvEcap) * sizeof(T);
-    static constexpr size_t sg = sa + size_t(kFvGcap) * 16;
-    static constexpr size_t buf = sg + size_t(kFvR1cap) * 16 * sizeof(T);
-    // shared by the items
-    static constexpr size_t sv = 2 * buf;
-    static constexpr size_t sacc = sv + size_t(kFvGcap) * 16 * sizeof(T);
-    static constexpr size_t bar = sacc + size_t(2 * kQ + 1) * kFvThreads * sizeof(T);
-    static constexpr size_t bytes = bar + 16;
-};
-
-struct FvItem {
-    int base, cnt, h0, nh, nr1, adj0;
-};
-
-__device__ __forceinline__ FvItem fv_item(const FvItems &W, int k) {
-    const int4 hd = W.hdr[k];
-    FvItem it;
-    it.base = hd.x;
-    it.cnt = hd.y;
-    it.h0 = hd.z;
-    it.nh = W.hdr[k + 1].z - hd.z;
-    it.nr1 = W.r1[k];
-    it.adj0 = hd.w;
-    return it;
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// cp.async of the staging buffer of one item (f^(J) of item, ring-1 and ring-2 cells; stage 1:
-// tau and dt of each; adjacency of item and ring-1 cells; ring-1 geometry)
-template <class T, int STAGE>
-__device__ __forceinline__ void fvp_stage_buffer(unsigned char *b, const FvItem &it, const T *__restrict__ fin,
-                                                 const T *__restrict__ tau, const FvItems &W,
-                                                 const Geo<T> &G, const CompactGeo<T> &CG) {
-    T *sf = reinterpret_cast<T *>(b + FvpSmem<T>::sf);
-    T *sf0 = reinterpret_cast<T *>(b + FvpSmem<T>::sf0);
-    T *stau = reinterpret_cast<T *>(b + FvpSmem<T>::st);
-    T *sdt = stau + kFvEcap;
-    uint4 *sa = reinterpret_cast<uint4 *>(b + FvpSmem<T>::sa);
-    T *sg = reinterpret_cast<T *>(b + FvpSmem<T>::sg);
-    const size_t np = G.np;
-    const int E = it.cnt + it.nh, NG = it.cnt + it.nr1;
-    for (int e = threadIdx.x; e < E; e += kFvThreads) {
-        const int gid = e < it.cnt ? it.base + e : W.halo[it.h0 + e - it.cnt];
-        const int sw = (e & 4) ? 4 : 0;
-#pragma unroll
-        for (int a = 1; a < kQ; ++a)
-            cp_async<sizeof(T)>(sf + e * 8 + (fv_pos(a) ^ sw), fin + a * np + gid);
-        cp_async<sizeof(T)>(sf0 + e, fin + gid);
-        if (STAGE == 1) {
-            cp_async<sizeof(T)>(stau + e, tau + gid);
-            if (G.dtc != nullptr) cp_async<sizeof(T)>(sdt + e, G.dtc + gid);
-        }
-        if (e < NG) {
-            cp_async<16>(sa + e, W.adj + it.adj0 + e);
-            if (e >= it.cnt) {  // ring-1 geometry, swizzled 16-byte chunks like the face values
-                const int r = e - it.cnt, cs = (e >> 1) & 3;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    cp_async<sizeof(T)>(sg + r * 16 + 4 * ((k >> 2) ^ cs) + (k & 3), CG.gq + k * np + gid);
-                    cp_async<sizeof(T)>(sg + r * 16 + 4 * ((2 + (k >> 2)) ^ cs) + (k & 3), G.lsq + k * np + gid);
-                }
-            }
-        }
-    }
-}
-
-// Copies of one item issued once the previous item has finished with the single buffers:
-// the item cells' geometry into their face-value rows (cp.async) and, by thread 0, the
-// accumulator rows and tau (bulk copies on the mbarrier).
-template <class T, int STAGE>
-__device__ __forceinline__ void fvp_stage_item_rows(const FvItem &it, T *sv, T *sacc, unsigned long long *bar,
-                                                    const T *__restrict__ fin, const T *__restrict__ Bacc,
-                                                    const T *__restrict__ Cacc, const T *__restrict__ tau,
-                                                    const Geo<T> &G, const CompactGeo<T> &CG) {
-    const size_t np = G.np;
-    const int e = threadIdx.x;
-    if (e < it.cnt) {
-        const int gid = it.base + e, cs = (e >> 1) & 3;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            cp_async<sizeof(T)>(sv + e * 16 + 4 * ((k >> 2) ^ cs) + (k & 3), CG.gq + k * np + gid);
-            cp_async<sizeof(T)>(sv + e * 16 + 4 * ((2 + (k >> 2)) ^ cs) + (k & 3), G.lsq + k * np + gid);
-        }
-    }
-    if (e == 0) {
-        const unsigned row = static_cast<unsigned>(it.cnt * sizeof(T));
-        const int nrows = (STAGE == 2 ? 2 * kQ : kQ) + (STAGE == 1 ? 0 : 1);
-        mbar_expect_tx(bar, row * nrows);
-        const T *a1g = STAGE == 1 ? fin : (STAGE == 2 ? Bacc : Cacc);
-        for (int a = 0; a < kQ; ++a) bulk_g2s(sacc + a * kFvThreads, a1g + a * np + it.base, row, bar);
-        if (STAGE == 2)
-            for (int a = 0; a < kQ; ++a)
-                bulk_g2s(sacc + (kQ + a) * kFvThreads, Cacc + a * np + it.base, row, bar);
-        if (STAGE != 1) bulk_g2s(sacc + 2 * kQ * kFvThreads, tau + it.base, row, bar);
-    }
-}
-
-template <class T, int STAGE, bool STATS>
-__global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 2 : 1)
-    k_fused_fvp(const T *__restrict__ fin, T *__restrict__ fs_out, T *__restrict__ fn,
-                T *__restrict__ Bacc, T *__restrict__ Cacc, const T *__restrict__ tau,
-                T *__restrict__ mac, double *__restrict__ partial, Geo<T> G, FvItems W,
-                CompactGeo<T> CG, int nitem) {
-    using PV = FvPair<T>;
-    using V = typename PV::V;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T *sv = reinterpret_cast<T *>(smem_raw + FvpSmem<T>::sv);
-    T *sacc = reinterpret_cast<T *>(smem_raw + FvpSmem<T>::sacc);
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + FvpSmem<T>::bar);
-    const int t = threadIdx.x;
-    const size_t np = G.np;
-
-    int k = blockIdx.x;
-    if (k >= nitem) return;
-    if (t == 0) mbar_init(bar);
-    __syncthreads();
-    // prologue: the first item's copies
-    FvItem it = fv_item(W, k);
-    fvp_stage_buffer<T, STAGE>(smem_raw, it, fin, tau, W, G, CG);
-    fvp_stage_item_rows<T, STAGE>(it, sv, sacc, bar, fin, Bacc, Cacc, tau, G, CG);
-    cp_async_commit();
-    unsigned phase = 0;
-    for (int p = 0; k < nitem; k += gridDim.x, p ^= 1, phase ^= 1) {
-        unsigned char *b = smem_raw + p * FvpSmem<T>::buf;
-        T *sf = reinterpret_cast<T *>(b + FvpSmem<T>::sf);
-        T *sf0 = reinterpret_cast<T *>(b + FvpSmem<T>::sf0);
-        T *stau = reinterpret_cast<T *>(b + FvpSmem<T>::st);
-        T *sdt = stau + kFvEcap;
-        uint4 *sa = reinterpret_cast<uint4 *>(b + FvpSmem<T>::sa);
-        T *sg = reinterpret_cast<T *>(b + FvpSmem<T>::sg);
-        const int nk = k + gridDim.x;
-        FvItem nx;
-        if (nk < nitem) {  // the next item's staging buffer, while this one computes
-            nx = fv_item(W, nk);
-            fvp_stage_buffer<T, STAGE>(smem_raw + (p ^ 1) * FvpSmem<T>::buf, nx, fin, tau, W, G, CG);
-        }
-        cp_async_commit();
-        cp_async_wait_group<1>();  // everything of this item has landed (only the newest group may not)
-
-        const int cnt = it.cnt, E = it.cnt + it.nh, NG = it.cnt + it.nr1;
-        const InstParam *__restrict__ Pp = G.ip + G.tile_inst[it.base / kTile];
-        const T rho0 = ipv<T>(Pp->rho0, Pp->rho0_f);
-        const bool mine = t < cnt;
-        const int i = it.base + t;
-        if (STAGE == 1) {  // f^(1) of the cells this thread staged (their copies have landed)
-            const T dtg = ipv<T>(Pp->dt, Pp->dt_f);
-            for (int e = t; e < E; e += kFvThreads)
-                fv_relax_row(sf, sf0, e, rho0, G.dtc != nullptr ? sdt[e] : dtg, stau[e]);
-        }
-        __syncthreads();
-
-        // gradients and outgoing face values of item cells (geometry in their face-value rows)
-        // and ring-1 cells (geometry in the staging buffer)
-        T q[8];
-        if (mine) {
-            T lw[8];
-            fv_load_vals(sv, t, 0, q);
-            fv_load_vals(sv, t, 1, q + 4);
-            fv_load_vals(sv, t, 2, lw);
-            fv_load_vals(sv, t, 3, lw + 4);
-            fv_cell<T>(t, q, lw, sa[t], sf, sf0[t], sv, G, rho0);
-        }
-        for (int c = (mine ? t + kFvThreads : t); c < NG; c += kFvThreads) {
-            if (c < cnt) continue;
-            T qr[8], lr[8];
-            const T *g = sg + (c - cnt) * 16;   // swizzled like face-value row c
-            const int cs = (c >> 1) & 3;
-#pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-                qr[k4] = g[4 * (0 ^ cs) + k4];
-                qr[4 + k4] = g[4 * (1 ^ cs) + k4];
-                lr[k4] = g[4 * (2 ^ cs) + k4];
-                lr[4 + k4] = g[4 * (3 ^ cs) + k4];
-            }
-            fv_cell<T>(c, qr, lr, sa[c], sf, sf0[c], sv, G, rho0);
-        }
-        __syncthreads();
-
-        // the accumulator rows of this item (issued when the previous item finished)
-        {
-            long long itw = 0;
-            bool done = W.wait_first > 0 ? mbar_try_wait(bar, phase) : mbar_test_wait(bar, phase);
-            while (!done && ++itw < W.wait_first) done = mbar_try_wait(bar, phase);
-            if (__syncthreads_or(!done)) {
-                if (t == 0) atomicExch(W.err, 1);
-                for (long long w = 0; w < kWaitLimit && !mbar_try_wait(bar, phase); ++w) {
-                }
-                cp_async_wait_all();  // nothing may land in shared memory after the CTA leaves
-                return;
-            }
-        }
-
-        double st[4] = {0.0, 0.0, 0.0, 0.0};
-        if (mine) {
-            T fi[kQ], acc[kQ];
-            const uint4 wt = sa[t];
-            V fr[4];
-            fv_load_row(sf, t, fr);
-            fi[0] = sf0[t];
-#pragma unroll
-            for (int q2 = 0; q2 < 4; ++q2) {
-                fi[fv_first(q2)] = fr[q2].x;
-                fi[fv_second(q2)] = fr[q2].y;
-            }
-            fv_flux<T>(t, q, wt, fi, sv, G, rho0, acc);
-            const InstParam P = *Pp;
-            T macv[3];
-            T uo = T(0), vo0 = T(0);
-            if (STATS) {
-                uo = mac[1 * np + i];
-                vo0 = mac[2 * np + i];
-            }
-            const T tau_i = STAGE == 1 ? stau[t] : sacc[2 * kQ * kFvThreads + t];
-            stage_algebra<T, STAGE, false, kFvThreads, false>(i, np, fi, acc, P, tau_i, cell_dt(G, P, i), sacc,
-                                                              kFvThreads, t, sacc + kQ * kFvThreads, kFvThreads,
-                                                              t, fs_out, fn, Bacc, Cacc, mac, nullptr, G.area,
-                                                              nullptr, false, T(0), macv);
-            if (STATS) {
-                const double un = double(macv[1]), vn = double(macv[2]), r = double(macv[0]);
-                const bool bad = !(isfinite(un) && isfinite(vn) && isfinite(r));
-                st[0] = (un - double(uo)) * (un - double(uo)) + (vn - double(vo0)) * (vn - double(vo0));
-                st[1] = un * un + vn * vn;
-                st[2] = r * double(G.area[i]);
-                st[3] = bad ? 1.0 : 0.0;
-            }
-        }
-        if (STATS) block_sum<4, kFvThreads>(st, partial + 4 * k);
-        __syncthreads();  // this item is done with the face values, the accumulators and its buffer
-        if (nk < nitem) {
-            fvp_stage_item_rows<T, STAGE>(nx, sv, sacc, bar, fin, Bacc, Cacc, tau, G, CG);
-            cp_async_commit();  // its own group: the next iteration's wait covers it
-            it = nx;
-        }
-    }
-    cp_async_wait_all();
 }

@@ -856,6 +856,21 @@ template int check_prepared<Dual>(const PreparedT<Dual> &, std::string *);
 
 }  // namespace fvlbm
 
+extern "C" int fvlbm_cell_geometry(const fvlbm_mesh *mesh, const fvlbm_bc *bc,
+                                   const fvlbm_params *params, double *area, double *wdist) {
+    if (!mesh || !bc || !params) return FVLBM_ERR_BAD_PARAM;
+    fvlbm::Prepared P;
+    std::string msg;
+    const int rc = fvlbm::prepare_instance(*mesh, *bc, *params, &P, &msg);
+    if (rc != FVLBM_OK) return rc;
+    for (int k = 0; k < P.nc; ++k) {  // internal order -> input order
+        const int c = P.perm[k];
+        if (area) area[c] = P.area[k];
+        if (wdist) wdist[c] = P.wdist[k];
+    }
+    return FVLBM_OK;
+}
+
 extern "C" int fvlbm_check_mesh(const fvlbm_mesh *mesh, const fvlbm_bc *bc, const fvlbm_params *params,
                                 double *dt, char *why, int why_len) {
     std::string msg;

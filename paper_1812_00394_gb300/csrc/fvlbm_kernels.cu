@@ -345,7 +345,30 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *out) {
 // The collision terms are formed from differences that are not scaled by z: with
 // f^(J) = (X + zJ f^eq) / (1 + zJ), dt Gamma^c(J) = dt/tau (f^eq - X) / (1 + zJ) exactly, so a
 // rounding of X or f^eq is multiplied by dt/tau / (1 + zJ) <= 1/m_JJ instead of dt/tau.
-template <class T, int STAGE, bool STATS, int NT, bool FN_FROM_F1 = false>
+// Store of a stage value f^(2) or f^(3): structure of arrays, or (ROWS) the cell-major rows of
+// the face-value stages: alpha = 1..8 in pair order (1,3)(2,4)(5,7)(6,8) at f[8 i] (the two
+// halves swapped where bit 2 of i is set), f_0 at f[8 np + i].
+template <class T, bool ROWS>
+__device__ __forceinline__ void store_stage(T *__restrict__ f, size_t np, int i, const T *o) {
+    if constexpr (!ROWS) {
+        store9(f, np, i, o);
+    } else {
+        T *row = f + 8 * static_cast<size_t>(i);
+        const int sw = (i & 4) ? 4 : 0;  // halves swapped where bit 2 of the cell index is set
+        if constexpr (std::is_same<T, float>::value) {
+            *reinterpret_cast<float4 *>(row + sw) = make_float4(o[1], o[3], o[2], o[4]);
+            *reinterpret_cast<float4 *>(row + (sw ^ 4)) = make_float4(o[5], o[7], o[6], o[8]);
+        } else {
+            *reinterpret_cast<double2 *>(row + sw) = make_double2(o[1], o[3]);
+            *reinterpret_cast<double2 *>(row + sw + 2) = make_double2(o[2], o[4]);
+            *reinterpret_cast<double2 *>(row + (sw ^ 4)) = make_double2(o[5], o[7]);
+            *reinterpret_cast<double2 *>(row + (sw ^ 4) + 2) = make_double2(o[6], o[8]);
+        }
+        f[8 * np + i] = o[0];
+    }
+}
+
+template <class T, int STAGE, bool STATS, int NT, bool FN_FROM_F1 = false, bool ROWS = false>
 __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, const T *acc,
                                               const InstParam &P, T t_i, T dt_i, const T *a1, size_t ld1,
                                               int c1, const T *a2, size_t ld2, int c2,
@@ -403,7 +426,7 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
             Bacc[a * np + i] = X[a] + T(1.0 / 3.0) * (dgc1[a] + dgc2);
             Cacc[a * np + i] = dt6 * acc[a];
         }
-        store9(fs_out, np, i, f2);
+        store_stage<T, ROWS>(fs_out, np, i, f2);
     } else if (STAGE == 2) {
         T X[kQ], eq[kQ], dr, r, u, v, f3[kQ];
 #pragma unroll
@@ -417,7 +440,7 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
             f3[a] = (X[a] + zt * eq[a]) * inv;
             Cacc[a * np + i] = a2[a * ld2 + c2] + dt6 * acc[a];
         }
-        store9(fs_out, np, i, f3);
+        store_stage<T, ROWS>(fs_out, np, i, f3);
     } else if (STAGE == 4) {
         // explicit Euler (comparison scheme): f^{n+1} = f^n + dt [Gamma^a + Gamma^c](f^n)
         T eq[kQ], fnew[kQ], dr, r, u, v;
@@ -947,11 +970,22 @@ struct SstFace {
 // Convection (limited second-order upwind, mean face velocity), central diffusion (mean face
 // coefficient), explicit production and cross diffusion, point-implicit destruction; then f2,
 // nu_t = a1 k / max(a1 omega, S f2) and tau = (nu + nu_t)/cs^2.
+// The own-cell gradient enters the update only through three invariants: S_ij S_ij, div u and
+// grad k . grad omega (Sec. 2: production, nu_t limiter, cross diffusion).
+template <class T>
+__device__ __forceinline__ void sst_invariants(const T *g, T &SS, T &dv, T &kw) {
+    const T s11 = g[0], s22 = g[3], s12 = T(0.5) * (g[1] + g[2]);
+    SS = s11 * s11 + s22 * s22 + T(2) * s12 * s12;
+    dv = s11 + s22;
+    kw = g[4] * g[6] + g[5] * g[7];
+}
+
+// g (the own gradients) is read by the reading variants only; SS, dv, kw are its invariants.
 template <class T, bool NONORTH>
 __device__ __forceinline__ void sst_cell_update(const InstParam &P, T dt, T ui, T vi, T ki, T wi,
-                                                T nti, T di, const T *g, const T *lgi, T f1,
-                                                const SstFace<T> *F, T &kn, T &wn, T &ntn,
-                                                T &tnew) {
+                                                T nti, T di, const T *g, T SS, T dv, T kw,
+                                                const T *lgi, T f1, const SstFace<T> *F, T &kn,
+                                                T &wn, T &ntn, T &tnew) {
     const T nu = ipv<T>(P.nu, P.nu_f);
     const T sk_i = f1 * T(kSk1) + (T(1) - f1) * T(kSk2);
     const T sw_i = f1 * T(kSw1) + (T(1) - f1) * T(kSw2);
@@ -1006,9 +1040,6 @@ __device__ __forceinline__ void sst_cell_update(const InstParam &P, T dt, T ui, 
             dw += (nu + sw_i * nti) * dwn * dla;
         }
     }
-    const T s11 = g[0], s22 = g[3], s12 = T(0.5) * (g[1] + g[2]);
-    const T SS = s11 * s11 + s22 * s22 + T(2) * s12 * s12;
-    const T dv = s11 + s22;
     const T Sabs = sqrt(T(2) * SS);
     const T cw1 = T(kB1 / kBstar - kSw1 * kKappa * kKappa / 0.3);
     const T cw2 = T(kB2 / kBstar - kSw2 * kKappa * kKappa / 0.3);
@@ -1020,7 +1051,7 @@ __device__ __forceinline__ void sst_cell_update(const InstParam &P, T dt, T ui, 
     }
     T pw = gam * (T(2) * SS - T(2.0 / 3.0) * dv * dv);
     if (nti > T(0)) pw -= T(2.0 / 3.0) * gam * ki * dv / nti;
-    const T cross = T(2) * (T(1) - f1) * T(kSw2) / wi * (g[4] * g[6] + g[5] * g[7]);
+    const T cross = T(2) * (T(1) - f1) * T(kSw2) / wi * kw;
     const T rk = -ck + dk + pk;
     const T rw = -cw + dw + pw + cross;
     const T beta = f1 * T(kB1) + (T(1) - f1) * T(kB2);
@@ -1078,10 +1109,50 @@ __device__ __forceinline__ void compact_face_geo(const CompactGeo<T> &CG, size_t
     }
 }
 
+// Packed per-cell SST records of the fused path, written by the gradient kernel and gathered
+// by the update kernel for every neighbour: rec8 = (u, v, k, omega, limited grad k, limited
+// grad omega) in one 32-byte (FP32) row and rec2 = (f1, nu_t), so that a neighbour costs
+// three vector loads instead of ten scattered ones.
+template <class T>
+__device__ __forceinline__ void sst_store_rec(T *__restrict__ rec8, T *__restrict__ rec2, int i, const T *v8,
+                                              T f1, T nut) {
+    T *r = rec8 + 8 * static_cast<size_t>(i);
+    if constexpr (std::is_same<T, float>::value) {
+        *reinterpret_cast<float4 *>(r) = make_float4(v8[0], v8[1], v8[2], v8[3]);
+        *reinterpret_cast<float4 *>(r + 4) = make_float4(v8[4], v8[5], v8[6], v8[7]);
+        *reinterpret_cast<float2 *>(rec2 + 2 * static_cast<size_t>(i)) = make_float2(f1, nut);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) r[c] = v8[c];
+        rec2[2 * static_cast<size_t>(i)] = f1;
+        rec2[2 * static_cast<size_t>(i) + 1] = nut;
+    }
+}
+template <class T>
+__device__ __forceinline__ void sst_load_rec(const T *__restrict__ rec8, const T *__restrict__ rec2, int i, T *v8,
+                                             T &f1, T &nut) {
+    const T *r = rec8 + 8 * static_cast<size_t>(i);
+    if constexpr (std::is_same<T, float>::value) {
+        const float4 a = *reinterpret_cast<const float4 *>(r), b = *reinterpret_cast<const float4 *>(r + 4);
+        v8[0] = a.x; v8[1] = a.y; v8[2] = a.z; v8[3] = a.w;
+        v8[4] = b.x; v8[5] = b.y; v8[6] = b.z; v8[7] = b.w;
+        const float2 c = *reinterpret_cast<const float2 *>(rec2 + 2 * static_cast<size_t>(i));
+        f1 = c.x;
+        nut = c.y;
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v8[c] = r[c];
+        f1 = rec2[2 * static_cast<size_t>(i)];
+        nut = rec2[2 * static_cast<size_t>(i) + 1];
+    }
+}
+
 template <class T, bool COMPACT>
 __global__ void __launch_bounds__(kTile)
     k_sst_grad(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
-               T *__restrict__ grads, T *__restrict__ f1out, Geo<T> G, CompactGeo<T> CG) {
+               T *__restrict__ grads, T *__restrict__ f1out, Geo<T> G, CompactGeo<T> CG,
+               const T *__restrict__ nut = nullptr, T *__restrict__ rec8 = nullptr,
+               T *__restrict__ rec2 = nullptr, bool inv_only = false) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
@@ -1137,11 +1208,24 @@ __global__ void __launch_bounds__(kTile)
     }
     T g[8], lg[4], f1;
     sst_cell_grad(own[2], own[3], di, nu, has, q, W, R, own, g, lg, f1);
+    if (inv_only) {  // the update needs the invariants of the own gradient only
+        T SS, dv, kw;
+        sst_invariants(g, SS, dv, kw);
+        grads[i] = SS;
+        grads[np + i] = dv;
+        grads[2 * np + i] = kw;
+    } else {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) grads[c * np + i] = g[c];
+        for (int c = 0; c < 8; ++c) grads[c * np + i] = g[c];
+    }
+    if (rec8 != nullptr) {  // fused path: the packed record the update gathers
+        const T v8[8] = {own[0], own[1], own[2], own[3], lg[0], lg[1], lg[2], lg[3]};
+        sst_store_rec(rec8, rec2, i, v8, f1, nut[i]);
+    } else {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) grads[(8 + c) * np + i] = lg[c];
-    f1out[i] = f1;
+        for (int c = 0; c < 4; ++c) grads[(8 + c) * np + i] = lg[c];
+        f1out[i] = f1;
+    }
 }
 
 // The k / omega update and the new relaxation time (and, on the fused path, f^(1)).  In
@@ -1155,19 +1239,39 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 5 : 1)
                  const T *__restrict__ nut, const T *__restrict__ grads,
                  const T *__restrict__ f1a, T *__restrict__ k_out, T *__restrict__ w_out,
                  T *__restrict__ nut_out, T *__restrict__ tau, Geo<T> G,
-                 const T *__restrict__ fn, T *__restrict__ frel, CompactGeo<T> CG) {
+                 const T *__restrict__ fn, T *__restrict__ frel, CompactGeo<T> CG,
+                 const T *__restrict__ rec8 = nullptr, const T *__restrict__ rec2 = nullptr) {
     const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
     const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
     if (!P.sst) return;  // laminar instance
     const T nu = ipv<T>(P.nu, P.nu_f);
-    const T ui = mac[np + i], vi = mac[2 * np + i], ki = kk[i], wi = ww[i], nti = nut[i];
-    const T di = G.wdist[i];
+    const bool packed = COMPACT && rec8 != nullptr;
+    T ui, vi, ki, wi, nti, f1i;
     T g[8], lgi[4];
+    if (packed) {
+        T v8[8];
+        sst_load_rec(rec8, rec2, i, v8, f1i, nti);
+        ui = v8[0]; vi = v8[1]; ki = v8[2]; wi = v8[3];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) g[c] = grads[c * np + i];
+        for (int c = 0; c < 4; ++c) lgi[c] = v8[4 + c];
+    } else {
+        ui = mac[np + i]; vi = mac[2 * np + i]; ki = kk[i]; wi = ww[i]; nti = nut[i];
+        f1i = f1a[i];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) lgi[c] = grads[(8 + c) * np + i];
+        for (int c = 0; c < 4; ++c) lgi[c] = grads[(8 + c) * np + i];
+    }
+    const T di = G.wdist[i];
+    T SS, dv, kw;
+    if (packed && !NONORTH) {  // the grad kernel stored the invariants alone
+        SS = grads[i];
+        dv = grads[np + i];
+        kw = grads[2 * np + i];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) g[c] = grads[c * np + i];
+        sst_invariants(g, SS, dv, kw);
+    }
     SstFace<T> F[4];
     int nbs[4];
     bool has[4];
@@ -1201,23 +1305,32 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 5 : 1)
         f.rox = R[2 * m]; f.roy = R[2 * m + 1];
         f.dinv = DI[m];
         if (nb >= 0) {
-            f.u = mac[np + nb]; f.v = mac[2 * np + nb]; f.k = kk[nb]; f.w = ww[nb];
             f.rnx = RN[2 * m]; f.rny = RN[2 * m + 1];
+            if (packed) {
+                T v8[8];
+                sst_load_rec(rec8, rec2, nb, v8, f.f1, f.nut);
+                f.u = v8[0]; f.v = v8[1]; f.k = v8[2]; f.w = v8[3];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) f.lg[c] = grads[(8 + c) * np + nb];
+                for (int c = 0; c < 4; ++c) f.lg[c] = v8[4 + c];
+            } else {
+                f.u = mac[np + nb]; f.v = mac[2 * np + nb]; f.k = kk[nb]; f.w = ww[nb];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) f.lg[c] = grads[(8 + c) * np + nb];
+                f.f1 = f1a[nb];
+                f.nut = nut[nb];
+            }
             if (NONORTH && (P.variant & 2)) {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) f.gn[c] = grads[(4 + c) * np + nb];
             }
-            f.f1 = f1a[nb];
-            f.nut = nut[nb];
         } else {
             sst_bvals(G, -nb - 1, nu, ui, vi, ki, wi, di, f.u, f.v, f.k, f.w);
         }
     }
     T kn, wn, ntn, tnew;
     const T dt_i = cell_dt(G, P, i);
-    sst_cell_update<T, NONORTH>(P, dt_i, ui, vi, ki, wi, nti, di, g, lgi, f1a[i], F, kn, wn, ntn, tnew);
+    sst_cell_update<T, NONORTH>(P, dt_i, ui, vi, ki, wi, nti, di, g, SS, dv, kw, lgi, f1i, F, kn, wn, ntn,
+                                tnew);
     k_out[i] = kn;
     w_out[i] = wn;
     nut_out[i] = ntn;
@@ -1349,6 +1462,55 @@ __global__ void k_scatter_state(T *__restrict__ f, T *__restrict__ mac, T *__res
     store9(frel, np, i, d);
 }
 
+// Cell lists of one instance (halo exchange of a partitioned mesh): map[j] = the internal id
+// of input cell cells[j] of the instance (amap: input id -> internal id, from the instance's
+// first cell).
+__global__ void k_cell_map(const int *__restrict__ amap, const int *__restrict__ cells, int n,
+                           int *__restrict__ map) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) map[j] = amap[cells[j]];
+}
+
+// out_f[j][9] = f of cell map[j] (absolute: deviation + w_alpha rho0); k, omega, nu_t of the
+// current ping-pong buffers into out_t[3][n] when kk is given.
+template <class T>
+__global__ void k_get_cells(const T *__restrict__ f, const T *__restrict__ kk, const T *__restrict__ ww,
+                            const T *__restrict__ nut, const int *__restrict__ map, int n, double rho0,
+                            size_t np, double *__restrict__ out_f, double *__restrict__ out_t) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int i = map[j];
+    for (int a = 0; a < kQ; ++a) {
+        const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        out_f[static_cast<size_t>(j) * kQ + a] = value_of(f[a * np + i]) + wa * rho0;
+    }
+    if (kk != nullptr) {
+        out_t[j] = value_of(kk[i]);
+        out_t[n + j] = value_of(ww[i]);
+        out_t[2 * n + j] = value_of(nut[i]);
+    }
+}
+
+// k, omega, nu_t of cell map[j] from in[3][n] (into the current ping-pong buffers).
+template <class T>
+__global__ void k_set_turb(T *__restrict__ kk, T *__restrict__ ww, T *__restrict__ nut,
+                           const int *__restrict__ map, int n, const double *__restrict__ in) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int i = map[j];
+    kk[i] = T(in[j]);
+    ww[i] = T(in[n + j]);
+    nut[i] = T(in[2 * n + j]);
+}
+
+// Wall distance of cell map[j] from in[j].
+template <class T>
+__global__ void k_set_wdist(T *__restrict__ wdist, const int *__restrict__ map, int n,
+                            const double *__restrict__ in) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) wdist[map[j]] = T(in[j]);
+}
+
 // Output fields[q][j] for the fields q (rho, u, v, k, omega, nu_t) selected by mask bit q.
 template <class T>
 __global__ void k_gather_fields_map(const T *__restrict__ mac, const T *__restrict__ kk,
@@ -1462,17 +1624,16 @@ struct fvlbm_handle {
         int *d_inst_blk0 = nullptr;
         unsigned *d_adj = nullptr;
     } hs[2];                // [0]: 256-cell blocks, [1]: 128-cell blocks
-    struct FvSet {          // work items of the face-value fused kernels (configs 3 and 4)
+    struct FvSet {          // work items of the face-value fused kernel (config 3)
         bool ok = false;
         int nitem = 0, n_split = 0;
-        int grid_p = 0;     // CTAs of the persistent form (SMs x resident CTAs, <= nitem)
         int4 *d_hdr = nullptr;
         int *d_r1 = nullptr, *d_halo = nullptr, *d_inst_item0 = nullptr;
         uint4 *d_adj = nullptr;
     } fv;
     bool fused = false;     // fused kernels available (IMEX scheme, kernel_path 0 or 2)
-    int config = 2;         // 0: fused 256, 1: fused 128, 2: two-pass, 3: face-value fused,
-                            // 4: face-value fused, persistent (see fvlbm_autotune)
+    int config = 2;         // 0: fused 256, 1: fused 128, 2: two-pass, 3: face-value fused
+                            // (see fvlbm_autotune)
     int scheme = 0;         // 0: IMEX Runge-Kutta; 1: explicit Euler (comparison scheme)
     int kernel_path = 0;    // as requested at create (fvlbm_params.kernel_path)
     bool limit_f = false;   // an instance uses the limiter variant (two-pass kernels only)
@@ -1495,6 +1656,7 @@ struct fvlbm_handle {
     int *d_err = nullptr;   // device error flag (a staging wait gave up)
     long long wait_first = kWaitLimit;  // polls of the fused kernels' first staging wait
     void *gq = nullptr;     // fused path: node positions minus centroid [8 np]
+    void *geo16 = nullptr;  // face-value path: per cell q[8] then least-squares W[8] [np][16]
     void *dvec = nullptr;   // fused path: neighbour-centroid offsets d_m [8 np]
     InstParam *d_ip = nullptr;
     void *sn = nullptr, *lsq = nullptr, *rown = nullptr, *rnbr = nullptr, *dinv = nullptr;
@@ -1505,6 +1667,7 @@ struct fvlbm_handle {
     void *dtc = nullptr;    // local time stepping: dt of each cell (NULL: every instance global)
     void *kk[2] = {nullptr, nullptr}, *ww[2] = {nullptr, nullptr}, *nut[2] = {nullptr, nullptr};
     void *sgrad = nullptr, *f1 = nullptr;
+    void *sst_rec8 = nullptr, *sst_rec2 = nullptr;  // fused path: packed SST records [np][8], [np][2]
     int turb = 0;  // which of the k/omega/nu_t ping-pong buffers is current
     double *d_partial = nullptr, *d_inst_sums = nullptr, *d_io = nullptr;
     size_t io_bytes = 0;
@@ -1697,7 +1860,8 @@ void enqueue_fused(fvlbm_handle *h, bool stats, const fvlbm_handle::HaloSet &S) 
     }
 }
 
-// The three stages in the face-value form (config 3).
+// The three stages in the face-value form (config 3): stage 1 reads f^n and writes f^(2) in
+// cell-major rows into s1, stage 2 reads them and writes f^(3) likewise into s0.
 template <class T>
 void enqueue_fused_fv(fvlbm_handle *h, bool stats) {
     Geo<T> G = geo_of<T>(h);
@@ -1706,60 +1870,25 @@ void enqueue_fused_fv(fvlbm_handle *h, bool stats) {
     T *B = static_cast<T *>(h->bacc), *C = static_cast<T *>(h->cacc);
     T *tau = static_cast<T *>(h->tau), *mac = static_cast<T *>(h->mac);
     const FvItems W{h->fv.d_hdr, h->fv.d_r1, h->fv.d_halo, h->fv.d_adj, h->d_err, h->wait_first};
-    const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
+    const T *geo = static_cast<const T *>(h->geo16);
     const dim3 fg(h->fv.nitem), fb(kFvThreads);
     const size_t sm = FvSmem<T>::bytes;
-    // stage 1 stages f^n and relaxes it on chip; no f^(1) array is kept between steps
     launch(h, K_FUSED1, "fused_stage1", [&] {
-        k_fused_fv<T, 1, false><<<fg, fb, sm, s>>>(fn, s1, fn, B, C, tau, mac, nullptr, G, W, nullptr, CG);
+        k_fused_fv<T, 1, false><<<fg, fb, sm, s>>>(fn, s1, fn, B, C, tau, mac, nullptr, G, W, geo);
     });
     launch(h, K_FUSED2, "fused_stage2", [&] {
-        k_fused_fv<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, W, nullptr, CG);
+        k_fused_fv<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, W, geo);
     });
     if (stats) {
         launch(h, K_FUSED3, "fused_stage3", [&] {
-            k_fused_fv<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, W, nullptr,
-                                                      CG);
+            k_fused_fv<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, W, geo);
         });
         launch(h, K_REDUCE, "reduce", [&] {
             k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->fv.d_inst_item0, h->d_inst_sums);
         });
     } else {
         launch(h, K_FUSED3, "fused_stage3", [&] {
-            k_fused_fv<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, W, nullptr, CG);
-        });
-    }
-}
-
-// The three stages in the persistent face-value form (config 4).
-template <class T>
-void enqueue_fused_fvp(fvlbm_handle *h, bool stats) {
-    Geo<T> G = geo_of<T>(h);
-    cudaStream_t s = h->stream;
-    T *fn = static_cast<T *>(h->fn), *s0 = static_cast<T *>(h->s0), *s1 = static_cast<T *>(h->s1);
-    T *B = static_cast<T *>(h->bacc), *C = static_cast<T *>(h->cacc);
-    T *tau = static_cast<T *>(h->tau), *mac = static_cast<T *>(h->mac);
-    const FvItems W{h->fv.d_hdr, h->fv.d_r1, h->fv.d_halo, h->fv.d_adj, h->d_err, h->wait_first};
-    const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
-    const int ni = h->fv.nitem;
-    const dim3 fg(h->fv.grid_p), fb(kFvThreads);
-    const size_t sm = FvpSmem<T>::bytes;
-    launch(h, K_FUSED1, "fused_stage1", [&] {
-        k_fused_fvp<T, 1, false><<<fg, fb, sm, s>>>(fn, s1, fn, B, C, tau, mac, nullptr, G, W, CG, ni);
-    });
-    launch(h, K_FUSED2, "fused_stage2", [&] {
-        k_fused_fvp<T, 2, false><<<fg, fb, sm, s>>>(s1, s0, fn, B, C, tau, mac, nullptr, G, W, CG, ni);
-    });
-    if (stats) {
-        launch(h, K_FUSED3, "fused_stage3", [&] {
-            k_fused_fvp<T, 3, true><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, h->d_partial, G, W, CG, ni);
-        });
-        launch(h, K_REDUCE, "reduce", [&] {
-            k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->fv.d_inst_item0, h->d_inst_sums);
-        });
-    } else {
-        launch(h, K_FUSED3, "fused_stage3", [&] {
-            k_fused_fvp<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, W, CG, ni);
+            k_fused_fv<T, 3, false><<<fg, fb, sm, s>>>(s0, s1, fn, B, C, tau, mac, nullptr, G, W, geo);
         });
     }
 }
@@ -1792,19 +1921,21 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
         const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
         if constexpr (kHasFused<T>) {
             if (h->config != 2) {  // compact geometry, and stage 1's f^(1) with the new tau
+                T *r8 = static_cast<T *>(h->sst_rec8), *r2 = static_cast<T *>(h->sst_rec2);
                 launch(h, K_SST_GRAD, "sst_grad", [&] {
-                    k_sst_grad<T, true><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG);
+                    k_sst_grad<T, true><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG, nc, r8, r2,
+                                                               !h->nonorth);
                 });
                 launch(h, K_SST_UPDATE, "sst_update", [&] {
                     // the face-value stages relax f^n themselves; the other fused form reads
                     // stage 1's f^(1), relaxed here with the new tau
-                    T *fr = h->config >= 3 ? nullptr : static_cast<T *>(h->frel);
+                    T *fr = h->config == 3 ? nullptr : static_cast<T *>(h->frel);
                     if (h->nonorth)
                         k_sst_update<T, true, true><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn,
-                                                                           tau, G, fn, fr, CG);
+                                                                           tau, G, fn, fr, CG, r8, r2);
                     else
                         k_sst_update<T, true, false><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn,
-                                                                            tau, G, fn, fr, CG);
+                                                                            tau, G, fn, fr, CG, r8, r2);
                 });
             }
         }
@@ -1891,10 +2022,6 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
     if constexpr (kHasFused<T>) {
         if (h->config == 3) {
             enqueue_fused_fv<T>(h, stats);
-            return;
-        }
-        if (h->config == 4) {
-            enqueue_fused_fvp<T>(h, stats);
             return;
         }
         if (h->config == 0) {
@@ -2107,7 +2234,7 @@ int build_fv_items(fvlbm_handle *h, const std::vector<int> &nbr, const std::vect
                 if (v >= 0 && local[v] < 0) { local[v] = next++; ring2.push_back(v); }
             }
         const int E = next, NG = cnt + static_cast<int>(ring1.size());
-        const bool fit = E <= kFvEcap && NG <= kFvGcap && static_cast<int>(ring1.size()) <= kFvR1cap;
+        const bool fit = E <= kFvEcap && NG <= kFvGcap;
         if (fit && commit) {
             hdr.push_back(make_int4(base, cnt, static_cast<int>(halo.size()), static_cast<int>(adj.size())));
             r1n.push_back(static_cast<int>(ring1.size()));
@@ -2183,23 +2310,6 @@ int build_fv_items(fvlbm_handle *h, const std::vector<int> &nbr, const std::vect
                             static_cast<int>(FvSmem<T>::bytes)));
     CK(cudaFuncSetAttribute(k_fused_fv<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             static_cast<int>(FvSmem<T>::bytes)));
-    const int pb = static_cast<int>(FvpSmem<T>::bytes);
-    CK(cudaFuncSetAttribute(k_fused_fvp<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb));
-    CK(cudaFuncSetAttribute(k_fused_fvp<T, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb));
-    CK(cudaFuncSetAttribute(k_fused_fvp<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb));
-    CK(cudaFuncSetAttribute(k_fused_fvp<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb));
-    {  // persistent grid: every SM times the CTAs of the tightest stage kernel that fit on it
-        int dev = 0, sms = 0, per = 1 << 30, occ = 0;
-        CK(cudaGetDevice(&dev));
-        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_fvp<T, 1, false>, kFvThreads, pb));
-        per = std::min(per, occ);
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_fvp<T, 2, false>, kFvThreads, pb));
-        per = std::min(per, occ);
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_fvp<T, 3, true>, kFvThreads, pb));
-        per = std::min(per, occ);
-        h->fv.grid_p = std::max(1, std::min(static_cast<int>(hdr.size()) - 1, sms * std::max(per, 1)));
-    }
     h->fv.nitem = nitem;
     h->fv.n_split = n_split;
     h->fv.ok = true;
@@ -2235,6 +2345,8 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
     }
     if (h->sst) {
         if ((rc = dalloc(h, &h->sgrad, 12 * np * ts))) return rc;
+        if ((rc = dalloc(h, &h->sst_rec8, 8 * np * ts))) return rc;
+        if ((rc = dalloc(h, &h->sst_rec2, 2 * np * ts))) return rc;
         if ((rc = dalloc(h, &h->f1, np * ts))) return rc;
     }
     // geometry, concatenated over instances with neighbour / boundary ids offset
@@ -2346,9 +2458,17 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
             if ((rc = build_halos<T>(h, h->hs[0], 256, nbr, back, nface, inst_tile0))) return rc;
             if ((rc = build_halos<T>(h, h->hs[1], 128, nbr, back, nface, inst_tile0))) return rc;
             if ((rc = build_fv_items<T>(h, nbr, back, sn, inst_tile0))) return rc;
+            if (h->fv.ok) {  // cell-major geometry of the face-value kernels (64 B per cell)
+                std::vector<double> g16(16 * np);
+                for (size_t k = 0; k < np; ++k)
+                    for (int c = 0; c < 8; ++c) {
+                        g16[16 * k + c] = gq[c * np + k];
+                        g16[16 * k + 8 + c] = lsq[c * np + k];
+                    }
+                if ((rc = upload_as<T>(h, &h->geo16, g16))) return rc;
+            }
             h->config = h->hs[0].ok ? 0 : (h->hs[1].ok ? 1 : 2);
             if (h->fv.ok && (h->kernel_path == 2 || h->config == 2)) h->config = 3;
-            if (h->fv.ok && h->kernel_path == 3) h->config = 4;
             if (h->config == 2) h->fused = false;
         }
     }
@@ -2451,7 +2571,7 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
     bool periodic_inexact = false;
     for (int q = 0; q < n; ++q) periodic_inexact |= !(P[q]->periodic_gap <= 1e-12);
     h->kernel_path = params[0].kernel_path;
-    if (h->kernel_path < 0 || h->kernel_path > 3) return FVLBM_ERR_BAD_PARAM;
+    if (h->kernel_path < 0 || h->kernel_path > 2) return FVLBM_ERR_BAD_PARAM;
     h->fused = h->kernel_path != 1 && h->scheme == 0 && prec != FVLBM_FP64_TANGENT &&
                !h->limit_f && !h->per_stage && !periodic_inexact;
     h->ninst = n;
@@ -2634,7 +2754,7 @@ int async_slot(fvlbm_handle *h, double **buf, size_t *cap, size_t bytes) {
 // (tangent handles), dalpha the derivative of the free-stream angle in radians; fsrc (may be
 // NULL: the current state) the distributions they are taken from.
 int forces_impl(fvlbm_handle *h, int instance, double dalpha, double *out, double *dout, double *cp,
-                const void *fsrc = nullptr) {
+                const void *fsrc = nullptr, double *fxy = nullptr) {
     if (!h || instance < 0 || instance >= h->ninst || !out) return FVLBM_ERR_BAD_PARAM;
     CK(cudaSetDevice(h->device));
     const InstInfo &I = h->inst[instance];
@@ -2657,12 +2777,18 @@ int forces_impl(fvlbm_handle *h, int instance, double dalpha, double *out, doubl
     double fx = 0, fy = 0, dfx = 0, dfy = 0;
     if (cp)
         for (int b = 0; b < I.n_bedges_in; ++b) cp[b] = 0.0;
+    if (fxy)
+        for (int b = 0; b < 2 * I.n_bedges_in; ++b) fxy[b] = 0.0;
     for (int b = 0; b < nbi; ++b) {
         fx += host[b];
         fy += host[nbi + b];
         dfx += host[3 * nbi + b];
         dfy += host[4 * nbi + b];
         if (cp) cp[I.bedge_of[b]] = host[2 * nbi + b];
+        if (fxy) {
+            fxy[2 * I.bedge_of[b]] = host[b];
+            fxy[2 * I.bedge_of[b] + 1] = host[nbi + b];
+        }
     }
     const double q = 0.5 * I.rho0 * I.uref * I.uref;
     const double al = I.alpha_deg * M_PI / 180.0;
@@ -2850,6 +2976,126 @@ int fvlbm_get_fields(fvlbm_handle *h, int instance, double *rho, double *u, doub
             CK(cudaMemcpyAsync(dst[q], h->d_io + q * n, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return FVLBM_OK;
+}
+
+// ---- cell lists of one instance (halo exchange of a partitioned mesh)
+// Stages the list in the I/O buffer and maps it to internal ids: d_map receives them, d_vals
+// the first byte after them (vals_bytes of room).  BAD_PARAM for an id outside the instance.
+static int stage_cells(fvlbm_handle *h, int instance, int n, const int *cells, size_t vals_bytes,
+                int **d_map, char **d_vals) {
+    const InstInfo &I = h->inst[instance];
+    for (int j = 0; j < n; ++j)
+        if (cells[j] < 0 || cells[j] >= I.nc) return FVLBM_ERR_BAD_PARAM;
+    const size_t ids = (2 * sizeof(int) * static_cast<size_t>(n) + 15) / 16 * 16;
+    int rc = io_buffer(h, ids + vals_bytes);
+    if (rc) return rc;
+    int *d_cells = reinterpret_cast<int *>(h->d_io);
+    *d_map = d_cells + n;
+    *d_vals = reinterpret_cast<char *>(h->d_io) + ids;
+    CK(cudaMemcpyAsync(d_cells, cells, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+    k_cell_map<<<(n + 255) / 256, 256, 0, h->stream>>>(h->d_all_map + perm_offset(h, instance), d_cells, n,
+                                                       *d_map);
+    CK(cudaGetLastError());
+    return FVLBM_OK;
+}
+
+int fvlbm_get_cells(fvlbm_handle *h, int instance, int n, const int *cells, double *f, double *k,
+                    double *omega, double *nut) {
+    if (!h || instance < 0 || instance >= h->ninst || n < 0 || (n > 0 && !cells)) return FVLBM_ERR_BAD_PARAM;
+    if (n == 0) return FVLBM_OK;
+    CK(cudaSetDevice(h->device));
+    const bool turb = k || omega || nut;
+    const size_t nf = static_cast<size_t>(n) * kQ, nt = 3 * static_cast<size_t>(n);
+    int *d_map = nullptr;
+    char *d_vals = nullptr;
+    int rc = stage_cells(h, instance, n, cells, sizeof(double) * (nf + nt), &d_map, &d_vals);
+    if (rc) return rc;
+    double *d_f = reinterpret_cast<double *>(d_vals), *d_t = d_f + nf;
+    const InstInfo &I = h->inst[instance];
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        const int c = h->turb;
+        k_get_cells<T><<<(n + 255) / 256, 256, 0, h->stream>>>(
+            static_cast<const T *>(h->fn), turb ? static_cast<const T *>(h->kk[c]) : nullptr,
+            static_cast<const T *>(h->ww[c]), static_cast<const T *>(h->nut[c]), d_map, n, I.rho0, h->np,
+            d_f, d_t);
+    });
+    CK(cudaGetLastError());
+    std::vector<double> t(turb ? nt : 0);
+    if (f) CK(cudaMemcpyAsync(f, d_f, sizeof(double) * nf, cudaMemcpyDeviceToHost, h->stream));
+    if (turb) CK(cudaMemcpyAsync(t.data(), d_t, sizeof(double) * nt, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int j = 0; turb && j < n; ++j) {
+        if (k) k[j] = t[j];
+        if (omega) omega[j] = t[n + j];
+        if (nut) nut[j] = t[2 * static_cast<size_t>(n) + j];
+    }
+    return FVLBM_OK;
+}
+
+int fvlbm_set_cells(fvlbm_handle *h, int instance, int n, const int *cells, const double *f,
+                    const double *k, const double *omega, const double *nut) {
+    if (!h || instance < 0 || instance >= h->ninst || n < 0 || (n > 0 && !cells)) return FVLBM_ERR_BAD_PARAM;
+    const bool turb = k || omega || nut;
+    if (turb && !(k && omega && nut)) return FVLBM_ERR_BAD_PARAM;
+    if (n == 0) return FVLBM_OK;
+    CK(cudaSetDevice(h->device));
+    const size_t nf = static_cast<size_t>(n) * kQ, nt = 3 * static_cast<size_t>(n);
+    int *d_map = nullptr;
+    char *d_vals = nullptr;
+    int rc = stage_cells(h, instance, n, cells, sizeof(double) * (nf + nt), &d_map, &d_vals);
+    if (rc) return rc;
+    double *d_f = reinterpret_cast<double *>(d_vals), *d_t = d_f + nf;
+    if (f) CK(cudaMemcpyAsync(d_f, f, sizeof(double) * nf, cudaMemcpyHostToDevice, h->stream));
+    if (turb) {
+        std::vector<double> t(nt);
+        std::copy(k, k + n, t.begin());
+        std::copy(omega, omega + n, t.begin() + n);
+        std::copy(nut, nut + n, t.begin() + 2 * static_cast<size_t>(n));
+        CK(cudaMemcpyAsync(d_t, t.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));  // t is a local buffer
+    }
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        const int c = h->turb;
+        if (f)  // f^n, the macros and f^(1) of the coming step, as fvlbm_set_f
+            k_scatter_state<T, double><<<(n + 255) / 256, 256, 0, h->stream>>>(
+                static_cast<T *>(h->fn), static_cast<T *>(h->mac), static_cast<T *>(h->frel),
+                static_cast<const T *>(h->tau), d_map, n, geo_of<T>(h), d_f);
+        if (turb)
+            k_set_turb<T><<<(n + 255) / 256, 256, 0, h->stream>>>(static_cast<T *>(h->kk[c]),
+                                                                 static_cast<T *>(h->ww[c]),
+                                                                 static_cast<T *>(h->nut[c]), d_map, n, d_t);
+    });
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return FVLBM_OK;
+}
+
+int fvlbm_set_wall_distance(fvlbm_handle *h, int instance, const double *d) {
+    if (!h || instance < 0 || instance >= h->ninst || !d) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    const InstInfo &I = h->inst[instance];
+    for (int j = 0; j < I.nc; ++j)
+        if (!(d[j] > 0.0)) return FVLBM_ERR_BAD_PARAM;
+    int rc = io_buffer(h, sizeof(double) * std::max(I.nc, 1));
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(h->d_io, d, sizeof(double) * I.nc, cudaMemcpyHostToDevice, h->stream));
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        k_set_wdist<T><<<(I.nc + 255) / 256, 256, 0, h->stream>>>(static_cast<T *>(h->wdist),
+                                                                  h->d_all_map + perm_offset(h, instance),
+                                                                  I.nc, h->d_io);
+    });
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
+    return FVLBM_OK;
+}
+
+int fvlbm_forces_edges(fvlbm_handle *h, int instance, double *fxy) {
+    if (!fxy) return FVLBM_ERR_BAD_PARAM;
+    double out[4];
+    return forces_impl(h, instance, 0.0, out, nullptr, nullptr, nullptr, fxy);
 }
 
 int fvlbm_set_f_async(fvlbm_handle *h, int instance, const double *f) {
@@ -3201,7 +3447,7 @@ int fvlbm_autotune(fvlbm_handle *h, int trial_steps, int *chosen, double *ms_per
     if (!h || trial_steps <= 0) return FVLBM_ERR_BAD_PARAM;
     CK(cudaSetDevice(h->device));
     if (ms_per_step)
-        for (int c = 0; c < 5; ++c) ms_per_step[c] = -1.0;
+        for (int c = 0; c < 4; ++c) ms_per_step[c] = -1.0;
     if (h->scheme != 0 || (!h->hs[0].ok && !h->hs[1].ok && !h->fv.ok)) {  // nothing to choose
         if (chosen) *chosen = h->config;
         return FVLBM_OK;
@@ -3231,9 +3477,9 @@ int fvlbm_autotune(fvlbm_handle *h, int trial_steps, int *chosen, double *ms_per
     double best = 1e300;
     int best_c = h->config;
     cudaError_t err = cudaSuccess;
-    for (int c = 0; c < 5 && err == cudaSuccess; ++c) {
+    for (int c = 0; c < 4 && err == cudaSuccess; ++c) {
         if (c < 2 && !h->hs[c].ok) continue;
-        if (c >= 3 && !h->fv.ok) continue;
+        if (c == 3 && !h->fv.ok) continue;
         h->config = c;
         for (int k = 0; k < 2; ++k) enqueue(h, false);  // warm-up
         cudaEventRecord(e0, h->stream);
@@ -3319,6 +3565,12 @@ int fvlbm_load_state(fvlbm_handle *h, const void *buf, long long bytes) {
         CK(cudaMemcpyAsync(e.first, src, e.second, cudaMemcpyHostToDevice, h->stream));
         src += e.second;
     }
+    // a blob saved under the face-value configuration holds no f^(1) of the coming step: the
+    // other fused configurations relax it from f^n again (bitwise what they would have stored)
+    if (h->config == 0 || h->config == 1)
+        dispatch(h->precision, [&](auto z_) {
+            if constexpr (kHasFused<decltype(z_)>) relax_all<decltype(z_)>(h);
+        });
     CK(cudaStreamSynchronize(h->stream));
     h->steps = hd.steps;
     h->turb = hd.turb;

@@ -70,7 +70,9 @@ EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "
            "fvlbm_set_adjoint_budget", "fvlbm_state_bytes", "fvlbm_save_state",
            "fvlbm_load_state", "fvlbm_set_rollback", "fvlbm_set_f_async",
            "fvlbm_get_fields_async", "fvlbm_wait", "fvlbm_get_fdev_f32", "fvlbm_set_fdev_f32_async",
-           "fvlbm_check_mesh", "fvlbm_adjoint_params", "fvlbm_set_wait_limit"]
+           "fvlbm_check_mesh", "fvlbm_adjoint_params", "fvlbm_set_wait_limit",
+           "fvlbm_get_cells", "fvlbm_set_cells", "fvlbm_set_wall_distance", "fvlbm_cell_geometry",
+           "fvlbm_forces_edges"]
 
 _lib = None
 
@@ -126,6 +128,11 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_strerror.restype = C.c_char_p
     lib.fvlbm_stats_reduce_static.argtypes = [vp] * 6 + [i, vp, vp]
     lib.fvlbm_check_mesh.argtypes = [P(fvlbm_mesh), P(fvlbm_bc), P(fvlbm_params), P(d), C.c_char_p, i]
+    lib.fvlbm_get_cells.argtypes = [vp, i, i, vp, vp, vp, vp, vp]
+    lib.fvlbm_set_cells.argtypes = [vp, i, i, vp, vp, vp, vp, vp]
+    lib.fvlbm_set_wall_distance.argtypes = [vp, i, vp]
+    lib.fvlbm_cell_geometry.argtypes = [P(fvlbm_mesh), P(fvlbm_bc), P(fvlbm_params), vp, vp]
+    lib.fvlbm_forces_edges.argtypes = [vp, i, vp]
     for name in EXPORTS:
         if name not in ("fvlbm_destroy", "fvlbm_strerror"):
             getattr(lib, name).restype = i
@@ -243,6 +250,36 @@ def fvlbm_forces(h, instance: int = 0, with_cp: bool = False) -> dict:
     return res
 
 
+def fvlbm_get_cells(h, instance: int, cells) -> tuple:
+    """(f [n, 9], k, omega, nu_t) of the listed cells (input ids of the instance)."""
+    cells = np.ascontiguousarray(cells, np.int32)
+    n = cells.shape[0]
+    f, k, w, nt = np.empty((n, Q)), np.empty(n), np.empty(n), np.empty(n)
+    _check(load().fvlbm_get_cells(h, instance, n, _p(cells), _p(f), _p(k), _p(w), _p(nt)),
+           "fvlbm_get_cells")
+    return f, k, w, nt
+
+
+def fvlbm_set_cells(h, instance: int, cells, f=None, k=None, omega=None, nut=None) -> None:
+    cells = np.ascontiguousarray(cells, np.int32)
+    arr = [None if a is None else np.ascontiguousarray(a, np.float64) for a in (f, k, omega, nut)]
+    _check(load().fvlbm_set_cells(h, instance, cells.shape[0], _p(cells), *(_p(a) for a in arr)),
+           "fvlbm_set_cells")
+
+
+def fvlbm_set_wall_distance(h, instance: int, d) -> None:
+    d = np.ascontiguousarray(d, np.float64)
+    _check(load().fvlbm_set_wall_distance(h, instance, _p(d)), "fvlbm_set_wall_distance")
+
+
+def fvlbm_forces_edges(h, instance: int = 0) -> np.ndarray:
+    """[n_bedges, 2] wall force (Fx, Fy) per boundary edge (0 off the walls)."""
+    _, nb, _ = fvlbm_info(h, instance)
+    out = np.zeros((nb, 2))
+    _check(load().fvlbm_forces_edges(h, instance, _p(out)), "fvlbm_forces_edges")
+    return out
+
+
 def fvlbm_footprint(h):
     b, lps = C.c_longlong(), C.c_int()
     _check(load().fvlbm_footprint(h, C.byref(b), C.byref(lps)), "fvlbm_footprint")
@@ -276,10 +313,10 @@ def fvlbm_autotune(h, trial_steps: int = 5):
     """Time the available kernel configurations on a snapshot and keep the fastest.
     Returns (chosen, {name: ms_per_step})."""
     chosen = C.c_int()
-    ms = np.zeros(5)
+    ms = np.zeros(4)
     _check(load().fvlbm_autotune(h, int(trial_steps), C.byref(chosen), _p(ms)), "fvlbm_autotune")
-    names = ("fused256", "fused128", "twopass", "facevalue", "facevalue_persistent")
-    return names[chosen.value], {names[k]: float(ms[k]) for k in range(5) if ms[k] >= 0}
+    names = ("fused256", "fused128", "twopass", "facevalue")
+    return names[chosen.value], {names[k]: float(ms[k]) for k in range(4) if ms[k] >= 0}
 
 
 def fvlbm_tangent_seed(h, instance: int, dbedge_val: np.ndarray | None = None,
@@ -436,6 +473,16 @@ def check_case(case, precision: int = FVLBM_FP64, kernel_path: int = 0,
     return fvlbm_check_mesh(pk.mesh, pk.bc, pk.params)
 
 
+def case_geometry(case) -> tuple[np.ndarray, np.ndarray]:
+    """(area, wall distance) per cell of ``case`` as create computes them (host only)."""
+    pk = _Pack(case, FVLBM_FP64)
+    n = case.mesh.n_cells
+    area, wd = np.empty(n), np.empty(n)
+    _check(load().fvlbm_cell_geometry(C.byref(pk.mesh), C.byref(pk.bc), C.byref(pk.params), _p(area),
+                                      _p(wd)), "fvlbm_cell_geometry")
+    return area, wd
+
+
 class Solver:
     """One handle over one case or a batch of cases (``meshgen.Case``)."""
 
@@ -472,6 +519,18 @@ class Solver:
 
     def set_f(self, f: np.ndarray, i: int = 0) -> None:
         fvlbm_set_f(self.h, i, f)
+
+    def get_cells(self, cells, i: int = 0):
+        return fvlbm_get_cells(self.h, i, cells)
+
+    def set_cells(self, cells, f=None, k=None, omega=None, nut=None, i: int = 0) -> None:
+        fvlbm_set_cells(self.h, i, cells, f, k, omega, nut)
+
+    def set_wall_distance(self, d, i: int = 0) -> None:
+        fvlbm_set_wall_distance(self.h, i, d)
+
+    def forces_edges(self, i: int = 0) -> np.ndarray:
+        return fvlbm_forces_edges(self.h, i)
 
     def fields(self, i: int = 0) -> dict:
         return fvlbm_get_fields(self.h, i)

@@ -41,7 +41,7 @@ CASES_FP64 = {
 }
 
 
-@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
+@pytest.mark.parametrize("path", [0, 1, 2], ids=["fused", "twopass", "facevalue"])
 @pytest.mark.parametrize("name", sorted(CASES_FP64))
 def test_fp64_step_parity(name, path):
     case = CASES_FP64[name]()
@@ -68,7 +68,7 @@ def test_fp64_delaunay_full_size_z5_and_z50():
         assert _rel_max(s.get_f(), o.get_f()) < 1e-10, z
 
 
-@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
+@pytest.mark.parametrize("path", [0, 1, 2], ids=["fused", "twopass", "facevalue"])
 @pytest.mark.parametrize("maker", [lambda: mg.bfs_hybrid(n_target=3000),
                                    lambda: mg.naca0012_cmesh(n_target=4000, alpha_deg=5.0)])
 def test_fp64_sst_parity(maker, path):
@@ -154,7 +154,7 @@ def test_set_f_get_f_roundtrip_and_watchdog():
     assert st["diverged"] == 1
 
 
-@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
+@pytest.mark.parametrize("path", [0, 1, 2], ids=["fused", "twopass", "facevalue"])
 def test_fp32_dev_cavity_parity(path):
     case = mg.cavity_quad(64, re=400.0)
     s = fvlbm.Solver(case, precision=FP32, device=0, kernel_path=path)
@@ -174,7 +174,7 @@ def test_fp32_dev_delaunay_full_size():
     assert _vel_l2(s.fields(), o.fields()) < 1e-4
 
 
-@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
+@pytest.mark.parametrize("path", [0, 1, 2], ids=["fused", "twopass", "facevalue"])
 @pytest.mark.parametrize("maker", [lambda: mg.bfs_hybrid(n_target=3000),
                                    lambda: mg.naca0012_cmesh(n_target=4000, alpha_deg=7.0)])
 def test_fp32_dev_sst_parity(maker, path):
@@ -189,7 +189,7 @@ def test_fp32_dev_sst_parity(maker, path):
     assert _rel_l2(fg["omega"], fo["omega"]) < 1e-3
 
 
-@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
+@pytest.mark.parametrize("path", [0, 1, 2], ids=["fused", "twopass", "facevalue"])
 def test_fp32_dev_forces_within_half_percent(path):
     """C_D and C_L each within 0.5 % of itself (the benchmark spec's bound on the force
     coefficients), at alpha = 7 degrees where both are far from zero."""
@@ -204,7 +204,7 @@ def test_fp32_dev_forces_within_half_percent(path):
     assert abs(fg["cl"] - fo["cl"]) <= 5e-3 * abs(fo["cl"])
 
 
-@pytest.mark.parametrize("path", [0, 2, 3], ids=["fused", "facevalue", "persistent"])
+@pytest.mark.parametrize("path", [0, 2], ids=["fused", "facevalue"])
 def test_fused_matches_twopass_fp64(path):
     """The fused shared-memory kernels (either form) and the two-pass kernels compute the same
     step (FP64, up to the rounding of the reconstruction offsets and the summation order)."""
@@ -228,7 +228,7 @@ def test_periodic_box_read_with_six_digits():
     case = mg.Case(rounded, nu=2e-3, cfl=0.5, rho=1.0 + 1e-3 * rng.uniform(-1, 1, n),
                    u=0.05 * rng.uniform(-1, 1, n), v=0.05 * rng.uniform(-1, 1, n))
     fused = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=0)
-    face = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=3)
+    face = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=2)
     twop = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
     o = Oracle(case)
     m0 = fused.step(1, stats=True)["mass"]
@@ -249,15 +249,14 @@ def test_periodic_box_read_with_six_digits():
 @pytest.mark.parametrize("maker", [lambda: mg.naca0012_cmesh(n_target=60000, alpha_deg=8.0, seed=3001),
                                    lambda: mg.bfs_hybrid(n_target=80000, seed=2000)],
                          ids=["naca60k", "bfs80k"])
-@pytest.mark.parametrize("path", [2, 3], ids=["facevalue", "persistent"])
-def test_fp32_long_run_within_target_of_fp64(maker, path):
+def test_fp32_long_run_within_target_of_fp64(maker):
     """Over 1,010 steps (the length the benchmark's default run reaches) the FP32 deviation path
     of the face-value kernels stays within the benchmark spec's bounds of the FP64 path: velocity
     relative L2 <= 1e-4 and C_D, C_L each within 0.5 %.  The FP64 GPU path is the reference
     here because it matches the oracle to 1e-10 per step (the parity tests above); running
     the CPU oracle itself for 1,010 steps of these meshes would take minutes."""
     case = maker()
-    a = fvlbm.Solver(case, precision=FP32, device=0, kernel_path=path)
+    a = fvlbm.Solver(case, precision=FP32, device=0, kernel_path=2)
     b = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=1)
     a.step(1010)
     b.step(1010)
@@ -268,7 +267,7 @@ def test_fp32_long_run_within_target_of_fp64(maker, path):
             assert abs(fa[key] - fb[key]) <= 5e-3 * abs(fb[key]), key
 
 
-@pytest.mark.parametrize("path", [0, 2, 3], ids=["fused", "facevalue", "persistent"])
+@pytest.mark.parametrize("path", [0, 2], ids=["fused", "facevalue"])
 def test_full_sweep_fp32_sampled_against_oracle(path):
     """The benchmark's workload and launch configuration (48 instances in one FP32 handle, fused
     kernels, graph replay): after 2 steps, sampled instances match the FP64 oracle."""
@@ -373,7 +372,7 @@ def _single_triangle(lid=0.1):
     return mg.Case(m, nu=0.01, cfl=0.4)
 
 
-@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
+@pytest.mark.parametrize("path", [0, 1, 2], ids=["fused", "twopass", "facevalue"])
 def test_single_cell_mesh(path):
     """One triangle with three wall faces (one moving): a block of 255 padding cells and one
     real cell."""
@@ -408,7 +407,7 @@ def test_autotune_restores_state_and_keeps_parity(prec):
     before = [s.get_f(i) for i in range(2)]
     om = s.fields(0)["omega"]
     chosen, times = s.autotune(3)
-    assert chosen in ("fused256", "fused128", "twopass", "facevalue", "facevalue_persistent")
+    assert chosen in ("fused256", "fused128", "twopass", "facevalue")
     assert set(times) >= {"twopass"} and all(t > 0 for t in times.values())
     for i in range(2):
         assert np.array_equal(s.get_f(i), before[i])
@@ -464,7 +463,7 @@ LOCAL_CASES = {
 }
 
 
-@pytest.mark.parametrize("path", [0, 1, 2, 3], ids=["fused", "twopass", "facevalue", "persistent"])
+@pytest.mark.parametrize("path", [0, 1, 2], ids=["fused", "twopass", "facevalue"])
 @pytest.mark.parametrize("name", sorted(LOCAL_CASES))
 def test_local_dt_parity_fp64(name, path):
     """Local time stepping: every cell's own dt in the stages, the implicit collision and the
@@ -603,17 +602,18 @@ def test_variant_sensitivity_is_bounded():
 
 
 # ----------------------------------------------------------------- checkpoint / rollback
+@pytest.mark.parametrize("path", [0, 2], ids=["fused", "facevalue"])
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
-def test_save_load_state_resumes_bitwise(prec):
+def test_save_load_state_resumes_bitwise(prec, path):
     """A state blob saved after 10 steps and loaded into a fresh handle built from the same
     cases continues bit for bit like the original (SST parity, step count and f^(1) included);
     a blob of another configuration is refused and changes nothing."""
     cases = [mg.naca0012_cmesh(n_target=3000, alpha_deg=3.0), mg.cavity_quad(20, re=400.0)]
-    a = fvlbm.Solver(cases, precision=prec, device=0)
+    a = fvlbm.Solver(cases, precision=prec, device=0, kernel_path=path)
     a.step(11)
     blob = a.save_state()
     a.step(21)
-    b = fvlbm.Solver(cases, precision=prec, device=0)
+    b = fvlbm.Solver(cases, precision=prec, device=0, kernel_path=path)
     b.load_state(blob)
     st = b.step(21, stats=True)
     assert st["steps"] == 32
@@ -628,11 +628,43 @@ def test_save_load_state_resumes_bitwise(prec):
     np.testing.assert_array_equal(other.get_f(), before)
 
 
-def test_rollback_restores_last_finite_state():
+@pytest.mark.parametrize("src,dst", [(2, 0), (0, 2), (2, 1)])
+def test_state_moves_between_kernel_configurations(src, dst):
+    """A blob saved under one kernel configuration resumes under another: the face-value
+    stages keep f^n as cell-major rows and no f^(1), the other fused stages the reverse, and
+    each rebuilds what it keeps from f^n.  FP64, so the two continuations agree to rounding;
+    set_f of one instance into a face-value handle is seen by its next step as well."""
+    cases = [mg.naca0012_cmesh(n_target=3000, alpha_deg=3.0), mg.cavity_quad(20, re=400.0)]
+    a = fvlbm.Solver(cases, precision=FP64, device=0, kernel_path=src)
+    a.step(11)
+    blob = a.save_state()
+    a.step(9)
+    b = fvlbm.Solver(cases, precision=FP64, device=0, kernel_path=dst)
+    b.step(2)                      # rows or f^(1) of a state that the blob then replaces
+    b.load_state(blob)
+    b.step(9)
+    for i in range(2):
+        assert _rel_max(b.get_f(i), a.get_f(i)) < 1e-11, i
+        assert _rel_max(b.fields(i)["nut"] + 1.0, a.fields(i)["nut"] + 1.0) < 1e-11, i
+    # set_f of the cavity alone: its next steps start from the new f^n (laminar: f alone is
+    # the state), the airfoil is untouched
+    f1 = a.get_f(1)
+    b.set_f(f1, 1)
+    ref = fvlbm.Solver(cases[1], precision=FP64, device=0, kernel_path=dst)
+    ref.set_f(f1)
+    b.step(5)
+    ref.step(5)
+    a.step(5)
+    assert _rel_max(b.get_f(1), ref.get_f()) < 1e-13
+    assert _rel_max(b.get_f(0), a.get_f(0)) < 1e-11
+
+
+@pytest.mark.parametrize("path", [0, 2], ids=["fused", "facevalue"])
+def test_rollback_restores_last_finite_state(path):
     """With rollback on, a step that produces NaN (planted on the host through set_f) returns
     DIVERGED and leaves the handle at the last finite checkpoint, from which it continues."""
     case = mg.bfs_hybrid(n_target=2000)
-    s = fvlbm.Solver(case, precision=FP32, device=0)
+    s = fvlbm.Solver(case, precision=FP32, device=0, kernel_path=path)
     s.set_rollback(5)
     assert s.step(10, stats=True)["diverged"] == 0
     good = s.get_f()
@@ -644,18 +676,19 @@ def test_rollback_restores_last_finite_state():
     assert st["diverged"] == 1 and st["steps"] == 10
     np.testing.assert_array_equal(s.get_f(), good)
     np.testing.assert_array_equal(s.fields()["omega"], om)
-    ref = fvlbm.Solver(case, precision=FP32, device=0)
+    ref = fvlbm.Solver(case, precision=FP32, device=0, kernel_path=path)
     ref.step(13)
     s.step(3)
     np.testing.assert_array_equal(s.get_f(), ref.get_f())
 
 
-def test_async_io_pipeline_matches_synchronous_calls():
+@pytest.mark.parametrize("path", [0, 2], ids=["fused", "facevalue"])
+def test_async_io_pipeline_matches_synchronous_calls(path):
     """fvlbm_set_f_async / fvlbm_get_fields_async in a pipeline (two inputs alternating, five
     calls of each kind queued on two device slots, one wait at the end) give bit for bit what
     the synchronous calls give."""
     cases = [mg.naca0012_cmesh(n_target=3000, alpha_deg=3.0), mg.cavity_quad(20, re=400.0)]
-    ref = fvlbm.Solver(cases, precision=FP32, device=0)
+    ref = fvlbm.Solver(cases, precision=FP32, device=0, kernel_path=path)
     ref.step(5)
     f0 = fvlbm.fvlbm_get_f(ref.h, -1)
     rng = np.random.default_rng(3)
@@ -667,7 +700,7 @@ def test_async_io_pipeline_matches_synchronous_calls():
         ref.step(2)
         fl = fvlbm.fvlbm_get_fields(ref.h, -1)
         want.append((fl["u"].copy(), fl["v"].copy()))
-    s = fvlbm.Solver(cases, precision=FP32, device=0)
+    s = fvlbm.Solver(cases, precision=FP32, device=0, kernel_path=path)
     s.step(5)
     lib = fvlbm.load()
     outs = [(np.empty(n), np.empty(n)) for _ in range(5)]
@@ -684,11 +717,12 @@ def test_async_io_pipeline_matches_synchronous_calls():
         np.testing.assert_array_equal(outs[j][1], want[j][1])
 
 
-def test_fp32_deviation_io_roundtrip_and_pipeline():
+@pytest.mark.parametrize("path", [0, 2], ids=["fused", "facevalue"])
+def test_fp32_deviation_io_roundtrip_and_pipeline(path):
     """The FP32 deviation format is the FP32 path's storage: get -> async set -> get is the
     identity bit for bit, and a step from it matches a step from the double interface."""
     cases = [mg.naca0012_cmesh(n_target=3000, alpha_deg=3.0), mg.cavity_quad(20, re=400.0)]
-    s = fvlbm.Solver(cases, precision=FP32, device=0)
+    s = fvlbm.Solver(cases, precision=FP32, device=0, kernel_path=path)
     s.step(7)
     lib = fvlbm.load()
     import ctypes as C
@@ -712,14 +746,15 @@ def test_fp32_deviation_io_roundtrip_and_pipeline():
     np.testing.assert_allclose(d2.astype(np.float64) + w * 1.0, s.get_f(1), rtol=0, atol=1e-15)
 
 
-def test_staging_wait_give_up_is_reported_and_cleared():
-    """The bounded staging wait of the fused kernel (kernel_path 0) reports FVLBM_ERR_TIMEOUT
-    through the device flag that a stats step reads; the flag is cleared, and with the normal
-    bound back and the saved state restored the next steps are clean and match the oracle.  No
-    fault is involved: only the first wait is shortened (to one poll); every block still waits,
-    with the full bound, for its own copies before it returns."""
+@pytest.mark.parametrize("path", [0, 2], ids=["fused", "facevalue"])
+def test_staging_wait_give_up_is_reported_and_cleared(path):
+    """The bounded staging wait of the fused kernels (both fused forms) reports
+    FVLBM_ERR_TIMEOUT through the device flag that a stats step reads; the flag is cleared, and
+    with the normal bound back and the saved state restored the next steps are clean and match
+    the oracle.  No fault is involved: only the first wait is shortened (to one poll); every
+    block still waits, with the full bound, for its own copies before it returns."""
     case = mg.naca0012_cmesh(n_target=6000, alpha_deg=4.0)
-    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=0)
+    s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=path)
     blob = s.save_state()
     fvlbm.fvlbm_set_wait_limit(s.h, 0)
     with pytest.raises(fvlbm.FvlbmError) as ei:
