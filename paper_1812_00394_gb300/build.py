@@ -52,6 +52,13 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+# Single-precision arithmetic of the kernels (double is untouched): division and square root
+# to within 2 ulp instead of correctly rounded, and denormals flushed to zero.  The FP32 path
+# stores deviations f - w rho0 of size ~1e-2 whose rounding (~1e-9) dominates these; measured
+# on the sweep, the step is 6-7 % faster and FP32 stays within 1e-4 of FP64 over 1,010 steps.
+FP32_FLAGS = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile libfvlbm.so if any source is newer than it; return its path."""
     if not force and not _stale():
@@ -69,7 +76,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         ["g++", "-O2", "-std=c++17", "-fPIC", "-fopenmp", *inc, "-c",
          os.path.join(CSRC, "fvlbm_host.cpp"), "-o", host_o],
         [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
-         *inc, "-c", os.path.join(CSRC, "fvlbm_kernels.cu"), "-o", dev_o],
+         *FP32_FLAGS, *inc, "-c", os.path.join(CSRC, "fvlbm_kernels.cu"), "-o", dev_o],
         [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          *inc, "-c", os.path.join(CSRC, "fvlbm_noalloc.cu"), "-o", na_o],
     ]
