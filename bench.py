@@ -412,7 +412,7 @@ def run_ours(args):
                                   "ms_per_step": results["f32"]["autotune"][1]},
                          "fp64": {"chosen": results["f64"]["autotune"][0],
                                   "ms_per_step": results["f64"]["autotune"][1]}},
-            "kernels": {k: {"avg_ms": v["ms"] / v["launches"], "launches": v["launches"]}
+            "kernels": {k: _kernel_line(k, v, total_cells, sst_cells, face_value, hbm)
                         for k, v in prof.items()},
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -474,6 +474,20 @@ def _ncu_traffic(kname, workload, world, face_value=False):
     if kname not in vals:
         return None, f"profiles/{fname} has no figure for {kname}"
     return float(vals[kname]), f"ncu capture committed in profiles/{fname} (kernel sources sha256 {sha[:16]}...)"
+
+
+def _kernel_line(kname, v, cells, sst_cells, face_value, hbm):
+    """Average launch time of one kernel and, where its algorithmic bytes are defined, its
+    achieved GB/s and fraction of the measured HBM peak."""
+    ms = v["ms"] / v["launches"]
+    out = {"avg_ms": ms, "launches": v["launches"]}
+    try:
+        b = _kernel_bytes(kname, "f32", cells, sst_cells, face_value)
+    except KeyError:
+        return out
+    gbs = b / (ms * 1e-3) / 1e9
+    out.update(algorithmic_bytes=b, achieved_gbs=gbs, frac=gbs / hbm)
+    return out
 
 
 def _kernel_bytes(kname, prec, cells, sst_cells, face_value=False):
