@@ -683,6 +683,95 @@ def run_adjoint_mode(args):
     return 0
 
 
+def run_config_mode(args):
+    """The per-configuration runs (not bench lines; one JSON object per run): the 64 x 64
+    cavity in FP64 over its 2,000 steps against the oracle; the 40k-triangle Delaunay cavity at
+    dt = 5 tau and 50 tau in FP32 and FP64 until the residual falls below 1e-8 (at most 20,000
+    steps), with the residual every 1,000 steps; the backward-facing step and a NACA 0012
+    C-mesh (k-omega SST) in FP32 against FP64 after the same steps.  Time per step from the
+    wall clock around graph-replayed steps (synchronised)."""
+    import torch
+    from paper_1812_00394_gb300 import fvlbm, meshgen as mg
+    torch.cuda.set_device(0)
+    FP32, FP64 = fvlbm.FVLBM_FP32_DEV, fvlbm.FVLBM_FP64
+
+    def vel(fl):
+        return np.concatenate([fl["u"], fl["v"]])
+
+    def run(case, prec, steps, every, tol=0.0):
+        s = fvlbm.Solver(case, precision=prec, device=0)
+        tuned = s.autotune(3)[0]
+        hist, done, el = [], 0, 0.0
+        while done < steps:
+            n = min(every, steps - done)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = s.step(n, stats=True)
+            el += time.perf_counter() - t0
+            done += n
+            hist.append([done, st["residual"]])
+            if st["diverged"] or (tol > 0 and st["residual"] < tol):
+                break
+        out = {"steps": done, "ms_per_step": el / done * 1e3, "residual": hist[-1][1],
+               "residual_every": hist, "diverged": int(st["diverged"]), "config": tuned}
+        return s, out
+
+    res = []
+    # configs[0]: 64 x 64 quad cavity, Re 400, FP64, 2,000 steps, against the oracle
+    from oracle import oracle as orc
+    from oracle.oracle import Oracle
+    orc.set_threads(host_cores())
+    c0 = mg.cavity_quad(64, re=400.0, seed=1)
+    s, out = run(c0, FP64, 2000, 500)
+    o = Oracle(c0)
+    o.step(2000)
+    fo, fg = o.get_f(), s.get_f()
+    out.update(name="cavity64_re400_fp64", cells=c0.mesh.n_cells,
+               fp64_vs_oracle_f_rel_max=float(np.abs(fg - fo).max() / np.abs(fo).max()),
+               oracle_residual=o.residual())
+    s.close()
+    res.append(out)
+    # configs[1]: 40k Delaunay cavity, Re 1000, dt = 5 tau and 50 tau, to residual 1e-8
+    for z in (5.0, 50.0):
+        case = mg.cavity_delaunay(re=1000.0, z=z, seed=2)
+        runs = {}
+        for prec, tag in ((FP32, "fp32"), (FP64, "fp64")):
+            s, out = run(case, prec, args.converge_steps, 1000, tol=1e-8)
+            runs[tag] = (s, out)
+        a, b = runs["fp32"][0].fields(), runs["fp64"][0].fields()
+        same = runs["fp32"][1]["steps"] == runs["fp64"][1]["steps"]
+        for tag in ("fp32", "fp64"):
+            out = runs[tag][1]
+            out.update(name=f"delaunay_re1000_z{z:g}_{tag}", cells=case.mesh.n_cells,
+                       dt_over_tau=z)
+            if same:
+                out["fp32_vs_fp64_velocity_rel_l2"] = float(np.linalg.norm(vel(a) - vel(b)) /
+                                                            np.linalg.norm(vel(b)))
+            res.append(out)
+            runs[tag][0].close()
+    # configs[2], configs[3]: SST backward-facing step and NACA 0012 C-mesh, FP32 vs FP64
+    for case, name in ((mg.bfs_hybrid(n_target=80000), "bfs80k_sst"),
+                       (mg.naca0012_cmesh(n_target=200000, alpha_deg=4.0), "naca200k_sst_a4")):
+        s32, o32 = run(case, FP32, args.sst_steps, 1000)
+        s64, o64 = run(case, FP64, args.sst_steps, 1000)
+        f32, f64 = s32.fields(), s64.fields()
+        fr32, fr64 = s32.forces(), s64.forces()
+        o32.update(name=name + "_fp32", cells=case.mesh.n_cells,
+                   fp32_vs_fp64_velocity_rel_l2=float(np.linalg.norm(vel(f32) - vel(f64)) /
+                                                      np.linalg.norm(vel(f64))),
+                   fp32_vs_fp64_nut_rel_l2=float(np.linalg.norm(f32["nut"] - f64["nut"]) /
+                                                 np.linalg.norm(f64["nut"])),
+                   fp32_vs_fp64_cd_rel=abs(fr32["cd"] - fr64["cd"]) / abs(fr64["cd"]),
+                   fp32_vs_fp64_cl_rel=abs(fr32["cl"] - fr64["cl"]) / max(abs(fr64["cl"]), 1e-30),
+                   fp64_ms_per_step=o64["ms_per_step"])
+        res.append(o32)
+        s32.close()
+        s64.close()
+    for r in res:
+        print(json.dumps(r), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -696,6 +785,11 @@ def main():
                     help="seconds the reference arm's steps may take; it samples fewer instances "
                          "to stay within it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config-mode", action="store_true",
+                    help="the per-configuration runs (cavity 64 against the oracle, the Delaunay "
+                         "cavity to residual 1e-8, the SST cases FP32 vs FP64); not a bench line")
+    ap.add_argument("--converge-steps", type=int, default=20000)
+    ap.add_argument("--sst-steps", type=int, default=2000)
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--profile-mode", action="store_true",
                     help="only build the workload and run warmup + steps (for ncu)")
@@ -715,6 +809,8 @@ def main():
         return run_reference(args)
     if args.profile_mode:
         return run_profile_mode(args)
+    if args.config_mode:
+        return run_config_mode(args)
     if args.adjoint_mode:
         return run_adjoint_mode(args)
     return run_ours(args)
