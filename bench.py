@@ -740,10 +740,12 @@ def run_config_mode(args):
             runs[tag] = (s, out)
         a, b = runs["fp32"][0].fields(), runs["fp64"][0].fields()
         same = runs["fp32"][1]["steps"] == runs["fp64"][1]["steps"]
+        import dataclasses
+        dt_cfl1 = fvlbm.check_case(dataclasses.replace(case, dt=0.0, cfl=1.0))[1]
         for tag in ("fp32", "fp64"):
             out = runs[tag][1]
             out.update(name=f"delaunay_re1000_z{z:g}_{tag}", cells=case.mesh.n_cells,
-                       dt_over_tau=z)
+                       dt_over_tau=z, dt=runs[tag][0].dt(), convective_cfl=runs[tag][0].dt() / dt_cfl1)
             if same:
                 out["fp32_vs_fp64_velocity_rel_l2"] = float(np.linalg.norm(vel(a) - vel(b)) /
                                                             np.linalg.norm(vel(b)))
@@ -788,7 +790,7 @@ def main():
     ap.add_argument("--config-mode", action="store_true",
                     help="the per-configuration runs (cavity 64 against the oracle, the Delaunay "
                          "cavity to residual 1e-8, the SST cases FP32 vs FP64); not a bench line")
-    ap.add_argument("--converge-steps", type=int, default=20000)
+    ap.add_argument("--converge-steps", type=int, default=300000)
     ap.add_argument("--sst-steps", type=int, default=2000)
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--profile-mode", action="store_true",

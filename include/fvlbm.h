@@ -101,6 +101,12 @@ typedef struct {
                                   2: fused stage kernels in the face-value form (each cell
                                   publishes its upwind face values once per face; the
                                   autotuner may still pick any fused form).
+                                  FVLBM_FP32_DEV handles run the face-value form for 0 and 2
+                                  (two-pass where its items do not fit): the 256- and
+                                  128-cell forms derive the least-squares weights on chip,
+                                  which in FP32 leaves wall cells of high aspect ratio with
+                                  few correct digits; the face-value and two-pass kernels
+                                  read weights formed in FP64 on the host.
                                   A handle with a periodic pair whose edges are translates only
                                   to the gluing tolerance (not to 1e-12 of the edge length)
                                   runs the two-pass kernels: they give both sides of the glued
@@ -309,8 +315,8 @@ int fvlbm_profile_kernels(fvlbm_handle *h, int n_steps, int max_kernels, char *n
  * state, restores the state exactly, and keeps the fastest for all later steps.  *chosen (may
  * be NULL) receives the configuration and ms_per_step[4] (may be NULL) the measured
  * milliseconds per step, -1 for configurations not
- * available (a block's halo too large for shared memory, kernel_path 1, or the explicit
- * scheme).  Allocates a temporary snapshot of the state (about 28 words per cell) and
+ * available (a block's halo too large for shared memory, kernel_path 1, the explicit
+ * scheme, or configurations 0 and 1 on FVLBM_FP32_DEV handles, see kernel_path).  Allocates a temporary snapshot of the state (about 28 words per cell) and
  * synchronises the stream.  Errors: BAD_PARAM, OOM, CUDA. */
 int fvlbm_autotune(fvlbm_handle *h, int trial_steps, int *chosen, double *ms_per_step);
 

@@ -63,6 +63,7 @@ struct FvItems {
     const uint4 *__restrict__ adj;      // per item [cells + r1] adjacency (cell-major)
     int *__restrict__ err;              // set to 1 if the bulk-copy wait gave up
     long long wait_first;               // polls of that wait (fvlbm_set_wait_limit)
+    int item0;                          // first item of this launch (CTA b takes item0 + b)
 };
 
 // Pair p: first members alpha = 1, 2, 5, 6 and their opposites 3, 4, 7, 8.
@@ -425,10 +426,11 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem_raw + FvSmem<T>::bar);
 
     const int t = threadIdx.x;
-    const int4 hd = W.hdr[blockIdx.x];
+    const int it = W.item0 + static_cast<int>(blockIdx.x);
+    const int4 hd = W.hdr[it];
     const int base = hd.x, cnt = hd.y, h0 = hd.z;
-    const int nh = W.hdr[blockIdx.x + 1].z - h0;
-    const int nr1 = W.r1[blockIdx.x];
+    const int nh = W.hdr[it + 1].z - h0;
+    const int nr1 = W.r1[it];
     const int E = cnt + nh, NG = cnt + nr1;
     const uint4 *__restrict__ adj_g = W.adj + hd.w;
     const size_t np = G.np;
@@ -587,5 +589,5 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
             st[3] = bad ? 1.0 : 0.0;
         }
     }
-    if (STATS) block_sum<4, kFvThreads>(st, partial + 4 * blockIdx.x);
+    if (STATS) block_sum<4, kFvThreads>(st, partial + 4 * it);
 }

@@ -141,6 +141,34 @@ def test_batch_equals_separate_fp64():
         assert np.array_equal(bt.fields(i)["nut"], one.fields()["nut"])
 
 
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_laminar_and_sst_groups_on_two_streams_equal_separate_handles(prec):
+    """A batch whose laminar instances precede its SST instances steps the two groups on two
+    streams (face-value stages): every instance equals its own handle bit for bit after
+    graph-replayed and eager steps, the statistics combine both groups, and after an autotune
+    (which times the two-stream step too) the state is unchanged."""
+    cases = [mg.cavity_quad(20, re=400.0), mg.cavity_quad(17, re=400.0, jitter=0.2, seed=3),
+             mg.naca0012_cmesh(n_target=3000, alpha_deg=3.0), mg.bfs_hybrid(n_target=2000)]
+    b = fvlbm.Solver(cases, precision=prec, device=0, kernel_path=2)
+    b.step(23)
+    st = b.step(3, stats=True)
+    sts = []
+    for i, c in enumerate(cases):
+        one = fvlbm.Solver(c, precision=prec, device=0, kernel_path=2)
+        one.step(23)
+        sts.append(one.step(3, stats=True))
+        np.testing.assert_array_equal(b.get_f(i), one.get_f())
+        np.testing.assert_array_equal(b.fields(i)["nut"], one.fields()["nut"])
+        one.close()
+    assert st["residual"] == max(x["residual"] for x in sts)
+    assert abs(st["mass"] - sum(x["mass"] for x in sts)) <= 1e-13 * st["mass"]
+    f_before = [b.get_f(i) for i in range(len(cases))]
+    b.autotune(2)
+    for i in range(len(cases)):
+        np.testing.assert_array_equal(b.get_f(i), f_before[i])
+    b.close()
+
+
 def test_set_f_get_f_roundtrip_and_watchdog():
     case = mg.cavity_quad(16)
     s = fvlbm.Solver(case, precision=FP64, device=0)
