@@ -355,7 +355,7 @@ __device__ __forceinline__ void fv_flux(int t, const T *q, const uint4 &wt, cons
 #pragma unroll
     for (int m = 0; m < 4; ++m)
         if (m < 3 || !tri) a2x += q[2 * m] * FV_END_Y(m) - FV_END_X(m) * q[2 * m + 1];
-    const T inv_a = a2x > T(0) ? T(2) / a2x : T(0);  // padding cells have no faces
+    const T inv_a = a2x > T(0) ? sdiv(T(2), a2x) : T(0);  // padding cells have no faces
     V ac[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) ac[p] = PV::bcast(T(0));

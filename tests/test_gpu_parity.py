@@ -275,8 +275,9 @@ def test_periodic_box_read_with_six_digits():
 
 
 @pytest.mark.parametrize("maker", [lambda: mg.naca0012_cmesh(n_target=60000, alpha_deg=8.0, seed=3001),
+                                   lambda: mg.naca0012_cmesh(n_target=200000, alpha_deg=4.0),
                                    lambda: mg.bfs_hybrid(n_target=80000, seed=2000)],
-                         ids=["naca60k", "bfs80k"])
+                         ids=["naca60k", "naca200k", "bfs80k"])
 def test_fp32_long_run_within_target_of_fp64(maker):
     """Over 1,010 steps (the length the benchmark's default run reaches) the FP32 deviation path
     of the face-value kernels stays within the benchmark spec's bounds of the FP64 path: velocity
