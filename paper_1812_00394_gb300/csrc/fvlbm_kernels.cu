@@ -1166,11 +1166,10 @@ __global__ void __launch_bounds__(kTile)
     k_sst_grad(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
                T *__restrict__ grads, T *__restrict__ f1out, Geo<T> G, CompactGeo<T> CG,
                const T *__restrict__ nut = nullptr, T *__restrict__ rec8 = nullptr,
-               T *__restrict__ rec2 = nullptr, bool inv_only = false, int tile0 = 0) {
-    const int tile = tile0 + static_cast<int>(blockIdx.x);
-    const int i = tile * kTile + threadIdx.x;
+               T *__restrict__ rec2 = nullptr, bool inv_only = false) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
-    const InstParam P = G.ip[G.tile_inst[tile]];
+    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
     if (!P.sst) return;  // laminar instance: tau stays nu / cs^2
     const T nu = ipv<T>(P.nu, P.nu_f);
     const T own[4] = {mac[np + i], mac[2 * np + i], kk[i], ww[i]};
@@ -1255,12 +1254,10 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 5 : 1)
                  const T *__restrict__ f1a, T *__restrict__ k_out, T *__restrict__ w_out,
                  T *__restrict__ nut_out, T *__restrict__ tau, Geo<T> G,
                  const T *__restrict__ fn, T *__restrict__ frel, CompactGeo<T> CG,
-                 const T *__restrict__ rec8 = nullptr, const T *__restrict__ rec2 = nullptr,
-                 int tile0 = 0) {
-    const int tile = tile0 + static_cast<int>(blockIdx.x);
-    const int i = tile * kTile + threadIdx.x;
+                 const T *__restrict__ rec8 = nullptr, const T *__restrict__ rec2 = nullptr) {
+    const int i = blockIdx.x * kTile + threadIdx.x;
     const size_t np = G.np;
-    const InstParam P = G.ip[G.tile_inst[tile]];
+    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
     if (!P.sst) return;  // laminar instance
     const T nu = ipv<T>(P.nu, P.nu_f);
     const bool packed = COMPACT && rec8 != nullptr;
@@ -1475,8 +1472,10 @@ __global__ void k_scatter_state(T *__restrict__ f, T *__restrict__ mac, T *__res
     mac[i] = r;
     mac[np + i] = u;
     mac[2 * np + i] = v;
-    relax9(d, ipv<T>(P.rho0, P.rho0_f), cell_dt(G, P, i), tau[i]);
-    store9(frel, np, i, d);
+    if (frel != nullptr) {  // f^(1) of the coming step, for the forms that stage it
+        relax9(d, ipv<T>(P.rho0, P.rho0_f), cell_dt(G, P, i), tau[i]);
+        store9(frel, np, i, d);
+    }
 }
 
 // Cell lists of one instance (halo exchange of a partitioned mesh): map[j] = the internal id
@@ -1644,7 +1643,6 @@ struct fvlbm_handle {
     struct FvSet {          // work items of the face-value fused kernel (config 3)
         bool ok = false;
         int nitem = 0, n_split = 0;
-        std::vector<int> inst_item0;  // first item of each instance (host copy)
         int4 *d_hdr = nullptr;
         int *d_r1 = nullptr, *d_halo = nullptr, *d_inst_item0 = nullptr;
         uint4 *d_adj = nullptr;
@@ -1693,15 +1691,6 @@ struct fvlbm_handle {
     // ping-pong parity 0 or 1 (laminar runs use [1] only)
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
     bool profiling = false;
-    // A batch whose laminar instances all precede its SST instances steps the two groups on
-    // two streams (face-value stages): the laminar stages need nothing from the SST kernels.
-    struct Split {
-        bool ok = false;
-        int lam_items = 0;             // items [0, lam_items) are laminar
-        int sst_tile0 = 0;             // first tile of the SST instances
-        cudaStream_t side = nullptr;   // the laminar group's stream
-        cudaEvent_t fork = nullptr, join = nullptr;
-    } split;
     std::vector<KernelTimer> timers;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
@@ -1925,50 +1914,6 @@ void enqueue_fused_fv(fvlbm_handle *h, bool stats) {
         });
 }
 
-// One step of a batch whose laminar instances precede its SST instances, face-value stages:
-// the laminar group's three stages on the side stream, concurrently with the SST group's SST
-// update and stages on the handle's stream; the two join before the statistics (Sec. 3.2:
-// the SST update only feeds the relaxation times of its own instances).
-template <class T>
-void enqueue_split(fvlbm_handle *h, bool stats) {
-    auto &S = h->split;
-    cudaStream_t s = h->stream;
-    cudaEventRecord(S.fork, s);
-    cudaStreamWaitEvent(S.side, S.fork, 0);
-    fv_stages<T>(h, stats, 0, S.lam_items, S.side);
-    {
-        Geo<T> G = geo_of<T>(h);
-        const int c = h->turb, n = 1 - h->turb;
-        T *kc = static_cast<T *>(h->kk[c]), *wc = static_cast<T *>(h->ww[c]), *nc = static_cast<T *>(h->nut[c]);
-        T *kn = static_cast<T *>(h->kk[n]), *wn = static_cast<T *>(h->ww[n]), *nn = static_cast<T *>(h->nut[n]);
-        T *sg = static_cast<T *>(h->sgrad), *f1 = static_cast<T *>(h->f1);
-        T *tau = static_cast<T *>(h->tau), *mac = static_cast<T *>(h->mac), *fn = static_cast<T *>(h->fn);
-        T *r8 = static_cast<T *>(h->sst_rec8), *r2 = static_cast<T *>(h->sst_rec2);
-        const CompactGeo<T> CG{static_cast<const T *>(h->gq), static_cast<const T *>(h->dvec)};
-        const int t0 = S.sst_tile0;
-        const dim3 grid(static_cast<unsigned>(h->ntiles - t0)), block(kTile);
-        launch(h, K_SST_GRAD, "sst_grad", [&] {
-            k_sst_grad<T, true><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG, nc, r8, r2, !h->nonorth, t0);
-        });
-        launch(h, K_SST_UPDATE, "sst_update", [&] {
-            if (h->nonorth)
-                k_sst_update<T, true, true><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn,
-                                                                   nullptr, CG, r8, r2, t0);
-            else
-                k_sst_update<T, true, false><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G,
-                                                                    fn, nullptr, CG, r8, r2, t0);
-        });
-        h->turb = n;
-    }
-    fv_stages<T>(h, stats, S.lam_items, h->fv.nitem - S.lam_items, s);
-    cudaEventRecord(S.join, S.side);
-    cudaStreamWaitEvent(s, S.join, 0);
-    if (stats)
-        launch(h, K_REDUCE, "reduce", [&] {
-            k_reduce_instances<<<h->ninst, kTile, 0, s>>>(h->d_partial, h->fv.d_inst_item0, h->d_inst_sums);
-        });
-}
-
 // Gradient of f for the two-pass kernels, with the limiter variant when an instance asks for it.
 template <class T>
 void grad_f(const fvlbm_handle *h, dim3 grid, dim3 block, cudaStream_t s, const T *f, T *g,
@@ -1987,14 +1932,6 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
     T *fn = static_cast<T *>(h->fn), *s0 = static_cast<T *>(h->s0), *s1 = static_cast<T *>(h->s1);
     T *B = static_cast<T *>(h->bacc), *C = static_cast<T *>(h->cacc);
     T *g = static_cast<T *>(h->grad), *tau = static_cast<T *>(h->tau), *mac = static_cast<T *>(h->mac);
-    if constexpr (kHasFused<T>) {
-        // laminar and SST groups on two streams (not while profiling: the per-kernel events sit
-        // on the handle's stream)
-        if (h->config == 3 && h->split.ok && h->sst && !h->profiling) {
-            enqueue_split<T>(h, stats);
-            return;
-        }
-    }
     if (h->sst) {
         const int c = h->turb, n = 1 - h->turb;
         T *kc = static_cast<T *>(h->kk[c]), *wc = static_cast<T *>(h->ww[c]);
@@ -2396,34 +2333,7 @@ int build_fv_items(fvlbm_handle *h, const std::vector<int> &nbr, const std::vect
                             static_cast<int>(FvSmem<T>::bytes)));
     h->fv.nitem = nitem;
     h->fv.n_split = n_split;
-    h->fv.inst_item0 = inst_item0;
     h->fv.ok = true;
-    return FVLBM_OK;
-}
-
-// The two-stream step of the face-value stages: possible when the batch mixes laminar and SST
-// instances, all laminar ones first, and no reading variant couples the stages to the SST
-// (per-stage SST runs the two-pass kernels anyway).
-int build_split(fvlbm_handle *h) {
-    if (!h->fv.ok || h->scheme != 0 || h->per_stage) return FVLBM_OK;
-    int first_sst = h->ninst;
-    for (int q = 0; q < h->ninst; ++q)
-        if (h->inst[q].sst) {
-            first_sst = q;
-            break;
-        }
-    if (first_sst == 0 || first_sst == h->ninst) return FVLBM_OK;  // one kind only
-    for (int q = first_sst; q < h->ninst; ++q)
-        if (!h->inst[q].sst) return FVLBM_OK;                          // not grouped
-    auto &S = h->split;
-    S.lam_items = h->fv.inst_item0[first_sst];
-    S.sst_tile0 = h->inst[first_sst].tile_off;
-    if (S.lam_items <= 0 || S.lam_items >= h->fv.nitem || S.sst_tile0 <= 0 || S.sst_tile0 >= h->ntiles)
-        return FVLBM_OK;
-    CK(cudaStreamCreateWithFlags(&S.side, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&S.fork, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&S.join, cudaEventDisableTiming));
-    S.ok = true;
     return FVLBM_OK;
 }
 
@@ -2584,7 +2494,6 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
             // 256- and 128-cell forms invert M on chip, in FP32 a few digits on y+ ~ 1 cells)
             if (h->precision == FVLBM_FP32_DEV) h->config = h->fv.ok ? 3 : 2;
             if (h->config == 2) h->fused = false;
-            if ((rc = build_split(h))) return rc;
         }
     }
     {
@@ -2635,9 +2544,6 @@ void free_all(fvlbm_handle *h) {
         if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
     for (void *p : h->allocs) cudaFree(p);
     h->allocs.clear();
-    if (h->split.side) cudaStreamDestroy(h->split.side);
-    if (h->split.fork) cudaEventDestroy(h->split.fork);
-    if (h->split.join) cudaEventDestroy(h->split.join);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -2803,6 +2709,10 @@ size_t io_cells(const fvlbm_handle *h, int instance) {
     return instance == -1 ? static_cast<size_t>(h->total_nc) : static_cast<size_t>(h->inst[instance].nc);
 }
 
+// f^(1) of the coming step is kept only for the 256- and 128-cell fused forms (configurations
+// 0, 1); a switch to them (the autotuner) or a load relaxes it again from f^n.
+void *frel_target(const fvlbm_handle *h) { return h->config == 0 || h->config == 1 ? h->frel : nullptr; }
+
 // The state from a DEVICE buffer (input cell order, [cells][9]; IN = double: absolute f,
 // float: FP32 deviations) into f^n, the macros and f^(1) of the coming step; handle's stream.
 template <class IN>
@@ -2812,7 +2722,7 @@ void scatter_state_dev(fvlbm_handle *h, int instance, const IN *src) {
     dispatch(h->precision, [&](auto z_) {
         using T = decltype(z_);
         k_scatter_state<T, IN><<<(n + 255) / 256, 256, 0, h->stream>>>(
-            static_cast<T *>(h->fn), static_cast<T *>(h->mac), static_cast<T *>(h->frel),
+            static_cast<T *>(h->fn), static_cast<T *>(h->mac), static_cast<T *>(frel_target(h)),
             static_cast<const T *>(h->tau), h->d_all_map + po, n, geo_of<T>(h), src);
     });
 }
@@ -3178,7 +3088,7 @@ int fvlbm_set_cells(fvlbm_handle *h, int instance, int n, const int *cells, cons
         const int c = h->turb;
         if (f)  // f^n, the macros and f^(1) of the coming step, as fvlbm_set_f
             k_scatter_state<T, double><<<(n + 255) / 256, 256, 0, h->stream>>>(
-                static_cast<T *>(h->fn), static_cast<T *>(h->mac), static_cast<T *>(h->frel),
+                static_cast<T *>(h->fn), static_cast<T *>(h->mac), static_cast<T *>(frel_target(h)),
                 static_cast<const T *>(h->tau), d_map, n, geo_of<T>(h), d_f);
         if (turb)
             k_set_turb<T><<<(n + 255) / 256, 256, 0, h->stream>>>(static_cast<T *>(h->kk[c]),

@@ -142,11 +142,10 @@ def test_batch_equals_separate_fp64():
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
-def test_laminar_and_sst_groups_on_two_streams_equal_separate_handles(prec):
-    """A batch whose laminar instances precede its SST instances steps the two groups on two
-    streams (face-value stages): every instance equals its own handle bit for bit after
-    graph-replayed and eager steps, the statistics combine both groups, and after an autotune
-    (which times the two-stream step too) the state is unchanged."""
+def test_mixed_batch_on_face_value_stages_equals_separate_handles(prec):
+    """A batch of laminar and SST instances on the face-value stages: every instance equals its
+    own handle bit for bit after graph-replayed and eager steps, the statistics combine all
+    instances, and an autotune leaves the state unchanged."""
     cases = [mg.cavity_quad(20, re=400.0), mg.cavity_quad(17, re=400.0, jitter=0.2, seed=3),
              mg.naca0012_cmesh(n_target=3000, alpha_deg=3.0), mg.bfs_hybrid(n_target=2000)]
     b = fvlbm.Solver(cases, precision=prec, device=0, kernel_path=2)
