@@ -202,7 +202,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "sample_cells": cells, "precision": "fp64-cpu"},
+        "config": {"workload": _workload_desc(args.workload), "instances": len(cases),
+                   "cells": sum(c.mesh.n_cells for c in cases), "sample_cells": cells,
+                   "precision": "fp64 CPU oracle (a bounded sample of the workload per step)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "host_nproc": cores,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
