@@ -275,8 +275,9 @@ def test_periodic_box_read_with_six_digits():
 
 @pytest.mark.parametrize("maker", [lambda: mg.naca0012_cmesh(n_target=60000, alpha_deg=8.0, seed=3001),
                                    lambda: mg.naca0012_cmesh(n_target=200000, alpha_deg=4.0),
-                                   lambda: mg.bfs_hybrid(n_target=80000, seed=2000)],
-                         ids=["naca60k", "naca200k", "bfs80k"])
+                                   lambda: mg.bfs_hybrid(n_target=80000, seed=2000),
+                                   lambda: mg.cavity_delaunay(re=1000.0, z=5.0, seed=2)],
+                         ids=["naca60k", "naca200k", "bfs80k", "delaunay40k_z5"])
 def test_fp32_long_run_within_target_of_fp64(maker):
     """Over 1,010 steps (the length the benchmark's default run reaches) the FP32 deviation path
     of the face-value kernels stays within the benchmark spec's bounds of the FP64 path: velocity
@@ -293,6 +294,24 @@ def test_fp32_long_run_within_target_of_fp64(maker):
     for key in ("cd", "cl"):
         if abs(fb[key]) > 1e-3:
             assert abs(fa[key] - fb[key]) <= 5e-3 * abs(fb[key]), key
+
+
+def test_cavity64_fp64_over_its_2000_steps_matches_oracle():
+    """The 64 x 64 quad cavity (Re 400, lid 0.1, seeded density noise) in FP64 over the 2,000
+    steps of its configuration: the GPU state stays within 1e-10 of the oracle's (per-step
+    rounding differences do not grow), and so does the residual."""
+    import os
+    from oracle import oracle as orc
+    orc.set_threads(os.cpu_count() or 1)   # all host cores; the results do not depend on the count
+    case = mg.cavity_quad(64, re=400.0, seed=1)
+    s = fvlbm.Solver(case, precision=FP64, device=0)
+    s.step(1999)
+    st = s.step(1, stats=True)
+    o = Oracle(case)
+    o.step(2000)
+    assert _rel_max(s.get_f(), o.get_f()) < 1e-10
+    assert abs(st["residual"] - o.residual()) <= 1e-8 * o.residual()
+    orc.set_threads(1)
 
 
 @pytest.mark.parametrize("path", [0, 2], ids=["fused", "facevalue"])
