@@ -56,7 +56,8 @@ def _stale() -> bool:
 # (double is untouched).  Measured on the sweep: the SST update 16 % faster, the FP32 error
 # against FP64 unchanged.  (Approximate division everywhere, or denormals flushed to zero,
 # did raise the error on a 200k-cell SST airfoil: to 1.2e-4 and 3.0e-5 against 1.2e-5 after
-# 1,000 steps; the stage algebra alone takes the fast quotient, see sdiv in the kernels.)
+# 1,000 steps; the stage algebra and the SST gradients take the fast quotient, see sdiv in the
+# kernels.)
 FP32_FLAGS = ["-prec-sqrt=false"]
 
 

@@ -114,12 +114,12 @@ __device__ __forceinline__ T cell_dt(const Geo<T> &G, const InstParam &P, int i)
 }
 
 // ------------------------------------------------------------------ cell algebra
-// Quotient a / b in the collision and stage algebra.  In float it is the fast form (within
-// 2 ulp instead of correctly rounded): the FP32 path stores deviations f - w rho0 whose
-// rounding (~1e-9 of values ~1e-2) dominates it, and the algebra divides several times per cell
-// and stage.  The SST keeps correctly rounded division: its far-field blending is sensitive to
-// it (measured on a 200k-cell airfoil after 1,000 steps: 1.2e-4 velocity error against FP64
-// with fast division everywhere, 1.2e-5 with it in the stage algebra only).
+// Quotient a / b in the collision and stage algebra and in the SST gradients (limiter, f1).
+// In float it is the fast form (within 2 ulp instead of correctly rounded): the FP32 path
+// stores deviations f - w rho0 whose rounding (~1e-9 of values ~1e-2) dominates it.  The SST
+// update (point-implicit destruction, f2, nu_t) keeps correctly rounded division: measured on
+// a 200k-cell airfoil after 1,000 steps, the FP32 velocity error against FP64 is 1.2e-5 either
+// way for the stage algebra and the gradients, and 1.2e-4 with the fast form in the update.
 template <class T>
 __device__ __forceinline__ T sdiv(T a, T b) {
     if constexpr (std::is_same<T, float>::value)
@@ -950,20 +950,20 @@ __device__ __forceinline__ void sst_cell_grad(T ki, T wi, T di, T nu, const bool
         if (!has[m]) continue;
         const T rx = R[2 * m], ry = R[2 * m + 1];
         const T dkf = g[4] * rx + g[5] * ry, dwf = g[6] * rx + g[7] * ry;
-        if (dkf > T(0)) pk = fmin(pk, (khi - ki) / dkf);
-        else if (dkf < T(0)) pk = fmin(pk, (klo - ki) / dkf);
-        if (dwf > T(0)) pw = fmin(pw, (whi - wi) / dwf);
-        else if (dwf < T(0)) pw = fmin(pw, (wlo - wi) / dwf);
+        if (dkf > T(0)) pk = fmin(pk, sdiv(khi - ki, dkf));
+        else if (dkf < T(0)) pk = fmin(pk, sdiv(klo - ki, dkf));
+        if (dwf > T(0)) pw = fmin(pw, sdiv(whi - wi, dwf));
+        else if (dwf < T(0)) pw = fmin(pw, sdiv(wlo - wi, dwf));
     }
     lg[0] = pk * g[4];
     lg[1] = pk * g[5];
     lg[2] = pw * g[6];
     lg[3] = pw * g[7];
-    T cd = T(2 * kSw2) / wi * (g[4] * g[6] + g[5] * g[7]);
+    T cd = sdiv(T(2 * kSw2), wi) * (g[4] * g[6] + g[5] * g[7]);
     cd = cd > T(1e-20) ? cd : T(1e-20);
-    const T a = sqrt(ki) / (T(kBstar) * wi * di);
-    const T bb = T(500) * nu / (wi * di * di);
-    const T c = T(4 * kSw2) * ki / (cd * di * di);
+    const T a = sdiv(sqrt(ki), T(kBstar) * wi * di);
+    const T bb = sdiv(T(500) * nu, wi * di * di);
+    const T c = sdiv(T(4 * kSw2) * ki, cd * di * di);
     const T arg1 = fmin(fmax(a, bb), c);
     const T a2 = arg1 * arg1;
     f1 = tanh(a2 * a2);
