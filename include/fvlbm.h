@@ -269,6 +269,22 @@ int fvlbm_cell_geometry(const fvlbm_mesh *mesh, const fvlbm_bc *bc, const fvlbm_
                         double *area, double *wdist);
 int fvlbm_forces_edges(fvlbm_handle *h, int instance, double *fxy);
 
+/* The ghost exchange on DEVICE buffers (for NCCL send / receive between GPUs, no host copy).
+ *
+ * fvlbm_set_exchange_list: registers n cells of `instance` (host array, input cell order, each
+ * in [0, n_cells), else BAD_PARAM and nothing is registered) as one list and returns its id in
+ * *list_id.  Lists live as long as the handle.  Synchronises.  Errors: BAD_PARAM, OOM, CUDA.
+ *
+ * fvlbm_pack_cells_dev: vals (DEVICE pointer, n * 12 doubles, row j for cell j of the list)
+ * receives f (9, absolute as fvlbm_get_f), k, omega, nu_t of the list's cells.
+ * fvlbm_unpack_cells_dev: the reverse, as fvlbm_set_cells with all four fields (the macros
+ * follow f).  Both are enqueued on the handle's stream and do not synchronise: vals must stay
+ * valid until that work has run, and a caller that moves vals on another stream orders it
+ * against the handle's stream.  Errors: BAD_PARAM (unknown list, NULL vals), CUDA. */
+int fvlbm_set_exchange_list(fvlbm_handle *h, int instance, int n, const int *cells, int *list_id);
+int fvlbm_pack_cells_dev(fvlbm_handle *h, int list_id, double *vals);
+int fvlbm_unpack_cells_dev(fvlbm_handle *h, int list_id, const double *vals);
+
 /* Pipelined variants of fvlbm_set_f and fvlbm_get_fields that do not synchronise, so that host
  * transfers overlap the steps (no counterpart in the paper).  Each call stages its data in one
  * of two device slots per direction (alternating), copies on a transfer stream of the handle

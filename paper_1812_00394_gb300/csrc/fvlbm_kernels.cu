@@ -89,6 +89,8 @@ __device__ __forceinline__ float ipv<float>(double, float f) {
     return f;
 }
 
+constexpr int kXRow = kQ + 3;  // doubles per cell in a ghost-exchange row: f, k, omega, nu_t
+
 template <class T>
 struct Geo {
     const int *__restrict__ nbr;   // [4 np]
@@ -1527,6 +1529,60 @@ __global__ void k_set_wdist(T *__restrict__ wdist, const int *__restrict__ map, 
     if (j < n) wdist[map[j]] = T(in[j]);
 }
 
+// Ghost exchange of a split mesh on device buffers: row j of vals (kXRow doubles) holds cell
+// map[j]'s f (absolute: deviation + w_alpha rho0), k, omega, nu_t (current buffers).
+template <class T>
+__global__ void k_pack_cells(const T *__restrict__ f, const T *__restrict__ kk, const T *__restrict__ ww,
+                             const T *__restrict__ nut, const int *__restrict__ map, int n, Geo<T> G,
+                             double *__restrict__ vals) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int i = map[j];
+    const size_t np = G.np;
+    const double rho0 = G.ip[G.tile_inst[i / kTile]].rho0;
+    double *v = vals + static_cast<size_t>(j) * kXRow;
+    for (int a = 0; a < kQ; ++a) {
+        const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        v[a] = value_of(f[a * np + i]) + wa * rho0;
+    }
+    v[9] = value_of(kk[i]);
+    v[10] = value_of(ww[i]);
+    v[11] = value_of(nut[i]);
+}
+
+// The reverse: f^n (deviation), the macros and, where kept, f^(1) of the coming step (as
+// fvlbm_set_f writes them), k, omega and nu_t of cell map[j] from row j of vals.
+template <class T>
+__global__ void k_unpack_cells(T *__restrict__ f, T *__restrict__ mac, T *__restrict__ frel,
+                               const T *__restrict__ tau, T *__restrict__ kk, T *__restrict__ ww,
+                               T *__restrict__ nut, const int *__restrict__ map, int n, Geo<T> G,
+                               const double *__restrict__ vals) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int i = map[j];
+    const size_t np = G.np;
+    const InstParam P = G.ip[G.tile_inst[i / kTile]];
+    const double *v = vals + static_cast<size_t>(j) * kXRow;
+    T d[kQ];
+    for (int a = 0; a < kQ; ++a) {
+        const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        d[a] = T(v[a] - wa * P.rho0);
+        f[a * np + i] = d[a];
+    }
+    T dr, r, u, w;
+    moments(d, ipv<T>(P.rho0, P.rho0_f), dr, r, u, w);
+    mac[i] = r;
+    mac[np + i] = u;
+    mac[2 * np + i] = w;
+    kk[i] = T(v[9]);
+    ww[i] = T(v[10]);
+    nut[i] = T(v[11]);
+    if (frel != nullptr) {
+        relax9(d, ipv<T>(P.rho0, P.rho0_f), cell_dt(G, P, i), tau[i]);
+        store9(frel, np, i, d);
+    }
+}
+
 // Output fields[q][j] for the fields q (rho, u, v, k, omega, nu_t) selected by mask bit q.
 template <class T>
 __global__ void k_gather_fields_map(const T *__restrict__ mac, const T *__restrict__ kk,
@@ -1624,6 +1680,11 @@ struct fvlbm_handle {
     long long steps = 0;
     size_t device_bytes = 0;
     std::vector<void *> allocs;
+    struct XList {           // ghost-exchange cell lists (fvlbm_set_exchange_list)
+        int instance, n;
+        int *d_map;          // internal ids
+    };
+    std::vector<XList> xlists;
     // device arrays (element type T = double or float; stored as void*)
     int *d_nbr = nullptr, *d_tile_inst = nullptr, *d_btype = nullptr, *d_bowner = nullptr;
     int *d_perm = nullptr, *d_inst_tile0 = nullptr;
@@ -3117,6 +3178,64 @@ int fvlbm_set_wall_distance(fvlbm_handle *h, int instance, const double *d) {
     });
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->stream));
+    return FVLBM_OK;
+}
+
+int fvlbm_set_exchange_list(fvlbm_handle *h, int instance, int n, const int *cells, int *list_id) {
+    if (!h || instance < 0 || instance >= h->ninst || n < 0 || (n > 0 && !cells) || !list_id)
+        return FVLBM_ERR_BAD_PARAM;
+    const InstInfo &I = h->inst[instance];
+    for (int j = 0; j < n; ++j)
+        if (cells[j] < 0 || cells[j] >= I.nc) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    fvlbm_handle::XList L{instance, n, nullptr};
+    int rc = dalloc(h, reinterpret_cast<void **>(&L.d_map), sizeof(int) * 2 * std::max(n, 1));
+    if (rc) return rc;
+    if (n > 0) {
+        int *d_cells = L.d_map + n;
+        CK(cudaMemcpyAsync(d_cells, cells, sizeof(int) * n, cudaMemcpyHostToDevice, h->stream));
+        k_cell_map<<<(n + 255) / 256, 256, 0, h->stream>>>(h->d_all_map + perm_offset(h, instance), d_cells, n,
+                                                           L.d_map);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    *list_id = static_cast<int>(h->xlists.size());
+    h->xlists.push_back(L);
+    return FVLBM_OK;
+}
+
+int fvlbm_pack_cells_dev(fvlbm_handle *h, int list_id, double *vals) {
+    if (!h || list_id < 0 || list_id >= static_cast<int>(h->xlists.size())) return FVLBM_ERR_BAD_PARAM;
+    const auto &L = h->xlists[list_id];
+    if (L.n == 0) return FVLBM_OK;
+    if (!vals) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        const int c = h->turb;
+        k_pack_cells<T><<<(L.n + 255) / 256, 256, 0, h->stream>>>(
+            static_cast<const T *>(h->fn), static_cast<const T *>(h->kk[c]), static_cast<const T *>(h->ww[c]),
+            static_cast<const T *>(h->nut[c]), L.d_map, L.n, geo_of<T>(h), vals);
+    });
+    CK(cudaGetLastError());
+    return FVLBM_OK;
+}
+
+int fvlbm_unpack_cells_dev(fvlbm_handle *h, int list_id, const double *vals) {
+    if (!h || list_id < 0 || list_id >= static_cast<int>(h->xlists.size())) return FVLBM_ERR_BAD_PARAM;
+    const auto &L = h->xlists[list_id];
+    if (L.n == 0) return FVLBM_OK;
+    if (!vals) return FVLBM_ERR_BAD_PARAM;
+    CK(cudaSetDevice(h->device));
+    dispatch(h->precision, [&](auto z_) {
+        using T = decltype(z_);
+        const int c = h->turb;
+        k_unpack_cells<T><<<(L.n + 255) / 256, 256, 0, h->stream>>>(
+            static_cast<T *>(h->fn), static_cast<T *>(h->mac), static_cast<T *>(frel_target(h)),
+            static_cast<const T *>(h->tau), static_cast<T *>(h->kk[c]), static_cast<T *>(h->ww[c]),
+            static_cast<T *>(h->nut[c]), L.d_map, L.n, geo_of<T>(h), vals);
+    });
+    CK(cudaGetLastError());
     return FVLBM_OK;
 }
 

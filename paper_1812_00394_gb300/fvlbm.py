@@ -72,7 +72,8 @@ EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "
            "fvlbm_get_fields_async", "fvlbm_wait", "fvlbm_get_fdev_f32", "fvlbm_set_fdev_f32_async",
            "fvlbm_check_mesh", "fvlbm_adjoint_params", "fvlbm_set_wait_limit",
            "fvlbm_get_cells", "fvlbm_set_cells", "fvlbm_set_wall_distance", "fvlbm_cell_geometry",
-           "fvlbm_forces_edges"]
+           "fvlbm_forces_edges", "fvlbm_set_exchange_list", "fvlbm_pack_cells_dev",
+           "fvlbm_unpack_cells_dev"]
 
 _lib = None
 
@@ -133,6 +134,9 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_set_wall_distance.argtypes = [vp, i, vp]
     lib.fvlbm_cell_geometry.argtypes = [P(fvlbm_mesh), P(fvlbm_bc), P(fvlbm_params), vp, vp]
     lib.fvlbm_forces_edges.argtypes = [vp, i, vp]
+    lib.fvlbm_set_exchange_list.argtypes = [vp, i, i, vp, P(i)]
+    lib.fvlbm_pack_cells_dev.argtypes = [vp, i, vp]
+    lib.fvlbm_unpack_cells_dev.argtypes = [vp, i, vp]
     for name in EXPORTS:
         if name not in ("fvlbm_destroy", "fvlbm_strerror"):
             getattr(lib, name).restype = i
@@ -278,6 +282,24 @@ def fvlbm_forces_edges(h, instance: int = 0) -> np.ndarray:
     out = np.zeros((nb, 2))
     _check(load().fvlbm_forces_edges(h, instance, _p(out)), "fvlbm_forces_edges")
     return out
+
+
+def fvlbm_set_exchange_list(h, instance: int, cells) -> int:
+    """Register a cell list for the device-buffer ghost exchange; returns its id."""
+    cells = np.ascontiguousarray(cells, np.int32)
+    lid = C.c_int()
+    _check(load().fvlbm_set_exchange_list(h, instance, cells.shape[0], _p(cells), C.byref(lid)),
+           "fvlbm_set_exchange_list")
+    return lid.value
+
+
+def fvlbm_pack_cells_dev(h, list_id: int, vals_ptr: int) -> None:
+    """Enqueue the packing of a list into a DEVICE buffer of n * 12 doubles (address)."""
+    _check(load().fvlbm_pack_cells_dev(h, list_id, C.c_void_p(vals_ptr)), "fvlbm_pack_cells_dev")
+
+
+def fvlbm_unpack_cells_dev(h, list_id: int, vals_ptr: int) -> None:
+    _check(load().fvlbm_unpack_cells_dev(h, list_id, C.c_void_p(vals_ptr)), "fvlbm_unpack_cells_dev")
 
 
 def fvlbm_footprint(h):
@@ -525,6 +547,15 @@ class Solver:
 
     def set_cells(self, cells, f=None, k=None, omega=None, nut=None, i: int = 0) -> None:
         fvlbm_set_cells(self.h, i, cells, f, k, omega, nut)
+
+    def set_exchange_list(self, cells, i: int = 0) -> int:
+        return fvlbm_set_exchange_list(self.h, i, cells)
+
+    def pack_cells_dev(self, list_id: int, vals_ptr: int) -> None:
+        fvlbm_pack_cells_dev(self.h, list_id, vals_ptr)
+
+    def unpack_cells_dev(self, list_id: int, vals_ptr: int) -> None:
+        fvlbm_unpack_cells_dev(self.h, list_id, vals_ptr)
 
     def set_wall_distance(self, d, i: int = 0) -> None:
         fvlbm_set_wall_distance(self.h, i, d)

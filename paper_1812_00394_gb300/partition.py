@@ -305,18 +305,42 @@ class _Combine:
                 "cl": (-fx * np.sin(al) + fy * np.cos(al)) / (q * c.lref)}
 
 
+XROW = 12  # doubles per cell in a ghost row: f (9), k, omega, nu_t
+
+
 class LocalPartitionedRun:
     """Every part in this process (one handle each, e.g. on one GPU); the ghost exchange is a
-    copy between the handles after each step."""
+    copy between the handles after each step: through host arrays, or with device_buffers=True
+    through one device buffer per (owner, receiver) pair that the handles pack and unpack with
+    their own kernels (the form a run on several GPUs moves with NCCL)."""
 
-    def __init__(self, partition: MeshPartition, make_solver: Callable):
+    def __init__(self, partition: MeshPartition, make_solver: Callable, device_buffers: bool = False):
         self.pt = partition
         self.solvers = [make_solver(P.case) for P in partition.parts]
         for P, s in zip(partition.parts, self.solvers):
             if P.wdist is not None:
                 s.set_wall_distance(P.wdist)
+        self.dev = None
+        if device_buffers:
+            import torch
+            self.dev = {}
+            for q, Q in enumerate(partition.parts):
+                for p, lids in Q.send.items():
+                    send_id = self.solvers[q].set_exchange_list(lids)
+                    recv_id = self.solvers[p].set_exchange_list(partition.parts[p].recv[q])
+                    buf = torch.empty((lids.shape[0], XROW), dtype=torch.float64, device="cuda")
+                    self.dev[(q, p)] = (send_id, recv_id, buf)
 
     def exchange(self):
+        if self.dev is not None:
+            import torch
+            for (q, p), (sid, _, buf) in self.dev.items():
+                self.solvers[q].pack_cells_dev(sid, buf.data_ptr())
+            torch.cuda.synchronize()  # the packs ran on the owners' streams
+            for (q, p), (_, rid, buf) in self.dev.items():
+                self.solvers[p].unpack_cells_dev(rid, buf.data_ptr())
+            torch.cuda.synchronize()  # the buffers are reused by the next exchange
+            return
         out = {}
         for q, Q in enumerate(self.pt.parts):
             for p, lids in Q.send.items():
@@ -383,14 +407,41 @@ class PartitionedRank:
         import torch
         return torch.as_tensor(np.ascontiguousarray(a, np.float64), device=self.device)
 
+    def _device_lists(self):
+        """On a GPU with a handle that packs on the device: the exchange lists registered once,
+        one device buffer per peer; the rows then go from kernel to NCCL to kernel."""
+        import torch
+        P = self.part
+        self._dsend = {p: (self.solver.set_exchange_list(l),
+                           torch.empty((l.shape[0], XROW), dtype=torch.float64, device=self.device))
+                       for p, l in sorted(P.send.items())}
+        self._drecv = {q: (self.solver.set_exchange_list(l),
+                           torch.empty((l.shape[0], XROW), dtype=torch.float64, device=self.device))
+                       for q, l in sorted(P.recv.items())}
+
     def exchange(self):
         if self.dist is None:
             return
         import torch
         P = self.part
+        on_device = str(self.device).startswith("cuda") and hasattr(self.solver, "pack_cells_dev")
+        if on_device:
+            if not hasattr(self, "_dsend"):
+                self._device_lists()
+            for p, (lid, buf) in self._dsend.items():
+                self.solver.pack_cells_dev(lid, buf.data_ptr())
+            torch.cuda.synchronize()  # the packs ran on the handle's stream
+            reqs = [self.dist.irecv(buf, src=q) for q, (_, buf) in self._drecv.items()]
+            reqs += [self.dist.isend(buf, dst=p) for p, (_, buf) in self._dsend.items()]
+            for r in reqs:
+                r.wait()
+            torch.cuda.synchronize()  # the transfers ran on torch's stream
+            for q, (lid, buf) in self._drecv.items():
+                self.solver.unpack_cells_dev(lid, buf.data_ptr())
+            return
         reqs, bufs = [], {}
         for q, lids in sorted(P.recv.items()):
-            bufs[q] = torch.empty((lids.shape[0], 12), dtype=torch.float64, device=self.device)
+            bufs[q] = torch.empty((lids.shape[0], XROW), dtype=torch.float64, device=self.device)
             reqs.append(self.dist.irecv(bufs[q], src=q))
         sends = []
         for p, lids in sorted(P.send.items()):

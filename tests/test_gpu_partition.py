@@ -111,3 +111,29 @@ def test_cell_list_calls_and_wall_distance():
     assert _rel(c.fields()["nut"], a.fields()["nut"]) > 1e-6
     with pytest.raises(fvlbm.FvlbmError):
         a.set_wall_distance(np.zeros(a.cells[0]))
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_device_buffer_exchange_equals_host_exchange(prec):
+    """The ghost rows moved through device buffers (fvlbm_set_exchange_list, then
+    fvlbm_pack_cells_dev / fvlbm_unpack_cells_dev on the handles' streams) give bit for bit what
+    the host path (fvlbm_get_cells / fvlbm_set_cells) gives; bad lists and ids are refused."""
+    case = _perturbed(mg.naca0012_cmesh(n_target=6000, re_c=1e4, alpha_deg=4.0), 22)
+    pt = _split(case, 3)
+    make = lambda c: fvlbm.Solver(c, precision=prec, device=0, kernel_path=2)  # noqa: E731
+    host = LocalPartitionedRun(pt, make)
+    dev = LocalPartitionedRun(pt, make, device_buffers=True)
+    host.step(6)
+    dev.step(6)
+    np.testing.assert_array_equal(dev.get_f(), host.get_f())
+    fd, fh = dev.fields(), host.fields()
+    for key in ("k", "omega", "nut"):
+        np.testing.assert_array_equal(fd[key], fh[key])
+    s = dev.solvers[0]
+    with pytest.raises(fvlbm.FvlbmError) as ei:
+        s.set_exchange_list(np.array([0, s.cells[0]], np.int32))
+    assert ei.value.code == fvlbm.FVLBM_ERR_BAD_PARAM
+    with pytest.raises(fvlbm.FvlbmError):
+        s.pack_cells_dev(10 ** 6, 0)
+    host.close()
+    dev.close()
