@@ -111,6 +111,8 @@ def make_workload(name: str):
     from paper_1812_00394_gb300 import meshgen as mg
     if name == "sweep":
         return mg.batched_sweep(seed=5)
+    if name == "sweep_small":  # the sweep's kinds in small (7 instances), for counter captures
+        return mg.batched_sweep(seed=5, n_cavity=4, n_bfs=1, n_naca=2)
     if name == "delaunay40k":
         return [mg.cavity_delaunay(re=1000.0, z=5.0, seed=2)]
     if name == "cavity64":
@@ -438,7 +440,9 @@ def _workload_desc(name):
                      "Re 100-3200, 4 SST backward-facing steps ~80k cells, 12 SST NACA0012 "
                      "C-meshes 50k-200k cells alpha 0-12 deg), CFL 0.5 each",
             "delaunay40k": "laminar lid-driven cavity Re 1000, seeded Delaunay ~40k triangles, dt = 5 tau",
-            "cavity64": "laminar lid-driven cavity Re 400, 64x64 quads, CFL 0.5"}[name]
+            "cavity64": "laminar lid-driven cavity Re 400, 64x64 quads, CFL 0.5",
+            "sweep_small": "the batched sweep's kinds in small: 4 cavities, 1 SST backward-facing "
+                           "step, 2 SST NACA0012 C-meshes"}[name]
 
 
 PROFILE_SUMMARY = {False: "k_fused_stage_fp32_sweep.md", True: "k_fused_fv_fp32_sweep.md"}
@@ -782,7 +786,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "delaunay40k", "cavity64"])
+    ap.add_argument("--workload", default="sweep",
+                    choices=["sweep", "sweep_small", "delaunay40k", "cavity64"])
     ap.add_argument("--check-steps", type=int, default=5)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=150.0,

@@ -281,6 +281,13 @@ int fvlbm_forces_edges(fvlbm_handle *h, int instance, double *fxy);
  * follow f).  Both are enqueued on the handle's stream and do not synchronise: vals must stay
  * valid until that work has run, and a caller that moves vals on another stream orders it
  * against the handle's stream.  Errors: BAD_PARAM (unknown list, NULL vals), CUDA. */
+/* FP64 arithmetic peak of `device` (the current device when < 0), measured (no counterpart in
+ * the paper): the rate of double-precision fused multiply-adds of a kernel that runs
+ * independent FMA chains on every SM and reads no memory, in TFLOP/s (2 flops per FMA), the
+ * best of three timed launches.  The roofline of the FP64 path, which the FP64 pipe bounds.
+ * Synchronises.  Errors: BAD_PARAM, OOM, CUDA. */
+int fvlbm_fp64_peak(int device, double *tflops);
+
 int fvlbm_set_exchange_list(fvlbm_handle *h, int instance, int n, const int *cells, int *list_id);
 int fvlbm_pack_cells_dev(fvlbm_handle *h, int list_id, double *vals);
 int fvlbm_unpack_cells_dev(fvlbm_handle *h, int list_id, const double *vals);

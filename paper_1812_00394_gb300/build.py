@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libfvlbm.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["fvlbm_host.cpp", "fvlbm_kernels.cu", "fvlbm_noalloc.cu"]
+SOURCES = ["fvlbm_host.cpp", "fvlbm_kernels.cu", "fvlbm_noalloc.cu", "fvlbm_peak.cu"]
 HEADERS = ["fvlbm_internal.h", "fvlbm_dual.h", "fvlbm_adjoint.cuh", "fvlbm_adjoint_sst.cuh",
            "fvlbm_fused_fv.cuh"]
 
@@ -74,6 +74,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     host_o = os.path.join(BUILD, "fvlbm_host.o")
     dev_o = os.path.join(BUILD, "fvlbm_kernels.o")
     na_o = os.path.join(BUILD, "fvlbm_noalloc.o")
+    pk_o = os.path.join(BUILD, "fvlbm_peak.o")
     cmds = [
         ["g++", "-O2", "-std=c++17", "-fPIC", "-fopenmp", *inc, "-c",
          os.path.join(CSRC, "fvlbm_host.cpp"), "-o", host_o],
@@ -81,6 +82,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
          *FP32_FLAGS, *inc, "-c", os.path.join(CSRC, "fvlbm_kernels.cu"), "-o", dev_o],
         [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          *inc, "-c", os.path.join(CSRC, "fvlbm_noalloc.cu"), "-o", na_o],
+        [nvcc, ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+         *inc, "-c", os.path.join(CSRC, "fvlbm_peak.cu"), "-o", pk_o],
     ]
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
              for c in cmds]
@@ -94,7 +97,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         fh.write(outs[1])
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc, ARCH, "-shared", "-Xcompiler", "-fopenmp", host_o, dev_o, na_o,
-                           "-o", tmp])
+                           pk_o, "-o", tmp])
     os.replace(tmp, LIB)
     with open(_stamp(), "w") as fh:
         fh.write(_config())

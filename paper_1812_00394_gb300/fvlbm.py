@@ -73,7 +73,7 @@ EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "
            "fvlbm_check_mesh", "fvlbm_adjoint_params", "fvlbm_set_wait_limit",
            "fvlbm_get_cells", "fvlbm_set_cells", "fvlbm_set_wall_distance", "fvlbm_cell_geometry",
            "fvlbm_forces_edges", "fvlbm_set_exchange_list", "fvlbm_pack_cells_dev",
-           "fvlbm_unpack_cells_dev"]
+           "fvlbm_unpack_cells_dev", "fvlbm_fp64_peak"]
 
 _lib = None
 
@@ -137,6 +137,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_set_exchange_list.argtypes = [vp, i, i, vp, P(i)]
     lib.fvlbm_pack_cells_dev.argtypes = [vp, i, vp]
     lib.fvlbm_unpack_cells_dev.argtypes = [vp, i, vp]
+    lib.fvlbm_fp64_peak.argtypes = [i, P(d)]
     for name in EXPORTS:
         if name not in ("fvlbm_destroy", "fvlbm_strerror"):
             getattr(lib, name).restype = i
@@ -300,6 +301,13 @@ def fvlbm_pack_cells_dev(h, list_id: int, vals_ptr: int) -> None:
 
 def fvlbm_unpack_cells_dev(h, list_id: int, vals_ptr: int) -> None:
     _check(load().fvlbm_unpack_cells_dev(h, list_id, C.c_void_p(vals_ptr)), "fvlbm_unpack_cells_dev")
+
+
+def fvlbm_fp64_peak(device: int = -1) -> float:
+    """Measured FP64 FMA throughput of the device in TFLOP/s."""
+    t = C.c_double()
+    _check(load().fvlbm_fp64_peak(device, C.byref(t)), "fvlbm_fp64_peak")
+    return t.value
 
 
 def fvlbm_footprint(h):
