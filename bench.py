@@ -399,7 +399,10 @@ def run_ours(args):
                        "parallelism": f"{world} process(es), one per GPU; the sweep's instances split "
                                       f"across them by cell count"},
             "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / args.steps,
-                           "speedup_fp32_over_fp64": value / value64},
+                           "speedup_fp32_over_fp64": value / value64,
+                           "roofline": _fp64_roofline(fvlbm, dev, total_cells, sst_cells,
+                                                      ms64 / args.steps, args.workload,
+                                                      results["f64"]["autotune"][0])},
             "explicit_euler_fp32": {"ms_per_step": ms_euler / args.steps,
                                     "imex_over_euler_cost_per_step": ms32 / ms_euler,
                                     "note": "comparison scheme of Sec. 4.1: stable only for dt < 2 tau"},
@@ -480,6 +483,38 @@ def _ncu_traffic(kname, workload, world, face_value=False):
     if kname not in vals:
         return None, f"profiles/{fname} has no figure for {kname}"
     return float(vals[kname]), f"ncu capture committed in profiles/{fname} (kernel sources sha256 {sha[:16]}...)"
+
+
+def _fp64_roofline(fvlbm, dev, cells, sst_cells, ms_per_step, workload, config):
+    """The FP64 path against the FP64 pipe: FP64 flops per step (from the committed ncu count of
+    the two-pass kernels' DADD, DMUL and DFMA instructions, per cell and per SST cell, valid
+    while the kernel sources hash to the recorded value) over the measured FMA peak."""
+    import re
+    try:
+        peak = fvlbm.fvlbm_fp64_peak(dev)
+    except Exception as e:  # noqa: BLE001 -- reported, not fatal
+        return {"bound": "alu", "pipe": "fp64", "peak": None, "error": str(e)}
+    out = {"bound": "alu", "pipe": "fp64", "peak": peak, "unit": "TFLOP/s",
+           "peak_kind": "measured FP64 FMA rate (fvlbm_fp64_peak)", "achieved": None, "frac": None}
+    if workload != "sweep" or config != "twopass":
+        out["source"] = "flop counts are for the two-pass kernels on the sweep only"
+        return out
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_flux_stage_fp64_sweep.md")) as fh:
+            txt = fh.read()
+    except OSError:
+        out["source"] = "profiles/k_flux_stage_fp64_sweep.md not found"
+        return out
+    m = re.search(r"kernel_source_sha256=([0-9a-f]{64}) fp64_flops_per_cell=([0-9.e+]+) "
+                  r"fp64_flops_per_sst_cell=([0-9.e+]+)", txt)
+    if not m or m.group(1) != kernel_source_sha256():
+        out["source"] = "profiles/k_flux_stage_fp64_sweep.md was counted on other kernel sources"
+        return out
+    flops = cells * float(m.group(2)) + sst_cells * float(m.group(3))
+    out.update(flops_per_step=flops, achieved=flops / (ms_per_step * 1e-3) / 1e12,
+               source="ncu instruction counts committed in profiles/k_flux_stage_fp64_sweep.md")
+    out["frac"] = out["achieved"] / peak
+    return out
 
 
 def _kernel_line(kname, v, cells, sst_cells, face_value, hbm):
@@ -637,9 +672,9 @@ def run_profile_mode(args):
     st = s.step(0, stats=False)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
-    _, lps = s.footprint()
+    nbytes, lps = s.footprint()
     print(json.dumps({"mode": "profile", "workload": args.workload, "precision": args.precision,
-                      "kernel_path": args.kernel_path,
+                      "kernel_path": args.kernel_path, "device_bytes": nbytes,
                       "cells": sum(c.mesh.n_cells for c in cases), "launches_per_step": lps,
                       "warmup": args.warmup, "steps": args.steps, "wall_s": el, "st": st}))
     s.close()

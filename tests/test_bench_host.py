@@ -38,3 +38,30 @@ def test_reference_arm_sampling_follows_the_budget():
     tight = _run("--workload", "sweep", "--steps", "1", "--warmup", "3", "--ref-budget", "1e-9")
     assert "1 instances" in tight["cpu_baseline"]["sample"]
     assert tight["config"]["sample_cells"] < wide["config"]["sample_cells"]
+
+
+def test_fp64_roofline_reads_the_committed_counts(monkeypatch):
+    """The FP64 line's achieved rate is the committed per-cell and per-SST-cell FP64 flop counts
+    times the units over the step time; counts taken on other kernel sources are not used."""
+    import re
+    import bench
+
+    class Peak:
+        @staticmethod
+        def fvlbm_fp64_peak(dev):
+            return 2.0
+
+    with open(os.path.join(ROOT, "profiles", "k_flux_stage_fp64_sweep.md")) as fh:
+        m = re.search(r"kernel_source_sha256=([0-9a-f]{64}) fp64_flops_per_cell=([0-9.]+) "
+                      r"fp64_flops_per_sst_cell=([0-9.]+)", fh.read())
+    assert m, "the profile records no FP64 flop counts"
+    monkeypatch.setattr(bench, "kernel_source_sha256", lambda: m.group(1))
+    r = bench._fp64_roofline(Peak, 0, 1000, 400, 0.5, "sweep", "twopass")
+    flops = 1000 * float(m.group(2)) + 400 * float(m.group(3))
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] == 2.0
+    assert abs(r["achieved"] - flops / 0.5e-3 / 1e12) <= 1e-12 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / 2.0) <= 1e-15
+    monkeypatch.setattr(bench, "kernel_source_sha256", lambda: "0" * 64)
+    stale = bench._fp64_roofline(Peak, 0, 1000, 400, 0.5, "sweep", "twopass")
+    assert stale["achieved"] is None and "other kernel sources" in stale["source"]
+    assert bench._fp64_roofline(Peak, 0, 1000, 400, 0.5, "sweep", "fused")["achieved"] is None
