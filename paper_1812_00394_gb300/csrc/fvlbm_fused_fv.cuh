@@ -56,15 +56,29 @@ constexpr int kFvGcap = 352;
 constexpr unsigned kFvNone = 0xFFFFFFFFu;
 constexpr unsigned kFvBnd = 0x80000000u;
 
+// Halo slots of an item in the fixed-stride table: a 256-cell item has at most
+// kFvEcap - 256 halo cells; the larger halos of split items continue in an overflow table.
+constexpr int kFvHs = kFvEcap - kFvThreads;
+
+// The item tables are laid out so that a CTA can issue its first loads -- the item's halo ids
+// and its header -- together, from its item index alone: the halo ids and the adjacency sit at
+// fixed strides per item, and the header carries what the later steps need.  Staging then
+// waits on two memory round trips (ids, then the rows they name) instead of three.
 struct FvItems {
-    const int4 *__restrict__ hdr;       // [nitem + 1]: base cell, cells, halo offset, adj offset
-    const int *__restrict__ r1;         // [nitem] ring-1 count
-    const int *__restrict__ halo;       // global ids: ring 1 then ring 2, per item
-    const uint4 *__restrict__ adj;      // per item [cells + r1] adjacency (cell-major)
+    const int4 *__restrict__ hdr;       // [nitem]: base cell, cells | ring-1 cells << 16,
+                                        // instance, overflow offset (-1: none)
+    const int *__restrict__ halo;       // [nitem][kFvHs] global ids, ring 1 then ring 2, -1 after
+    const int *__restrict__ ovf;        // halo slots kFvHs.. of the items that have them
+    const uint4 *__restrict__ adj;      // [nitem][kFvGcap] adjacency of item and ring-1 cells
     int *__restrict__ err;              // set to 1 if the bulk-copy wait gave up
     long long wait_first;               // polls of that wait (fvlbm_set_wait_limit)
     int item0;                          // first item of this launch (CTA b takes item0 + b)
 };
+
+// Global id of halo slot r of item it (header word hd.w: its overflow offset).
+__device__ __forceinline__ int fv_halo_id(const FvItems &W, int it, int ovf, int r) {
+    return r < kFvHs ? W.halo[static_cast<size_t>(it) * kFvHs + r] : W.ovf[ovf + r - kFvHs];
+}
 
 // Pair p: first members alpha = 1, 2, 5, 6 and their opposites 3, 4, 7, 8.
 __host__ __device__ constexpr int fv_first(int p) { return p == 0 ? 1 : (p == 1 ? 2 : (p == 2 ? 5 : 6)); }
@@ -427,14 +441,16 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
 
     const int t = threadIdx.x;
     const int it = W.item0 + static_cast<int>(blockIdx.x);
+    // halo slot t of the fixed-stride table and the header, loaded together
+    const int gid0 = t < kFvHs ? W.halo[static_cast<size_t>(it) * kFvHs + t] : -1;
     const int4 hd = W.hdr[it];
-    const int base = hd.x, cnt = hd.y, h0 = hd.z;
-    const int nh = W.hdr[it + 1].z - h0;
-    const int nr1 = W.r1[it];
-    const int E = cnt + nh, NG = cnt + nr1;
-    const uint4 *__restrict__ adj_g = W.adj + hd.w;
+    const int base = hd.x, cnt = hd.y & 0xFFFF, nr1 = hd.y >> 16;
+    const int NG = cnt + nr1;
+    // slot kFvHs + t, in the overflow table (items split for their large halo only)
+    const int gid1 = hd.w >= 0 && t < kFvHs ? W.ovf[hd.w + t] : -1;
+    const uint4 *__restrict__ adj_g = W.adj + static_cast<size_t>(it) * kFvGcap;
     const size_t np = G.np;
-    const InstParam *__restrict__ Pp = G.ip + G.tile_inst[base / kTile];  // read where used
+    const InstParam *__restrict__ Pp = G.ip + hd.z;  // read where used
     const T rho0 = ipv<T>(Pp->rho0, Pp->rho0_f);
     const bool mine = t < cnt;
     const int i = base + t;
@@ -461,8 +477,11 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
         }
     }
     constexpr int per = 16 / sizeof(T);  // elements per 16-byte chunk
-    for (int e = cnt + t; e < E; e += kFvThreads) {  // halo cells (item rows come in bulk)
-        const int gid = W.halo[h0 + e - cnt];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {  // halo cells (item rows come in bulk): slots t, kFvHs + t
+        const int gid = k == 0 ? gid0 : gid1;
+        if (gid < 0) continue;
+        const int e = cnt + t + k * kFvHs;
         if (STAGE == 1) {  // f^n is structure of arrays: one element per direction
 #pragma unroll
             for (int a = 1; a < kQ; ++a) cp_async<sizeof(T)>(sf + fv_alpha_off(e, a), fin + a * np + gid);
@@ -495,7 +514,10 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
     // stage 1: each thread relaxes the halo cells it staged (its own copies have landed)
     const T dtg = ipv<T>(Pp->dt, Pp->dt_f);
     if (STAGE == 1) {
-        for (int e = cnt + t; e < E; e += kFvThreads) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if ((k == 0 ? gid0 : gid1) < 0) continue;
+            const int e = cnt + t + k * kFvHs;
             T f[kQ];
             f[0] = sf0[e];
 #pragma unroll
@@ -548,7 +570,7 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
         // from the global rows
         const int c = cnt + (u >> 2);
         T q2[8], l2[8];
-        fv_load_geo_row(geo + 16 * static_cast<size_t>(W.halo[h0 + (u >> 2)]), q2, l2);
+        fv_load_geo_row(geo + 16 * static_cast<size_t>(fv_halo_id(W, it, hd.w, u >> 2)), q2, l2);
         fv_cell_pair<T>(c, u & 3, q2, l2, sa[c], sf, sf0, sv, G, rho0);
     }
     __syncthreads();

@@ -1705,7 +1705,7 @@ struct fvlbm_handle {
         bool ok = false;
         int nitem = 0, n_split = 0;
         int4 *d_hdr = nullptr;
-        int *d_r1 = nullptr, *d_halo = nullptr, *d_inst_item0 = nullptr;
+        int *d_halo = nullptr, *d_ovf = nullptr, *d_inst_item0 = nullptr;
         uint4 *d_adj = nullptr;
     } fv;
     bool fused = false;     // fused kernels available (IMEX scheme, kernel_path 0 or 2)
@@ -1947,7 +1947,7 @@ void fv_stages(fvlbm_handle *h, bool stats, int item0, int nitem, cudaStream_t s
     T *fn = static_cast<T *>(h->fn), *s0 = static_cast<T *>(h->s0), *s1 = static_cast<T *>(h->s1);
     T *B = static_cast<T *>(h->bacc), *C = static_cast<T *>(h->cacc);
     T *tau = static_cast<T *>(h->tau), *mac = static_cast<T *>(h->mac);
-    const FvItems W{h->fv.d_hdr, h->fv.d_r1, h->fv.d_halo, h->fv.d_adj, h->d_err, h->wait_first, item0};
+    const FvItems W{h->fv.d_hdr, h->fv.d_halo, h->fv.d_ovf, h->fv.d_adj, h->d_err, h->wait_first, item0};
     const T *geo = static_cast<const T *>(h->geo16);
     const dim3 fg(static_cast<unsigned>(nitem)), fb(kFvThreads);
     const size_t sm = FvSmem<T>::bytes;
@@ -2269,8 +2269,9 @@ int build_halos(fvlbm_handle *h, fvlbm_handle::HaloSet &S, int blk, const std::v
 // the adjacency words (cell-major) of item and ring-1 cells, and per face which member of each
 // direction pair leaves the cell through it -- decided once per face from the FP64 normal of
 // one side (e_alpha . n >= 0, the upwind rule of Eq. (advection)) and complemented on the
-// other side, so that both sides always agree.  The set is left unusable (ok = false) if a
-// quarter block still does not fit.
+// other side, so that both sides always agree.  The ring lists and the adjacency sit at fixed
+// strides per item (FvItems).  The set is left unusable (ok = false) if a quarter block still
+// does not fit.
 template <class T>
 int build_fv_items(fvlbm_handle *h, const std::vector<int> &nbr, const std::vector<int> &back,
                    const std::vector<double> &sn, const std::vector<int> &inst_tile0) {
@@ -2294,13 +2295,13 @@ int build_fv_items(fvlbm_handle *h, const std::vector<int> &nbr, const std::vect
             pbits[m * np + g] = static_cast<unsigned char>(owner ? bits : (~bits & 15u));
         }
     std::vector<int4> hdr;
-    std::vector<int> r1n, halo, item_inst;
+    std::vector<int> halo, ovf, item_inst;
     std::vector<uint4> adj;
     std::vector<int> local(np, -1), ring1, ring2;
     int n_split = 0;
     bool fits_all = true;
-    // try one item of cnt cells at base; returns false if it does not fit
-    auto try_item = [&](int base, int cnt, bool commit) -> bool {
+    // try one item of cnt cells at base (instance inst); returns false if it does not fit
+    auto try_item = [&](int base, int cnt, int inst, bool commit) -> bool {
         for (int c = 0; c < cnt; ++c) local[base + c] = c;
         ring1.clear();
         ring2.clear();
@@ -2316,12 +2317,28 @@ int build_fv_items(fvlbm_handle *h, const std::vector<int> &nbr, const std::vect
                 if (v >= 0 && local[v] < 0) { local[v] = next++; ring2.push_back(v); }
             }
         const int E = next, NG = cnt + static_cast<int>(ring1.size());
-        const bool fit = E <= kFvEcap && NG <= kFvGcap;
+        const bool fit = E <= kFvEcap && NG <= kFvGcap && E - cnt <= 2 * kFvHs;
         if (fit && commit) {
-            hdr.push_back(make_int4(base, cnt, static_cast<int>(halo.size()), static_cast<int>(adj.size())));
-            r1n.push_back(static_cast<int>(ring1.size()));
-            halo.insert(halo.end(), ring1.begin(), ring1.end());
-            halo.insert(halo.end(), ring2.begin(), ring2.end());
+            // halo ids: kFvHs slots per item, the rest (split items only: E <= kFvEcap and
+            // cnt >= 64 leave at most 2 kFvHs) in a kFvHs-slot chunk of the overflow table
+            const int nh = E - cnt;
+            const size_t h0 = halo.size();
+            halo.resize(h0 + kFvHs, -1);
+            int ovf0 = -1;
+            if (nh > kFvHs) {
+                ovf0 = static_cast<int>(ovf.size());
+                ovf.resize(ovf.size() + kFvHs, -1);
+            }
+            for (int r = 0; r < nh; ++r) {
+                const int g = r < static_cast<int>(ring1.size()) ? ring1[r] : ring2[r - ring1.size()];
+                if (r < kFvHs)
+                    halo[h0 + r] = g;
+                else
+                    ovf[ovf0 + r - kFvHs] = g;
+            }
+            hdr.push_back(make_int4(base, cnt | (static_cast<int>(ring1.size()) << 16), inst, ovf0));
+            const size_t a0 = adj.size();
+            adj.resize(a0 + kFvGcap, make_uint4(kFvNone, kFvNone, kFvNone, kFvNone));
             for (int c = 0; c < NG; ++c) {
                 const int g = c < cnt ? base + c : ring1[c - cnt];
                 unsigned w[4];
@@ -2335,7 +2352,7 @@ int build_fv_items(fvlbm_handle *h, const std::vector<int> &nbr, const std::vect
                         w[m] = static_cast<unsigned>(local[v]) | (static_cast<unsigned>(back[m * np + g]) << 16) |
                                (static_cast<unsigned>(pbits[m * np + g]) << 18);
                 }
-                adj.push_back(make_uint4(w[0], w[1], w[2], w[3]));
+                adj[a0 + c] = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
         for (int c = 0; c < cnt; ++c) local[base + c] = -1;
@@ -2351,37 +2368,36 @@ int build_fv_items(fvlbm_handle *h, const std::vector<int> &nbr, const std::vect
     for (int b = 0; b < nblk && fits_all; ++b) {
         const int base = b * IT;
         int inst = tile_inst_of[base / kTile];
-        if (try_item(base, IT, true)) {
+        if (try_item(base, IT, inst, true)) {
             item_inst.push_back(inst);
             continue;
         }
         ++n_split;
         for (int half = 0; half < 2 && fits_all; ++half) {
             const int hb = base + HALF * half;
-            if (try_item(hb, HALF, true)) {
+            if (try_item(hb, HALF, inst, true)) {
                 item_inst.push_back(inst);
                 continue;
             }
             for (int qq = 0; qq < 2 && fits_all; ++qq) {
-                if (try_item(hb + QUART * qq, QUART, true))
+                if (try_item(hb + QUART * qq, QUART, inst, true))
                     item_inst.push_back(inst);
                 else
                     fits_all = false;
             }
         }
     }
-    if (!fits_all || hdr.empty() || adj.size() >= (1u << 31)) return FVLBM_OK;  // not usable
+    if (!fits_all || hdr.empty() || ovf.size() >= (1u << 31)) return FVLBM_OK;  // not usable
     const int nitem = static_cast<int>(hdr.size());
-    hdr.push_back(make_int4(static_cast<int>(np), 0, static_cast<int>(halo.size()), static_cast<int>(adj.size())));
     std::vector<int> inst_item0(h->ninst + 1, nitem);
     for (int k = nitem - 1; k >= 0; --k) inst_item0[item_inst[k]] = k;
     for (int q = h->ninst - 1; q >= 0; --q)  // instances without items (none in practice)
         if (inst_item0[q] > inst_item0[q + 1]) inst_item0[q] = inst_item0[q + 1];
-    if (halo.empty()) halo.push_back(0);
+    if (ovf.empty()) ovf.push_back(-1);
     int rc;
     if ((rc = upload_raw(h, &h->fv.d_hdr, hdr))) return rc;
-    if ((rc = upload_raw(h, &h->fv.d_r1, r1n))) return rc;
     if ((rc = upload_raw(h, &h->fv.d_halo, halo))) return rc;
+    if ((rc = upload_raw(h, &h->fv.d_ovf, ovf))) return rc;
     if ((rc = upload_raw(h, &h->fv.d_adj, adj))) return rc;
     if ((rc = upload_raw(h, &h->fv.d_inst_item0, inst_item0))) return rc;
     CK(cudaFuncSetAttribute(k_fused_fv<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
