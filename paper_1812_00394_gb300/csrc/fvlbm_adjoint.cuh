@@ -749,13 +749,8 @@ void adj_forward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in,
     auto solve = [&](const double *mac, double *sg, double *f1, double *ko, double *wo, double *nto,
                      double *tau_out) {
         const CompactGeo<double> CG{nullptr, nullptr};
-        k_sst_grad<double, false><<<grid, block, 0, s>>>(mac, in.k, in.w, sg, f1, G, CG);
-        if (h->nonorth)
-            k_sst_update<double, false, true><<<grid, block, 0, s>>>(mac, in.k, in.w, in.nt, sg, f1, ko, wo, nto,
-                                                                     tau_out, G, nullptr, nullptr, CG);
-        else
-            k_sst_update<double, false, false><<<grid, block, 0, s>>>(mac, in.k, in.w, in.nt, sg, f1, ko, wo, nto,
-                                                                      tau_out, G, nullptr, nullptr, CG);
+        sst_grad_twopass<double>(h, mac, in.k, in.w, sg, f1, G, CG);
+        sst_update_twopass<double>(h, mac, in.k, in.w, in.nt, sg, f1, ko, wo, nto, tau_out, G, CG);
     };
     if (h->scheme == 1) {  // explicit Euler: the SST solve, then one flux + collision update
         if (h->sst) solve(in.mac, S.sg, S.f1, out.k, out.w, out.nt, S.tau);
@@ -788,13 +783,8 @@ void adj_forward_step(fvlbm_handle *h, const Geo<double> &G, const AdjState &in,
     }
     if (h->sst) {
         const CompactGeo<double> CG{nullptr, nullptr};
-        k_sst_grad<double, false><<<grid, block, 0, s>>>(in.mac, in.k, in.w, S.sg, S.f1, G, CG);
-        if (h->nonorth)  // reading variants 2 / 8 compiled in
-            k_sst_update<double, false, true><<<grid, block, 0, s>>>(in.mac, in.k, in.w, in.nt, S.sg, S.f1, out.k,
-                                                                     out.w, out.nt, S.tau, G, nullptr, nullptr, CG);
-        else
-            k_sst_update<double, false, false><<<grid, block, 0, s>>>(in.mac, in.k, in.w, in.nt, S.sg, S.f1, out.k,
-                                                                      out.w, out.nt, S.tau, G, nullptr, nullptr, CG);
+        sst_grad_twopass<double>(h, in.mac, in.k, in.w, S.sg, S.f1, G, CG);
+        sst_update_twopass<double>(h, in.mac, in.k, in.w, in.nt, S.sg, S.f1, out.k, out.w, out.nt, S.tau, G, CG);
         tau = S.tau;
         mac_out = out.mac;
     }

@@ -1163,16 +1163,19 @@ __device__ __forceinline__ void sst_load_rec(const T *__restrict__ rec8, const T
     }
 }
 
+// Both SST kernels run over one contiguous run of SST tiles per launch (tile0 + block; a
+// laminar instance keeps tau = nu / cs^2 and is not visited), so a thread issues the loads of
+// its own cell at once, without waiting for the instance parameters first.
 template <class T, bool COMPACT>
 __global__ void __launch_bounds__(kTile)
     k_sst_grad(const T *__restrict__ mac, const T *__restrict__ kk, const T *__restrict__ ww,
                T *__restrict__ grads, T *__restrict__ f1out, Geo<T> G, CompactGeo<T> CG,
-               const T *__restrict__ nut = nullptr, T *__restrict__ rec8 = nullptr,
-               T *__restrict__ rec2 = nullptr, bool inv_only = false) {
-    const int i = blockIdx.x * kTile + threadIdx.x;
+               const T *__restrict__ nut, T *__restrict__ rec8, T *__restrict__ rec2, bool inv_only,
+               int tile0) {
+    const int tile = tile0 + static_cast<int>(blockIdx.x);
+    const int i = tile * kTile + threadIdx.x;
     const size_t np = G.np;
-    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
-    if (!P.sst) return;  // laminar instance: tau stays nu / cs^2
+    const InstParam P = G.ip[G.tile_inst[tile]];
     const T nu = ipv<T>(P.nu, P.nu_f);
     const T own[4] = {mac[np + i], mac[2 * np + i], kk[i], ww[i]};
     const T di = G.wdist[i];
@@ -1256,11 +1259,11 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 5 : 1)
                  const T *__restrict__ f1a, T *__restrict__ k_out, T *__restrict__ w_out,
                  T *__restrict__ nut_out, T *__restrict__ tau, Geo<T> G,
                  const T *__restrict__ fn, T *__restrict__ frel, CompactGeo<T> CG,
-                 const T *__restrict__ rec8 = nullptr, const T *__restrict__ rec2 = nullptr) {
-    const int i = blockIdx.x * kTile + threadIdx.x;
+                 const T *__restrict__ rec8, const T *__restrict__ rec2, int tile0) {
+    const int tile = tile0 + static_cast<int>(blockIdx.x);
+    const int i = tile * kTile + threadIdx.x;
     const size_t np = G.np;
-    const InstParam P = G.ip[G.tile_inst[blockIdx.x]];
-    if (!P.sst) return;  // laminar instance
+    const InstParam P = G.ip[G.tile_inst[tile]];
     const T nu = ipv<T>(P.nu, P.nu_f);
     const bool packed = COMPACT && rec8 != nullptr;
     T ui, vi, ki, wi, nti, f1i;
@@ -1688,6 +1691,7 @@ struct fvlbm_handle {
     // device arrays (element type T = double or float; stored as void*)
     int *d_nbr = nullptr, *d_tile_inst = nullptr, *d_btype = nullptr, *d_bowner = nullptr;
     int *d_perm = nullptr, *d_inst_tile0 = nullptr;
+    std::vector<int2> sst_runs;  // (first tile, tiles) of each contiguous run of SST instances
     int *d_all_map = nullptr;   // output position (all instances) -> internal cell
     int *d_back = nullptr;      // FP64 handles: slot of each face at its neighbour [4 np] (adjoint)
     size_t adj_budget = 0;      // device bytes the adjoint may keep stage values in (0: half the free)
@@ -1985,6 +1989,36 @@ void grad_f(const fvlbm_handle *h, dim3 grid, dim3 block, cudaStream_t s, const 
         k_grad<T, false><<<grid, block, 0, s>>>(f, g, G);
 }
 
+// One launch of an SST kernel per contiguous run of SST tiles: f(blocks, first tile).
+template <class F>
+void for_sst_runs(const fvlbm_handle *h, F &&f) {
+    for (const int2 &r : h->sst_runs) f(dim3(static_cast<unsigned>(r.y)), r.x);
+}
+
+// The two SST kernels of the two-pass path (unpacked gradients, geometry read as stored), on
+// stream h->stream: gradients and f1 of the macros mac, then k, omega, nu_t and tau_out.
+template <class T>
+void sst_grad_twopass(const fvlbm_handle *h, const T *mac, const T *kc, const T *wc, T *sg, T *f1,
+                      const Geo<T> &G, const CompactGeo<T> &CG) {
+    for_sst_runs(h, [&](dim3 g, int t0) {
+        k_sst_grad<T, false><<<g, kTile, 0, h->stream>>>(mac, kc, wc, sg, f1, G, CG, nullptr, nullptr,
+                                                         nullptr, false, t0);
+    });
+}
+template <class T>
+void sst_update_twopass(const fvlbm_handle *h, const T *mac, const T *kc, const T *wc, const T *nc,
+                        const T *sg, const T *f1, T *kn, T *wn, T *nn, T *tau_out, const Geo<T> &G,
+                        const CompactGeo<T> &CG) {
+    for_sst_runs(h, [&](dim3 g, int t0) {
+        if (h->nonorth)
+            k_sst_update<T, false, true><<<g, kTile, 0, h->stream>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau_out,
+                                                                     G, nullptr, nullptr, CG, nullptr, nullptr, t0);
+        else
+            k_sst_update<T, false, false><<<g, kTile, 0, h->stream>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn, tau_out,
+                                                                      G, nullptr, nullptr, CG, nullptr, nullptr, t0);
+    });
+}
+
 template <class T>
 void enqueue_step(fvlbm_handle *h, bool stats) {
     Geo<T> G = geo_of<T>(h);
@@ -2005,33 +2039,30 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
             if (h->config != 2) {  // compact geometry, and stage 1's f^(1) with the new tau
                 T *r8 = static_cast<T *>(h->sst_rec8), *r2 = static_cast<T *>(h->sst_rec2);
                 launch(h, K_SST_GRAD, "sst_grad", [&] {
-                    k_sst_grad<T, true><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG, nc, r8, r2,
-                                                               !h->nonorth);
+                    for_sst_runs(h, [&](dim3 sg_grid, int t0) {
+                        k_sst_grad<T, true><<<sg_grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG, nc, r8, r2,
+                                                                      !h->nonorth, t0);
+                    });
                 });
                 launch(h, K_SST_UPDATE, "sst_update", [&] {
                     // the face-value stages relax f^n themselves; the other fused form reads
                     // stage 1's f^(1), relaxed here with the new tau
                     T *fr = h->config == 3 ? nullptr : static_cast<T *>(h->frel);
-                    if (h->nonorth)
-                        k_sst_update<T, true, true><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn,
-                                                                           tau, G, fn, fr, CG, r8, r2);
-                    else
-                        k_sst_update<T, true, false><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn,
-                                                                            tau, G, fn, fr, CG, r8, r2);
+                    for_sst_runs(h, [&](dim3 sg_grid, int t0) {
+                        if (h->nonorth)
+                            k_sst_update<T, true, true><<<sg_grid, block, 0, s>>>(
+                                mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn, fr, CG, r8, r2, t0);
+                        else
+                            k_sst_update<T, true, false><<<sg_grid, block, 0, s>>>(
+                                mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, fn, fr, CG, r8, r2, t0);
+                    });
                 });
             }
         }
         if (h->config == 2) {
-            launch(h, K_SST_GRAD, "sst_grad", [&] {
-                k_sst_grad<T, false><<<grid, block, 0, s>>>(mac, kc, wc, sg, f1, G, CG);
-            });
+            launch(h, K_SST_GRAD, "sst_grad", [&] { sst_grad_twopass<T>(h, mac, kc, wc, sg, f1, G, CG); });
             launch(h, K_SST_UPDATE, "sst_update", [&] {
-                if (h->nonorth)
-                    k_sst_update<T, false, true><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn,
-                                                                        tau, G, fn, nullptr, CG);
-                else
-                    k_sst_update<T, false, false><<<grid, block, 0, s>>>(mac, kc, wc, nc, sg, f1, kn, wn, nn,
-                                                                         tau, G, fn, nullptr, CG);
+                sst_update_twopass<T>(h, mac, kc, wc, nc, sg, f1, kn, wn, nn, tau, G, CG);
             });
         }
         if (h->per_stage && h->scheme == 0) {
@@ -2039,16 +2070,9 @@ void enqueue_step(fvlbm_handle *h, bool stats) {
             // stages 2 and 3 with the macros of f^(1) and f^(2); stage J relaxes with tau^(J)
             T *t1 = static_cast<T *>(h->tau1), *m2 = static_cast<T *>(h->mac2);
             auto solve = [&](T *macp, T *tau_out) {
-                launch(h, K_SST_GRAD, "sst_grad", [&] {
-                    k_sst_grad<T, false><<<grid, block, 0, s>>>(macp, kc, wc, sg, f1, G, CG);
-                });
+                launch(h, K_SST_GRAD, "sst_grad", [&] { sst_grad_twopass<T>(h, macp, kc, wc, sg, f1, G, CG); });
                 launch(h, K_SST_UPDATE, "sst_update", [&] {
-                    if (h->nonorth)
-                        k_sst_update<T, false, true><<<grid, block, 0, s>>>(macp, kc, wc, nc, sg, f1, kn, wn,
-                                                                            nn, tau_out, G, fn, nullptr, CG);
-                    else
-                        k_sst_update<T, false, false><<<grid, block, 0, s>>>(macp, kc, wc, nc, sg, f1, kn, wn,
-                                                                             nn, tau_out, G, fn, nullptr, CG);
+                    sst_update_twopass<T>(h, macp, kc, wc, nc, sg, f1, kn, wn, nn, tau_out, G, CG);
                 });
             };
             // the solve of the step start already ran above into tau; stage 1 relaxes with it
@@ -2733,6 +2757,14 @@ int create_impl(int n, const fvlbm_mesh *meshes, const fvlbm_bc *bcs, const fvlb
         h->inst.push_back(I);
     }
     inst_tile0.push_back(cell_off / kTile);
+    for (int q = 0; q < n; ++q) {  // contiguous runs of SST tiles: the SST kernels visit these only
+        const int t0 = h->inst[q].tile_off, nt = h->inst[q].np / kTile;
+        if (!params[q].sst || nt == 0) continue;
+        if (!h->sst_runs.empty() && h->sst_runs.back().x + h->sst_runs.back().y == t0)
+            h->sst_runs.back().y += nt;
+        else
+            h->sst_runs.push_back(make_int2(t0, nt));
+    }
     h->np = cell_off;
     h->nbt = bface_off;
     h->ntiles = cell_off / kTile;
