@@ -75,11 +75,6 @@ struct FvItems {
     int item0;                          // first item of this launch (CTA b takes item0 + b)
 };
 
-// Global id of halo slot r of item it (header word hd.w: its overflow offset).
-__device__ __forceinline__ int fv_halo_id(const FvItems &W, int it, int ovf, int r) {
-    return r < kFvHs ? W.halo[static_cast<size_t>(it) * kFvHs + r] : W.ovf[ovf + r - kFvHs];
-}
-
 // Pair p: first members alpha = 1, 2, 5, 6 and their opposites 3, 4, 7, 8.
 __host__ __device__ constexpr int fv_first(int p) { return p == 0 ? 1 : (p == 1 ? 2 : (p == 2 ? 5 : 6)); }
 __host__ __device__ constexpr int fv_second(int p) { return p == 0 ? 3 : (p == 1 ? 4 : (p == 2 ? 7 : 8)); }
@@ -126,6 +121,7 @@ struct FvPair<double> {
 //   sa  [kFvGcap]      adjacency words (uint4)
 //   sacc [19][256]     the item's rows for the stage algebra, structure of arrays: stage 1
 //                      f^n; stage 2 B and C; stage 3 C; then tau
+//   the item's instance parameters (copied during staging, read by the stage algebra)
 //   one mbarrier for the bulk copies
 template <class T>
 struct FvSmem {
@@ -135,7 +131,8 @@ struct FvSmem {
     static constexpr size_t sv = st + 2 * size_t(kFvEcap) * sizeof(T);
     static constexpr size_t sa = sv + size_t(kFvGcap) * 16 * sizeof(T);
     static constexpr size_t sacc = sa + size_t(kFvGcap) * 16;
-    static constexpr size_t bar = sacc + size_t(2 * kQ + 1) * kFvThreads * sizeof(T);
+    static constexpr size_t ip = sacc + size_t(2 * kQ + 1) * kFvThreads * sizeof(T);
+    static constexpr size_t bar = ip + sizeof(InstParam);
     static constexpr size_t bytes = bar + 16;
 };
 
@@ -508,6 +505,9 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
         }
     }
     for (int e = t; e < NG; e += kFvThreads) cp_async<16>(sa + e, adj_g + e);
+    static_assert(sizeof(InstParam) % 16 == 0 && FvSmem<T>::ip % 16 == 0, "16-byte copies of the parameters");
+    if (t < static_cast<int>(sizeof(InstParam) / 16))  // (device arrays of InstParam: 16-byte aligned rows)
+        cp_async<16>(smem_raw + FvSmem<T>::ip + 16 * t, reinterpret_cast<const unsigned char *>(Pp) + 16 * t);
     T q[8], lw[8];
     if (mine) fv_load_geo_row(geo + 16 * static_cast<size_t>(i), q, lw);  // the item cell's geometry row
     cp_async_wait_all();
@@ -565,13 +565,23 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
     //    cells with one direction pair per thread
     if (mine) fv_cell<T>(t, q, lw, sa[t], sf, sf0[t], sv, G, rho0);
     if (t < ru) fv_cell_pair<T>(cnt + (t >> 2), t & 3, qr, lr, wr, sf, sf0, sv, G, rho0);
-    for (int u = t + kFvThreads; u < ru; u += kFvThreads) {  // items with more than 64 ring-1 cells
-        // the face-value rows of these cells may already hold values: read their geometry
-        // from the global rows
+    // items with more than 64 ring-1 cells: further rounds of 256 units.  A ring-1 row is
+    // written only by the four threads of its own unit (consecutive lanes of one warp) in its
+    // own round, so each thread reads the geometry from its row and the warp syncs before any
+    // of them writes a face value there.  The round count is the same for the whole block.
+    for (int u0 = kFvThreads; u0 < ru; u0 += kFvThreads) {
+        const int u = u0 + t;
+        const bool act = u < ru;
         const int c = cnt + (u >> 2);
         T q2[8], l2[8];
-        fv_load_geo_row(geo + 16 * static_cast<size_t>(fv_halo_id(W, it, hd.w, u >> 2)), q2, l2);
-        fv_cell_pair<T>(c, u & 3, q2, l2, sa[c], sf, sf0, sv, G, rho0);
+        if (act) {
+            fv_load_vals(sv, c, 0, q2);
+            fv_load_vals(sv, c, 1, q2 + 4);
+            fv_load_vals(sv, c, 2, l2);
+            fv_load_vals(sv, c, 3, l2 + 4);
+        }
+        __syncwarp();
+        if (act) fv_cell_pair<T>(c, u & 3, q2, l2, sa[c], sf, sf0, sv, G, rho0);
     }
     __syncthreads();
 
@@ -590,8 +600,8 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
         }
         fv_flux<T>(t, q, wt, fi, sv, G, rho0, acc);
 
-        // 4. the stage algebra, with the accumulator rows and tau from shared memory
-        const InstParam P = *Pp;
+        // 4. the stage algebra, with the accumulator rows, tau and the parameters from shared memory
+        const InstParam &P = *reinterpret_cast<const InstParam *>(smem_raw + FvSmem<T>::ip);
         T macv[3];
         T uo = T(0), vo0 = T(0);
         if (STATS) {
