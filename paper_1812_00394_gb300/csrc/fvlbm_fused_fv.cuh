@@ -218,13 +218,20 @@ __device__ __forceinline__ void fv_store_vals(T *sv, int c, int m, const T *v) {
     }
 }
 
-// Boundary face values (boundary_values) of a cell whose f is given as 4 pairs and f_0, as 4
-// pairs.
+// Boundary face values (boundary_values) on boundary face bf of a cell whose f is given as 4
+// pairs and f_0, as 4 pairs.  The face's type and (rho, u, v) are read kept in L2, like the
+// item tables: a few hundred kB read once per launch by the items along the boundaries.
 template <class T>
-__device__ __forceinline__ void fv_boundary_pairs(int type, const T *__restrict__ bval, int nbt, T nx, T ny,
+__device__ __forceinline__ void fv_boundary_pairs(const Geo<T> &G, int bf, T nx, T ny,
                                                   const typename FvPair<T>::V *fc, T f0, T rho0,
                                                   typename FvPair<T>::V *out) {
     using PV = FvPair<T>;
+    const unsigned long long keep = l2_keep_policy();
+    const int type = ld_keep(G.btype + bf, keep);
+    T bval[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) bval[c] = ld_keep(G.bval + static_cast<size_t>(c) * G.nbt + bf, keep);
+    const int nbt = 1;
     T fcs[kQ], fb[kQ], dr, r, u, v;
     fcs[0] = f0;
 #pragma unroll
@@ -283,7 +290,7 @@ __device__ __forceinline__ void fv_cell(int c, const T *q, const T *lw, const ui
             // boundary face: its value at the face midpoint is one more data point
             const int bf = static_cast<int>(w[m] & ~kFvBnd);
             const T nx = FV_END_Y(m) - q[2 * m + 1], ny = -(FV_END_X(m) - q[2 * m]);  // outward
-            fv_boundary_pairs<T>(G.btype[bf], G.bval + bf, G.nbt, nx, ny, fc, f0, rho0, fm);
+            fv_boundary_pairs<T>(G, bf, nx, ny, fc, f0, rho0, fm);
         } else {
             fv_load_row(sf, static_cast<int>(w[m] & 0xFFFFu), fm);
         }
@@ -333,7 +340,7 @@ __device__ __forceinline__ void fv_cell_pair(int c, int p, const T *q, const T *
             const T nx = FV_END_Y(m) - q[2 * m + 1], ny = -(FV_END_X(m) - q[2 * m]);
             V fall[4], fb[4];
             fv_load_row(sf, c, fall);
-            fv_boundary_pairs<T>(G.btype[bf], G.bval + bf, G.nbt, nx, ny, fall, sf0[c], rho0, fb);
+            fv_boundary_pairs<T>(G, bf, nx, ny, fall, sf0[c], rho0, fb);
             fm = p == 0 ? fb[0] : (p == 1 ? fb[1] : (p == 2 ? fb[2] : fb[3]));
         } else {
             fm = *reinterpret_cast<const V *>(sf + fv_pair_off(static_cast<int>(w[m] & 0xFFFFu), p));
@@ -382,7 +389,7 @@ __device__ __forceinline__ void fv_flux(int t, const T *q, const uint4 &wt, cons
         if (w[m] & kFvBnd) {
             const int bf = static_cast<int>(w[m] & ~kFvBnd);
             V fb[4];
-            fv_boundary_pairs<T>(G.btype[bf], G.bval + bf, G.nbt, snx, sny, fc, fi[0], rho0, fb);
+            fv_boundary_pairs<T>(G, bf, snx, sny, fc, fi[0], rho0, fb);
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
                 const T en = fv_en<T>(p, snx, sny);
@@ -438,13 +445,14 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
 
     const int t = threadIdx.x;
     const int it = W.item0 + static_cast<int>(blockIdx.x);
-    // halo slot t of the fixed-stride table and the header, loaded together
-    const int gid0 = t < kFvHs ? W.halo[static_cast<size_t>(it) * kFvHs + t] : -1;
-    const int4 hd = W.hdr[it];
+    // halo slot t of the fixed-stride table and the header, loaded together (kept in L2)
+    const unsigned long long keep = l2_keep_policy();
+    const int gid0 = t < kFvHs ? ld_keep(W.halo + static_cast<size_t>(it) * kFvHs + t, keep) : -1;
+    const int4 hd = ld_keep(W.hdr + it, keep);
     const int base = hd.x, cnt = hd.y & 0xFFFF, nr1 = hd.y >> 16;
     const int NG = cnt + nr1;
     // slot kFvHs + t, in the overflow table (items split for their large halo only)
-    const int gid1 = hd.w >= 0 && t < kFvHs ? W.ovf[hd.w + t] : -1;
+    const int gid1 = hd.w >= 0 && t < kFvHs ? ld_keep(W.ovf + hd.w + t, keep) : -1;
     const uint4 *__restrict__ adj_g = W.adj + static_cast<size_t>(it) * kFvGcap;
     const size_t np = G.np;
     const InstParam *__restrict__ Pp = G.ip + hd.z;  // read where used

@@ -653,6 +653,37 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// Loads of small tables that every launch reads once per item (the face-value items' headers
+// and halo ids), marked evict-last in L2 so that the streamed state does not push them out
+// between launches: their load is the first memory round trip of every CTA.
+__device__ __forceinline__ unsigned long long l2_keep_policy() {
+    unsigned long long p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ int ld_keep(const int *a, unsigned long long pol) {
+    int v;
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float ld_keep(const float *a, unsigned long long pol) {
+    float v;
+    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_keep(const double *a, unsigned long long pol) {
+    double v;
+    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ int4 ld_keep(const int4 *a, unsigned long long pol) {
+    int4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(a), "l"(pol));
+    return v;
+}
+
 // Face m of a cell whose node positions (relative to its centroid) are q[(2k + c) * ld]:
 // midpoint r = (q_m + q_{m+1}) / 2 and edge vector e = q_{m+1} - q_m.
 template <class T>
