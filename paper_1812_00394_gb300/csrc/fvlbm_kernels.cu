@@ -1480,13 +1480,53 @@ __global__ void k_gather_f_all(const T *__restrict__ f, const int *__restrict__ 
     }
 }
 
-// State input: positions j < n of the concatenated input order (map gives the internal cell).
+// State input: internal cells [i0, i0 + n), each reading its record at input position
+// inv[i] - po of the concatenated input order (padding cells: inv = -1, left as they are).
 // IN = double: absolute f; IN = float: the FP32 deviation f - w_alpha rho0.  Writes f^n, the
 // macros and f^(1) of the coming step (relaxed like k_stage1, for the fused stages).
 template <class T, class IN>
 __global__ void k_scatter_state(T *__restrict__ f, T *__restrict__ mac, T *__restrict__ frel,
-                                const T *__restrict__ tau, const int *__restrict__ map, int n,
-                                Geo<T> G, const IN *__restrict__ in) {
+                                const T *__restrict__ tau, const int *__restrict__ inv, int i0, int n,
+                                int po, Geo<T> G, const IN *__restrict__ in) {
+    // one thread per internal cell i (the state arrays are written coalesced; the input record
+    // of the cell, 9 consecutive values, is read where the input order puts it)
+    const int i = i0 + static_cast<int>(blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= i0 + n) return;
+    const int jo = inv[i];
+    if (jo < 0) return;  // padding cell of a tile
+    const size_t j = static_cast<size_t>(jo - po);
+    const size_t np = G.np;
+    const InstParam P = G.ip[G.tile_inst[i / kTile]];
+    T d[kQ];
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) {
+        if constexpr (sizeof(IN) == sizeof(double)) {
+            const double wa = a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+            d[a] = T(double(in[j * kQ + a]) - wa * P.rho0);
+        } else if constexpr (std::is_same<T, float>::value) {
+            d[a] = in[j * kQ + a];  // the deviation itself, with no round trip through double
+        } else {
+            d[a] = T(double(in[j * kQ + a]));
+        }
+        f[a * np + i] = d[a];
+    }
+    T dr, r, u, v;
+    moments(d, ipv<T>(P.rho0, P.rho0_f), dr, r, u, v);
+    mac[i] = r;
+    mac[np + i] = u;
+    mac[2 * np + i] = v;
+    if (frel != nullptr) {  // f^(1) of the coming step, for the forms that stage it
+        relax9(d, ipv<T>(P.rho0, P.rho0_f), cell_dt(G, P, i), tau[i]);
+        store9(frel, np, i, d);
+    }
+}
+
+// The same for a list of cells: position j < n of the input takes internal cell map[j] (the
+// cell lists of fvlbm_set_cells).
+template <class T, class IN>
+__global__ void k_scatter_list(T *__restrict__ f, T *__restrict__ mac, T *__restrict__ frel,
+                               const T *__restrict__ tau, const int *__restrict__ map, int n,
+                               Geo<T> G, const IN *__restrict__ in) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int i = map[j];
@@ -1508,7 +1548,7 @@ __global__ void k_scatter_state(T *__restrict__ f, T *__restrict__ mac, T *__res
     mac[i] = r;
     mac[np + i] = u;
     mac[2 * np + i] = v;
-    if (frel != nullptr) {  // f^(1) of the coming step, for the forms that stage it
+    if (frel != nullptr) {
         relax9(d, ipv<T>(P.rho0, P.rho0_f), cell_dt(G, P, i), tau[i]);
         store9(frel, np, i, d);
     }
@@ -1724,6 +1764,7 @@ struct fvlbm_handle {
     int *d_perm = nullptr, *d_inst_tile0 = nullptr;
     std::vector<int2> sst_runs;  // (first tile, tiles) of each contiguous run of SST instances
     int *d_all_map = nullptr;   // output position (all instances) -> internal cell
+    int *d_all_inv = nullptr;   // internal cell -> output position (all instances), -1: padding
     int *d_back = nullptr;      // FP64 handles: slot of each face at its neighbour [4 np] (adjoint)
     size_t adj_budget = 0;      // device bytes the adjoint may keep stage values in (0: half the free)
     int total_nc = 0, total_nb = 0;
@@ -2567,16 +2608,20 @@ int allocate_state(fvlbm_handle *h, const std::vector<const Prepared *> &P,
         h->order_hash = hsh;
     }
     {
-        std::vector<int> map;
+        std::vector<int> map, inv(h->np, -1);
         int out_off = 0;
         for (int q = 0; q < h->ninst; ++q) {
             const Prepared &p = *P[q];
             map.resize(out_off + p.nc);
-            for (int k = 0; k < p.nc; ++k) map[out_off + p.perm[k]] = h->inst[q].cell_off + k;
+            for (int k = 0; k < p.nc; ++k) {
+                map[out_off + p.perm[k]] = h->inst[q].cell_off + k;
+                inv[h->inst[q].cell_off + k] = out_off + p.perm[k];
+            }
             out_off += p.nc;
         }
         h->total_nc = out_off;
         if ((rc = upload_raw(h, &h->d_all_map, map))) return rc;
+        if ((rc = upload_raw(h, &h->d_all_inv, inv))) return rc;
     }
     if ((rc = upload_as<T>(h, &h->sn, sn))) return rc;
     if ((rc = upload_as<T>(h, &h->lsq, lsq))) return rc;
@@ -2857,13 +2902,15 @@ void *frel_target(const fvlbm_handle *h) { return h->config == 0 || h->config ==
 // float: FP32 deviations) into f^n, the macros and f^(1) of the coming step; handle's stream.
 template <class IN>
 void scatter_state_dev(fvlbm_handle *h, int instance, const IN *src) {
-    const int n = static_cast<int>(io_cells(h, instance));
+    // the internal cells of the instance (all instances: every cell), padding included
+    const int i0 = instance == -1 ? 0 : h->inst[instance].cell_off;
+    const int n = instance == -1 ? static_cast<int>(h->np) : h->inst[instance].np;
     const int po = instance == -1 ? 0 : perm_offset(h, instance);
     dispatch(h->precision, [&](auto z_) {
         using T = decltype(z_);
         k_scatter_state<T, IN><<<(n + 255) / 256, 256, 0, h->stream>>>(
             static_cast<T *>(h->fn), static_cast<T *>(h->mac), static_cast<T *>(frel_target(h)),
-            static_cast<const T *>(h->tau), h->d_all_map + po, n, geo_of<T>(h), src);
+            static_cast<const T *>(h->tau), h->d_all_inv, i0, n, po, geo_of<T>(h), src);
     });
 }
 
@@ -3227,7 +3274,7 @@ int fvlbm_set_cells(fvlbm_handle *h, int instance, int n, const int *cells, cons
         using T = decltype(z_);
         const int c = h->turb;
         if (f)  // f^n, the macros and f^(1) of the coming step, as fvlbm_set_f
-            k_scatter_state<T, double><<<(n + 255) / 256, 256, 0, h->stream>>>(
+            k_scatter_list<T, double><<<(n + 255) / 256, 256, 0, h->stream>>>(
                 static_cast<T *>(h->fn), static_cast<T *>(h->mac), static_cast<T *>(frel_target(h)),
                 static_cast<const T *>(h->tau), d_map, n, geo_of<T>(h), d_f);
         if (turb)
