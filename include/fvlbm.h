@@ -208,7 +208,7 @@ int fvlbm_step(fvlbm_handle *h, int n_steps, fvlbm_stats *stats);
 /* Diagnostic for the error path above (not in the paper): the number of polls the first
  * staging wait of the fused stage kernels (both fused forms: kernel_path 0 with 256- and
  * 128-cell blocks, and the face-value form of kernel_path 2) makes before giving up; default
- * 2^26, 0 gives up after the first poll.  Only that wait changes: before a block returns it
+ * 2^26, 0 gives up at once, without polling.  Only that wait changes: before a block returns it
  * still waits, with the full bound, for its own copies in flight, so that no copy lands in
  * shared memory after the block has left.  Drops the captured step graphs.
  * Errors: BAD_PARAM. */

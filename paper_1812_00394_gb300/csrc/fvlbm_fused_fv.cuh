@@ -462,23 +462,36 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
     const T *fa0 = fin + 8 * np;  // stages 2, 3: f_0 of every cell after the cell-major rows
 
     // 1. staging, issued before any wait
-    if (t == 0) mbar_init(bar);
+    // The bulk copies are shared out over the lanes 0 of the 8 warps, so that no warp issues
+    // more than 3 of them: each such lane arrives on the mbarrier (count 8) with the bytes of
+    // its own copies, then issues them.
+    constexpr int kWarps = kFvThreads / 32;
+    if (t == 0) mbar_init(bar, kWarps);
     __syncthreads();
-    if (t == 0) {
+    if ((t & 31) == 0) {
         const unsigned row = static_cast<unsigned>(cnt * sizeof(T));
-        // accumulator rows (stage 1: f^n, stage 2: B and C, stage 3: C), tau, and in stages
-        // 2, 3 the item's f rows and f_0
+        // copies: (stages 2, 3) the item's f rows and f_0, then the accumulator rows (stage 1:
+        // f^n, stage 2: B and C, stage 3: C), then tau
         const T *a1g = STAGE == 1 ? fin : (STAGE == 2 ? Bacc : Cacc);
-        unsigned bytes = row * (STAGE == 2 ? 2 * kQ + 1 : kQ + 1);
-        if (STAGE != 1) bytes += 9 * row;
+        constexpr int nf = STAGE == 1 ? 0 : 2, nacc = STAGE == 2 ? 2 * kQ : kQ, ncopy = nf + nacc + 1;
+        const int w = t >> 5;
+        unsigned bytes = 0;
+        for (int c = w; c < ncopy; c += kWarps) bytes += (nf > 0 && c == 0) ? 8 * row : row;
         mbar_expect_tx(bar, bytes);
-        for (int a = 0; a < kQ; ++a) bulk_g2s(sacc + a * kFvThreads, a1g + a * np + base, row, bar);
-        if (STAGE == 2)
-            for (int a = 0; a < kQ; ++a) bulk_g2s(sacc + (kQ + a) * kFvThreads, Cacc + a * np + base, row, bar);
-        bulk_g2s(sacc + 2 * kQ * kFvThreads, tau + base, row, bar);
-        if (STAGE != 1) {
-            bulk_g2s(sf, fin + 8 * static_cast<size_t>(base), 8 * row, bar);
-            bulk_g2s(sf0, fa0 + base, row, bar);
+        for (int c = w; c < ncopy; c += kWarps) {
+            if (nf > 0 && c == 0) {
+                bulk_g2s(sf, fin + 8 * static_cast<size_t>(base), 8 * row, bar);
+            } else if (nf > 0 && c == 1) {
+                bulk_g2s(sf0, fa0 + base, row, bar);
+            } else if (c < nf + kQ) {
+                const int a = c - nf;
+                bulk_g2s(sacc + a * kFvThreads, a1g + a * np + base, row, bar);
+            } else if (c < nf + nacc) {  // stage 2: the C rows
+                const int a = c - nf - kQ;
+                bulk_g2s(sacc + (kQ + a) * kFvThreads, Cacc + a * np + base, row, bar);
+            } else {
+                bulk_g2s(sacc + 2 * kQ * kFvThreads, tau + base, row, bar);
+            }
         }
     }
     constexpr int per = 16 / sizeof(T);  // elements per 16-byte chunk
@@ -535,9 +548,8 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
     }
     {
         long long it = 0;
-        // (a limit of 0 polls once without blocking: try_wait itself may suspend the thread for
-        // a while, test_wait returns at once)
-        bool done = W.wait_first > 0 ? mbar_try_wait(bar, 0) : mbar_test_wait(bar, 0);
+        // (a limit of 0 gives up at once, without polling: the diagnostic of the error path)
+        bool done = W.wait_first > 0 && mbar_try_wait(bar, 0);
         while (!done && ++it < W.wait_first) done = mbar_try_wait(bar, 0);
         // the block leaves together if any thread gave up: flag it, wait once more (with the
         // full bound) for its own copies in flight, then return

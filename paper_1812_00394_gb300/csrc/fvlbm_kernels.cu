@@ -605,8 +605,8 @@ struct CompactGeo {
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
     return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count = 1) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
@@ -618,17 +618,6 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// non-blocking test of the phase (returns at once)
-__device__ __forceinline__ bool mbar_test_wait(unsigned long long *bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
@@ -791,9 +780,8 @@ __global__ void __launch_bounds__(BLK, sizeof(T) == 4 ? (768 / BLK) : 1)
     cp_async_wait_all();
     {
         long long it = 0;
-        // (a limit of 0 polls once without blocking: try_wait itself may suspend the thread for
-        // a while, test_wait returns at once)
-        bool done = H.wait_first > 0 ? mbar_try_wait(bar, 0) : mbar_test_wait(bar, 0);
+        // (a limit of 0 gives up at once, without polling: the diagnostic of the error path)
+        bool done = H.wait_first > 0 && mbar_try_wait(bar, 0);
         while (!done && ++it < H.wait_first) done = mbar_try_wait(bar, 0);
         // the block leaves together if any thread gave up: flag it, wait once more (bounded)
         if (__syncthreads_or(!done)) {

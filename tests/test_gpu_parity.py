@@ -798,8 +798,9 @@ def test_staging_wait_give_up_is_reported_and_cleared(path):
     """The bounded staging wait of the fused kernels (both fused forms) reports
     FVLBM_ERR_TIMEOUT through the device flag that a stats step reads; the flag is cleared, and
     with the normal bound back and the saved state restored the next steps are clean and match
-    the oracle.  No fault is involved: only the first wait is shortened (to one poll); every
-    block still waits, with the full bound, for its own copies before it returns."""
+    the oracle.  No fault is involved: only the first wait is shortened (to none: a block gives
+    up without polling); every block still waits, with the full bound, for its own copies before
+    it returns."""
     case = mg.naca0012_cmesh(n_target=6000, alpha_deg=4.0)
     s = fvlbm.Solver(case, precision=FP64, device=0, kernel_path=path)
     blob = s.save_state()
