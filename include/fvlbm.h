@@ -214,6 +214,14 @@ int fvlbm_step(fvlbm_handle *h, int n_steps, fvlbm_stats *stats);
  * Errors: BAD_PARAM. */
 int fvlbm_set_wait_limit(fvlbm_handle *h, long long polls);
 
+/* Diagnostic (not in the paper): the work items of the face-value stages (kernel_path 2).
+ * *nitem: items (256-cell blocks, or their halves / quarters); *n_split: 256-cell blocks split
+ * because their ring-1 + ring-2 halo did not fit the shared memory; *n_overflow: items whose
+ * halo has more than 192 cells (its ids continue in a second table).  All 0 when the handle
+ * has no face-value items.  Lets a test check that a mesh exercises those paths.
+ * Errors: BAD_PARAM (null pointer). */
+int fvlbm_fv_items(fvlbm_handle *h, int *nitem, int *n_split, int *n_overflow);
+
 /* Force on the wall faces of `instance`: F = sum over wall faces of sum_alpha e_alpha
  * (e_alpha . n) f_{alpha,bc} Delta l (momentum flux of the Eq. (advection) face values, FP64).
  * out[4] = {Fx, Fy, C_D, C_L}, coefficients along / normal to alpha_deg, normalised by

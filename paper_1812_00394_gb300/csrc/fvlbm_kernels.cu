@@ -1767,7 +1767,7 @@ struct fvlbm_handle {
     } hs[2];                // [0]: 256-cell blocks, [1]: 128-cell blocks
     struct FvSet {          // work items of the face-value fused kernel (config 3)
         bool ok = false;
-        int nitem = 0, n_split = 0;
+        int nitem = 0, n_split = 0, n_ovf = 0;  // items; blocks split; items using the overflow
         int4 *d_hdr = nullptr;
         int *d_halo = nullptr, *d_ovf = nullptr, *d_inst_item0 = nullptr;
         uint4 *d_adj = nullptr;
@@ -2382,7 +2382,7 @@ int build_fv_items(fvlbm_handle *h, const std::vector<int> &nbr, const std::vect
     std::vector<int> halo, ovf, item_inst;
     std::vector<uint4> adj;
     std::vector<int> local(np, -1), ring1, ring2;
-    int n_split = 0;
+    int n_split = 0, n_ovf = 0;
     bool fits_all = true;
     // try one item of cnt cells at base (instance inst); returns false if it does not fit
     auto try_item = [&](int base, int cnt, int inst, bool commit) -> bool {
@@ -2410,6 +2410,7 @@ int build_fv_items(fvlbm_handle *h, const std::vector<int> &nbr, const std::vect
             halo.resize(h0 + kFvHs, -1);
             int ovf0 = -1;
             if (nh > kFvHs) {
+                ++n_ovf;
                 ovf0 = static_cast<int>(ovf.size());
                 ovf.resize(ovf.size() + kFvHs, -1);
             }
@@ -2494,6 +2495,7 @@ int build_fv_items(fvlbm_handle *h, const std::vector<int> &nbr, const std::vect
                             static_cast<int>(FvSmem<T>::bytes)));
     h->fv.nitem = nitem;
     h->fv.n_split = n_split;
+    h->fv.n_ovf = n_ovf;
     h->fv.ok = true;
     return FVLBM_OK;
 }
@@ -3512,6 +3514,14 @@ int fvlbm_adjoint_params(fvlbm_handle *h, int instance, int n_steps, const doubl
     }
     if (dJ_dalpha) *dJ_dalpha = da;
     if (dJ_dratio) *dJ_dratio = dr;
+    return FVLBM_OK;
+}
+
+int fvlbm_fv_items(fvlbm_handle *h, int *nitem, int *n_split, int *n_overflow) {
+    if (!h || !nitem || !n_split || !n_overflow) return FVLBM_ERR_BAD_PARAM;
+    *nitem = h->fv.ok ? h->fv.nitem : 0;
+    *n_split = h->fv.ok ? h->fv.n_split : 0;
+    *n_overflow = h->fv.ok ? h->fv.n_ovf : 0;
     return FVLBM_OK;
 }
 

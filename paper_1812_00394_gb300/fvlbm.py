@@ -73,7 +73,7 @@ EXPORTS = ["fvlbm_create", "fvlbm_create_batch", "fvlbm_step", "fvlbm_forces", "
            "fvlbm_check_mesh", "fvlbm_adjoint_params", "fvlbm_set_wait_limit",
            "fvlbm_get_cells", "fvlbm_set_cells", "fvlbm_set_wall_distance", "fvlbm_cell_geometry",
            "fvlbm_forces_edges", "fvlbm_set_exchange_list", "fvlbm_pack_cells_dev",
-           "fvlbm_unpack_cells_dev", "fvlbm_fp64_peak"]
+           "fvlbm_unpack_cells_dev", "fvlbm_fp64_peak", "fvlbm_fv_items"]
 
 _lib = None
 
@@ -123,6 +123,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     lib.fvlbm_set_adjoint_budget.argtypes = [vp, C.c_longlong]
     lib.fvlbm_adjoint_params.argtypes = [vp, i, i, vp, i, vp, vp, vp, vp, vp, vp, vp]
     lib.fvlbm_set_wait_limit.argtypes = [vp, C.c_longlong]
+    lib.fvlbm_fv_items.argtypes = [vp, vp, vp, vp]
     lib.fvlbm_destroy.argtypes = [vp]
     lib.fvlbm_destroy.restype = None
     lib.fvlbm_strerror.argtypes = [i]
@@ -437,6 +438,13 @@ def fvlbm_load_state(h, blob: bytes) -> None:
 def fvlbm_set_wait_limit(h, polls: int) -> None:
     """Diagnostic: polls of the fused kernels' first staging wait (see the header)."""
     _check(load().fvlbm_set_wait_limit(h, int(polls)), "fvlbm_set_wait_limit")
+
+
+def fvlbm_fv_items(h) -> tuple:
+    """Diagnostic: (items, blocks split, items using the halo overflow) of the face-value stages."""
+    v = (C.c_int * 3)()
+    _check(load().fvlbm_fv_items(h, C.byref(v, 0), C.byref(v, 4), C.byref(v, 8)), "fvlbm_fv_items")
+    return tuple(int(x) for x in v)
 
 
 def fvlbm_set_rollback(h, every: int) -> None:
