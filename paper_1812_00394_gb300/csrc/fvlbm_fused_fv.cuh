@@ -34,8 +34,10 @@
 // (node offsets q[8] and least-squares weights W[8]) is likewise one 64-byte row per cell.
 //
 // Staging, all issued before any wait: the item's own rows (its stage values, its accumulator
-// rows and tau) by bulk copies on one mbarrier; the halo rows, the adjacency and the ring-1
-// geometry by cp.async; the item cell's own geometry straight into registers.  Stage 1 takes
+// rows and tau) by bulk copies on one mbarrier, shared out over the warps; the halo rows, the
+// adjacency, the ring-1 geometry and the instance parameters by cp.async; the item cell's own
+// geometry straight into registers.  A CTA's first loads (its halo ids and its header) do not
+// depend on each other, so the gathers wait on two memory round trips.  Stage 1 takes
 // its own f^n rows from the accumulator copy (the algebra reads them there too) and relaxes
 // every staged cell to f^(1) on chip (Eq. (fnewstage), J = 1), so no f^(1) array passes
 // through HBM and f^n is never recovered from a rounded f^(1).
@@ -248,8 +250,9 @@ __device__ __forceinline__ void fv_boundary_pairs(const Geo<T> &G, int bf, T nx,
 // Stage 1: f^(1) = [f^n + (dt/tau)/4 f^eq(f^n)] / (1 + (dt/tau)/4) (Eq. (fnewstage), J = 1)
 // of a cell given as f[9] (alpha order), written to staged row e.
 template <class T>
-__device__ __forceinline__ void fv_relax_to_row(T *f, T *sf, T *sf0, int e, T rho0, T dt, T tau_e) {
-    relax9(f, rho0, dt, tau_e);
+__device__ __forceinline__ void fv_relax_to_row(T *f, T *sf, T *sf0, int e, T rho0, T dt, T tau_e,
+                                                T *eq_out = nullptr) {
+    relax9(f, rho0, dt, tau_e, eq_out);
     sf0[e] = f[0];
     if constexpr (sizeof(T) == 4) {
         *reinterpret_cast<float4 *>(sf + e * 8 + 4 * fv_half(e, 0)) = make_float4(f[1], f[3], f[2], f[4]);
@@ -565,7 +568,12 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
         T f[kQ];
 #pragma unroll
         for (int a = 0; a < kQ; ++a) f[a] = sacc[a * kFvThreads + t];
-        fv_relax_to_row(f, sf, sf0, t, rho0, G.dtc != nullptr ? G.dtc[i] : dtg, sacc[2 * kQ * kFvThreads + t]);
+        // its f^eq(f^n) goes to the free accumulator rows kQ.. (stage 1 copies no C rows), where
+        // the stage-1 algebra reads it instead of forming it again
+        T eq[kQ];
+        fv_relax_to_row(f, sf, sf0, t, rho0, G.dtc != nullptr ? G.dtc[i] : dtg, sacc[2 * kQ * kFvThreads + t], eq);
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) sacc[(kQ + a) * kFvThreads + t] = eq[a];
     }
     // ring-1 geometry for the pair-split work below, read before any face value is written
     const int ru = 4 * nr1;  // ring-1 work units: (cell, pair)
@@ -629,7 +637,7 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 3 : 1)
             vo0 = mac[2 * np + i];
         }
         const T tau_i = sacc[2 * kQ * kFvThreads + t];
-        stage_algebra<T, STAGE, false, kFvThreads, false, true>(
+        stage_algebra<T, STAGE, false, kFvThreads, false, true, STAGE == 1>(
             i, np, fi, acc, P, tau_i, cell_dt(G, P, i), sacc, kFvThreads, t, sacc + kQ * kFvThreads, kFvThreads,
             t, fs_out, fn, Bacc, Cacc, mac, nullptr, G.area, nullptr, false, T(0), macv);
         if (STATS) {

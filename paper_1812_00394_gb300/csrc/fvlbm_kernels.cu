@@ -201,14 +201,17 @@ __device__ __forceinline__ void store9(T *__restrict__ f, size_t np, int i, cons
 // ------------------------------------------------------------------ stage 1 (local)
 // f^(1) = [f^n + (dt/tau)(1/4) f^eq(rho^n, u^n)] / (1 + (dt/tau)/4): Eq. (fnewstage), J = 1.
 template <class T>
-__device__ __forceinline__ void relax9(T *f, T rho0, T dt, T tau_i) {
+__device__ __forceinline__ void relax9(T *f, T rho0, T dt, T tau_i, T *eq_out = nullptr) {
     T eq[kQ], dr, r, u, v;
     moments(f, rho0, dr, r, u, v);
     feq_dev(dr, r, u, v, eq);
     const T zq = sdiv(dt, tau_i) * T(0.25);
     const T inv = sdiv(T(1), T(1) + zq);
 #pragma unroll
-    for (int a = 0; a < kQ; ++a) f[a] = (f[a] + zq * eq[a]) * inv;
+    for (int a = 0; a < kQ; ++a) {
+        if (eq_out != nullptr) eq_out[a] = eq[a];  // f^eq(f^n), for a later stage-1 algebra
+        f[a] = (f[a] + zq * eq[a]) * inv;
+    }
 }
 
 template <class T>
@@ -384,7 +387,9 @@ __device__ __forceinline__ void store_stage(T *__restrict__ f, size_t np, int i,
     }
 }
 
-template <class T, int STAGE, bool STATS, int NT, bool FN_FROM_F1 = false, bool ROWS = false>
+// EQ1_IN_A2 (stage 1): f^eq(f^n) is given in a2 (the face-value stage relaxed the cell with it).
+template <class T, int STAGE, bool STATS, int NT, bool FN_FROM_F1 = false, bool ROWS = false,
+          bool EQ1_IN_A2 = false>
 __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, const T *acc,
                                               const InstParam &P, T t_i, T dt_i, const T *a1, size_t ld1,
                                               int c1, const T *a2, size_t ld2, int c2,
@@ -417,8 +422,13 @@ __device__ __forceinline__ void stage_algebra(int i, size_t np, const T *fi, con
         } else {
 #pragma unroll
             for (int a = 0; a < kQ; ++a) f0[a] = FN_FROM_F1 ? fn[a * np + i] : a1[a * ld1 + c1];
-            moments(f0, rho0, dr, r, u, v);
-            feq_dev(dr, r, u, v, eq);
+            if constexpr (EQ1_IN_A2) {
+#pragma unroll
+                for (int a = 0; a < kQ; ++a) eq[a] = a2[a * ld2 + c2];
+            } else {
+                moments(f0, rho0, dr, r, u, v);
+                feq_dev(dr, r, u, v, eq);
+            }
             // f^(1) = (f^n + zq1 f^eq) / (1 + zq1), relaxed with tau^(1) (= tau unless the SST
             // is solved per stage, when stage 2 has its own tau)
             T s1 = z * inv;
